@@ -1,0 +1,138 @@
+"""Closed-form flows, viscosity laws, forcing and boundary data for the oracle.
+
+TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
+
+* ``tg2d``: decaying 2D Taylor-Green vortex u = (sin x cos y, -cos x sin y) e^{-2 nu t},
+  p = 1/4 (cos 2x + cos 2y) e^{-4 nu t}; an exact Navier-Stokes solution for
+  constant nu (the periodic 2D workload on [0, 2 pi]^2).
+* ``tg3d``: the disturbed Taylor-Green initial field of Sec. 4.3, Eq.
+  (transition:v0), shifted by pi/2 in x and y so that it reads
+  (sin x cos y cos z, -cos x sin y cos z, 0) on [0, 2 pi]^3.
+* ``tgtravel``: the traveling Taylor-Green vortex of Sec. 4.1 with phase speed 1,
+  decay rate 8 pi^2 nu_0.
+* viscosity laws: constant; nu(x, y, t) = nu_0 (1 + 1/2 sin 2 pi x sin 2 pi y cos t);
+  nu(v) = nu_0 + nu_1 (|v| / v_max)^2 (Sec. 4.2).
+* forcing ``tgtravel_varnu``: f = (nu_0 - nu) lap v - (grad v + grad v^T) grad nu, the
+  right-hand side that makes the traveling vortex exact under the variable viscosity
+  (pattern of Eq. var-visc-test:rhs: f = d_t v + div(v v) - div(nu (grad v + grad v^T)) + grad p).
+"""
+import numpy as np
+
+TWO_PI = 2.0 * np.pi
+
+
+def tg2d_velocity(X, t, nu):
+    x, y = X[..., 0], X[..., 1]
+    F = np.exp(-2.0 * nu * t)
+    return np.stack([np.sin(x) * np.cos(y) * F, -np.cos(x) * np.sin(y) * F])
+
+
+def tg2d_pressure(X, t, nu):
+    x, y = X[..., 0], X[..., 1]
+    return 0.25 * (np.cos(2 * x) + np.cos(2 * y)) * np.exp(-4.0 * nu * t)
+
+
+def tg3d_velocity(X):
+    x, y, z = X[..., 0], X[..., 1], X[..., 2]
+    return np.stack([np.sin(x) * np.cos(y) * np.cos(z),
+                     -np.cos(x) * np.sin(y) * np.cos(z),
+                     np.zeros_like(x)])
+
+
+def tgtravel_velocity(X, t, nu0):
+    x, y = X[..., 0], X[..., 1]
+    a = TWO_PI * (x - t)
+    b = TWO_PI * (y - 0.125 - t)
+    F = np.exp(-8.0 * np.pi ** 2 * nu0 * t)
+    return np.stack([1.0 + np.sin(a) * np.cos(b) * F, 1.0 - np.cos(a) * np.sin(b) * F])
+
+
+def tgtravel_grad(X, t, nu0):
+    """G[c, k] = d v_c / d x_k of the traveling vortex."""
+    x, y = X[..., 0], X[..., 1]
+    a = TWO_PI * (x - t)
+    b = TWO_PI * (y - 0.125 - t)
+    F = np.exp(-8.0 * np.pi ** 2 * nu0 * t)
+    G = np.zeros((2, 2) + x.shape)
+    G[0, 0] = TWO_PI * np.cos(a) * np.cos(b) * F
+    G[0, 1] = -TWO_PI * np.sin(a) * np.sin(b) * F
+    G[1, 0] = TWO_PI * np.sin(a) * np.sin(b) * F
+    G[1, 1] = -TWO_PI * np.cos(a) * np.cos(b) * F
+    return G
+
+
+def nu_varxyt(X, t, nu0):
+    x, y = X[..., 0], X[..., 1]
+    return nu0 * (1.0 + 0.5 * np.sin(TWO_PI * x) * np.sin(TWO_PI * y) * np.cos(t))
+
+
+def nu_varxyt_grad(X, t, nu0):
+    x, y = X[..., 0], X[..., 1]
+    c = 0.5 * nu0 * np.cos(t) * TWO_PI
+    return np.stack([c * np.cos(TWO_PI * x) * np.sin(TWO_PI * y),
+                     c * np.sin(TWO_PI * x) * np.cos(TWO_PI * y)])
+
+
+def forcing_tgtravel_varnu(X, t, nu0):
+    v = tgtravel_velocity(X, t, nu0)
+    lap = -8.0 * np.pi ** 2 * (v - 1.0)          # Laplacian of the oscillating part
+    nu = nu_varxyt(X, t, nu0)
+    gnu = nu_varxyt_grad(X, t, nu0)
+    G = tgtravel_grad(X, t, nu0)
+    f = np.zeros_like(v)
+    for c in range(2):
+        f[c] = (nu0 - nu) * lap[c]
+        for k in range(2):
+            f[c] -= gnu[k] * (G[c, k] + G[k, c])
+    return f
+
+
+class Flow:
+    """A flow case: initial data, viscosity law, forcing, boundary data, exact solution."""
+
+    def __init__(self, kind, nu0, nu_kind="const", nu1=0.0, vmax=1.0):
+        self.kind = kind
+        self.nu0 = float(nu0)
+        self.nu_kind = nu_kind
+        self.nu1 = float(nu1)
+        self.vmax = float(vmax)
+
+    # --- viscosity ------------------------------------------------------
+    def variable_nu(self):
+        return self.nu_kind != "const"
+
+    def nu(self, X, t, v):
+        if self.nu_kind == "const":
+            return np.full(X.shape[:-1], self.nu0)
+        if self.nu_kind == "varxyt":
+            return nu_varxyt(X, t, self.nu0)
+        if self.nu_kind == "velocity":
+            mag2 = np.sum(np.asarray(v) ** 2, axis=0).reshape(X.shape[:-1])
+            return self.nu0 + self.nu1 * mag2 / self.vmax ** 2
+        raise ValueError(self.nu_kind)
+
+    # --- fields -----------------------------------------------------------
+    def exact(self, X, t):
+        if self.kind == "tg2d":
+            return tg2d_velocity(X, t, self.nu0)
+        if self.kind == "tgtravel":
+            return tgtravel_velocity(X, t, self.nu0)
+        if self.kind == "tg3d":
+            if t != 0.0:
+                raise ValueError("tg3d has no closed form for t > 0")
+            return tg3d_velocity(X)
+        raise ValueError(self.kind)
+
+    def initial(self, X):
+        return self.exact(X, 0.0)
+
+    def boundary(self, X, t):
+        return self.exact(X, t)
+
+    def has_forcing(self):
+        return self.kind == "tgtravel" and self.nu_kind == "varxyt"
+
+    def forcing(self, X, t):
+        if self.has_forcing():
+            return forcing_tgtravel_varnu(X, t, self.nu0)
+        return np.zeros((X.shape[-1],) + X.shape[:-1])

@@ -1,0 +1,295 @@
+"""Alg. 3 (IMEX RK) and Alg. 4 (SISDC) for incompressible flow, plain FP64.
+
+TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
+
+The right-hand side splits as in Sec. 3.2, F = F_c + F_d1 + F_d2 + F_d3 + F_p + F_s:
+
+* F_c  = -div(v v)                   (dg.Convection, LLF flux, over-integration)
+* F_d1 = div(nu grad v)              = -M^{-1} (A(nu) v - r_b(nu, v_b))   (SIPG)
+* F_d2 = div(nu (grad v)^T)          = sum_k D_k (nu D_c v_k)
+* F_d3 = -grad(nu div v)             = -D_c (nu sum_k D_k v_k)
+* F_s  = f(x, t)
+
+with D_k the nodal DG derivative of dg.dg_derivative_matrix.  The pressure
+Poisson problems of Alg. 3 (line "psi'' <- solve ...") and Alg. 4 are solved in
+the weak form  L psi = B v' - int_{dOmega} (n . v_b) q, with L either the SIPG
+matrix on Q_{P-1} (homogeneous Neumann faces) or, in the "consistent" mode,
+L = B M^{-1} B^T, which makes the projected velocity discretely
+divergence-free.  The velocity update is v'' = v' - G psi with G = M^{-1} B^T.
+All linear systems are solved directly (sparse LU); the singular pressure
+problems are bordered with the constant vector.
+"""
+import numpy as np
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+from . import dg, gll
+from .scalar import sdc_nodes
+from .tableaux import get as get_tableau
+
+
+class Discretization:
+    def __init__(self, mesh, flow, poisson="sipg"):
+        if mesh.P < 2:
+            raise ValueError("velocity degree P must be at least 2")
+        self.mesh = mesh
+        self.flow = flow
+        self.poisson_mode = poisson
+        d = mesh.d
+        self.d = d
+        self.Nv = mesh.P + 1
+        self.Np = mesh.P
+        self.X = mesh.node_coords(self.Nv)          # (ne, ndv, d)
+        self.nv = mesh.ne * self.Nv ** d
+        self.npr = mesh.ne * self.Np ** d
+        self.Mv = dg.mass_diag(mesh, self.Nv)
+        self.Mp = dg.mass_diag(mesh, self.Np)
+        self.B = dg.div_matrix(mesh, self.Nv, self.Np)
+        self.BT = self.B.T.tocsr()
+        self.Dk = [dg.dg_derivative_matrix(mesh, self.Nv, k) for k in range(d)]
+        self.conv = dg.Convection(mesh)
+        if poisson == "sipg":
+            L = dg.sipg_matrix(mesh, self.Np, 1.0, dirichlet=False)
+        elif poisson == "consistent":
+            L = (self.B @ sp.diags(1.0 / np.tile(self.Mv, d)) @ self.BT).tocsr()
+        else:
+            raise ValueError(poisson)
+        self.L = L
+        one = sp.csr_matrix(np.ones((self.npr, 1)))
+        bordered = sp.bmat([[L, one], [one.T, None]], format="csc")
+        self._poisson_lu = spla.splu(bordered)
+        self._helm_cache = {}
+        self._A_const = None
+        self.has_boundary = not all(mesh.periodic)
+
+    # ------------------------------------------------------------------ fields
+    def nodal(self, field_fn, t):
+        return np.asarray(field_fn(self.X, t)).reshape(self.d, -1) if field_fn else None
+
+    def nu_field(self, t, v):
+        X = self.X
+        return np.asarray(self.flow.nu(X, t, np.asarray(v).reshape(self.d, *X.shape[:-1]))).ravel()
+
+    def vb(self, t):
+        if not self.has_boundary:
+            return None
+        return np.asarray(self.flow.boundary(self.X, t)).reshape(self.d, -1)
+
+    def fs(self, t):
+        return np.asarray(self.flow.forcing(self.X, t)).reshape(self.d, -1)
+
+    # -------------------------------------------------------------- operators
+    def A(self, nu):
+        if not self.flow.variable_nu():
+            if self._A_const is None:
+                self._A_const = dg.sipg_matrix(self.mesh, self.Nv, self.flow.nu0, dirichlet=True)
+            return self._A_const
+        return dg.sipg_matrix(self.mesh, self.Nv, nu, dirichlet=True)
+
+    def Fc(self, v, vb):
+        return self.conv(v, vb)
+
+    def Fd1(self, v, nu, vb, A=None):
+        A = self.A(nu) if A is None else A
+        out = np.empty((self.d, self.nv))
+        for c in range(self.d):
+            r = A @ v[c]
+            if vb is not None:
+                r -= dg.sipg_dirichlet_rhs(self.mesh, self.Nv, nu, vb[c])
+            out[c] = -r / self.Mv
+        return out
+
+    def divergence_nodal(self, v):
+        return sum(self.Dk[k] @ v[k] for k in range(self.d))
+
+    def Fd3(self, v, nu):
+        phi = nu * self.divergence_nodal(v)
+        return np.stack([-(self.Dk[c] @ phi) for c in range(self.d)])
+
+    def Fd2(self, v, nu):
+        out = np.zeros((self.d, self.nv))
+        for c in range(self.d):
+            for k in range(self.d):
+                out[c] += self.Dk[k] @ (nu * (self.Dk[c] @ v[k]))
+        return out
+
+    def grad_p(self, psi):
+        g = self.BT @ psi
+        return g.reshape(self.d, self.nv) / self.Mv[None, :]
+
+    def div_rhs(self, v, vb_or_none, mode):
+        """B v - int (n . w) q with w = v_b (mode 'data') or w = v (mode 'trace')."""
+        b = self.B @ np.asarray(v).ravel()
+        if self.has_boundary:
+            w = vb_or_none if mode == "data" else v
+            b -= dg.div_boundary_vector(self.mesh, self.Nv, self.Np, w)
+        return b
+
+    def poisson(self, b):
+        """Solve L psi = b on the mean-free subspace; returns psi with zero mass-weighted mean."""
+        b = b - b.mean()
+        rhs = np.concatenate([b, [0.0]])
+        sol = self._poisson_lu.solve(rhs)
+        psi = sol[:-1]
+        return psi - np.dot(self.Mp, psi) / self.Mp.sum()
+
+    def helmholtz(self, g, nu, gamma, vb):
+        """(M + gamma A(nu)) u = M g + gamma r_b(nu, v_b), one solve per component."""
+        key = gamma if not self.flow.variable_nu() else None
+        lu = self._helm_cache.get(key) if key is not None else None
+        if lu is None:
+            H = (sp.diags(self.Mv) + gamma * self.A(nu)).tocsc()
+            lu = spla.splu(H)
+            if key is not None:
+                self._helm_cache[key] = lu
+        out = np.empty_like(g)
+        for c in range(self.d):
+            rhs = self.Mv * g[c]
+            if vb is not None:
+                rhs = rhs + gamma * dg.sipg_dirichlet_rhs(self.mesh, self.Nv, nu, vb[c])
+            out[c] = lu.solve(rhs)
+        return out
+
+    def stage_rhs(self, v, nu, t, vb, need_fd2):
+        """E = F_c + F_d2 + F_d3, F_d1, F_d3, F_s at one stage."""
+        Fc = self.Fc(v, vb)
+        Fd1 = self.Fd1(v, nu, vb)
+        Fd3 = self.Fd3(v, nu)
+        E = Fc + Fd3
+        if need_fd2:
+            E = E + self.Fd2(v, nu)
+        Fs = self.fs(t)
+        return E, Fd1, Fd3, Fs
+
+
+def divergence_norm(disc, v, vb, t):
+    """RMS of the weak divergence residual B v - int (n . v_b) q (zero after a consistent projection)."""
+    b = disc.div_rhs(v, vb, "data")
+    return float(np.sqrt(np.mean(b ** 2)))
+
+
+# ---------------------------------------------------------------------------
+# Alg. 3: IMEX RK for incompressible flow with variable viscosity
+# ---------------------------------------------------------------------------
+def rk_step(disc, tab, v, t, dt, final_projection=None, need_fd2=None):
+    """One step of Alg. 3; returns (v_new, info)."""
+    if isinstance(tab, str):
+        tab = get_tableau(tab)
+    c, AI, bI, AE, bE = tab.as_float()
+    s = tab.s
+    varnu = disc.flow.variable_nu()
+    if final_projection is None:
+        final_projection = varnu
+    if need_fd2 is None:
+        need_fd2 = varnu
+    v = np.asarray(v, dtype=np.float64).reshape(disc.d, disc.nv)
+    E, Fd1, Fd3, Fs = [None] * s, [None] * s, [None] * s, [None] * s
+    nu1 = disc.nu_field(t, v)
+    E[0], Fd1[0], Fd3[0], Fs[0] = disc.stage_rhs(v, nu1, t, disc.vb(t), need_fd2)
+    vi = v
+    psi = None
+    for i in range(1, s):
+        ti = t + c[i] * dt
+        vb_i = disc.vb(ti)
+        Fs[i] = disc.fs(ti)
+        vp = v.copy()
+        for j in range(i):
+            vp += dt * AE[i][j] * (E[j] + Fd1[j] + Fd3[j])
+        for j in range(i + 1):
+            vp += dt * AI[i][j] * Fs[j]
+        psi = disc.poisson(disc.div_rhs(vp, vb_i, "data"))
+        vpp = vp - disc.grad_p(psi)
+        nu_i = disc.nu_field(ti, vpp)
+        g = vpp.copy()
+        for j in range(i):
+            g += dt * ((AI[i][j] - AE[i][j]) * Fd1[j] - AE[i][j] * Fd3[j])
+        vi = disc.helmholtz(g, nu_i, dt * AI[i][i], vb_i)
+        E[i], Fd1[i], Fd3[i], _ = disc.stage_rhs(vi, nu_i, ti, vb_i, need_fd2)
+    vnew = vi.copy()
+    for i in range(s):
+        fe = bE[i] - AE[s - 1][i]
+        fi = bI[i] - AI[s - 1][i]
+        if fe != 0.0:
+            vnew += dt * fe * E[i]
+        if fi != 0.0:
+            vnew += dt * fi * (Fd1[i] + Fs[i])
+    if final_projection:
+        psi_f = disc.poisson(disc.div_rhs(vnew, None, "trace"))
+        vnew = vnew - disc.grad_p(psi_f)
+    return vnew, {"psi": psi}
+
+
+# ---------------------------------------------------------------------------
+# Alg. 4: SISDC corrector with an RK (or IMEX Euler) predictor
+# ---------------------------------------------------------------------------
+def sdc_step(disc, M, K, predictor, v, t, dt, final_projection=None):
+    """One step of the SISDC method of Sec. 3.2.3 (predictor sweep + K corrector sweeps).
+
+    Readings: the quadrature term sums w_{q,m} F(x, t_q, v^k_q, 0) over the
+    sub-nodes q with F = F_c + F_d1 + F_d2 + F_d3 + F_s evaluated with
+    nu(x, t_q, v^k_q); w_{q,m} integrates l_q over (t_{m-1}, t_m).
+    """
+    d = disc.d
+    varnu = disc.flow.variable_nu()
+    if final_projection is None:
+        final_projection = varnu
+    need_fd2 = varnu
+    tau, W = sdc_nodes(M)
+    tm = t + dt * tau
+    dts = np.diff(tm)
+    v0 = np.asarray(v, dtype=np.float64).reshape(d, disc.nv)
+    # predictor: one RK step per subinterval
+    vk = [v0]
+    for m in range(1, M + 1):
+        vn, _ = rk_step(disc, predictor, vk[-1], tm[m - 1], dts[m - 1],
+                        final_projection=final_projection, need_fd2=need_fd2)
+        vk.append(vn)
+
+    def f_ex(vm, num, tq):
+        vb = disc.vb(tq)
+        out = disc.Fc(vm, vb) + disc.Fd3(vm, num)
+        if need_fd2:
+            out = out + disc.Fd2(vm, num)
+        return out
+
+    # initial viscosity and RHS
+    nuk = [disc.nu_field(tm[m], vk[m]) for m in range(M + 1)]
+    FEX = [f_ex(vk[m], nuk[m], tm[m]) if m < M else None for m in range(M + 1)]
+    FIM = [None] + [disc.Fd1(vk[m], nuk[m - 1], disc.vb(tm[m])) for m in range(1, M + 1)]
+    for _k in range(K):
+        # full right-hand side at the sub-nodes for the quadrature term
+        Fq = []
+        for q in range(M + 1):
+            vbq = disc.vb(tm[q])
+            Fq.append(f_ex(vk[q], nuk[q], tm[q]) + disc.Fd1(vk[q], nuk[q], vbq) + disc.fs(tm[q]))
+        vnew = [vk[0]]
+        nunew = [nuk[0]]
+        FEXn = [FEX[0]]
+        FIMn = [None]
+        for m in range(1, M + 1):
+            vb_m = disc.vb(tm[m])
+            Fd1p = disc.Fd1(vk[m], nunew[m - 1], vb_m)
+            Fd3p = disc.Fd3(vk[m], nunew[m - 1])
+            S = sum(dt * W[m, q] * Fq[q] for q in range(M + 1))
+            vp = vnew[m - 1] + dts[m - 1] * (FEXn[m - 1] + Fd1p + Fd3p - (FEX[m - 1] + FIM[m])) + S
+            psi = disc.poisson(disc.div_rhs(vp, vb_m, "data"))
+            vpp = vp - disc.grad_p(psi)
+            g = vpp - dts[m - 1] * (Fd1p + Fd3p)
+            vppp = disc.helmholtz(g, nunew[m - 1], dts[m - 1], vb_m)
+            if final_projection:
+                psi_f = disc.poisson(disc.div_rhs(vppp, None, "trace"))
+                vppp = vppp - disc.grad_p(psi_f)
+            vnew.append(vppp)
+            nunew.append(disc.nu_field(tm[m], vppp))
+            FEXn.append(f_ex(vppp, nunew[m], tm[m]) if m < M else None)
+            FIMn.append(disc.Fd1(vppp, nunew[m], vb_m))
+        vk, nuk, FEX, FIM = vnew, nunew, FEXn, FIMn
+    return vk[-1]
+
+
+def rms(x):
+    return float(np.sqrt(np.mean(np.asarray(x) ** 2)))
+
+
+def relative_l2(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
