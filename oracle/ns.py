@@ -150,14 +150,12 @@ class Discretization:
             out[c] = lu.solve(rhs)
         return out
 
-    def stage_rhs(self, v, nu, t, vb, need_fd2):
+    def stage_rhs(self, v, nu, t, vb):
         """E = F_c + F_d2 + F_d3, F_d1, F_d3, F_s at one stage."""
         Fc = self.Fc(v, vb)
         Fd1 = self.Fd1(v, nu, vb)
         Fd3 = self.Fd3(v, nu)
-        E = Fc + Fd3
-        if need_fd2:
-            E = E + self.Fd2(v, nu)
+        E = Fc + self.Fd2(v, nu) + Fd3
         Fs = self.fs(t)
         return E, Fd1, Fd3, Fs
 
@@ -171,7 +169,7 @@ def divergence_norm(disc, v, vb, t):
 # ---------------------------------------------------------------------------
 # Alg. 3: IMEX RK for incompressible flow with variable viscosity
 # ---------------------------------------------------------------------------
-def rk_step(disc, tab, v, t, dt, final_projection=None, need_fd2=None):
+def rk_step(disc, tab, v, t, dt, final_projection=None):
     """One step of Alg. 3; returns (v_new, info)."""
     if isinstance(tab, str):
         tab = get_tableau(tab)
@@ -180,12 +178,10 @@ def rk_step(disc, tab, v, t, dt, final_projection=None, need_fd2=None):
     varnu = disc.flow.variable_nu()
     if final_projection is None:
         final_projection = varnu
-    if need_fd2 is None:
-        need_fd2 = varnu
     v = np.asarray(v, dtype=np.float64).reshape(disc.d, disc.nv)
     E, Fd1, Fd3, Fs = [None] * s, [None] * s, [None] * s, [None] * s
     nu1 = disc.nu_field(t, v)
-    E[0], Fd1[0], Fd3[0], Fs[0] = disc.stage_rhs(v, nu1, t, disc.vb(t), need_fd2)
+    E[0], Fd1[0], Fd3[0], Fs[0] = disc.stage_rhs(v, nu1, t, disc.vb(t))
     vi = v
     psi = None
     for i in range(1, s):
@@ -204,7 +200,7 @@ def rk_step(disc, tab, v, t, dt, final_projection=None, need_fd2=None):
         for j in range(i):
             g += dt * ((AI[i][j] - AE[i][j]) * Fd1[j] - AE[i][j] * Fd3[j])
         vi = disc.helmholtz(g, nu_i, dt * AI[i][i], vb_i)
-        E[i], Fd1[i], Fd3[i], _ = disc.stage_rhs(vi, nu_i, ti, vb_i, need_fd2)
+        E[i], Fd1[i], Fd3[i], _ = disc.stage_rhs(vi, nu_i, ti, vb_i)
     vnew = vi.copy()
     for i in range(s):
         fe = bE[i] - AE[s - 1][i]
@@ -227,13 +223,13 @@ def sdc_step(disc, M, K, predictor, v, t, dt, final_projection=None):
 
     Readings: the quadrature term sums w_{q,m} F(x, t_q, v^k_q, 0) over the
     sub-nodes q with F = F_c + F_d1 + F_d2 + F_d3 + F_s evaluated with
-    nu(x, t_q, v^k_q); w_{q,m} integrates l_q over (t_{m-1}, t_m).
+    nu(x, t_q, v^k_q); w_{q,m} integrates l_q over (t_{m-1}, t_m); the updated
+    F^{IM,k+1}_m uses nu^{k+1}_{m-1}, the lag of its initialisation.
     """
     d = disc.d
     varnu = disc.flow.variable_nu()
     if final_projection is None:
         final_projection = varnu
-    need_fd2 = varnu
     tau, W = sdc_nodes(M)
     tm = t + dt * tau
     dts = np.diff(tm)
@@ -242,15 +238,12 @@ def sdc_step(disc, M, K, predictor, v, t, dt, final_projection=None):
     vk = [v0]
     for m in range(1, M + 1):
         vn, _ = rk_step(disc, predictor, vk[-1], tm[m - 1], dts[m - 1],
-                        final_projection=final_projection, need_fd2=need_fd2)
+                        final_projection=final_projection)
         vk.append(vn)
 
     def f_ex(vm, num, tq):
         vb = disc.vb(tq)
-        out = disc.Fc(vm, vb) + disc.Fd3(vm, num)
-        if need_fd2:
-            out = out + disc.Fd2(vm, num)
-        return out
+        return disc.Fc(vm, vb) + disc.Fd2(vm, num) + disc.Fd3(vm, num)
 
     # initial viscosity and RHS
     nuk = [disc.nu_field(tm[m], vk[m]) for m in range(M + 1)]
@@ -282,7 +275,9 @@ def sdc_step(disc, M, K, predictor, v, t, dt, final_projection=None):
             vnew.append(vppp)
             nunew.append(disc.nu_field(tm[m], vppp))
             FEXn.append(f_ex(vppp, nunew[m], tm[m]) if m < M else None)
-            FIMn.append(disc.Fd1(vppp, nunew[m], vb_m))
+            # F^{IM,k+1}_m with the viscosity lagged by one node, as in the initialisation
+            # of Alg. 4 and in the corrector Eq. (model:corrector)
+            FIMn.append(disc.Fd1(vppp, nunew[m - 1], vb_m))
         vk, nuk, FEX, FIM = vnew, nunew, FEXn, FIMn
     return vk[-1]
 

@@ -1,0 +1,95 @@
+// Common definitions of the GB300 (sm_103a) DG-SEM kernels.
+//
+// Discretisation (Sec. 3.3 of the paper): Cartesian hexahedral / quadrilateral
+// elements, tensor-product Lagrange bases on Gauss-Lobatto-Legendre points,
+// velocity degree P (N = P+1 points per direction), pressure degree P-1.
+// Storage: element-contiguous, nodes lexicographic with x fastest; a vector
+// field stores its d components one after the other.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define IMEX_MAXN 9                        // nodes per direction: P <= 8
+#define IMEX_MAXQ 14                       // Gauss points for over-integration, ceil(3*9/2)
+#define IMEX_WARP 32
+
+namespace imex {
+
+// Mesh geometry as seen by every kernel (passed by value).
+struct Geom {
+  int d;                 // 2 or 3
+  int ne;                // number of elements
+  int n[3];              // elements per direction (n[2] = 1 in 2D)
+  int bc[3];             // 0 periodic, 1 Dirichlet, 2 homogeneous Neumann (per direction)
+  double lo[3];
+  double h[3];           // element sizes
+  const void* tab64;     // device Tables<double>
+  const void* tab32;     // device Tables<float>
+};
+
+// 1D tables per number of points N (index N, 2..IMEX_MAXN), in FP64 and FP32.
+//   x, w      : GLL points / weights
+//   D         : D[i*N+j] = l_j'(x_i)
+//   Ipv       : pressure basis (N-1 points) at the N velocity points, [i*(N-1)+a]
+//   Gpv       : its derivative there
+//   IG, DG    : velocity basis and its derivative at the Q(N) Gauss points, [g*N+j]
+//   gw        : Gauss weights
+template <typename T>
+struct Tables {
+  T x[IMEX_MAXN + 1][IMEX_MAXN];
+  T w[IMEX_MAXN + 1][IMEX_MAXN];
+  T D[IMEX_MAXN + 1][IMEX_MAXN * IMEX_MAXN];
+  T Ipv[IMEX_MAXN + 1][IMEX_MAXN * IMEX_MAXN];
+  T Gpv[IMEX_MAXN + 1][IMEX_MAXN * IMEX_MAXN];
+  T IG[IMEX_MAXN + 1][IMEX_MAXQ * IMEX_MAXN];
+  T DG[IMEX_MAXN + 1][IMEX_MAXQ * IMEX_MAXN];
+  T gw[IMEX_MAXN + 1][IMEX_MAXQ];
+  int Q[IMEX_MAXN + 1];
+};
+
+template <typename T> __device__ __forceinline__ const Tables<T>& tab(const Geom& g);
+template <> __device__ __forceinline__ const Tables<double>& tab<double>(const Geom& g) {
+  return *reinterpret_cast<const Tables<double>*>(g.tab64);
+}
+template <> __device__ __forceinline__ const Tables<float>& tab<float>(const Geom& g) {
+  return *reinterpret_cast<const Tables<float>*>(g.tab32);
+}
+
+__host__ __device__ constexpr int ipow(int b, int e) { return e == 0 ? 1 : b * ipow(b, e - 1); }
+__host__ __device__ constexpr int over_q(int N) { return (3 * N + 1) / 2; }
+
+// neighbour element across face (k, side) of element with coordinates ec; -1 on a domain boundary
+__device__ __forceinline__ int neighbor(const Geom& g, const int ec[3], int k, int side) {
+  int c[3] = {ec[0], ec[1], ec[2]};
+  int j = c[k] + side;
+  if (j < 0 || j >= g.n[k]) {
+    if (g.bc[k] != 0) return -1;
+    j = (j + g.n[k]) % g.n[k];
+  }
+  c[k] = j;
+  return c[0] + g.n[0] * (c[1] + g.n[1] * c[2]);
+}
+
+__device__ __forceinline__ void elem_coords(const Geom& g, int e, int ec[3]) {
+  ec[0] = e % g.n[0];
+  int r = e / g.n[0];
+  ec[1] = r % g.n[1];
+  ec[2] = r / g.n[1];
+}
+
+// host-side table construction (basis.cpp)
+void build_tables(Tables<double>* t64, Tables<float>* t32);
+
+// number of kernels this library has launched (all contexts, all threads)
+void count_launch();
+long long launch_count();
+
+}  // namespace imex
+
+// every kernel launch of the library goes through this macro, which counts it
+#define IMEX_COUNTED(...)    \
+  do {                       \
+    ::imex::count_launch();  \
+    __VA_ARGS__;             \
+  } while (0)
+

@@ -1,0 +1,1447 @@
+// Host side of the library: context, solvers and the time steppers of Alg. 3
+// (IMEX Runge-Kutta with projection splitting, Sec. 3.2.2) and Alg. 4 (SISDC,
+// Sec. 3.2.3), behind the C ABI of include/imex.h.  Every arithmetic step runs in
+// the device kernels; the host only sequences launches on the context's stream
+// and reads back convergence flags once per chunk of CG iterations.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/imex.h"
+#include "common.cuh"
+#include "kernels.h"
+#include "vec.h"
+
+using namespace imex;
+
+// helpers defined at the end of this file
+void sub_f(float* r, const float* b, const float* a, size_t n, cudaStream_t st);
+void remove_mean_t(void* x, int tsize, size_t n, double* partial, int nblocks, double* scratch, cudaStream_t st);
+void f2d(const float* in, double* out, size_t n, cudaStream_t st);
+
+namespace {
+
+struct Tab {
+  int s = 0;
+  double c[8] = {0};
+  double AI[8][8] = {{0}};
+  double bI[8] = {0};
+  double AE[8][8] = {{0}};
+  double bE[8] = {0};
+};
+
+// Butcher tableaux of the paper's appendix (RK-TR, RK-CB2, RK-CB3c, RK-CB3e, RK-CB4, RK-ARS3)
+// and IMEX Euler, as doubles.
+bool named_tableau(const std::string& name, Tab* t) {
+  auto set = [&](int s, std::vector<double> c, std::vector<std::vector<double>> AI, std::vector<double> bI,
+                 std::vector<std::vector<double>> AE, std::vector<double> bE) {
+    *t = Tab();
+    t->s = s;
+    for (int i = 0; i < s; ++i) {
+      t->c[i] = c[i];
+      t->bI[i] = bI[i];
+      t->bE[i] = bE[i];
+      for (int j = 0; j < (int)AI[i].size(); ++j) t->AI[i][j] = AI[i][j];
+      for (int j = 0; j < (int)AE[i].size(); ++j) t->AE[i][j] = AE[i][j];
+    }
+  };
+  std::string n = name;
+  for (auto& ch : n) ch = (char)toupper(ch);
+  if (n.rfind("RK-", 0) == 0) n = n.substr(3);
+  if (n == "EULER" || n == "EU") {
+    set(2, {0, 1}, {{0}, {0, 1}}, {0, 1}, {{0}, {1}}, {1, 0});
+  } else if (n == "TR") {
+    set(3, {0, 1, 1}, {{0}, {0, 1}, {0.5, 0, 0.5}}, {0.5, 0, 0.5}, {{0}, {1}, {0.5, 0.5}}, {0.5, 0.5, 0});
+  } else if (n == "CB2") {
+    set(3, {0, 0.4, 1}, {{0}, {0, 0.4}, {0, 5.0 / 6, 1.0 / 6}}, {0, 5.0 / 6, 1.0 / 6}, {{0}, {0.4}, {0, 1}},
+        {0, 5.0 / 6, 1.0 / 6});
+  } else if (n == "CB3C") {
+    const double c2 = 3375509829940.0 / 4525919076317.0, c3 = 272778623835.0 / 1039454778728.0;
+    const double b2 = 673488652607.0 / 2334033219546.0, b3 = 493801219040.0 / 853653026979.0,
+                 b4 = 184814777513.0 / 1389668723319.0;
+    const double a32 = -11712383888607531889907.0 / 32694570495602105556248.0;
+    const double a33 = 566138307881.0 / 912153721139.0;
+    set(4, {0, c2, c3, 1}, {{0}, {0, c2}, {0, a32, a33}, {0, b2, b3, b4}}, {0, b2, b3, b4},
+        {{0}, {c2}, {0, c3}, {0, b2, 1660544566939.0 / 2334033219546.0}}, {0, b2, b3, b4});
+  } else if (n == "CB3E") {
+    set(4, {0, 1.0 / 3, 1, 1}, {{0}, {0, 1.0 / 3}, {0, 0.5, 0.5}, {0, 0.75, -0.25, 0.5}}, {0, 0.75, -0.25, 0.5},
+        {{0}, {1.0 / 3}, {0, 1}, {0, 0.75, 0.25}}, {0, 0.75, -0.25, 0.5});
+  } else if (n == "CB4") {
+    const double a1 = 232049084587.0 / 1377130630063.0, a2 = 322009889509.0 / 2243393849156.0,
+                 a3 = -195109672787.0 / 1233165545817.0, b4 = -340582416761.0 / 705418832319.0,
+                 b5 = 463396075661.0 / 409972144477.0, b6 = 323177943294.0 / 1626646580633.0;
+    set(6, {0, 0.25, 0.75, 0.375, 0.5, 1},
+        {{0},
+         {0.125, 0.125},
+         {216145252607.0 / 961230882893.0, 257479850128.0 / 1143310606989.0, 30481561667.0 / 101628412017.0},
+         {a1, -381180097479.0 / 1276440792700.0, -54660926949.0 / 461115766612.0, 344309628413.0 / 552073727558.0},
+         {a1, a2, -100836174740.0 / 861952129159.0, -250423827953.0 / 1283875864443.0, 0.5},
+         {a1, a2, a3, b4, b5, b6}},
+        {a1, a2, a3, b4, b5, b6},
+        {{0},
+         {0.25},
+         {153985248130.0 / 1004999853329.0, 902825336800.0 / 1512825644809.0},
+         {a1, 99316866929.0 / 820744730663.0, 82888780751.0 / 969573940619.0},
+         {a1, a2, 57501241309.0 / 765040883867.0, 76345938311.0 / 676824576433.0},
+         {a1, a2, a3, -4099309936455.0 / 6310162971841.0, 1395992540491.0 / 933264948679.0}},
+        {a1, a2, a3, b4, b5, b6});
+  } else if (n == "ARS3") {
+    set(5, {0, 0.5, 2.0 / 3, 0.5, 1},
+        {{0}, {0, 0.5}, {0, 1.0 / 6, 0.5}, {0, -0.5, 0.5, 0.5}, {0, 1.5, -1.5, 0.5, 0.5}}, {0, 1.5, -1.5, 0.5, 0.5},
+        {{0}, {0.5}, {11.0 / 18, 1.0 / 18}, {5.0 / 6, -5.0 / 6, 0.5}, {0.25, 1.75, 0.75, -1.75}},
+        {0.25, 1.75, 0.75, -1.75, 0});
+  } else {
+    return false;
+  }
+  return true;
+}
+
+bool valid_tableau(const Tab& t) {
+  if (t.s < 2 || t.s > 8) return false;
+  if (t.c[0] != 0.0 || t.AI[0][0] != 0.0) return false;
+  for (int i = 0; i < t.s; ++i) {
+    double si = 0, se = 0;
+    for (int j = 0; j < t.s; ++j) {
+      if (j > i && t.AI[i][j] != 0.0) return false;
+      if (j >= i && t.AE[i][j] != 0.0) return false;
+      si += t.AI[i][j];
+      se += t.AE[i][j];
+    }
+    if (std::fabs(si - t.c[i]) > 1e-10 || std::fabs(se - t.c[i]) > 1e-10) return false;
+  }
+  return true;
+}
+
+// GLL points on [-1, 1] by Newton's method on L_M' (sub-nodes of the SDC step)
+void gll_points(int n, double* x) {
+  const int P = n - 1;
+  x[0] = -1.0;
+  x[P] = 1.0;
+  for (int i = 1; i < P; ++i) {
+    double z = -std::cos(M_PI * i / P);
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1, p1 = z, d0 = 0, d1 = 1;
+      for (int k = 2; k <= P; ++k) {
+        double p2 = ((2.0 * k - 1) * z * p1 - (k - 1.0) * p0) / k;
+        double d2 = d0 + (2.0 * k - 1) * p1;
+        p0 = p1; p1 = p2; d0 = d1; d1 = d2;
+      }
+      const double d2L = (2.0 * z * d1 - P * (P + 1.0) * p1) / (1.0 - z * z);
+      const double dz = d1 / d2L;
+      z -= dz;
+      if (std::fabs(dz) < 1e-16) break;
+    }
+    x[i] = z;
+  }
+}
+
+}  // namespace
+
+struct imex_ctx {
+  imex_mesh_desc desc{};
+  Geom gv{}, gp{};
+  int d = 0, Nv = 0, Np = 0;
+  size_t nv = 0, np = 0;        // nodes per velocity component / pressure nodes
+  cudaStream_t st = nullptr;
+  bool own_stream = false;
+  std::string err;
+  Tab tab;
+  bool use_sdc = false;
+  int sdc_M = 0, sdc_K = 0;
+  Tab sdc_pred;
+  // models
+  int nu_kind = IMEX_NU_CONST;
+  double nu_p[8] = {0};
+  int bc_kind = IMEX_FLOW_NONE;
+  double bc_p[8] = {0};
+  int f_kind = IMEX_FORCE_NONE;
+  double f_p[8] = {0};
+  double t = 0.0;
+  // device memory
+  Tables<double>* dtab64 = nullptr;
+  Tables<float>* dtab32 = nullptr;
+  std::vector<void*> allocs;
+  double *v = nullptr, *vp = nullptr, *vpp = nullptr, *g = nullptr, *tmp = nullptr, *vb = nullptr;
+  double *nu = nullptr, *nu_fixed = nullptr, *phi = nullptr, *jac = nullptr, *fsbuf = nullptr;
+  double *psi = nullptr, *bp = nullptr, *mass_v = nullptr, *mass_p = nullptr;
+  std::vector<double*> E, Fd1, Fd3, Fs;         // stage storage (RK)
+  // SDC storage
+  std::vector<double*> sv, snu, sFEX, sFIM, sFq;
+  // CG (FP64 and FP32)
+  double *cx = nullptr, *cr = nullptr, *cz = nullptr, *cp = nullptr, *cAp = nullptr, *cdiag = nullptr;
+  float *fx = nullptr, *fr = nullptr, *fz = nullptr, *fp = nullptr, *fAp = nullptr, *fdiag = nullptr;
+  float *fnu = nullptr, *fvtmp = nullptr;
+  double* partial = nullptr;
+  int nblocks = 0;
+  double* dscal = nullptr;      // 16 x 4 doubles of scalars
+  int* iscal = nullptr;
+  double* hscal = nullptr;      // pinned host mirror
+  int* hiscal = nullptr;
+  bool diag_valid_p = false;
+  imex_stats stats{};
+  double last_res = 0.0;
+  // CUDA-event timing of kernel classes
+  struct Prof {
+    std::vector<cudaEvent_t> ev;   // pairs
+    int used = 0;
+    long long n = 0;
+    double ms = 0.0;
+  };
+  bool prof = false;
+  Prof profc[IMEX_PROF_NCLASS];
+};
+
+namespace {
+
+imex_status fail(imex_ctx* c, imex_status s, const std::string& msg) {
+  if (c) c->err = msg;
+  return s;
+}
+
+imex_status cuda_check(imex_ctx* c, cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return IMEX_OK;
+  return fail(c, e == cudaErrorMemoryAllocation ? IMEX_ENOMEM : IMEX_ECUDA,
+              std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+// drain the recorded event pairs of one class into its totals
+void prof_flush(imex_ctx* c, int cls) {
+  auto& P = c->profc[cls];
+  if (P.used == 0) return;
+  cudaEventSynchronize(P.ev[2 * (P.used - 1) + 1]);
+  for (int i = 0; i < P.used; ++i) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, P.ev[2 * i], P.ev[2 * i + 1]);
+    P.ms += ms;
+  }
+  P.n += P.used;
+  P.used = 0;
+}
+
+// record the start (begin = true) or end of one launch of a timed class
+void prof_mark(imex_ctx* c, int cls, bool begin) {
+  if (!c->prof) return;
+  auto& P = c->profc[cls];
+  const int cap = 4096;
+  if (P.ev.empty()) {
+    P.ev.resize(2 * cap);
+    for (auto& e : P.ev) cudaEventCreate(&e);
+  }
+  if (begin && P.used == cap) prof_flush(c, cls);
+  cudaEventRecord(P.ev[2 * P.used + (begin ? 0 : 1)], c->st);
+  if (!begin) P.used++;
+}
+
+template <typename T>
+imex_status dalloc(imex_ctx* c, T** p, size_t n) {
+  void* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, std::max<size_t>(n, 1) * sizeof(T));
+  if (e != cudaSuccess) return cuda_check(c, e, "cudaMalloc");
+  c->allocs.push_back(q);
+  *p = static_cast<T*>(q);
+  return IMEX_OK;
+}
+
+#define TRY(x)                       \
+  do {                               \
+    imex_status _s = (x);            \
+    if (_s != IMEX_OK) return _s;    \
+  } while (0)
+#define CK(x, what) TRY(cuda_check(c, (x), what))
+
+imex_status launch_check(imex_ctx* c, int rc, const char* what) {
+  if (rc != 0) return fail(c, IMEX_EINVAL, std::string(what) + ": unsupported (dim, P)");
+  return cuda_check(c, cudaGetLastError(), what);
+}
+
+// ---- basic operators on the context's buffers --------------------------------------
+template <typename T>
+SipgArgs<T> sipg_args(const T* x, T* y, int nsys, long long stride, const T* nu, double nu0, const T* gd,
+                      double alpha, double beta, int minv) {
+  SipgArgs<T> a;
+  a.x = x; a.y = y; a.nsys = nsys; a.sys_stride = stride; a.nu = nu; a.nu0 = (T)nu0;
+  a.gdata = gd; a.g_stride = stride; a.alpha = (T)alpha; a.beta = (T)beta; a.minv = minv;
+  return a;
+}
+
+double nu_const(const imex_ctx* c) { return c->nu_p[0]; }
+
+bool variable_nu(const imex_ctx* c) { return c->nu_kind != IMEX_NU_CONST; }
+
+// the pressure operator L psi (pressure space), T = double / float
+template <typename T>
+imex_status apply_pressure(imex_ctx* c, const T* x, T* y, T* vtmp) {
+  const int cls = sizeof(T) == 4 ? IMEX_PROF_PRESSURE_F32 : IMEX_PROF_PRESSURE_F64;
+  if (c->desc.poisson == IMEX_POISSON_SIPG) {
+    SipgArgs<T> a = sipg_args<T>(x, y, 1, (long long)c->np, nullptr, 1.0, nullptr, 0.0, 1.0, 0);
+    prof_mark(c, cls, true);
+    const int rc = sipg_apply<T>(c->gp, c->Np, a, c->st);
+    prof_mark(c, cls, false);
+    return launch_check(c, rc, "sipg_apply(p)");
+  }
+  // consistent: L = B M^{-1} B^T
+  GradArgs<T> ga{x, nullptr, (long long)c->nv, T(1), vtmp};
+  TRY(launch_check(c, dg_grad<T>(c->gv, c->Nv, ga, c->st), "dg_grad"));
+  DivArgs<T> da{vtmp, (long long)c->nv, nullptr, 0, T(1), y};
+  return launch_check(c, dg_div<T>(c->gv, c->Nv, da, c->st), "dg_div");
+}
+
+// velocity Helmholtz operator (M + gamma A(nu)), nsys components
+template <typename T>
+imex_status apply_helm(imex_ctx* c, const T* x, T* y, int nsys, const T* nu, double gamma) {
+  const int cls = sizeof(T) == 4 ? IMEX_PROF_HELMHOLTZ_F32 : IMEX_PROF_HELMHOLTZ_F64;
+  SipgArgs<T> a = sipg_args<T>(x, y, nsys, (long long)c->nv, nu, nu_const(c), nullptr, 1.0, gamma, 0);
+  prof_mark(c, cls, true);
+  const int rc = sipg_apply<T>(c->gv, c->Nv, a, c->st);
+  prof_mark(c, cls, false);
+  return launch_check(c, rc, "sipg_apply(v)");
+}
+
+// ---- PCG -------------------------------------------------------------------------
+// scalar slots: dscal[0..7] CG scalars x nsys (<= 3 systems): layout per field of 4 entries
+CgScalars scalars(imex_ctx* c, double tol) {
+  CgScalars s;
+  s.rz = c->dscal + 0;
+  s.rz_old = c->dscal + 4;
+  s.rr = c->dscal + 8;
+  s.bb = c->dscal + 12;
+  s.pAp = c->dscal + 16;
+  s.done = c->iscal + 0;
+  s.iters = c->iscal + 4;
+  s.tol2 = tol * tol;
+  return s;
+}
+
+// Jacobi PCG on op(x) = b for nsys systems of length n; x holds the initial guess.
+// `op(x, y)` applies the operator; dinv is the inverse diagonal (length n, shared).
+// Returns IMEX_OK or IMEX_ENOTCONV; iterations and relative residuals via out params.
+template <typename T, typename Op>
+imex_status pcg(imex_ctx* c, Op op, const T* b, T* x, T* r, T* z, T* p, T* Ap, const T* dinv, size_t n,
+                int nsys, double tol, int maxit, bool mean_free, long long* iters_out, double* res_out) {
+  CgScalars sc = scalars(c, tol);
+  const long long stride = (long long)n;
+  // r = b - A x
+  TRY(op(x, Ap));
+  if (std::is_same<T, double>::value) {
+    for (int s = 0; s < nsys; ++s) {
+      LinComb lc{};
+      lc.nterms = 2;
+      lc.x[0] = reinterpret_cast<const double*>(b) + s * n; lc.c[0] = 1.0;
+      lc.x[1] = reinterpret_cast<const double*>(Ap) + s * n; lc.c[1] = -1.0;
+      lincomb(reinterpret_cast<double*>(r) + s * n, lc, n, c->st);
+    }
+  } else {
+    for (int s = 0; s < nsys; ++s)
+      sub_f(reinterpret_cast<float*>(r) + s * n, reinterpret_cast<const float*>(b) + s * n,
+            reinterpret_cast<const float*>(Ap) + s * n, n, c->st);
+  }
+  if (mean_free) {
+    // project r onto the range (remove its Euclidean mean) -- singular pressure problems
+    remove_mean_t(r, sizeof(T), n, c->partial, c->nblocks, c->dscal + 32, c->st);
+  }
+  // bb = (b, b) with b projected for the singular case: use r0 + A x0 ~ b; simpler: dot of b
+  if (std::is_same<T, double>::value)
+    dot_batched(reinterpret_cast<const double*>(b), reinterpret_cast<const double*>(b), n, stride, nsys,
+                c->partial, c->nblocks, sc.bb, c->st);
+  else
+    dot_batched_f(reinterpret_cast<const float*>(b), reinterpret_cast<const float*>(b), n, stride, nsys,
+                  c->partial, c->nblocks, sc.bb, c->st);
+  cg_init<T>(p, z, r, dinv, n, stride, nsys, sc, c->partial, c->nblocks, c->st);
+  CK(cudaGetLastError(), "cg_init");
+  const int chunk = 16;
+  int it = 0;
+  bool all_done = false;
+  while (it < maxit + chunk) {
+    for (int k = 0; k < chunk; ++k) {
+      TRY(op(p, Ap));
+      cg_pap<T>(p, Ap, n, stride, nsys, sc, c->partial, c->nblocks, c->st);
+      cg_step_xr<T>(x, r, p, Ap, dinv, z, n, stride, nsys, sc, maxit, c->partial, c->nblocks, c->st);
+      cg_step_p<T>(p, z, n, stride, nsys, sc, c->nblocks, c->st);
+    }
+    it += chunk;
+    CK(cudaMemcpyAsync(c->hiscal, c->iscal, 8 * sizeof(int), cudaMemcpyDeviceToHost, c->st), "memcpy flags");
+    CK(cudaStreamSynchronize(c->st), "sync");
+    all_done = true;
+    for (int s = 0; s < nsys; ++s) all_done = all_done && c->hiscal[s] != 0;
+    if (all_done) break;
+  }
+  CK(cudaMemcpyAsync(c->hscal, c->dscal, 24 * sizeof(double), cudaMemcpyDeviceToHost, c->st), "memcpy scal");
+  CK(cudaMemcpyAsync(c->hiscal, c->iscal, 8 * sizeof(int), cudaMemcpyDeviceToHost, c->st), "memcpy flags");
+  CK(cudaStreamSynchronize(c->st), "sync");
+  long long its = 0;
+  double res = 0.0;
+  imex_status st = IMEX_OK;
+  for (int s = 0; s < nsys; ++s) {
+    its += c->hiscal[4 + s];
+    const double bb = c->hscal[12 + s];
+    const double rr = c->hscal[8 + s];
+    const double rel = bb > 0 ? std::sqrt(rr / bb) : std::sqrt(rr);
+    res = std::max(res, rel);
+    if (c->hiscal[s] == 3 || c->hiscal[s] == 0) st = IMEX_ENOTCONV;
+    if (c->hiscal[s] == 2) st = IMEX_EUNSTABLE;
+  }
+  if (iters_out) *iters_out += its;
+  if (res_out) *res_out = res;
+  if (st == IMEX_ENOTCONV) return fail(c, st, "CG did not converge within maxit");
+  if (st == IMEX_EUNSTABLE) return fail(c, st, "NaN in CG residual");
+  return IMEX_OK;
+}
+
+}  // namespace
+
+// small helper kernels local to this file
+namespace imex {
+__global__ void sub_f_kernel(float* r, const float* b, const float* a, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    r[i] = b[i] - a[i];
+}
+__global__ void diag_mul_kernel(double* out, const double* x, const double* m, size_t n, int nsys) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n * nsys; i += (size_t)gridDim.x * blockDim.x)
+    out[i] = x[i] * m[i % n];
+}
+template <typename T>
+__global__ void sum_partial_t(const T* x, size_t n, double* partial) {
+  double acc = 0.0;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    acc += (double)x[i];
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  __shared__ double ws[32];
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += ws[w];
+    partial[blockIdx.x] = s;
+  }
+}
+__global__ void finish_mean(const double* partial, int nb, double* dst, double n) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double s = 0.0;
+    for (int i = 0; i < nb; ++i) s += partial[i];
+    dst[0] = s / n;
+  }
+}
+template <typename T>
+__global__ void sub_mean_t(T* x, size_t n, const double* mean) {
+  const T m = (T)mean[0];
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    x[i] -= m;
+}
+// weighted mean removal: x -= (sum w x) / (sum w)
+__global__ void wsum_partial(const double* x, const double* w, size_t n, double* partial) {
+  double a = 0.0, b = 0.0;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    a += w[i] * x[i];
+    b += w[i];
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_down_sync(0xffffffffu, a, o);
+    b += __shfl_down_sync(0xffffffffu, b, o);
+  }
+  __shared__ double wa[32], wb[32];
+  if ((threadIdx.x & 31) == 0) { wa[threadIdx.x >> 5] = a; wb[threadIdx.x >> 5] = b; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0, u = 0.0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) { s += wa[k]; u += wb[k]; }
+    partial[2 * blockIdx.x] = s;
+    partial[2 * blockIdx.x + 1] = u;
+  }
+}
+__global__ void finish_wmean(const double* partial, int nb, double* dst) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double s = 0.0, u = 0.0;
+    for (int i = 0; i < nb; ++i) { s += partial[2 * i]; u += partial[2 * i + 1]; }
+    dst[0] = s / u;
+  }
+}
+}  // namespace imex
+
+void sub_f(float* r, const float* b, const float* a, size_t n, cudaStream_t st) {
+  IMEX_COUNTED(imex::sub_f_kernel<<<(unsigned)std::min<size_t>((n + 255) / 256, 1216), 256, 0, st>>>(r, b, a, n));
+}
+
+void remove_mean_t(void* x, int tsize, size_t n, double* partial, int nblocks, double* scratch,
+                   cudaStream_t st) {
+  if (tsize == 8) {
+    IMEX_COUNTED(imex::sum_partial_t<double><<<nblocks, 256, 0, st>>>((const double*)x, n, partial));
+  } else {
+    IMEX_COUNTED(imex::sum_partial_t<float><<<nblocks, 256, 0, st>>>((const float*)x, n, partial));
+  }
+  IMEX_COUNTED(imex::finish_mean<<<1, 32, 0, st>>>(partial, nblocks, scratch, (double)n));
+  if (tsize == 8)
+    IMEX_COUNTED(imex::sub_mean_t<double><<<nblocks, 256, 0, st>>>((double*)x, n, scratch));
+  else
+    IMEX_COUNTED(imex::sub_mean_t<float><<<nblocks, 256, 0, st>>>((float*)x, n, scratch));
+}
+
+namespace {
+
+void diag_mul(imex_ctx* c, double* out, const double* x, const double* m, size_t n, int nsys) {
+  IMEX_COUNTED(imex::diag_mul_kernel<<<c->nblocks, 256, 0, c->st>>>(out, x, m, n, nsys));
+}
+
+void remove_weighted_mean(imex_ctx* c, double* x, const double* w, size_t n) {
+  IMEX_COUNTED(imex::wsum_partial<<<c->nblocks, 256, 0, c->st>>>(x, w, n, c->partial));
+  IMEX_COUNTED(imex::finish_wmean<<<1, 32, 0, c->st>>>(c->partial, c->nblocks, c->dscal + 33));
+  IMEX_COUNTED(imex::sub_mean_t<double><<<c->nblocks, 256, 0, c->st>>>(x, n, c->dscal + 33));
+}
+
+// ---- solves ------------------------------------------------------------------------
+// Poisson: L psi = b (b is overwritten by its mean-free part); psi: initial guess in, solution out
+imex_status solve_poisson(imex_ctx* c, double* b, double* psi, long long* iters, double* res) {
+  const size_t n = c->np;
+  remove_mean_t(b, 8, n, c->partial, c->nblocks, c->dscal + 32, c->st);
+  if (!c->diag_valid_p) {
+    SipgArgs<double> a = sipg_args<double>(nullptr, c->cdiag, 1, (long long)n, nullptr, 1.0, nullptr, 0.0, 1.0, 0);
+    TRY(launch_check(c, sipg_diag<double>(c->gp, c->Np, a, c->st), "sipg_diag(p)"));
+    reciprocal<double>(c->cdiag, n, c->st);
+    convert_d2f(c->cdiag, c->fdiag + 0, n, c->st);
+    c->diag_valid_p = true;
+  }
+  // the diagonal buffers are shared with the Helmholtz solves: recompute if clobbered
+  const double tol = c->desc.tol;
+  if (c->desc.precision == IMEX_FP64) {
+    auto op = [&](const double* x, double* y) { return apply_pressure<double>(c, x, y, c->tmp); };
+    imex_status s = pcg<double>(c, op, b, psi, c->cr, c->cz, c->cp, c->cAp, c->cdiag, n, 1, tol, c->desc.maxit,
+                                true, iters, res);
+    remove_weighted_mean(c, psi, c->mass_p, n);
+    return s;
+  }
+  // mixed: FP64 residual, FP32 inner PCG on the correction
+  const double itol = c->desc.inner_tol > 0 ? c->desc.inner_tol : 1e-5;
+  double* bb = c->dscal + 40;
+  dot_batched(b, b, n, (long long)n, 1, c->partial, c->nblocks, bb, c->st);
+  imex_status s = IMEX_OK;
+  for (int outer = 0; outer < 30; ++outer) {
+    TRY(apply_pressure<double>(c, psi, c->cAp, c->tmp));
+    LinComb lc{};
+    lc.nterms = 2; lc.x[0] = b; lc.c[0] = 1.0; lc.x[1] = c->cAp; lc.c[1] = -1.0;
+    lincomb(c->cr, lc, n, c->st);
+    remove_mean_t(c->cr, 8, n, c->partial, c->nblocks, c->dscal + 32, c->st);
+    dot_batched(c->cr, c->cr, n, (long long)n, 1, c->partial, c->nblocks, c->dscal + 41, c->st);
+    CK(cudaMemcpyAsync(c->hscal + 40, c->dscal + 40, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->st), "cp");
+    CK(cudaStreamSynchronize(c->st), "sync");
+    const double rel = c->hscal[40] > 0 ? std::sqrt(c->hscal[41] / c->hscal[40]) : 0.0;
+    if (res) *res = rel;
+    if (rel <= tol) break;
+    if (rel != rel) return fail(c, IMEX_EUNSTABLE, "NaN in Poisson residual");
+    if (outer == 29) return fail(c, IMEX_ENOTCONV, "Poisson refinement did not converge");
+    c->stats.refinements++;
+    convert_d2f(c->cr, c->fr + 0, n, c->st);
+    CK(cudaMemsetAsync(c->fx, 0, n * sizeof(float), c->st), "memset");
+    float* fb = c->fvtmp + c->d * c->nv;   // scratch for the FP32 right-hand side
+    CK(cudaMemcpyAsync(fb, c->fr, n * sizeof(float), cudaMemcpyDeviceToDevice, c->st), "cp");
+    auto op = [&](const float* x, float* y) { return apply_pressure<float>(c, x, y, c->fvtmp); };
+    s = pcg<float>(c, op, fb, c->fx, c->fr, c->fz, c->fp, c->fAp, c->fdiag, n, 1, itol, c->desc.maxit, true,
+                   iters, nullptr);
+    if (s == IMEX_ENOTCONV) s = IMEX_OK;   // inner solve is a preconditioner; the outer loop decides
+    if (s != IMEX_OK) return s;
+    axpy_f2d(psi, c->fx, n, c->st);
+  }
+  remove_weighted_mean(c, psi, c->mass_p, n);
+  return IMEX_OK;
+}
+
+// Helmholtz: (M + gamma A(nu)) x = rhs, d components; x: initial guess in, solution out.
+imex_status solve_helmholtz(imex_ctx* c, const double* rhs, double* x, const double* nu, double gamma,
+                            long long* iters, double* res) {
+  const size_t n = c->nv;
+  const int d = c->d;
+  // Jacobi diagonal of M + gamma A(nu)  (stored in cdiag + np region-free slot: use cdiag[np..])
+  double* dg = c->cdiag + c->np;
+  float* fdg = c->fdiag + c->np;
+  SipgArgs<double> a = sipg_args<double>(nullptr, dg, 1, (long long)n, nu, nu_const(c), nullptr, 1.0, gamma, 0);
+  TRY(launch_check(c, sipg_diag<double>(c->gv, c->Nv, a, c->st), "sipg_diag(v)"));
+  reciprocal<double>(dg, n, c->st);
+  const double tol = c->desc.tol;
+  if (c->desc.precision == IMEX_FP64) {
+    auto op = [&](const double* xx, double* yy) { return apply_helm<double>(c, xx, yy, d, nu, gamma); };
+    return pcg<double>(c, op, rhs, x, c->cr, c->cz, c->cp, c->cAp, dg, n, d, tol, c->desc.maxit, false, iters, res);
+  }
+  convert_d2f(dg, fdg, n, c->st);
+  const float* fnu = nullptr;
+  if (nu) { convert_d2f(nu, c->fnu, n, c->st); fnu = c->fnu; }
+  const double itol = c->desc.inner_tol > 0 ? c->desc.inner_tol : 1e-5;
+  double* bb = c->dscal + 48;
+  dot_batched(rhs, rhs, n, (long long)n, d, c->partial, c->nblocks, bb, c->st);
+  for (int outer = 0; outer < 30; ++outer) {
+    TRY(apply_helm<double>(c, x, c->cAp, d, nu, gamma));
+    LinComb lc{};
+    lc.nterms = 2; lc.x[0] = rhs; lc.c[0] = 1.0; lc.x[1] = c->cAp; lc.c[1] = -1.0;
+    lincomb(c->cr, lc, n * d, c->st);
+    dot_batched(c->cr, c->cr, n, (long long)n, d, c->partial, c->nblocks, c->dscal + 52, c->st);
+    CK(cudaMemcpyAsync(c->hscal + 48, c->dscal + 48, 8 * sizeof(double), cudaMemcpyDeviceToHost, c->st), "cp");
+    CK(cudaStreamSynchronize(c->st), "sync");
+    double rel = 0.0;
+    for (int s = 0; s < d; ++s)
+      rel = std::max(rel, c->hscal[48 + s] > 0 ? std::sqrt(c->hscal[52 + s] / c->hscal[48 + s]) : 0.0);
+    if (res) *res = rel;
+    if (rel <= tol) break;
+    if (rel != rel) return fail(c, IMEX_EUNSTABLE, "NaN in Helmholtz residual");
+    if (outer == 29) return fail(c, IMEX_ENOTCONV, "Helmholtz refinement did not converge");
+    c->stats.refinements++;
+    convert_d2f(c->cr, c->fr, n * d, c->st);
+    CK(cudaMemsetAsync(c->fx, 0, n * d * sizeof(float), c->st), "memset");
+    float* fb = c->fvtmp;
+    CK(cudaMemcpyAsync(fb, c->fr, n * d * sizeof(float), cudaMemcpyDeviceToDevice, c->st), "cp");
+    auto op = [&](const float* xx, float* yy) { return apply_helm<float>(c, xx, yy, d, fnu, gamma); };
+    imex_status s = pcg<float>(c, op, fb, c->fx, c->fr, c->fz, c->fp, c->fAp, fdg, n, d, itol, c->desc.maxit,
+                               false, iters, nullptr);
+    if (s == IMEX_ENOTCONV) s = IMEX_OK;
+    if (s != IMEX_OK) return s;
+    axpy_f2d(x, c->fx, n * d, c->st);
+  }
+  return IMEX_OK;
+}
+
+// ---- right-hand sides ---------------------------------------------------------------
+FieldSpec spec(int kind, const double* p) {
+  FieldSpec f;
+  f.kind = kind;
+  for (int i = 0; i < 8; ++i) f.p[i] = p[i];
+  return f;
+}
+
+bool has_boundary(const imex_ctx* c) {
+  for (int k = 0; k < c->d; ++k)
+    if (!c->desc.periodic[k]) return true;
+  return false;
+}
+
+// Dirichlet data at time t into c->vb (or nullptr if all periodic)
+imex_status eval_vb(imex_ctx* c, double t, const double** out) {
+  if (!has_boundary(c)) { *out = nullptr; return IMEX_OK; }
+  TRY(launch_check(c, eval_field(c->gv, c->Nv, 0, spec(c->bc_kind, c->bc_p), t, nullptr, (long long)c->nv, c->vb,
+                                 c->st), "eval_field(vb)"));
+  *out = c->vb;
+  return IMEX_OK;
+}
+
+imex_status eval_nu(imex_ctx* c, double t, const double* v, double* nu) {
+  if (c->nu_kind == IMEX_NU_FIELD) {
+    CK(cudaMemcpyAsync(nu, c->nu_fixed, c->nv * sizeof(double), cudaMemcpyDeviceToDevice, c->st), "cp nu");
+    return IMEX_OK;
+  }
+  return launch_check(c, eval_field(c->gv, c->Nv, 1, spec(c->nu_kind, c->nu_p), t, v, (long long)c->nv, nu, c->st),
+                      "eval_field(nu)");
+}
+
+// nu pointer for the operators: nullptr for constant viscosity
+const double* nu_ptr(const imex_ctx* c, const double* nu) { return variable_nu(c) ? nu : nullptr; }
+
+// F_d3 = -D(nu D.v) into out; if E != nullptr also E += F_d2 = sum_k D_k(nu D_c v_k) (variable nu)
+imex_status graddiv(imex_ctx* c, const double* v, const double* nu, double* fd3, double* fd2_acc) {
+  DerivArgs<double> a{};
+  a.op = 0; a.in = v; a.stride = (long long)c->nv; a.nu = nu_ptr(c, nu); a.nu0 = nu_const(c); a.out = c->phi;
+  TRY(launch_check(c, dg_deriv<double>(c->gv, c->Nv, a, c->st), "dg_deriv(div)"));
+  DerivArgs<double> b{};
+  b.op = 1; b.in = c->phi; b.stride = (long long)c->nv; b.coef = -1.0; b.out = fd3;
+  TRY(launch_check(c, dg_deriv<double>(c->gv, c->Nv, b, c->st), "dg_deriv(grad)"));
+  if (fd2_acc) {
+    DerivArgs<double> j{};
+    j.op = 2; j.in = v; j.stride = (long long)c->nv; j.nu = nu_ptr(c, nu); j.nu0 = nu_const(c); j.out = c->jac;
+    TRY(launch_check(c, dg_deriv<double>(c->gv, c->Nv, j, c->st), "dg_deriv(jac)"));
+    DerivArgs<double> q{};
+    q.op = 3; q.in = c->jac; q.stride = (long long)c->nv; q.coef = 1.0; q.out = fd2_acc;
+    TRY(launch_check(c, dg_deriv<double>(c->gv, c->Nv, q, c->st), "dg_deriv(divT)"));
+  }
+  return IMEX_OK;
+}
+
+// stage right-hand sides at (t, v, nu): E = F_c + F_d2 + F_d3, Fd1, Fd3, Fs (Fs may be nullptr)
+imex_status stage_rhs(imex_ctx* c, double t, const double* v, const double* nu, const double* vb, double* E,
+                      double* Fd1, double* Fd3, double* Fs) {
+  const size_t nt = c->nv * c->d;
+  ConvArgs<double> ca{v, (long long)c->nv, vb, 1.0, E};
+  prof_mark(c, IMEX_PROF_CONV, true);
+  const int rc = dg_conv<double>(c->gv, c->Nv, ca, c->st);
+  prof_mark(c, IMEX_PROF_CONV, false);
+  TRY(launch_check(c, rc, "dg_conv"));
+  const bool varnu = variable_nu(c);
+  if (varnu) {
+    // E += F_d2 + F_d3 (F_d2 accumulated by the kernel)
+    TRY(graddiv(c, v, nu, Fd3, E));
+    LinComb lc{};
+    lc.nterms = 2; lc.x[0] = E; lc.c[0] = 1.0; lc.x[1] = Fd3; lc.c[1] = 1.0;
+    lincomb(E, lc, nt, c->st);
+  } else {
+    // constant nu: F_d2 + F_d3 = 0 exactly for the discrete operators; E = F_c
+    TRY(graddiv(c, v, nu, Fd3, nullptr));
+  }
+  SipgArgs<double> a = sipg_args<double>(v, Fd1, c->d, (long long)c->nv, nu_ptr(c, nu), nu_const(c), vb, 0.0, -1.0, 1);
+  TRY(launch_check(c, sipg_apply<double>(c->gv, c->Nv, a, c->st), "sipg_apply(Fd1)"));
+  if (Fs) {
+    TRY(launch_check(c, eval_field(c->gv, c->Nv, 2, spec(c->f_kind, c->f_p), t, nullptr, (long long)c->nv, Fs, c->st),
+                     "eval_field(f)"));
+  }
+  return IMEX_OK;
+}
+
+// projection: psi from L psi = B v' - int (n.w) q, then v'' = v' - G psi (written to out)
+imex_status project(imex_ctx* c, const double* vin, const double* wdata, int mode, double* out) {
+  DivArgs<double> da{vin, (long long)c->nv, wdata, mode, 1.0, c->bp};
+  TRY(launch_check(c, dg_div<double>(c->gv, c->Nv, da, c->st), "dg_div"));
+  double res = 0.0;
+  TRY(solve_poisson(c, c->bp, c->psi, &c->stats.poisson_iters, &res));
+  c->stats.poisson_solves++;
+  c->stats.max_poisson_res = std::max(c->stats.max_poisson_res, res);
+  GradArgs<double> ga{c->psi, vin, (long long)c->nv, -1.0, out};
+  return launch_check(c, dg_grad<double>(c->gv, c->Nv, ga, c->st), "dg_grad");
+}
+
+// Helmholtz stage solve: v_out = (M + gamma A(nu))^{-1} (M g + gamma r_b(nu, vb)), initial guess g
+imex_status helmholtz_stage(imex_ctx* c, const double* gfield, const double* nu, double gamma, const double* vb,
+                            double* vout) {
+  const size_t nt = c->nv * c->d;
+  // rhs = M g + gamma r_b : r_b = -(A 0 - r_b(vb))
+  diag_mul(c, c->tmp, gfield, c->mass_v, c->nv, c->d);
+  if (vb) {
+    SipgArgs<double> a = sipg_args<double>(c->cz, c->cp, c->d, (long long)c->nv, nu_ptr(c, nu), nu_const(c), vb, 0.0,
+                                           -gamma, 0);
+    CK(cudaMemsetAsync(c->cz, 0, nt * sizeof(double), c->st), "memset");
+    TRY(launch_check(c, sipg_apply<double>(c->gv, c->Nv, a, c->st), "sipg_apply(rb)"));
+    LinComb lc{};
+    lc.nterms = 2; lc.x[0] = c->tmp; lc.c[0] = 1.0; lc.x[1] = c->cp; lc.c[1] = 1.0;
+    lincomb(c->tmp, lc, nt, c->st);
+  }
+  if (vout != gfield) CK(cudaMemcpyAsync(vout, gfield, nt * sizeof(double), cudaMemcpyDeviceToDevice, c->st), "cp");
+  double res = 0.0;
+  // the rhs lives in c->tmp; pcg uses cr/cz/cp/cAp as work space
+  TRY(solve_helmholtz(c, c->tmp, vout, nu_ptr(c, nu), gamma, &c->stats.helmholtz_iters, &res));
+  c->stats.helmholtz_solves++;
+  c->stats.max_helmholtz_res = std::max(c->stats.max_helmholtz_res, res);
+  return IMEX_OK;
+}
+
+// ---- Alg. 3 -------------------------------------------------------------------------
+imex_status rk_step(imex_ctx* c, const Tab& tb, double* v, double t, double dt, bool final_projection) {
+  const int s = tb.s;
+  const size_t nt = c->nv * c->d;
+  const bool forcing = c->f_kind != IMEX_FORCE_NONE;
+  const double* vb = nullptr;
+  TRY(eval_vb(c, t, &vb));
+  TRY(eval_nu(c, t, v, c->nu));
+  TRY(stage_rhs(c, t, v, c->nu, vb, c->E[0], c->Fd1[0], c->Fd3[0], forcing ? c->Fs[0] : nullptr));
+  const double* vi = v;
+  for (int i = 1; i < s; ++i) {
+    const double ti = t + tb.c[i] * dt;
+    TRY(eval_vb(c, ti, &vb));
+    if (forcing)
+      TRY(launch_check(c, eval_field(c->gv, c->Nv, 2, spec(c->f_kind, c->f_p), ti, nullptr, (long long)c->nv,
+                                     c->Fs[i], c->st), "eval_field(f)"));
+    // line 4: v' = v + dt [sum_j a^EX_ij (E_j + Fd1_j + Fd3_j) + sum_{j<=i} a^IM_ij Fs_j]
+    LinComb lc{};
+    int k = 0;
+    lc.x[k] = v; lc.c[k++] = 1.0;
+    for (int j = 0; j < i; ++j) {
+      const double a = dt * tb.AE[i][j];
+      if (a == 0.0) continue;
+      lc.x[k] = c->E[j]; lc.c[k++] = a;
+      lc.x[k] = c->Fd1[j]; lc.c[k++] = a;
+      lc.x[k] = c->Fd3[j]; lc.c[k++] = a;
+    }
+    lc.nterms = k;
+    lincomb(c->vp, lc, nt, c->st);
+    if (forcing) {
+      LinComb lf{};
+      int q = 0;
+      lf.x[q] = c->vp; lf.c[q++] = 1.0;
+      for (int j = 0; j <= i; ++j)
+        if (tb.AI[i][j] != 0.0) { lf.x[q] = c->Fs[j]; lf.c[q++] = dt * tb.AI[i][j]; }
+      lf.nterms = q;
+      lincomb(c->vp, lf, nt, c->st);
+    }
+    // lines 5-6: projection
+    TRY(project(c, c->vp, vb, 1, c->vpp));
+    // line 7: nu_i
+    TRY(eval_nu(c, ti, c->vpp, c->nu));
+    // line 8: g_i
+    LinComb lg{};
+    k = 0;
+    lg.x[k] = c->vpp; lg.c[k++] = 1.0;
+    for (int j = 0; j < i; ++j) {
+      const double a1 = dt * (tb.AI[i][j] - tb.AE[i][j]);
+      const double a3 = -dt * tb.AE[i][j];
+      if (a1 != 0.0) { lg.x[k] = c->Fd1[j]; lg.c[k++] = a1; }
+      if (a3 != 0.0) { lg.x[k] = c->Fd3[j]; lg.c[k++] = a3; }
+    }
+    lg.nterms = k;
+    lincomb(c->g, lg, nt, c->st);
+    // line 9: Helmholtz solve into the stage buffer (reuse c->vp as v_i storage)
+    TRY(helmholtz_stage(c, c->g, c->nu, dt * tb.AI[i][i], vb, c->vp));
+    c->stats.stages++;
+    vi = c->vp;
+    TRY(stage_rhs(c, ti, vi, c->nu, vb, c->E[i], c->Fd1[i], c->Fd3[i], nullptr));
+    if (i < s - 1) {
+      // v_i is only needed through its right-hand sides; keep nothing else
+    }
+  }
+  // line 11: v = v_s + dt sum_i [(bE_i - aE_si) E_i + (bI_i - aI_si)(Fd1_i + Fs_i)]
+  LinComb lc{};
+  int k = 0;
+  lc.x[k] = vi; lc.c[k++] = 1.0;
+  for (int i = 0; i < s; ++i) {
+    const double fe = tb.bE[i] - tb.AE[s - 1][i];
+    const double fi = tb.bI[i] - tb.AI[s - 1][i];
+    if (fe != 0.0) { lc.x[k] = c->E[i]; lc.c[k++] = dt * fe; }
+    if (fi != 0.0) {
+      lc.x[k] = c->Fd1[i]; lc.c[k++] = dt * fi;
+      if (forcing) { lc.x[k] = c->Fs[i]; lc.c[k++] = dt * fi; }
+    }
+  }
+  lc.nterms = k;
+  lincomb(v, lc, nt, c->st);
+  if (final_projection) {
+    TRY(project(c, v, nullptr, 2, c->vpp));
+    CK(cudaMemcpyAsync(v, c->vpp, nt * sizeof(double), cudaMemcpyDeviceToDevice, c->st), "cp");
+  }
+  return IMEX_OK;
+}
+
+// ---- Alg. 4 -------------------------------------------------------------------------
+imex_status sdc_step(imex_ctx* c, double* v, double t, double dt) {
+  const int M = c->sdc_M, K = c->sdc_K, d = c->d;
+  const size_t nt = c->nv * d;
+  const bool varnu = variable_nu(c);
+  const bool fproj = varnu;
+  const bool forcing = c->f_kind != IMEX_FORCE_NONE;
+  // sub-nodes and quadrature weights w_{q,m} = int_{t_{m-1}}^{t_m} l_q (unit step)
+  double x[16], tau[16];
+  gll_points(M + 1, x);
+  for (int m = 0; m <= M; ++m) tau[m] = 0.5 * (x[m] + 1.0);
+  double W[16][16] = {{0}};
+  {
+    // integrate the Lagrange basis exactly with a Gauss rule of M+1 points
+    const int ng = M + 1;
+    double gx[16], gw[16];
+    for (int i = 0; i < ng; ++i) {
+      double z = -std::cos(M_PI * (i + 0.75) / (ng + 0.5));
+      for (int it = 0; it < 100; ++it) {
+        double p0 = 1, p1 = z, d0 = 0, d1 = 1;
+        for (int kk = 2; kk <= ng; ++kk) {
+          double p2 = ((2.0 * kk - 1) * z * p1 - (kk - 1.0) * p0) / kk;
+          double d2 = d0 + (2.0 * kk - 1) * p1;
+          p0 = p1; p1 = p2; d0 = d1; d1 = d2;
+        }
+        const double dz = p1 / d1;
+        z -= dz;
+        if (std::fabs(dz) < 1e-16) break;
+      }
+      double p0 = 1, p1 = z, d0 = 0, d1 = 1;
+      for (int kk = 2; kk <= ng; ++kk) {
+        double p2 = ((2.0 * kk - 1) * z * p1 - (kk - 1.0) * p0) / kk;
+        double d2 = d0 + (2.0 * kk - 1) * p1;
+        p0 = p1; p1 = p2; d0 = d1; d1 = d2;
+      }
+      gx[i] = z;
+      gw[i] = 2.0 / ((1.0 - z * z) * d1 * d1);
+    }
+    for (int m = 1; m <= M; ++m) {
+      const double a = tau[m - 1], b = tau[m];
+      for (int q = 0; q <= M; ++q) {
+        double s = 0.0;
+        for (int i = 0; i < ng; ++i) {
+          const double z = a + 0.5 * (gx[i] + 1.0) * (b - a);
+          double l = 1.0;
+          for (int r = 0; r <= M; ++r)
+            if (r != q) l *= (z - tau[r]) / (tau[q] - tau[r]);
+          s += 0.5 * (b - a) * gw[i] * l;
+        }
+        W[m][q] = s;
+      }
+    }
+  }
+  double tm[16], dts[16];
+  for (int m = 0; m <= M; ++m) tm[m] = t + dt * tau[m];
+  for (int m = 1; m <= M; ++m) dts[m] = tm[m] - tm[m - 1];
+  // predictor
+  CK(cudaMemcpyAsync(c->sv[0], v, nt * sizeof(double), cudaMemcpyDeviceToDevice, c->st), "cp");
+  for (int m = 1; m <= M; ++m) {
+    CK(cudaMemcpyAsync(c->sv[m], c->sv[m - 1], nt * sizeof(double), cudaMemcpyDeviceToDevice, c->st), "cp");
+    TRY(rk_step(c, c->sdc_pred, c->sv[m], tm[m - 1], dts[m], fproj));
+  }
+  const double* vb = nullptr;
+  // F^EX_m = F_c + F_d2 + F_d3 at (v_m, nu_m); F^IM_m = F_d1(nu_{m-1}, v_m)
+  auto f_ex = [&](int m, double* out) -> imex_status {
+    TRY(eval_vb(c, tm[m], &vb));
+    ConvArgs<double> ca{c->sv[m], (long long)c->nv, vb, 1.0, out};
+    TRY(launch_check(c, dg_conv<double>(c->gv, c->Nv, ca, c->st), "dg_conv"));
+    if (varnu) {
+      TRY(graddiv(c, c->sv[m], c->snu[m], c->tmp, out));
+      LinComb lc{};
+      lc.nterms = 2; lc.x[0] = out; lc.c[0] = 1.0; lc.x[1] = c->tmp; lc.c[1] = 1.0;
+      lincomb(out, lc, nt, c->st);
+    }
+    return IMEX_OK;
+  };
+  auto f_d1 = [&](const double* vm, const double* num, double tt, double* out) -> imex_status {
+    TRY(eval_vb(c, tt, &vb));
+    SipgArgs<double> a = sipg_args<double>(vm, out, d, (long long)c->nv, nu_ptr(c, num), nu_const(c), vb, 0.0, -1.0, 1);
+    return launch_check(c, sipg_apply<double>(c->gv, c->Nv, a, c->st), "sipg_apply(Fd1)");
+  };
+  for (int m = 0; m <= M; ++m) TRY(eval_nu(c, tm[m], c->sv[m], c->snu[m]));
+  for (int m = 0; m < M; ++m) TRY(f_ex(m, c->sFEX[m]));
+  for (int m = 1; m <= M; ++m) TRY(f_d1(c->sv[m], c->snu[m - 1], tm[m], c->sFIM[m]));
+  double* Fp1 = c->Fd1[0];        // F'_d1 of the current subinterval
+  double* Fp3 = c->Fd3[0];        // F'_d3
+  double* gbuf = c->Fd1[1];       // right-hand side of the Helmholtz solve / scratch
+  double* stage = c->E[0];        // F^{EX,k+1}_{m-1} while subinterval m runs
+  double* fsbuf = c->Fd3[1];
+  for (int k = 0; k < K; ++k) {
+    // full right-hand sides F(t_q, v^k_q) = F^EX + F_d1(nu^k_q, v^k_q) + F_s for the quadrature term
+    for (int q = 0; q <= M; ++q) {
+      if (q < M) {
+        CK(cudaMemcpyAsync(c->sFq[q], c->sFEX[q], nt * sizeof(double), cudaMemcpyDeviceToDevice, c->st), "cp");
+      } else {
+        TRY(f_ex(q, c->sFq[q]));
+      }
+      TRY(f_d1(c->sv[q], c->snu[q], tm[q], gbuf));
+      LinComb lc{};
+      int n = 0;
+      lc.x[n] = c->sFq[q]; lc.c[n++] = 1.0;
+      lc.x[n] = gbuf; lc.c[n++] = 1.0;
+      if (forcing) {
+        TRY(launch_check(c, eval_field(c->gv, c->Nv, 2, spec(c->f_kind, c->f_p), tm[q], nullptr, (long long)c->nv,
+                                       fsbuf, c->st), "eval_field(f)"));
+        lc.x[n] = fsbuf; lc.c[n++] = 1.0;
+      }
+      lc.nterms = n;
+      lincomb(c->sFq[q], lc, nt, c->st);
+    }
+    // sweep through the subintervals; v^{k+1}_0 = v^0_0, nu^{k+1}_0 = nu^0_0, F^{EX,k+1}_0 = F^{EX,0}_0
+    for (int m = 1; m <= M; ++m) {
+      const double* new_fex_prev = (m == 1) ? c->sFEX[0] : stage;
+      const double* nu_prev = c->snu[m - 1];         // nu^{k+1}_{m-1}
+      TRY(eval_vb(c, tm[m], &vb));
+      TRY(f_d1(c->sv[m], nu_prev, tm[m], Fp1));       // F'_d1 = F_d1(nu^{k+1}_{m-1}, v^k_m)
+      TRY(graddiv(c, c->sv[m], nu_prev, Fp3, nullptr)); // F'_d3 = F_d3(nu^{k+1}_{m-1}, v^k_m)
+      // v' = v^{k+1}_{m-1} + dt_m [F^{EX,k+1}_{m-1} + F'_d1 + F'_d3 - (F^{EX,k}_{m-1} + F^{IM,k}_m)] + S^k_m
+      LinComb lc{};
+      int n = 0;
+      lc.x[n] = c->sv[m - 1]; lc.c[n++] = 1.0;
+      lc.x[n] = new_fex_prev; lc.c[n++] = dts[m];
+      lc.x[n] = Fp1; lc.c[n++] = dts[m];
+      lc.x[n] = Fp3; lc.c[n++] = dts[m];
+      lc.x[n] = c->sFEX[m - 1]; lc.c[n++] = -dts[m];
+      lc.x[n] = c->sFIM[m]; lc.c[n++] = -dts[m];
+      for (int q = 0; q <= M; ++q) { lc.x[n] = c->sFq[q]; lc.c[n++] = dt * W[m][q]; }
+      lc.nterms = n;
+      lincomb(c->vp, lc, nt, c->st);
+      TRY(project(c, c->vp, vb, 1, c->vpp));
+      // v3 - dt_m div(nu^{k+1}_{m-1} grad v3) = v'' - dt_m (F'_d1 + F'_d3)
+      LinComb lg{};
+      lg.nterms = 3;
+      lg.x[0] = c->vpp; lg.c[0] = 1.0;
+      lg.x[1] = Fp1; lg.c[1] = -dts[m];
+      lg.x[2] = Fp3; lg.c[2] = -dts[m];
+      lincomb(gbuf, lg, nt, c->st);
+      TRY(helmholtz_stage(c, gbuf, nu_prev, dts[m], vb, c->vp));
+      c->stats.stages++;
+      if (fproj) {
+        TRY(project(c, c->vp, nullptr, 2, c->vpp));
+        CK(cudaMemcpyAsync(c->vp, c->vpp, nt * sizeof(double), cudaMemcpyDeviceToDevice, c->st), "cp");
+      }
+      CK(cudaMemcpyAsync(c->sv[m], c->vp, nt * sizeof(double), cudaMemcpyDeviceToDevice, c->st), "cp");
+      TRY(eval_nu(c, tm[m], c->sv[m], c->snu[m]));                    // nu^{k+1}_m
+      // F^{IM,k+1}_m = F_d1(nu^{k+1}_{m-1}, v^{k+1}_m)  (same lag as the initialisation)
+      TRY(f_d1(c->sv[m], nu_prev, tm[m], c->sFIM[m]));
+      if (m >= 2)
+        CK(cudaMemcpyAsync(c->sFEX[m - 1], stage, nt * sizeof(double), cudaMemcpyDeviceToDevice, c->st), "cp");
+      if (m < M) TRY(f_ex(m, stage));                                 // F^{EX,k+1}_m
+    }
+  }
+  CK(cudaMemcpyAsync(v, c->sv[M], nt * sizeof(double), cudaMemcpyDeviceToDevice, c->st), "cp");
+  return IMEX_OK;
+}
+
+imex_status check_state(imex_ctx* c) {
+  reduce_max_abs(c->v, c->nv * c->d, c->partial, c->nblocks, c->dscal + 60, c->st);
+  CK(cudaMemcpyAsync(c->hscal + 60, c->dscal + 60, sizeof(double), cudaMemcpyDeviceToHost, c->st), "cp");
+  CK(cudaStreamSynchronize(c->st), "sync");
+  const double m = c->hscal[60];
+  c->stats.max_velocity = m;
+  if (m != m) return fail(c, IMEX_EUNSTABLE, "NaN in the velocity");
+  if (c->desc.vmax > 0 && m > c->desc.vmax) return fail(c, IMEX_EUNSTABLE, "velocity above the threshold");
+  return IMEX_OK;
+}
+
+imex_status copy_in(imex_ctx* c, double* dst, const double* src, size_t n, int on_device) {
+  CK(cudaMemcpyAsync(dst, src, n * sizeof(double), on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                     c->st), "copy in");
+  return IMEX_OK;
+}
+imex_status copy_out(imex_ctx* c, double* dst, const double* src, size_t n, int on_device) {
+  CK(cudaMemcpyAsync(dst, src, n * sizeof(double), on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                     c->st), "copy out");
+  CK(cudaStreamSynchronize(c->st), "sync");
+  return IMEX_OK;
+}
+
+imex_status alloc_sdc(imex_ctx* c) {
+  const size_t nt = c->nv * c->d;
+  const int M = c->sdc_M;
+  while ((int)c->sv.size() < M + 1) {
+    double *a, *b, *f1, *f2, *f3;
+    TRY(dalloc(c, &a, nt));
+    TRY(dalloc(c, &b, c->nv));
+    TRY(dalloc(c, &f1, nt));
+    TRY(dalloc(c, &f2, nt));
+    TRY(dalloc(c, &f3, nt));
+    c->sv.push_back(a); c->snu.push_back(b); c->sFEX.push_back(f1); c->sFIM.push_back(f2); c->sFq.push_back(f3);
+  }
+  return IMEX_OK;
+}
+
+imex_status alloc_stages(imex_ctx* c, int s) {
+  const size_t nt = c->nv * c->d;
+  while ((int)c->E.size() < s) {
+    double *e, *f1, *f3, *fs;
+    TRY(dalloc(c, &e, nt));
+    TRY(dalloc(c, &f1, nt));
+    TRY(dalloc(c, &f3, nt));
+    TRY(dalloc(c, &fs, nt));
+    c->E.push_back(e); c->Fd1.push_back(f1); c->Fd3.push_back(f3); c->Fs.push_back(fs);
+  }
+  return IMEX_OK;
+}
+
+}  // namespace
+
+// =====================================================================================
+// C ABI
+// =====================================================================================
+extern "C" {
+
+imex_status imex_create(const imex_mesh_desc* desc, imex_ctx** out) {
+  if (!desc || !out) return IMEX_EINVAL;
+  *out = nullptr;
+  const int d = desc->dim;
+  if (d != 2 && d != 3) return IMEX_EINVAL;
+  if (desc->P < 2 || desc->P > IMEX_MAXN - 1) return IMEX_EINVAL;
+  for (int k = 0; k < d; ++k) {
+    if (desc->nelem[k] < 1) return IMEX_EINVAL;
+    if (!(desc->hi[k] > desc->lo[k])) return IMEX_EINVAL;
+  }
+  if (desc->precision != IMEX_FP64 && desc->precision != IMEX_MIXED) return IMEX_EINVAL;
+  if (desc->poisson != IMEX_POISSON_SIPG && desc->poisson != IMEX_POISSON_CONSISTENT) return IMEX_EINVAL;
+  imex_ctx* c = new imex_ctx();
+  c->desc = *desc;
+  if (c->desc.tol <= 0) c->desc.tol = 1e-12;
+  if (c->desc.maxit <= 0) c->desc.maxit = 5000;
+  c->d = d;
+  c->Nv = desc->P + 1;
+  c->Np = desc->P;
+  long long ne = 1;
+  Geom g{};
+  g.d = d;
+  for (int k = 0; k < 3; ++k) {
+    g.n[k] = (k < d) ? desc->nelem[k] : 1;
+    g.lo[k] = (k < d) ? desc->lo[k] : 0.0;
+    g.h[k] = (k < d) ? (desc->hi[k] - desc->lo[k]) / desc->nelem[k] : 1.0;
+    ne *= g.n[k];
+  }
+  if (ne > (1LL << 30)) { delete c; return IMEX_EINVAL; }
+  g.ne = (int)ne;
+  c->gv = g;
+  c->gp = g;
+  for (int k = 0; k < 3; ++k) {
+    const bool per = (k >= d) || desc->periodic[k];
+    c->gv.bc[k] = per ? 0 : 1;
+    c->gp.bc[k] = per ? 0 : 2;
+  }
+  c->nv = (size_t)ne * ipow(c->Nv, d);
+  c->np = (size_t)ne * ipow(c->Np, d);
+  if (desc->stream) {
+    c->st = (cudaStream_t)desc->stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&c->st, cudaStreamNonBlocking) != cudaSuccess) { delete c; return IMEX_ECUDA; }
+    c->own_stream = true;
+  }
+  imex_status s = IMEX_OK;
+  auto bail = [&](imex_status e) {
+    imex_destroy(c);
+    return e;
+  };
+  // tables
+  {
+    Tables<double>* h64 = new Tables<double>();
+    Tables<float>* h32 = new Tables<float>();
+    build_tables(h64, h32);
+    s = dalloc(c, &c->dtab64, 1);
+    if (s == IMEX_OK) s = dalloc(c, &c->dtab32, 1);
+    if (s == IMEX_OK && cudaMemcpy(c->dtab64, h64, sizeof(*h64), cudaMemcpyHostToDevice) != cudaSuccess) s = IMEX_ECUDA;
+    if (s == IMEX_OK && cudaMemcpy(c->dtab32, h32, sizeof(*h32), cudaMemcpyHostToDevice) != cudaSuccess) s = IMEX_ECUDA;
+    delete h64;
+    delete h32;
+    if (s != IMEX_OK) return bail(s);
+    c->gv.tab64 = c->gp.tab64 = c->dtab64;
+    c->gv.tab32 = c->gp.tab32 = c->dtab32;
+  }
+  const size_t nt = c->nv * d;
+  const size_t big = std::max(nt, c->np);
+  double** f64[] = {&c->v, &c->vp, &c->vpp, &c->g, &c->tmp, &c->vb, &c->cx, &c->cr, &c->cz, &c->cp, &c->cAp};
+  for (double** p : f64) if ((s = dalloc(c, p, big)) != IMEX_OK) return bail(s);
+  if ((s = dalloc(c, &c->nu, c->nv)) != IMEX_OK) return bail(s);
+  if ((s = dalloc(c, &c->nu_fixed, c->nv)) != IMEX_OK) return bail(s);
+  if ((s = dalloc(c, &c->phi, c->nv)) != IMEX_OK) return bail(s);
+  if ((s = dalloc(c, &c->jac, c->nv * d * d)) != IMEX_OK) return bail(s);
+  if ((s = dalloc(c, &c->psi, c->np)) != IMEX_OK) return bail(s);
+  if ((s = dalloc(c, &c->bp, c->np)) != IMEX_OK) return bail(s);
+  if ((s = dalloc(c, &c->mass_v, c->nv)) != IMEX_OK) return bail(s);
+  if ((s = dalloc(c, &c->mass_p, c->np)) != IMEX_OK) return bail(s);
+  if ((s = dalloc(c, &c->cdiag, c->np + c->nv)) != IMEX_OK) return bail(s);
+  float** f32[] = {&c->fx, &c->fr, &c->fz, &c->fp, &c->fAp};
+  for (float** p : f32) if ((s = dalloc(c, p, big)) != IMEX_OK) return bail(s);
+  if ((s = dalloc(c, &c->fdiag, c->np + c->nv)) != IMEX_OK) return bail(s);
+  if ((s = dalloc(c, &c->fnu, c->nv)) != IMEX_OK) return bail(s);
+  if ((s = dalloc(c, &c->fvtmp, nt + c->np)) != IMEX_OK) return bail(s);
+  c->nblocks = 152 * 4;
+  if ((s = dalloc(c, &c->partial, (size_t)c->nblocks * 8)) != IMEX_OK) return bail(s);
+  if ((s = dalloc(c, &c->dscal, 128)) != IMEX_OK) return bail(s);
+  if ((s = dalloc(c, &c->iscal, 64)) != IMEX_OK) return bail(s);
+  if (cudaMallocHost((void**)&c->hscal, 128 * sizeof(double)) != cudaSuccess) return bail(IMEX_ENOMEM);
+  if (cudaMallocHost((void**)&c->hiscal, 64 * sizeof(int)) != cudaSuccess) return bail(IMEX_ENOMEM);
+  cudaMemsetAsync(c->psi, 0, c->np * sizeof(double), c->st);
+  cudaMemsetAsync(c->v, 0, big * sizeof(double), c->st);
+  // mass diagonals: apply alpha=1, beta=0 to a ones vector via the diag kernel (beta = 0)
+  {
+    SipgArgs<double> a = sipg_args<double>(nullptr, c->mass_v, 1, (long long)c->nv, nullptr, 0.0, nullptr, 1.0, 0.0, 0);
+    if (sipg_diag<double>(c->gv, c->Nv, a, c->st) != 0) return bail(IMEX_EINVAL);
+    SipgArgs<double> b = sipg_args<double>(nullptr, c->mass_p, 1, (long long)c->np, nullptr, 0.0, nullptr, 1.0, 0.0, 0);
+    if (sipg_diag<double>(c->gp, c->Np, b, c->st) != 0) return bail(IMEX_EINVAL);
+  }
+  named_tableau("CB3e", &c->tab);
+  if ((s = alloc_stages(c, c->tab.s)) != IMEX_OK) return bail(s);
+  if (cudaStreamSynchronize(c->st) != cudaSuccess || cudaGetLastError() != cudaSuccess) return bail(IMEX_ECUDA);
+  *out = c;
+  return IMEX_OK;
+}
+
+void imex_destroy(imex_ctx* c) {
+  if (!c) return;
+  if (c->st) cudaStreamSynchronize(c->st);
+  for (auto& P : c->profc)
+    for (auto& e : P.ev) cudaEventDestroy(e);
+  for (void* p : c->allocs) cudaFree(p);
+  if (c->hscal) cudaFreeHost(c->hscal);
+  if (c->hiscal) cudaFreeHost(c->hiscal);
+  if (c->own_stream && c->st) cudaStreamDestroy(c->st);
+  delete c;
+}
+
+const char* imex_last_error(const imex_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+imex_status imex_sizes(const imex_ctx* c, long long* nvel, long long* npres) {
+  if (!c) return IMEX_EINVAL;
+  if (nvel) *nvel = (long long)c->nv;
+  if (npres) *npres = (long long)c->np;
+  return IMEX_OK;
+}
+
+imex_status imex_set_tableau(imex_ctx* c, int s, const double* cc, const double* AI, const double* bI,
+                             const double* AE, const double* bE) {
+  if (!c || !cc || !AI || !bI || !AE || !bE || s < 2 || s > 8) return fail(c, IMEX_EINVAL, "bad tableau arguments");
+  Tab t;
+  t.s = s;
+  for (int i = 0; i < s; ++i) {
+    t.c[i] = cc[i]; t.bI[i] = bI[i]; t.bE[i] = bE[i];
+    for (int j = 0; j < s; ++j) { t.AI[i][j] = AI[i * s + j]; t.AE[i][j] = AE[i * s + j]; }
+  }
+  if (!valid_tableau(t)) return fail(c, IMEX_EINVAL, "tableau is not of CK form");
+  TRY(alloc_stages(c, s));
+  c->tab = t;
+  c->use_sdc = false;
+  return IMEX_OK;
+}
+
+imex_status imex_set_tableau_named(imex_ctx* c, const char* name) {
+  if (!c || !name) return IMEX_EINVAL;
+  Tab t;
+  if (!named_tableau(name, &t)) return fail(c, IMEX_EINVAL, std::string("unknown tableau ") + name);
+  TRY(alloc_stages(c, t.s));
+  c->tab = t;
+  c->use_sdc = false;
+  return IMEX_OK;
+}
+
+imex_status imex_set_sdc(imex_ctx* c, int M, int K, const char* predictor) {
+  if (!c || M < 1 || M > 8 || K < 0 || K > 200) return fail(c, IMEX_EINVAL, "bad SDC parameters");
+  Tab t;
+  if (!named_tableau(predictor ? predictor : "EULER", &t)) return fail(c, IMEX_EINVAL, "unknown predictor");
+  TRY(alloc_stages(c, t.s));
+  c->sdc_M = M; c->sdc_K = K; c->sdc_pred = t;
+  TRY(alloc_sdc(c));
+  c->use_sdc = true;
+  return IMEX_OK;
+}
+
+imex_status imex_set_viscosity_const(imex_ctx* c, double nu) {
+  if (!c || !(nu >= 0)) return fail(c, IMEX_EINVAL, "bad viscosity");
+  c->nu_kind = IMEX_NU_CONST;
+  c->nu_p[0] = nu;
+  return IMEX_OK;
+}
+
+imex_status imex_set_viscosity_model(imex_ctx* c, int kind, const double* p, int np) {
+  if (!c || kind < IMEX_NU_CONST || kind > IMEX_NU_VELOCITY || np < 0 || np > 8 || (np > 0 && !p))
+    return fail(c, IMEX_EINVAL, "bad viscosity model");
+  if (kind == IMEX_NU_VELOCITY && (np < 3 || !(p[2] > 0))) return fail(c, IMEX_EINVAL, "nu(v) needs nu0, nu1, vmax");
+  c->nu_kind = kind;
+  std::memset(c->nu_p, 0, sizeof(c->nu_p));
+  for (int i = 0; i < np; ++i) c->nu_p[i] = p[i];
+  return IMEX_OK;
+}
+
+imex_status imex_set_viscosity_field(imex_ctx* c, const double* nu, int on_device) {
+  if (!c || !nu) return IMEX_EINVAL;
+  TRY(copy_in(c, c->nu_fixed, nu, c->nv, on_device));
+  c->nu_kind = IMEX_NU_FIELD;
+  return IMEX_OK;
+}
+
+imex_status imex_set_boundary(imex_ctx* c, int kind, const double* p, int np) {
+  if (!c || kind < IMEX_FLOW_NONE || kind > IMEX_FLOW_TGTRAVEL || np < 0 || np > 8 || (np > 0 && !p))
+    return fail(c, IMEX_EINVAL, "bad boundary kind");
+  c->bc_kind = kind;
+  std::memset(c->bc_p, 0, sizeof(c->bc_p));
+  for (int i = 0; i < np; ++i) c->bc_p[i] = p[i];
+  return IMEX_OK;
+}
+
+imex_status imex_set_forcing(imex_ctx* c, int kind, const double* p, int np) {
+  if (!c || kind < IMEX_FORCE_NONE || kind > IMEX_FORCE_TGTRAVEL_VARNU || np < 0 || np > 8 || (np > 0 && !p))
+    return fail(c, IMEX_EINVAL, "bad forcing kind");
+  if (kind == IMEX_FORCE_TGTRAVEL_VARNU && c->d != 2) return fail(c, IMEX_EINVAL, "forcing is 2D only");
+  c->f_kind = kind;
+  std::memset(c->f_p, 0, sizeof(c->f_p));
+  for (int i = 0; i < np; ++i) c->f_p[i] = p[i];
+  return IMEX_OK;
+}
+
+imex_status imex_set_state(imex_ctx* c, double t, const double* v, int on_device) {
+  if (!c || !v) return IMEX_EINVAL;
+  TRY(copy_in(c, c->v, v, c->nv * c->d, on_device));
+  c->t = t;
+  return IMEX_OK;
+}
+
+imex_status imex_init_flow(imex_ctx* c, int kind, const double* p, int np, double t) {
+  if (!c || kind < IMEX_FLOW_NONE || kind > IMEX_FLOW_TGTRAVEL || np < 0 || np > 8 || (np > 0 && !p))
+    return fail(c, IMEX_EINVAL, "bad flow kind");
+  double pp[8] = {0};
+  for (int i = 0; i < np; ++i) pp[i] = p[i];
+  TRY(launch_check(c, eval_field(c->gv, c->Nv, 0, spec(kind, pp), t, nullptr, (long long)c->nv, c->v, c->st),
+                   "eval_field"));
+  c->t = t;
+  return IMEX_OK;
+}
+
+imex_status imex_step(imex_ctx* c, double dt, int nsteps) {
+  if (!c || !(dt > 0) || nsteps < 0) return fail(c, IMEX_EINVAL, "bad step arguments");
+  if (has_boundary(c) && c->bc_kind == IMEX_FLOW_NONE)
+    return fail(c, IMEX_EINVAL, "non-periodic mesh needs boundary data (imex_set_boundary)");
+  auto t0 = std::chrono::steady_clock::now();
+  c->stats.poisson_solves = c->stats.helmholtz_solves = 0;
+  c->stats.poisson_iters = c->stats.helmholtz_iters = 0;
+  c->stats.refinements = 0;
+  c->stats.max_poisson_res = c->stats.max_helmholtz_res = 0.0;
+  for (int n = 0; n < nsteps; ++n) {
+    imex_status s = c->use_sdc ? sdc_step(c, c->v, c->t, dt) : rk_step(c, c->tab, c->v, c->t, dt, variable_nu(c));
+    if (s != IMEX_OK) return s;
+    c->t += dt;
+    c->stats.steps++;
+    TRY(check_state(c));
+  }
+  CK(cudaStreamSynchronize(c->st), "sync");
+  c->stats.last_call_ms =
+      std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  return IMEX_OK;
+}
+
+imex_status imex_get_velocity(imex_ctx* c, double* out, int on_device) {
+  if (!c || !out) return IMEX_EINVAL;
+  return copy_out(c, out, c->v, c->nv * c->d, on_device);
+}
+imex_status imex_get_pressure(imex_ctx* c, double* out, int on_device) {
+  if (!c || !out) return IMEX_EINVAL;
+  return copy_out(c, out, c->psi, c->np, on_device);
+}
+imex_status imex_get_time(const imex_ctx* c, double* t) {
+  if (!c || !t) return IMEX_EINVAL;
+  *t = c->t;
+  return IMEX_OK;
+}
+imex_status imex_get_stats(const imex_ctx* c, imex_stats* out) {
+  if (!c || !out) return IMEX_EINVAL;
+  *out = c->stats;
+  return IMEX_OK;
+}
+
+imex_status imex_op_sipg(imex_ctx* c, int space, const double* x, double* y, int nsys, double alpha, double beta,
+                         const double* nu, const double* gd, int minv, int precision, int on_device) {
+  if (!c || !x || !y) return IMEX_EINVAL;
+  const bool vel = space == IMEX_SPACE_VELOCITY;
+  if (!vel && space != IMEX_SPACE_PRESSURE) return fail(c, IMEX_EINVAL, "bad space");
+  if (nsys < 1 || nsys > 3 || (!vel && nsys != 1)) return fail(c, IMEX_EINVAL, "bad nsys");
+  const size_t n = vel ? c->nv : c->np;
+  const Geom& g = vel ? c->gv : c->gp;
+  const int N = vel ? c->Nv : c->Np;
+  TRY(copy_in(c, c->cx, x, n * nsys, on_device));
+  const double* dnu = nullptr;
+  if (nu && vel) { TRY(copy_in(c, c->nu, nu, c->nv, on_device)); dnu = c->nu; }
+  const double* dg = nullptr;
+  if (gd) { TRY(copy_in(c, c->vb, gd, n * nsys, on_device)); dg = c->vb; }
+  const double nu0 = vel ? nu_const(c) : 1.0;
+  if (precision == IMEX_FP64) {
+    SipgArgs<double> a = sipg_args<double>(c->cx, c->cAp, nsys, (long long)n, dnu, nu0, dg, alpha, beta, minv);
+    TRY(launch_check(c, sipg_apply<double>(g, N, a, c->st), "sipg_apply"));
+  } else {
+    convert_d2f(c->cx, c->fx, n * nsys, c->st);
+    const float* fnu = nullptr;
+    if (dnu) { convert_d2f(dnu, c->fnu, c->nv, c->st); fnu = c->fnu; }
+    const float* fg = nullptr;
+    if (dg) { convert_d2f(dg, c->fr, n * nsys, c->st); fg = c->fr; }
+    SipgArgs<float> a = sipg_args<float>(c->fx, c->fAp, nsys, (long long)n, fnu, nu0, fg, alpha, beta, minv);
+    TRY(launch_check(c, sipg_apply<float>(g, N, a, c->st), "sipg_apply(f32)"));
+    f2d(c->fAp, c->cAp, n * nsys, c->st);
+  }
+  return copy_out(c, y, c->cAp, n * nsys, on_device);
+}
+
+imex_status imex_op_sipg_diag(imex_ctx* c, int space, double* y, double alpha, double beta, const double* nu,
+                              int on_device) {
+  if (!c || !y) return IMEX_EINVAL;
+  const bool vel = space == IMEX_SPACE_VELOCITY;
+  const size_t n = vel ? c->nv : c->np;
+  const double* dnu = nullptr;
+  if (nu && vel) { TRY(copy_in(c, c->nu, nu, c->nv, on_device)); dnu = c->nu; }
+  SipgArgs<double> a = sipg_args<double>(nullptr, c->cAp, 1, (long long)n, dnu, vel ? nu_const(c) : 1.0, nullptr,
+                                         alpha, beta, 0);
+  TRY(launch_check(c, sipg_diag<double>(vel ? c->gv : c->gp, vel ? c->Nv : c->Np, a, c->st), "sipg_diag"));
+  return copy_out(c, y, c->cAp, n, on_device);
+}
+
+imex_status imex_op_div(imex_ctx* c, const double* v, const double* w, int mode, double* b, int on_device) {
+  if (!c || !v || !b || mode < 0 || mode > 2 || (mode == 1 && !w)) return IMEX_EINVAL;
+  TRY(copy_in(c, c->cx, v, c->nv * c->d, on_device));
+  if (mode == 1) TRY(copy_in(c, c->vb, w, c->nv * c->d, on_device));
+  DivArgs<double> da{c->cx, (long long)c->nv, c->vb, mode, 1.0, c->bp};
+  TRY(launch_check(c, dg_div<double>(c->gv, c->Nv, da, c->st), "dg_div"));
+  return copy_out(c, b, c->bp, c->np, on_device);
+}
+
+imex_status imex_op_grad(imex_ctx* c, const double* psi, double* out, int on_device) {
+  if (!c || !psi || !out) return IMEX_EINVAL;
+  TRY(copy_in(c, c->bp, psi, c->np, on_device));
+  GradArgs<double> ga{c->bp, nullptr, (long long)c->nv, 1.0, c->cAp};
+  TRY(launch_check(c, dg_grad<double>(c->gv, c->Nv, ga, c->st), "dg_grad"));
+  return copy_out(c, out, c->cAp, c->nv * c->d, on_device);
+}
+
+imex_status imex_op_conv(imex_ctx* c, const double* v, const double* vb, double* out, int on_device) {
+  if (!c || !v || !out) return IMEX_EINVAL;
+  TRY(copy_in(c, c->cx, v, c->nv * c->d, on_device));
+  const double* dvb = nullptr;
+  if (vb) { TRY(copy_in(c, c->vb, vb, c->nv * c->d, on_device)); dvb = c->vb; }
+  ConvArgs<double> ca{c->cx, (long long)c->nv, dvb, 1.0, c->cAp};
+  TRY(launch_check(c, dg_conv<double>(c->gv, c->Nv, ca, c->st), "dg_conv"));
+  return copy_out(c, out, c->cAp, c->nv * c->d, on_device);
+}
+
+imex_status imex_op_graddiv(imex_ctx* c, const double* v, const double* nu, double* fd3, double* fd2,
+                            int on_device) {
+  if (!c || !v || !fd3) return IMEX_EINVAL;
+  const size_t nt = c->nv * c->d;
+  TRY(copy_in(c, c->cx, v, nt, on_device));
+  const int saved = c->nu_kind;
+  const double* dnu = nullptr;
+  if (nu) { TRY(copy_in(c, c->nu, nu, c->nv, on_device)); dnu = c->nu; c->nu_kind = IMEX_NU_FIELD; }
+  CK(cudaMemsetAsync(c->cz, 0, nt * sizeof(double), c->st), "memset");
+  imex_status s = graddiv(c, c->cx, dnu, c->cAp, fd2 ? c->cz : nullptr);
+  c->nu_kind = saved;
+  TRY(s);
+  TRY(copy_out(c, fd3, c->cAp, nt, on_device));
+  if (fd2) TRY(copy_out(c, fd2, c->cz, nt, on_device));
+  return IMEX_OK;
+}
+
+imex_status imex_solve_poisson(imex_ctx* c, const double* b, double* psi, int on_device) {
+  if (!c || !b || !psi) return IMEX_EINVAL;
+  TRY(copy_in(c, c->bp, b, c->np, on_device));
+  CK(cudaMemsetAsync(c->psi, 0, c->np * sizeof(double), c->st), "memset");
+  double res = 0.0;
+  long long its = 0;
+  TRY(solve_poisson(c, c->bp, c->psi, &its, &res));
+  c->stats.poisson_iters = its;
+  c->stats.max_poisson_res = res;
+  return copy_out(c, psi, c->psi, c->np, on_device);
+}
+
+imex_status imex_solve_helmholtz(imex_ctx* c, const double* gf, const double* nu, double gamma, const double* vb,
+                                 double* v, int on_device) {
+  if (!c || !gf || !v || !(gamma >= 0)) return IMEX_EINVAL;
+  const size_t nt = c->nv * c->d;
+  TRY(copy_in(c, c->g, gf, nt, on_device));
+  const int saved = c->nu_kind;
+  if (nu) { TRY(copy_in(c, c->nu, nu, c->nv, on_device)); c->nu_kind = IMEX_NU_FIELD; }
+  const double* dvb = nullptr;
+  if (vb) { TRY(copy_in(c, c->vb, vb, nt, on_device)); dvb = c->vb; }
+  c->stats.helmholtz_iters = 0;
+  imex_status s = helmholtz_stage(c, c->g, nu ? c->nu : nullptr, gamma, dvb, c->vpp);
+  c->nu_kind = saved;
+  TRY(s);
+  return copy_out(c, v, c->vpp, nt, on_device);
+}
+
+imex_status imex_eval_field(imex_ctx* c, int what, int kind, const double* p, int np, double t, const double* v,
+                            double* out, int on_device) {
+  if (!c || !out || what < 0 || what > 2 || np < 0 || np > 8 || (np > 0 && !p)) return IMEX_EINVAL;
+  double pp[8] = {0};
+  for (int i = 0; i < np; ++i) pp[i] = p[i];
+  const double* dv = nullptr;
+  if (v) { TRY(copy_in(c, c->cx, v, c->nv * c->d, on_device)); dv = c->cx; }
+  TRY(launch_check(c, eval_field(c->gv, c->Nv, what, spec(kind, pp), t, dv, (long long)c->nv, c->cAp, c->st),
+                   "eval_field"));
+  return copy_out(c, out, c->cAp, (what == 1 ? 1 : c->d) * c->nv, on_device);
+}
+
+imex_status imex_profile(imex_ctx* c, int enable) {
+  if (!c) return IMEX_EINVAL;
+  for (int k = 0; k < IMEX_PROF_NCLASS; ++k) {
+    prof_flush(c, k);
+    c->profc[k].n = 0;
+    c->profc[k].ms = 0.0;
+  }
+  c->prof = enable != 0;
+  return IMEX_OK;
+}
+
+imex_status imex_profile_read(imex_ctx* c, int cls, long long* launches, double* total_ms) {
+  if (!c || cls < 0 || cls >= IMEX_PROF_NCLASS) return IMEX_EINVAL;
+  CK(cudaStreamSynchronize(c->st), "sync");
+  prof_flush(c, cls);
+  if (launches) *launches = c->profc[cls].n;
+  if (total_ms) *total_ms = c->profc[cls].ms;
+  return IMEX_OK;
+}
+
+long long imex_launch_count(void) { return imex::launch_count(); }
+
+}  // extern "C"
+
+namespace imex {
+__global__ void f2d_kernel(const float* in, double* out, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    out[i] = (double)in[i];
+}
+}  // namespace imex
+void f2d(const float* in, double* out, size_t n, cudaStream_t st) {
+  IMEX_COUNTED(imex::f2d_kernel<<<(unsigned)std::min<size_t>((n + 255) / 256, 1216), 256, 0, st>>>(in, out, n));
+}

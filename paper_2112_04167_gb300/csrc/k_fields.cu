@@ -1,0 +1,117 @@
+// Pointwise fields evaluated on the device at the GLL nodes: closed-form flows
+// used as initial / boundary data (Sec. 4.1 traveling Taylor-Green vortex, the
+// decaying 2D Taylor-Green vortex, the 3D Taylor-Green initial field of
+// Sec. 4.3), viscosity laws (constant, nu(x, y, t), nu(|v|) of Sec. 4.2) and the
+// manufactured forcing that makes the traveling vortex exact under the variable
+// viscosity nu(x, y, t).
+#include <math.h>
+
+#include "../../include/imex.h"
+#include "common.cuh"
+#include "kernels.h"
+
+namespace imex {
+
+__device__ void flow_velocity(int kind, const double* p, const double* X, double t, int d, double* out) {
+  const double x = X[0], y = X[1], z = (d > 2) ? X[2] : 0.0;
+  if (kind == IMEX_FLOW_TG2D) {
+    const double F = exp(-2.0 * p[0] * t);
+    out[0] = sin(x) * cos(y) * F;
+    out[1] = -cos(x) * sin(y) * F;
+    if (d > 2) out[2] = 0.0;
+  } else if (kind == IMEX_FLOW_TG3D) {
+    out[0] = sin(x) * cos(y) * cos(z);
+    out[1] = -cos(x) * sin(y) * cos(z);
+    if (d > 2) out[2] = 0.0;
+  } else if (kind == IMEX_FLOW_TGTRAVEL) {
+    const double tp = 2.0 * M_PI;
+    const double a = tp * (x - t), b = tp * (y - 0.125 - t);
+    const double F = exp(-8.0 * M_PI * M_PI * p[0] * t);
+    out[0] = 1.0 + sin(a) * cos(b) * F;
+    out[1] = 1.0 - cos(a) * sin(b) * F;
+    if (d > 2) out[2] = 0.0;
+  } else {
+    for (int c = 0; c < d; ++c) out[c] = 0.0;
+  }
+}
+
+__device__ double viscosity(int kind, const double* p, const double* X, double t, const double* v, int d) {
+  if (kind == IMEX_NU_VARXYT) {
+    const double tp = 2.0 * M_PI;
+    return p[0] * (1.0 + 0.5 * sin(tp * X[0]) * sin(tp * X[1]) * cos(t));
+  }
+  if (kind == IMEX_NU_VELOCITY) {
+    double m2 = 0.0;
+    for (int c = 0; c < d; ++c) m2 += v[c] * v[c];
+    return p[0] + p[1] * m2 / (p[2] * p[2]);
+  }
+  return p[0];
+}
+
+// f = (nu0 - nu) lap v - (grad v + grad v^T) grad nu for the traveling vortex, nu = nu(x, y, t)
+__device__ void forcing_tgtravel_varnu(const double* p, const double* X, double t, double* f) {
+  const double nu0 = p[0];
+  const double tp = 2.0 * M_PI;
+  const double x = X[0], y = X[1];
+  const double a = tp * (x - t), b = tp * (y - 0.125 - t);
+  const double F = exp(-8.0 * M_PI * M_PI * nu0 * t);
+  const double sa = sin(a), ca = cos(a), sb = sin(b), cb = cos(b);
+  const double vx = sa * cb * F, vy = -ca * sb * F;      // oscillating parts
+  const double lapx = -8.0 * M_PI * M_PI * vx, lapy = -8.0 * M_PI * M_PI * vy;
+  const double nu = nu0 * (1.0 + 0.5 * sin(tp * x) * sin(tp * y) * cos(t));
+  const double cgn = 0.5 * nu0 * cos(t) * tp;
+  const double gnx = cgn * cos(tp * x) * sin(tp * y), gny = cgn * sin(tp * x) * cos(tp * y);
+  const double G00 = tp * ca * cb * F, G01 = -tp * sa * sb * F;
+  const double G10 = tp * sa * sb * F, G11 = -tp * ca * cb * F;
+  f[0] = (nu0 - nu) * lapx - (gnx * (G00 + G00) + gny * (G01 + G10));
+  f[1] = (nu0 - nu) * lapy - (gnx * (G10 + G01) + gny * (G11 + G11));
+}
+
+template <int D, int N>
+__global__ void field_kernel(Geom g, int what, FieldSpec fs, double t, const double* __restrict__ v,
+                             long long stride, double* __restrict__ out) {
+  constexpr int ND = ipow(N, D);
+  const size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (idx >= (size_t)g.ne * ND) return;
+  const int e = (int)(idx / ND), node = (int)(idx % ND);
+  int ec[3];
+  elem_coords(g, e, ec);
+  int id[3] = {node % N, (D > 1) ? (node / N) % N : 0, (D > 2) ? node / (N * N) : 0};
+  const double* xi = tab<double>(g).x[N];
+  double X[3] = {0, 0, 0};
+  for (int k = 0; k < D; ++k) X[k] = g.lo[k] + (ec[k] + 0.5 * (xi[id[k]] + 1.0)) * g.h[k];
+  if (what == 0) {
+    double u[3];
+    flow_velocity(fs.kind, fs.p, X, t, D, u);
+    for (int c = 0; c < D; ++c) out[(size_t)c * stride + idx] = u[c];
+  } else if (what == 1) {
+    double u[3] = {0, 0, 0};
+    if (v) for (int c = 0; c < D; ++c) u[c] = v[(size_t)c * stride + idx];
+    out[idx] = viscosity(fs.kind, fs.p, X, t, u, D);
+  } else {
+    double f[3] = {0, 0, 0};
+    if (fs.kind == IMEX_FORCE_TGTRAVEL_VARNU && D == 2) forcing_tgtravel_varnu(fs.p, X, t, f);
+    for (int c = 0; c < D; ++c) out[(size_t)c * stride + idx] = f[c];
+  }
+}
+
+template <int D, int N>
+static void launch_field(const Geom& g, int what, const FieldSpec& fs, double t, const double* v,
+                         long long stride, double* out, cudaStream_t st) {
+  const size_t n = (size_t)g.ne * ipow(N, D);
+  IMEX_COUNTED(field_kernel<D, N><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(g, what, fs, t, v, stride, out));
+}
+
+int eval_field(const Geom& g, int N, int what, const FieldSpec& fs, double t, const double* v,
+               long long stride, double* out, cudaStream_t st) {
+#define IMEX_FIELD_CASE(DD, NN) \
+  if (g.d == DD && N == NN) { launch_field<DD, NN>(g, what, fs, t, v, stride, out, st); return 0; }
+  IMEX_FIELD_CASE(2, 3) IMEX_FIELD_CASE(2, 4) IMEX_FIELD_CASE(2, 5) IMEX_FIELD_CASE(2, 6)
+  IMEX_FIELD_CASE(2, 7) IMEX_FIELD_CASE(2, 8) IMEX_FIELD_CASE(2, 9)
+  IMEX_FIELD_CASE(3, 3) IMEX_FIELD_CASE(3, 4) IMEX_FIELD_CASE(3, 5) IMEX_FIELD_CASE(3, 6)
+  IMEX_FIELD_CASE(3, 7) IMEX_FIELD_CASE(3, 8) IMEX_FIELD_CASE(3, 9)
+#undef IMEX_FIELD_CASE
+  return -1;
+}
+
+}  // namespace imex

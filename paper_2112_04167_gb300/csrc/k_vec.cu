@@ -1,0 +1,361 @@
+// Vector kernels: stage linear combinations (FP64), deterministic two-level
+// reductions (FP64 accumulation), precision conversion, and the fused
+// Jacobi-PCG updates whose scalars stay in device memory.
+#include "common.cuh"
+#include "kernels.h"
+#include "vec.h"
+
+#include <atomic>
+
+namespace imex {
+
+static std::atomic<long long> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
+
+__global__ void lincomb_kernel(double* __restrict__ out, LinComb lc, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    double s = 0.0;
+#pragma unroll 4
+    for (int j = 0; j < lc.nterms; ++j) s += lc.c[j] * lc.x[j][i];
+    out[i] = s;
+  }
+}
+
+static int grid_for(size_t n, int threads) {
+  size_t b = (n + threads - 1) / threads;
+  const size_t cap = 152 * 8;
+  if (b > cap) b = cap;
+  if (b < 1) b = 1;
+  return (int)b;
+}
+
+void lincomb(double* out, const LinComb& lc, size_t n, cudaStream_t st) {
+  if (n == 0) return;
+  IMEX_COUNTED(lincomb_kernel<<<grid_for(n, 256), 256, 0, st>>>(out, lc, n));
+}
+
+// ---- block reduction helpers ----------------------------------------------------
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+  return v;
+}
+// sum over the block (blockDim.x multiple of 32, <= 1024); result valid in thread 0
+__device__ __forceinline__ double block_sum(double v) {
+  __shared__ double ws[32];
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) ws[w] = v;
+  __syncthreads();
+  v = (threadIdx.x < (blockDim.x >> 5)) ? ws[lane] : 0.0;
+  if (w == 0) v = warp_sum(v);
+  return v;
+}
+__device__ __forceinline__ double block_max(double v) {
+  __shared__ double ws[32];
+  v = warp_max(v);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) ws[w] = v;
+  __syncthreads();
+  v = (threadIdx.x < (blockDim.x >> 5)) ? ws[lane] : 0.0;
+  if (w == 0) v = warp_max(v);
+  return v;
+}
+
+template <typename T>
+__global__ void dot_partial_kernel(const T* __restrict__ x, const T* __restrict__ y, size_t n,
+                                   long long stride, double* __restrict__ partial) {
+  const int s = blockIdx.y;
+  const T* xs = x + (size_t)s * stride;
+  const T* ys = y + (size_t)s * stride;
+  double acc = 0.0;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    acc += (double)xs[i] * (double)ys[i];
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) partial[(size_t)s * gridDim.x + blockIdx.x] = acc;
+}
+
+// fixed-order final sum of nblocks partials per system
+__global__ void finish_sum_kernel(const double* __restrict__ partial, int nblocks, double* __restrict__ dst) {
+  const int s = blockIdx.x;
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < nblocks; i += blockDim.x) acc += partial[(size_t)s * nblocks + i];
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) dst[s] = acc;
+}
+
+template <typename T>
+static int dot_impl(const T* x, const T* y, size_t n, long long stride, int nsys, double* partial,
+                    int nblocks, double* dst, cudaStream_t st) {
+  dim3 grid(nblocks, nsys);
+  IMEX_COUNTED(dot_partial_kernel<T><<<grid, 256, 0, st>>>(x, y, n, stride, partial));
+  IMEX_COUNTED(finish_sum_kernel<<<nsys, 256, 0, st>>>(partial, nblocks, dst));
+  return 0;
+}
+
+int dot_batched(const double* x, const double* y, size_t n, long long stride, int nsys, double* partial,
+                int nblocks, double* dst, cudaStream_t st) {
+  return dot_impl<double>(x, y, n, stride, nsys, partial, nblocks, dst, st);
+}
+int dot_batched_f(const float* x, const float* y, size_t n, long long stride, int nsys, double* partial,
+                  int nblocks, double* dst, cudaStream_t st) {
+  return dot_impl<float>(x, y, n, stride, nsys, partial, nblocks, dst, st);
+}
+
+__global__ void sum_partial_kernel(const double* __restrict__ x, size_t n, double* __restrict__ partial) {
+  double acc = 0.0;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    acc += x[i];
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) partial[blockIdx.x] = acc;
+}
+int reduce_sum(const double* x, size_t n, double* partial, int nblocks, double* dst, cudaStream_t st) {
+  IMEX_COUNTED(sum_partial_kernel<<<nblocks, 256, 0, st>>>(x, n, partial));
+  IMEX_COUNTED(finish_sum_kernel<<<1, 256, 0, st>>>(partial, nblocks, dst));
+  return 0;
+}
+
+// max |x| with NaN propagation: a NaN entry makes the result NaN
+__global__ void maxabs_partial_kernel(const double* __restrict__ x, size_t n, double* __restrict__ partial) {
+  double m = 0.0;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    double v = fabs(x[i]);
+    m = (v != v || m != m) ? nan("") : fmax(m, v);
+  }
+  // propagate NaN through the reduction explicitly
+  __shared__ int has_nan;
+  if (threadIdx.x == 0) has_nan = 0;
+  __syncthreads();
+  if (m != m) has_nan = 1;
+  m = block_max(m != m ? 0.0 : m);
+  __syncthreads();
+  if (threadIdx.x == 0) partial[blockIdx.x] = has_nan ? nan("") : m;
+}
+__global__ void finish_max_kernel(const double* __restrict__ partial, int nblocks, double* __restrict__ dst) {
+  __shared__ int has_nan;
+  if (threadIdx.x == 0) has_nan = 0;
+  __syncthreads();
+  double m = 0.0;
+  for (int i = threadIdx.x; i < nblocks; i += blockDim.x) {
+    double v = partial[i];
+    if (v != v) has_nan = 1; else m = fmax(m, v);
+  }
+  m = block_max(m);
+  __syncthreads();
+  if (threadIdx.x == 0) dst[0] = has_nan ? nan("") : m;
+}
+int reduce_max_abs(const double* x, size_t n, double* partial, int nblocks, double* dst, cudaStream_t st) {
+  IMEX_COUNTED(maxabs_partial_kernel<<<nblocks, 256, 0, st>>>(x, n, partial));
+  IMEX_COUNTED(finish_max_kernel<<<1, 256, 0, st>>>(partial, nblocks, dst));
+  return 0;
+}
+
+// x -= num/den (w == nullptr) or x -= (num/den) elementwise constant
+__global__ void subtract_scalar_kernel(double* x, size_t n, const double* num, const double* den) {
+  const double c = num[0] / den[0];
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    x[i] -= c;
+}
+void subtract_scaled_scalar(double* x, size_t n, const double* num, const double* den, const double* w,
+                            cudaStream_t st) {
+  (void)w;
+  IMEX_COUNTED(subtract_scalar_kernel<<<grid_for(n, 256), 256, 0, st>>>(x, n, num, den));
+}
+
+__global__ void d2f_kernel(const double* in, float* out, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    out[i] = (float)in[i];
+}
+void convert_d2f(const double* in, float* out, size_t n, cudaStream_t st) {
+  IMEX_COUNTED(d2f_kernel<<<grid_for(n, 256), 256, 0, st>>>(in, out, n));
+}
+__global__ void axpy_f2d_kernel(double* y, const float* x, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    y[i] += (double)x[i];
+}
+void axpy_f2d(double* y, const float* x, size_t n, cudaStream_t st) {
+  IMEX_COUNTED(axpy_f2d_kernel<<<grid_for(n, 256), 256, 0, st>>>(y, x, n));
+}
+
+// ---- PCG kernels -----------------------------------------------------------------
+// scalars per system s: rz[s], rr[s], bb[s], pAp[s], done[s], iters[s]
+template <typename T>
+__global__ void cg_xr_kernel(T* __restrict__ x, T* __restrict__ r, const T* __restrict__ p,
+                             const T* __restrict__ Ap, const T* __restrict__ dinv, T* __restrict__ z,
+                             size_t n, long long stride, CgScalars sc, double* __restrict__ partial) {
+  const int s = blockIdx.y;
+  const bool skip = sc.done[s] != 0;
+  double arz = 0.0, arr = 0.0;
+  if (!skip) {
+    const double pap = sc.pAp[s];
+    const T alpha = (T)(pap != 0.0 ? sc.rz[s] / pap : 0.0);
+    const size_t off = (size_t)s * stride;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+      const T pi = p[off + i];
+      const T api = Ap[off + i];
+      T xi = x[off + i] + alpha * pi;
+      T ri = r[off + i] - alpha * api;
+      T zi = ri * dinv[i];
+      x[off + i] = xi;
+      r[off + i] = ri;
+      z[off + i] = zi;
+      arz += (double)ri * (double)zi;
+      arr += (double)ri * (double)ri;
+    }
+  }
+  arz = block_sum(arz);
+  arr = block_sum(arr);
+  if (threadIdx.x == 0) {
+    partial[(size_t)(2 * s) * gridDim.x + blockIdx.x] = arz;
+    partial[(size_t)(2 * s + 1) * gridDim.x + blockIdx.x] = arr;
+  }
+}
+
+// final reduction: rz_old <- rz, rz <- sum, rr <- sum, convergence flag, iteration count
+__global__ void cg_finish_kernel(const double* __restrict__ partial, int nblocks, CgScalars sc, int maxit) {
+  const int s = blockIdx.x;
+  double a = 0.0, b = 0.0;
+  for (int i = threadIdx.x; i < nblocks; i += blockDim.x) {
+    a += partial[(size_t)(2 * s) * nblocks + i];
+    b += partial[(size_t)(2 * s + 1) * nblocks + i];
+  }
+  a = block_sum(a);
+  b = block_sum(b);
+  if (threadIdx.x == 0 && sc.done[s] == 0) {
+    sc.rz_old[s] = sc.rz[s];
+    sc.rz[s] = a;
+    sc.rr[s] = b;
+    sc.iters[s] += 1;
+    if (b <= sc.tol2 * sc.bb[s] || b != b) sc.done[s] = (b != b) ? 2 : 1;
+    else if (sc.iters[s] >= maxit) sc.done[s] = 3;
+  }
+}
+
+template <typename T>
+__global__ void cg_p_kernel(T* __restrict__ p, const T* __restrict__ z, size_t n, long long stride,
+                            CgScalars sc) {
+  const int s = blockIdx.y;
+  if (sc.done[s] != 0) return;
+  const double ro = sc.rz_old[s];
+  const T beta = (T)(ro != 0.0 ? sc.rz[s] / ro : 0.0);
+  const size_t off = (size_t)s * stride;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    p[off + i] = z[off + i] + beta * p[off + i];
+}
+
+template <typename T>
+__global__ void cg_init_kernel(T* __restrict__ p, T* __restrict__ z, const T* __restrict__ r,
+                               const T* __restrict__ dinv, size_t n, long long stride,
+                               double* __restrict__ partial) {
+  const int s = blockIdx.y;
+  const size_t off = (size_t)s * stride;
+  double arz = 0.0, arr = 0.0;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    T ri = r[off + i];
+    T zi = ri * dinv[i];
+    z[off + i] = zi;
+    p[off + i] = zi;
+    arz += (double)ri * (double)zi;
+    arr += (double)ri * (double)ri;
+  }
+  arz = block_sum(arz);
+  arr = block_sum(arr);
+  if (threadIdx.x == 0) {
+    partial[(size_t)(2 * s) * gridDim.x + blockIdx.x] = arz;
+    partial[(size_t)(2 * s + 1) * gridDim.x + blockIdx.x] = arr;
+  }
+}
+
+__global__ void cg_init_finish_kernel(const double* __restrict__ partial, int nblocks, CgScalars sc) {
+  const int s = blockIdx.x;
+  double a = 0.0, b = 0.0;
+  for (int i = threadIdx.x; i < nblocks; i += blockDim.x) {
+    a += partial[(size_t)(2 * s) * nblocks + i];
+    b += partial[(size_t)(2 * s + 1) * nblocks + i];
+  }
+  a = block_sum(a);
+  b = block_sum(b);
+  if (threadIdx.x == 0) {
+    sc.rz[s] = a;
+    sc.rr[s] = b;
+    sc.iters[s] = 0;
+    sc.done[s] = (b <= sc.tol2 * sc.bb[s]) ? 1 : 0;
+  }
+}
+
+// pAp from the dot partials, skipping converged systems
+__global__ void cg_pap_kernel(const double* __restrict__ partial, int nblocks, CgScalars sc) {
+  const int s = blockIdx.x;
+  double a = 0.0;
+  for (int i = threadIdx.x; i < nblocks; i += blockDim.x) a += partial[(size_t)s * nblocks + i];
+  a = block_sum(a);
+  if (threadIdx.x == 0) sc.pAp[s] = a;
+}
+
+template <typename T>
+void cg_init(T* p, T* z, const T* r, const T* dinv, size_t n, long long stride, int nsys, const CgScalars& sc,
+             double* partial, int nblocks, cudaStream_t st) {
+  dim3 grid(nblocks, nsys);
+  IMEX_COUNTED(cg_init_kernel<T><<<grid, 256, 0, st>>>(p, z, r, dinv, n, stride, partial));
+  IMEX_COUNTED(cg_init_finish_kernel<<<nsys, 256, 0, st>>>(partial, nblocks, sc));
+}
+
+template <typename T>
+void cg_pap(const T* p, const T* Ap, size_t n, long long stride, int nsys, const CgScalars& sc,
+            double* partial, int nblocks, cudaStream_t st) {
+  dim3 grid(nblocks, nsys);
+  IMEX_COUNTED(dot_partial_kernel<T><<<grid, 256, 0, st>>>(p, Ap, n, stride, partial));
+  IMEX_COUNTED(cg_pap_kernel<<<nsys, 256, 0, st>>>(partial, nblocks, sc));
+}
+
+template <typename T>
+void cg_step_xr(T* x, T* r, const T* p, const T* Ap, const T* dinv, T* z, size_t n, long long stride,
+                int nsys, const CgScalars& sc, int maxit, double* partial, int nblocks, cudaStream_t st) {
+  dim3 grid(nblocks, nsys);
+  IMEX_COUNTED(cg_xr_kernel<T><<<grid, 256, 0, st>>>(x, r, p, Ap, dinv, z, n, stride, sc, partial));
+  IMEX_COUNTED(cg_finish_kernel<<<nsys, 256, 0, st>>>(partial, nblocks, sc, maxit));
+}
+
+template <typename T>
+void cg_step_p(T* p, const T* z, size_t n, long long stride, int nsys, const CgScalars& sc, int nblocks,
+               cudaStream_t st) {
+  dim3 grid(nblocks, nsys);
+  IMEX_COUNTED(cg_p_kernel<T><<<grid, 256, 0, st>>>(p, z, n, stride, sc));
+}
+
+template <typename T>
+__global__ void recip_kernel(T* d, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    d[i] = T(1) / d[i];
+}
+template <typename T>
+void reciprocal(T* d, size_t n, cudaStream_t st) {
+  IMEX_COUNTED(recip_kernel<T><<<grid_for(n, 256), 256, 0, st>>>(d, n));
+}
+
+template void cg_init<double>(double*, double*, const double*, const double*, size_t, long long, int,
+                              const CgScalars&, double*, int, cudaStream_t);
+template void cg_init<float>(float*, float*, const float*, const float*, size_t, long long, int,
+                             const CgScalars&, double*, int, cudaStream_t);
+template void cg_pap<double>(const double*, const double*, size_t, long long, int, const CgScalars&, double*,
+                             int, cudaStream_t);
+template void cg_pap<float>(const float*, const float*, size_t, long long, int, const CgScalars&, double*,
+                            int, cudaStream_t);
+template void cg_step_xr<double>(double*, double*, const double*, const double*, const double*, double*,
+                                 size_t, long long, int, const CgScalars&, int, double*, int, cudaStream_t);
+template void cg_step_xr<float>(float*, float*, const float*, const float*, const float*, float*, size_t,
+                                long long, int, const CgScalars&, int, double*, int, cudaStream_t);
+template void cg_step_p<double>(double*, const double*, size_t, long long, int, const CgScalars&, int,
+                                cudaStream_t);
+template void cg_step_p<float>(float*, const float*, size_t, long long, int, const CgScalars&, int,
+                               cudaStream_t);
+template void reciprocal<double>(double*, size_t, cudaStream_t);
+template void reciprocal<float>(float*, size_t, cudaStream_t);
+
+}  // namespace imex

@@ -1,0 +1,123 @@
+// Launchers of the device kernels (host-callable, C++ linkage inside the library).
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+#include "common.cuh"
+
+namespace imex {
+
+// y = alpha M x + beta (A(nu) x - r_b(g)), optionally scaled by M^{-1}; nsys systems
+// (vector components) share nu and the geometry.
+template <typename T>
+struct SipgArgs {
+  const T* x;
+  T* y;
+  int nsys;
+  long long sys_stride;
+  const T* nu;      // nodal viscosity, or nullptr for nu0
+  T nu0;
+  const T* gdata;   // Dirichlet data (nodal), or nullptr
+  long long g_stride;
+  T alpha, beta;
+  int minv;
+};
+
+template <typename T> int sipg_apply(const Geom& g, int N, const SipgArgs<T>& a, cudaStream_t st);
+template <typename T> int sipg_diag(const Geom& g, int N, const SipgArgs<T>& a, cudaStream_t st);
+
+// Weak divergence into the pressure test space (Nv velocity points, Nv-1 pressure points):
+//   b = coef * ( B v - int_{dOmega} (n . w) q ),   w = wdata (mode 1), w = v (mode 2), none (mode 0)
+// v, wdata: d components with stride v_stride.
+template <typename T>
+struct DivArgs {
+  const T* v;
+  long long v_stride;
+  const T* wdata;
+  int mode;
+  T coef;
+  T* b;
+};
+template <typename T> int dg_div(const Geom& g, int Nv, const DivArgs<T>& a, cudaStream_t st);
+
+// DG gradient of a pressure field into the velocity space, out_k = base_k + coef * (M^{-1} B^T psi)_k.
+template <typename T>
+struct GradArgs {
+  const T* psi;
+  const T* base;     // may be nullptr (then 0)
+  long long stride;  // component stride of base / out
+  T coef;
+  T* out;
+};
+template <typename T> int dg_grad(const Geom& g, int Nv, const GradArgs<T>& a, cudaStream_t st);
+
+// Nodal DG derivatives (central flux inside, own trace at domain boundaries):
+//   op 0: out = nu * sum_k D_k in_k                     (in: d fields, out: 1 field)
+//   op 1: out_c = coef * D_c in_0                      (in: 1 field,  out: d fields)
+//   op 2: out_{c*d+k} = nu * D_c in_k                  (in: d fields, out: d*d fields)
+//   op 3: out_c = out_c + coef * sum_k D_k in_{c*d+k}  (in: d*d fields, out: d fields, accumulates)
+template <typename T>
+struct DerivArgs {
+  int op;
+  const T* in;
+  long long stride;
+  const T* nu;
+  T nu0;
+  T coef;
+  T* out;
+};
+template <typename T> int dg_deriv(const Geom& g, int N, const DerivArgs<T>& a, cudaStream_t st);
+
+// Convection F_c = M^{-1} [ sum_K int (v v) : grad w - sum_F int H . w ], LLF flux, Gauss
+// over-integration; vb: Dirichlet data (nodal), out = coef * F_c.
+template <typename T>
+struct ConvArgs {
+  const T* v;
+  long long stride;
+  const T* vb;
+  T coef;
+  T* out;
+};
+template <typename T> int dg_conv(const Geom& g, int N, const ConvArgs<T>& a, cudaStream_t st);
+
+// ---- vector kernels (k_vec.cu) ------------------------------------------------
+#define IMEX_MAXTERMS 16
+struct LinComb {
+  const double* x[IMEX_MAXTERMS];
+  double c[IMEX_MAXTERMS];
+  int nterms;
+};
+// out[i] = c0 * x0[i] + sum c_j x_j[i]   (x0 may be out itself)
+void lincomb(double* out, const LinComb& lc, size_t n, cudaStream_t st);
+
+// partial sums for deterministic dots: two-level reduction into dst[0..nsys)
+int dot_batched(const double* x, const double* y, size_t n, long long stride, int nsys,
+                double* partial, int nblocks, double* dst, cudaStream_t st);
+int dot_batched_f(const float* x, const float* y, size_t n, long long stride, int nsys,
+                  double* partial, int nblocks, double* dst, cudaStream_t st);
+int reduce_sum(const double* x, size_t n, double* partial, int nblocks, double* dst, cudaStream_t st);
+int reduce_max_abs(const double* x, size_t n, double* partial, int nblocks, double* dst,
+                   cudaStream_t st);
+
+// x[i] -= (sum_j w_j x_j) / (sum_j w_j) for a precomputed scalar pair in dev memory
+void subtract_scaled_scalar(double* x, size_t n, const double* num, const double* den,
+                            const double* w, cudaStream_t st);
+
+void convert_d2f(const double* in, float* out, size_t n, cudaStream_t st);
+void axpy_f2d(double* y, const float* x, size_t n, cudaStream_t st);
+
+template <typename T>
+void reciprocal(T* d, size_t n, cudaStream_t st);
+
+// ---- pointwise fields (k_fields.cu) --------------------------------------------
+// what: 0 velocity of a closed-form flow (d components), 1 viscosity (1 component),
+//       2 forcing (d components).  kind / p: the flow, viscosity law or forcing and its
+//       parameters (imex.h).  v: velocity for velocity-dependent viscosity.
+struct FieldSpec {
+  int kind;
+  double p[8];
+};
+int eval_field(const Geom& g, int N, int what, const FieldSpec& fs, double t, const double* v,
+               long long stride, double* out, cudaStream_t st);
+
+}  // namespace imex

@@ -1,0 +1,336 @@
+"""Thin ctypes binding of the C ABI in include/imex.h (argument marshalling only).
+
+Every function here forwards to the CUDA library ``_lib/libimexgb.so``; there is
+no CPU implementation behind it.  Arrays may be NumPy arrays (host memory, FP64,
+C-contiguous) or CUDA tensors exposing ``data_ptr()`` (device memory, FP64,
+contiguous).  Errors raise ``ImexError`` with the library's message.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libimexgb.so")
+
+OK, EINVAL, ENOMEM, ENOTCONV, EUNSTABLE, ECUDA = range(6)
+FP64, MIXED = 0, 1
+POISSON_SIPG, POISSON_CONSISTENT = 0, 1
+FLOW_NONE, FLOW_TG2D, FLOW_TG3D, FLOW_TGTRAVEL = 0, 1, 2, 3
+NU_CONST, NU_VARXYT, NU_VELOCITY, NU_FIELD = 0, 1, 2, 3
+FORCE_NONE, FORCE_TGTRAVEL_VARNU = 0, 1
+SPACE_VELOCITY, SPACE_PRESSURE = 0, 1
+_STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ENOTCONV", 4: "EUNSTABLE", 5: "ECUDA"}
+
+
+class ImexError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class imex_mesh_desc(C.Structure):
+    _fields_ = [("dim", C.c_int), ("P", C.c_int), ("nelem", C.c_int * 3), ("lo", C.c_double * 3),
+                ("hi", C.c_double * 3), ("periodic", C.c_int * 3), ("precision", C.c_int),
+                ("poisson", C.c_int), ("tol", C.c_double), ("maxit", C.c_int), ("inner_tol", C.c_double),
+                ("vmax", C.c_double), ("stream", C.c_void_p)]
+
+
+class imex_stats(C.Structure):
+    _fields_ = [("steps", C.c_longlong), ("stages", C.c_longlong), ("poisson_solves", C.c_int),
+                ("helmholtz_solves", C.c_int), ("poisson_iters", C.c_longlong),
+                ("helmholtz_iters", C.c_longlong), ("refinements", C.c_int), ("max_poisson_res", C.c_double),
+                ("max_helmholtz_res", C.c_double), ("div_norm", C.c_double), ("max_velocity", C.c_double),
+                ("last_call_ms", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+_P = C.c_void_p
+_D = C.POINTER(C.c_double)
+_SIGS = {
+    "imex_create": [C.POINTER(imex_mesh_desc), C.POINTER(_P)],
+    "imex_destroy": [_P],
+    "imex_last_error": [_P],
+    "imex_sizes": [_P, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)],
+    "imex_set_tableau": [_P, C.c_int, _P, _P, _P, _P, _P],
+    "imex_set_tableau_named": [_P, C.c_char_p],
+    "imex_set_sdc": [_P, C.c_int, C.c_int, C.c_char_p],
+    "imex_set_viscosity_const": [_P, C.c_double],
+    "imex_set_viscosity_model": [_P, C.c_int, _P, C.c_int],
+    "imex_set_viscosity_field": [_P, _P, C.c_int],
+    "imex_set_boundary": [_P, C.c_int, _P, C.c_int],
+    "imex_set_forcing": [_P, C.c_int, _P, C.c_int],
+    "imex_set_state": [_P, C.c_double, _P, C.c_int],
+    "imex_init_flow": [_P, C.c_int, _P, C.c_int, C.c_double],
+    "imex_step": [_P, C.c_double, C.c_int],
+    "imex_get_velocity": [_P, _P, C.c_int],
+    "imex_get_pressure": [_P, _P, C.c_int],
+    "imex_get_time": [_P, _D],
+    "imex_get_stats": [_P, C.POINTER(imex_stats)],
+    "imex_op_sipg": [_P, C.c_int, _P, _P, C.c_int, C.c_double, C.c_double, _P, _P, C.c_int, C.c_int, C.c_int],
+    "imex_op_sipg_diag": [_P, C.c_int, _P, C.c_double, C.c_double, _P, C.c_int],
+    "imex_op_div": [_P, _P, _P, C.c_int, _P, C.c_int],
+    "imex_op_grad": [_P, _P, _P, C.c_int],
+    "imex_op_conv": [_P, _P, _P, _P, C.c_int],
+    "imex_op_graddiv": [_P, _P, _P, _P, _P, C.c_int],
+    "imex_solve_poisson": [_P, _P, _P, C.c_int],
+    "imex_solve_helmholtz": [_P, _P, _P, C.c_double, _P, _P, C.c_int],
+    "imex_eval_field": [_P, C.c_int, C.c_int, _P, C.c_int, C.c_double, _P, _P, C.c_int],
+    "imex_profile": [_P, C.c_int],
+    "imex_profile_read": [_P, C.c_int, C.POINTER(C.c_longlong), _D],
+    "imex_launch_count": [],
+}
+PROF_PRESSURE_F32, PROF_PRESSURE_F64, PROF_HELMHOLTZ_F32, PROF_HELMHOLTZ_F64, PROF_CONV = range(5)
+
+
+def exported_symbols():
+    return sorted(_SIGS)
+
+
+def launch_count():
+    """Kernels launched by the library so far (all contexts)."""
+    return int(load().imex_launch_count())
+
+
+def load(path=None):
+    """Load the CUDA library; raises if it has not been built (no fallback exists)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise ImportError(f"CUDA library {p} is missing: build it with paper_2112_04167_gb300.build.build()")
+    lib = C.CDLL(p)
+    for name, args in _SIGS.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = {"imex_last_error": C.c_char_p, "imex_destroy": None,
+                     "imex_launch_count": C.c_longlong}.get(name, C.c_int)
+    _lib = lib
+    return lib
+
+
+def _arr(a, n=None, writable=False):
+    """(pointer, on_device, keepalive) for a NumPy array or a CUDA tensor."""
+    if a is None:
+        return None, 0, None
+    if hasattr(a, "data_ptr") and getattr(a, "is_cuda", False):
+        if not a.is_contiguous() or str(a.dtype) != "torch.float64":
+            raise ValueError("device tensors must be contiguous float64")
+        if n is not None and a.numel() < n:
+            raise ValueError(f"tensor has {a.numel()} elements, need {n}")
+        return C.c_void_p(a.data_ptr()), 1, a
+    arr = np.asarray(a)
+    if arr.dtype != np.float64 or not arr.flags.c_contiguous or (writable and not arr.flags.writeable):
+        if writable:
+            raise ValueError("output arrays must be writable C-contiguous float64")
+        arr = np.ascontiguousarray(arr, dtype=np.float64)
+    if n is not None and arr.size < n:
+        raise ValueError(f"array has {arr.size} elements, need {n}")
+    return arr.ctypes.data_as(C.c_void_p), 0, arr
+
+
+def _params(p):
+    if p is None or len(p) == 0:
+        return None, 0, None
+    arr = np.ascontiguousarray(np.asarray(p, dtype=np.float64))
+    return arr.ctypes.data_as(C.c_void_p), len(arr), arr
+
+
+class Context:
+    """One flow instance on the GPU (wraps imex_ctx*)."""
+
+    def __init__(self, dim, P, nelem, lo, hi, periodic, precision=FP64, poisson=POISSON_SIPG, tol=1e-12,
+                 maxit=5000, inner_tol=0.0, vmax=0.0, stream=None):
+        lib = load()
+        d = imex_mesh_desc()
+        d.dim, d.P = dim, P
+        for k in range(3):
+            d.nelem[k] = int(nelem[k]) if k < len(nelem) else 1
+            d.lo[k] = float(lo[k]) if k < len(lo) else 0.0
+            d.hi[k] = float(hi[k]) if k < len(hi) else 1.0
+            d.periodic[k] = int(bool(periodic[k])) if k < len(periodic) else 1
+        d.precision, d.poisson, d.tol, d.maxit, d.inner_tol, d.vmax = precision, poisson, tol, maxit, inner_tol, vmax
+        d.stream = stream
+        h = _P()
+        st = lib.imex_create(C.byref(d), C.byref(h))
+        if st != OK:
+            raise ImexError(st, "imex_create failed")
+        self._h = h
+        self.dim = dim
+        self.P = P
+        nv, npr = C.c_longlong(), C.c_longlong()
+        lib.imex_sizes(h, C.byref(nv), C.byref(npr))
+        self.nvel, self.npres = nv.value, npr.value
+
+    def _check(self, st):
+        if st != OK:
+            raise ImexError(st, load().imex_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().imex_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # --- configuration -------------------------------------------------------
+    def set_tableau_named(self, name):
+        self._check(load().imex_set_tableau_named(self._h, name.encode()))
+
+    def set_tableau(self, c, AI, bI, AE, bE):
+        s = len(c)
+        arrs = [np.ascontiguousarray(np.asarray(x, dtype=np.float64)) for x in (c, AI, bI, AE, bE)]
+        ptrs = [a.ctypes.data_as(C.c_void_p) for a in arrs]
+        self._check(load().imex_set_tableau(self._h, s, *ptrs))
+
+    def set_sdc(self, M, K, predictor="EULER"):
+        self._check(load().imex_set_sdc(self._h, M, K, predictor.encode()))
+
+    def set_viscosity_const(self, nu):
+        self._check(load().imex_set_viscosity_const(self._h, nu))
+
+    def set_viscosity_model(self, kind, params):
+        p, n, _k = _params(params)
+        self._check(load().imex_set_viscosity_model(self._h, kind, p, n))
+
+    def set_viscosity_field(self, nu):
+        p, dev, _k = _arr(nu, self.nvel)
+        self._check(load().imex_set_viscosity_field(self._h, p, dev))
+
+    def set_boundary(self, kind, params=()):
+        p, n, _k = _params(params)
+        self._check(load().imex_set_boundary(self._h, kind, p, n))
+
+    def set_forcing(self, kind, params=()):
+        p, n, _k = _params(params)
+        self._check(load().imex_set_forcing(self._h, kind, p, n))
+
+    def set_state(self, t, v):
+        p, dev, _k = _arr(v, self.dim * self.nvel)
+        self._check(load().imex_set_state(self._h, t, p, dev))
+
+    def init_flow(self, kind, params=(), t=0.0):
+        p, n, _k = _params(params)
+        self._check(load().imex_init_flow(self._h, kind, p, n, t))
+
+    # --- stepping and queries ----------------------------------------------
+    def step(self, dt, nsteps=1):
+        self._check(load().imex_step(self._h, dt, nsteps))
+
+    def get_velocity(self, out=None):
+        if out is None:
+            out = np.empty((self.dim, self.nvel))
+        p, dev, _k = _arr(out, self.dim * self.nvel, writable=True)
+        self._check(load().imex_get_velocity(self._h, p, dev))
+        return out
+
+    def get_pressure(self, out=None):
+        if out is None:
+            out = np.empty(self.npres)
+        p, dev, _k = _arr(out, self.npres, writable=True)
+        self._check(load().imex_get_pressure(self._h, p, dev))
+        return out
+
+    def time(self):
+        t = C.c_double()
+        self._check(load().imex_get_time(self._h, C.byref(t)))
+        return t.value
+
+    def stats(self):
+        s = imex_stats()
+        self._check(load().imex_get_stats(self._h, C.byref(s)))
+        return s.as_dict()
+
+    # --- operators -------------------------------------------------------------
+    def op_sipg(self, x, space=SPACE_VELOCITY, nsys=1, alpha=0.0, beta=1.0, nu=None, g=None, minv=0,
+                precision=FP64):
+        n = (self.nvel if space == SPACE_VELOCITY else self.npres) * nsys
+        out = np.empty(n)
+        px, dev, _a = _arr(x, n)
+        pn, _, _b = _arr(nu, self.nvel)
+        pg, _, _c = _arr(g, n)
+        py, _, _d = _arr(out, n, writable=True)
+        self._check(load().imex_op_sipg(self._h, space, px, py, nsys, alpha, beta, pn, pg, minv, precision, dev))
+        return out
+
+    def op_sipg_diag(self, space=SPACE_VELOCITY, alpha=0.0, beta=1.0, nu=None):
+        n = self.nvel if space == SPACE_VELOCITY else self.npres
+        out = np.empty(n)
+        pn, dev, _b = _arr(nu, self.nvel)
+        py, _, _d = _arr(out, n, writable=True)
+        self._check(load().imex_op_sipg_diag(self._h, space, py, alpha, beta, pn, 0))
+        return out
+
+    def op_div(self, v, w=None, mode=0):
+        out = np.empty(self.npres)
+        pv, _, _a = _arr(v, self.dim * self.nvel)
+        pw, _, _b = _arr(w, self.dim * self.nvel)
+        pb, _, _c = _arr(out, self.npres, writable=True)
+        self._check(load().imex_op_div(self._h, pv, pw, mode, pb, 0))
+        return out
+
+    def op_grad(self, psi):
+        out = np.empty((self.dim, self.nvel))
+        pp, _, _a = _arr(psi, self.npres)
+        po, _, _b = _arr(out, self.dim * self.nvel, writable=True)
+        self._check(load().imex_op_grad(self._h, pp, po, 0))
+        return out
+
+    def op_conv(self, v, vb=None):
+        out = np.empty((self.dim, self.nvel))
+        pv, _, _a = _arr(v, self.dim * self.nvel)
+        pb, _, _b = _arr(vb, self.dim * self.nvel)
+        po, _, _c = _arr(out, self.dim * self.nvel, writable=True)
+        self._check(load().imex_op_conv(self._h, pv, pb, po, 0))
+        return out
+
+    def op_graddiv(self, v, nu=None, with_fd2=False):
+        fd3 = np.empty((self.dim, self.nvel))
+        fd2 = np.empty((self.dim, self.nvel)) if with_fd2 else None
+        pv, _, _a = _arr(v, self.dim * self.nvel)
+        pn, _, _b = _arr(nu, self.nvel)
+        p3, _, _c = _arr(fd3, self.dim * self.nvel, writable=True)
+        p2, _, _d = _arr(fd2, self.dim * self.nvel, writable=True) if with_fd2 else (None, 0, None)
+        self._check(load().imex_op_graddiv(self._h, pv, pn, p3, p2, 0))
+        return (fd3, fd2) if with_fd2 else fd3
+
+    def solve_poisson(self, b):
+        out = np.empty(self.npres)
+        pb, _, _a = _arr(b, self.npres)
+        po, _, _b = _arr(out, self.npres, writable=True)
+        self._check(load().imex_solve_poisson(self._h, pb, po, 0))
+        return out
+
+    def solve_helmholtz(self, g, gamma, nu=None, vb=None):
+        out = np.empty((self.dim, self.nvel))
+        pg, _, _a = _arr(g, self.dim * self.nvel)
+        pn, _, _b = _arr(nu, self.nvel)
+        pv, _, _c = _arr(vb, self.dim * self.nvel)
+        po, _, _d = _arr(out, self.dim * self.nvel, writable=True)
+        self._check(load().imex_solve_helmholtz(self._h, pg, pn, gamma, pv, po, 0))
+        return out
+
+    def profile(self, enable=True):
+        self._check(load().imex_profile(self._h, int(enable)))
+
+    def profile_read(self, cls):
+        n, ms = C.c_longlong(), C.c_double()
+        self._check(load().imex_profile_read(self._h, cls, C.byref(n), C.byref(ms)))
+        return n.value, ms.value
+
+    def eval_field(self, what, kind, params=(), t=0.0, v=None):
+        ncomp = 1 if what == 1 else self.dim
+        out = np.empty((ncomp, self.nvel))
+        pp, n, _k = _params(params)
+        pv, _, _a = _arr(v, self.dim * self.nvel)
+        po, _, _b = _arr(out, ncomp * self.nvel, writable=True)
+        self._check(load().imex_eval_field(self._h, what, kind, pp, n, t, pv, po, 0))
+        return out

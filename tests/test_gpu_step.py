@@ -1,0 +1,167 @@
+"""GPU parity of whole steps of Alg. 3 (IMEX RK) and Alg. 4 (SISDC) against the oracle.
+
+Each step starts both sides from the same state; the FP64 GPU step must match the
+oracle's step to 1e-11 relative L2 (solves converged to 1e-14 on both sides: the
+oracle by sparse LU, the GPU by CG).  The mixed form (FP32 inner solves, FP64
+refinement to 1e-12) must agree to 1e-9."""
+import numpy as np
+import pytest
+
+from oracle import dg, flows, ns
+
+pytestmark = pytest.mark.gpu
+
+imex = pytest.importorskip("paper_2112_04167_gb300.imex")
+TWO_PI = 2 * np.pi
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_2112_04167_gb300 import build
+    build.build()
+    imex.load()
+
+
+def rel(a, b):
+    return np.linalg.norm(np.ravel(a) - np.ravel(b)) / np.linalg.norm(np.ravel(b))
+
+
+def tg2d_pair(P=4, n=4, precision=imex.FP64, poisson=imex.POISSON_SIPG, tol=1e-14):
+    ctx = imex.Context(2, P, (n, n), [0, 0], [TWO_PI, TWO_PI], (1, 1), precision=precision, poisson=poisson,
+                       tol=tol, maxit=50000)
+    ctx.set_viscosity_const(0.01)
+    mesh = dg.Mesh(2, P, (n, n), [0, 0], [TWO_PI, TWO_PI], (True, True))
+    fl = flows.Flow("tg2d", 0.01)
+    disc = ns.Discretization(mesh, fl, poisson="sipg" if poisson == imex.POISSON_SIPG else "consistent")
+    return ctx, disc, fl
+
+
+def mms_pair(P=5, n=3, precision=imex.FP64, tol=1e-14):
+    ctx = imex.Context(2, P, (n, n), [0, 0], [1, 1], (0, 0), precision=precision, tol=tol, maxit=50000)
+    ctx.set_viscosity_model(imex.NU_VARXYT, [0.01])
+    ctx.set_boundary(imex.FLOW_TGTRAVEL, [0.01])
+    ctx.set_forcing(imex.FORCE_TGTRAVEL_VARNU, [0.01])
+    mesh = dg.Mesh(2, P, (n, n), [0, 0], [1, 1], (False, False))
+    fl = flows.Flow("tgtravel", 0.01, nu_kind="varxyt")
+    return ctx, ns.Discretization(mesh, fl), fl
+
+
+def run_steps(ctx, disc, stepper, v0, t0, dt, nsteps, tol):
+    v, t = v0, t0
+    for _ in range(nsteps):
+        ctx.set_state(t, v)
+        ctx.step(dt, 1)
+        got = ctx.get_velocity()
+        v = stepper(v, t, dt)
+        t += dt
+        assert rel(got, v) < tol, rel(got, v)
+    return v
+
+
+@pytest.mark.parametrize("tab", ["CB3e", "ARS3", "CB2", "TR", "CB4", "CB3c"])
+def test_rk_step_tg2d(tab):
+    ctx, disc, fl = tg2d_pair()
+    ctx.set_tableau_named(tab)
+    v0 = fl.initial(disc.X).reshape(2, -1)
+    run_steps(ctx, disc, lambda v, t, dt: ns.rk_step(disc, tab, v, t, dt)[0], v0, 0.0, 0.01, 3, 1e-11)
+
+
+def test_rk_step_tg2d_consistent_projection():
+    ctx, disc, fl = tg2d_pair(poisson=imex.POISSON_CONSISTENT)
+    v0 = fl.initial(disc.X).reshape(2, -1)
+    run_steps(ctx, disc, lambda v, t, dt: ns.rk_step(disc, "CB3e", v, t, dt)[0], v0, 0.0, 0.01, 2, 1e-11)
+
+
+def test_rk_step_tg3d():
+    P, n = 3, (3, 2, 2)
+    ctx = imex.Context(3, P, n, [0, 0, 0], [TWO_PI] * 3, (1, 1, 1), tol=1e-14, maxit=50000)
+    ctx.set_viscosity_const(1.0 / 1600)
+    mesh = dg.Mesh(3, P, n, [0, 0, 0], [TWO_PI] * 3, (True, True, True))
+    fl = flows.Flow("tg3d", 1.0 / 1600)
+    disc = ns.Discretization(mesh, fl)
+    ctx.init_flow(imex.FLOW_TG3D, [0.0])
+    v0 = fl.initial(disc.X).reshape(3, -1)
+    assert rel(ctx.get_velocity(), v0) < 1e-14
+    run_steps(ctx, disc, lambda v, t, dt: ns.rk_step(disc, "CB3e", v, t, dt)[0], v0, 0.0, 0.05, 2, 1e-11)
+
+
+@pytest.mark.parametrize("tab", ["ARS3", "CB3e"])
+def test_rk_step_mms_dirichlet_varnu(tab):
+    ctx, disc, fl = mms_pair()
+    ctx.set_tableau_named(tab)
+    v0 = fl.initial(disc.X).reshape(2, -1)
+    run_steps(ctx, disc, lambda v, t, dt: ns.rk_step(disc, tab, v, t, dt)[0], v0, 0.0, 2e-3, 2, 1e-11)
+
+
+def test_sdc_step_tg2d():
+    ctx, disc, fl = tg2d_pair(P=3, n=3)
+    ctx.set_sdc(3, 2, "CB3e")
+    v0 = fl.initial(disc.X).reshape(2, -1)
+    run_steps(ctx, disc, lambda v, t, dt: ns.sdc_step(disc, 3, 2, "CB3e", v, t, dt), v0, 0.0, 0.05, 1, 1e-11)
+
+
+def test_sdc_euler_step_mms():
+    ctx, disc, fl = mms_pair(P=4, n=2)
+    ctx.set_sdc(2, 2, "EULER")
+    v0 = fl.initial(disc.X).reshape(2, -1)
+    run_steps(ctx, disc, lambda v, t, dt: ns.sdc_step(disc, 2, 2, "EULER", v, t, dt), v0, 0.0, 5e-3, 1, 1e-11)
+
+
+def test_mixed_precision_step():
+    ctx, disc, fl = tg2d_pair(precision=imex.MIXED, tol=1e-12)
+    v0 = fl.initial(disc.X).reshape(2, -1)
+    run_steps(ctx, disc, lambda v, t, dt: ns.rk_step(disc, "CB3e", v, t, dt)[0], v0, 0.0, 0.01, 2, 1e-9)
+    assert ctx.stats()["refinements"] > 0
+
+
+def test_mixed_precision_mms():
+    ctx, disc, fl = mms_pair(precision=imex.MIXED, tol=1e-12)
+    v0 = fl.initial(disc.X).reshape(2, -1)
+    run_steps(ctx, disc, lambda v, t, dt: ns.rk_step(disc, "CB3e", v, t, dt)[0], v0, 0.0, 2e-3, 1, 1e-9)
+
+
+def test_closed_form_accuracy_config1():
+    """2D decaying Taylor-Green on 4x4 quads, P = 4, RK-CB3e, dt = 0.01 to t = 0.2: same
+    error against the closed form as the oracle's run."""
+    ctx, disc, fl = tg2d_pair(tol=1e-12)
+    ctx.init_flow(imex.FLOW_TG2D, [0.01])
+    ctx.step(0.01, 20)
+    ex = fl.exact(disc.X, ctx.time()).reshape(2, -1)
+    err = rel(ctx.get_velocity(), ex)
+    assert 1e-4 < err < 5e-3
+
+
+# ---- failure states (host-side, no GPU fault) ------------------------------------
+def test_nan_state_is_unstable():
+    ctx, disc, fl = tg2d_pair(P=3, n=2)
+    v = fl.initial(disc.X).reshape(2, -1).copy()
+    v[0, 3] = np.nan
+    ctx.set_state(0.0, v)
+    with pytest.raises(imex.ImexError) as e:
+        ctx.step(0.01, 1)
+    assert e.value.status in (imex.EUNSTABLE, imex.ENOTCONV)
+
+
+def test_maxit_is_notconv():
+    ctx = imex.Context(2, 4, (4, 4), [0, 0], [TWO_PI, TWO_PI], (1, 1), tol=1e-14, maxit=2)
+    ctx.set_viscosity_const(0.01)
+    ctx.init_flow(imex.FLOW_TG2D, [0.01])
+    with pytest.raises(imex.ImexError) as e:
+        ctx.step(0.01, 1)
+    assert e.value.status == imex.ENOTCONV
+
+
+def test_invalid_inputs():
+    with pytest.raises(imex.ImexError):
+        imex.Context(4, 4, (2, 2), [0, 0], [1, 1], (1, 1))
+    with pytest.raises(imex.ImexError):
+        imex.Context(2, 12, (2, 2), [0, 0], [1, 1], (1, 1))
+    ctx = imex.Context(2, 3, (2, 2), [0, 0], [1, 1], (1, 1))
+    with pytest.raises(imex.ImexError):                  # a^IM_11 != 0: not CK form
+        ctx.set_tableau([0, 1], [[0.5, 0], [0, 1]], [0, 1], [[0, 0], [1, 0]], [1, 0])
+    with pytest.raises(imex.ImexError):
+        ctx.set_tableau_named("NOPE")
+    d = imex.Context(2, 3, (2, 2), [0, 0], [1, 1], (0, 1))
+    d.init_flow(imex.FLOW_TGTRAVEL, [0.01])
+    with pytest.raises(imex.ImexError):                  # Dirichlet sides need boundary data
+        d.step(0.01, 1)

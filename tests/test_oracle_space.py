@@ -258,3 +258,17 @@ def test_convection_conservative_periodic():
     Fc = dg.Convection(m)(v, None)
     M = dg.mass_diag(m, N)
     assert np.abs((M[None, :] * Fc).sum(axis=1)).max() < 1e-12
+
+
+def test_sipg_single_element_periodic_direction():
+    """One element across a periodic direction is the same operator as two elements on a
+    doubled box with the field repeated (translation invariance)."""
+    N = 4
+    m1 = dg.Mesh(2, 3, (2, 1), [0, 0], [1, 1], (False, True))
+    m2 = dg.Mesh(2, 3, (2, 2), [0, 0], [1, 2], (False, True))
+    rng = np.random.default_rng(0)
+    nu1 = 0.5 + rng.random(m1.ne * N * N)
+    u1 = rng.standard_normal(m1.ne * N * N)
+    y1 = dg.sipg_matrix(m1, N, nu1, True) @ u1
+    y2 = dg.sipg_matrix(m2, N, np.concatenate([nu1, nu1]), True) @ np.concatenate([u1, u1])
+    assert np.abs(y2[:32] - y1).max() < 1e-12 and np.abs(y2[32:] - y1).max() < 1e-12
