@@ -163,6 +163,16 @@ imex_status imex_solve_helmholtz(imex_ctx* ctx, const double* g, const double* n
 imex_status imex_eval_field(imex_ctx* ctx, int what, int kind, const double* params, int nparams,
                             double t, const double* v, double* out, int on_device);
 
+/* ---- reductions (FP64 accumulation, deterministic two-level sums) -------------------- */
+enum { IMEX_REDUCE_DOT = 0, IMEX_REDUCE_SUM = 1, IMEX_REDUCE_MAXABS = 2 };
+/* *out (host) = sum_i x_i y_i (DOT), sum_i x_i (SUM) or max_i |x_i| (MAXABS; NaN if any x_i
+   is NaN) over n doubles; y is used by DOT only.  With on_device = 0 the inputs are host
+   arrays staged through the context, which needs n <= d * nvel (else IMEX_EINVAL).  These are
+   the reductions behind the solver tolerances, the pressure mean and the instability check
+   (Sec. 4: RMS residuals; Sec. 4.2.3: |v| threshold / NaN). */
+imex_status imex_reduce(imex_ctx* ctx, int op, const double* x, const double* y, long long n,
+                        double* out, int on_device);
+
 /* ---- instrumentation ---------------------------------------------------------------- */
 
 /* kernel classes timed by imex_profile: the operator applies inside the CG solves

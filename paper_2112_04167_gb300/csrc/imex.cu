@@ -1412,6 +1412,37 @@ imex_status imex_eval_field(imex_ctx* c, int what, int kind, const double* p, in
   return copy_out(c, out, c->cAp, (what == 1 ? 1 : c->d) * c->nv, on_device);
 }
 
+imex_status imex_reduce(imex_ctx* c, int op, const double* x, const double* y, long long n, double* out,
+                        int on_device) {
+  if (!c || !x || !out || n < 0 || op < IMEX_REDUCE_DOT || op > IMEX_REDUCE_MAXABS || (op == IMEX_REDUCE_DOT && !y))
+    return fail(c, IMEX_EINVAL, "bad reduction arguments");
+  const size_t cap = std::max(c->nv * c->d, c->np);
+  if (!on_device && (size_t)n > cap) return fail(c, IMEX_EINVAL, "host reduction larger than the context buffers");
+  const double* dx = x;
+  const double* dy = y;
+  if (!on_device) {
+    TRY(copy_in(c, c->cx, x, (size_t)n, 0));
+    dx = c->cx;
+    if (op == IMEX_REDUCE_DOT) { TRY(copy_in(c, c->cz, y, (size_t)n, 0)); dy = c->cz; }
+  }
+  double* res = c->dscal + 64;
+  if (n == 0) {
+    *out = 0.0;
+    return IMEX_OK;
+  }
+  if (op == IMEX_REDUCE_DOT)
+    dot_batched(dx, dy, (size_t)n, (long long)n, 1, c->partial, c->nblocks, res, c->st);
+  else if (op == IMEX_REDUCE_SUM)
+    reduce_sum(dx, (size_t)n, c->partial, c->nblocks, res, c->st);
+  else
+    reduce_max_abs(dx, (size_t)n, c->partial, c->nblocks, res, c->st);
+  CK(cudaGetLastError(), "reduction");
+  CK(cudaMemcpyAsync(c->hscal + 64, res, sizeof(double), cudaMemcpyDeviceToHost, c->st), "copy result");
+  CK(cudaStreamSynchronize(c->st), "sync");
+  *out = c->hscal[64];
+  return IMEX_OK;
+}
+
 imex_status imex_profile(imex_ctx* c, int enable) {
   if (!c) return IMEX_EINVAL;
   for (int k = 0; k < IMEX_PROF_NCLASS; ++k) {

@@ -79,11 +79,13 @@ _SIGS = {
     "imex_solve_poisson": [_P, _P, _P, C.c_int],
     "imex_solve_helmholtz": [_P, _P, _P, C.c_double, _P, _P, C.c_int],
     "imex_eval_field": [_P, C.c_int, C.c_int, _P, C.c_int, C.c_double, _P, _P, C.c_int],
+    "imex_reduce": [_P, C.c_int, _P, _P, C.c_longlong, _D, C.c_int],
     "imex_profile": [_P, C.c_int],
     "imex_profile_read": [_P, C.c_int, C.POINTER(C.c_longlong), _D],
     "imex_launch_count": [],
 }
 PROF_PRESSURE_F32, PROF_PRESSURE_F64, PROF_HELMHOLTZ_F32, PROF_HELMHOLTZ_F64, PROF_CONV = range(5)
+REDUCE_DOT, REDUCE_SUM, REDUCE_MAXABS = range(3)
 
 
 def exported_symbols():
@@ -317,6 +319,15 @@ class Context:
         po, _, _d = _arr(out, self.dim * self.nvel, writable=True)
         self._check(load().imex_solve_helmholtz(self._h, pg, pn, gamma, pv, po, 0))
         return out
+
+    def reduce(self, op, x, y=None):
+        """Device reduction of x (and y) -- DOT, SUM or MAXABS -- with FP64 accumulation."""
+        n = int(x.numel()) if hasattr(x, "numel") else int(np.asarray(x).size)
+        px, dev, _a = _arr(x, n)
+        py, _, _b = _arr(y, n) if y is not None else (None, 0, None)
+        out = C.c_double()
+        self._check(load().imex_reduce(self._h, op, px, py, n, C.byref(out), dev))
+        return out.value
 
     def profile(self, enable=True):
         self._check(load().imex_profile(self._h, int(enable)))

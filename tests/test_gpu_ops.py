@@ -213,3 +213,17 @@ def test_fields(case):
     got = ctx.eval_field(1, imex.NU_VELOCITY, [0.01, 0.02, 2.0], v=v)
     ref = 0.01 + 0.02 * np.sum(v.reshape(d, -1) ** 2, axis=0) / 4.0
     assert np.abs(got.ravel() - ref).max() < 1e-15
+
+
+def test_reductions():
+    ctx, mesh = make(CASES[3])
+    n = ctx.dim * ctx.nvel
+    x = inputs.field(n, seed=21)
+    y = inputs.field(n, seed=22)
+    assert ctx.reduce(imex.REDUCE_DOT, x, y) == pytest.approx(float(np.dot(x, y)), rel=1e-13)
+    assert ctx.reduce(imex.REDUCE_SUM, x) == pytest.approx(float(np.sum(x)), rel=1e-12, abs=1e-12)
+    assert ctx.reduce(imex.REDUCE_MAXABS, x) == float(np.abs(x).max())
+    x[17] = np.nan
+    assert np.isnan(ctx.reduce(imex.REDUCE_MAXABS, x))
+    with pytest.raises(imex.ImexError):
+        ctx.reduce(imex.REDUCE_SUM, np.zeros(n + 1))
