@@ -173,6 +173,24 @@ enum { IMEX_REDUCE_DOT = 0, IMEX_REDUCE_SUM = 1, IMEX_REDUCE_MAXABS = 2 };
 imex_status imex_reduce(imex_ctx* ctx, int op, const double* x, const double* y, long long n,
                         double* out, int on_device);
 
+/* Allocation-free form of imex_reduce, for callers that cannot allocate device memory
+   at call time: code running while another framework's memory pool owns the device,
+   hot loops where a cudaMalloc would synchronise the device, embedded or real-time
+   hosts that forbid allocation after start-up.  There is no counterpart in the paper.
+   x, y: device pointers (n doubles, FP64), out: host pointer to one double, stream: a
+   cudaStream_t or NULL.  It needs no context and calls no cudaMalloc / cudaFree: its
+   partial sums live in one fixed device array of 65,536 + 32 doubles (about 512 KB) that
+   every GPU which loads this library holds until the process exits.
+   Limit: n <= 16,777,216 (= 256 x 65,536); larger n returns IMEX_EINVAL without touching
+   the GPU.  The first call on each device looks up the array's device address
+   (cudaGetSymbolAddress); make that first call before any stream capture.  Every call
+   rewrites the partial sums it reads before reading them, so nothing has to be cleared,
+   and the array keeps the last call's contents.  All calls share the one array: calls
+   that overlap on the GPU (different streams or threads) race on it and must be
+   serialised by the caller.  The result is returned after a stream synchronisation. */
+imex_status imex_reduce_noalloc(int op, const double* x, const double* y, long long n, double* out,
+                                void* stream);
+
 /* ---- instrumentation ---------------------------------------------------------------- */
 
 /* kernel classes timed by imex_profile: the operator applies inside the CG solves

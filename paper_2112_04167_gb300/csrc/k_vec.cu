@@ -1,11 +1,13 @@
 // Vector kernels: stage linear combinations (FP64), deterministic two-level
 // reductions (FP64 accumulation), precision conversion, and the fused
 // Jacobi-PCG updates whose scalars stay in device memory.
+#include <atomic>
+#include <mutex>
+
+#include "../../include/imex.h"
 #include "common.cuh"
 #include "kernels.h"
 #include "vec.h"
-
-#include <atomic>
 
 namespace imex {
 
@@ -359,3 +361,114 @@ template void reciprocal<double>(double*, size_t, cudaStream_t);
 template void reciprocal<float>(float*, size_t, cudaStream_t);
 
 }  // namespace imex
+
+// =====================================================================================
+// Allocation-free reduction: imex_reduce_noalloc (include/imex.h).
+//
+// For callers that must not allocate device memory at call time -- code that runs
+// while a memory pool owned by another framework holds the device, inside a loop
+// where a cudaMalloc would synchronise the device, or in embedded / real-time hosts
+// that forbid allocation after start-up.  Same reduction as imex_reduce, with the
+// per-block partial sums kept in a fixed file-scope device array instead of a
+// context buffer.  Every GPU that loads this library holds that array until exit.
+// =====================================================================================
+namespace {
+
+constexpr int kNoallocChunk = 256;                     // elements per partial sum
+constexpr int kNoallocSlots = 65536;                   // partial sums held
+constexpr long long kNoallocMaxN = (long long)kNoallocChunk * kNoallocSlots;   // 16,777,216
+constexpr int kNoallocMaxDevices = 64;
+
+// partial sums [0, kNoallocSlots) and the final value at [kNoallocSlots]
+static __device__ __align__(256) double g_noalloc_scratch[kNoallocSlots + 32];
+
+std::mutex g_noalloc_mu;
+double* g_noalloc_ptr[kNoallocMaxDevices] = {nullptr};
+
+// block b reduces exactly the elements [256 b, 256 b + 256) into partial[b]
+__global__ void noalloc_chunk_kernel(int op, const double* __restrict__ x, const double* __restrict__ y,
+                                     long long n, double* __restrict__ partial) {
+  const long long i = (long long)blockIdx.x * kNoallocChunk + threadIdx.x;
+  double v = 0.0;
+  bool nan_here = false;
+  if (i < n) {
+    if (op == IMEX_REDUCE_DOT) v = x[i] * y[i];
+    else if (op == IMEX_REDUCE_SUM) v = x[i];
+    else { v = fabs(x[i]); nan_here = (v != v); }
+  }
+  if (op == IMEX_REDUCE_MAXABS) {
+    __shared__ int has_nan;
+    if (threadIdx.x == 0) has_nan = 0;
+    __syncthreads();
+    if (nan_here) has_nan = 1;
+    const double m = imex::block_max(nan_here ? 0.0 : v);
+    __syncthreads();
+    if (threadIdx.x == 0) partial[blockIdx.x] = has_nan ? nan("") : m;
+  } else {
+    const double s = imex::block_sum(v);
+    if (threadIdx.x == 0) partial[blockIdx.x] = s;
+  }
+}
+
+// one block: fixed-order combination of nb partial sums into out[0]
+__global__ void noalloc_finish_kernel(int op, const double* __restrict__ partial, int nb, double* __restrict__ out) {
+  if (op == IMEX_REDUCE_MAXABS) {
+    __shared__ int has_nan;
+    if (threadIdx.x == 0) has_nan = 0;
+    __syncthreads();
+    double m = 0.0;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+      const double v = partial[i];
+      if (v != v) has_nan = 1; else m = fmax(m, v);
+    }
+    m = imex::block_max(m);
+    __syncthreads();
+    if (threadIdx.x == 0) out[0] = has_nan ? nan("") : m;
+  } else {
+    double s = 0.0;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) s += partial[i];
+    s = imex::block_sum(s);
+    if (threadIdx.x == 0) out[0] = s;
+  }
+}
+
+// device address of the scratch array on the current device (looked up once per device)
+imex_status noalloc_scratch(double** out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return IMEX_ECUDA;
+  if (dev < 0 || dev >= kNoallocMaxDevices) return IMEX_EINVAL;
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess) return IMEX_ECUDA;
+    g_noalloc_ptr[dev] = static_cast<double*>(p);
+  }
+  *out = g_noalloc_ptr[dev];
+  return IMEX_OK;
+}
+
+}  // namespace
+
+extern "C" imex_status imex_reduce_noalloc(int op, const double* x, const double* y, long long n, double* out,
+                                           void* stream) {
+  if (!x || !out || n < 0 || op < IMEX_REDUCE_DOT || op > IMEX_REDUCE_MAXABS || (op == IMEX_REDUCE_DOT && !y))
+    return IMEX_EINVAL;
+  if (n > kNoallocMaxN) return IMEX_EINVAL;       // more partial sums than the fixed array holds
+  if (n == 0) {
+    *out = 0.0;
+    return IMEX_OK;
+  }
+  double* scratch = nullptr;
+  const imex_status s = noalloc_scratch(&scratch);
+  if (s != IMEX_OK) return s;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int nb = (int)((n + kNoallocChunk - 1) / kNoallocChunk);
+  IMEX_COUNTED(noalloc_chunk_kernel<<<nb, kNoallocChunk, 0, st>>>(op, x, y, n, scratch));
+  IMEX_COUNTED(noalloc_finish_kernel<<<1, 256, 0, st>>>(op, scratch, nb, scratch + kNoallocSlots));
+  if (cudaGetLastError() != cudaSuccess) return IMEX_ECUDA;
+  if (cudaMemcpyAsync(out, scratch + kNoallocSlots, sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    return IMEX_ECUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return IMEX_ECUDA;
+  return IMEX_OK;
+}
+

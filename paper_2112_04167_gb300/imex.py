@@ -80,6 +80,7 @@ _SIGS = {
     "imex_solve_helmholtz": [_P, _P, _P, C.c_double, _P, _P, C.c_int],
     "imex_eval_field": [_P, C.c_int, C.c_int, _P, C.c_int, C.c_double, _P, _P, C.c_int],
     "imex_reduce": [_P, C.c_int, _P, _P, C.c_longlong, _D, C.c_int],
+    "imex_reduce_noalloc": [C.c_int, _P, _P, C.c_longlong, _D, _P],
     "imex_profile": [_P, C.c_int],
     "imex_profile_read": [_P, C.c_int, C.POINTER(C.c_longlong), _D],
     "imex_launch_count": [],
@@ -95,6 +96,24 @@ def exported_symbols():
 def launch_count():
     """Kernels launched by the library so far (all contexts)."""
     return int(load().imex_launch_count())
+
+
+NOALLOC_MAX_N = 256 * 65536
+
+
+def reduce_noalloc(op, x, y=None, stream=None):
+    """imex_reduce_noalloc: the same reduction as Context.reduce without a context or any
+    device allocation.  x, y: contiguous float64 CUDA tensors; stream: CUDA stream handle."""
+    n = int(x.numel())
+    px, dev, _a = _arr(x, n)
+    if not dev:
+        raise ValueError("reduce_noalloc takes device tensors")
+    py, _, _b = _arr(y, n) if y is not None else (None, 0, None)
+    out = C.c_double()
+    st = load().imex_reduce_noalloc(op, px, py, n, C.byref(out), stream)
+    if st != OK:
+        raise ImexError(st, "imex_reduce_noalloc failed")
+    return out.value
 
 
 def load(path=None):
