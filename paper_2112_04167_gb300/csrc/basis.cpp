@@ -143,4 +143,67 @@ void build_tables(Tables<double>* t, Tables<float>* f) {
   std::memcpy(f->Q, t->Q, sizeof(t->Q));
 }
 
+// 1D SIPG line operators (unit viscosity) for each direction of a Cartesian mesh:
+// volume (2/h) sum_q w_q D_qi D_qj, plus the own-element face terms of the interior-penalty
+// form at the left (outward normal -1) and right (+1) ends, factor 1/2 on interior faces,
+// 1 with penalty 2 tau on Dirichlet faces, nothing on Neumann faces, tau = N^2 / h.
+void build_line_ops(const Tables<double>& t, int N, const double* h, int d, LineOps<double>* o,
+                    LineOps<float>* f) {
+  std::memset(o, 0, sizeof(*o));
+  const double* D = t.D[N];
+  const double* w = t.w[N];
+  for (int k = 0; k < d; ++k) {
+    const double s = 2.0 / h[k];
+    const double tau = N * N / h[k];
+    for (int i = 0; i < N; ++i) o->Wt[k][i] = 0.5 * h[k] * w[i];
+    for (int j = 0; j < N; ++j) {
+      o->dn[k][0][j] = s * D[(N - 1) * N + j];   // left neighbour: derivative at its right end
+      o->dn[k][1][j] = s * D[0 * N + j];         // right neighbour: derivative at its left end
+    }
+    for (int kl = 0; kl < 3; ++kl)
+      for (int kr = 0; kr < 3; ++kr) {
+        double* A = o->A[k][3 * kl + kr];
+        for (int i = 0; i < N; ++i)
+          for (int j = 0; j < N; ++j) {
+            double v = 0.0;
+            for (int q = 0; q < N; ++q) v += w[q] * D[q * N + i] * D[q * N + j];
+            A[i * N + j] = s * v;
+          }
+        const double fl = (kl == 1) ? 0.5 : (kl == 2 ? 1.0 : 0.0);
+        const double fr = (kr == 1) ? 0.5 : (kr == 2 ? 1.0 : 0.0);
+        const double tl = (kl == 1) ? tau : (kl == 2 ? 2.0 * tau : 0.0);
+        const double tr = (kr == 1) ? tau : (kr == 2 ? 2.0 * tau : 0.0);
+        for (int i = 0; i < N; ++i)
+          for (int j = 0; j < N; ++j) {
+            double v = 0.0;
+            // left end, n = -1
+            if (i == 0) v += fl * s * D[0 * N + j];
+            if (j == 0) v += fl * s * D[0 * N + i];
+            if (i == 0 && j == 0) v += tl;
+            // right end, n = +1
+            if (i == N - 1) v -= fr * s * D[(N - 1) * N + j];
+            if (j == N - 1) v -= fr * s * D[(N - 1) * N + i];
+            if (i == N - 1 && j == N - 1) v += tr;
+            A[i * N + j] += v;
+          }
+      }
+    for (int kind = 0; kind < 3; ++kind) {
+      const double fac = (kind == 1) ? 0.5 : (kind == 2 ? 1.0 : 0.0);
+      const double pen = (kind == 1) ? tau : (kind == 2 ? 2.0 * tau : 0.0);
+      for (int i = 0; i < N; ++i) {
+        // left face: trace (or datum) and normal derivative of the neighbour
+        o->C[k][0][kind][0][i] = -fac * s * D[0 * N + i] - (i == 0 ? pen : 0.0);
+        o->C[k][0][kind][1][i] = (kind == 1 && i == 0) ? 0.5 : 0.0;
+        // right face
+        o->C[k][1][kind][0][i] = fac * s * D[(N - 1) * N + i] - (i == N - 1 ? pen : 0.0);
+        o->C[k][1][kind][1][i] = (kind == 1 && i == N - 1) ? -0.5 : 0.0;
+      }
+    }
+  }
+  const double* src = reinterpret_cast<const double*>(o);
+  float* dst = reinterpret_cast<float*>(f);
+  const size_t n = sizeof(LineOps<double>) / sizeof(double);
+  for (size_t i = 0; i < n; ++i) dst[i] = static_cast<float>(src[i]);
+}
+
 }  // namespace imex

@@ -23,9 +23,14 @@ struct Geom {
   int bc[3];             // 0 periodic, 1 Dirichlet, 2 homogeneous Neumann (per direction)
   double lo[3];
   double h[3];           // element sizes
+  float hf[3];           // the same in FP32 (FP32 kernels take no FP64 conversion per thread)
   const void* tab64;     // device Tables<double>
   const void* tab32;     // device Tables<float>
 };
+
+template <typename T> __host__ __device__ __forceinline__ T geom_h(const Geom& g, int k);
+template <> __host__ __device__ __forceinline__ double geom_h<double>(const Geom& g, int k) { return g.h[k]; }
+template <> __host__ __device__ __forceinline__ float geom_h<float>(const Geom& g, int k) { return g.hf[k]; }
 
 // 1D tables per number of points N (index N, 2..IMEX_MAXN), in FP64 and FP32.
 //   x, w      : GLL points / weights
@@ -45,6 +50,25 @@ struct Tables {
   T DG[IMEX_MAXN + 1][IMEX_MAXQ * IMEX_MAXN];
   T gw[IMEX_MAXN + 1][IMEX_MAXQ];
   int Q[IMEX_MAXN + 1];
+};
+
+// One-dimensional SIPG line operators of a Cartesian mesh with constant viscosity (unit nu).
+// On affine Cartesian elements with GLL collocation the SIPG operator is a sum over the
+// directions k of (tangential mass) x (1D SIPG operator along k), so per direction the
+// element's own block and its rank-2 coupling to each neighbour along k are fixed matrices:
+//   A[k][3*kl + kr][i*N + j] : own block for left / right face kinds kl, kr
+//   C[k][side][kind][0][i]   : coefficient of the neighbour's trace (or Dirichlet datum)
+//   C[k][side][kind][1][i]   : coefficient of the neighbour's normal derivative
+//   dn[k][side][j]           : row forming that derivative from the neighbour's line
+//   Wt[k][i]                 : (h_k / 2) w_i, the factor that direction k contributes to
+//                              tangential and volume weights
+// face kinds: 0 no terms (Neumann), 1 interior, 2 Dirichlet
+template <typename T>
+struct LineOps {
+  T A[3][9][IMEX_MAXN * IMEX_MAXN];
+  T C[3][2][3][2][IMEX_MAXN];
+  T dn[3][2][IMEX_MAXN];
+  T Wt[3][IMEX_MAXN];
 };
 
 template <typename T> __device__ __forceinline__ const Tables<T>& tab(const Geom& g);
@@ -79,6 +103,8 @@ __device__ __forceinline__ void elem_coords(const Geom& g, int e, int ec[3]) {
 
 // host-side table construction (basis.cpp)
 void build_tables(Tables<double>* t64, Tables<float>* t32);
+void build_line_ops(const Tables<double>& t, int N, const double* h, int d, LineOps<double>* o64,
+                    LineOps<float>* o32);
 
 // number of kernels this library has launched (all contexts, all threads)
 void count_launch();

@@ -7,8 +7,10 @@
 
 #include <algorithm>
 #include <chrono>
+#include <climits>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -166,6 +168,11 @@ struct imex_ctx {
   // device memory
   Tables<double>* dtab64 = nullptr;
   Tables<float>* dtab32 = nullptr;
+  // constant-viscosity line operators of the velocity (v) and pressure (p) spaces
+  LineOps<double>* ops64_v = nullptr;
+  LineOps<float>* ops32_v = nullptr;
+  LineOps<double>* ops64_p = nullptr;
+  LineOps<float>* ops32_p = nullptr;
   std::vector<void*> allocs;
   double *v = nullptr, *vp = nullptr, *vpp = nullptr, *g = nullptr, *tmp = nullptr, *vb = nullptr;
   double *nu = nullptr, *nu_fixed = nullptr, *phi = nullptr, *jac = nullptr, *fsbuf = nullptr;
@@ -175,14 +182,30 @@ struct imex_ctx {
   std::vector<double*> sv, snu, sFEX, sFIM, sFq;
   // CG (FP64 and FP32)
   double *cx = nullptr, *cr = nullptr, *cz = nullptr, *cp = nullptr, *cAp = nullptr, *cdiag = nullptr;
-  float *fx = nullptr, *fr = nullptr, *fz = nullptr, *fp = nullptr, *fAp = nullptr, *fdiag = nullptr;
+  float *fx = nullptr, *fr = nullptr, *fp = nullptr, *fAp = nullptr, *fdiag = nullptr;
   float *fnu = nullptr, *fvtmp = nullptr;
   double* partial = nullptr;
+  double* apartial = nullptr;   // per-block partials of the fused apply + dot
+  unsigned int* counters = nullptr;
   int nblocks = 0;
   double* dscal = nullptr;      // 16 x 4 doubles of scalars
   int* iscal = nullptr;
   double* hscal = nullptr;      // pinned host mirror
   int* hiscal = nullptr;
+  // segmented CG: the systems of the pressure space and of the velocity space (one per
+  // component), their per-system scalars (device, and a pinned host mirror) and partials
+  struct Seg {
+    SegTable t{};
+    size_t total = 0;
+  };
+  Seg segp, segv;
+  int maxsys = 0;
+  double* cg_d = nullptr;       // 12 x maxsys
+  float* cg_f = nullptr;        // 4 x maxsys
+  int* cg_i = nullptr;          // 2 x maxsys
+  double* cg_hd = nullptr;
+  int* cg_hi = nullptr;
+  double* seg_partial = nullptr;
   bool diag_valid_p = false;
   imex_stats stats{};
   double last_res = 0.0;
@@ -255,6 +278,61 @@ imex_status dalloc(imex_ctx* c, T** p, size_t n) {
   } while (0)
 #define CK(x, what) TRY(cuda_check(c, (x), what))
 
+// Segment table of nseg systems: system s occupies [off[s], off[s] + len[s]) of the CG
+// vectors and starts at doff[s] in the Jacobi diagonal; blocks of SEG_CHUNK elements.
+imex_status make_seg(imex_ctx* c, int nseg, const long long* off, const long long* doff, const long long* len,
+                     imex_ctx::Seg* out) {
+  std::vector<int> blen(nseg), blk_seg, blk_lo, blk0(nseg + 1);
+  std::vector<SegBlock> blk;
+  size_t total = 0;
+  for (int s = 0; s < nseg; ++s) {
+    if (len[s] <= 0 || len[s] > (long long)INT_MAX - SEG_CHUNK) return fail(c, IMEX_EINVAL, "segment size");
+    blen[s] = (int)len[s];
+    blk0[s] = (int)blk_seg.size();
+    for (long long lo = 0; lo < len[s]; lo += SEG_CHUNK) {
+      blk_seg.push_back(s);
+      blk_lo.push_back((int)lo);
+      SegBlock b{};
+      b.off = off[s] + lo;
+      b.doff = doff[s] + lo;
+      b.n = (int)std::min<long long>(SEG_CHUNK, len[s] - lo);
+      b.s = s;
+      blk.push_back(b);
+    }
+    total = std::max(total, (size_t)(off[s] + len[s]));
+  }
+  blk0[nseg] = (int)blk_seg.size();
+  long long *doff_d = nullptr, *off_d = nullptr;
+  int *len_d = nullptr, *bs_d = nullptr, *bl_d = nullptr, *b0_d = nullptr;
+  TRY(dalloc(c, &off_d, nseg));
+  TRY(dalloc(c, &doff_d, nseg));
+  TRY(dalloc(c, &len_d, nseg));
+  TRY(dalloc(c, &bs_d, blk_seg.size()));
+  TRY(dalloc(c, &bl_d, blk_lo.size()));
+  TRY(dalloc(c, &b0_d, nseg + 1));
+  SegBlock* blk_d = nullptr;
+  TRY(dalloc(c, &blk_d, blk.size()));
+  CK(cudaMemcpy(blk_d, blk.data(), blk.size() * sizeof(SegBlock), cudaMemcpyHostToDevice), "cp seg");
+  CK(cudaMemcpy(off_d, off, nseg * sizeof(long long), cudaMemcpyHostToDevice), "cp seg");
+  CK(cudaMemcpy(doff_d, doff, nseg * sizeof(long long), cudaMemcpyHostToDevice), "cp seg");
+  CK(cudaMemcpy(len_d, blen.data(), nseg * sizeof(int), cudaMemcpyHostToDevice), "cp seg");
+  CK(cudaMemcpy(bs_d, blk_seg.data(), blk_seg.size() * sizeof(int), cudaMemcpyHostToDevice), "cp seg");
+  CK(cudaMemcpy(bl_d, blk_lo.data(), blk_lo.size() * sizeof(int), cudaMemcpyHostToDevice), "cp seg");
+  CK(cudaMemcpy(b0_d, blk0.data(), (nseg + 1) * sizeof(int), cudaMemcpyHostToDevice), "cp seg");
+  out->t.nseg = nseg;
+  out->t.nblk = (int)blk_seg.size();
+  out->t.off = off_d;
+  out->t.doff = doff_d;
+  out->t.len = len_d;
+  out->t.blk_seg = bs_d;
+  out->t.blk_lo = bl_d;
+  out->t.seg_blk0 = b0_d;
+  out->t.blk = blk_d;
+  out->total = total;
+  return IMEX_OK;
+}
+
+
 imex_status launch_check(imex_ctx* c, int rc, const char* what) {
   if (rc != 0) return fail(c, IMEX_EINVAL, std::string(what) + ": unsupported (dim, P)");
   return cuda_check(c, cudaGetLastError(), what);
@@ -267,19 +345,50 @@ SipgArgs<T> sipg_args(const T* x, T* y, int nsys, long long stride, const T* nu,
   SipgArgs<T> a;
   a.x = x; a.y = y; a.nsys = nsys; a.sys_stride = stride; a.nu = nu; a.nu0 = (T)nu0;
   a.gdata = gd; a.g_stride = stride; a.alpha = (T)alpha; a.beta = (T)beta; a.minv = minv;
+  a.ops = nullptr;
+  a.dot_partial = nullptr;
+  a.dot_counter = nullptr;
+  a.dot_out = nullptr;
+  a.cg_rz = nullptr;
+  a.cg_alpha = nullptr;
+  a.cg_alpha_f = nullptr;
+  a.cg_done = nullptr;
   return a;
+}
+
+template <typename T> const LineOps<T>* line_ops(const imex_ctx* c, bool velocity);
+template <> const LineOps<double>* line_ops<double>(const imex_ctx* c, bool velocity) {
+  return velocity ? c->ops64_v : c->ops64_p;
+}
+template <> const LineOps<float>* line_ops<float>(const imex_ctx* c, bool velocity) {
+  return velocity ? c->ops32_v : c->ops32_p;
 }
 
 double nu_const(const imex_ctx* c) { return c->nu_p[0]; }
 
 bool variable_nu(const imex_ctx* c) { return c->nu_kind != IMEX_NU_CONST; }
 
+// fused CG dot of an operator apply: (p, A p) into cg->pAp and the step length alpha
+template <typename T>
+void fuse_cg(imex_ctx* c, SipgArgs<T>& a, const CgScalars* cg) {
+  if (!cg) return;
+  a.dot_out = cg->pAp;
+  a.dot_partial = c->apartial;
+  a.dot_counter = c->counters;
+  a.cg_rz = cg->rz;
+  a.cg_alpha = cg->alpha;
+  a.cg_alpha_f = cg->alpha_f;
+  a.cg_done = cg->done;
+}
+
 // the pressure operator L psi (pressure space), T = double / float
 template <typename T>
-imex_status apply_pressure(imex_ctx* c, const T* x, T* y, T* vtmp) {
+imex_status apply_pressure(imex_ctx* c, const T* x, T* y, T* vtmp, const CgScalars* cg = nullptr) {
   const int cls = sizeof(T) == 4 ? IMEX_PROF_PRESSURE_F32 : IMEX_PROF_PRESSURE_F64;
   if (c->desc.poisson == IMEX_POISSON_SIPG) {
     SipgArgs<T> a = sipg_args<T>(x, y, 1, (long long)c->np, nullptr, 1.0, nullptr, 0.0, 1.0, 0);
+    a.ops = line_ops<T>(c, false);
+    fuse_cg(c, a, cg);
     prof_mark(c, cls, true);
     const int rc = sipg_apply<T>(c->gp, c->Np, a, c->st);
     prof_mark(c, cls, false);
@@ -294,9 +403,12 @@ imex_status apply_pressure(imex_ctx* c, const T* x, T* y, T* vtmp) {
 
 // velocity Helmholtz operator (M + gamma A(nu)), nsys components
 template <typename T>
-imex_status apply_helm(imex_ctx* c, const T* x, T* y, int nsys, const T* nu, double gamma) {
+imex_status apply_helm(imex_ctx* c, const T* x, T* y, int nsys, const T* nu, double gamma,
+                       const CgScalars* cg = nullptr) {
   const int cls = sizeof(T) == 4 ? IMEX_PROF_HELMHOLTZ_F32 : IMEX_PROF_HELMHOLTZ_F64;
   SipgArgs<T> a = sipg_args<T>(x, y, nsys, (long long)c->nv, nu, nu_const(c), nullptr, 1.0, gamma, 0);
+  a.ops = line_ops<T>(c, true);
+  fuse_cg(c, a, cg);
   prof_mark(c, cls, true);
   const int rc = sipg_apply<T>(c->gv, c->Nv, a, c->st);
   prof_mark(c, cls, false);
@@ -304,92 +416,233 @@ imex_status apply_helm(imex_ctx* c, const T* x, T* y, int nsys, const T* nu, dou
 }
 
 // ---- PCG -------------------------------------------------------------------------
-// scalar slots: dscal[0..7] CG scalars x nsys (<= 3 systems): layout per field of 4 entries
-CgScalars scalars(imex_ctx* c, double tol) {
+// per-system CG scalars: cg_d holds rz, rz_old, rr, bb, pAp, zmean, a mean scratch, the true
+// residual norm (mixed form), rmean, dsum, alpha and beta, maxsys entries each; cg_f the FP32
+// alpha, beta, zmean, rmean; cg_i holds done and iters
+CgScalars scalars(imex_ctx* c, double tol, bool project) {
+  const int m = c->maxsys;
   CgScalars s;
-  s.rz = c->dscal + 0;
-  s.rz_old = c->dscal + 4;
-  s.rr = c->dscal + 8;
-  s.bb = c->dscal + 12;
-  s.pAp = c->dscal + 16;
-  s.done = c->iscal + 0;
-  s.iters = c->iscal + 4;
+  s.rz = c->cg_d + 0 * m;
+  s.rz_old = c->cg_d + 1 * m;
+  s.rr = c->cg_d + 2 * m;
+  s.bb = c->cg_d + 3 * m;
+  s.pAp = c->cg_d + 4 * m;
+  s.zmean = c->cg_d + 5 * m;
+  s.rmean = c->cg_d + 8 * m;
+  s.dsum = c->cg_d + 9 * m;
+  s.alpha = c->cg_d + 10 * m;
+  s.beta = c->cg_d + 11 * m;
+  s.alpha_f = c->cg_f + 0 * m;
+  s.beta_f = c->cg_f + 1 * m;
+  s.zmean_f = c->cg_f + 2 * m;
+  s.rmean_f = c->cg_f + 3 * m;
+  s.done = c->cg_i + 0 * m;
+  s.iters = c->cg_i + 1 * m;
   s.tol2 = tol * tol;
+  s.project = project ? 1 : 0;
   return s;
 }
 
-// Jacobi PCG on op(x) = b for nsys systems of length n; x holds the initial guess.
-// `op(x, y)` applies the operator; dinv is the inverse diagonal (length n, shared).
-// Returns IMEX_OK or IMEX_ENOTCONV; iterations and relative residuals via out params.
-template <typename T, typename Op>
-imex_status pcg(imex_ctx* c, Op op, const T* b, T* x, T* r, T* z, T* p, T* Ap, const T* dinv, size_t n,
-                int nsys, double tol, int maxit, bool mean_free, long long* iters_out, double* res_out) {
-  CgScalars sc = scalars(c, tol);
-  const long long stride = (long long)n;
-  // r = b - A x
+// copy the per-system flags (done, iters) and the recursive rr, bb to the host mirrors
+imex_status pull_scalars(imex_ctx* c, int nsys) {
+  const int m = c->maxsys;
+  CK(cudaMemcpyAsync(c->cg_hi, c->cg_i, 2 * m * sizeof(int), cudaMemcpyDeviceToHost, c->st), "cp flags");
+  CK(cudaMemcpyAsync(c->cg_hd + 2 * m, c->cg_d + 2 * m, 2 * m * sizeof(double), cudaMemcpyDeviceToHost, c->st),
+     "cp rr bb");
+  CK(cudaStreamSynchronize(c->st), "sync");
+  (void)nsys;
+  return IMEX_OK;
+}
+
+// Jacobi PCG (FP64) on the systems of a segment table; x holds the initial guess.  `project`:
+// the systems are singular with the constants as null space (the pressure problems): the
+// residual is projected onto the range and the preconditioned residual kept mean-free.
+template <typename Op, typename OpDot>
+imex_status pcg(imex_ctx* c, const imex_ctx::Seg& sg, Op op, OpDot op_dot, bool fused, const double* b, double* x,
+                const double* dinv, double tol, int maxit, bool project, long long* iters_out, double* res_out) {
+  const SegTable& t = sg.t;
+  CgScalars sc = scalars(c, tol, project);
+  const int nsys = t.nseg;
+  const int m = c->maxsys;
+  double* r = c->cr;
+  double* p = c->cp;
+  double* Ap = c->cAp;
   TRY(op(x, Ap));
-  if (std::is_same<T, double>::value) {
-    for (int s = 0; s < nsys; ++s) {
-      LinComb lc{};
-      lc.nterms = 2;
-      lc.x[0] = reinterpret_cast<const double*>(b) + s * n; lc.c[0] = 1.0;
-      lc.x[1] = reinterpret_cast<const double*>(Ap) + s * n; lc.c[1] = -1.0;
-      lincomb(reinterpret_cast<double*>(r) + s * n, lc, n, c->st);
-    }
-  } else {
-    for (int s = 0; s < nsys; ++s)
-      sub_f(reinterpret_cast<float*>(r) + s * n, reinterpret_cast<const float*>(b) + s * n,
-            reinterpret_cast<const float*>(Ap) + s * n, n, c->st);
-  }
-  if (mean_free) {
-    // project r onto the range (remove its Euclidean mean) -- singular pressure problems
-    remove_mean_t(r, sizeof(T), n, c->partial, c->nblocks, c->dscal + 32, c->st);
-  }
-  // bb = (b, b) with b projected for the singular case: use r0 + A x0 ~ b; simpler: dot of b
-  if (std::is_same<T, double>::value)
-    dot_batched(reinterpret_cast<const double*>(b), reinterpret_cast<const double*>(b), n, stride, nsys,
-                c->partial, c->nblocks, sc.bb, c->st);
-  else
-    dot_batched_f(reinterpret_cast<const float*>(b), reinterpret_cast<const float*>(b), n, stride, nsys,
-                  c->partial, c->nblocks, sc.bb, c->st);
-  cg_init<T>(p, z, r, dinv, n, stride, nsys, sc, c->partial, c->nblocks, c->st);
+  LinComb lc{};
+  lc.nterms = 2;
+  lc.x[0] = b; lc.c[0] = 1.0;
+  lc.x[1] = Ap; lc.c[1] = -1.0;
+  lincomb(r, lc, sg.total, c->st);        // r = b - A x (the segments tile [0, total))
+  if (project) seg_remove_mean(r, t, c->cg_d + 6 * m, c->seg_partial, c->counters + 3, c->st);
+  seg_dot<double>(b, b, t, sc.bb, c->seg_partial, c->counters + 3, c->st);
+  seg_init<double>(r, dinv, t, sc, c->seg_partial, c->counters + 2, 1, c->st);
+  seg_step_p<double>(p, r, dinv, t, sc, 1, c->st);
   CK(cudaGetLastError(), "cg_init");
   const int chunk = 16;
-  int it = 0;
-  bool all_done = false;
-  while (it < maxit + chunk) {
+  for (int it = 0; it < maxit + chunk; it += chunk) {
     for (int k = 0; k < chunk; ++k) {
-      TRY(op(p, Ap));
-      cg_pap<T>(p, Ap, n, stride, nsys, sc, c->partial, c->nblocks, c->st);
-      cg_step_xr<T>(x, r, p, Ap, dinv, z, n, stride, nsys, sc, maxit, c->partial, c->nblocks, c->st);
-      cg_step_p<T>(p, z, n, stride, nsys, sc, c->nblocks, c->st);
+      if (fused) {
+        TRY(op_dot(p, Ap, &sc));                    // A p, (p, A p) and alpha in one launch
+      } else {
+        TRY(op(p, Ap));
+        seg_pap<double>(p, Ap, t, sc, c->seg_partial, c->counters + 3, c->st);
+      }
+      seg_step_xr<double>(x, r, p, Ap, dinv, t, sc, maxit, c->seg_partial, c->counters + 1, c->st);
+      seg_step_p<double>(p, r, dinv, t, sc, 0, c->st);
     }
-    it += chunk;
-    CK(cudaMemcpyAsync(c->hiscal, c->iscal, 8 * sizeof(int), cudaMemcpyDeviceToHost, c->st), "memcpy flags");
-    CK(cudaStreamSynchronize(c->st), "sync");
-    all_done = true;
-    for (int s = 0; s < nsys; ++s) all_done = all_done && c->hiscal[s] != 0;
-    if (all_done) break;
+    TRY(pull_scalars(c, nsys));
+    bool all = true;
+    for (int s = 0; s < nsys; ++s) all = all && c->cg_hi[s] != 0;
+    if (all) break;
   }
-  CK(cudaMemcpyAsync(c->hscal, c->dscal, 24 * sizeof(double), cudaMemcpyDeviceToHost, c->st), "memcpy scal");
-  CK(cudaMemcpyAsync(c->hiscal, c->iscal, 8 * sizeof(int), cudaMemcpyDeviceToHost, c->st), "memcpy flags");
-  CK(cudaStreamSynchronize(c->st), "sync");
   long long its = 0;
   double res = 0.0;
   imex_status st = IMEX_OK;
   for (int s = 0; s < nsys; ++s) {
-    its += c->hiscal[4 + s];
-    const double bb = c->hscal[12 + s];
-    const double rr = c->hscal[8 + s];
-    const double rel = bb > 0 ? std::sqrt(rr / bb) : std::sqrt(rr);
-    res = std::max(res, rel);
-    if (c->hiscal[s] == 3 || c->hiscal[s] == 0) st = IMEX_ENOTCONV;
-    if (c->hiscal[s] == 2) st = IMEX_EUNSTABLE;
+    its += c->cg_hi[m + s];
+    const double rr = c->cg_hd[2 * m + s], bb = c->cg_hd[3 * m + s];
+    res = std::max(res, bb > 0 ? std::sqrt(rr / bb) : std::sqrt(rr));
+    if (c->cg_hi[s] == 3 || c->cg_hi[s] == 0) st = IMEX_ENOTCONV;
+    if (c->cg_hi[s] == 2) st = IMEX_EUNSTABLE;
   }
   if (iters_out) *iters_out += its;
   if (res_out) *res_out = res;
   if (st == IMEX_ENOTCONV) return fail(c, st, "CG did not converge within maxit");
   if (st == IMEX_EUNSTABLE) return fail(c, st, "NaN in CG residual");
+  return IMEX_OK;
+}
+
+// Mixed-precision PCG (the IMEX_MIXED form).  The iteration itself runs entirely in FP32:
+// operator and Jacobi preconditioner applies, the correction y, the recursive residual and
+// the search directions (GB300's FP64 rate is a small fraction of its FP32 rate, so FP64
+// stays out of the per-node inner loop; dot products accumulate in FP32 per thread and in
+// FP64 across threads and blocks).  FP64 holds the iterate x and the true residual: when the
+// recursive residual has dropped by `delta` since the last replacement, or meets the
+// tolerance, the correction is flushed (x += y, y = 0) and the residual replaced by the
+// true FP64 residual b - A64 x (reliable updates; the FP32 recursion drifts from the true
+// residual by about eps32 times the residual it started from, so a replacement after every
+// two orders of magnitude keeps the drift at the 1e-5 level).  The search direction is kept
+// across a replacement while the recursive residual still tracks the true one (within a
+// factor sqrt 2) and restarts from the true residual otherwise.  Singular (pressure) systems keep the preconditioned residual and
+// the search directions mean-free.  A system is finished only when its true FP64 residual
+// meets the tolerance.
+template <typename Op64, typename Op32, typename Op32Dot>
+imex_status pcg_mixed(imex_ctx* c, const imex_ctx::Seg& sg, Op64 op64, Op32 op32, Op32Dot op32dot, bool fused,
+                      const double* b, double* x, const float* dinv, double tol, int maxit, bool project,
+                      long long* iters_out, double* res_out) {
+  const SegTable& t = sg.t;
+  const size_t ntot = sg.total;
+  CgScalars sc = scalars(c, tol, project);
+  const int nsys = t.nseg;
+  const int m = c->maxsys;
+  const double delta = 1e-2;
+  double* r64 = c->cr;
+  float* y = c->fx;
+  float* r = c->fr;
+  float* p = c->fp;
+  float* Ap = c->fAp;
+  double* rrtrue = c->cg_d + 7 * m;
+  seg_dot<double>(b, b, t, sc.bb, c->seg_partial, c->counters + 3, c->st);
+  CK(cudaMemsetAsync(y, 0, ntot * sizeof(float), c->st), "memset");
+  std::vector<double> rr_ref(nsys, 0.0);
+  std::vector<int> done_h(nsys, 0);
+  bool started = false, restart = true;
+  int breakdowns = 0;
+  auto replace = [&]() -> imex_status {
+    if (started) {
+      axpy_f2d(x, y, ntot, c->st);                                   // flush the correction
+      CK(cudaMemsetAsync(y, 0, ntot * sizeof(float), c->st), "memset");
+      // a constant in x is invisible to the exact operator but not to its rounding
+      // (A 1 is only zero to machine precision): keep the iterate of singular systems mean-free
+      if (project) seg_remove_mean(x, t, c->cg_d + 6 * m, c->seg_partial, c->counters + 3, c->st);
+    }
+    TRY(op64(x, c->cAp));
+    LinComb lc{};
+    lc.nterms = 2;
+    lc.x[0] = b; lc.c[0] = 1.0;
+    lc.x[1] = c->cAp; lc.c[1] = -1.0;
+    lincomb(r64, lc, ntot, c->st);
+    if (project) seg_remove_mean(r64, t, c->cg_d + 6 * m, c->seg_partial, c->counters + 3, c->st);
+    seg_dot<double>(r64, r64, t, rrtrue, c->seg_partial, c->counters + 3, c->st);
+    convert_d2f(r64, r, ntot, c->st);
+    CK(cudaMemcpyAsync(c->cg_hd + 7 * m, rrtrue, nsys * sizeof(double), cudaMemcpyDeviceToHost, c->st), "cp");
+    CK(cudaMemcpyAsync(c->cg_hd + 3 * m, sc.bb, nsys * sizeof(double), cudaMemcpyDeviceToHost, c->st), "cp");
+    CK(cudaStreamSynchronize(c->st), "sync");
+    const double* rt = c->cg_hd + 7 * m;
+    const double* bbh = c->cg_hd + 3 * m;
+    const double* rrec = c->cg_hd + 2 * m;
+    for (int s = 0; s < nsys; ++s)
+      if (started && done_h[s] == 0 && rt[s] > 2.0 * rrec[s]) restart = true;
+    for (int s = 0; s < nsys; ++s) {
+      if (rt[s] != rt[s]) return fail(c, IMEX_EUNSTABLE, "NaN in the residual");
+      if (done_h[s] == 4) continue;
+      if (rt[s] <= tol * tol * bbh[s]) {
+        done_h[s] = 4;
+      } else {
+        done_h[s] = 0;
+        rr_ref[s] = rt[s];
+      }
+    }
+    if (std::getenv("IMEX_DEBUG"))
+      for (int s = 0; s < nsys && s < 4; ++s)
+        std::fprintf(stderr, "[imex] replace sys %d its %d rec %.3e true %.3e bb %.3e done %d restart %d\n", s,
+                     c->cg_hi[m + s], std::sqrt(rrec[s]), std::sqrt(rt[s]), std::sqrt(bbh[s]), done_h[s],
+                     (int)restart);
+    CK(cudaMemcpyAsync(sc.done, done_h.data(), nsys * sizeof(int), cudaMemcpyHostToDevice, c->st), "cp flags");
+    const int keep = (started && !restart) ? 1 : 0;
+    seg_init<float>(r, dinv, t, sc, c->seg_partial, c->counters + 2, 0, c->st);
+    if (!keep) seg_step_p<float>(p, r, dinv, t, sc, 1, c->st);
+    started = true;
+    restart = false;
+    c->stats.refinements++;
+    return cuda_check(c, cudaGetLastError(), "cg_init_mixed");
+  };
+  CK(cudaMemsetAsync(sc.iters, 0, nsys * sizeof(int), c->st), "memset");
+  TRY(replace());
+  const int chunk = 16;
+  for (int round = 0;; ++round) {
+    bool all = true;
+    for (int s = 0; s < nsys; ++s) all = all && done_h[s] == 4;
+    if (all) break;
+    for (int k = 0; k < chunk; ++k) {
+      if (fused) {
+        TRY(op32dot(p, Ap, &sc));
+      } else {
+        TRY(op32(p, Ap));
+        seg_pap<float>(p, Ap, t, sc, c->seg_partial, c->counters + 3, c->st);
+      }
+      seg_step_xr<float>(y, r, p, Ap, dinv, t, sc, maxit, c->seg_partial, c->counters + 1, c->st);
+      seg_step_p<float>(p, r, dinv, t, sc, 0, c->st);
+    }
+    TRY(pull_scalars(c, nsys));
+    bool need = false;
+    for (int s = 0; s < nsys; ++s) {
+      int st = c->cg_hi[s];
+      if (done_h[s] == 4) continue;
+      if (st == 2) {
+        // FP32 breakdown: restart from the FP64 residual (bounded number of times)
+        if (++breakdowns > 2) return fail(c, IMEX_EUNSTABLE, "NaN in CG residual");
+        st = 0;
+        need = true;
+        restart = true;
+      }
+      if (st == 3) return fail(c, IMEX_ENOTCONV, "CG did not converge within maxit");
+      if (st == 1) { need = true; restart = true; }                  // recursive residual converged
+      if (st == 0 && c->cg_hd[2 * m + s] < delta * delta * rr_ref[s]) need = true;
+      done_h[s] = st;
+    }
+    if (need) TRY(replace());
+    if (round > 4 * (maxit / chunk + 4)) return fail(c, IMEX_ENOTCONV, "mixed CG did not converge");
+  }
+  long long its = 0;
+  double res = 0.0;
+  for (int s = 0; s < nsys; ++s) {
+    its += c->cg_hi[m + s];
+    const double bb = c->cg_hd[3 * m + s];
+    res = std::max(res, bb > 0 ? std::sqrt(c->cg_hd[7 * m + s] / bb) : 0.0);
+  }
+  if (iters_out) *iters_out += its;
+  if (res_out) *res_out = res;
   return IMEX_OK;
 }
 
@@ -509,42 +762,22 @@ imex_status solve_poisson(imex_ctx* c, double* b, double* psi, long long* iters,
   const double tol = c->desc.tol;
   if (c->desc.precision == IMEX_FP64) {
     auto op = [&](const double* x, double* y) { return apply_pressure<double>(c, x, y, c->tmp); };
-    imex_status s = pcg<double>(c, op, b, psi, c->cr, c->cz, c->cp, c->cAp, c->cdiag, n, 1, tol, c->desc.maxit,
-                                true, iters, res);
+    auto opd = [&](const double* x, double* y, const CgScalars* d) {
+      return apply_pressure<double>(c, x, y, c->tmp, d);
+    };
+    const bool fused = c->desc.poisson == IMEX_POISSON_SIPG;
+    imex_status s = pcg(c, c->segp, op, opd, fused, b, psi, c->cdiag, tol, c->desc.maxit, true, iters, res);
     remove_weighted_mean(c, psi, c->mass_p, n);
     return s;
   }
-  // mixed: FP64 residual, FP32 inner PCG on the correction
-  const double itol = c->desc.inner_tol > 0 ? c->desc.inner_tol : 1e-5;
-  double* bb = c->dscal + 40;
-  dot_batched(b, b, n, (long long)n, 1, c->partial, c->nblocks, bb, c->st);
-  imex_status s = IMEX_OK;
-  for (int outer = 0; outer < 30; ++outer) {
-    TRY(apply_pressure<double>(c, psi, c->cAp, c->tmp));
-    LinComb lc{};
-    lc.nterms = 2; lc.x[0] = b; lc.c[0] = 1.0; lc.x[1] = c->cAp; lc.c[1] = -1.0;
-    lincomb(c->cr, lc, n, c->st);
-    remove_mean_t(c->cr, 8, n, c->partial, c->nblocks, c->dscal + 32, c->st);
-    dot_batched(c->cr, c->cr, n, (long long)n, 1, c->partial, c->nblocks, c->dscal + 41, c->st);
-    CK(cudaMemcpyAsync(c->hscal + 40, c->dscal + 40, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->st), "cp");
-    CK(cudaStreamSynchronize(c->st), "sync");
-    const double rel = c->hscal[40] > 0 ? std::sqrt(c->hscal[41] / c->hscal[40]) : 0.0;
-    if (res) *res = rel;
-    if (rel <= tol) break;
-    if (rel != rel) return fail(c, IMEX_EUNSTABLE, "NaN in Poisson residual");
-    if (outer == 29) return fail(c, IMEX_ENOTCONV, "Poisson refinement did not converge");
-    c->stats.refinements++;
-    convert_d2f(c->cr, c->fr + 0, n, c->st);
-    CK(cudaMemsetAsync(c->fx, 0, n * sizeof(float), c->st), "memset");
-    float* fb = c->fvtmp + c->d * c->nv;   // scratch for the FP32 right-hand side
-    CK(cudaMemcpyAsync(fb, c->fr, n * sizeof(float), cudaMemcpyDeviceToDevice, c->st), "cp");
-    auto op = [&](const float* x, float* y) { return apply_pressure<float>(c, x, y, c->fvtmp); };
-    s = pcg<float>(c, op, fb, c->fx, c->fr, c->fz, c->fp, c->fAp, c->fdiag, n, 1, itol, c->desc.maxit, true,
-                   iters, nullptr);
-    if (s == IMEX_ENOTCONV) s = IMEX_OK;   // inner solve is a preconditioner; the outer loop decides
-    if (s != IMEX_OK) return s;
-    axpy_f2d(psi, c->fx, n, c->st);
-  }
+  // mixed: FP32 operator and preconditioner, FP64 iterate and residual with reliable updates
+  auto op64 = [&](const double* x, double* y) { return apply_pressure<double>(c, x, y, c->tmp); };
+  auto op32 = [&](const float* x, float* y) { return apply_pressure<float>(c, x, y, c->fvtmp); };
+  auto op32d = [&](const float* x, float* y, const CgScalars* d) {
+    return apply_pressure<float>(c, x, y, c->fvtmp, d);
+  };
+  const bool fused = c->desc.poisson == IMEX_POISSON_SIPG;
+  TRY(pcg_mixed(c, c->segp, op64, op32, op32d, fused, b, psi, c->fdiag, tol, c->desc.maxit, true, iters, res));
   remove_weighted_mean(c, psi, c->mass_p, n);
   return IMEX_OK;
 }
@@ -563,41 +796,20 @@ imex_status solve_helmholtz(imex_ctx* c, const double* rhs, double* x, const dou
   const double tol = c->desc.tol;
   if (c->desc.precision == IMEX_FP64) {
     auto op = [&](const double* xx, double* yy) { return apply_helm<double>(c, xx, yy, d, nu, gamma); };
-    return pcg<double>(c, op, rhs, x, c->cr, c->cz, c->cp, c->cAp, dg, n, d, tol, c->desc.maxit, false, iters, res);
+    auto opd = [&](const double* xx, double* yy, const CgScalars* dd) {
+      return apply_helm<double>(c, xx, yy, d, nu, gamma, dd);
+    };
+    return pcg(c, c->segv, op, opd, nu == nullptr, rhs, x, dg, tol, c->desc.maxit, false, iters, res);
   }
   convert_d2f(dg, fdg, n, c->st);
   const float* fnu = nullptr;
   if (nu) { convert_d2f(nu, c->fnu, n, c->st); fnu = c->fnu; }
-  const double itol = c->desc.inner_tol > 0 ? c->desc.inner_tol : 1e-5;
-  double* bb = c->dscal + 48;
-  dot_batched(rhs, rhs, n, (long long)n, d, c->partial, c->nblocks, bb, c->st);
-  for (int outer = 0; outer < 30; ++outer) {
-    TRY(apply_helm<double>(c, x, c->cAp, d, nu, gamma));
-    LinComb lc{};
-    lc.nterms = 2; lc.x[0] = rhs; lc.c[0] = 1.0; lc.x[1] = c->cAp; lc.c[1] = -1.0;
-    lincomb(c->cr, lc, n * d, c->st);
-    dot_batched(c->cr, c->cr, n, (long long)n, d, c->partial, c->nblocks, c->dscal + 52, c->st);
-    CK(cudaMemcpyAsync(c->hscal + 48, c->dscal + 48, 8 * sizeof(double), cudaMemcpyDeviceToHost, c->st), "cp");
-    CK(cudaStreamSynchronize(c->st), "sync");
-    double rel = 0.0;
-    for (int s = 0; s < d; ++s)
-      rel = std::max(rel, c->hscal[48 + s] > 0 ? std::sqrt(c->hscal[52 + s] / c->hscal[48 + s]) : 0.0);
-    if (res) *res = rel;
-    if (rel <= tol) break;
-    if (rel != rel) return fail(c, IMEX_EUNSTABLE, "NaN in Helmholtz residual");
-    if (outer == 29) return fail(c, IMEX_ENOTCONV, "Helmholtz refinement did not converge");
-    c->stats.refinements++;
-    convert_d2f(c->cr, c->fr, n * d, c->st);
-    CK(cudaMemsetAsync(c->fx, 0, n * d * sizeof(float), c->st), "memset");
-    float* fb = c->fvtmp;
-    CK(cudaMemcpyAsync(fb, c->fr, n * d * sizeof(float), cudaMemcpyDeviceToDevice, c->st), "cp");
-    auto op = [&](const float* xx, float* yy) { return apply_helm<float>(c, xx, yy, d, fnu, gamma); };
-    imex_status s = pcg<float>(c, op, fb, c->fx, c->fr, c->fz, c->fp, c->fAp, fdg, n, d, itol, c->desc.maxit,
-                               false, iters, nullptr);
-    if (s == IMEX_ENOTCONV) s = IMEX_OK;
-    if (s != IMEX_OK) return s;
-    axpy_f2d(x, c->fx, n * d, c->st);
-  }
+  auto op64 = [&](const double* xx, double* yy) { return apply_helm<double>(c, xx, yy, d, nu, gamma); };
+  auto op32 = [&](const float* xx, float* yy) { return apply_helm<float>(c, xx, yy, d, fnu, gamma); };
+  auto op32d = [&](const float* xx, float* yy, const CgScalars* dd) {
+    return apply_helm<float>(c, xx, yy, d, fnu, gamma, dd);
+  };
+  TRY(pcg_mixed(c, c->segv, op64, op32, op32d, fnu == nullptr, rhs, x, fdg, tol, c->desc.maxit, false, iters, res));
   return IMEX_OK;
 }
 
@@ -676,6 +888,7 @@ imex_status stage_rhs(imex_ctx* c, double t, const double* v, const double* nu, 
     TRY(graddiv(c, v, nu, Fd3, nullptr));
   }
   SipgArgs<double> a = sipg_args<double>(v, Fd1, c->d, (long long)c->nv, nu_ptr(c, nu), nu_const(c), vb, 0.0, -1.0, 1);
+  a.ops = c->ops64_v;
   TRY(launch_check(c, sipg_apply<double>(c->gv, c->Nv, a, c->st), "sipg_apply(Fd1)"));
   if (Fs) {
     TRY(launch_check(c, eval_field(c->gv, c->Nv, 2, spec(c->f_kind, c->f_p), t, nullptr, (long long)c->nv, Fs, c->st),
@@ -705,6 +918,7 @@ imex_status helmholtz_stage(imex_ctx* c, const double* gfield, const double* nu,
   if (vb) {
     SipgArgs<double> a = sipg_args<double>(c->cz, c->cp, c->d, (long long)c->nv, nu_ptr(c, nu), nu_const(c), vb, 0.0,
                                            -gamma, 0);
+    a.ops = c->ops64_v;
     CK(cudaMemsetAsync(c->cz, 0, nt * sizeof(double), c->st), "memset");
     TRY(launch_check(c, sipg_apply<double>(c->gv, c->Nv, a, c->st), "sipg_apply(rb)"));
     LinComb lc{};
@@ -884,6 +1098,7 @@ imex_status sdc_step(imex_ctx* c, double* v, double t, double dt) {
   auto f_d1 = [&](const double* vm, const double* num, double tt, double* out) -> imex_status {
     TRY(eval_vb(c, tt, &vb));
     SipgArgs<double> a = sipg_args<double>(vm, out, d, (long long)c->nv, nu_ptr(c, num), nu_const(c), vb, 0.0, -1.0, 1);
+    a.ops = c->ops64_v;
     return launch_check(c, sipg_apply<double>(c->gv, c->Nv, a, c->st), "sipg_apply(Fd1)");
   };
   for (int m = 0; m <= M; ++m) TRY(eval_nu(c, tm[m], c->sv[m], c->snu[m]));
@@ -1045,6 +1260,7 @@ imex_status imex_create(const imex_mesh_desc* desc, imex_ctx** out) {
     g.n[k] = (k < d) ? desc->nelem[k] : 1;
     g.lo[k] = (k < d) ? desc->lo[k] : 0.0;
     g.h[k] = (k < d) ? (desc->hi[k] - desc->lo[k]) / desc->nelem[k] : 1.0;
+    g.hf[k] = (float)g.h[k];
     ne *= g.n[k];
   }
   if (ne > (1LL << 30)) { delete c; return IMEX_EINVAL; }
@@ -1078,6 +1294,24 @@ imex_status imex_create(const imex_mesh_desc* desc, imex_ctx** out) {
     if (s == IMEX_OK) s = dalloc(c, &c->dtab32, 1);
     if (s == IMEX_OK && cudaMemcpy(c->dtab64, h64, sizeof(*h64), cudaMemcpyHostToDevice) != cudaSuccess) s = IMEX_ECUDA;
     if (s == IMEX_OK && cudaMemcpy(c->dtab32, h32, sizeof(*h32), cudaMemcpyHostToDevice) != cudaSuccess) s = IMEX_ECUDA;
+    if (s == IMEX_OK) init_const_lines(*h64);
+    if (s == IMEX_OK) {
+      double hh[3] = {g.h[0], g.h[1], g.h[2]};
+      LineOps<double>* o64 = new LineOps<double>();
+      LineOps<float>* o32 = new LineOps<float>();
+      const int Ns[2] = {c->Nv, c->Np};
+      for (int sp = 0; sp < 2 && s == IMEX_OK; ++sp) {
+        build_line_ops(*h64, Ns[sp], hh, d, o64, o32);
+        LineOps<double>** p64 = sp == 0 ? &c->ops64_v : &c->ops64_p;
+        LineOps<float>** p32 = sp == 0 ? &c->ops32_v : &c->ops32_p;
+        s = dalloc(c, p64, 1);
+        if (s == IMEX_OK) s = dalloc(c, p32, 1);
+        if (s == IMEX_OK && cudaMemcpy(*p64, o64, sizeof(*o64), cudaMemcpyHostToDevice) != cudaSuccess) s = IMEX_ECUDA;
+        if (s == IMEX_OK && cudaMemcpy(*p32, o32, sizeof(*o32), cudaMemcpyHostToDevice) != cudaSuccess) s = IMEX_ECUDA;
+      }
+      delete o64;
+      delete o32;
+    }
     delete h64;
     delete h32;
     if (s != IMEX_OK) return bail(s);
@@ -1097,17 +1331,39 @@ imex_status imex_create(const imex_mesh_desc* desc, imex_ctx** out) {
   if ((s = dalloc(c, &c->mass_v, c->nv)) != IMEX_OK) return bail(s);
   if ((s = dalloc(c, &c->mass_p, c->np)) != IMEX_OK) return bail(s);
   if ((s = dalloc(c, &c->cdiag, c->np + c->nv)) != IMEX_OK) return bail(s);
-  float** f32[] = {&c->fx, &c->fr, &c->fz, &c->fp, &c->fAp};
+  float** f32[] = {&c->fx, &c->fr, &c->fp, &c->fAp};
   for (float** p : f32) if ((s = dalloc(c, p, big)) != IMEX_OK) return bail(s);
   if ((s = dalloc(c, &c->fdiag, c->np + c->nv)) != IMEX_OK) return bail(s);
   if ((s = dalloc(c, &c->fnu, c->nv)) != IMEX_OK) return bail(s);
   if ((s = dalloc(c, &c->fvtmp, nt + c->np)) != IMEX_OK) return bail(s);
   c->nblocks = 152 * 4;
   if ((s = dalloc(c, &c->partial, (size_t)c->nblocks * 8)) != IMEX_OK) return bail(s);
+  if ((s = dalloc(c, &c->apartial, (size_t)(g.ne + 64) * 3)) != IMEX_OK) return bail(s);
+  if ((s = dalloc(c, &c->counters, 8)) != IMEX_OK) return bail(s);
+  cudaMemsetAsync(c->counters, 0, 8 * sizeof(unsigned int), c->st);
   if ((s = dalloc(c, &c->dscal, 128)) != IMEX_OK) return bail(s);
   if ((s = dalloc(c, &c->iscal, 64)) != IMEX_OK) return bail(s);
   if (cudaMallocHost((void**)&c->hscal, 128 * sizeof(double)) != cudaSuccess) return bail(IMEX_ENOMEM);
   if (cudaMallocHost((void**)&c->hiscal, 64 * sizeof(int)) != cudaSuccess) return bail(IMEX_ENOMEM);
+  {
+    // CG systems: the pressure (one system) and the d velocity components
+    const long long offp = 0, lenp = (long long)c->np;
+    long long offv[3], doffv[3] = {0, 0, 0}, lenv[3];
+    for (int k = 0; k < d; ++k) { offv[k] = (long long)(k * c->nv); lenv[k] = (long long)c->nv; }
+    if ((s = make_seg(c, 1, &offp, &offp, &lenp, &c->segp)) != IMEX_OK) return bail(s);
+    if ((s = make_seg(c, d, offv, doffv, lenv, &c->segv)) != IMEX_OK) return bail(s);
+    c->maxsys = d;
+    const int nblk = std::max(c->segp.t.nblk, c->segv.t.nblk);
+    if ((s = dalloc(c, &c->seg_partial, (size_t)5 * nblk + 64)) != IMEX_OK) return bail(s);
+    if ((s = dalloc(c, &c->cg_d, (size_t)12 * c->maxsys)) != IMEX_OK) return bail(s);
+    if ((s = dalloc(c, &c->cg_i, (size_t)2 * c->maxsys)) != IMEX_OK) return bail(s);
+    cudaMemsetAsync(c->cg_d, 0, 12 * c->maxsys * sizeof(double), c->st);
+    if ((s = dalloc(c, &c->cg_f, (size_t)4 * c->maxsys)) != IMEX_OK) return bail(s);
+    cudaMemsetAsync(c->cg_f, 0, 4 * c->maxsys * sizeof(float), c->st);
+    cudaMemsetAsync(c->cg_i, 0, 2 * c->maxsys * sizeof(int), c->st);
+    if (cudaMallocHost((void**)&c->cg_hd, 12 * c->maxsys * sizeof(double)) != cudaSuccess) return bail(IMEX_ENOMEM);
+    if (cudaMallocHost((void**)&c->cg_hi, 2 * c->maxsys * sizeof(int)) != cudaSuccess) return bail(IMEX_ENOMEM);
+  }
   cudaMemsetAsync(c->psi, 0, c->np * sizeof(double), c->st);
   cudaMemsetAsync(c->v, 0, big * sizeof(double), c->st);
   // mass diagonals: apply alpha=1, beta=0 to a ones vector via the diag kernel (beta = 0)
@@ -1132,6 +1388,8 @@ void imex_destroy(imex_ctx* c) {
   for (void* p : c->allocs) cudaFree(p);
   if (c->hscal) cudaFreeHost(c->hscal);
   if (c->hiscal) cudaFreeHost(c->hiscal);
+  if (c->cg_hd) cudaFreeHost(c->cg_hd);
+  if (c->cg_hi) cudaFreeHost(c->cg_hi);
   if (c->own_stream && c->st) cudaStreamDestroy(c->st);
   delete c;
 }
@@ -1301,6 +1559,7 @@ imex_status imex_op_sipg(imex_ctx* c, int space, const double* x, double* y, int
   const double nu0 = vel ? nu_const(c) : 1.0;
   if (precision == IMEX_FP64) {
     SipgArgs<double> a = sipg_args<double>(c->cx, c->cAp, nsys, (long long)n, dnu, nu0, dg, alpha, beta, minv);
+    a.ops = line_ops<double>(c, vel);
     TRY(launch_check(c, sipg_apply<double>(g, N, a, c->st), "sipg_apply"));
   } else {
     convert_d2f(c->cx, c->fx, n * nsys, c->st);
@@ -1309,6 +1568,7 @@ imex_status imex_op_sipg(imex_ctx* c, int space, const double* x, double* y, int
     const float* fg = nullptr;
     if (dg) { convert_d2f(dg, c->fr, n * nsys, c->st); fg = c->fr; }
     SipgArgs<float> a = sipg_args<float>(c->fx, c->fAp, nsys, (long long)n, fnu, nu0, fg, alpha, beta, minv);
+    a.ops = line_ops<float>(c, vel);
     TRY(launch_check(c, sipg_apply<float>(g, N, a, c->st), "sipg_apply(f32)"));
     f2d(c->fAp, c->cAp, n * nsys, c->st);
   }

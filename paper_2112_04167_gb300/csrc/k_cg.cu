@@ -1,0 +1,508 @@
+// Segmented Jacobi-PCG kernels (the linear solves of Sec. 3: pressure Poisson and viscous
+// Helmholtz problems, both symmetric positive (semi-)definite, preconditioned by the
+// operator's diagonal).
+//
+// The systems solved together (the vector components of one instance, or the instances of
+// a batch) are segments of the same vectors.  A 1D grid of blocks covers them, each block
+// one chunk of SEG_CHUNK elements of one segment, so uneven segment lengths cost no idle
+// blocks.  Per-block partial sums are combined in block order (deterministic) by the last
+// block to finish; the per-system scalars never leave device memory.
+//
+// Singular systems (project = 1; null space = the constants) run the projected iteration:
+// the residual r' = r - rho 1 (rho = mean r) and the preconditioned residual
+// z' = D^{-1} r' - mean(D^{-1} r') are kept out of the null space.  Rounding in A p lets the
+// recursive residual pick up a constant part every iteration; the partial sums
+// S_rz = (r, D^{-1} r), S_rr = (r, r), S_z = sum D^{-1} r, S_r = sum r of the unprojected r give
+// the projected scalars in closed form,
+//   (r', z') = S_rz - 2 rho S_z + rho^2 sum D^{-1},  (r', r') = S_rr - n rho^2,
+//   mean(D^{-1} r') = (S_z - rho sum D^{-1}) / n,
+// and the direction update stores r' back, so the drift never accumulates.
+//
+// Data movement: every kernel streams its vectors with 16-byte loads, all of a thread's loads
+// issued before the arithmetic (the kernels are bound by bytes in flight, not by issue), and
+// falls back to scalar accesses for chunks whose addresses are not 16-byte aligned.  FP32
+// instances accumulate per thread and per warp in FP32 and switch to FP64 at the per-warp
+// level (GB300 executes FP64 at a small fraction of the FP32 rate).
+#include <cstdint>
+#include <type_traits>
+
+#include "common.cuh"
+#include "kernels.h"
+#include "vec.h"
+
+namespace imex {
+namespace {
+
+constexpr int CG_THREADS = 256;
+
+template <typename T> struct Vec16;
+template <> struct Vec16<float> { using V = float4; static constexpr int n = 4; };
+template <> struct Vec16<double> { using V = double2; static constexpr int n = 2; };
+
+__device__ __forceinline__ void vload(const float* p, float (&o)[4]) {
+  const float4 v = *reinterpret_cast<const float4*>(p);
+  o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+}
+__device__ __forceinline__ void vload(const double* p, double (&o)[2]) {
+  const double2 v = *reinterpret_cast<const double2*>(p);
+  o[0] = v.x; o[1] = v.y;
+}
+__device__ __forceinline__ void vstore(float* p, const float (&o)[4]) {
+  *reinterpret_cast<float4*>(p) = make_float4(o[0], o[1], o[2], o[3]);
+}
+__device__ __forceinline__ void vstore(double* p, const double (&o)[2]) {
+  *reinterpret_cast<double2*>(p) = make_double2(o[0], o[1]);
+}
+__device__ __forceinline__ bool al16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+template <typename T>
+__device__ __forceinline__ T warp_sum_t(T v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// K block sums of per-thread values in T; out[] valid in thread 0 (per-warp sums in T, added
+// in FP64 in warp order).  Ends with a barrier, so it may be called repeatedly.
+template <typename T, int K>
+__device__ __forceinline__ void block_sum_k(T (&v)[K], double (&out)[K]) {
+  __shared__ T ws[K][32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < K; ++k) v[k] = warp_sum_t(v[k]);
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) ws[k][w] = v[k];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int nw = (int)(blockDim.x >> 5);
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      double acc = 0.0;
+      for (int i = 0; i < nw; ++i) acc += (double)ws[k][i];
+      out[k] = acc;
+    }
+  }
+  __syncthreads();
+}
+
+// last block of the grid? (thread 0 publishes; all threads get the answer)
+__device__ __forceinline__ bool last_block(unsigned int* counter) {
+  __shared__ int am_last;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    am_last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (am_last) __threadfence();
+  return am_last != 0;
+}
+
+// Totals over the blocks of each segment of the K partials partial[k * nblk + b], handed to
+// fn(q, tot) once per segment (by one thread).  Few segments: the whole block adds each
+// segment's partials (one load latency); many: one warp per segment.
+template <int K, typename Fn>
+__device__ __forceinline__ void seg_totals(const SegTable& t, const double* __restrict__ partial, Fn fn) {
+  if (t.nseg <= 4) {
+    for (int q = 0; q < t.nseg; ++q) {
+      double v[K];
+#pragma unroll
+      for (int k = 0; k < K; ++k) v[k] = 0.0;
+      for (int b = t.seg_blk0[q] + threadIdx.x; b < t.seg_blk0[q + 1]; b += blockDim.x) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) v[k] += partial[(size_t)k * t.nblk + b];
+      }
+      double tot[K];
+      block_sum_k<double, K>(v, tot);
+      if (threadIdx.x == 0) fn(q, tot);
+    }
+  } else {
+    const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5, lane = threadIdx.x & 31;
+    for (int q = warp; q < t.nseg; q += nw) {
+      double v[K];
+#pragma unroll
+      for (int k = 0; k < K; ++k) v[k] = 0.0;
+#pragma unroll 4
+      for (int b = t.seg_blk0[q] + lane; b < t.seg_blk0[q + 1]; b += 32) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) v[k] += partial[(size_t)k * t.nblk + b];
+      }
+#pragma unroll
+      for (int k = 0; k < K; ++k) v[k] = warp_sum_t(v[k]);
+      if (lane == 0) fn(q, v);
+    }
+  }
+}
+
+// projected (or plain) CG scalars of one segment from its totals S_rz, S_rr, S_z, S_r
+struct SegSums {
+  double rz, rr, zmean, rmean;
+};
+__device__ __forceinline__ SegSums seg_scalars(const double* tot, double n, double dsum, int project) {
+  SegSums o;
+  o.rz = tot[0];
+  o.rr = tot[1];
+  o.zmean = 0.0;
+  o.rmean = 0.0;
+  if (project) {
+    const double rho = tot[3] / n;
+    o.rz = tot[0] - 2.0 * rho * tot[2] + rho * rho * dsum;
+    o.rr = fmax(tot[1] - n * rho * rho, 0.0);
+    o.zmean = (tot[2] - rho * dsum) / n;
+    o.rmean = rho;
+  }
+  return o;
+}
+
+// this block's chunk (one 32-byte load)
+__device__ __forceinline__ SegBlock chunk_of(const SegTable& t) {
+  const int4* p = reinterpret_cast<const int4*>(t.blk + blockIdx.x);
+  const int4 a = p[0], b = p[1];
+  SegBlock c;
+  c.off = ((long long)(unsigned)a.x) | ((long long)a.y << 32);
+  c.doff = ((long long)(unsigned)a.z) | ((long long)a.w << 32);
+  c.n = b.x;
+  c.s = b.y;
+  return c;
+}
+
+template <typename T> __device__ __forceinline__ T pick(const double* d, const float* f, int s);
+template <> __device__ __forceinline__ float pick<float>(const double*, const float* f, int s) { return f[s]; }
+template <> __device__ __forceinline__ double pick<double>(const double* d, const float*, int s) { return d[s]; }
+
+__host__ __device__ constexpr int unroll_of(int vec) { return SEG_CHUNK / (vec * CG_THREADS); }
+
+// x += alpha p, r -= alpha A p, and the partial sums of the new residual; the last block
+// forms the new scalars and the next direction coefficient beta = rz_new / rz
+template <typename T>
+__global__ void __launch_bounds__(CG_THREADS, sizeof(T) == 4 ? 4 : 2)
+seg_xr_kernel(T* __restrict__ x, T* __restrict__ r, const T* __restrict__ p, const T* __restrict__ Ap,
+              const T* __restrict__ dinv, SegTable t, CgScalars sc, double* __restrict__ partial,
+              unsigned int* __restrict__ counter, int maxit) {
+  constexpr int VN = Vec16<T>::n, U = unroll_of(VN);
+  const SegBlock c = chunk_of(t);
+  T acc[4] = {T(0), T(0), T(0), T(0)};          // (r, z), (r, r), sum z, sum r
+  if (sc.done[c.s] == 0) {
+    const T a = pick<T>(sc.alpha, sc.alpha_f, c.s);
+    T* xs = x + c.off;
+    T* rs = r + c.off;
+    const T* ps = p + c.off;
+    const T* aps = Ap + c.off;
+    const T* ds = dinv + c.doff;
+    const int n = c.n;
+    int done_n = 0;
+    if (al16(xs) && al16(rs) && al16(ps) && al16(aps) && al16(ds)) {
+      const int nv = n / VN;
+      T rv[U][VN], av[U][VN], dv[U][VN], xv[U][VN], pv[U][VN];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int v = threadIdx.x + u * CG_THREADS;
+        if (v < nv) {
+          vload(rs + v * VN, rv[u]); vload(aps + v * VN, av[u]); vload(ds + v * VN, dv[u]);
+          vload(xs + v * VN, xv[u]); vload(ps + v * VN, pv[u]);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int v = threadIdx.x + u * CG_THREADS;
+        if (v < nv) {
+#pragma unroll
+          for (int j = 0; j < VN; ++j) {
+            const T ri = rv[u][j] - a * av[u][j];
+            const T zi = ri * dv[u][j];
+            xv[u][j] += a * pv[u][j];
+            rv[u][j] = ri;
+            acc[0] += ri * zi;
+            acc[1] += ri * ri;
+            acc[2] += zi;
+            acc[3] += ri;
+          }
+          vstore(xs + v * VN, xv[u]);
+          vstore(rs + v * VN, rv[u]);
+        }
+      }
+      done_n = nv * VN;
+    }
+    for (int i = done_n + threadIdx.x; i < n; i += CG_THREADS) {
+      const T ri = rs[i] - a * aps[i];
+      const T zi = ri * ds[i];
+      xs[i] += a * ps[i];
+      rs[i] = ri;
+      acc[0] += ri * zi;
+      acc[1] += ri * ri;
+      acc[2] += zi;
+      acc[3] += ri;
+    }
+  }
+  double bs[4];
+  block_sum_k<T, 4>(acc, bs);
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < 4; ++k) partial[(size_t)k * t.nblk + blockIdx.x] = bs[k];
+  }
+  if (!last_block(counter)) return;
+  seg_totals<4>(t, partial, [&](int q, const double* tot) {
+    if (sc.done[q] != 0) return;
+    const SegSums o = seg_scalars(tot, (double)t.len[q], sc.dsum[q], sc.project);
+    const double bt = sc.rz[q] != 0.0 ? o.rz / sc.rz[q] : 0.0;
+    sc.rz_old[q] = sc.rz[q];
+    sc.rz[q] = o.rz;
+    sc.rr[q] = o.rr;
+    sc.zmean[q] = o.zmean;
+    sc.rmean[q] = o.rmean;
+    sc.zmean_f[q] = (float)o.zmean;
+    sc.rmean_f[q] = (float)o.rmean;
+    sc.beta[q] = bt;
+    sc.beta_f[q] = (float)bt;
+    sc.iters[q] += 1;
+    if (o.rr != o.rr || !isfinite(bt)) sc.done[q] = 2;
+    else if (o.rr <= sc.tol2 * sc.bb[q]) sc.done[q] = 1;
+    else if (sc.iters[q] >= maxit) sc.done[q] = 3;
+  });
+  if (threadIdx.x == 0) *counter = 0u;
+}
+
+// z' = D^{-1} (r - rmean) - zmean, p = z' + beta p (beta = 0 with restart = 1); projected
+// systems store r - rmean back
+template <typename T>
+__global__ void __launch_bounds__(CG_THREADS)
+seg_p_kernel(T* __restrict__ p, T* __restrict__ r, const T* __restrict__ dinv, SegTable t, CgScalars sc,
+             int restart) {
+  constexpr int VN = Vec16<T>::n, U = unroll_of(VN);
+  const SegBlock c = chunk_of(t);
+  if (sc.done[c.s] != 0) return;
+  const bool proj = sc.project != 0;
+  const T beta = restart ? T(0) : pick<T>(sc.beta, sc.beta_f, c.s);
+  const T zm = proj ? pick<T>(sc.zmean, sc.zmean_f, c.s) : T(0);
+  const T rm = proj ? pick<T>(sc.rmean, sc.rmean_f, c.s) : T(0);
+  T* ps = p + c.off;
+  T* rs = r + c.off;
+  const T* ds = dinv + c.doff;
+  const int n = c.n;
+  int done_n = 0;
+  if (al16(ps) && al16(rs) && al16(ds)) {
+    const int nv = n / VN;
+    T rv[U][VN], dv[U][VN], pv[U][VN];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int v = threadIdx.x + u * CG_THREADS;
+      if (v < nv) {
+        vload(rs + v * VN, rv[u]); vload(ds + v * VN, dv[u]);
+        if (!restart) {
+          vload(ps + v * VN, pv[u]);
+        } else {
+#pragma unroll
+          for (int j = 0; j < VN; ++j) pv[u][j] = T(0);
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int v = threadIdx.x + u * CG_THREADS;
+      if (v < nv) {
+#pragma unroll
+        for (int j = 0; j < VN; ++j) {
+          const T ri = rv[u][j] - rm;
+          const T zi = ri * dv[u][j] - zm;
+          rv[u][j] = ri;
+          pv[u][j] = zi + beta * pv[u][j];
+        }
+        if (proj) vstore(rs + v * VN, rv[u]);
+        vstore(ps + v * VN, pv[u]);
+      }
+    }
+    done_n = nv * VN;
+  }
+  for (int i = done_n + threadIdx.x; i < n; i += CG_THREADS) {
+    const T ri = rs[i] - rm;
+    const T zi = ri * ds[i] - zm;
+    if (proj) rs[i] = ri;
+    ps[i] = restart ? zi : zi + beta * ps[i];
+  }
+}
+
+// streaming dot of one chunk into acc (16-byte loads where aligned)
+template <typename T>
+__device__ __forceinline__ T chunk_dot(const T* xs, const T* ys, int n) {
+  constexpr int VN = Vec16<T>::n, U = unroll_of(VN);
+  T acc = T(0);
+  int done_n = 0;
+  if (al16(xs) && al16(ys)) {
+    const int nv = n / VN;
+    T xv[U][VN], yv[U][VN];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int v = threadIdx.x + u * CG_THREADS;
+      if (v < nv) { vload(xs + v * VN, xv[u]); vload(ys + v * VN, yv[u]); }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int v = threadIdx.x + u * CG_THREADS;
+      if (v < nv) {
+#pragma unroll
+        for (int j = 0; j < VN; ++j) acc += xv[u][j] * yv[u][j];
+      }
+    }
+    done_n = nv * VN;
+  }
+  for (int i = done_n + threadIdx.x; i < n; i += CG_THREADS) acc += xs[i] * ys[i];
+  return acc;
+}
+
+// dot per segment into out[s]
+template <typename T>
+__global__ void __launch_bounds__(CG_THREADS)
+seg_dot_kernel(const T* __restrict__ x, const T* __restrict__ y, SegTable t, double* __restrict__ out,
+               double* __restrict__ partial, unsigned int* __restrict__ counter) {
+  const SegBlock c = chunk_of(t);
+  T acc[1] = {chunk_dot(x + c.off, y + c.off, c.n)};
+  double bs[1];
+  block_sum_k<T, 1>(acc, bs);
+  if (threadIdx.x == 0) partial[blockIdx.x] = bs[0];
+  if (!last_block(counter)) return;
+  seg_totals<1>(t, partial, [&](int q, const double* tot) { out[q] = tot[0]; });
+  if (threadIdx.x == 0) *counter = 0u;
+}
+
+// (p, A p) per running system into sc.pAp and the step length alpha = rz / pAp
+template <typename T>
+__global__ void __launch_bounds__(CG_THREADS)
+seg_pap_kernel(const T* __restrict__ p, const T* __restrict__ Ap, SegTable t, CgScalars sc,
+               double* __restrict__ partial, unsigned int* __restrict__ counter) {
+  const SegBlock c = chunk_of(t);
+  T acc[1] = {sc.done[c.s] == 0 ? chunk_dot(p + c.off, Ap + c.off, c.n) : T(0)};
+  double bs[1];
+  block_sum_k<T, 1>(acc, bs);
+  if (threadIdx.x == 0) partial[blockIdx.x] = bs[0];
+  if (!last_block(counter)) return;
+  seg_totals<1>(t, partial, [&](int q, const double* tot) {
+    if (sc.done[q] != 0) return;
+    const double al = tot[0] != 0.0 ? sc.rz[q] / tot[0] : 0.0;
+    const bool ok = isfinite(al);
+    sc.pAp[q] = tot[0];
+    sc.alpha[q] = ok ? al : 0.0;
+    sc.alpha_f[q] = ok ? (float)al : 0.f;
+    if (!ok) sc.done[q] = 2;
+  });
+  if (threadIdx.x == 0) *counter = 0u;
+}
+
+// CG scalars of a new residual r for the running systems (all systems with reset = 1,
+// which also restarts their iteration counts and convergence flags); also sum D^{-1}
+template <typename T>
+__global__ void __launch_bounds__(CG_THREADS)
+seg_init_kernel(const T* __restrict__ r, const T* __restrict__ dinv, SegTable t, CgScalars sc,
+                double* __restrict__ partial, unsigned int* __restrict__ counter, int reset) {
+  const SegBlock c = chunk_of(t);
+  T acc[5] = {T(0), T(0), T(0), T(0), T(0)};   // (r, z), (r, r), sum z, sum r, sum D^{-1}
+  if (sc.done[c.s] == 0 || reset) {
+    const T* rs = r + c.off;
+    const T* ds = dinv + c.doff;
+    for (int i = threadIdx.x; i < c.n; i += CG_THREADS) {
+      const T ri = rs[i];
+      const T di = ds[i];
+      const T zi = ri * di;
+      acc[0] += ri * zi;
+      acc[1] += ri * ri;
+      acc[2] += zi;
+      acc[3] += ri;
+      acc[4] += di;
+    }
+  }
+  double bs[5];
+  block_sum_k<T, 5>(acc, bs);
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < 5; ++k) partial[(size_t)k * t.nblk + blockIdx.x] = bs[k];
+  }
+  if (!last_block(counter)) return;
+  seg_totals<5>(t, partial, [&](int q, const double* tot) {
+    if (!(reset || sc.done[q] == 0)) return;
+    const SegSums o = seg_scalars(tot, (double)t.len[q], tot[4], sc.project);
+    sc.dsum[q] = tot[4];
+    sc.rz[q] = o.rz;
+    sc.rr[q] = o.rr;
+    sc.zmean[q] = o.zmean;
+    sc.rmean[q] = o.rmean;
+    sc.zmean_f[q] = (float)o.zmean;
+    sc.rmean_f[q] = (float)o.rmean;
+    if (reset) {
+      sc.iters[q] = 0;
+      sc.done[q] = (o.rr <= sc.tol2 * sc.bb[q]) ? 1 : 0;
+    }
+  });
+  if (threadIdx.x == 0) *counter = 0u;
+}
+
+// per-segment mean removal: x -= mean over the segment (two passes)
+__global__ void __launch_bounds__(CG_THREADS)
+seg_sum_kernel(const double* __restrict__ x, SegTable t, double* __restrict__ out, double* __restrict__ partial,
+               unsigned int* __restrict__ counter) {
+  const SegBlock c = chunk_of(t);
+  double acc[1] = {0.0};
+  for (int i = threadIdx.x; i < c.n; i += CG_THREADS) acc[0] += x[c.off + i];
+  double bs[1];
+  block_sum_k<double, 1>(acc, bs);
+  if (threadIdx.x == 0) partial[blockIdx.x] = bs[0];
+  if (!last_block(counter)) return;
+  seg_totals<1>(t, partial, [&](int q, const double* tot) { out[q] = tot[0] / (double)t.len[q]; });
+  if (threadIdx.x == 0) *counter = 0u;
+}
+__global__ void __launch_bounds__(CG_THREADS)
+seg_sub_kernel(double* __restrict__ x, SegTable t, const double* __restrict__ mean) {
+  const SegBlock c = chunk_of(t);
+  const double m = mean[c.s];
+  for (int i = threadIdx.x; i < c.n; i += CG_THREADS) x[c.off + i] -= m;
+}
+
+}  // namespace
+
+template <typename T>
+void seg_step_xr(T* x, T* r, const T* p, const T* Ap, const T* dinv, const SegTable& t, const CgScalars& sc,
+                 int maxit, double* partial, unsigned int* counter, cudaStream_t st) {
+  IMEX_COUNTED(seg_xr_kernel<T><<<t.nblk, CG_THREADS, 0, st>>>(x, r, p, Ap, dinv, t, sc, partial, counter, maxit));
+}
+template <typename T>
+void seg_step_p(T* p, T* r, const T* dinv, const SegTable& t, const CgScalars& sc, int restart, cudaStream_t st) {
+  IMEX_COUNTED(seg_p_kernel<T><<<t.nblk, CG_THREADS, 0, st>>>(p, r, dinv, t, sc, restart));
+}
+template <typename T>
+void seg_dot(const T* x, const T* y, const SegTable& t, double* out, double* partial, unsigned int* counter,
+             cudaStream_t st) {
+  IMEX_COUNTED(seg_dot_kernel<T><<<t.nblk, CG_THREADS, 0, st>>>(x, y, t, out, partial, counter));
+}
+template <typename T>
+void seg_pap(const T* p, const T* Ap, const SegTable& t, const CgScalars& sc, double* partial, unsigned int* counter,
+             cudaStream_t st) {
+  IMEX_COUNTED(seg_pap_kernel<T><<<t.nblk, CG_THREADS, 0, st>>>(p, Ap, t, sc, partial, counter));
+}
+template <typename T>
+void seg_init(const T* r, const T* dinv, const SegTable& t, const CgScalars& sc, double* partial,
+              unsigned int* counter, int reset, cudaStream_t st) {
+  IMEX_COUNTED(seg_init_kernel<T><<<t.nblk, CG_THREADS, 0, st>>>(r, dinv, t, sc, partial, counter, reset));
+}
+void seg_remove_mean(double* x, const SegTable& t, double* mean, double* partial, unsigned int* counter,
+                     cudaStream_t st) {
+  IMEX_COUNTED(seg_sum_kernel<<<t.nblk, CG_THREADS, 0, st>>>(x, t, mean, partial, counter));
+  IMEX_COUNTED(seg_sub_kernel<<<t.nblk, CG_THREADS, 0, st>>>(x, t, mean));
+}
+
+template void seg_step_xr<double>(double*, double*, const double*, const double*, const double*, const SegTable&,
+                                  const CgScalars&, int, double*, unsigned int*, cudaStream_t);
+template void seg_step_xr<float>(float*, float*, const float*, const float*, const float*, const SegTable&,
+                                 const CgScalars&, int, double*, unsigned int*, cudaStream_t);
+template void seg_step_p<double>(double*, double*, const double*, const SegTable&, const CgScalars&, int,
+                                 cudaStream_t);
+template void seg_step_p<float>(float*, float*, const float*, const SegTable&, const CgScalars&, int, cudaStream_t);
+template void seg_dot<double>(const double*, const double*, const SegTable&, double*, double*, unsigned int*,
+                              cudaStream_t);
+template void seg_dot<float>(const float*, const float*, const SegTable&, double*, double*, unsigned int*,
+                             cudaStream_t);
+template void seg_pap<double>(const double*, const double*, const SegTable&, const CgScalars&, double*,
+                              unsigned int*, cudaStream_t);
+template void seg_pap<float>(const float*, const float*, const SegTable&, const CgScalars&, double*, unsigned int*,
+                             cudaStream_t);
+template void seg_init<double>(const double*, const double*, const SegTable&, const CgScalars&, double*,
+                               unsigned int*, int, cudaStream_t);
+template void seg_init<float>(const float*, const float*, const SegTable&, const CgScalars&, double*,
+                              unsigned int*, int, cudaStream_t);
+
+}  // namespace imex

@@ -13,10 +13,74 @@
 // the neighbour's trace, normal derivative and viscosity in shared memory; the
 // symmetric face term is folded into the volume flux at the face nodes, so one
 // transposed derivative pass per direction produces the whole result.
+#include <type_traits>
+
 #include "common.cuh"
 #include "kernels.h"
 
 namespace imex {
+
+// Deterministic block sum for any block size: thread values through shared memory, then
+// warp 0 adds them in a fixed order.  Result valid in thread 0.
+__device__ __forceinline__ double block_sum_any(double v, double* red) {
+  red[threadIdx.x] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x < 32) {
+    for (int i = threadIdx.x; i < (int)blockDim.x; i += 32) s += red[i];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  }
+  __syncthreads();
+  return s;
+}
+
+// The same for a value of the vector type T: the per-thread values are staged in T and
+// only warp 0 converts (FP32 kernels keep FP64 arithmetic out of the per-thread path).
+template <typename T>
+__device__ __forceinline__ double block_sum_any_t(T v, double* red_storage) {
+  T* red = reinterpret_cast<T*>(red_storage);
+  red[threadIdx.x] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x < 32) {
+    T ls = T(0);
+    for (int i = threadIdx.x; i < (int)blockDim.x; i += 32) ls += red[i];
+    s = (double)ls;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  }
+  __syncthreads();
+  return s;
+}
+
+// Fused CG dot: each block has left its partial per system in a.dot_partial; the last block
+// to finish adds the partials in block order and writes a.dot_out, then resets the counter.
+template <typename T>
+__device__ void fused_dot_finish(const SipgArgs<T>& a, double* red) {
+  __shared__ int am_last;
+  if (threadIdx.x == 0) {
+    __threadfence();                       // this block's partials (written by thread 0) are visible
+    am_last = (atomicAdd(a.dot_counter, 1u) == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!am_last) return;
+  __threadfence();
+  for (int s = 0; s < a.nsys; ++s) {
+    double v = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) v += a.dot_partial[(size_t)s * gridDim.x + b];
+    v = block_sum_any(v, red);
+    if (threadIdx.x == 0) {
+      a.dot_out[s] = v;
+      if (a.cg_rz) {
+        const double al = v != 0.0 ? a.cg_rz[s] / v : 0.0;
+        const bool ok = isfinite(al);
+        a.cg_alpha[s] = ok ? al : 0.0;
+        a.cg_alpha_f[s] = ok ? (float)al : 0.f;
+        if (!ok && a.cg_done[s] == 0) a.cg_done[s] = 2;
+      }
+    }
+  }
+  if (threadIdx.x == 0) *a.dot_counter = 0u;
+}
 
 template <typename T, int D, int N>
 struct SipgShape {
@@ -67,7 +131,7 @@ sipg_apply_kernel(Geom g, SipgArgs<T> a) {
 
   T hinv2[D];
   T jac = T(1);
-  for (int k = 0; k < D; ++k) { hinv2[k] = T(2) / T(g.h[k]); jac *= T(g.h[k]) * T(0.5); }
+  for (int k = 0; k < D; ++k) { hinv2[k] = T(2) / geom_h<T>(g, k); jac *= geom_h<T>(g, k) * T(0.5); }
   T Wq = jac;
   for (int k = 0; k < D; ++k) Wq *= sw[id[k]];
 
@@ -162,7 +226,7 @@ sipg_apply_kernel(Geom g, SipgArgs<T> a) {
           const int nb = snb[le][fi];
           const int bc = g.bc[k];
           if (nb < 0 && bc != 1) continue;                 // Neumann: no face terms
-          T Wf = jac / (T(g.h[k]) * T(0.5));
+          T Wf = jac / (geom_h<T>(g, k) * T(0.5));
           int f = 0, mul = 1;
           for (int j = 0; j < D; ++j) {
             if (j == k) continue;
@@ -206,6 +270,716 @@ sipg_apply_kernel(Geom g, SipgArgs<T> a) {
   }
 }
 
+// ---------------------------------------------------------------------------------
+// 3D form: N^2 threads per element, each owning one z-column (i0, i1) of the element
+// tile in registers.  x / y derivatives read the tile from shared memory, z
+// derivatives stay in registers; the neighbours' traces and normal derivatives on
+// the four lateral faces are staged cooperatively (one face node per thread and
+// face), those of the two z-faces per thread in registers.
+// ---------------------------------------------------------------------------------
+template <int N>
+struct Sipg3Shape {
+  static constexpr int NN = N * N;
+  static constexpr int ND = N * N * N;
+  static constexpr int EPB = (NN >= 49) ? 4 : (NN >= 16 ? 256 / NN : 16);
+  static constexpr int THREADS = EPB * NN;
+};
+
+// face contribution at one node: the symmetric term enters the flux Qk, the
+// consistency and penalty terms the nodal value yface.  kind: 0 none, 1 interior, 2 Dirichlet
+template <typename T>
+__device__ __forceinline__ void sipg_face(int kind, T Wf, T n, T uo, T gk, T nuq, T un, T dn, T nun, T pen, T& Qk,
+                                          T& yface) {
+  if (kind == 1) {
+    const T jump = uo - un;
+    Qk += -Wf * T(0.5) * nuq * jump * n;
+    const T tau = pen * (nuq > nun ? nuq : nun);
+    yface += Wf * (-T(0.5) * n * (nuq * gk + nun * dn) + tau * jump);
+  } else if (kind == 2) {
+    const T jump = uo - un;
+    Qk += -Wf * nuq * jump * n;
+    yface += Wf * (-nuq * n * gk + T(2) * pen * nuq * jump);
+  }
+}
+
+template <typename T, int N>
+constexpr size_t sipg3_smem() {
+  using S = Sipg3Shape<N>;
+  return sizeof(T) * (size_t)(N * N + N + 3 * S::EPB * S::ND + 3 * S::EPB * 4 * S::NN);
+}
+
+template <typename T, int N, bool VARNU>
+__global__ void __launch_bounds__(Sipg3Shape<N>::THREADS)
+sipg3_apply_kernel(Geom g, SipgArgs<T> a) {
+  using S = Sipg3Shape<N>;
+  constexpr int NN = S::NN, ND = S::ND, EPB = S::EPB;
+  extern __shared__ unsigned char smem_raw[];
+  T* sD = reinterpret_cast<T*>(smem_raw);
+  T* sw = sD + N * N;
+  T (*su)[ND] = reinterpret_cast<T (*)[ND]>(sw + N);
+  T (*sQx)[ND] = su + EPB;
+  T (*sQy)[ND] = sQx + EPB;
+  T (*sfu)[4][NN] = reinterpret_cast<T (*)[4][NN]>(sQy + EPB);
+  T (*sfd)[4][NN] = sfu + EPB;
+  T (*sfn)[4][NN] = sfd + EPB;
+  __shared__ int snb[EPB][6];
+
+  const Tables<T>& tb = tab<T>(g);
+  for (int i = threadIdx.x; i < N * N; i += blockDim.x) sD[i] = tb.D[N][i];
+  for (int i = threadIdx.x; i < N; i += blockDim.x) sw[i] = tb.w[N][i];
+  const int le = threadIdx.x / NN;
+  const int t = threadIdx.x - le * NN;
+  const int i0 = t % N, i1 = t / N;
+  const int e = blockIdx.x * EPB + le;
+  const bool valid = e < g.ne;
+  int ec[3] = {0, 0, 0};
+  if (valid) elem_coords(g, e, ec);
+  if (valid && t < 6) snb[le][t] = neighbor(g, ec, t >> 1, (t & 1) ? 1 : -1);
+  __syncthreads();
+
+  const T hx = T(2) / geom_h<T>(g, 0), hy = T(2) / geom_h<T>(g, 1), hz = T(2) / geom_h<T>(g, 2);
+  const T jac = geom_h<T>(g, 0) * geom_h<T>(g, 1) * geom_h<T>(g, 2) * T(0.125);
+  const T jfx = geom_h<T>(g, 1) * geom_h<T>(g, 2) * T(0.25), jfy = geom_h<T>(g, 0) * geom_h<T>(g, 2) * T(0.25),
+          jfz = geom_h<T>(g, 0) * geom_h<T>(g, 1) * T(0.25);
+  const T penx = T(N * N) * T(0.5) * hx, peny = T(N * N) * T(0.5) * hy, penz = T(N * N) * T(0.5) * hz;
+  const size_t ebase = (size_t)e * ND;
+
+  // own viscosity column (constant viscosity: one register)
+  T nuc[VARNU ? N : 1];
+#pragma unroll
+  for (int k = 0; k < (VARNU ? N : 1); ++k) nuc[k] = (VARNU && valid) ? a.nu[ebase + k * NN + t] : a.nu0;
+  // face kinds: 0 none (Neumann), 1 interior, 2 Dirichlet
+  int kind[6];
+#pragma unroll
+  for (int f = 0; f < 6; ++f) {
+    const int nb = valid ? snb[le][f] : -1;
+    kind[f] = nb >= 0 ? 1 : (g.bc[f >> 1] == 1 ? 2 : 0);
+  }
+
+  for (int s = 0; s < a.nsys; ++s) {
+    const T* x = a.x + (size_t)s * a.sys_stride;
+    const T* gd = a.gdata ? a.gdata + (size_t)s * a.g_stride : nullptr;
+    T* y = a.y + (size_t)s * a.sys_stride;
+    T u[N];
+    if (s > 0) __syncthreads();
+    if (valid) {
+#pragma unroll
+      for (int k = 0; k < N; ++k) {
+        u[k] = x[ebase + k * NN + t];
+        su[le][k * NN + t] = u[k];
+      }
+      // lateral faces: face node t = (c0, c1) with c1 = t / N the z index
+      const int c0 = t % N, kk = t / N;
+#pragma unroll
+      for (int fi = 0; fi < 4; ++fi) {
+        const int dir = fi >> 1, side = fi & 1;
+        const int nb = snb[le][fi];
+        T tr = T(0), dv = T(0), nn = a.nu0;
+        if (nb >= 0) {
+          const int iface = side ? 0 : N - 1;                    // neighbour's index on the shared face
+          const size_t nbase = (size_t)nb * ND + kk * NN;
+          T acc = T(0);
+          if (dir == 0) {
+            const T* row = x + nbase + c0 * N;                  // neighbour row along x at (y = c0, z = kk)
+#pragma unroll
+            for (int j = 0; j < N; ++j) { const T v = row[j]; acc += sD[iface * N + j] * v; if (j == iface) tr = v; }
+            dv = acc * hx;
+            if (VARNU) nn = a.nu[nbase + c0 * N + iface];
+          } else {
+            const T* col = x + nbase + c0;                      // neighbour column along y at (x = c0, z = kk)
+#pragma unroll
+            for (int j = 0; j < N; ++j) { const T v = col[j * N]; acc += sD[iface * N + j] * v; if (j == iface) tr = v; }
+            dv = acc * hy;
+            if (VARNU) nn = a.nu[nbase + iface * N + c0];
+          }
+        } else if (g.bc[dir] == 1) {
+          const int own = side ? N - 1 : 0;
+          const size_t on = ebase + kk * NN + (dir == 0 ? c0 * N + own : own * N + c0);
+          tr = gd ? gd[on] : T(0);
+          if (VARNU) nn = a.nu[on];
+        }
+        sfu[le][fi][t] = tr;
+        sfd[le][fi][t] = dv;
+        sfn[le][fi][t] = nn;
+      }
+    }
+    // z-faces: the neighbour columns through this thread's (i0, i1)
+    T zu[2] = {T(0), T(0)}, zd[2] = {T(0), T(0)}, zn[2] = {a.nu0, a.nu0};
+    if (valid) {
+#pragma unroll
+      for (int side = 0; side < 2; ++side) {
+        const int nb = snb[le][4 + side];
+        if (nb >= 0) {
+          const int iface = side ? 0 : N - 1;
+          const T* col = x + (size_t)nb * ND + t;
+          T acc = T(0);
+#pragma unroll
+          for (int j = 0; j < N; ++j) { const T v = col[j * NN]; acc += sD[iface * N + j] * v; if (j == iface) zu[side] = v; }
+          zd[side] = acc * hz;
+          if (VARNU) zn[side] = a.nu[(size_t)nb * ND + iface * NN + t];
+        } else if (g.bc[2] == 1) {
+          const int own = side ? N - 1 : 0;
+          zu[side] = gd ? gd[ebase + own * NN + t] : T(0);
+          zn[side] = nuc[VARNU ? own : 0];
+        }
+      }
+    }
+    __syncthreads();
+    T Qz[N], yf[N];
+    if (valid) {
+      const T wxy = sw[i0] * sw[i1];
+#pragma unroll
+      for (int k = 0; k < N; ++k) {
+        const T* plane = &su[le][k * NN];
+        T gx = T(0), gy = T(0), gz = T(0);
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+          gx += sD[i0 * N + j] * plane[i1 * N + j];
+          gy += sD[i1 * N + j] * plane[j * N + i0];
+          gz += sD[k * N + j] * u[j];
+        }
+        gx *= hx; gy *= hy; gz *= hz;
+        const T nuq = nuc[VARNU ? k : 0];
+        const T W = jac * wxy * sw[k];
+        T Qx = W * nuq * gx, Qy = W * nuq * gy, Qzk = W * nuq * gz;
+        T yface = T(0);
+        const int fxy0 = i1 + N * k, fxy1 = i0 + N * k;
+        if (i0 == 0) sipg_face<T>(kind[0], jfx * sw[i1] * sw[k], T(-1), u[k], gx, nuq, sfu[le][0][fxy0],
+                                  sfd[le][0][fxy0], sfn[le][0][fxy0], penx, Qx, yface);
+        if (i0 == N - 1) sipg_face<T>(kind[1], jfx * sw[i1] * sw[k], T(1), u[k], gx, nuq, sfu[le][1][fxy0],
+                                      sfd[le][1][fxy0], sfn[le][1][fxy0], penx, Qx, yface);
+        if (i1 == 0) sipg_face<T>(kind[2], jfy * sw[i0] * sw[k], T(-1), u[k], gy, nuq, sfu[le][2][fxy1],
+                                  sfd[le][2][fxy1], sfn[le][2][fxy1], peny, Qy, yface);
+        if (i1 == N - 1) sipg_face<T>(kind[3], jfy * sw[i0] * sw[k], T(1), u[k], gy, nuq, sfu[le][3][fxy1],
+                                      sfd[le][3][fxy1], sfn[le][3][fxy1], peny, Qy, yface);
+        if (k == 0) sipg_face<T>(kind[4], jfz * wxy, T(-1), u[k], gz, nuq, zu[0], zd[0], zn[0], penz, Qzk, yface);
+        if (k == N - 1) sipg_face<T>(kind[5], jfz * wxy, T(1), u[k], gz, nuq, zu[1], zd[1], zn[1], penz, Qzk, yface);
+        sQx[le][k * NN + t] = Qx;
+        sQy[le][k * NN + t] = Qy;
+        Qz[k] = Qzk;
+        yf[k] = yface;
+      }
+    }
+    __syncthreads();
+    if (valid) {
+      const T wxy = sw[i0] * sw[i1];
+#pragma unroll
+      for (int k = 0; k < N; ++k) {
+        const T* px = &sQx[le][k * NN];
+        const T* py = &sQy[le][k * NN];
+        T ax = T(0), ay = T(0), az = T(0);
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+          ax += sD[j * N + i0] * px[i1 * N + j];
+          ay += sD[j * N + i1] * py[j * N + i0];
+          az += sD[j * N + k] * Qz[j];
+        }
+        const T W = jac * wxy * sw[k];
+        const T yv = yf[k] + hx * ax + hy * ay + hz * az;
+        T out = a.alpha * W * u[k] + a.beta * yv;
+        if (a.minv) out /= W;
+        y[ebase + k * NN + t] = out;
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------
+// Constant-viscosity fast path.  With constant nu the operator is
+//   y = alpha M u + beta nu0 sum_k W_perp,k (A_k u_line + sum_sides C_k (trace, dn)_nb)
+// with the precomputed line operators of LineOps: per node one N-term row of A_k per
+// direction plus two or four neighbour terms, a single synchronisation per element.
+// 3D: N^2 threads per element, each owning a z-column in registers.
+// ---------------------------------------------------------------------------------
+template <int N>
+struct Sipg3cShape {
+  static constexpr int NN = N * N;
+  static constexpr int ND = N * N * N;
+  static constexpr int EPB = (NN >= 49) ? 4 : (NN >= 16 ? 256 / NN : 16);
+  static constexpr int THREADS = EPB * NN;
+};
+
+template <typename T, int N>
+constexpr size_t sipg3c_smem() {
+  using S = Sipg3cShape<N>;
+  // A[3][9][N*N] + C[3][2][3][2][N] + dn[3][2][N] + Wt[3][N] + tile + 4 lateral faces x (trace, dn)
+  return sizeof(T) * (size_t)(27 * N * N + 36 * N + 6 * N + 3 * N + S::EPB * S::ND + S::EPB * 8 * S::NN);
+}
+
+template <typename T, int N>
+__global__ void __launch_bounds__(Sipg3cShape<N>::THREADS)
+sipg3c_apply_kernel(Geom g, SipgArgs<T> a) {
+  using S = Sipg3cShape<N>;
+  constexpr int NN = S::NN, ND = S::ND, EPB = S::EPB;
+  extern __shared__ unsigned char smem_raw[];
+  T* sA = reinterpret_cast<T*>(smem_raw);        // [3][9][NN]
+  T* sC = sA + 27 * NN;                          // [3][2][3][2][N]
+  T* sdn = sC + 36 * N;                          // [3][2][N]
+  T* sWt = sdn + 6 * N;                          // [3][N]
+  T (*su)[ND] = reinterpret_cast<T (*)[ND]>(sWt + 3 * N);
+  T (*sf)[8][NN] = reinterpret_cast<T (*)[8][NN]>(su + EPB);   // [face 0..3][trace | dn]
+  __shared__ int snb[EPB][6];
+  const LineOps<T>& op = *a.ops;
+  for (int i = threadIdx.x; i < 27 * NN; i += blockDim.x) {
+    const int kv = i / NN, r = i % NN;
+    sA[i] = op.A[kv / 9][kv % 9][r];
+  }
+  for (int i = threadIdx.x; i < 36 * N; i += blockDim.x) {
+    const int q = i / N, r = i % N;   // q = ((k*2 + side)*3 + kind)*2 + which
+    sC[i] = op.C[q / 12][(q / 6) % 2][(q / 2) % 3][q % 2][r];
+  }
+  for (int i = threadIdx.x; i < 6 * N; i += blockDim.x) sdn[i] = op.dn[i / (2 * N)][(i / N) % 2][i % N];
+  for (int i = threadIdx.x; i < 3 * N; i += blockDim.x) sWt[i] = op.Wt[i / N][i % N];
+  const int le = threadIdx.x / NN;
+  const int t = threadIdx.x - le * NN;
+  const int i0 = t % N, i1 = t / N;
+  const int e = blockIdx.x * EPB + le;
+  const bool valid = e < g.ne;
+  int ec[3] = {0, 0, 0};
+  if (valid) elem_coords(g, e, ec);
+  if (valid && t < 6) snb[le][t] = neighbor(g, ec, t >> 1, (t & 1) ? 1 : -1);
+  __syncthreads();
+  int kind[6];
+#pragma unroll
+  for (int f = 0; f < 6; ++f) {
+    const int nb = valid ? snb[le][f] : -1;
+    kind[f] = nb >= 0 ? 1 : (g.bc[f >> 1] == 1 ? 2 : 0);
+  }
+  const size_t ebase = (size_t)e * ND;
+  const T scale = a.beta * a.nu0;
+  __shared__ double red[S::THREADS];
+  for (int s = 0; s < a.nsys; ++s) {
+    const T* x = a.x + (size_t)s * a.sys_stride;
+    const T* gd = a.gdata ? a.gdata + (size_t)s * a.g_stride : nullptr;
+    T* y = a.y + (size_t)s * a.sys_stride;
+    if (s > 0) __syncthreads();
+    T u[N];
+    T dacc = T(0);
+    T zt[2] = {T(0), T(0)}, zd[2] = {T(0), T(0)};
+    if (valid) {
+#pragma unroll
+      for (int k = 0; k < N; ++k) {
+        u[k] = x[ebase + k * NN + t];
+        su[le][k * NN + t] = u[k];
+      }
+      // lateral faces: face node t = (c0, kk), kk the z index
+      const int c0 = t % N, kk = t / N;
+#pragma unroll
+      for (int fi = 0; fi < 4; ++fi) {
+        const int dir = fi >> 1, side = fi & 1;
+        const int nb = snb[le][fi];
+        T tr = T(0), dv = T(0);
+        if (nb >= 0) {
+          const int iface = side ? 0 : N - 1;
+          const T* dr = sdn + (dir * 2 + side) * N;
+          const size_t nbase = (size_t)nb * ND + kk * NN;
+          if (dir == 0) {
+            const T* row = x + nbase + c0 * N;
+#pragma unroll
+            for (int j = 0; j < N; ++j) { const T v = row[j]; dv += dr[j] * v; if (j == iface) tr = v; }
+          } else {
+            const T* col = x + nbase + c0;
+#pragma unroll
+            for (int j = 0; j < N; ++j) { const T v = col[j * N]; dv += dr[j] * v; if (j == iface) tr = v; }
+          }
+        } else if (kind[fi] == 2 && gd) {
+          const int own = side ? N - 1 : 0;
+          tr = gd[ebase + kk * NN + (dir == 0 ? c0 * N + own : own * N + c0)];
+        }
+        sf[le][2 * fi][t] = tr;
+        sf[le][2 * fi + 1][t] = dv;
+      }
+#pragma unroll
+      for (int side = 0; side < 2; ++side) {
+        const int nb = snb[le][4 + side];
+        if (nb >= 0) {
+          const int iface = side ? 0 : N - 1;
+          const T* dr = sdn + (2 * 2 + side) * N;
+          const T* col = x + (size_t)nb * ND + t;
+#pragma unroll
+          for (int j = 0; j < N; ++j) { const T v = col[j * NN]; zd[side] += dr[j] * v; if (j == iface) zt[side] = v; }
+        } else if (kind[4 + side] == 2 && gd) {
+          zt[side] = gd[ebase + (side ? N - 1 : 0) * NN + t];
+        }
+      }
+    }
+    __syncthreads();
+    if (valid) {
+      const T* Ax = sA + (0 * 9 + 3 * kind[0] + kind[1]) * NN + i0 * N;
+      const T* Ay = sA + (1 * 9 + 3 * kind[2] + kind[3]) * NN + i1 * N;
+      const T* Az = sA + (2 * 9 + 3 * kind[4] + kind[5]) * NN;
+      // neighbour coefficients of this thread's rows: C[k][side][kind][which][i]
+      const T cxl0 = sC[((0 * 2 + 0) * 3 + kind[0]) * 2 * N + i0], cxl1 = sC[(((0 * 2 + 0) * 3 + kind[0]) * 2 + 1) * N + i0];
+      const T cxr0 = sC[((0 * 2 + 1) * 3 + kind[1]) * 2 * N + i0], cxr1 = sC[(((0 * 2 + 1) * 3 + kind[1]) * 2 + 1) * N + i0];
+      const T cyl0 = sC[((1 * 2 + 0) * 3 + kind[2]) * 2 * N + i1], cyl1 = sC[(((1 * 2 + 0) * 3 + kind[2]) * 2 + 1) * N + i1];
+      const T cyr0 = sC[((1 * 2 + 1) * 3 + kind[3]) * 2 * N + i1], cyr1 = sC[(((1 * 2 + 1) * 3 + kind[3]) * 2 + 1) * N + i1];
+      const T* czl = sC + ((2 * 2 + 0) * 3 + kind[4]) * 2 * N;
+      const T* czr = sC + ((2 * 2 + 1) * 3 + kind[5]) * 2 * N;
+      const T wx = sWt[i0], wy = sWt[N + i1];
+#pragma unroll
+      for (int k = 0; k < N; ++k) {
+        const T* plane = &su[le][k * NN];
+        T yx = T(0), yy = T(0), yz = T(0);
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+          yx += Ax[j] * plane[i1 * N + j];
+          yy += Ay[j] * plane[j * N + i0];
+          yz += Az[k * N + j] * u[j];
+        }
+        const int fx = i1 + N * k, fy = i0 + N * k;
+        yx += cxl0 * sf[le][0][fx] + cxl1 * sf[le][1][fx] + cxr0 * sf[le][2][fx] + cxr1 * sf[le][3][fx];
+        yy += cyl0 * sf[le][4][fy] + cyl1 * sf[le][5][fy] + cyr0 * sf[le][6][fy] + cyr1 * sf[le][7][fy];
+        yz += czl[k] * zt[0] + czl[N + k] * zd[0] + czr[k] * zt[1] + czr[N + k] * zd[1];
+        const T wz = sWt[2 * N + k];
+        const T W = wx * wy * wz;
+        const T yv = wy * wz * yx + wx * wz * yy + wx * wy * yz;
+        T out = a.alpha * W * u[k] + scale * yv;
+        if (a.minv) out /= W;
+        y[ebase + k * NN + t] = out;
+        dacc += u[k] * out;
+      }
+    }
+    if (a.dot_out) {
+      const double bs = block_sum_any_t<T>(dacc, red);
+      if (threadIdx.x == 0) a.dot_partial[(size_t)s * gridDim.x + blockIdx.x] = bs;
+    }
+  }
+  if (a.dot_out) fused_dot_finish(a, red);
+}
+
+// 2D: one thread per node, EPB elements per block.
+template <int N>
+struct Sipg2cShape {
+  static constexpr int NN = N * N;
+  static constexpr int EPB = (256 / NN) > 0 ? 256 / NN : 1;
+  static constexpr int THREADS = EPB * NN;
+};
+
+template <typename T, int N>
+constexpr size_t sipg2c_smem() {
+  using S = Sipg2cShape<N>;
+  return sizeof(T) * (size_t)(18 * N * N + 24 * N + 4 * N + 2 * N + S::EPB * S::NN + S::EPB * 8 * N);
+}
+
+template <typename T, int N>
+__global__ void __launch_bounds__(Sipg2cShape<N>::THREADS)
+sipg2c_apply_kernel(Geom g, SipgArgs<T> a) {
+  using S = Sipg2cShape<N>;
+  constexpr int NN = S::NN, EPB = S::EPB;
+  extern __shared__ unsigned char smem_raw[];
+  T* sA = reinterpret_cast<T*>(smem_raw);        // [2][9][NN]
+  T* sC = sA + 18 * NN;                          // [2][2][3][2][N]
+  T* sdn = sC + 24 * N;                          // [2][2][N]
+  T* sWt = sdn + 4 * N;                          // [2][N]
+  T (*su)[NN] = reinterpret_cast<T (*)[NN]>(sWt + 2 * N);
+  T (*sf)[8][N] = reinterpret_cast<T (*)[8][N]>(su + EPB);
+  __shared__ int snb[EPB][4];
+  const LineOps<T>& op = *a.ops;
+  for (int i = threadIdx.x; i < 18 * NN; i += blockDim.x) {
+    const int kv = i / NN, r = i % NN;
+    sA[i] = op.A[kv / 9][kv % 9][r];
+  }
+  for (int i = threadIdx.x; i < 24 * N; i += blockDim.x) {
+    const int q = i / N, r = i % N;
+    sC[i] = op.C[q / 12][(q / 6) % 2][(q / 2) % 3][q % 2][r];
+  }
+  for (int i = threadIdx.x; i < 4 * N; i += blockDim.x) sdn[i] = op.dn[i / (2 * N)][(i / N) % 2][i % N];
+  for (int i = threadIdx.x; i < 2 * N; i += blockDim.x) sWt[i] = op.Wt[i / N][i % N];
+  const int le = threadIdx.x / NN;
+  const int t = threadIdx.x - le * NN;
+  const int i0 = t % N, i1 = t / N;
+  const int e = blockIdx.x * EPB + le;
+  const bool valid = e < g.ne;
+  int ec[3] = {0, 0, 0};
+  if (valid) elem_coords(g, e, ec);
+  if (valid && t < 4) snb[le][t] = neighbor(g, ec, t >> 1, (t & 1) ? 1 : -1);
+  __syncthreads();
+  int kind[4];
+#pragma unroll
+  for (int f = 0; f < 4; ++f) {
+    const int nb = valid ? snb[le][f] : -1;
+    kind[f] = nb >= 0 ? 1 : (g.bc[f >> 1] == 1 ? 2 : 0);
+  }
+  const size_t ebase = (size_t)e * NN;
+  const T scale = a.beta * a.nu0;
+  __shared__ double red[S::THREADS];
+  for (int s = 0; s < a.nsys; ++s) {
+    const T* x = a.x + (size_t)s * a.sys_stride;
+    const T* gd = a.gdata ? a.gdata + (size_t)s * a.g_stride : nullptr;
+    T* y = a.y + (size_t)s * a.sys_stride;
+    if (s > 0) __syncthreads();
+    T uo = T(0);
+    T dacc = T(0);
+    if (valid) {
+      uo = x[ebase + t];
+      su[le][t] = uo;
+      // face data: face fi = q / N, face node c = q % N for q = t, t + N^2, ... < 4N
+      for (int q = t; q < 4 * N; q += NN) {
+        const int fi = q / N, c = q % N, dir = fi >> 1, side = fi & 1;
+        const int nb = snb[le][fi];
+        T tr = T(0), dv = T(0);
+        if (nb >= 0) {
+          const int iface = side ? 0 : N - 1;
+          const T* dr = sdn + (dir * 2 + side) * N;
+          const T* line = x + (size_t)nb * NN + (dir == 0 ? c * N : c);
+          const int stride = dir == 0 ? 1 : N;
+#pragma unroll
+          for (int j = 0; j < N; ++j) { const T v = line[j * stride]; dv += dr[j] * v; if (j == iface) tr = v; }
+        } else if (kind[fi] == 2 && gd) {
+          const int own = side ? N - 1 : 0;
+          tr = gd[ebase + (dir == 0 ? c * N + own : own * N + c)];
+        }
+        sf[le][2 * fi][c] = tr;
+        sf[le][2 * fi + 1][c] = dv;
+      }
+    }
+    __syncthreads();
+    if (valid) {
+      const T* Ax = sA + (0 * 9 + 3 * kind[0] + kind[1]) * NN + i0 * N;
+      const T* Ay = sA + (1 * 9 + 3 * kind[2] + kind[3]) * NN + i1 * N;
+      T yx = T(0), yy = T(0);
+#pragma unroll
+      for (int j = 0; j < N; ++j) {
+        yx += Ax[j] * su[le][i1 * N + j];
+        yy += Ay[j] * su[le][j * N + i0];
+      }
+      yx += sC[((0 * 2 + 0) * 3 + kind[0]) * 2 * N + i0] * sf[le][0][i1] +
+            sC[(((0 * 2 + 0) * 3 + kind[0]) * 2 + 1) * N + i0] * sf[le][1][i1] +
+            sC[((0 * 2 + 1) * 3 + kind[1]) * 2 * N + i0] * sf[le][2][i1] +
+            sC[(((0 * 2 + 1) * 3 + kind[1]) * 2 + 1) * N + i0] * sf[le][3][i1];
+      yy += sC[((1 * 2 + 0) * 3 + kind[2]) * 2 * N + i1] * sf[le][4][i0] +
+            sC[(((1 * 2 + 0) * 3 + kind[2]) * 2 + 1) * N + i1] * sf[le][5][i0] +
+            sC[((1 * 2 + 1) * 3 + kind[3]) * 2 * N + i1] * sf[le][6][i0] +
+            sC[(((1 * 2 + 1) * 3 + kind[3]) * 2 + 1) * N + i1] * sf[le][7][i0];
+      const T wx = sWt[i0], wy = sWt[N + i1];
+      const T W = wx * wy;
+      T out = a.alpha * W * uo + scale * (wy * yx + wx * yy);
+      if (a.minv) out /= W;
+      y[ebase + t] = out;
+      dacc = uo * out;
+    }
+    if (a.dot_out) {
+      const double bs = block_sum_any_t<T>(dacc, red);
+      if (threadIdx.x == 0) a.dot_partial[(size_t)s * gridDim.x + blockIdx.x] = bs;
+    }
+  }
+  if (a.dot_out) fused_dot_finish(a, red);
+}
+
+// ---------------------------------------------------------------------------------
+// Periodic constant-viscosity path (every face interior): the unit-size line operator of
+// the element (interior on both ends), its neighbour coefficients and the derivative rows
+// live in constant memory.  For element size h the line operator is
+//   (1/h) [A1 u + C_tr1 trace_nb + C_dn1 (dn1 . u_nb)]
+// with every unit-size quantity (A, the trace coefficients and the derivative rows scale
+// as 1/h, the derivative coefficients are dimensionless), and the weights scale as h/2.
+// The z-direction terms use compile-time offsets into constant memory, the x rows are read
+// from the shared tile with vector loads, the y columns with scalar loads.
+// ---------------------------------------------------------------------------------
+template <typename T>
+struct ConstLine {
+  T A[IMEX_MAXN * IMEX_MAXN];
+  T ctrL[IMEX_MAXN], cdnL[IMEX_MAXN], ctrR[IMEX_MAXN], cdnR[IMEX_MAXN];
+  T dnL[IMEX_MAXN], dnR[IMEX_MAXN];
+  T w[IMEX_MAXN];
+};
+__constant__ ConstLine<float> c_line32[IMEX_MAXN + 1];
+__constant__ ConstLine<double> c_line64[IMEX_MAXN + 1];
+template <typename T> __device__ __forceinline__ const ConstLine<T>& cline(int N);
+template <> __device__ __forceinline__ const ConstLine<float>& cline<float>(int N) { return c_line32[N]; }
+template <> __device__ __forceinline__ const ConstLine<double>& cline<double>(int N) { return c_line64[N]; }
+
+template <typename T, int N>
+struct Sipg3pShape {
+  static constexpr int NN = N * N;
+  static constexpr int VEC = 16 / sizeof(T);                       // elements per 16-byte load
+  static constexpr int NP = ((N + VEC - 1) / VEC) * VEC;           // padded row length
+  static constexpr int TILE = N * N * NP;
+  static constexpr int EPB = (NN >= 49) ? 4 : (NN >= 16 ? 256 / NN : 16);
+  static constexpr int THREADS = EPB * NN;
+};
+
+template <typename T, int N>
+constexpr size_t sipg3p_smem() {
+  using S = Sipg3pShape<T, N>;
+  return sizeof(T) * (size_t)(S::EPB * S::TILE + S::EPB * 8 * S::NN);
+}
+
+template <typename T, int N>
+__global__ void __launch_bounds__(Sipg3pShape<T, N>::THREADS, (sizeof(T) == 4 && N <= 8) ? 3 : 1)
+sipg3p_apply_kernel(Geom g, SipgArgs<T> a) {
+  using S = Sipg3pShape<T, N>;
+  constexpr int NN = S::NN, ND = N * N * N, EPB = S::EPB, NP = S::NP, TILE = S::TILE, VEC = S::VEC;
+  using V = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* tile = reinterpret_cast<T*>(smem_raw);                       // [EPB][z][y][NP]
+  T (*sf)[8][NN] = reinterpret_cast<T (*)[8][NN]>(tile + EPB * TILE);
+  const ConstLine<T>& L = cline<T>(N);
+  const int le = threadIdx.x / NN;
+  const int t = threadIdx.x - le * NN;
+  const int i0 = t % N, i1 = t / N;
+  const int e = blockIdx.x * EPB + le;
+  const bool valid = e < g.ne;
+  int ec[3] = {0, 0, 0};
+  int nb[6] = {0, 0, 0, 0, 0, 0};
+  if (valid) {
+    elem_coords(g, e, ec);
+#pragma unroll
+    for (int f = 0; f < 6; ++f) nb[f] = neighbor(g, ec, f >> 1, (f & 1) ? 1 : -1);
+  }
+  const T ihx = T(1) / geom_h<T>(g, 0), ihy = T(1) / geom_h<T>(g, 1), ihz = T(1) / geom_h<T>(g, 2);
+  const T hx2 = T(0.5) * geom_h<T>(g, 0), hy2 = T(0.5) * geom_h<T>(g, 1), hz2 = T(0.5) * geom_h<T>(g, 2);
+  // this thread's rows of the x and y line operators and neighbour coefficients
+  T ax[N], ay[N];
+#pragma unroll
+  for (int j = 0; j < N; ++j) { ax[j] = L.A[i0 * N + j]; ay[j] = L.A[i1 * N + j]; }
+  const T cxl0 = L.ctrL[i0], cxl1 = L.cdnL[i0], cxr0 = L.ctrR[i0], cxr1 = L.cdnR[i0];
+  const T cyl0 = L.ctrL[i1], cyl1 = L.cdnL[i1], cyr0 = L.ctrR[i1], cyr1 = L.cdnR[i1];
+  const T wx = hx2 * L.w[i0], wy = hy2 * L.w[i1];
+  const size_t ebase = (size_t)e * ND;
+  const T scale = a.beta * a.nu0;
+  T* mytile = tile + le * TILE;
+  __shared__ double red[S::THREADS];
+  for (int s = 0; s < a.nsys; ++s) {
+    const T* x = a.x + (size_t)s * a.sys_stride;
+    T* y = a.y + (size_t)s * a.sys_stride;
+    if (s > 0) __syncthreads();
+    T u[N];
+    T zt0 = T(0), zd0 = T(0), zt1 = T(0), zd1 = T(0);
+    T dacc = T(0);
+    if (valid) {
+#pragma unroll
+      for (int k = 0; k < N; ++k) {
+        u[k] = x[ebase + k * NN + t];
+        mytile[(k * N + i1) * NP + i0] = u[k];
+      }
+      const int c0 = t % N, kk = t / N;
+      {  // x-neighbours: rows along x at (y = c0, z = kk)
+        const T* rl = x + (size_t)nb[0] * ND + kk * NN + c0 * N;
+        const T* rr = x + (size_t)nb[1] * ND + kk * NN + c0 * N;
+        T tl = T(0), dl = T(0), tr = T(0), dr = T(0);
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+          const T vl = rl[j], vr = rr[j];
+          dl += L.dnL[j] * vl;
+          dr += L.dnR[j] * vr;
+          if (j == N - 1) tl = vl;
+          if (j == 0) tr = vr;
+        }
+        sf[le][0][t] = tl; sf[le][1][t] = dl; sf[le][2][t] = tr; sf[le][3][t] = dr;
+      }
+      {  // y-neighbours: columns along y at (x = c0, z = kk)
+        const T* cl = x + (size_t)nb[2] * ND + kk * NN + c0;
+        const T* cr = x + (size_t)nb[3] * ND + kk * NN + c0;
+        T tl = T(0), dl = T(0), tr = T(0), dr = T(0);
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+          const T vl = cl[j * N], vr = cr[j * N];
+          dl += L.dnL[j] * vl;
+          dr += L.dnR[j] * vr;
+          if (j == N - 1) tl = vl;
+          if (j == 0) tr = vr;
+        }
+        sf[le][4][t] = tl; sf[le][5][t] = dl; sf[le][6][t] = tr; sf[le][7][t] = dr;
+      }
+      {  // z-neighbours: columns along z through (i0, i1)
+        const T* cl = x + (size_t)nb[4] * ND + t;
+        const T* cr = x + (size_t)nb[5] * ND + t;
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+          const T vl = cl[j * NN], vr = cr[j * NN];
+          zd0 += L.dnL[j] * vl;
+          zd1 += L.dnR[j] * vr;
+          if (j == N - 1) zt0 = vl;
+          if (j == 0) zt1 = vr;
+        }
+      }
+    }
+    __syncthreads();
+    if (valid) {
+#pragma unroll
+      for (int k = 0; k < N; ++k) {
+        // x: the padded row (y = i1, z = k) by 16-byte loads
+        T row[NP];
+        const V* rv = reinterpret_cast<const V*>(mytile + (k * N + i1) * NP);
+#pragma unroll
+        for (int q = 0; q < NP / VEC; ++q) {
+          const V v = rv[q];
+          if (VEC == 4) {
+            const float4 f = *reinterpret_cast<const float4*>(&v);
+            reinterpret_cast<float*>(row)[4 * q + 0] = f.x;
+            reinterpret_cast<float*>(row)[4 * q + 1] = f.y;
+            reinterpret_cast<float*>(row)[4 * q + 2] = f.z;
+            reinterpret_cast<float*>(row)[4 * q + 3] = f.w;
+          } else {
+            const double2 f = *reinterpret_cast<const double2*>(&v);
+            reinterpret_cast<double*>(row)[2 * q + 0] = f.x;
+            reinterpret_cast<double*>(row)[2 * q + 1] = f.y;
+          }
+        }
+        T yx = T(0), yy = T(0), yz = T(0);
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+          yx += ax[j] * row[j];
+          yy += ay[j] * mytile[(k * N + j) * NP + i0];
+          yz += L.A[k * N + j] * u[j];
+        }
+        const int f = i1 + N * k, fy = i0 + N * k;
+        yx += cxl0 * sf[le][0][f] + cxl1 * sf[le][1][f] + cxr0 * sf[le][2][f] + cxr1 * sf[le][3][f];
+        yy += cyl0 * sf[le][4][fy] + cyl1 * sf[le][5][fy] + cyr0 * sf[le][6][fy] + cyr1 * sf[le][7][fy];
+        yz += L.ctrL[k] * zt0 + L.cdnL[k] * zd0 + L.ctrR[k] * zt1 + L.cdnR[k] * zd1;
+        const T wz = hz2 * L.w[k];
+        const T W = wx * wy * wz;
+        const T yv = wy * wz * ihx * yx + wx * wz * ihy * yy + wx * wy * ihz * yz;
+        T out = a.alpha * W * u[k] + scale * yv;
+        if (a.minv) out /= W;
+        y[ebase + k * NN + t] = out;
+        dacc += u[k] * out;
+      }
+    }
+    if (a.dot_out) {
+      const double bs = block_sum_any_t<T>(dacc, red);
+      if (threadIdx.x == 0) a.dot_partial[(size_t)s * gridDim.x + blockIdx.x] = bs;
+    }
+  }
+  if (a.dot_out) fused_dot_finish(a, red);
+}
+
+// fill the constant-memory line operators once per device
+static bool g_cline_ready[64] = {false};
+void init_const_lines(const Tables<double>& t) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64 || g_cline_ready[dev]) return;
+  static ConstLine<double> h64[IMEX_MAXN + 1];
+  static ConstLine<float> h32[IMEX_MAXN + 1];
+  LineOps<double>* o = new LineOps<double>();
+  LineOps<float>* of = new LineOps<float>();
+  const double one[3] = {1.0, 1.0, 1.0};
+  for (int N = 2; N <= IMEX_MAXN; ++N) {
+    build_line_ops(t, N, one, 1, o, of);
+    ConstLine<double>& c = h64[N];
+    for (int i = 0; i < N * N; ++i) c.A[i] = o->A[0][4][i];
+    for (int i = 0; i < N; ++i) {
+      c.ctrL[i] = o->C[0][0][1][0][i];
+      c.cdnL[i] = o->C[0][0][1][1][i];
+      c.ctrR[i] = o->C[0][1][1][0][i];
+      c.cdnR[i] = o->C[0][1][1][1][i];
+      c.dnL[i] = o->dn[0][0][i];
+      c.dnR[i] = o->dn[0][1][i];
+      c.w[i] = t.w[N][i];
+    }
+    const double* src = reinterpret_cast<const double*>(&c);
+    float* dst = reinterpret_cast<float*>(&h32[N]);
+    for (size_t i = 0; i < sizeof(ConstLine<double>) / sizeof(double); ++i) dst[i] = (float)src[i];
+  }
+  delete o;
+  delete of;
+  if (cudaMemcpyToSymbol(c_line64, h64, sizeof(h64)) == cudaSuccess &&
+      cudaMemcpyToSymbol(c_line32, h32, sizeof(h32)) == cudaSuccess)
+    g_cline_ready[dev] = true;
+}
+
 // Diagonal of alpha M + beta A (Jacobi preconditioner).
 template <typename T, int D, int N>
 __global__ void __launch_bounds__(SipgShape<T, D, N>::THREADS)
@@ -234,7 +1008,7 @@ sipg_diag_kernel(Geom g, SipgArgs<T> a) {
   id[2] = (D > 2) ? node / (N * N) : 0;
   T hinv2[D];
   T jac = T(1);
-  for (int k = 0; k < D; ++k) { hinv2[k] = T(2) / T(g.h[k]); jac *= T(g.h[k]) * T(0.5); }
+  for (int k = 0; k < D; ++k) { hinv2[k] = T(2) / geom_h<T>(g, k); jac *= geom_h<T>(g, k) * T(0.5); }
   T Wq = jac;
   for (int k = 0; k < D; ++k) Wq *= sw[id[k]];
   const T nuq = snu[le][node];
@@ -256,7 +1030,7 @@ sipg_diag_kernel(Geom g, SipgArgs<T> a) {
       if (id[k] != (side ? N - 1 : 0)) continue;
       const int nb = neighbor(g, ec, k, side ? 1 : -1);
       if (nb < 0 && g.bc[k] != 1) continue;
-      T Wf = jac / (T(g.h[k]) * T(0.5));
+      T Wf = jac / (geom_h<T>(g, k) * T(0.5));
       for (int j = 0; j < D; ++j) if (j != k) Wf *= sw[id[j]];
       const T n = side ? T(1) : T(-1);
       const T dself = n * sD[id[k] * N + id[k]] * hinv2[k];   // d(e_j)/dn at its own face node
@@ -277,9 +1051,44 @@ sipg_diag_kernel(Geom g, SipgArgs<T> a) {
 
 template <typename T, int D, int N>
 static void launch_apply(const Geom& g, const SipgArgs<T>& a, cudaStream_t st) {
+  if (D == 2 && !a.nu && a.ops) {
+    using C = Sipg2cShape<N>;
+    constexpr size_t sm = sipg2c_smem<T, N>();
+    cudaFuncSetAttribute(sipg2c_apply_kernel<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    IMEX_COUNTED(sipg2c_apply_kernel<T, N><<<(g.ne + C::EPB - 1) / C::EPB, C::THREADS, sm, st>>>(g, a));
+    return;
+  }
   using S = SipgShape<T, D, N>;
   int blocks = (g.ne + S::EPB - 1) / S::EPB;
   IMEX_COUNTED(sipg_apply_kernel<T, D, N><<<blocks, S::THREADS, 0, st>>>(g, a));
+}
+
+template <typename T, int D, int N>
+static void launch_apply3(const Geom& g, const SipgArgs<T>& a, cudaStream_t st) {
+  if (!a.nu && a.ops && g.bc[0] == 0 && g.bc[1] == 0 && g.bc[2] == 0) {
+    using P = Sipg3pShape<T, N>;
+    constexpr size_t sm = sipg3p_smem<T, N>();
+    cudaFuncSetAttribute(sipg3p_apply_kernel<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    IMEX_COUNTED(sipg3p_apply_kernel<T, N><<<(g.ne + P::EPB - 1) / P::EPB, P::THREADS, sm, st>>>(g, a));
+    return;
+  }
+  if (!a.nu && a.ops) {
+    using C = Sipg3cShape<N>;
+    constexpr size_t sm = sipg3c_smem<T, N>();
+    cudaFuncSetAttribute(sipg3c_apply_kernel<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    IMEX_COUNTED(sipg3c_apply_kernel<T, N><<<(g.ne + C::EPB - 1) / C::EPB, C::THREADS, sm, st>>>(g, a));
+    return;
+  }
+  using S = Sipg3Shape<N>;
+  const int blocks = (g.ne + S::EPB - 1) / S::EPB;
+  constexpr size_t smem = sipg3_smem<T, N>();
+  if (a.nu) {
+    cudaFuncSetAttribute(sipg3_apply_kernel<T, N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    IMEX_COUNTED(sipg3_apply_kernel<T, N, true><<<blocks, S::THREADS, smem, st>>>(g, a));
+  } else {
+    cudaFuncSetAttribute(sipg3_apply_kernel<T, N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    IMEX_COUNTED(sipg3_apply_kernel<T, N, false><<<blocks, S::THREADS, smem, st>>>(g, a));
+  }
 }
 
 template <typename T, int D, int N>
@@ -304,8 +1113,9 @@ static void launch_diag(const Geom& g, const SipgArgs<T>& a, cudaStream_t st) {
 
 template <typename T>
 int sipg_apply(const Geom& g, int N, const SipgArgs<T>& a, cudaStream_t st) {
+  if (a.dot_out && (a.nu || !a.ops)) return -2;     // the fused dot exists on the constant-nu path only
   if (g.d == 2) { IMEX_DISPATCH_N(2, launch_apply, g, a, st) }
-  else { IMEX_DISPATCH_N(3, launch_apply, g, a, st) }
+  else { IMEX_DISPATCH_N(3, launch_apply3, g, a, st) }
   return 0;
 }
 

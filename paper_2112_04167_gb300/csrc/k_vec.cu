@@ -1,8 +1,9 @@
 // Vector kernels: stage linear combinations (FP64), deterministic two-level
-// reductions (FP64 accumulation), precision conversion, and the fused
-// Jacobi-PCG updates whose scalars stay in device memory.
+// reductions (FP64 accumulation), precision conversion and the allocation-free
+// reduction entry point.  The Jacobi-PCG kernels live in k_cg.cu.
 #include <atomic>
 #include <mutex>
+#include <type_traits>
 
 #include "../../include/imex.h"
 #include "common.cuh"
@@ -76,10 +77,10 @@ __global__ void dot_partial_kernel(const T* __restrict__ x, const T* __restrict_
   const int s = blockIdx.y;
   const T* xs = x + (size_t)s * stride;
   const T* ys = y + (size_t)s * stride;
-  double acc = 0.0;
+  T tacc = T(0);                      // per-thread partial in the data type (FP64 is scarce on GB300)
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-    acc += (double)xs[i] * (double)ys[i];
-  acc = block_sum(acc);
+    tacc += xs[i] * ys[i];
+  double acc = block_sum((double)tacc);
   if (threadIdx.x == 0) partial[(size_t)s * gridDim.x + blockIdx.x] = acc;
 }
 
@@ -185,152 +186,6 @@ void axpy_f2d(double* y, const float* x, size_t n, cudaStream_t st) {
   IMEX_COUNTED(axpy_f2d_kernel<<<grid_for(n, 256), 256, 0, st>>>(y, x, n));
 }
 
-// ---- PCG kernels -----------------------------------------------------------------
-// scalars per system s: rz[s], rr[s], bb[s], pAp[s], done[s], iters[s]
-template <typename T>
-__global__ void cg_xr_kernel(T* __restrict__ x, T* __restrict__ r, const T* __restrict__ p,
-                             const T* __restrict__ Ap, const T* __restrict__ dinv, T* __restrict__ z,
-                             size_t n, long long stride, CgScalars sc, double* __restrict__ partial) {
-  const int s = blockIdx.y;
-  const bool skip = sc.done[s] != 0;
-  double arz = 0.0, arr = 0.0;
-  if (!skip) {
-    const double pap = sc.pAp[s];
-    const T alpha = (T)(pap != 0.0 ? sc.rz[s] / pap : 0.0);
-    const size_t off = (size_t)s * stride;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-      const T pi = p[off + i];
-      const T api = Ap[off + i];
-      T xi = x[off + i] + alpha * pi;
-      T ri = r[off + i] - alpha * api;
-      T zi = ri * dinv[i];
-      x[off + i] = xi;
-      r[off + i] = ri;
-      z[off + i] = zi;
-      arz += (double)ri * (double)zi;
-      arr += (double)ri * (double)ri;
-    }
-  }
-  arz = block_sum(arz);
-  arr = block_sum(arr);
-  if (threadIdx.x == 0) {
-    partial[(size_t)(2 * s) * gridDim.x + blockIdx.x] = arz;
-    partial[(size_t)(2 * s + 1) * gridDim.x + blockIdx.x] = arr;
-  }
-}
-
-// final reduction: rz_old <- rz, rz <- sum, rr <- sum, convergence flag, iteration count
-__global__ void cg_finish_kernel(const double* __restrict__ partial, int nblocks, CgScalars sc, int maxit) {
-  const int s = blockIdx.x;
-  double a = 0.0, b = 0.0;
-  for (int i = threadIdx.x; i < nblocks; i += blockDim.x) {
-    a += partial[(size_t)(2 * s) * nblocks + i];
-    b += partial[(size_t)(2 * s + 1) * nblocks + i];
-  }
-  a = block_sum(a);
-  b = block_sum(b);
-  if (threadIdx.x == 0 && sc.done[s] == 0) {
-    sc.rz_old[s] = sc.rz[s];
-    sc.rz[s] = a;
-    sc.rr[s] = b;
-    sc.iters[s] += 1;
-    if (b <= sc.tol2 * sc.bb[s] || b != b) sc.done[s] = (b != b) ? 2 : 1;
-    else if (sc.iters[s] >= maxit) sc.done[s] = 3;
-  }
-}
-
-template <typename T>
-__global__ void cg_p_kernel(T* __restrict__ p, const T* __restrict__ z, size_t n, long long stride,
-                            CgScalars sc) {
-  const int s = blockIdx.y;
-  if (sc.done[s] != 0) return;
-  const double ro = sc.rz_old[s];
-  const T beta = (T)(ro != 0.0 ? sc.rz[s] / ro : 0.0);
-  const size_t off = (size_t)s * stride;
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-    p[off + i] = z[off + i] + beta * p[off + i];
-}
-
-template <typename T>
-__global__ void cg_init_kernel(T* __restrict__ p, T* __restrict__ z, const T* __restrict__ r,
-                               const T* __restrict__ dinv, size_t n, long long stride,
-                               double* __restrict__ partial) {
-  const int s = blockIdx.y;
-  const size_t off = (size_t)s * stride;
-  double arz = 0.0, arr = 0.0;
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-    T ri = r[off + i];
-    T zi = ri * dinv[i];
-    z[off + i] = zi;
-    p[off + i] = zi;
-    arz += (double)ri * (double)zi;
-    arr += (double)ri * (double)ri;
-  }
-  arz = block_sum(arz);
-  arr = block_sum(arr);
-  if (threadIdx.x == 0) {
-    partial[(size_t)(2 * s) * gridDim.x + blockIdx.x] = arz;
-    partial[(size_t)(2 * s + 1) * gridDim.x + blockIdx.x] = arr;
-  }
-}
-
-__global__ void cg_init_finish_kernel(const double* __restrict__ partial, int nblocks, CgScalars sc) {
-  const int s = blockIdx.x;
-  double a = 0.0, b = 0.0;
-  for (int i = threadIdx.x; i < nblocks; i += blockDim.x) {
-    a += partial[(size_t)(2 * s) * nblocks + i];
-    b += partial[(size_t)(2 * s + 1) * nblocks + i];
-  }
-  a = block_sum(a);
-  b = block_sum(b);
-  if (threadIdx.x == 0) {
-    sc.rz[s] = a;
-    sc.rr[s] = b;
-    sc.iters[s] = 0;
-    sc.done[s] = (b <= sc.tol2 * sc.bb[s]) ? 1 : 0;
-  }
-}
-
-// pAp from the dot partials, skipping converged systems
-__global__ void cg_pap_kernel(const double* __restrict__ partial, int nblocks, CgScalars sc) {
-  const int s = blockIdx.x;
-  double a = 0.0;
-  for (int i = threadIdx.x; i < nblocks; i += blockDim.x) a += partial[(size_t)s * nblocks + i];
-  a = block_sum(a);
-  if (threadIdx.x == 0) sc.pAp[s] = a;
-}
-
-template <typename T>
-void cg_init(T* p, T* z, const T* r, const T* dinv, size_t n, long long stride, int nsys, const CgScalars& sc,
-             double* partial, int nblocks, cudaStream_t st) {
-  dim3 grid(nblocks, nsys);
-  IMEX_COUNTED(cg_init_kernel<T><<<grid, 256, 0, st>>>(p, z, r, dinv, n, stride, partial));
-  IMEX_COUNTED(cg_init_finish_kernel<<<nsys, 256, 0, st>>>(partial, nblocks, sc));
-}
-
-template <typename T>
-void cg_pap(const T* p, const T* Ap, size_t n, long long stride, int nsys, const CgScalars& sc,
-            double* partial, int nblocks, cudaStream_t st) {
-  dim3 grid(nblocks, nsys);
-  IMEX_COUNTED(dot_partial_kernel<T><<<grid, 256, 0, st>>>(p, Ap, n, stride, partial));
-  IMEX_COUNTED(cg_pap_kernel<<<nsys, 256, 0, st>>>(partial, nblocks, sc));
-}
-
-template <typename T>
-void cg_step_xr(T* x, T* r, const T* p, const T* Ap, const T* dinv, T* z, size_t n, long long stride,
-                int nsys, const CgScalars& sc, int maxit, double* partial, int nblocks, cudaStream_t st) {
-  dim3 grid(nblocks, nsys);
-  IMEX_COUNTED(cg_xr_kernel<T><<<grid, 256, 0, st>>>(x, r, p, Ap, dinv, z, n, stride, sc, partial));
-  IMEX_COUNTED(cg_finish_kernel<<<nsys, 256, 0, st>>>(partial, nblocks, sc, maxit));
-}
-
-template <typename T>
-void cg_step_p(T* p, const T* z, size_t n, long long stride, int nsys, const CgScalars& sc, int nblocks,
-               cudaStream_t st) {
-  dim3 grid(nblocks, nsys);
-  IMEX_COUNTED(cg_p_kernel<T><<<grid, 256, 0, st>>>(p, z, n, stride, sc));
-}
-
 template <typename T>
 __global__ void recip_kernel(T* d, size_t n) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
@@ -341,26 +196,11 @@ void reciprocal(T* d, size_t n, cudaStream_t st) {
   IMEX_COUNTED(recip_kernel<T><<<grid_for(n, 256), 256, 0, st>>>(d, n));
 }
 
-template void cg_init<double>(double*, double*, const double*, const double*, size_t, long long, int,
-                              const CgScalars&, double*, int, cudaStream_t);
-template void cg_init<float>(float*, float*, const float*, const float*, size_t, long long, int,
-                             const CgScalars&, double*, int, cudaStream_t);
-template void cg_pap<double>(const double*, const double*, size_t, long long, int, const CgScalars&, double*,
-                             int, cudaStream_t);
-template void cg_pap<float>(const float*, const float*, size_t, long long, int, const CgScalars&, double*,
-                            int, cudaStream_t);
-template void cg_step_xr<double>(double*, double*, const double*, const double*, const double*, double*,
-                                 size_t, long long, int, const CgScalars&, int, double*, int, cudaStream_t);
-template void cg_step_xr<float>(float*, float*, const float*, const float*, const float*, float*, size_t,
-                                long long, int, const CgScalars&, int, double*, int, cudaStream_t);
-template void cg_step_p<double>(double*, const double*, size_t, long long, int, const CgScalars&, int,
-                                cudaStream_t);
-template void cg_step_p<float>(float*, const float*, size_t, long long, int, const CgScalars&, int,
-                               cudaStream_t);
 template void reciprocal<double>(double*, size_t, cudaStream_t);
 template void reciprocal<float>(float*, size_t, cudaStream_t);
 
 }  // namespace imex
+
 
 // =====================================================================================
 // Allocation-free reduction: imex_reduce_noalloc (include/imex.h).

@@ -21,9 +21,22 @@ struct SipgArgs {
   long long g_stride;
   T alpha, beta;
   int minv;
+  const LineOps<T>* ops;   // line operators of this space (constant-viscosity fast path), or nullptr
+  // optional fused CG dot (x, y) per system: block partials, completion counter, result
+  double* dot_partial;     // [nsys][gridDim.x]
+  unsigned int* dot_counter;
+  double* dot_out;         // [nsys]
+  // optional CG step length from the fused dot: alpha[s] = cg_rz[s] / dot_out[s] in FP64 and
+  // FP32; a non-finite step marks a running system (cg_done[s] == 0) as broken down (2)
+  const double* cg_rz;
+  double* cg_alpha;
+  float* cg_alpha_f;
+  int* cg_done;
 };
 
 template <typename T> int sipg_apply(const Geom& g, int N, const SipgArgs<T>& a, cudaStream_t st);
+// constant-memory line operators of the periodic fast path (once per device)
+void init_const_lines(const Tables<double>& t);
 template <typename T> int sipg_diag(const Geom& g, int N, const SipgArgs<T>& a, cudaStream_t st);
 
 // Weak divergence into the pressure test space (Nv velocity points, Nv-1 pressure points):

@@ -6,7 +6,8 @@
 namespace imex {
 
 // Per-system CG scalars, all in device memory.  done: 0 running, 1 converged,
-// 2 NaN in the residual, 3 iteration limit reached.
+// 2 NaN in the residual, 3 iteration limit reached (4: converged in the true residual,
+// set by the host of the mixed form).
 struct CgScalars {
   double* rz;
   double* rz_old;
@@ -16,19 +17,63 @@ struct CgScalars {
   int* done;
   int* iters;
   double tol2;     // (relative tolerance)^2 on ||r||_2 / ||b||_2
+  double* zmean;   // projected systems: mean of D^{-1} r'
+  double* rmean;   // projected systems: mean of the recursive residual r
+  double* dsum;    // projected systems: sum of D^{-1} over the system
+  int project;     // 1: singular systems with the constants as null space
+  // step coefficients, computed once per iteration by the kernel that finishes the
+  // reduction they need, in FP64 and FP32 (the streaming kernels read them directly)
+  double* alpha;   // rz / pAp
+  double* beta;    // rz / rz_old
+  float* alpha_f;
+  float* beta_f;
+  float* zmean_f;
+  float* rmean_f;
 };
 
+// Segments of a set of CG systems sharing vectors (see k_vec.cu): system s occupies
+// [off[s], off[s] + len[s]) of the vectors and [doff[s], doff[s] + len[s]) of the Jacobi
+// diagonal; blocks of SEG_CHUNK elements, blk_seg / blk_lo per block, seg_blk0[s] the first
+// block of system s (seg_blk0[nseg] = nblk).
+constexpr int SEG_CHUNK = 2048;
+// one block's chunk: vectors [off, off + n), diagonal [doff, doff + n), system s
+struct alignas(16) SegBlock {
+  long long off;
+  long long doff;
+  int n;
+  int s;
+  int pad[2];
+};
+struct SegTable {
+  int nseg;
+  int nblk;
+  const long long* off;
+  const long long* doff;
+  const int* len;
+  const int* blk_seg;
+  const int* blk_lo;
+  const int* seg_blk0;
+  const SegBlock* blk;
+};
+// x += alpha p, r -= alpha A p, the new (projected) CG scalars and the convergence test
 template <typename T>
-void cg_init(T* p, T* z, const T* r, const T* dinv, size_t n, long long stride, int nsys, const CgScalars& sc,
-             double* partial, int nblocks, cudaStream_t st);
+void seg_step_xr(T* x, T* r, const T* p, const T* Ap, const T* dinv, const SegTable& t, const CgScalars& sc,
+                 int maxit, double* partial, unsigned int* counter, cudaStream_t st);
+// p = z' + beta p with z' the (projected) preconditioned residual (beta = 0 with restart = 1)
 template <typename T>
-void cg_pap(const T* p, const T* Ap, size_t n, long long stride, int nsys, const CgScalars& sc,
-            double* partial, int nblocks, cudaStream_t st);
+void seg_step_p(T* p, T* r, const T* dinv, const SegTable& t, const CgScalars& sc, int restart, cudaStream_t st);
 template <typename T>
-void cg_step_xr(T* x, T* r, const T* p, const T* Ap, const T* dinv, T* z, size_t n, long long stride,
-                int nsys, const CgScalars& sc, int maxit, double* partial, int nblocks, cudaStream_t st);
+void seg_dot(const T* x, const T* y, const SegTable& t, double* out, double* partial, unsigned int* counter,
+             cudaStream_t st);
+// (p, A p) per system into sc.pAp, and the step length alpha = rz / pAp
 template <typename T>
-void cg_step_p(T* p, const T* z, size_t n, long long stride, int nsys, const CgScalars& sc, int nblocks,
-               cudaStream_t st);
+void seg_pap(const T* p, const T* Ap, const SegTable& t, const CgScalars& sc, double* partial, unsigned int* counter,
+             cudaStream_t st);
+// CG scalars of a new residual (reset = 1: all systems, iteration counts and flags restart)
+template <typename T>
+void seg_init(const T* r, const T* dinv, const SegTable& t, const CgScalars& sc, double* partial,
+              unsigned int* counter, int reset, cudaStream_t st);
+void seg_remove_mean(double* x, const SegTable& t, double* mean, double* partial, unsigned int* counter,
+                     cudaStream_t st);
 
 }  // namespace imex
