@@ -207,6 +207,35 @@ imex_status imex_profile_read(imex_ctx* ctx, int cls, long long* launches, doubl
 /* kernels launched by this library so far, all contexts */
 long long imex_launch_count(void);
 
+/* ---- Batches of instances ---------------------------------------------------------------
+ * Many independent instances advanced together (the ensemble and serving forms of the
+ * per-stage work of Alg. 3).  imex_batch_create groups the given contexts by everything that
+ * is not per-instance (d, P, periodicity, precision, solver settings, model kinds, tableau);
+ * each group becomes one union mesh whose operators run as one launch over all its
+ * instances and whose CG systems (each instance's pressure, each velocity component of
+ * each instance) advance together with per-system step lengths and convergence tests.
+ * Per instance: mesh box and element counts, viscosity and model parameters, time, time
+ * step.  The batch copies the instances' current velocity, pressure and time at creation
+ * and owns the stepped state from then on; the instance contexts are not modified and may
+ * be destroyed.  RK tableaux only (SDC contexts and IMEX_NU_FIELD viscosity: IMEX_EINVAL).
+ * Errors of a group (IMEX_ENOTCONV, IMEX_EUNSTABLE) are returned by imex_batch_step with the
+ * group named in imex_batch_last_error; the other groups still complete their steps. */
+typedef struct imex_batch imex_batch;
+/* insts: n contexts (borrowed for the call); out: the new batch. */
+imex_status imex_batch_create(imex_ctx* const* insts, int n, imex_batch** out);
+void imex_batch_destroy(imex_batch* b);
+const char* imex_batch_last_error(const imex_batch* b);
+/* number of union-mesh groups the instances were sorted into */
+int imex_batch_groups(const imex_batch* b);
+/* nsteps steps of every instance; dt[i] > 0 is instance i's time step (host array of n) */
+imex_status imex_batch_step(imex_batch* b, const double* dt, int nsteps);
+/* instance i's velocity [d][its elements][nodes] / pressure / time, as for one context */
+imex_status imex_batch_get_velocity(imex_batch* b, int i, double* out, int on_device);
+imex_status imex_batch_get_pressure(imex_batch* b, int i, double* out, int on_device);
+imex_status imex_batch_get_time(const imex_batch* b, int i, double* t);
+/* totals of the last imex_batch_step over all groups (steps: per instance) */
+imex_status imex_batch_get_stats(const imex_batch* b, imex_stats* out);
+
 #ifdef __cplusplus
 }
 #endif

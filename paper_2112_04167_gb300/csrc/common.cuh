@@ -15,7 +15,27 @@
 
 namespace imex {
 
-// Mesh geometry as seen by every kernel (passed by value).
+// One instance of a batched mesh: its elements are [e0, e0 + ne) of the union, its own
+// Cartesian box, element counts and sizes, constant viscosity, time step and current time,
+// and the parameters of its analytic viscosity model, boundary data and forcing.
+struct InstGeom {
+  int e0;
+  int ne;
+  int n[3];
+  double lo[3];
+  double h[3];
+  float hf[3];
+  double nu0;
+  float nu0f;
+  double dt;
+  float dtf;
+  double t;
+  double nu_p[8], bc_p[8], f_p[8];
+};
+
+// Mesh geometry as seen by every kernel (passed by value).  A batched mesh is the union of
+// several instances of the same space (d, N): inst / elem_inst give each element's instance
+// and local_geom() the element's own view of it.
 struct Geom {
   int d;                 // 2 or 3
   int ne;                // number of elements
@@ -26,6 +46,14 @@ struct Geom {
   float hf[3];           // the same in FP32 (FP32 kernels take no FP64 conversion per thread)
   const void* tab64;     // device Tables<double>
   const void* tab32;     // device Tables<float>
+  const InstGeom* inst;  // batched mesh: per-instance geometry, or nullptr
+  const int* elem_inst;  // batched mesh: instance of each element
+  // set by local_geom for the element at hand (defaults for a single instance)
+  int e0;                // first element of the instance
+  double inu0;           // the instance's constant viscosity
+  float inu0f;
+  double idt;            // the instance's time step
+  float idtf;
 };
 
 template <typename T> __host__ __device__ __forceinline__ T geom_h(const Geom& g, int k);
@@ -82,7 +110,39 @@ template <> __device__ __forceinline__ const Tables<float>& tab<float>(const Geo
 __host__ __device__ constexpr int ipow(int b, int e) { return e == 0 ? 1 : b * ipow(b, e - 1); }
 __host__ __device__ constexpr int over_q(int N) { return (3 * N + 1) / 2; }
 
-// neighbour element across face (k, side) of element with coordinates ec; -1 on a domain boundary
+// The geometry of element e as seen from its own instance: box, counts and sizes of the
+// instance, and el = e - e0 its index there.  Single-instance meshes return g unchanged.
+__device__ __forceinline__ Geom local_geom(const Geom& g, int e, int& el) {
+  if (!g.inst) {
+    el = e;
+    return g;
+  }
+  const InstGeom& I = g.inst[g.elem_inst[e]];
+  Geom l = g;
+  for (int k = 0; k < 3; ++k) {
+    l.n[k] = I.n[k];
+    l.lo[k] = I.lo[k];
+    l.h[k] = I.h[k];
+    l.hf[k] = I.hf[k];
+  }
+  l.e0 = I.e0;
+  l.inu0 = I.nu0;
+  l.inu0f = I.nu0f;
+  l.idt = I.dt;
+  l.idtf = I.dtf;
+  el = e - I.e0;
+  return l;
+}
+
+template <typename T> __host__ __device__ __forceinline__ T geom_nu0(const Geom& g);
+template <> __host__ __device__ __forceinline__ double geom_nu0<double>(const Geom& g) { return g.inu0; }
+template <> __host__ __device__ __forceinline__ float geom_nu0<float>(const Geom& g) { return g.inu0f; }
+template <typename T> __host__ __device__ __forceinline__ T geom_dt(const Geom& g);
+template <> __host__ __device__ __forceinline__ double geom_dt<double>(const Geom& g) { return g.idt; }
+template <> __host__ __device__ __forceinline__ float geom_dt<float>(const Geom& g) { return g.idtf; }
+
+// neighbour element (index in the union) across face (k, side) of the element with local
+// coordinates ec; -1 on a domain boundary.  g is the element's local_geom.
 __device__ __forceinline__ int neighbor(const Geom& g, const int ec[3], int k, int side) {
   int c[3] = {ec[0], ec[1], ec[2]};
   int j = c[k] + side;
@@ -91,12 +151,13 @@ __device__ __forceinline__ int neighbor(const Geom& g, const int ec[3], int k, i
     j = (j + g.n[k]) % g.n[k];
   }
   c[k] = j;
-  return c[0] + g.n[0] * (c[1] + g.n[1] * c[2]);
+  return g.e0 + c[0] + g.n[0] * (c[1] + g.n[1] * c[2]);
 }
 
-__device__ __forceinline__ void elem_coords(const Geom& g, int e, int ec[3]) {
-  ec[0] = e % g.n[0];
-  int r = e / g.n[0];
+// local coordinates of the element with local index el (g: its local_geom)
+__device__ __forceinline__ void elem_coords(const Geom& g, int el, int ec[3]) {
+  ec[0] = el % g.n[0];
+  int r = el / g.n[0];
   ec[1] = r % g.n[1];
   ec[2] = r / g.n[1];
 }

@@ -13,6 +13,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/imex.h"
@@ -23,8 +24,6 @@
 using namespace imex;
 
 // helpers defined at the end of this file
-void sub_f(float* r, const float* b, const float* a, size_t n, cudaStream_t st);
-void remove_mean_t(void* x, int tsize, size_t n, double* partial, int nblocks, double* scratch, cudaStream_t st);
 void f2d(const float* in, double* out, size_t n, cudaStream_t st);
 
 namespace {
@@ -207,6 +206,13 @@ struct imex_ctx {
   int* cg_hi = nullptr;
   double* seg_partial = nullptr;
   bool diag_valid_p = false;
+  // instances of the mesh: one for a plain context; several for the union mesh of a batch
+  // group, whose kernels see per-element geometry, viscosity, time step and time
+  bool batched = false;
+  std::vector<InstGeom> inst;
+  InstGeom* inst_d = nullptr;
+  int* elem_inst_d = nullptr;
+  double* edt = nullptr;        // per-element time step (batched)
   imex_stats stats{};
   double last_res = 0.0;
   // CUDA-event timing of kernel classes
@@ -353,6 +359,8 @@ SipgArgs<T> sipg_args(const T* x, T* y, int nsys, long long stride, const T* nu,
   a.cg_alpha = nullptr;
   a.cg_alpha_f = nullptr;
   a.cg_done = nullptr;
+  a.inst_nu = 0;
+  a.inst_dt = 0;
   return a;
 }
 
@@ -379,6 +387,15 @@ void fuse_cg(imex_ctx* c, SipgArgs<T>& a, const CgScalars* cg) {
   a.cg_alpha = cg->alpha;
   a.cg_alpha_f = cg->alpha_f;
   a.cg_done = cg->done;
+}
+
+// batch groups: velocity operators take the constant viscosity of each element's instance
+// and, where their scale is a multiple of the time step, the instance's step
+template <typename T>
+void vel_flags(const imex_ctx* c, SipgArgs<T>& a, bool dt_scaled) {
+  if (!c->batched) return;
+  a.inst_nu = a.nu == nullptr ? 1 : 0;
+  a.inst_dt = dt_scaled ? 1 : 0;
 }
 
 // the pressure operator L psi (pressure space), T = double / float
@@ -408,6 +425,7 @@ imex_status apply_helm(imex_ctx* c, const T* x, T* y, int nsys, const T* nu, dou
   const int cls = sizeof(T) == 4 ? IMEX_PROF_HELMHOLTZ_F32 : IMEX_PROF_HELMHOLTZ_F64;
   SipgArgs<T> a = sipg_args<T>(x, y, nsys, (long long)c->nv, nu, nu_const(c), nullptr, 1.0, gamma, 0);
   a.ops = line_ops<T>(c, true);
+  vel_flags(c, a, true);
   fuse_cg(c, a, cg);
   prof_mark(c, cls, true);
   const int rc = sipg_apply<T>(c->gv, c->Nv, a, c->st);
@@ -650,89 +668,11 @@ imex_status pcg_mixed(imex_ctx* c, const imex_ctx::Seg& sg, Op64 op64, Op32 op32
 
 // small helper kernels local to this file
 namespace imex {
-__global__ void sub_f_kernel(float* r, const float* b, const float* a, size_t n) {
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-    r[i] = b[i] - a[i];
-}
 __global__ void diag_mul_kernel(double* out, const double* x, const double* m, size_t n, int nsys) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n * nsys; i += (size_t)gridDim.x * blockDim.x)
     out[i] = x[i] * m[i % n];
 }
-template <typename T>
-__global__ void sum_partial_t(const T* x, size_t n, double* partial) {
-  double acc = 0.0;
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-    acc += (double)x[i];
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-  __shared__ double ws[32];
-  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = acc;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double s = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += ws[w];
-    partial[blockIdx.x] = s;
-  }
-}
-__global__ void finish_mean(const double* partial, int nb, double* dst, double n) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) {
-    double s = 0.0;
-    for (int i = 0; i < nb; ++i) s += partial[i];
-    dst[0] = s / n;
-  }
-}
-template <typename T>
-__global__ void sub_mean_t(T* x, size_t n, const double* mean) {
-  const T m = (T)mean[0];
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-    x[i] -= m;
-}
-// weighted mean removal: x -= (sum w x) / (sum w)
-__global__ void wsum_partial(const double* x, const double* w, size_t n, double* partial) {
-  double a = 0.0, b = 0.0;
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-    a += w[i] * x[i];
-    b += w[i];
-  }
-  for (int o = 16; o > 0; o >>= 1) {
-    a += __shfl_down_sync(0xffffffffu, a, o);
-    b += __shfl_down_sync(0xffffffffu, b, o);
-  }
-  __shared__ double wa[32], wb[32];
-  if ((threadIdx.x & 31) == 0) { wa[threadIdx.x >> 5] = a; wb[threadIdx.x >> 5] = b; }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double s = 0.0, u = 0.0;
-    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) { s += wa[k]; u += wb[k]; }
-    partial[2 * blockIdx.x] = s;
-    partial[2 * blockIdx.x + 1] = u;
-  }
-}
-__global__ void finish_wmean(const double* partial, int nb, double* dst) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) {
-    double s = 0.0, u = 0.0;
-    for (int i = 0; i < nb; ++i) { s += partial[2 * i]; u += partial[2 * i + 1]; }
-    dst[0] = s / u;
-  }
-}
 }  // namespace imex
-
-void sub_f(float* r, const float* b, const float* a, size_t n, cudaStream_t st) {
-  IMEX_COUNTED(imex::sub_f_kernel<<<(unsigned)std::min<size_t>((n + 255) / 256, 1216), 256, 0, st>>>(r, b, a, n));
-}
-
-void remove_mean_t(void* x, int tsize, size_t n, double* partial, int nblocks, double* scratch,
-                   cudaStream_t st) {
-  if (tsize == 8) {
-    IMEX_COUNTED(imex::sum_partial_t<double><<<nblocks, 256, 0, st>>>((const double*)x, n, partial));
-  } else {
-    IMEX_COUNTED(imex::sum_partial_t<float><<<nblocks, 256, 0, st>>>((const float*)x, n, partial));
-  }
-  IMEX_COUNTED(imex::finish_mean<<<1, 32, 0, st>>>(partial, nblocks, scratch, (double)n));
-  if (tsize == 8)
-    IMEX_COUNTED(imex::sub_mean_t<double><<<nblocks, 256, 0, st>>>((double*)x, n, scratch));
-  else
-    IMEX_COUNTED(imex::sub_mean_t<float><<<nblocks, 256, 0, st>>>((float*)x, n, scratch));
-}
 
 namespace {
 
@@ -740,17 +680,13 @@ void diag_mul(imex_ctx* c, double* out, const double* x, const double* m, size_t
   IMEX_COUNTED(imex::diag_mul_kernel<<<c->nblocks, 256, 0, c->st>>>(out, x, m, n, nsys));
 }
 
-void remove_weighted_mean(imex_ctx* c, double* x, const double* w, size_t n) {
-  IMEX_COUNTED(imex::wsum_partial<<<c->nblocks, 256, 0, c->st>>>(x, w, n, c->partial));
-  IMEX_COUNTED(imex::finish_wmean<<<1, 32, 0, c->st>>>(c->partial, c->nblocks, c->dscal + 33));
-  IMEX_COUNTED(imex::sub_mean_t<double><<<c->nblocks, 256, 0, c->st>>>(x, n, c->dscal + 33));
-}
 
 // ---- solves ------------------------------------------------------------------------
 // Poisson: L psi = b (b is overwritten by its mean-free part); psi: initial guess in, solution out
 imex_status solve_poisson(imex_ctx* c, double* b, double* psi, long long* iters, double* res) {
   const size_t n = c->np;
-  remove_mean_t(b, 8, n, c->partial, c->nblocks, c->dscal + 32, c->st);
+  const int m = c->maxsys;
+  seg_remove_mean(b, c->segp.t, c->cg_d + 6 * m, c->seg_partial, c->counters + 3, c->st);
   if (!c->diag_valid_p) {
     SipgArgs<double> a = sipg_args<double>(nullptr, c->cdiag, 1, (long long)n, nullptr, 1.0, nullptr, 0.0, 1.0, 0);
     TRY(launch_check(c, sipg_diag<double>(c->gp, c->Np, a, c->st), "sipg_diag(p)"));
@@ -765,9 +701,9 @@ imex_status solve_poisson(imex_ctx* c, double* b, double* psi, long long* iters,
     auto opd = [&](const double* x, double* y, const CgScalars* d) {
       return apply_pressure<double>(c, x, y, c->tmp, d);
     };
-    const bool fused = c->desc.poisson == IMEX_POISSON_SIPG;
+    const bool fused = c->desc.poisson == IMEX_POISSON_SIPG && !c->batched;
     imex_status s = pcg(c, c->segp, op, opd, fused, b, psi, c->cdiag, tol, c->desc.maxit, true, iters, res);
-    remove_weighted_mean(c, psi, c->mass_p, n);
+    seg_remove_wmean(psi, c->mass_p, c->segp.t, c->cg_d + 6 * m, c->seg_partial, c->counters + 3, c->st);
     return s;
   }
   // mixed: FP32 operator and preconditioner, FP64 iterate and residual with reliable updates
@@ -776,9 +712,9 @@ imex_status solve_poisson(imex_ctx* c, double* b, double* psi, long long* iters,
   auto op32d = [&](const float* x, float* y, const CgScalars* d) {
     return apply_pressure<float>(c, x, y, c->fvtmp, d);
   };
-  const bool fused = c->desc.poisson == IMEX_POISSON_SIPG;
+  const bool fused = c->desc.poisson == IMEX_POISSON_SIPG && !c->batched;
   TRY(pcg_mixed(c, c->segp, op64, op32, op32d, fused, b, psi, c->fdiag, tol, c->desc.maxit, true, iters, res));
-  remove_weighted_mean(c, psi, c->mass_p, n);
+  seg_remove_wmean(psi, c->mass_p, c->segp.t, c->cg_d + 6 * m, c->seg_partial, c->counters + 3, c->st);
   return IMEX_OK;
 }
 
@@ -791,6 +727,7 @@ imex_status solve_helmholtz(imex_ctx* c, const double* rhs, double* x, const dou
   double* dg = c->cdiag + c->np;
   float* fdg = c->fdiag + c->np;
   SipgArgs<double> a = sipg_args<double>(nullptr, dg, 1, (long long)n, nu, nu_const(c), nullptr, 1.0, gamma, 0);
+  vel_flags(c, a, true);
   TRY(launch_check(c, sipg_diag<double>(c->gv, c->Nv, a, c->st), "sipg_diag(v)"));
   reciprocal<double>(dg, n, c->st);
   const double tol = c->desc.tol;
@@ -799,7 +736,7 @@ imex_status solve_helmholtz(imex_ctx* c, const double* rhs, double* x, const dou
     auto opd = [&](const double* xx, double* yy, const CgScalars* dd) {
       return apply_helm<double>(c, xx, yy, d, nu, gamma, dd);
     };
-    return pcg(c, c->segv, op, opd, nu == nullptr, rhs, x, dg, tol, c->desc.maxit, false, iters, res);
+    return pcg(c, c->segv, op, opd, nu == nullptr && !c->batched, rhs, x, dg, tol, c->desc.maxit, false, iters, res);
   }
   convert_d2f(dg, fdg, n, c->st);
   const float* fnu = nullptr;
@@ -809,7 +746,8 @@ imex_status solve_helmholtz(imex_ctx* c, const double* rhs, double* x, const dou
   auto op32d = [&](const float* xx, float* yy, const CgScalars* dd) {
     return apply_helm<float>(c, xx, yy, d, fnu, gamma, dd);
   };
-  TRY(pcg_mixed(c, c->segv, op64, op32, op32d, fnu == nullptr, rhs, x, fdg, tol, c->desc.maxit, false, iters, res));
+  TRY(pcg_mixed(c, c->segv, op64, op32, op32d, fnu == nullptr && !c->batched, rhs, x, fdg, tol, c->desc.maxit, false,
+                iters, res));
   return IMEX_OK;
 }
 
@@ -852,6 +790,7 @@ const double* nu_ptr(const imex_ctx* c, const double* nu) { return variable_nu(c
 imex_status graddiv(imex_ctx* c, const double* v, const double* nu, double* fd3, double* fd2_acc) {
   DerivArgs<double> a{};
   a.op = 0; a.in = v; a.stride = (long long)c->nv; a.nu = nu_ptr(c, nu); a.nu0 = nu_const(c); a.out = c->phi;
+  a.inst_nu = c->batched && a.nu == nullptr;
   TRY(launch_check(c, dg_deriv<double>(c->gv, c->Nv, a, c->st), "dg_deriv(div)"));
   DerivArgs<double> b{};
   b.op = 1; b.in = c->phi; b.stride = (long long)c->nv; b.coef = -1.0; b.out = fd3;
@@ -859,6 +798,7 @@ imex_status graddiv(imex_ctx* c, const double* v, const double* nu, double* fd3,
   if (fd2_acc) {
     DerivArgs<double> j{};
     j.op = 2; j.in = v; j.stride = (long long)c->nv; j.nu = nu_ptr(c, nu); j.nu0 = nu_const(c); j.out = c->jac;
+    j.inst_nu = c->batched && j.nu == nullptr;
     TRY(launch_check(c, dg_deriv<double>(c->gv, c->Nv, j, c->st), "dg_deriv(jac)"));
     DerivArgs<double> q{};
     q.op = 3; q.in = c->jac; q.stride = (long long)c->nv; q.coef = 1.0; q.out = fd2_acc;
@@ -889,6 +829,7 @@ imex_status stage_rhs(imex_ctx* c, double t, const double* v, const double* nu, 
   }
   SipgArgs<double> a = sipg_args<double>(v, Fd1, c->d, (long long)c->nv, nu_ptr(c, nu), nu_const(c), vb, 0.0, -1.0, 1);
   a.ops = c->ops64_v;
+  vel_flags(c, a, false);
   TRY(launch_check(c, sipg_apply<double>(c->gv, c->Nv, a, c->st), "sipg_apply(Fd1)"));
   if (Fs) {
     TRY(launch_check(c, eval_field(c->gv, c->Nv, 2, spec(c->f_kind, c->f_p), t, nullptr, (long long)c->nv, Fs, c->st),
@@ -919,6 +860,7 @@ imex_status helmholtz_stage(imex_ctx* c, const double* gfield, const double* nu,
     SipgArgs<double> a = sipg_args<double>(c->cz, c->cp, c->d, (long long)c->nv, nu_ptr(c, nu), nu_const(c), vb, 0.0,
                                            -gamma, 0);
     a.ops = c->ops64_v;
+    vel_flags(c, a, true);
     CK(cudaMemsetAsync(c->cz, 0, nt * sizeof(double), c->st), "memset");
     TRY(launch_check(c, sipg_apply<double>(c->gv, c->Nv, a, c->st), "sipg_apply(rb)"));
     LinComb lc{};
@@ -935,17 +877,35 @@ imex_status helmholtz_stage(imex_ctx* c, const double* gfield, const double* nu,
 }
 
 // ---- Alg. 3 -------------------------------------------------------------------------
+// Time-step scaling of the stage combinations: plain contexts fold dt into the coefficients;
+// batch groups leave it to the per-element time step applied by the linear combination.
+double dtc(const imex_ctx* c, double dt) { return c->batched ? 1.0 : dt; }
+// time at fraction f of the step [t, t + dt]; batch groups pass the fraction and the field
+// kernels add it to each instance's own time and step
+double tat(const imex_ctx* c, double t, double dt, double f) { return c->batched ? f : t + f * dt; }
+// linear combination of velocity-space vectors whose terms after the first nfixed are
+// proportional to the time step
+void lcomb_dt(imex_ctx* c, double* out, LinComb& lc, int nfixed, size_t n) {
+  if (c->batched) {
+    lc.edt = c->edt;
+    lc.cstride = (long long)c->nv;
+    lc.nd = ipow(c->Nv, c->d);
+    lc.nfixed = nfixed;
+  }
+  lincomb(out, lc, n, c->st);
+}
+
 imex_status rk_step(imex_ctx* c, const Tab& tb, double* v, double t, double dt, bool final_projection) {
   const int s = tb.s;
   const size_t nt = c->nv * c->d;
   const bool forcing = c->f_kind != IMEX_FORCE_NONE;
   const double* vb = nullptr;
-  TRY(eval_vb(c, t, &vb));
-  TRY(eval_nu(c, t, v, c->nu));
-  TRY(stage_rhs(c, t, v, c->nu, vb, c->E[0], c->Fd1[0], c->Fd3[0], forcing ? c->Fs[0] : nullptr));
+  TRY(eval_vb(c, tat(c, t, dt, 0.0), &vb));
+  TRY(eval_nu(c, tat(c, t, dt, 0.0), v, c->nu));
+  TRY(stage_rhs(c, tat(c, t, dt, 0.0), v, c->nu, vb, c->E[0], c->Fd1[0], c->Fd3[0], forcing ? c->Fs[0] : nullptr));
   const double* vi = v;
   for (int i = 1; i < s; ++i) {
-    const double ti = t + tb.c[i] * dt;
+    const double ti = tat(c, t, dt, tb.c[i]);
     TRY(eval_vb(c, ti, &vb));
     if (forcing)
       TRY(launch_check(c, eval_field(c->gv, c->Nv, 2, spec(c->f_kind, c->f_p), ti, nullptr, (long long)c->nv,
@@ -955,22 +915,22 @@ imex_status rk_step(imex_ctx* c, const Tab& tb, double* v, double t, double dt, 
     int k = 0;
     lc.x[k] = v; lc.c[k++] = 1.0;
     for (int j = 0; j < i; ++j) {
-      const double a = dt * tb.AE[i][j];
+      const double a = dtc(c, dt) * tb.AE[i][j];
       if (a == 0.0) continue;
       lc.x[k] = c->E[j]; lc.c[k++] = a;
       lc.x[k] = c->Fd1[j]; lc.c[k++] = a;
       lc.x[k] = c->Fd3[j]; lc.c[k++] = a;
     }
     lc.nterms = k;
-    lincomb(c->vp, lc, nt, c->st);
+    lcomb_dt(c, c->vp, lc, 1, nt);
     if (forcing) {
       LinComb lf{};
       int q = 0;
       lf.x[q] = c->vp; lf.c[q++] = 1.0;
       for (int j = 0; j <= i; ++j)
-        if (tb.AI[i][j] != 0.0) { lf.x[q] = c->Fs[j]; lf.c[q++] = dt * tb.AI[i][j]; }
+        if (tb.AI[i][j] != 0.0) { lf.x[q] = c->Fs[j]; lf.c[q++] = dtc(c, dt) * tb.AI[i][j]; }
       lf.nterms = q;
-      lincomb(c->vp, lf, nt, c->st);
+      lcomb_dt(c, c->vp, lf, 1, nt);
     }
     // lines 5-6: projection
     TRY(project(c, c->vp, vb, 1, c->vpp));
@@ -981,15 +941,15 @@ imex_status rk_step(imex_ctx* c, const Tab& tb, double* v, double t, double dt, 
     k = 0;
     lg.x[k] = c->vpp; lg.c[k++] = 1.0;
     for (int j = 0; j < i; ++j) {
-      const double a1 = dt * (tb.AI[i][j] - tb.AE[i][j]);
-      const double a3 = -dt * tb.AE[i][j];
+      const double a1 = dtc(c, dt) * (tb.AI[i][j] - tb.AE[i][j]);
+      const double a3 = -dtc(c, dt) * tb.AE[i][j];
       if (a1 != 0.0) { lg.x[k] = c->Fd1[j]; lg.c[k++] = a1; }
       if (a3 != 0.0) { lg.x[k] = c->Fd3[j]; lg.c[k++] = a3; }
     }
     lg.nterms = k;
-    lincomb(c->g, lg, nt, c->st);
+    lcomb_dt(c, c->g, lg, 1, nt);
     // line 9: Helmholtz solve into the stage buffer (reuse c->vp as v_i storage)
-    TRY(helmholtz_stage(c, c->g, c->nu, dt * tb.AI[i][i], vb, c->vp));
+    TRY(helmholtz_stage(c, c->g, c->nu, dtc(c, dt) * tb.AI[i][i], vb, c->vp));
     c->stats.stages++;
     vi = c->vp;
     TRY(stage_rhs(c, ti, vi, c->nu, vb, c->E[i], c->Fd1[i], c->Fd3[i], nullptr));
@@ -1004,14 +964,14 @@ imex_status rk_step(imex_ctx* c, const Tab& tb, double* v, double t, double dt, 
   for (int i = 0; i < s; ++i) {
     const double fe = tb.bE[i] - tb.AE[s - 1][i];
     const double fi = tb.bI[i] - tb.AI[s - 1][i];
-    if (fe != 0.0) { lc.x[k] = c->E[i]; lc.c[k++] = dt * fe; }
+    if (fe != 0.0) { lc.x[k] = c->E[i]; lc.c[k++] = dtc(c, dt) * fe; }
     if (fi != 0.0) {
-      lc.x[k] = c->Fd1[i]; lc.c[k++] = dt * fi;
-      if (forcing) { lc.x[k] = c->Fs[i]; lc.c[k++] = dt * fi; }
+      lc.x[k] = c->Fd1[i]; lc.c[k++] = dtc(c, dt) * fi;
+      if (forcing) { lc.x[k] = c->Fs[i]; lc.c[k++] = dtc(c, dt) * fi; }
     }
   }
   lc.nterms = k;
-  lincomb(v, lc, nt, c->st);
+  lcomb_dt(c, v, lc, 1, nt);
   if (final_projection) {
     TRY(project(c, v, nullptr, 2, c->vpp));
     CK(cudaMemcpyAsync(v, c->vpp, nt * sizeof(double), cudaMemcpyDeviceToDevice, c->st), "cp");
@@ -1227,64 +1187,13 @@ imex_status alloc_stages(imex_ctx* c, int s) {
   return IMEX_OK;
 }
 
-}  // namespace
-
-// =====================================================================================
-// C ABI
-// =====================================================================================
-extern "C" {
-
-imex_status imex_create(const imex_mesh_desc* desc, imex_ctx** out) {
-  if (!desc || !out) return IMEX_EINVAL;
-  *out = nullptr;
-  const int d = desc->dim;
-  if (d != 2 && d != 3) return IMEX_EINVAL;
-  if (desc->P < 2 || desc->P > IMEX_MAXN - 1) return IMEX_EINVAL;
-  for (int k = 0; k < d; ++k) {
-    if (desc->nelem[k] < 1) return IMEX_EINVAL;
-    if (!(desc->hi[k] > desc->lo[k])) return IMEX_EINVAL;
-  }
-  if (desc->precision != IMEX_FP64 && desc->precision != IMEX_MIXED) return IMEX_EINVAL;
-  if (desc->poisson != IMEX_POISSON_SIPG && desc->poisson != IMEX_POISSON_CONSISTENT) return IMEX_EINVAL;
-  imex_ctx* c = new imex_ctx();
-  c->desc = *desc;
-  if (c->desc.tol <= 0) c->desc.tol = 1e-12;
-  if (c->desc.maxit <= 0) c->desc.maxit = 5000;
-  c->d = d;
-  c->Nv = desc->P + 1;
-  c->Np = desc->P;
-  long long ne = 1;
-  Geom g{};
-  g.d = d;
-  for (int k = 0; k < 3; ++k) {
-    g.n[k] = (k < d) ? desc->nelem[k] : 1;
-    g.lo[k] = (k < d) ? desc->lo[k] : 0.0;
-    g.h[k] = (k < d) ? (desc->hi[k] - desc->lo[k]) / desc->nelem[k] : 1.0;
-    g.hf[k] = (float)g.h[k];
-    ne *= g.n[k];
-  }
-  if (ne > (1LL << 30)) { delete c; return IMEX_EINVAL; }
-  g.ne = (int)ne;
-  c->gv = g;
-  c->gp = g;
-  for (int k = 0; k < 3; ++k) {
-    const bool per = (k >= d) || desc->periodic[k];
-    c->gv.bc[k] = per ? 0 : 1;
-    c->gp.bc[k] = per ? 0 : 2;
-  }
-  c->nv = (size_t)ne * ipow(c->Nv, d);
-  c->np = (size_t)ne * ipow(c->Np, d);
-  if (desc->stream) {
-    c->st = (cudaStream_t)desc->stream;
-  } else {
-    if (cudaStreamCreateWithFlags(&c->st, cudaStreamNonBlocking) != cudaSuccess) { delete c; return IMEX_ECUDA; }
-    c->own_stream = true;
-  }
+// Device state of a context whose geometry (gv, gp, nv, np, stream) and instance list are
+// set: tables, line operators, work vectors, CG systems, mass diagonals, stage storage.
+imex_status init_ctx(imex_ctx* c) {
+  const int d = c->d;
+  const Geom& g = c->gv;
   imex_status s = IMEX_OK;
-  auto bail = [&](imex_status e) {
-    imex_destroy(c);
-    return e;
-  };
+  auto bail = [&](imex_status e) { return e; };
   // tables
   {
     Tables<double>* h64 = new Tables<double>();
@@ -1296,7 +1205,7 @@ imex_status imex_create(const imex_mesh_desc* desc, imex_ctx** out) {
     if (s == IMEX_OK && cudaMemcpy(c->dtab32, h32, sizeof(*h32), cudaMemcpyHostToDevice) != cudaSuccess) s = IMEX_ECUDA;
     if (s == IMEX_OK) init_const_lines(*h64);
     if (s == IMEX_OK) {
-      double hh[3] = {g.h[0], g.h[1], g.h[2]};
+      const double hh[3] = {1.0, 1.0, 1.0};      // unit-size line operators, scaled per element
       LineOps<double>* o64 = new LineOps<double>();
       LineOps<float>* o32 = new LineOps<float>();
       const int Ns[2] = {c->Nv, c->Np};
@@ -1317,6 +1226,21 @@ imex_status imex_create(const imex_mesh_desc* desc, imex_ctx** out) {
     if (s != IMEX_OK) return bail(s);
     c->gv.tab64 = c->gp.tab64 = c->dtab64;
     c->gv.tab32 = c->gp.tab32 = c->dtab32;
+  }
+  if (c->batched) {
+    // per-instance geometry and the instance of every element
+    std::vector<int> ei(g.ne);
+    for (size_t i = 0; i < c->inst.size(); ++i)
+      for (int e = 0; e < c->inst[i].ne; ++e) ei[c->inst[i].e0 + e] = (int)i;
+    if ((s = dalloc(c, &c->inst_d, c->inst.size())) != IMEX_OK) return bail(s);
+    if ((s = dalloc(c, &c->elem_inst_d, (size_t)g.ne)) != IMEX_OK) return bail(s);
+    if ((s = dalloc(c, &c->edt, (size_t)g.ne)) != IMEX_OK) return bail(s);
+    if (cudaMemcpy(c->inst_d, c->inst.data(), c->inst.size() * sizeof(InstGeom), cudaMemcpyHostToDevice) !=
+            cudaSuccess ||
+        cudaMemcpy(c->elem_inst_d, ei.data(), ei.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess)
+      return bail(IMEX_ECUDA);
+    c->gv.inst = c->gp.inst = c->inst_d;
+    c->gv.elem_inst = c->gp.elem_inst = c->elem_inst_d;
   }
   const size_t nt = c->nv * d;
   const size_t big = std::max(nt, c->np);
@@ -1346,13 +1270,24 @@ imex_status imex_create(const imex_mesh_desc* desc, imex_ctx** out) {
   if (cudaMallocHost((void**)&c->hscal, 128 * sizeof(double)) != cudaSuccess) return bail(IMEX_ENOMEM);
   if (cudaMallocHost((void**)&c->hiscal, 64 * sizeof(int)) != cudaSuccess) return bail(IMEX_ENOMEM);
   {
-    // CG systems: the pressure (one system) and the d velocity components
-    const long long offp = 0, lenp = (long long)c->np;
-    long long offv[3], doffv[3] = {0, 0, 0}, lenv[3];
-    for (int k = 0; k < d; ++k) { offv[k] = (long long)(k * c->nv); lenv[k] = (long long)c->nv; }
-    if ((s = make_seg(c, 1, &offp, &offp, &lenp, &c->segp)) != IMEX_OK) return bail(s);
-    if ((s = make_seg(c, d, offv, doffv, lenv, &c->segv)) != IMEX_OK) return bail(s);
-    c->maxsys = d;
+    // CG systems: the pressure of each instance, and each velocity component of each
+    // instance (component-major); the Jacobi diagonal of the velocity is shared by the
+    // components of an instance
+    const int ni = (int)c->inst.size();
+    const long long ndv = ipow(c->Nv, d), ndp = ipow(c->Np, d);
+    std::vector<long long> offp(ni), lenp(ni), offv(d * ni), doffv(d * ni), lenv(d * ni);
+    for (int i = 0; i < ni; ++i) {
+      offp[i] = c->inst[i].e0 * ndp;
+      lenp[i] = c->inst[i].ne * ndp;
+      for (int k = 0; k < d; ++k) {
+        offv[k * ni + i] = (long long)(k * c->nv) + c->inst[i].e0 * ndv;
+        doffv[k * ni + i] = c->inst[i].e0 * ndv;
+        lenv[k * ni + i] = c->inst[i].ne * ndv;
+      }
+    }
+    if ((s = make_seg(c, ni, offp.data(), offp.data(), lenp.data(), &c->segp)) != IMEX_OK) return bail(s);
+    if ((s = make_seg(c, d * ni, offv.data(), doffv.data(), lenv.data(), &c->segv)) != IMEX_OK) return bail(s);
+    c->maxsys = d * ni;
     const int nblk = std::max(c->segp.t.nblk, c->segv.t.nblk);
     if ((s = dalloc(c, &c->seg_partial, (size_t)5 * nblk + 64)) != IMEX_OK) return bail(s);
     if ((s = dalloc(c, &c->cg_d, (size_t)12 * c->maxsys)) != IMEX_OK) return bail(s);
@@ -1373,9 +1308,204 @@ imex_status imex_create(const imex_mesh_desc* desc, imex_ctx** out) {
     SipgArgs<double> b = sipg_args<double>(nullptr, c->mass_p, 1, (long long)c->np, nullptr, 0.0, nullptr, 1.0, 0.0, 0);
     if (sipg_diag<double>(c->gp, c->Np, b, c->st) != 0) return bail(IMEX_EINVAL);
   }
-  named_tableau("CB3e", &c->tab);
-  if ((s = alloc_stages(c, c->tab.s)) != IMEX_OK) return bail(s);
+  if ((s = alloc_stages(c, 4)) != IMEX_OK) return bail(s);
   if (cudaStreamSynchronize(c->st) != cudaSuccess || cudaGetLastError() != cudaSuccess) return bail(IMEX_ECUDA);
+  return IMEX_OK;
+}
+
+
+// ---- batches ------------------------------------------------------------------------
+// Two instances can share a batch group when every setting that is not per-instance matches:
+// space (d, P, periodicity), precision, solvers, model kinds and the time integrator.
+bool same_group(const imex_ctx* a, const imex_ctx* b) {
+  if (a->d != b->d || a->Nv != b->Nv) return false;
+  for (int k = 0; k < a->d; ++k)
+    if ((a->desc.periodic[k] != 0) != (b->desc.periodic[k] != 0)) return false;
+  if (a->desc.precision != b->desc.precision || a->desc.poisson != b->desc.poisson) return false;
+  if (a->desc.tol != b->desc.tol || a->desc.maxit != b->desc.maxit || a->desc.vmax != b->desc.vmax) return false;
+  if (a->nu_kind != b->nu_kind || a->bc_kind != b->bc_kind || a->f_kind != b->f_kind) return false;
+  if (a->use_sdc || b->use_sdc) return false;
+  return std::memcmp(&a->tab, &b->tab, sizeof(Tab)) == 0;
+}
+
+// The union-mesh context of a batch group: the instances' elements concatenated in the
+// given order, each vector field stored [component][union element][node], so that every
+// operator is one launch over all instances and each CG system (an instance's pressure, or
+// one velocity component of an instance) a segment of the union vectors.
+imex_status create_union(const std::vector<imex_ctx*>& src, imex_ctx** out) {
+  const imex_ctx* s0 = src[0];
+  imex_ctx* c = new imex_ctx();
+  c->desc = s0->desc;
+  c->desc.stream = nullptr;
+  c->d = s0->d;
+  c->Nv = s0->Nv;
+  c->Np = s0->Np;
+  c->batched = true;
+  c->tab = s0->tab;
+  c->nu_kind = s0->nu_kind;
+  c->bc_kind = s0->bc_kind;
+  c->f_kind = s0->f_kind;
+  std::memcpy(c->nu_p, s0->nu_p, sizeof(c->nu_p));
+  std::memcpy(c->bc_p, s0->bc_p, sizeof(c->bc_p));
+  std::memcpy(c->f_p, s0->f_p, sizeof(c->f_p));
+  long long ne = 0;
+  for (const imex_ctx* x : src) {
+    InstGeom I{};
+    I.e0 = (int)ne;
+    I.ne = x->gv.ne;
+    for (int k = 0; k < 3; ++k) {
+      I.n[k] = x->gv.n[k];
+      I.lo[k] = x->gv.lo[k];
+      I.h[k] = x->gv.h[k];
+      I.hf[k] = x->gv.hf[k];
+    }
+    I.nu0 = x->nu_p[0];
+    I.nu0f = (float)x->nu_p[0];
+    I.dt = 0.0;
+    I.t = x->t;
+    std::memcpy(I.nu_p, x->nu_p, sizeof(I.nu_p));
+    std::memcpy(I.bc_p, x->bc_p, sizeof(I.bc_p));
+    std::memcpy(I.f_p, x->f_p, sizeof(I.f_p));
+    c->inst.push_back(I);
+    ne += x->gv.ne;
+  }
+  if (ne > (1LL << 30)) {
+    delete c;
+    return IMEX_EINVAL;
+  }
+  c->gv = s0->gv;
+  c->gp = s0->gp;
+  c->gv.ne = c->gp.ne = (int)ne;
+  c->nv = (size_t)ne * ipow(c->Nv, c->d);
+  c->np = (size_t)ne * ipow(c->Np, c->d);
+  if (cudaStreamCreateWithFlags(&c->st, cudaStreamNonBlocking) != cudaSuccess) {
+    delete c;
+    return IMEX_ECUDA;
+  }
+  c->own_stream = true;
+  imex_status s = init_ctx(c);
+  if (s == IMEX_OK) s = alloc_stages(c, c->tab.s);
+  // the instances' current fields, re-laid out per component
+  const size_t ndv = ipow(c->Nv, c->d), ndp = ipow(c->Np, c->d);
+  for (size_t i = 0; i < src.size() && s == IMEX_OK; ++i) {
+    imex_ctx* x = src[i];
+    if (cudaStreamSynchronize(x->st) != cudaSuccess) s = IMEX_ECUDA;
+    for (int k = 0; k < c->d && s == IMEX_OK; ++k)
+      if (cudaMemcpyAsync(c->v + k * c->nv + c->inst[i].e0 * ndv, x->v + k * x->nv, x->nv * sizeof(double),
+                          cudaMemcpyDeviceToDevice, c->st) != cudaSuccess)
+        s = IMEX_ECUDA;
+    if (s == IMEX_OK && cudaMemcpyAsync(c->psi + c->inst[i].e0 * ndp, x->psi, x->np * sizeof(double),
+                                        cudaMemcpyDeviceToDevice, c->st) != cudaSuccess)
+      s = IMEX_ECUDA;
+  }
+  if (s == IMEX_OK && cudaStreamSynchronize(c->st) != cudaSuccess) s = IMEX_ECUDA;
+  if (s != IMEX_OK) {
+    imex_destroy(c);
+    return s;
+  }
+  *out = c;
+  return IMEX_OK;
+}
+
+// per-instance time steps of a group: the instance table and the per-element step
+imex_status set_group_dt(imex_ctx* c, const std::vector<double>& dt) {
+  std::vector<double> edt(c->gv.ne);
+  for (size_t i = 0; i < c->inst.size(); ++i) {
+    c->inst[i].dt = dt[i];
+    c->inst[i].dtf = (float)dt[i];
+    for (int e = 0; e < c->inst[i].ne; ++e) edt[c->inst[i].e0 + e] = dt[i];
+  }
+  CK(cudaMemcpyAsync(c->edt, edt.data(), edt.size() * sizeof(double), cudaMemcpyHostToDevice, c->st), "cp dt");
+  CK(cudaMemcpyAsync(c->inst_d, c->inst.data(), c->inst.size() * sizeof(InstGeom), cudaMemcpyHostToDevice, c->st),
+     "cp inst");
+  CK(cudaStreamSynchronize(c->st), "sync");
+  return IMEX_OK;
+}
+
+// one step of every instance of a group, each with its own time step
+imex_status group_step(imex_ctx* c) {
+  TRY(rk_step(c, c->tab, c->v, 0.0, 1.0, variable_nu(c)));
+  for (auto& I : c->inst) I.t += I.dt;
+  CK(cudaMemcpyAsync(c->inst_d, c->inst.data(), c->inst.size() * sizeof(InstGeom), cudaMemcpyHostToDevice, c->st),
+     "cp inst");
+  c->stats.steps++;
+  TRY(check_state(c));
+  return IMEX_OK;
+}
+
+}  // namespace
+
+// =====================================================================================
+// C ABI
+// =====================================================================================
+extern "C" {
+
+imex_status imex_create(const imex_mesh_desc* desc, imex_ctx** out) {
+  if (!desc || !out) return IMEX_EINVAL;
+  *out = nullptr;
+  const int d = desc->dim;
+  if (d != 2 && d != 3) return IMEX_EINVAL;
+  if (desc->P < 2 || desc->P > IMEX_MAXN - 1) return IMEX_EINVAL;
+  for (int k = 0; k < d; ++k) {
+    if (desc->nelem[k] < 1) return IMEX_EINVAL;
+    if (!(desc->hi[k] > desc->lo[k])) return IMEX_EINVAL;
+  }
+  if (desc->precision != IMEX_FP64 && desc->precision != IMEX_MIXED) return IMEX_EINVAL;
+  if (desc->poisson != IMEX_POISSON_SIPG && desc->poisson != IMEX_POISSON_CONSISTENT) return IMEX_EINVAL;
+  imex_ctx* c = new imex_ctx();
+  c->desc = *desc;
+  if (c->desc.tol <= 0) c->desc.tol = 1e-12;
+  if (c->desc.maxit <= 0) c->desc.maxit = 5000;
+  c->d = d;
+  c->Nv = desc->P + 1;
+  c->Np = desc->P;
+  long long ne = 1;
+  Geom g{};
+  g.idt = 1.0;
+  g.idtf = 1.f;
+  g.d = d;
+  for (int k = 0; k < 3; ++k) {
+    g.n[k] = (k < d) ? desc->nelem[k] : 1;
+    g.lo[k] = (k < d) ? desc->lo[k] : 0.0;
+    g.h[k] = (k < d) ? (desc->hi[k] - desc->lo[k]) / desc->nelem[k] : 1.0;
+    g.hf[k] = (float)g.h[k];
+    ne *= g.n[k];
+  }
+  if (ne > (1LL << 30)) { delete c; return IMEX_EINVAL; }
+  g.ne = (int)ne;
+  c->gv = g;
+  c->gp = g;
+  for (int k = 0; k < 3; ++k) {
+    const bool per = (k >= d) || desc->periodic[k];
+    c->gv.bc[k] = per ? 0 : 1;
+    c->gp.bc[k] = per ? 0 : 2;
+  }
+  c->nv = (size_t)ne * ipow(c->Nv, d);
+  c->np = (size_t)ne * ipow(c->Np, d);
+  if (desc->stream) {
+    c->st = (cudaStream_t)desc->stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&c->st, cudaStreamNonBlocking) != cudaSuccess) { delete c; return IMEX_ECUDA; }
+    c->own_stream = true;
+  }
+  InstGeom I{};
+  I.e0 = 0;
+  I.ne = g.ne;
+  for (int k = 0; k < 3; ++k) {
+    I.n[k] = g.n[k];
+    I.lo[k] = g.lo[k];
+    I.h[k] = g.h[k];
+    I.hf[k] = g.hf[k];
+  }
+  I.dt = 1.0;
+  I.dtf = 1.f;
+  c->inst.push_back(I);
+  const imex_status s = init_ctx(c);
+  if (s != IMEX_OK) {
+    imex_destroy(c);
+    return s;
+  }
+  named_tableau("CB3e", &c->tab);
   *out = c;
   return IMEX_OK;
 }
@@ -1724,6 +1854,152 @@ imex_status imex_profile_read(imex_ctx* c, int cls, long long* launches, double*
 }
 
 long long imex_launch_count(void) { return imex::launch_count(); }
+
+
+// ---- batches of instances --------------------------------------------------------------
+struct imex_batch {
+  std::vector<imex_ctx*> groups;
+  std::vector<std::vector<int>> members;   // per group: the caller's instance indices
+  std::vector<int> grp, loc;               // per instance: group and position in it
+  std::string err;
+  imex_stats stats{};
+};
+
+imex_status imex_batch_create(imex_ctx* const* insts, int n, imex_batch** out) {
+  if (!insts || n <= 0 || !out) return IMEX_EINVAL;
+  *out = nullptr;
+  for (int i = 0; i < n; ++i) {
+    if (!insts[i] || insts[i]->batched) return IMEX_EINVAL;
+    if (insts[i]->use_sdc || insts[i]->nu_kind == IMEX_NU_FIELD) return IMEX_EINVAL;
+    if (has_boundary(insts[i]) && insts[i]->bc_kind == IMEX_FLOW_NONE) return IMEX_EINVAL;
+  }
+  imex_batch* b = new imex_batch();
+  b->grp.assign(n, -1);
+  b->loc.assign(n, -1);
+  for (int i = 0; i < n; ++i) {
+    int g = -1;
+    for (size_t q = 0; q < b->members.size() && g < 0; ++q)
+      if (same_group(insts[b->members[q][0]], insts[i])) g = (int)q;
+    if (g < 0) {
+      g = (int)b->members.size();
+      b->members.emplace_back();
+    }
+    b->grp[i] = g;
+    b->loc[i] = (int)b->members[g].size();
+    b->members[g].push_back(i);
+  }
+  for (auto& m : b->members) {
+    std::vector<imex_ctx*> src;
+    for (int i : m) src.push_back(insts[i]);
+    imex_ctx* c = nullptr;
+    const imex_status s = create_union(src, &c);
+    if (s != IMEX_OK) {
+      imex_batch_destroy(b);
+      return s;
+    }
+    b->groups.push_back(c);
+  }
+  *out = b;
+  return IMEX_OK;
+}
+
+void imex_batch_destroy(imex_batch* b) {
+  if (!b) return;
+  for (imex_ctx* c : b->groups) imex_destroy(c);
+  delete b;
+}
+
+const char* imex_batch_last_error(const imex_batch* b) { return b ? b->err.c_str() : "null batch"; }
+
+int imex_batch_groups(const imex_batch* b) { return b ? (int)b->groups.size() : 0; }
+
+imex_status imex_batch_step(imex_batch* b, const double* dt, int nsteps) {
+  if (!b || !dt || nsteps < 0) return IMEX_EINVAL;
+  const int n = (int)b->grp.size();
+  for (int i = 0; i < n; ++i)
+    if (!(dt[i] > 0)) return IMEX_EINVAL;
+  auto t0 = std::chrono::steady_clock::now();
+  // the groups run concurrently, each from its own host thread on its own stream
+  std::vector<imex_status> st(b->groups.size(), IMEX_OK);
+  auto run = [&](size_t q) {
+    imex_ctx* c = b->groups[q];
+    std::vector<double> gdt;
+    for (int i : b->members[q]) gdt.push_back(dt[i]);
+    c->stats.poisson_solves = c->stats.helmholtz_solves = 0;
+    c->stats.poisson_iters = c->stats.helmholtz_iters = 0;
+    c->stats.refinements = 0;
+    c->stats.max_poisson_res = c->stats.max_helmholtz_res = 0.0;
+    imex_status s = set_group_dt(c, gdt);
+    for (int k = 0; k < nsteps && s == IMEX_OK; ++k) s = group_step(c);
+    if (s == IMEX_OK && cudaStreamSynchronize(c->st) != cudaSuccess) s = IMEX_ECUDA;
+    st[q] = s;
+  };
+  if (b->groups.size() == 1) {
+    run(0);
+  } else {
+    std::vector<std::thread> th;
+    for (size_t q = 0; q < b->groups.size(); ++q) th.emplace_back(run, q);
+    for (auto& t : th) t.join();
+  }
+  imex_stats tot{};
+  imex_status res = IMEX_OK;
+  for (size_t q = 0; q < b->groups.size(); ++q) {
+    const imex_stats& g = b->groups[q]->stats;
+    tot.steps = std::max(tot.steps, g.steps);
+    tot.stages += g.stages;
+    tot.poisson_solves += g.poisson_solves;
+    tot.helmholtz_solves += g.helmholtz_solves;
+    tot.poisson_iters += g.poisson_iters;
+    tot.helmholtz_iters += g.helmholtz_iters;
+    tot.refinements += g.refinements;
+    tot.max_poisson_res = std::max(tot.max_poisson_res, g.max_poisson_res);
+    tot.max_helmholtz_res = std::max(tot.max_helmholtz_res, g.max_helmholtz_res);
+    tot.max_velocity = std::max(tot.max_velocity, g.max_velocity);
+    if (st[q] != IMEX_OK && res == IMEX_OK) {
+      res = st[q];
+      b->err = "group " + std::to_string(q) + ": " + b->groups[q]->err;
+    }
+  }
+  tot.last_call_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  b->stats = tot;
+  return res;
+}
+
+imex_status imex_batch_get_velocity(imex_batch* b, int i, double* out, int on_device) {
+  if (!b || !out || i < 0 || i >= (int)b->grp.size()) return IMEX_EINVAL;
+  imex_ctx* c = b->groups[b->grp[i]];
+  const InstGeom& I = c->inst[b->loc[i]];
+  const size_t ndv = ipow(c->Nv, c->d);
+  const size_t n = (size_t)I.ne * ndv;
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  for (int k = 0; k < c->d; ++k)
+    if (cudaMemcpyAsync(out + k * n, c->v + k * c->nv + I.e0 * ndv, n * sizeof(double), kind, c->st) != cudaSuccess)
+      return IMEX_ECUDA;
+  return cudaStreamSynchronize(c->st) == cudaSuccess ? IMEX_OK : IMEX_ECUDA;
+}
+
+imex_status imex_batch_get_pressure(imex_batch* b, int i, double* out, int on_device) {
+  if (!b || !out || i < 0 || i >= (int)b->grp.size()) return IMEX_EINVAL;
+  imex_ctx* c = b->groups[b->grp[i]];
+  const InstGeom& I = c->inst[b->loc[i]];
+  const size_t ndp = ipow(c->Np, c->d);
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  if (cudaMemcpyAsync(out, c->psi + I.e0 * ndp, (size_t)I.ne * ndp * sizeof(double), kind, c->st) != cudaSuccess)
+    return IMEX_ECUDA;
+  return cudaStreamSynchronize(c->st) == cudaSuccess ? IMEX_OK : IMEX_ECUDA;
+}
+
+imex_status imex_batch_get_time(const imex_batch* b, int i, double* t) {
+  if (!b || !t || i < 0 || i >= (int)b->grp.size()) return IMEX_EINVAL;
+  *t = b->groups[b->grp[i]]->inst[b->loc[i]].t;
+  return IMEX_OK;
+}
+
+imex_status imex_batch_get_stats(const imex_batch* b, imex_stats* out) {
+  if (!b || !out) return IMEX_EINVAL;
+  *out = b->stats;
+  return IMEX_OK;
+}
 
 }  // extern "C"
 

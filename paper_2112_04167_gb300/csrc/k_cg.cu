@@ -446,6 +446,27 @@ seg_sum_kernel(const double* __restrict__ x, SegTable t, double* __restrict__ ou
   seg_totals<1>(t, partial, [&](int q, const double* tot) { out[q] = tot[0] / (double)t.len[q]; });
   if (threadIdx.x == 0) *counter = 0u;
 }
+// weighted mean per segment: out[q] = sum w x / sum w
+__global__ void __launch_bounds__(CG_THREADS)
+seg_wsum_kernel(const double* __restrict__ x, const double* __restrict__ w, SegTable t, double* __restrict__ out,
+                double* __restrict__ partial, unsigned int* __restrict__ counter) {
+  const SegBlock c = chunk_of(t);
+  double acc[2] = {0.0, 0.0};
+  for (int i = threadIdx.x; i < c.n; i += CG_THREADS) {
+    const double wi = w[c.doff + i];
+    acc[0] += wi * x[c.off + i];
+    acc[1] += wi;
+  }
+  double bs[2];
+  block_sum_k<double, 2>(acc, bs);
+  if (threadIdx.x == 0) {
+    partial[blockIdx.x] = bs[0];
+    partial[(size_t)t.nblk + blockIdx.x] = bs[1];
+  }
+  if (!last_block(counter)) return;
+  seg_totals<2>(t, partial, [&](int q, const double* tot) { out[q] = tot[1] != 0.0 ? tot[0] / tot[1] : 0.0; });
+  if (threadIdx.x == 0) *counter = 0u;
+}
 __global__ void __launch_bounds__(CG_THREADS)
 seg_sub_kernel(double* __restrict__ x, SegTable t, const double* __restrict__ mean) {
   const SegBlock c = chunk_of(t);
@@ -482,6 +503,12 @@ void seg_init(const T* r, const T* dinv, const SegTable& t, const CgScalars& sc,
 void seg_remove_mean(double* x, const SegTable& t, double* mean, double* partial, unsigned int* counter,
                      cudaStream_t st) {
   IMEX_COUNTED(seg_sum_kernel<<<t.nblk, CG_THREADS, 0, st>>>(x, t, mean, partial, counter));
+  IMEX_COUNTED(seg_sub_kernel<<<t.nblk, CG_THREADS, 0, st>>>(x, t, mean));
+}
+
+void seg_remove_wmean(double* x, const double* w, const SegTable& t, double* mean, double* partial,
+                      unsigned int* counter, cudaStream_t st) {
+  IMEX_COUNTED(seg_wsum_kernel<<<t.nblk, CG_THREADS, 0, st>>>(x, w, t, mean, partial, counter));
   IMEX_COUNTED(seg_sub_kernel<<<t.nblk, CG_THREADS, 0, st>>>(x, t, mean));
 }
 

@@ -97,11 +97,13 @@ __global__ void dg_div_kernel(Geom g, DivArgs<T> a) {
   for (int i = threadIdx.x; i < NV * NP; i += blockDim.x) { sIp[i] = tb.Ipv[NV][i]; sGp[i] = tb.Gpv[NV][i]; }
   for (int i = threadIdx.x; i < NV; i += blockDim.x) sw[i] = tb.w[NV][i];
   const int e = blockIdx.x;
+  int el = 0;
+  const Geom gl = local_geom(g, e, el);
   int ec[3];
-  elem_coords(g, e, ec);
+  elem_coords(gl, el, ec);
   __syncthreads();
   T jac = T(1);
-  for (int k = 0; k < D; ++k) jac *= T(g.h[k]) * T(0.5);
+  for (int k = 0; k < D; ++k) jac *= T(gl.h[k]) * T(0.5);
   for (int node = threadIdx.x; node < ND; node += blockDim.x) {
     int id[3] = {node % NV, (D > 1) ? (node / NV) % NV : 0, (D > 2) ? node / (NV * NV) : 0};
     T Wq = jac;
@@ -112,9 +114,9 @@ __global__ void dg_div_kernel(Geom g, DivArgs<T> a) {
       buf[(1 + k) * ND + node] = Wq * vk;
       for (int side = 0; side < 2; ++side) {
         if (id[k] != (side ? NV - 1 : 0)) continue;
-        const int nb = neighbor(g, ec, k, side ? 1 : -1);
+        const int nb = neighbor(gl, ec, k, side ? 1 : -1);
         const T n = side ? T(1) : T(-1);
-        T Wf = jac / (T(g.h[k]) * T(0.5));
+        T Wf = jac / (T(gl.h[k]) * T(0.5));
         for (int j = 0; j < D; ++j) if (j != k) Wf *= sw[id[j]];
         T cflux = T(0);
         if (nb >= 0) {
@@ -138,7 +140,7 @@ __global__ void dg_div_kernel(Geom g, DivArgs<T> a) {
   for (int m = 0; m < D; ++m) {
     T* src = buf + (size_t)cur * (D + 1) * ND;
     T* dst = buf + (size_t)(1 - cur) * (D + 1) * ND;
-    const T hm = T(2) / T(g.h[m]);
+    const T hm = T(2) / T(gl.h[m]);
     contract2<T, D>(src, src + (1 + m) * ND, hm, dst, sz, m, NP, sIp, sGp, threadIdx.x, blockDim.x);
     for (int k = m + 1; k < D; ++k)
       contract2<T, D>(src + (1 + k) * ND, (const T*)nullptr, T(0), dst + (1 + k) * ND, sz, m, NP, sIp,
@@ -170,14 +172,16 @@ __global__ void dg_grad_kernel(Geom g, GradArgs<T> a) {
   for (int i = threadIdx.x; i < NV * NP; i += blockDim.x) { sIp[i] = tb.Ipv[NV][i]; sGp[i] = tb.Gpv[NV][i]; }
   for (int i = threadIdx.x; i < NV; i += blockDim.x) sw[i] = tb.w[NV][i];
   const int e = blockIdx.x;
+  int el = 0;
+  const Geom gl = local_geom(g, e, el);
   int ec[3];
-  elem_coords(g, e, ec);
+  elem_coords(gl, el, ec);
   for (int i = threadIdx.x; i < NDP; i += blockDim.x) sp[i] = a.psi[(size_t)e * NDP + i];
   __syncthreads();
   // pressure jumps on the pressure face grid: own - neighbour, interior faces only
   for (int t = threadIdx.x; t < 2 * D * NFP; t += blockDim.x) {
     const int fi = t / NFP, f = t % NFP, k = fi >> 1, side = fi & 1;
-    const int nb = neighbor(g, ec, k, side ? 1 : -1);
+    const int nb = neighbor(gl, ec, k, side ? 1 : -1);
     int c[3] = {0, 0, 0};
     face_coords<D>(f, k, NP, c);
     if (nb >= 0) {
@@ -226,7 +230,7 @@ __global__ void dg_grad_kernel(Geom g, GradArgs<T> a) {
       in = bufs[cur];
       cur ^= 1;
     }
-    const T hk = T(2) / T(g.h[k]);
+    const T hk = T(2) / T(gl.h[k]);
     for (int node = threadIdx.x; node < ND; node += blockDim.x) {
       int id[3] = {node % NV, (D > 1) ? (node / NV) % NV : 0, (D > 2) ? node / (NV * NV) : 0};
       T val = hk * in[node];
@@ -281,12 +285,14 @@ __global__ void __launch_bounds__(ipow(N, D)) dg_deriv_kernel(Geom g, DerivArgs<
   for (int i = threadIdx.x; i < N * N; i += blockDim.x) sD[i] = tb.D[N][i];
   for (int i = threadIdx.x; i < N; i += blockDim.x) sw[i] = tb.w[N][i];
   const int e = blockIdx.x;
+  int el = 0;
+  const Geom gl = local_geom(g, e, el);
   const int node = threadIdx.x;
   int ec[3];
-  elem_coords(g, e, ec);
+  elem_coords(gl, el, ec);
   int id[3] = {node % N, (D > 1) ? (node / N) % N : 0, (D > 2) ? node / (N * N) : 0};
   const size_t o = (size_t)e * ND + node;
-  const T nu = a.nu ? a.nu[o] : a.nu0;
+  const T nu = a.nu ? a.nu[o] : (a.inst_nu ? geom_nu0<T>(gl) : a.nu0);
   // op 3 runs one output component per pass over its d input fields
   const int passes = (a.op == 3) ? D : 1;
   for (int c3 = 0; c3 < passes; ++c3) {
@@ -299,21 +305,21 @@ __global__ void __launch_bounds__(ipow(N, D)) dg_deriv_kernel(Geom g, DerivArgs<
     if (a.op == 0) {
       T s = T(0);
       for (int k = 0; k < D; ++k)
-        s += nodal_deriv<T, D, N>(g, ec, e, id, node, k, su[k], a.in + (size_t)k * a.stride, sD, wend);
+        s += nodal_deriv<T, D, N>(gl, ec, e, id, node, k, su[k], a.in + (size_t)k * a.stride, sD, wend);
       a.out[o] = nu * s;
     } else if (a.op == 1) {
       for (int c = 0; c < D; ++c)
         a.out[(size_t)c * a.stride + o] =
-            a.coef * nodal_deriv<T, D, N>(g, ec, e, id, node, c, su[0], a.in, sD, wend);
+            a.coef * nodal_deriv<T, D, N>(gl, ec, e, id, node, c, su[0], a.in, sD, wend);
     } else if (a.op == 2) {
       for (int c = 0; c < D; ++c)
         for (int k = 0; k < D; ++k)
           a.out[(size_t)(c * D + k) * a.stride + o] =
-              nu * nodal_deriv<T, D, N>(g, ec, e, id, node, c, su[k], a.in + (size_t)k * a.stride, sD, wend);
+              nu * nodal_deriv<T, D, N>(gl, ec, e, id, node, c, su[k], a.in + (size_t)k * a.stride, sD, wend);
     } else {
       T s = T(0);
       for (int k = 0; k < D; ++k)
-        s += nodal_deriv<T, D, N>(g, ec, e, id, node, k, su[k], a.in + (size_t)(f0 + k) * a.stride, sD, wend);
+        s += nodal_deriv<T, D, N>(gl, ec, e, id, node, k, su[k], a.in + (size_t)(f0 + k) * a.stride, sD, wend);
       a.out[(size_t)c3 * a.stride + o] += a.coef * s;
     }
   }
@@ -360,8 +366,10 @@ __global__ void dg_conv_kernel(Geom g, ConvArgs<T> a) {
   for (int i = threadIdx.x; i < Q; i += blockDim.x) sgw[i] = tb.gw[N][i];
   for (int i = threadIdx.x; i < N; i += blockDim.x) sw[i] = tb.w[N][i];
   const int e = blockIdx.x;
+  int el = 0;
+  const Geom gl = local_geom(g, e, el);
   int ec[3];
-  elem_coords(g, e, ec);
+  elem_coords(gl, el, ec);
   for (int c = 0; c < D; ++c)
     for (int i = threadIdx.x; i < ND; i += blockDim.x) {
       sv[c * ND + i] = a.v[(size_t)c * a.stride + (size_t)e * ND + i];
@@ -370,7 +378,7 @@ __global__ void dg_conv_kernel(Geom g, ConvArgs<T> a) {
   __syncthreads();
   const int t = threadIdx.x, nt = blockDim.x;
   T jac = T(1);
-  for (int k = 0; k < D; ++k) jac *= T(g.h[k]) * T(0.5);
+  for (int k = 0; k < D; ++k) jac *= T(gl.h[k]) * T(0.5);
   // --- interpolate v to the Gauss points
   for (int c = 0; c < D; ++c) {
     int sz[3] = {N, D > 1 ? N : 1, D > 2 ? N : 1};
@@ -389,7 +397,7 @@ __global__ void dg_conv_kernel(Geom g, ConvArgs<T> a) {
   // --- volume term: acc_c += sum_k (test derivative in k) [W_g v_c v_k]
   for (int c = 0; c < D; ++c) {
     for (int k = 0; k < D; ++k) {
-      const T hk = T(2) / T(g.h[k]);                 // derivative scale of the test function
+      const T hk = T(2) / T(gl.h[k]);                 // derivative scale of the test function
       for (int q = t; q < NQ; q += nt) {
         int r = q;
         T W = jac * hk;
@@ -419,7 +427,7 @@ __global__ void dg_conv_kernel(Geom g, ConvArgs<T> a) {
   // --- face terms
   for (int k = 0; k < D; ++k) {
     for (int side = 0; side < 2; ++side) {
-      const int nb = neighbor(g, ec, k, side ? 1 : -1);
+      const int nb = neighbor(gl, ec, k, side ? 1 : -1);
       const T n = side ? T(1) : T(-1);
       // traces on the N^{D-1} face nodes -> interpolate tangentially to Q^{D-1}
       for (int c = 0; c < D; ++c) {
@@ -476,7 +484,7 @@ __global__ void dg_conv_kernel(Geom g, ConvArgs<T> a) {
       // LLF flux per component, weighted, projected back onto the face nodes
       for (int c = 0; c < D; ++c) {
         for (int q = t; q < NFQ; q += nt) {
-          T W = jac / (T(g.h[k]) * T(0.5));
+          T W = jac / (T(gl.h[k]) * T(0.5));
           int r = q;
           for (int j = 0; j < D - 1; ++j) { W *= sgw[r % Q]; r /= Q; }
           const T vmn = n * fm[k * NFQ + q];

@@ -74,12 +74,21 @@ __global__ void field_kernel(Geom g, int what, FieldSpec fs, double t, const dou
   const size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   if (idx >= (size_t)g.ne * ND) return;
   const int e = (int)(idx / ND), node = (int)(idx % ND);
+  int el = 0;
+  const Geom gl = local_geom(g, e, el);
   int ec[3];
-  elem_coords(g, e, ec);
+  elem_coords(gl, el, ec);
   int id[3] = {node % N, (D > 1) ? (node / N) % N : 0, (D > 2) ? node / (N * N) : 0};
   const double* xi = tab<double>(g).x[N];
   double X[3] = {0, 0, 0};
-  for (int k = 0; k < D; ++k) X[k] = g.lo[k] + (ec[k] + 0.5 * (xi[id[k]] + 1.0)) * g.h[k];
+  for (int k = 0; k < D; ++k) X[k] = gl.lo[k] + (ec[k] + 0.5 * (xi[id[k]] + 1.0)) * gl.h[k];
+  // batched meshes: the instance's own parameters, and t read as a fraction of its time step
+  if (g.inst) {
+    const InstGeom& I = g.inst[g.elem_inst[e]];
+    const double* ip = what == 0 ? I.bc_p : (what == 1 ? I.nu_p : I.f_p);
+    for (int j = 0; j < 8; ++j) fs.p[j] = ip[j];
+    t = I.t + t * I.dt;
+  }
   if (what == 0) {
     double u[3];
     flow_velocity(fs.kind, fs.p, X, t, D, u);

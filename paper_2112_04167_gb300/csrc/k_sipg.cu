@@ -113,8 +113,11 @@ sipg_apply_kernel(Geom g, SipgArgs<T> a) {
   const int node = threadIdx.x % ND;
   const int e = blockIdx.x * EPB + le;
   const bool valid = e < g.ne;
+  int el = 0;
+  Geom gl = g;
+  if (valid) gl = local_geom(g, e, el);
   int ec[3] = {0, 0, 0};
-  if (valid) elem_coords(g, e, ec);
+  if (valid) elem_coords(gl, el, ec);
   int id[3];
   id[0] = node % N;
   id[1] = (D > 1) ? (node / N) % N : 0;
@@ -123,15 +126,15 @@ sipg_apply_kernel(Geom g, SipgArgs<T> a) {
   // neighbours (-1: boundary)
   if (valid && node < 2 * D) {
     const int k = node >> 1, side = node & 1;
-    snb[le][node] = neighbor(g, ec, k, side ? 1 : -1);
+    snb[le][node] = neighbor(gl, ec, k, side ? 1 : -1);
   }
   // viscosity of the element
-  if (valid) snu[le][node] = a.nu ? a.nu[(size_t)e * ND + node] : a.nu0;
+  if (valid) snu[le][node] = a.nu ? a.nu[(size_t)e * ND + node] : sipg_nu0(a, gl);
   __syncthreads();
 
   T hinv2[D];
   T jac = T(1);
-  for (int k = 0; k < D; ++k) { hinv2[k] = T(2) / geom_h<T>(g, k); jac *= geom_h<T>(g, k) * T(0.5); }
+  for (int k = 0; k < D; ++k) { hinv2[k] = T(2) / geom_h<T>(gl, k); jac *= geom_h<T>(gl, k) * T(0.5); }
   T Wq = jac;
   for (int k = 0; k < D; ++k) Wq *= sw[id[k]];
 
@@ -151,7 +154,7 @@ sipg_apply_kernel(Geom g, SipgArgs<T> a) {
       if (nb >= 0) {
         c[k] = side ? 0 : N - 1;                       // matching face of the neighbour
         int nn = c[0] + N * ((D > 1 ? c[1] : 0) + N * (D > 2 ? c[2] : 0));
-        sfnu[le][fi][f] = a.nu ? a.nu[(size_t)nb * ND + nn] : a.nu0;
+        sfnu[le][fi][f] = a.nu ? a.nu[(size_t)nb * ND + nn] : sipg_nu0(a, gl);
       } else {
         c[k] = side ? N - 1 : 0;
         int nn = c[0] + N * ((D > 1 ? c[1] : 0) + N * (D > 2 ? c[2] : 0));
@@ -226,7 +229,7 @@ sipg_apply_kernel(Geom g, SipgArgs<T> a) {
           const int nb = snb[le][fi];
           const int bc = g.bc[k];
           if (nb < 0 && bc != 1) continue;                 // Neumann: no face terms
-          T Wf = jac / (geom_h<T>(g, k) * T(0.5));
+          T Wf = jac / (geom_h<T>(gl, k) * T(0.5));
           int f = 0, mul = 1;
           for (int j = 0; j < D; ++j) {
             if (j == k) continue;
@@ -263,7 +266,7 @@ sipg_apply_kernel(Geom g, SipgArgs<T> a) {
         for (int q = 0; q < N; ++q) acc += sD[q * N + id[k]] * sQ[k][le][base + q * stride];
         yv += acc * hinv2[k];
       }
-      T out = a.alpha * Wq * su[le][node] + a.beta * yv;
+      T out = a.alpha * Wq * su[le][node] + sipg_beta(a, gl) * yv;
       if (a.minv) out /= Wq;
       y[(size_t)e * ND + node] = out;
     }
@@ -332,22 +335,25 @@ sipg3_apply_kernel(Geom g, SipgArgs<T> a) {
   const int i0 = t % N, i1 = t / N;
   const int e = blockIdx.x * EPB + le;
   const bool valid = e < g.ne;
+  int el = 0;
+  Geom gl = g;
+  if (valid) gl = local_geom(g, e, el);
   int ec[3] = {0, 0, 0};
-  if (valid) elem_coords(g, e, ec);
-  if (valid && t < 6) snb[le][t] = neighbor(g, ec, t >> 1, (t & 1) ? 1 : -1);
+  if (valid) elem_coords(gl, el, ec);
+  if (valid && t < 6) snb[le][t] = neighbor(gl, ec, t >> 1, (t & 1) ? 1 : -1);
   __syncthreads();
 
-  const T hx = T(2) / geom_h<T>(g, 0), hy = T(2) / geom_h<T>(g, 1), hz = T(2) / geom_h<T>(g, 2);
-  const T jac = geom_h<T>(g, 0) * geom_h<T>(g, 1) * geom_h<T>(g, 2) * T(0.125);
-  const T jfx = geom_h<T>(g, 1) * geom_h<T>(g, 2) * T(0.25), jfy = geom_h<T>(g, 0) * geom_h<T>(g, 2) * T(0.25),
-          jfz = geom_h<T>(g, 0) * geom_h<T>(g, 1) * T(0.25);
+  const T hx = T(2) / geom_h<T>(gl, 0), hy = T(2) / geom_h<T>(gl, 1), hz = T(2) / geom_h<T>(gl, 2);
+  const T jac = geom_h<T>(gl, 0) * geom_h<T>(gl, 1) * geom_h<T>(gl, 2) * T(0.125);
+  const T jfx = geom_h<T>(gl, 1) * geom_h<T>(gl, 2) * T(0.25), jfy = geom_h<T>(gl, 0) * geom_h<T>(gl, 2) * T(0.25),
+          jfz = geom_h<T>(gl, 0) * geom_h<T>(gl, 1) * T(0.25);
   const T penx = T(N * N) * T(0.5) * hx, peny = T(N * N) * T(0.5) * hy, penz = T(N * N) * T(0.5) * hz;
   const size_t ebase = (size_t)e * ND;
 
   // own viscosity column (constant viscosity: one register)
   T nuc[VARNU ? N : 1];
 #pragma unroll
-  for (int k = 0; k < (VARNU ? N : 1); ++k) nuc[k] = (VARNU && valid) ? a.nu[ebase + k * NN + t] : a.nu0;
+  for (int k = 0; k < (VARNU ? N : 1); ++k) nuc[k] = (VARNU && valid) ? a.nu[ebase + k * NN + t] : sipg_nu0(a, gl);
   // face kinds: 0 none (Neumann), 1 interior, 2 Dirichlet
   int kind[6];
 #pragma unroll
@@ -374,7 +380,7 @@ sipg3_apply_kernel(Geom g, SipgArgs<T> a) {
       for (int fi = 0; fi < 4; ++fi) {
         const int dir = fi >> 1, side = fi & 1;
         const int nb = snb[le][fi];
-        T tr = T(0), dv = T(0), nn = a.nu0;
+        T tr = T(0), dv = T(0), nn = sipg_nu0(a, gl);
         if (nb >= 0) {
           const int iface = side ? 0 : N - 1;                    // neighbour's index on the shared face
           const size_t nbase = (size_t)nb * ND + kk * NN;
@@ -404,7 +410,7 @@ sipg3_apply_kernel(Geom g, SipgArgs<T> a) {
       }
     }
     // z-faces: the neighbour columns through this thread's (i0, i1)
-    T zu[2] = {T(0), T(0)}, zd[2] = {T(0), T(0)}, zn[2] = {a.nu0, a.nu0};
+    T zu[2] = {T(0), T(0)}, zd[2] = {T(0), T(0)}, zn[2] = {sipg_nu0(a, gl), sipg_nu0(a, gl)};
     if (valid) {
 #pragma unroll
       for (int side = 0; side < 2; ++side) {
@@ -476,7 +482,7 @@ sipg3_apply_kernel(Geom g, SipgArgs<T> a) {
         }
         const T W = jac * wxy * sw[k];
         const T yv = yf[k] + hx * ax + hy * ay + hz * az;
-        T out = a.alpha * W * u[k] + a.beta * yv;
+        T out = a.alpha * W * u[k] + sipg_beta(a, gl) * yv;
         if (a.minv) out /= W;
         y[ebase + k * NN + t] = out;
       }
@@ -535,9 +541,12 @@ sipg3c_apply_kernel(Geom g, SipgArgs<T> a) {
   const int i0 = t % N, i1 = t / N;
   const int e = blockIdx.x * EPB + le;
   const bool valid = e < g.ne;
+  int el = 0;
+  Geom gl = g;
+  if (valid) gl = local_geom(g, e, el);
   int ec[3] = {0, 0, 0};
-  if (valid) elem_coords(g, e, ec);
-  if (valid && t < 6) snb[le][t] = neighbor(g, ec, t >> 1, (t & 1) ? 1 : -1);
+  if (valid) elem_coords(gl, el, ec);
+  if (valid && t < 6) snb[le][t] = neighbor(gl, ec, t >> 1, (t & 1) ? 1 : -1);
   __syncthreads();
   int kind[6];
 #pragma unroll
@@ -546,7 +555,7 @@ sipg3c_apply_kernel(Geom g, SipgArgs<T> a) {
     kind[f] = nb >= 0 ? 1 : (g.bc[f >> 1] == 1 ? 2 : 0);
   }
   const size_t ebase = (size_t)e * ND;
-  const T scale = a.beta * a.nu0;
+  const T scale = sipg_beta(a, gl) * sipg_nu0(a, gl);
   __shared__ double red[S::THREADS];
   for (int s = 0; s < a.nsys; ++s) {
     const T* x = a.x + (size_t)s * a.sys_stride;
@@ -615,7 +624,10 @@ sipg3c_apply_kernel(Geom g, SipgArgs<T> a) {
       const T cyr0 = sC[((1 * 2 + 1) * 3 + kind[3]) * 2 * N + i1], cyr1 = sC[(((1 * 2 + 1) * 3 + kind[3]) * 2 + 1) * N + i1];
       const T* czl = sC + ((2 * 2 + 0) * 3 + kind[4]) * 2 * N;
       const T* czr = sC + ((2 * 2 + 1) * 3 + kind[5]) * 2 * N;
-      const T wx = sWt[i0], wy = sWt[N + i1];
+      // unit-size line operators: direction k scales as 1 / h_k, its weights as h_k
+      const T hx = geom_h<T>(gl, 0), hy = geom_h<T>(gl, 1), hz = geom_h<T>(gl, 2);
+      const T ihx = T(1) / hx, ihy = T(1) / hy, ihz = T(1) / hz;
+      const T wx = hx * sWt[i0], wy = hy * sWt[N + i1];
 #pragma unroll
       for (int k = 0; k < N; ++k) {
         const T* plane = &su[le][k * NN];
@@ -630,9 +642,9 @@ sipg3c_apply_kernel(Geom g, SipgArgs<T> a) {
         yx += cxl0 * sf[le][0][fx] + cxl1 * sf[le][1][fx] + cxr0 * sf[le][2][fx] + cxr1 * sf[le][3][fx];
         yy += cyl0 * sf[le][4][fy] + cyl1 * sf[le][5][fy] + cyr0 * sf[le][6][fy] + cyr1 * sf[le][7][fy];
         yz += czl[k] * zt[0] + czl[N + k] * zd[0] + czr[k] * zt[1] + czr[N + k] * zd[1];
-        const T wz = sWt[2 * N + k];
+        const T wz = hz * sWt[2 * N + k];
         const T W = wx * wy * wz;
-        const T yv = wy * wz * yx + wx * wz * yy + wx * wy * yz;
+        const T yv = wy * wz * ihx * yx + wx * wz * ihy * yy + wx * wy * ihz * yz;
         T out = a.alpha * W * u[k] + scale * yv;
         if (a.minv) out /= W;
         y[ebase + k * NN + t] = out;
@@ -690,9 +702,12 @@ sipg2c_apply_kernel(Geom g, SipgArgs<T> a) {
   const int i0 = t % N, i1 = t / N;
   const int e = blockIdx.x * EPB + le;
   const bool valid = e < g.ne;
+  int el = 0;
+  Geom gl = g;
+  if (valid) gl = local_geom(g, e, el);
   int ec[3] = {0, 0, 0};
-  if (valid) elem_coords(g, e, ec);
-  if (valid && t < 4) snb[le][t] = neighbor(g, ec, t >> 1, (t & 1) ? 1 : -1);
+  if (valid) elem_coords(gl, el, ec);
+  if (valid && t < 4) snb[le][t] = neighbor(gl, ec, t >> 1, (t & 1) ? 1 : -1);
   __syncthreads();
   int kind[4];
 #pragma unroll
@@ -701,7 +716,7 @@ sipg2c_apply_kernel(Geom g, SipgArgs<T> a) {
     kind[f] = nb >= 0 ? 1 : (g.bc[f >> 1] == 1 ? 2 : 0);
   }
   const size_t ebase = (size_t)e * NN;
-  const T scale = a.beta * a.nu0;
+  const T scale = sipg_beta(a, gl) * sipg_nu0(a, gl);
   __shared__ double red[S::THREADS];
   for (int s = 0; s < a.nsys; ++s) {
     const T* x = a.x + (size_t)s * a.sys_stride;
@@ -751,9 +766,11 @@ sipg2c_apply_kernel(Geom g, SipgArgs<T> a) {
             sC[(((1 * 2 + 0) * 3 + kind[2]) * 2 + 1) * N + i1] * sf[le][5][i0] +
             sC[((1 * 2 + 1) * 3 + kind[3]) * 2 * N + i1] * sf[le][6][i0] +
             sC[(((1 * 2 + 1) * 3 + kind[3]) * 2 + 1) * N + i1] * sf[le][7][i0];
-      const T wx = sWt[i0], wy = sWt[N + i1];
+      // unit-size line operators: direction k scales as 1 / h_k, its weights as h_k
+      const T hx = geom_h<T>(gl, 0), hy = geom_h<T>(gl, 1);
+      const T wx = hx * sWt[i0], wy = hy * sWt[N + i1];
       const T W = wx * wy;
-      T out = a.alpha * W * uo + scale * (wy * yx + wx * yy);
+      T out = a.alpha * W * uo + scale * (wy * yx / hx + wx * yy / hy);
       if (a.minv) out /= W;
       y[ebase + t] = out;
       dacc = uo * out;
@@ -820,15 +837,18 @@ sipg3p_apply_kernel(Geom g, SipgArgs<T> a) {
   const int i0 = t % N, i1 = t / N;
   const int e = blockIdx.x * EPB + le;
   const bool valid = e < g.ne;
+  int el = 0;
+  Geom gl = g;
+  if (valid) gl = local_geom(g, e, el);
   int ec[3] = {0, 0, 0};
   int nb[6] = {0, 0, 0, 0, 0, 0};
   if (valid) {
-    elem_coords(g, e, ec);
+    elem_coords(gl, el, ec);
 #pragma unroll
-    for (int f = 0; f < 6; ++f) nb[f] = neighbor(g, ec, f >> 1, (f & 1) ? 1 : -1);
+    for (int f = 0; f < 6; ++f) nb[f] = neighbor(gl, ec, f >> 1, (f & 1) ? 1 : -1);
   }
-  const T ihx = T(1) / geom_h<T>(g, 0), ihy = T(1) / geom_h<T>(g, 1), ihz = T(1) / geom_h<T>(g, 2);
-  const T hx2 = T(0.5) * geom_h<T>(g, 0), hy2 = T(0.5) * geom_h<T>(g, 1), hz2 = T(0.5) * geom_h<T>(g, 2);
+  const T ihx = T(1) / geom_h<T>(gl, 0), ihy = T(1) / geom_h<T>(gl, 1), ihz = T(1) / geom_h<T>(gl, 2);
+  const T hx2 = T(0.5) * geom_h<T>(gl, 0), hy2 = T(0.5) * geom_h<T>(gl, 1), hz2 = T(0.5) * geom_h<T>(gl, 2);
   // this thread's rows of the x and y line operators and neighbour coefficients
   T ax[N], ay[N];
 #pragma unroll
@@ -837,7 +857,7 @@ sipg3p_apply_kernel(Geom g, SipgArgs<T> a) {
   const T cyl0 = L.ctrL[i1], cyl1 = L.cdnL[i1], cyr0 = L.ctrR[i1], cyr1 = L.cdnR[i1];
   const T wx = hx2 * L.w[i0], wy = hy2 * L.w[i1];
   const size_t ebase = (size_t)e * ND;
-  const T scale = a.beta * a.nu0;
+  const T scale = sipg_beta(a, gl) * sipg_nu0(a, gl);
   T* mytile = tile + le * TILE;
   __shared__ double red[S::THREADS];
   for (int s = 0; s < a.nsys; ++s) {
@@ -996,19 +1016,22 @@ sipg_diag_kernel(Geom g, SipgArgs<T> a) {
   const int node = threadIdx.x % ND;
   const int e = blockIdx.x * EPB + le;
   const bool valid = e < g.ne;
-  if (valid) snu[le][node] = a.nu ? a.nu[(size_t)e * ND + node] : a.nu0;
+  int el = 0;
+  Geom gl = g;
+  if (valid) gl = local_geom(g, e, el);
+  if (valid) snu[le][node] = a.nu ? a.nu[(size_t)e * ND + node] : sipg_nu0(a, gl);
   __syncthreads();
   if (!valid) return;
   (void)NF;
   int ec[3];
-  elem_coords(g, e, ec);
+  elem_coords(gl, el, ec);
   int id[3];
   id[0] = node % N;
   id[1] = (D > 1) ? (node / N) % N : 0;
   id[2] = (D > 2) ? node / (N * N) : 0;
   T hinv2[D];
   T jac = T(1);
-  for (int k = 0; k < D; ++k) { hinv2[k] = T(2) / geom_h<T>(g, k); jac *= geom_h<T>(g, k) * T(0.5); }
+  for (int k = 0; k < D; ++k) { hinv2[k] = T(2) / geom_h<T>(gl, k); jac *= geom_h<T>(gl, k) * T(0.5); }
   T Wq = jac;
   for (int k = 0; k < D; ++k) Wq *= sw[id[k]];
   const T nuq = snu[le][node];
@@ -1028,9 +1051,9 @@ sipg_diag_kernel(Geom g, SipgArgs<T> a) {
     diag += acc;
     for (int side = 0; side < 2; ++side) {
       if (id[k] != (side ? N - 1 : 0)) continue;
-      const int nb = neighbor(g, ec, k, side ? 1 : -1);
+      const int nb = neighbor(gl, ec, k, side ? 1 : -1);
       if (nb < 0 && g.bc[k] != 1) continue;
-      T Wf = jac / (geom_h<T>(g, k) * T(0.5));
+      T Wf = jac / (geom_h<T>(gl, k) * T(0.5));
       for (int j = 0; j < D; ++j) if (j != k) Wf *= sw[id[j]];
       const T n = side ? T(1) : T(-1);
       const T dself = n * sD[id[k] * N + id[k]] * hinv2[k];   // d(e_j)/dn at its own face node
@@ -1039,14 +1062,14 @@ sipg_diag_kernel(Geom g, SipgArgs<T> a) {
         int c[3] = {id[0], id[1], id[2]};
         c[k] = side ? 0 : N - 1;
         const int nn = c[0] + N * ((D > 1 ? c[1] : 0) + N * (D > 2 ? c[2] : 0));
-        const T nun = a.nu ? a.nu[(size_t)nb * ND + nn] : a.nu0;
+        const T nun = a.nu ? a.nu[(size_t)nb * ND + nn] : sipg_nu0(a, gl);
         diag += -Wf * nuq * dself + Wf * pen * (nuq > nun ? nuq : nun);
       } else {
         diag += -T(2) * Wf * nuq * dself + Wf * T(2) * pen * nuq;
       }
     }
   }
-  a.y[(size_t)e * ND + node] = a.alpha * Wq + a.beta * diag;
+  a.y[(size_t)e * ND + node] = a.alpha * Wq + sipg_beta(a, gl) * diag;
 }
 
 template <typename T, int D, int N>

@@ -19,8 +19,16 @@ long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
 __global__ void lincomb_kernel(double* __restrict__ out, LinComb lc, size_t n) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
     double s = 0.0;
+    if (lc.edt) {
+      double u = 0.0;
+      for (int j = 0; j < lc.nfixed; ++j) s += lc.c[j] * lc.x[j][i];
 #pragma unroll 4
-    for (int j = 0; j < lc.nterms; ++j) s += lc.c[j] * lc.x[j][i];
+      for (int j = lc.nfixed; j < lc.nterms; ++j) u += lc.c[j] * lc.x[j][i];
+      s += lc.edt[(i % (size_t)lc.cstride) / (size_t)lc.nd] * u;
+    } else {
+#pragma unroll 4
+      for (int j = 0; j < lc.nterms; ++j) s += lc.c[j] * lc.x[j][i];
+    }
     out[i] = s;
   }
 }

@@ -32,7 +32,20 @@ struct SipgArgs {
   double* cg_alpha;
   float* cg_alpha_f;
   int* cg_done;
+  // batched meshes: take the constant viscosity from each element's instance instead of nu0
+  // (inst_nu), and multiply beta by the instance's time step (inst_dt)
+  int inst_nu;
+  int inst_dt;
 };
+
+template <typename T>
+__device__ __forceinline__ T sipg_nu0(const SipgArgs<T>& a, const Geom& gl) {
+  return a.inst_nu ? geom_nu0<T>(gl) : a.nu0;
+}
+template <typename T>
+__device__ __forceinline__ T sipg_beta(const SipgArgs<T>& a, const Geom& gl) {
+  return a.inst_dt ? a.beta * geom_dt<T>(gl) : a.beta;
+}
 
 template <typename T> int sipg_apply(const Geom& g, int N, const SipgArgs<T>& a, cudaStream_t st);
 // constant-memory line operators of the periodic fast path (once per device)
@@ -78,6 +91,7 @@ struct DerivArgs {
   T nu0;
   T coef;
   T* out;
+  int inst_nu;     // batched meshes: constant viscosity of each element's instance
 };
 template <typename T> int dg_deriv(const Geom& g, int N, const DerivArgs<T>& a, cudaStream_t st);
 
@@ -99,6 +113,12 @@ struct LinComb {
   const double* x[IMEX_MAXTERMS];
   double c[IMEX_MAXTERMS];
   int nterms;
+  // batched meshes: terms j >= nfixed are also multiplied by the time step of the element
+  // holding entry i, edt[(i mod cstride) / nd] (edt == nullptr: no such factor)
+  const double* edt;
+  long long cstride;
+  int nd;
+  int nfixed;
 };
 // out[i] = c0 * x0[i] + sum c_j x_j[i]   (x0 may be out itself)
 void lincomb(double* out, const LinComb& lc, size_t n, cudaStream_t st);

@@ -75,5 +75,8 @@ void seg_init(const T* r, const T* dinv, const SegTable& t, const CgScalars& sc,
               unsigned int* counter, int reset, cudaStream_t st);
 void seg_remove_mean(double* x, const SegTable& t, double* mean, double* partial, unsigned int* counter,
                      cudaStream_t st);
+// x -= (sum w x / sum w) per segment; w indexed like the Jacobi diagonal (doff)
+void seg_remove_wmean(double* x, const double* w, const SegTable& t, double* mean, double* partial,
+                      unsigned int* counter, cudaStream_t st);
 
 }  // namespace imex

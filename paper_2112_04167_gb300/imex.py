@@ -84,6 +84,15 @@ _SIGS = {
     "imex_profile": [_P, C.c_int],
     "imex_profile_read": [_P, C.c_int, C.POINTER(C.c_longlong), _D],
     "imex_launch_count": [],
+    "imex_batch_create": [C.POINTER(_P), C.c_int, C.POINTER(_P)],
+    "imex_batch_destroy": [_P],
+    "imex_batch_last_error": [_P],
+    "imex_batch_groups": [_P],
+    "imex_batch_step": [_P, _D, C.c_int],
+    "imex_batch_get_velocity": [_P, C.c_int, _P, C.c_int],
+    "imex_batch_get_pressure": [_P, C.c_int, _P, C.c_int],
+    "imex_batch_get_time": [_P, C.c_int, _D],
+    "imex_batch_get_stats": [_P, C.POINTER(imex_stats)],
 }
 PROF_PRESSURE_F32, PROF_PRESSURE_F64, PROF_HELMHOLTZ_F32, PROF_HELMHOLTZ_F64, PROF_CONV = range(5)
 REDUCE_DOT, REDUCE_SUM, REDUCE_MAXABS = range(3)
@@ -128,8 +137,8 @@ def load(path=None):
     for name, args in _SIGS.items():
         f = getattr(lib, name)
         f.argtypes = args
-        f.restype = {"imex_last_error": C.c_char_p, "imex_destroy": None,
-                     "imex_launch_count": C.c_longlong}.get(name, C.c_int)
+        f.restype = {"imex_last_error": C.c_char_p, "imex_destroy": None, "imex_batch_last_error": C.c_char_p,
+                     "imex_batch_destroy": None, "imex_launch_count": C.c_longlong}.get(name, C.c_int)
     _lib = lib
     return lib
 
@@ -364,3 +373,69 @@ class Context:
         po, _, _b = _arr(out, ncomp * self.nvel, writable=True)
         self._check(load().imex_eval_field(self._h, what, kind, pp, n, t, pv, po, 0))
         return out
+
+
+class Batch:
+    """Instances advanced together (wraps imex_batch*): imex_batch_create groups the
+    contexts into union meshes; each step advances every instance by its own dt."""
+
+    def __init__(self, contexts):
+        lib = load()
+        n = len(contexts)
+        hs = (_P * n)(*[c._h for c in contexts])
+        self.sizes = [(c.dim, c.nvel, c.npres) for c in contexts]
+        h = _P()
+        st = lib.imex_batch_create(hs, n, C.byref(h))
+        if st != OK:
+            raise ImexError(st, "imex_batch_create failed")
+        self._h = h
+        self.n = n
+
+    def _check(self, st):
+        if st != OK:
+            raise ImexError(st, load().imex_batch_last_error(self._h).decode())
+
+    @property
+    def groups(self):
+        return int(load().imex_batch_groups(self._h))
+
+    def step(self, dt, nsteps=1):
+        arr = np.ascontiguousarray(np.broadcast_to(np.asarray(dt, dtype=np.float64), (self.n,)))
+        self._check(load().imex_batch_step(self._h, arr.ctypes.data_as(_D), nsteps))
+
+    def get_velocity(self, i, out=None):
+        d, nv, _ = self.sizes[i]
+        if out is None:
+            out = np.empty(d * nv)
+        p, dev, _k = _arr(out, d * nv, writable=True)
+        self._check(load().imex_batch_get_velocity(self._h, i, p, dev))
+        return out
+
+    def get_pressure(self, i, out=None):
+        _, _, npr = self.sizes[i]
+        if out is None:
+            out = np.empty(npr)
+        p, dev, _k = _arr(out, npr, writable=True)
+        self._check(load().imex_batch_get_pressure(self._h, i, p, dev))
+        return out
+
+    def time(self, i):
+        t = C.c_double()
+        self._check(load().imex_batch_get_time(self._h, i, C.byref(t)))
+        return t.value
+
+    def stats(self):
+        s = imex_stats()
+        self._check(load().imex_batch_get_stats(self._h, C.byref(s)))
+        return s.as_dict()
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().imex_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -11,7 +11,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 def _declared():
     src = open(os.path.join(ROOT, "include", "imex.h")).read()
-    pat = r"^\s*(?:imex_status|void|const char\*|long long)\s+(imex_\w+)\s*\("
+    pat = r"^\s*(?:imex_status|void|const char\*|long long|int)\s+(imex_\w+)\s*\("
     return sorted(set(re.findall(pat, src, re.M)))
 
 
