@@ -235,6 +235,11 @@ imex_status imex_batch_get_pressure(imex_batch* b, int i, double* out, int on_de
 imex_status imex_batch_get_time(const imex_batch* b, int i, double* t);
 /* totals of the last imex_batch_step over all groups (steps: per instance) */
 imex_status imex_batch_get_stats(const imex_batch* b, imex_stats* out);
+/* group q (0 <= q < imex_batch_groups): its instance count, degree P, velocity nodes per
+   component of its union mesh, its stats and the wall time (ms) of its part of the last
+   imex_batch_step; any output pointer may be NULL */
+imex_status imex_batch_group_info(const imex_batch* b, int q, int* ninst, int* P, long long* nvel, imex_stats* st,
+                                  double* last_ms);
 
 #ifdef __cplusplus
 }

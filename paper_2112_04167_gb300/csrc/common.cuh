@@ -167,9 +167,16 @@ void build_tables(Tables<double>* t64, Tables<float>* t32);
 void build_line_ops(const Tables<double>& t, int N, const double* h, int d, LineOps<double>* o64,
                     LineOps<float>* o32);
 
-// number of kernels this library has launched (all contexts, all threads)
+// number of kernels this library has launched (all contexts, all threads); add_launches
+// accounts for the kernels of a CUDA-graph replay
 void count_launch();
+void add_launches(long long n);
 long long launch_count();
+long long thread_launch_count();     // launches issued by the calling thread
+
+// raise a kernel's dynamic shared-memory limit once per device (kept out of the launch path,
+// so that launches can be captured into CUDA graphs)
+void smem_limit_once(const void* kernel, int bytes);
 
 }  // namespace imex
 

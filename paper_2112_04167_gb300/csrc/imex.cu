@@ -10,6 +10,7 @@
 #include <climits>
 #include <cmath>
 #include <cstdio>
+#include <cstdint>
 #include <cstdlib>
 #include <cstring>
 #include <string>
@@ -213,6 +214,14 @@ struct imex_ctx {
   InstGeom* inst_d = nullptr;
   int* elem_inst_d = nullptr;
   double* edt = nullptr;        // per-element time step (batched)
+  // CUDA graphs of CG iteration chunks, keyed by everything their launches depend on
+  struct GraphEntry {
+    std::vector<unsigned long long> key;
+    cudaGraphExec_t exec;
+    long long nkern;
+  };
+  std::vector<GraphEntry> graphs;
+  bool use_graphs = true;
   imex_stats stats{};
   double last_res = 0.0;
   // CUDA-event timing of kernel classes
@@ -461,6 +470,51 @@ CgScalars scalars(imex_ctx* c, double tol, bool project) {
   return s;
 }
 
+// Enqueue body() -- kernel launches only, no host synchronisation -- as a CUDA graph cached
+// under key: the first call captures it, later calls replay it with one launch.
+template <typename F>
+imex_status run_graph(imex_ctx* c, const std::vector<unsigned long long>& key, F body) {
+  if (!c->use_graphs || c->prof) return body();
+  for (auto& g : c->graphs)
+    if (g.key == key) {
+      CK(cudaGraphLaunch(g.exec, c->st), "graph launch");
+      add_launches(g.nkern);
+      return IMEX_OK;
+    }
+  const long long l0 = thread_launch_count();
+  CK(cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal), "begin capture");
+  const imex_status s = body();
+  cudaGraph_t graph = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(c->st, &graph);
+  const long long nk = thread_launch_count() - l0;
+  add_launches(-nk);                                  // capturing launched nothing
+  if (s != IMEX_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return s;
+  }
+  CK(e, "end capture");
+  cudaGraphExec_t exec = nullptr;
+  const cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  CK(ei, "graph instantiate");
+  if (c->graphs.size() >= 16) {                       // bounded cache: drop the oldest graph
+    CK(cudaStreamSynchronize(c->st), "sync");
+    cudaGraphExecDestroy(c->graphs.front().exec);
+    c->graphs.erase(c->graphs.begin());
+  }
+  c->graphs.push_back({key, exec, nk});
+  CK(cudaGraphLaunch(exec, c->st), "graph launch");
+  add_launches(nk);
+  return IMEX_OK;
+}
+
+unsigned long long bits(double x) {
+  unsigned long long u;
+  std::memcpy(&u, &x, sizeof(u));
+  return u;
+}
+unsigned long long addr(const void* p) { return (unsigned long long)(uintptr_t)p; }
+
 // copy the per-system flags (done, iters) and the recursive rr, bb to the host mirrors
 imex_status pull_scalars(imex_ctx* c, int nsys) {
   const int m = c->maxsys;
@@ -477,7 +531,8 @@ imex_status pull_scalars(imex_ctx* c, int nsys) {
 // residual is projected onto the range and the preconditioned residual kept mean-free.
 template <typename Op, typename OpDot>
 imex_status pcg(imex_ctx* c, const imex_ctx::Seg& sg, Op op, OpDot op_dot, bool fused, const double* b, double* x,
-                const double* dinv, double tol, int maxit, bool project, long long* iters_out, double* res_out) {
+                const double* dinv, double tol, int maxit, bool project,
+                const std::vector<unsigned long long>& opkey, long long* iters_out, double* res_out) {
   const SegTable& t = sg.t;
   CgScalars sc = scalars(c, tol, project);
   const int nsys = t.nseg;
@@ -497,7 +552,10 @@ imex_status pcg(imex_ctx* c, const imex_ctx::Seg& sg, Op op, OpDot op_dot, bool 
   seg_step_p<double>(p, r, dinv, t, sc, 1, c->st);
   CK(cudaGetLastError(), "cg_init");
   const int chunk = 16;
-  for (int it = 0; it < maxit + chunk; it += chunk) {
+  std::vector<unsigned long long> key = {64,        addr(&sg), addr(x), addr(b), addr(dinv), (unsigned long long)fused,
+                                         (unsigned long long)maxit, bits(tol), (unsigned long long)project};
+  key.insert(key.end(), opkey.begin(), opkey.end());
+  auto body = [&]() -> imex_status {
     for (int k = 0; k < chunk; ++k) {
       if (fused) {
         TRY(op_dot(p, Ap, &sc));                    // A p, (p, A p) and alpha in one launch
@@ -508,6 +566,10 @@ imex_status pcg(imex_ctx* c, const imex_ctx::Seg& sg, Op op, OpDot op_dot, bool 
       seg_step_xr<double>(x, r, p, Ap, dinv, t, sc, maxit, c->seg_partial, c->counters + 1, c->st);
       seg_step_p<double>(p, r, dinv, t, sc, 0, c->st);
     }
+    return IMEX_OK;
+  };
+  for (int it = 0; it < maxit + chunk; it += chunk) {
+    TRY(run_graph(c, key, body));
     TRY(pull_scalars(c, nsys));
     bool all = true;
     for (int s = 0; s < nsys; ++s) all = all && c->cg_hi[s] != 0;
@@ -547,7 +609,7 @@ imex_status pcg(imex_ctx* c, const imex_ctx::Seg& sg, Op op, OpDot op_dot, bool 
 template <typename Op64, typename Op32, typename Op32Dot>
 imex_status pcg_mixed(imex_ctx* c, const imex_ctx::Seg& sg, Op64 op64, Op32 op32, Op32Dot op32dot, bool fused,
                       const double* b, double* x, const float* dinv, double tol, int maxit, bool project,
-                      long long* iters_out, double* res_out) {
+                      const std::vector<unsigned long long>& opkey, long long* iters_out, double* res_out) {
   const SegTable& t = sg.t;
   const size_t ntot = sg.total;
   CgScalars sc = scalars(c, tol, project);
@@ -618,10 +680,10 @@ imex_status pcg_mixed(imex_ctx* c, const imex_ctx::Seg& sg, Op64 op64, Op32 op32
   CK(cudaMemsetAsync(sc.iters, 0, nsys * sizeof(int), c->st), "memset");
   TRY(replace());
   const int chunk = 16;
-  for (int round = 0;; ++round) {
-    bool all = true;
-    for (int s = 0; s < nsys; ++s) all = all && done_h[s] == 4;
-    if (all) break;
+  std::vector<unsigned long long> key = {32, addr(&sg), addr(dinv), (unsigned long long)fused,
+                                         (unsigned long long)maxit, bits(tol), (unsigned long long)project};
+  key.insert(key.end(), opkey.begin(), opkey.end());
+  auto body = [&]() -> imex_status {
     for (int k = 0; k < chunk; ++k) {
       if (fused) {
         TRY(op32dot(p, Ap, &sc));
@@ -632,6 +694,13 @@ imex_status pcg_mixed(imex_ctx* c, const imex_ctx::Seg& sg, Op64 op64, Op32 op32
       seg_step_xr<float>(y, r, p, Ap, dinv, t, sc, maxit, c->seg_partial, c->counters + 1, c->st);
       seg_step_p<float>(p, r, dinv, t, sc, 0, c->st);
     }
+    return IMEX_OK;
+  };
+  for (int round = 0;; ++round) {
+    bool all = true;
+    for (int s = 0; s < nsys; ++s) all = all && done_h[s] == 4;
+    if (all) break;
+    TRY(run_graph(c, key, body));
     TRY(pull_scalars(c, nsys));
     bool need = false;
     for (int s = 0; s < nsys; ++s) {
@@ -702,7 +771,7 @@ imex_status solve_poisson(imex_ctx* c, double* b, double* psi, long long* iters,
       return apply_pressure<double>(c, x, y, c->tmp, d);
     };
     const bool fused = c->desc.poisson == IMEX_POISSON_SIPG && !c->batched;
-    imex_status s = pcg(c, c->segp, op, opd, fused, b, psi, c->cdiag, tol, c->desc.maxit, true, iters, res);
+    imex_status s = pcg(c, c->segp, op, opd, fused, b, psi, c->cdiag, tol, c->desc.maxit, true, {1}, iters, res);
     seg_remove_wmean(psi, c->mass_p, c->segp.t, c->cg_d + 6 * m, c->seg_partial, c->counters + 3, c->st);
     return s;
   }
@@ -713,7 +782,7 @@ imex_status solve_poisson(imex_ctx* c, double* b, double* psi, long long* iters,
     return apply_pressure<float>(c, x, y, c->fvtmp, d);
   };
   const bool fused = c->desc.poisson == IMEX_POISSON_SIPG && !c->batched;
-  TRY(pcg_mixed(c, c->segp, op64, op32, op32d, fused, b, psi, c->fdiag, tol, c->desc.maxit, true, iters, res));
+  TRY(pcg_mixed(c, c->segp, op64, op32, op32d, fused, b, psi, c->fdiag, tol, c->desc.maxit, true, {1}, iters, res));
   seg_remove_wmean(psi, c->mass_p, c->segp.t, c->cg_d + 6 * m, c->seg_partial, c->counters + 3, c->st);
   return IMEX_OK;
 }
@@ -731,12 +800,15 @@ imex_status solve_helmholtz(imex_ctx* c, const double* rhs, double* x, const dou
   TRY(launch_check(c, sipg_diag<double>(c->gv, c->Nv, a, c->st), "sipg_diag(v)"));
   reciprocal<double>(dg, n, c->st);
   const double tol = c->desc.tol;
+  // the chunk graphs depend on gamma and on whether the viscosity is a field
+  const std::vector<unsigned long long> hkey = {2, bits(gamma), addr(nu), (unsigned long long)d};
   if (c->desc.precision == IMEX_FP64) {
     auto op = [&](const double* xx, double* yy) { return apply_helm<double>(c, xx, yy, d, nu, gamma); };
     auto opd = [&](const double* xx, double* yy, const CgScalars* dd) {
       return apply_helm<double>(c, xx, yy, d, nu, gamma, dd);
     };
-    return pcg(c, c->segv, op, opd, nu == nullptr && !c->batched, rhs, x, dg, tol, c->desc.maxit, false, iters, res);
+    return pcg(c, c->segv, op, opd, nu == nullptr && !c->batched, rhs, x, dg, tol, c->desc.maxit, false,
+               hkey, iters, res);
   }
   convert_d2f(dg, fdg, n, c->st);
   const float* fnu = nullptr;
@@ -747,7 +819,7 @@ imex_status solve_helmholtz(imex_ctx* c, const double* rhs, double* x, const dou
     return apply_helm<float>(c, xx, yy, d, fnu, gamma, dd);
   };
   TRY(pcg_mixed(c, c->segv, op64, op32, op32d, fnu == nullptr && !c->batched, rhs, x, fdg, tol, c->desc.maxit, false,
-                iters, res));
+                hkey, iters, res));
   return IMEX_OK;
 }
 
@@ -1515,6 +1587,7 @@ void imex_destroy(imex_ctx* c) {
   if (c->st) cudaStreamSynchronize(c->st);
   for (auto& P : c->profc)
     for (auto& e : P.ev) cudaEventDestroy(e);
+  for (auto& g : c->graphs) cudaGraphExecDestroy(g.exec);
   for (void* p : c->allocs) cudaFree(p);
   if (c->hscal) cudaFreeHost(c->hscal);
   if (c->hiscal) cudaFreeHost(c->hiscal);
@@ -1861,6 +1934,7 @@ struct imex_batch {
   std::vector<imex_ctx*> groups;
   std::vector<std::vector<int>> members;   // per group: the caller's instance indices
   std::vector<int> grp, loc;               // per instance: group and position in it
+  std::vector<double> group_ms;            // per group: wall time of the last imex_batch_step
   std::string err;
   imex_stats stats{};
 };
@@ -1921,7 +1995,9 @@ imex_status imex_batch_step(imex_batch* b, const double* dt, int nsteps) {
   auto t0 = std::chrono::steady_clock::now();
   // the groups run concurrently, each from its own host thread on its own stream
   std::vector<imex_status> st(b->groups.size(), IMEX_OK);
+  b->group_ms.assign(b->groups.size(), 0.0);
   auto run = [&](size_t q) {
+    const auto g0 = std::chrono::steady_clock::now();
     imex_ctx* c = b->groups[q];
     std::vector<double> gdt;
     for (int i : b->members[q]) gdt.push_back(dt[i]);
@@ -1933,6 +2009,7 @@ imex_status imex_batch_step(imex_batch* b, const double* dt, int nsteps) {
     for (int k = 0; k < nsteps && s == IMEX_OK; ++k) s = group_step(c);
     if (s == IMEX_OK && cudaStreamSynchronize(c->st) != cudaSuccess) s = IMEX_ECUDA;
     st[q] = s;
+    b->group_ms[q] = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - g0).count();
   };
   if (b->groups.size() == 1) {
     run(0);
@@ -1998,6 +2075,18 @@ imex_status imex_batch_get_time(const imex_batch* b, int i, double* t) {
 imex_status imex_batch_get_stats(const imex_batch* b, imex_stats* out) {
   if (!b || !out) return IMEX_EINVAL;
   *out = b->stats;
+  return IMEX_OK;
+}
+
+imex_status imex_batch_group_info(const imex_batch* b, int q, int* ninst, int* P, long long* nvel, imex_stats* st,
+                                  double* last_ms) {
+  if (!b || q < 0 || q >= (int)b->groups.size()) return IMEX_EINVAL;
+  const imex_ctx* c = b->groups[q];
+  if (ninst) *ninst = (int)c->inst.size();
+  if (P) *P = c->Nv - 1;
+  if (nvel) *nvel = (long long)c->nv;
+  if (st) *st = c->stats;
+  if (last_ms) *last_ms = q < (int)b->group_ms.size() ? b->group_ms[q] : 0.0;
   return IMEX_OK;
 }
 

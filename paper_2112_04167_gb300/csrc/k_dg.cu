@@ -544,7 +544,7 @@ template <typename T, int D, int N>
 static void launch_div(const Geom& g, const DivArgs<T>& a, cudaStream_t st) {
   constexpr int ND = ipow(N, D);
   const size_t smem = sizeof(T) * (size_t)(2 * N * (N - 1) + N + 2 * (D + 1) * ND);
-  cudaFuncSetAttribute(dg_div_kernel<T, D, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  smem_limit_once((const void*)dg_div_kernel<T, D, N>, (int)smem);
   int threads = ND < 128 ? 128 : ((ND + 31) / 32) * 32;
   if (threads > 512) threads = 512;
   IMEX_COUNTED(dg_div_kernel<T, D, N><<<g.ne, threads, smem, st>>>(g, a));
@@ -562,8 +562,7 @@ static void launch_deriv(const Geom& g, const DerivArgs<T>& a, cudaStream_t st) 
 template <typename T, int D, int N>
 static void launch_conv(const Geom& g, const ConvArgs<T>& a, cudaStream_t st) {
   using S = ConvShape<T, D, N>;
-  cudaFuncSetAttribute(dg_conv_kernel<T, D, N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)S::SMEM);
+  smem_limit_once((const void*)dg_conv_kernel<T, D, N>, (int)S::SMEM);
   IMEX_COUNTED(dg_conv_kernel<T, D, N><<<g.ne, S::THREADS, S::SMEM, st>>>(g, a));
 }
 

@@ -1077,7 +1077,7 @@ static void launch_apply(const Geom& g, const SipgArgs<T>& a, cudaStream_t st) {
   if (D == 2 && !a.nu && a.ops) {
     using C = Sipg2cShape<N>;
     constexpr size_t sm = sipg2c_smem<T, N>();
-    cudaFuncSetAttribute(sipg2c_apply_kernel<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    smem_limit_once((const void*)sipg2c_apply_kernel<T, N>, (int)sm);
     IMEX_COUNTED(sipg2c_apply_kernel<T, N><<<(g.ne + C::EPB - 1) / C::EPB, C::THREADS, sm, st>>>(g, a));
     return;
   }
@@ -1091,14 +1091,14 @@ static void launch_apply3(const Geom& g, const SipgArgs<T>& a, cudaStream_t st) 
   if (!a.nu && a.ops && g.bc[0] == 0 && g.bc[1] == 0 && g.bc[2] == 0) {
     using P = Sipg3pShape<T, N>;
     constexpr size_t sm = sipg3p_smem<T, N>();
-    cudaFuncSetAttribute(sipg3p_apply_kernel<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    smem_limit_once((const void*)sipg3p_apply_kernel<T, N>, (int)sm);
     IMEX_COUNTED(sipg3p_apply_kernel<T, N><<<(g.ne + P::EPB - 1) / P::EPB, P::THREADS, sm, st>>>(g, a));
     return;
   }
   if (!a.nu && a.ops) {
     using C = Sipg3cShape<N>;
     constexpr size_t sm = sipg3c_smem<T, N>();
-    cudaFuncSetAttribute(sipg3c_apply_kernel<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    smem_limit_once((const void*)sipg3c_apply_kernel<T, N>, (int)sm);
     IMEX_COUNTED(sipg3c_apply_kernel<T, N><<<(g.ne + C::EPB - 1) / C::EPB, C::THREADS, sm, st>>>(g, a));
     return;
   }
@@ -1106,10 +1106,10 @@ static void launch_apply3(const Geom& g, const SipgArgs<T>& a, cudaStream_t st) 
   const int blocks = (g.ne + S::EPB - 1) / S::EPB;
   constexpr size_t smem = sipg3_smem<T, N>();
   if (a.nu) {
-    cudaFuncSetAttribute(sipg3_apply_kernel<T, N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    smem_limit_once((const void*)sipg3_apply_kernel<T, N, true>, (int)smem);
     IMEX_COUNTED(sipg3_apply_kernel<T, N, true><<<blocks, S::THREADS, smem, st>>>(g, a));
   } else {
-    cudaFuncSetAttribute(sipg3_apply_kernel<T, N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    smem_limit_once((const void*)sipg3_apply_kernel<T, N, false>, (int)smem);
     IMEX_COUNTED(sipg3_apply_kernel<T, N, false><<<blocks, S::THREADS, smem, st>>>(g, a));
   }
 }

@@ -4,6 +4,7 @@
 #include <atomic>
 #include <mutex>
 #include <type_traits>
+#include <vector>
 
 #include "../../include/imex.h"
 #include "common.cuh"
@@ -13,7 +14,25 @@
 namespace imex {
 
 static std::atomic<long long> g_launches{0};
-void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+static thread_local long long t_launches = 0;
+void count_launch() {
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  ++t_launches;
+}
+void add_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+long long thread_launch_count() { return t_launches; }
+
+void smem_limit_once(const void* kernel, int bytes) {
+  static std::mutex mu;
+  static std::vector<std::pair<const void*, int>> done;   // (kernel, device)
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lock(mu);
+  for (const auto& d : done)
+    if (d.first == kernel && d.second == dev) return;
+  cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  done.emplace_back(kernel, dev);
+}
 long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
 
 __global__ void lincomb_kernel(double* __restrict__ out, LinComb lc, size_t n) {

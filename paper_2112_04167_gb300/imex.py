@@ -93,6 +93,8 @@ _SIGS = {
     "imex_batch_get_pressure": [_P, C.c_int, _P, C.c_int],
     "imex_batch_get_time": [_P, C.c_int, _D],
     "imex_batch_get_stats": [_P, C.POINTER(imex_stats)],
+    "imex_batch_group_info": [_P, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_longlong),
+                              C.POINTER(imex_stats), _D],
 }
 PROF_PRESSURE_F32, PROF_PRESSURE_F64, PROF_HELMHOLTZ_F32, PROF_HELMHOLTZ_F64, PROF_CONV = range(5)
 REDUCE_DOT, REDUCE_SUM, REDUCE_MAXABS = range(3)
@@ -428,6 +430,15 @@ class Batch:
         s = imex_stats()
         self._check(load().imex_batch_get_stats(self._h, C.byref(s)))
         return s.as_dict()
+
+    def group_info(self, q):
+        n, P, nv, ms = C.c_int(), C.c_int(), C.c_longlong(), C.c_double()
+        st = imex_stats()
+        self._check(load().imex_batch_group_info(self._h, q, C.byref(n), C.byref(P), C.byref(nv), C.byref(st),
+                                                 C.byref(ms)))
+        return {"instances": n.value, "P": P.value, "nvel": nv.value, "last_ms": ms.value,
+                "poisson_iters": st.poisson_iters, "poisson_solves": st.poisson_solves,
+                "helmholtz_iters": st.helmholtz_iters}
 
     def close(self):
         if getattr(self, "_h", None):
