@@ -241,6 +241,58 @@ imex_status imex_batch_get_stats(const imex_batch* b, imex_stats* out);
 imex_status imex_batch_group_info(const imex_batch* b, int q, int* ninst, int* P, long long* nvel, imex_stats* st,
                                   double* last_ms);
 
+/* ---- Serving: continuous batching ----------------------------------------------------
+ * A server admits flow requests in arrival order while the estimated device footprint of
+ * the active ones stays within an HBM budget, keeps every active request's fields and
+ * solver state on the device in the union-mesh groups of the batched form, and advances all
+ * active requests by one step per imex_server_tick; finished requests leave and queued ones
+ * join between ticks (the groups' layouts are repacked on the device, no per-request
+ * allocation).  Requests use RK-CB3e (Alg. 3). */
+typedef struct imex_server imex_server;
+typedef struct {
+  double hbm_budget_bytes;  /* device bytes the active requests may occupy (<= 0: half the free memory) */
+  int precision;            /* IMEX_FP64 | IMEX_MIXED */
+  int poisson;              /* IMEX_POISSON_SIPG | IMEX_POISSON_CONSISTENT */
+  double tol;               /* solver tolerance (<= 0: 1e-10) */
+  int maxit;                /* (<= 0: 20000) */
+  double vmax;              /* instability threshold on max |v| (0: none) */
+  int keep_results;         /* 1: keep each finished request's velocity for imex_server_result */
+} imex_server_desc;
+typedef struct {
+  int dim, P;
+  int nelem[3];
+  double lo[3], hi[3];
+  int periodic[3];
+  int flow; double flow_params[8];   /* initial field (IMEX_FLOW_*) at t0 */
+  int nu_kind; double nu_params[8];  /* viscosity model (not IMEX_NU_FIELD) */
+  int bc_kind; double bc_params[8];  /* Dirichlet data on non-periodic sides */
+  int f_kind; double f_params[8];    /* forcing */
+  double t0, dt;
+  int nsteps;
+} imex_request;
+enum { IMEX_REQ_QUEUED = 0, IMEX_REQ_ACTIVE = 1, IMEX_REQ_DONE = 2, IMEX_REQ_FAILED = 3 };
+typedef struct {
+  long long submitted, completed, failed, active, queued, ticks;
+  double p50_tick_ms, p99_tick_ms, mean_tick_ms;  /* wall time of a tick: admission, repack, one step */
+  double dof_stages;                              /* velocity DOF x nontrivial stages advanced */
+  double busy_s;                                  /* summed tick wall time */
+  double footprint_bytes, max_footprint_bytes, budget_bytes;
+  int groups;
+} imex_server_stats;
+imex_status imex_server_create(const imex_server_desc* desc, imex_server** out);
+void imex_server_destroy(imex_server* sv);
+const char* imex_server_last_error(const imex_server* sv);
+/* queue a request (copied); id: its handle.  IMEX_EINVAL for an invalid mesh or model. */
+imex_status imex_server_submit(imex_server* sv, const imex_request* r, long long* id);
+/* admit, repack, one step of every active request; active: requests still running after it.
+   A group whose step fails marks its requests IMEX_REQ_FAILED (message: imex_server_last_error). */
+imex_status imex_server_tick(imex_server* sv, int* active);
+/* state (IMEX_REQ_*), steps done and time of a request */
+imex_status imex_server_poll(const imex_server* sv, long long id, int* state, int* steps_done, double* t);
+/* velocity of a finished request into host memory ([d][elements][nodes]); frees the copy */
+imex_status imex_server_result(imex_server* sv, long long id, double* velocity);
+imex_status imex_server_get_stats(const imex_server* sv, imex_server_stats* out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -13,6 +13,7 @@
 #include <cstdint>
 #include <cstdlib>
 #include <cstring>
+#include <deque>
 #include <string>
 #include <thread>
 #include <vector>
@@ -197,6 +198,10 @@ struct imex_ctx {
   struct Seg {
     SegTable t{};
     size_t total = 0;
+    int nseg_cap = 0, nblk_cap = 0;       // capacity of the device arrays below
+    long long *off_d = nullptr, *doff_d = nullptr;
+    int *len_d = nullptr, *bs_d = nullptr, *bl_d = nullptr, *b0_d = nullptr;
+    SegBlock* blk_d = nullptr;
   };
   Seg segp, segv;
   int maxsys = 0;
@@ -210,6 +215,8 @@ struct imex_ctx {
   // instances of the mesh: one for a plain context; several for the union mesh of a batch
   // group, whose kernels see per-element geometry, viscosity, time step and time
   bool batched = false;
+  long long ne_cap = 0;         // element and instance capacity of the buffers (>= current)
+  int ninst_cap = 0;
   std::vector<InstGeom> inst;
   InstGeom* inst_d = nullptr;
   int* elem_inst_d = nullptr;
@@ -294,9 +301,11 @@ imex_status dalloc(imex_ctx* c, T** p, size_t n) {
 #define CK(x, what) TRY(cuda_check(c, (x), what))
 
 // Segment table of nseg systems: system s occupies [off[s], off[s] + len[s]) of the CG
-// vectors and starts at doff[s] in the Jacobi diagonal; blocks of SEG_CHUNK elements.
+// vectors and starts at doff[s] in the Jacobi diagonal; blocks of SEG_CHUNK elements.  The
+// device arrays are allocated once with capacity (nseg_cap systems, nblk_cap blocks) and
+// refilled when the layout changes.
 imex_status make_seg(imex_ctx* c, int nseg, const long long* off, const long long* doff, const long long* len,
-                     imex_ctx::Seg* out) {
+                     imex_ctx::Seg* out, int nseg_cap, int nblk_cap) {
   std::vector<int> blen(nseg), blk_seg, blk_lo, blk0(nseg + 1);
   std::vector<SegBlock> blk;
   size_t total = 0;
@@ -317,32 +326,35 @@ imex_status make_seg(imex_ctx* c, int nseg, const long long* off, const long lon
     total = std::max(total, (size_t)(off[s] + len[s]));
   }
   blk0[nseg] = (int)blk_seg.size();
-  long long *doff_d = nullptr, *off_d = nullptr;
-  int *len_d = nullptr, *bs_d = nullptr, *bl_d = nullptr, *b0_d = nullptr;
-  TRY(dalloc(c, &off_d, nseg));
-  TRY(dalloc(c, &doff_d, nseg));
-  TRY(dalloc(c, &len_d, nseg));
-  TRY(dalloc(c, &bs_d, blk_seg.size()));
-  TRY(dalloc(c, &bl_d, blk_lo.size()));
-  TRY(dalloc(c, &b0_d, nseg + 1));
-  SegBlock* blk_d = nullptr;
-  TRY(dalloc(c, &blk_d, blk.size()));
-  CK(cudaMemcpy(blk_d, blk.data(), blk.size() * sizeof(SegBlock), cudaMemcpyHostToDevice), "cp seg");
-  CK(cudaMemcpy(off_d, off, nseg * sizeof(long long), cudaMemcpyHostToDevice), "cp seg");
-  CK(cudaMemcpy(doff_d, doff, nseg * sizeof(long long), cudaMemcpyHostToDevice), "cp seg");
-  CK(cudaMemcpy(len_d, blen.data(), nseg * sizeof(int), cudaMemcpyHostToDevice), "cp seg");
-  CK(cudaMemcpy(bs_d, blk_seg.data(), blk_seg.size() * sizeof(int), cudaMemcpyHostToDevice), "cp seg");
-  CK(cudaMemcpy(bl_d, blk_lo.data(), blk_lo.size() * sizeof(int), cudaMemcpyHostToDevice), "cp seg");
-  CK(cudaMemcpy(b0_d, blk0.data(), (nseg + 1) * sizeof(int), cudaMemcpyHostToDevice), "cp seg");
+  const int nblk = (int)blk_seg.size();
+  if (out->nseg_cap == 0) {
+    out->nseg_cap = std::max(nseg, nseg_cap);
+    out->nblk_cap = std::max(nblk, nblk_cap);
+    TRY(dalloc(c, &out->off_d, out->nseg_cap));
+    TRY(dalloc(c, &out->doff_d, out->nseg_cap));
+    TRY(dalloc(c, &out->len_d, out->nseg_cap));
+    TRY(dalloc(c, &out->b0_d, out->nseg_cap + 1));
+    TRY(dalloc(c, &out->bs_d, out->nblk_cap));
+    TRY(dalloc(c, &out->bl_d, out->nblk_cap));
+    TRY(dalloc(c, &out->blk_d, out->nblk_cap));
+  }
+  if (nseg > out->nseg_cap || nblk > out->nblk_cap) return fail(c, IMEX_EINVAL, "segment table above capacity");
+  CK(cudaMemcpy(out->blk_d, blk.data(), blk.size() * sizeof(SegBlock), cudaMemcpyHostToDevice), "cp seg");
+  CK(cudaMemcpy(out->off_d, off, nseg * sizeof(long long), cudaMemcpyHostToDevice), "cp seg");
+  CK(cudaMemcpy(out->doff_d, doff, nseg * sizeof(long long), cudaMemcpyHostToDevice), "cp seg");
+  CK(cudaMemcpy(out->len_d, blen.data(), nseg * sizeof(int), cudaMemcpyHostToDevice), "cp seg");
+  CK(cudaMemcpy(out->bs_d, blk_seg.data(), blk_seg.size() * sizeof(int), cudaMemcpyHostToDevice), "cp seg");
+  CK(cudaMemcpy(out->bl_d, blk_lo.data(), blk_lo.size() * sizeof(int), cudaMemcpyHostToDevice), "cp seg");
+  CK(cudaMemcpy(out->b0_d, blk0.data(), (nseg + 1) * sizeof(int), cudaMemcpyHostToDevice), "cp seg");
   out->t.nseg = nseg;
-  out->t.nblk = (int)blk_seg.size();
-  out->t.off = off_d;
-  out->t.doff = doff_d;
-  out->t.len = len_d;
-  out->t.blk_seg = bs_d;
-  out->t.blk_lo = bl_d;
-  out->t.seg_blk0 = b0_d;
-  out->t.blk = blk_d;
+  out->t.nblk = nblk;
+  out->t.off = out->off_d;
+  out->t.doff = out->doff_d;
+  out->t.len = out->len_d;
+  out->t.blk_seg = out->bs_d;
+  out->t.blk_lo = out->bl_d;
+  out->t.seg_blk0 = out->b0_d;
+  out->t.blk = out->blk_d;
   out->total = total;
   return IMEX_OK;
 }
@@ -1247,7 +1259,7 @@ imex_status alloc_sdc(imex_ctx* c) {
 }
 
 imex_status alloc_stages(imex_ctx* c, int s) {
-  const size_t nt = c->nv * c->d;
+  const size_t nt = (size_t)std::max<long long>(c->ne_cap, c->gv.ne) * ipow(c->Nv, c->d) * c->d;
   while ((int)c->E.size() < s) {
     double *e, *f1, *f3, *fs;
     TRY(dalloc(c, &e, nt));
@@ -1256,6 +1268,55 @@ imex_status alloc_stages(imex_ctx* c, int s) {
     TRY(dalloc(c, &fs, nt));
     c->E.push_back(e); c->Fd1.push_back(f1); c->Fd3.push_back(f3); c->Fs.push_back(fs);
   }
+  return IMEX_OK;
+}
+
+// Layout of the instances in a context's buffers (the instance list c->inst, e0 contiguous
+// from 0): element count, vector sizes, the per-instance tables, the CG segment tables and the
+// mass diagonals.  Cached CUDA graphs depend on the layout and are dropped.
+imex_status set_layout(imex_ctx* c) {
+  const int d = c->d;
+  long long ne = 0;
+  for (const auto& I : c->inst) ne += I.ne;
+  const int ni = (int)c->inst.size();
+  if (ne > c->ne_cap || ni > c->ninst_cap || ni < 1) return fail(c, IMEX_EINVAL, "layout above capacity");
+  c->gv.ne = c->gp.ne = (int)ne;
+  const long long ndv = ipow(c->Nv, d), ndp = ipow(c->Np, d);
+  c->nv = (size_t)ne * ndv;
+  c->np = (size_t)ne * ndp;
+  if (c->batched) {
+    std::vector<int> ei(ne);
+    for (int i = 0; i < ni; ++i)
+      for (int e = 0; e < c->inst[i].ne; ++e) ei[c->inst[i].e0 + e] = i;
+    CK(cudaMemcpy(c->inst_d, c->inst.data(), ni * sizeof(InstGeom), cudaMemcpyHostToDevice), "cp inst");
+    CK(cudaMemcpy(c->elem_inst_d, ei.data(), ei.size() * sizeof(int), cudaMemcpyHostToDevice), "cp inst");
+  }
+  // CG systems: the pressure of each instance, and each velocity component of each
+  // instance (component-major); the Jacobi diagonal of the velocity is shared by the
+  // components of an instance
+  std::vector<long long> offp(ni), lenp(ni), offv(d * ni), doffv(d * ni), lenv(d * ni);
+  for (int i = 0; i < ni; ++i) {
+    offp[i] = c->inst[i].e0 * ndp;
+    lenp[i] = c->inst[i].ne * ndp;
+    for (int k = 0; k < d; ++k) {
+      offv[k * ni + i] = (long long)(k * c->nv) + c->inst[i].e0 * ndv;
+      doffv[k * ni + i] = c->inst[i].e0 * ndv;
+      lenv[k * ni + i] = c->inst[i].ne * ndv;
+    }
+  }
+  const int pcap = (int)((c->ne_cap * ndp) / SEG_CHUNK + c->ninst_cap + 1);
+  const int vcap = d * (int)((c->ne_cap * ndv) / SEG_CHUNK + c->ninst_cap + 1);
+  TRY(make_seg(c, ni, offp.data(), offp.data(), lenp.data(), &c->segp, c->ninst_cap, pcap));
+  TRY(make_seg(c, d * ni, offv.data(), doffv.data(), lenv.data(), &c->segv, d * c->ninst_cap, vcap));
+  // mass diagonals: the diag kernel with alpha = 1, beta = 0
+  SipgArgs<double> a = sipg_args<double>(nullptr, c->mass_v, 1, (long long)c->nv, nullptr, 0.0, nullptr, 1.0, 0.0, 0);
+  TRY(launch_check(c, sipg_diag<double>(c->gv, c->Nv, a, c->st), "mass(v)"));
+  SipgArgs<double> b = sipg_args<double>(nullptr, c->mass_p, 1, (long long)c->np, nullptr, 0.0, nullptr, 1.0, 0.0, 0);
+  TRY(launch_check(c, sipg_diag<double>(c->gp, c->Np, b, c->st), "mass(p)"));
+  c->diag_valid_p = false;
+  CK(cudaStreamSynchronize(c->st), "sync");
+  for (auto& gr : c->graphs) cudaGraphExecDestroy(gr.exec);
+  c->graphs.clear();
   return IMEX_OK;
 }
 
@@ -1299,42 +1360,39 @@ imex_status init_ctx(imex_ctx* c) {
     c->gv.tab64 = c->gp.tab64 = c->dtab64;
     c->gv.tab32 = c->gp.tab32 = c->dtab32;
   }
+  // buffers sized for the capacity: ne_cap elements, ninst_cap instances
+  if (c->ne_cap < g.ne) c->ne_cap = g.ne;
+  if (c->ninst_cap < (int)c->inst.size()) c->ninst_cap = (int)c->inst.size();
+  const long long ndv = ipow(c->Nv, d), ndp = ipow(c->Np, d);
+  const size_t nvc = (size_t)c->ne_cap * ndv, npc = (size_t)c->ne_cap * ndp;
   if (c->batched) {
-    // per-instance geometry and the instance of every element
-    std::vector<int> ei(g.ne);
-    for (size_t i = 0; i < c->inst.size(); ++i)
-      for (int e = 0; e < c->inst[i].ne; ++e) ei[c->inst[i].e0 + e] = (int)i;
-    if ((s = dalloc(c, &c->inst_d, c->inst.size())) != IMEX_OK) return bail(s);
-    if ((s = dalloc(c, &c->elem_inst_d, (size_t)g.ne)) != IMEX_OK) return bail(s);
-    if ((s = dalloc(c, &c->edt, (size_t)g.ne)) != IMEX_OK) return bail(s);
-    if (cudaMemcpy(c->inst_d, c->inst.data(), c->inst.size() * sizeof(InstGeom), cudaMemcpyHostToDevice) !=
-            cudaSuccess ||
-        cudaMemcpy(c->elem_inst_d, ei.data(), ei.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess)
-      return bail(IMEX_ECUDA);
+    if ((s = dalloc(c, &c->inst_d, (size_t)c->ninst_cap)) != IMEX_OK) return bail(s);
+    if ((s = dalloc(c, &c->elem_inst_d, (size_t)c->ne_cap)) != IMEX_OK) return bail(s);
+    if ((s = dalloc(c, &c->edt, (size_t)c->ne_cap)) != IMEX_OK) return bail(s);
     c->gv.inst = c->gp.inst = c->inst_d;
     c->gv.elem_inst = c->gp.elem_inst = c->elem_inst_d;
   }
-  const size_t nt = c->nv * d;
-  const size_t big = std::max(nt, c->np);
+  const size_t nt = nvc * d;
+  const size_t big = std::max(nt, npc);
   double** f64[] = {&c->v, &c->vp, &c->vpp, &c->g, &c->tmp, &c->vb, &c->cx, &c->cr, &c->cz, &c->cp, &c->cAp};
   for (double** p : f64) if ((s = dalloc(c, p, big)) != IMEX_OK) return bail(s);
-  if ((s = dalloc(c, &c->nu, c->nv)) != IMEX_OK) return bail(s);
-  if ((s = dalloc(c, &c->nu_fixed, c->nv)) != IMEX_OK) return bail(s);
-  if ((s = dalloc(c, &c->phi, c->nv)) != IMEX_OK) return bail(s);
-  if ((s = dalloc(c, &c->jac, c->nv * d * d)) != IMEX_OK) return bail(s);
-  if ((s = dalloc(c, &c->psi, c->np)) != IMEX_OK) return bail(s);
-  if ((s = dalloc(c, &c->bp, c->np)) != IMEX_OK) return bail(s);
-  if ((s = dalloc(c, &c->mass_v, c->nv)) != IMEX_OK) return bail(s);
-  if ((s = dalloc(c, &c->mass_p, c->np)) != IMEX_OK) return bail(s);
-  if ((s = dalloc(c, &c->cdiag, c->np + c->nv)) != IMEX_OK) return bail(s);
+  if ((s = dalloc(c, &c->nu, nvc)) != IMEX_OK) return bail(s);
+  if ((s = dalloc(c, &c->nu_fixed, nvc)) != IMEX_OK) return bail(s);
+  if ((s = dalloc(c, &c->phi, nvc)) != IMEX_OK) return bail(s);
+  if ((s = dalloc(c, &c->jac, nvc * d * d)) != IMEX_OK) return bail(s);
+  if ((s = dalloc(c, &c->psi, npc)) != IMEX_OK) return bail(s);
+  if ((s = dalloc(c, &c->bp, npc)) != IMEX_OK) return bail(s);
+  if ((s = dalloc(c, &c->mass_v, nvc)) != IMEX_OK) return bail(s);
+  if ((s = dalloc(c, &c->mass_p, npc)) != IMEX_OK) return bail(s);
+  if ((s = dalloc(c, &c->cdiag, npc + nvc)) != IMEX_OK) return bail(s);
   float** f32[] = {&c->fx, &c->fr, &c->fp, &c->fAp};
   for (float** p : f32) if ((s = dalloc(c, p, big)) != IMEX_OK) return bail(s);
-  if ((s = dalloc(c, &c->fdiag, c->np + c->nv)) != IMEX_OK) return bail(s);
-  if ((s = dalloc(c, &c->fnu, c->nv)) != IMEX_OK) return bail(s);
-  if ((s = dalloc(c, &c->fvtmp, nt + c->np)) != IMEX_OK) return bail(s);
+  if ((s = dalloc(c, &c->fdiag, npc + nvc)) != IMEX_OK) return bail(s);
+  if ((s = dalloc(c, &c->fnu, nvc)) != IMEX_OK) return bail(s);
+  if ((s = dalloc(c, &c->fvtmp, nt + npc)) != IMEX_OK) return bail(s);
   c->nblocks = 152 * 4;
   if ((s = dalloc(c, &c->partial, (size_t)c->nblocks * 8)) != IMEX_OK) return bail(s);
-  if ((s = dalloc(c, &c->apartial, (size_t)(g.ne + 64) * 3)) != IMEX_OK) return bail(s);
+  if ((s = dalloc(c, &c->apartial, (size_t)(c->ne_cap + 64) * 3)) != IMEX_OK) return bail(s);
   if ((s = dalloc(c, &c->counters, 8)) != IMEX_OK) return bail(s);
   cudaMemsetAsync(c->counters, 0, 8 * sizeof(unsigned int), c->st);
   if ((s = dalloc(c, &c->dscal, 128)) != IMEX_OK) return bail(s);
@@ -1342,25 +1400,9 @@ imex_status init_ctx(imex_ctx* c) {
   if (cudaMallocHost((void**)&c->hscal, 128 * sizeof(double)) != cudaSuccess) return bail(IMEX_ENOMEM);
   if (cudaMallocHost((void**)&c->hiscal, 64 * sizeof(int)) != cudaSuccess) return bail(IMEX_ENOMEM);
   {
-    // CG systems: the pressure of each instance, and each velocity component of each
-    // instance (component-major); the Jacobi diagonal of the velocity is shared by the
-    // components of an instance
-    const int ni = (int)c->inst.size();
-    const long long ndv = ipow(c->Nv, d), ndp = ipow(c->Np, d);
-    std::vector<long long> offp(ni), lenp(ni), offv(d * ni), doffv(d * ni), lenv(d * ni);
-    for (int i = 0; i < ni; ++i) {
-      offp[i] = c->inst[i].e0 * ndp;
-      lenp[i] = c->inst[i].ne * ndp;
-      for (int k = 0; k < d; ++k) {
-        offv[k * ni + i] = (long long)(k * c->nv) + c->inst[i].e0 * ndv;
-        doffv[k * ni + i] = c->inst[i].e0 * ndv;
-        lenv[k * ni + i] = c->inst[i].ne * ndv;
-      }
-    }
-    if ((s = make_seg(c, ni, offp.data(), offp.data(), lenp.data(), &c->segp)) != IMEX_OK) return bail(s);
-    if ((s = make_seg(c, d * ni, offv.data(), doffv.data(), lenv.data(), &c->segv)) != IMEX_OK) return bail(s);
-    c->maxsys = d * ni;
-    const int nblk = std::max(c->segp.t.nblk, c->segv.t.nblk);
+    // CG systems: each instance's pressure, each velocity component of each instance
+    c->maxsys = d * c->ninst_cap;
+    const int nblk = d * (int)((c->ne_cap * ndv) / SEG_CHUNK + c->ninst_cap + 1) + 1;
     if ((s = dalloc(c, &c->seg_partial, (size_t)5 * nblk + 64)) != IMEX_OK) return bail(s);
     if ((s = dalloc(c, &c->cg_d, (size_t)12 * c->maxsys)) != IMEX_OK) return bail(s);
     if ((s = dalloc(c, &c->cg_i, (size_t)2 * c->maxsys)) != IMEX_OK) return bail(s);
@@ -1371,15 +1413,9 @@ imex_status init_ctx(imex_ctx* c) {
     if (cudaMallocHost((void**)&c->cg_hd, 12 * c->maxsys * sizeof(double)) != cudaSuccess) return bail(IMEX_ENOMEM);
     if (cudaMallocHost((void**)&c->cg_hi, 2 * c->maxsys * sizeof(int)) != cudaSuccess) return bail(IMEX_ENOMEM);
   }
-  cudaMemsetAsync(c->psi, 0, c->np * sizeof(double), c->st);
+  cudaMemsetAsync(c->psi, 0, npc * sizeof(double), c->st);
   cudaMemsetAsync(c->v, 0, big * sizeof(double), c->st);
-  // mass diagonals: apply alpha=1, beta=0 to a ones vector via the diag kernel (beta = 0)
-  {
-    SipgArgs<double> a = sipg_args<double>(nullptr, c->mass_v, 1, (long long)c->nv, nullptr, 0.0, nullptr, 1.0, 0.0, 0);
-    if (sipg_diag<double>(c->gv, c->Nv, a, c->st) != 0) return bail(IMEX_EINVAL);
-    SipgArgs<double> b = sipg_args<double>(nullptr, c->mass_p, 1, (long long)c->np, nullptr, 0.0, nullptr, 1.0, 0.0, 0);
-    if (sipg_diag<double>(c->gp, c->Np, b, c->st) != 0) return bail(IMEX_EINVAL);
-  }
+  if ((s = set_layout(c)) != IMEX_OK) return bail(s);
   if ((s = alloc_stages(c, 4)) != IMEX_OK) return bail(s);
   if (cudaStreamSynchronize(c->st) != cudaSuccess || cudaGetLastError() != cudaSuccess) return bail(IMEX_ECUDA);
   return IMEX_OK;
@@ -1503,6 +1539,140 @@ imex_status group_step(imex_ctx* c) {
   c->stats.steps++;
   TRY(check_state(c));
   return IMEX_OK;
+}
+
+
+// ---- continuous batching ---------------------------------------------------------------
+// A member of a server group: its geometry and parameters (InstGeom), and for a member that
+// joins at the next regroup the initial field to set.
+struct JoinSpec {
+  InstGeom g;
+  int flow;
+  double flow_p[8];
+  double t0;
+};
+
+// New member list of a group: the surviving members (by their current index, in order) and
+// the joining ones; their fields are repacked into the new contiguous layout (survivors'
+// velocity and pressure copied, joiners' velocity from their initial flow, pressure zero).
+// dst may be c itself or a larger group taking over c's members (c then keeps its state).
+imex_status regroup(imex_ctx* c, imex_ctx* dst, const std::vector<int>& keep, const std::vector<JoinSpec>& join) {
+  const int d = c->d;
+  const size_t ndv = ipow(c->Nv, d), ndp = ipow(c->Np, d);
+  std::vector<InstGeom> ni;
+  long long e0 = 0;
+  for (int i : keep) {
+    InstGeom I = c->inst[i];
+    I.e0 = (int)e0;
+    e0 += I.ne;
+    ni.push_back(I);
+  }
+  for (const auto& j : join) {
+    InstGeom I = j.g;
+    I.e0 = (int)e0;
+    e0 += I.ne;
+    ni.push_back(I);
+  }
+  if (e0 > dst->ne_cap || (long long)ni.size() > dst->ninst_cap) return fail(c, IMEX_EINVAL, "group capacity");
+  if (ni.empty()) {
+    c->inst.clear();
+    return IMEX_OK;
+  }
+  const size_t nv_new = (size_t)e0 * ndv, np_new = (size_t)e0 * ndp;
+  // survivors: old layout of c -> new layout in dst's scratch (tmp, bp)
+  CK(cudaStreamSynchronize(c->st), "sync");
+  for (size_t q = 0; q < keep.size(); ++q) {
+    const InstGeom& O = c->inst[keep[q]];
+    const InstGeom& N = ni[q];
+    for (int k = 0; k < d; ++k)
+      CK(cudaMemcpyAsync(dst->tmp + k * nv_new + N.e0 * ndv, c->v + k * c->nv + O.e0 * ndv,
+                         (size_t)O.ne * ndv * sizeof(double), cudaMemcpyDeviceToDevice, dst->st), "cp v");
+    CK(cudaMemcpyAsync(dst->bp + N.e0 * ndp, c->psi + O.e0 * ndp, (size_t)O.ne * ndp * sizeof(double),
+                       cudaMemcpyDeviceToDevice, dst->st), "cp psi");
+  }
+  // joiners: initial velocity from the analytic flow on the instance's own mesh
+  for (size_t q = 0; q < join.size(); ++q) {
+    const InstGeom& N = ni[keep.size() + q];
+    Geom g1 = dst->gv;
+    g1.inst = nullptr;
+    g1.elem_inst = nullptr;
+    g1.ne = N.ne;
+    for (int k = 0; k < 3; ++k) {
+      g1.n[k] = N.n[k];
+      g1.lo[k] = N.lo[k];
+      g1.h[k] = N.h[k];
+      g1.hf[k] = N.hf[k];
+    }
+    double pp[8];
+    std::memcpy(pp, join[q].flow_p, sizeof(pp));
+    TRY(launch_check(dst, eval_field(g1, dst->Nv, 0, spec(join[q].flow, pp), join[q].t0, nullptr, (long long)nv_new,
+                                     dst->tmp + N.e0 * ndv, dst->st), "eval_field(join)"));
+    CK(cudaMemsetAsync(dst->bp + N.e0 * ndp, 0, (size_t)N.ne * ndp * sizeof(double), dst->st), "memset psi");
+  }
+  CK(cudaMemcpyAsync(dst->v, dst->tmp, d * nv_new * sizeof(double), cudaMemcpyDeviceToDevice, dst->st), "cp v");
+  CK(cudaMemcpyAsync(dst->psi, dst->bp, np_new * sizeof(double), cudaMemcpyDeviceToDevice, dst->st), "cp psi");
+  dst->inst = ni;
+  return set_layout(dst);
+}
+
+// An empty server group with the settings of the given mesh and models and room for
+// ne_cap elements and ninst_cap instances; its first member joins through regroup.
+imex_status create_group(const imex_mesh_desc& desc, int nu_kind, int bc_kind, int f_kind, const InstGeom& first,
+                         long long ne_cap, int ninst_cap, imex_ctx** out) {
+  imex_ctx* c = new imex_ctx();
+  c->desc = desc;
+  c->desc.stream = nullptr;
+  c->d = desc.dim;
+  c->Nv = desc.P + 1;
+  c->Np = desc.P;
+  c->batched = true;
+  named_tableau("CB3e", &c->tab);
+  c->nu_kind = nu_kind;
+  c->bc_kind = bc_kind;
+  c->f_kind = f_kind;
+  Geom g{};
+  g.d = c->d;
+  g.idt = 1.0;
+  g.idtf = 1.f;
+  for (int k = 0; k < 3; ++k) {
+    g.n[k] = first.n[k];
+    g.lo[k] = first.lo[k];
+    g.h[k] = first.h[k];
+    g.hf[k] = first.hf[k];
+  }
+  g.ne = first.ne;
+  c->gv = g;
+  c->gp = g;
+  for (int k = 0; k < 3; ++k) {
+    const bool per = (k >= c->d) || desc.periodic[k];
+    c->gv.bc[k] = per ? 0 : 1;
+    c->gp.bc[k] = per ? 0 : 2;
+  }
+  c->inst.push_back(first);
+  c->inst[0].e0 = 0;
+  c->ne_cap = std::max<long long>(ne_cap, first.ne);
+  c->ninst_cap = std::max(ninst_cap, 1);
+  if (cudaStreamCreateWithFlags(&c->st, cudaStreamNonBlocking) != cudaSuccess) {
+    delete c;
+    return IMEX_ECUDA;
+  }
+  c->own_stream = true;
+  imex_status s = init_ctx(c);
+  if (s == IMEX_OK) s = alloc_stages(c, c->tab.s);
+  if (s != IMEX_OK) {
+    imex_destroy(c);
+    return s;
+  }
+  *out = c;
+  return IMEX_OK;
+}
+
+// device bytes of one instance's share of a group's buffers (velocity nodes nv per
+// component, pressure nodes np, s stages)
+double footprint_bytes(int d, long long nv, long long np, int s) {
+  const double f64v = 11.0 * d + 4.0 + d * d + 2.0 + 4.0 * s * d;    // work vectors, fields, stages, diagonals
+  const double f32v = 5.0 * d + 2.0;
+  return (double)nv * (8.0 * f64v + 4.0 * f32v) + (double)np * (8.0 * 6.0 + 4.0 * 2.0) + 256.0;
 }
 
 }  // namespace
@@ -2087,6 +2257,365 @@ imex_status imex_batch_group_info(const imex_batch* b, int q, int* ninst, int* P
   if (nvel) *nvel = (long long)c->nv;
   if (st) *st = c->stats;
   if (last_ms) *last_ms = q < (int)b->group_ms.size() ? b->group_ms[q] : 0.0;
+  return IMEX_OK;
+}
+
+
+// ---- serving: continuous batching ------------------------------------------------------
+struct imex_server {
+  imex_server_desc desc{};
+  double budget = 0.0;
+  struct Req {
+    imex_request r{};
+    int state = IMEX_REQ_QUEUED;
+    int steps_done = 0;
+    double t = 0.0;
+    double footprint = 0.0;
+    long long dof = 0;
+    int group = -1;
+    std::vector<double> result;
+    std::string err;
+  };
+  std::vector<Req> reqs;
+  std::deque<long long> queue;
+  struct Group {
+    imex_ctx* c = nullptr;
+    std::vector<long long> members;   // request ids, in the group's instance order
+    std::vector<long long> joining;   // admitted, not yet in the layout
+    bool leaving = false;             // a member finished or failed: regroup before the next step
+  };
+  std::vector<Group> groups;
+  double active_fp = 0.0, max_fp = 0.0;
+  std::vector<double> tick_ms;
+  double dof_stages = 0.0, busy_s = 0.0;
+  long long completed = 0, failed = 0;
+  std::string err;
+};
+
+namespace {
+
+// settings that must agree within a group (the rest is per instance)
+bool same_server_group(const imex_request& a, const imex_request& b) {
+  if (a.dim != b.dim || a.P != b.P || a.nu_kind != b.nu_kind || a.bc_kind != b.bc_kind || a.f_kind != b.f_kind)
+    return false;
+  for (int k = 0; k < a.dim; ++k)
+    if ((a.periodic[k] != 0) != (b.periodic[k] != 0)) return false;
+  return true;
+}
+
+InstGeom req_geom(const imex_request& r) {
+  InstGeom I{};
+  I.ne = 1;
+  for (int k = 0; k < 3; ++k) {
+    const int n = k < r.dim ? r.nelem[k] : 1;
+    I.n[k] = n;
+    I.lo[k] = k < r.dim ? r.lo[k] : 0.0;
+    I.h[k] = k < r.dim ? (r.hi[k] - r.lo[k]) / n : 1.0;
+    I.hf[k] = (float)I.h[k];
+    I.ne *= n;
+  }
+  I.nu0 = r.nu_params[0];
+  I.nu0f = (float)r.nu_params[0];
+  I.dt = r.dt;
+  I.dtf = (float)r.dt;
+  I.t = r.t0;
+  std::memcpy(I.nu_p, r.nu_params, sizeof(I.nu_p));
+  std::memcpy(I.bc_p, r.bc_params, sizeof(I.bc_p));
+  std::memcpy(I.f_p, r.f_params, sizeof(I.f_p));
+  return I;
+}
+
+imex_mesh_desc req_desc(const imex_server* sv, const imex_request& r) {
+  imex_mesh_desc d{};
+  d.dim = r.dim;
+  d.P = r.P;
+  for (int k = 0; k < 3; ++k) {
+    d.nelem[k] = k < r.dim ? r.nelem[k] : 1;
+    d.lo[k] = r.lo[k];
+    d.hi[k] = r.hi[k];
+    d.periodic[k] = k < r.dim ? r.periodic[k] : 1;
+  }
+  d.precision = sv->desc.precision;
+  d.poisson = sv->desc.poisson;
+  d.tol = sv->desc.tol > 0 ? sv->desc.tol : 1e-10;
+  d.maxit = sv->desc.maxit > 0 ? sv->desc.maxit : 20000;
+  d.vmax = sv->desc.vmax;
+  return d;
+}
+
+// apply the pending joins and departures of a server group (growing it when needed)
+imex_status server_regroup(imex_server* sv, imex_server::Group& G) {
+  imex_ctx* c = G.c;
+  std::vector<int> keep;
+  std::vector<long long> kept_ids;
+  for (size_t i = 0; i < G.members.size(); ++i) {
+    const auto& R = sv->reqs[G.members[i]];
+    if (R.state == IMEX_REQ_ACTIVE) {
+      keep.push_back((int)i);
+      kept_ids.push_back(G.members[i]);
+    }
+  }
+  std::vector<JoinSpec> join;
+  long long ne = 0;
+  for (int i : keep) ne += c->inst[i].ne;
+  for (long long id : G.joining) {
+    const auto& R = sv->reqs[id];
+    JoinSpec j{};
+    j.g = req_geom(R.r);
+    j.flow = R.r.flow;
+    std::memcpy(j.flow_p, R.r.flow_params, sizeof(j.flow_p));
+    j.t0 = R.r.t0;
+    join.push_back(j);
+    ne += j.g.ne;
+  }
+  const int ni = (int)(keep.size() + join.size());
+  imex_ctx* dst = c;
+  if (ni > 0 && (ne > c->ne_cap || ni > c->ninst_cap)) {
+    // grow: a new group with twice the needed room takes the members over
+    const imex_request& r0 = sv->reqs[kept_ids.empty() ? G.joining[0] : kept_ids[0]].r;
+    TRY(create_group(req_desc(sv, r0), r0.nu_kind, r0.bc_kind, r0.f_kind, req_geom(r0), 2 * ne, 2 * ni, &dst));
+  }
+  const imex_status s = regroup(c, dst, keep, join);
+  if (dst != c) {
+    imex_destroy(c);
+    G.c = dst;
+  }
+  if (s != IMEX_OK) return s;
+  G.members = kept_ids;
+  G.members.insert(G.members.end(), G.joining.begin(), G.joining.end());
+  G.joining.clear();
+  G.leaving = false;
+  return IMEX_OK;
+}
+
+}  // namespace
+
+imex_status imex_server_create(const imex_server_desc* desc, imex_server** out) {
+  if (!desc || !out) return IMEX_EINVAL;
+  if (desc->precision != IMEX_FP64 && desc->precision != IMEX_MIXED) return IMEX_EINVAL;
+  imex_server* sv = new imex_server();
+  sv->desc = *desc;
+  sv->budget = desc->hbm_budget_bytes;
+  if (!(sv->budget > 0)) {
+    size_t fr = 0, tot = 0;
+    if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+      delete sv;
+      return IMEX_ECUDA;
+    }
+    sv->budget = 0.5 * (double)fr;
+  }
+  *out = sv;
+  return IMEX_OK;
+}
+
+void imex_server_destroy(imex_server* sv) {
+  if (!sv) return;
+  for (auto& G : sv->groups) imex_destroy(G.c);
+  delete sv;
+}
+
+const char* imex_server_last_error(const imex_server* sv) { return sv ? sv->err.c_str() : "null server"; }
+
+imex_status imex_server_submit(imex_server* sv, const imex_request* r, long long* id) {
+  if (!sv || !r || !id) return IMEX_EINVAL;
+  if ((r->dim != 2 && r->dim != 3) || r->P < 2 || r->P > IMEX_MAXN - 1 || !(r->dt > 0) || r->nsteps < 1)
+    return IMEX_EINVAL;
+  bool bnd = false;
+  for (int k = 0; k < r->dim; ++k) {
+    if (r->nelem[k] < 1 || !(r->hi[k] > r->lo[k])) return IMEX_EINVAL;
+    bnd = bnd || !r->periodic[k];
+  }
+  if (bnd && r->bc_kind == IMEX_FLOW_NONE) return IMEX_EINVAL;
+  if (r->nu_kind == IMEX_NU_FIELD) return IMEX_EINVAL;
+  imex_server::Req R;
+  R.r = *r;
+  R.t = r->t0;
+  const InstGeom I = req_geom(*r);
+  const long long nv = (long long)I.ne * ipow(r->P + 1, r->dim), np = (long long)I.ne * ipow(r->P, r->dim);
+  R.footprint = footprint_bytes(r->dim, nv, np, 4);
+  R.dof = r->dim * nv;
+  *id = (long long)sv->reqs.size();
+  sv->reqs.push_back(std::move(R));
+  sv->queue.push_back(*id);
+  return IMEX_OK;
+}
+
+imex_status imex_server_tick(imex_server* sv, int* active) {
+  if (!sv) return IMEX_EINVAL;
+  const auto t0 = std::chrono::steady_clock::now();
+  // 1. admission in arrival order while the active footprint stays within the budget
+  while (!sv->queue.empty()) {
+    const long long id = sv->queue.front();
+    auto& R = sv->reqs[id];
+    if (sv->active_fp + R.footprint > sv->budget) {
+      if (sv->active_fp > 0) break;                 // wait for room
+      R.state = IMEX_REQ_FAILED;                    // would not fit even alone
+      R.err = "request footprint above the HBM budget";
+      sv->failed++;
+      sv->queue.pop_front();
+      continue;
+    }
+    sv->queue.pop_front();
+    int g = -1;
+    for (size_t q = 0; q < sv->groups.size() && g < 0; ++q) {
+      const auto& G = sv->groups[q];
+      const long long any = !G.members.empty() ? G.members[0] : G.joining[0];
+      if (same_server_group(sv->reqs[any].r, R.r)) g = (int)q;
+    }
+    if (g < 0) {
+      imex_ctx* c = nullptr;
+      const InstGeom I = req_geom(R.r);
+      const imex_status s = create_group(req_desc(sv, R.r), R.r.nu_kind, R.r.bc_kind, R.r.f_kind, I,
+                                         2 * (long long)I.ne, 16, &c);
+      if (s != IMEX_OK) {
+        R.state = IMEX_REQ_FAILED;
+        R.err = "group creation failed";
+        sv->failed++;
+        continue;
+      }
+      imex_server::Group G;
+      G.c = c;
+      sv->groups.push_back(G);
+      g = (int)sv->groups.size() - 1;
+    }
+    sv->groups[g].joining.push_back(id);
+    R.group = g;
+    R.state = IMEX_REQ_ACTIVE;
+    sv->active_fp += R.footprint;
+    sv->max_fp = std::max(sv->max_fp, sv->active_fp);
+  }
+  // 2. layout changes, then drop empty groups
+  for (auto& G : sv->groups)
+    if (!G.joining.empty() || G.leaving) {
+      const imex_status s = server_regroup(sv, G);
+      if (s != IMEX_OK) {
+        for (long long id : G.joining) {
+          sv->reqs[id].state = IMEX_REQ_FAILED;
+          sv->reqs[id].err = "regroup failed";
+          sv->failed++;
+          sv->active_fp -= sv->reqs[id].footprint;
+        }
+        G.joining.clear();
+        sv->err = G.c ? G.c->err : "regroup failed";
+      }
+    }
+  for (size_t q = 0; q < sv->groups.size();)
+    if (sv->groups[q].members.empty() && sv->groups[q].joining.empty()) {
+      imex_destroy(sv->groups[q].c);
+      sv->groups.erase(sv->groups.begin() + q);
+      for (auto& R : sv->reqs)
+        if (R.state == IMEX_REQ_ACTIVE && R.group > (int)q) R.group--;
+    } else {
+      ++q;
+    }
+  // 3. one step of every active request, the groups concurrently
+  std::vector<imex_status> st(sv->groups.size(), IMEX_OK);
+  auto run = [&](size_t q) {
+    imex_ctx* c = sv->groups[q].c;
+    std::vector<double> dt;
+    for (long long id : sv->groups[q].members) dt.push_back(sv->reqs[id].r.dt);
+    imex_status s = set_group_dt(c, dt);
+    if (s == IMEX_OK) s = group_step(c);
+    if (s == IMEX_OK && cudaStreamSynchronize(c->st) != cudaSuccess) s = IMEX_ECUDA;
+    st[q] = s;
+  };
+  if (sv->groups.size() == 1) {
+    run(0);
+  } else if (!sv->groups.empty()) {
+    std::vector<std::thread> th;
+    for (size_t q = 0; q < sv->groups.size(); ++q) th.emplace_back(run, q);
+    for (auto& t : th) t.join();
+  }
+  // 4. bookkeeping: finished and failed requests leave at the next tick
+  int nact = 0;
+  for (size_t q = 0; q < sv->groups.size(); ++q) {
+    auto& G = sv->groups[q];
+    imex_ctx* c = G.c;
+    for (size_t i = 0; i < G.members.size(); ++i) {
+      auto& R = sv->reqs[G.members[i]];
+      if (R.state != IMEX_REQ_ACTIVE) continue;
+      if (st[q] != IMEX_OK) {
+        R.state = IMEX_REQ_FAILED;
+        R.err = c->err;
+        sv->failed++;
+        sv->active_fp -= R.footprint;
+        G.leaving = true;
+        continue;
+      }
+      R.steps_done++;
+      R.t = c->inst[i].t;
+      sv->dof_stages += (double)R.dof * (c->tab.s - 1);
+      if (R.steps_done >= R.r.nsteps) {
+        if (sv->desc.keep_results) {
+          const InstGeom& I = c->inst[i];
+          const size_t ndv = ipow(c->Nv, c->d), n = (size_t)I.ne * ndv;
+          R.result.resize(c->d * n);
+          for (int k = 0; k < c->d; ++k)
+            cudaMemcpy(R.result.data() + k * n, c->v + k * c->nv + I.e0 * ndv, n * sizeof(double),
+                       cudaMemcpyDeviceToHost);
+        }
+        R.state = IMEX_REQ_DONE;
+        sv->completed++;
+        sv->active_fp -= R.footprint;
+        G.leaving = true;
+      } else {
+        nact++;
+      }
+    }
+    if (st[q] != IMEX_OK) sv->err = "group " + std::to_string(q) + ": " + c->err;
+  }
+  const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  if (!sv->groups.empty()) {
+    sv->tick_ms.push_back(ms);
+    sv->busy_s += ms * 1e-3;
+  }
+  if (active) *active = nact;
+  return IMEX_OK;
+}
+
+imex_status imex_server_poll(const imex_server* sv, long long id, int* state, int* steps_done, double* t) {
+  if (!sv || id < 0 || id >= (long long)sv->reqs.size()) return IMEX_EINVAL;
+  const auto& R = sv->reqs[id];
+  if (state) *state = R.state;
+  if (steps_done) *steps_done = R.steps_done;
+  if (t) *t = R.t;
+  return IMEX_OK;
+}
+
+imex_status imex_server_result(imex_server* sv, long long id, double* velocity) {
+  if (!sv || !velocity || id < 0 || id >= (long long)sv->reqs.size()) return IMEX_EINVAL;
+  auto& R = sv->reqs[id];
+  if (R.state != IMEX_REQ_DONE || R.result.empty()) return IMEX_EINVAL;
+  std::memcpy(velocity, R.result.data(), R.result.size() * sizeof(double));
+  std::vector<double>().swap(R.result);
+  return IMEX_OK;
+}
+
+imex_status imex_server_get_stats(const imex_server* sv, imex_server_stats* out) {
+  if (!sv || !out) return IMEX_EINVAL;
+  imex_server_stats s{};
+  s.submitted = (long long)sv->reqs.size();
+  s.completed = sv->completed;
+  s.failed = sv->failed;
+  s.queued = (long long)sv->queue.size();
+  for (const auto& R : sv->reqs) s.active += R.state == IMEX_REQ_ACTIVE ? 1 : 0;
+  s.ticks = (long long)sv->tick_ms.size();
+  if (!sv->tick_ms.empty()) {
+    std::vector<double> t = sv->tick_ms;
+    std::sort(t.begin(), t.end());
+    s.p50_tick_ms = t[t.size() / 2];
+    s.p99_tick_ms = t[std::min(t.size() - 1, (size_t)(0.99 * (double)t.size()))];
+    double sum = 0.0;
+    for (double x : t) sum += x;
+    s.mean_tick_ms = sum / (double)t.size();
+  }
+  s.dof_stages = sv->dof_stages;
+  s.busy_s = sv->busy_s;
+  s.footprint_bytes = sv->active_fp;
+  s.max_footprint_bytes = sv->max_fp;
+  s.budget_bytes = sv->budget;
+  s.groups = (int)sv->groups.size();
+  *out = s;
   return IMEX_OK;
 }
 

@@ -36,6 +36,30 @@ class imex_mesh_desc(C.Structure):
                 ("vmax", C.c_double), ("stream", C.c_void_p)]
 
 
+class imex_server_desc(C.Structure):
+    _fields_ = [("hbm_budget_bytes", C.c_double), ("precision", C.c_int), ("poisson", C.c_int), ("tol", C.c_double),
+                ("maxit", C.c_int), ("vmax", C.c_double), ("keep_results", C.c_int)]
+
+
+class imex_request(C.Structure):
+    _fields_ = [("dim", C.c_int), ("P", C.c_int), ("nelem", C.c_int * 3), ("lo", C.c_double * 3),
+                ("hi", C.c_double * 3), ("periodic", C.c_int * 3), ("flow", C.c_int),
+                ("flow_params", C.c_double * 8), ("nu_kind", C.c_int), ("nu_params", C.c_double * 8),
+                ("bc_kind", C.c_int), ("bc_params", C.c_double * 8), ("f_kind", C.c_int),
+                ("f_params", C.c_double * 8), ("t0", C.c_double), ("dt", C.c_double), ("nsteps", C.c_int)]
+
+
+class imex_server_stats(C.Structure):
+    _fields_ = [("submitted", C.c_longlong), ("completed", C.c_longlong), ("failed", C.c_longlong),
+                ("active", C.c_longlong), ("queued", C.c_longlong), ("ticks", C.c_longlong),
+                ("p50_tick_ms", C.c_double), ("p99_tick_ms", C.c_double), ("mean_tick_ms", C.c_double),
+                ("dof_stages", C.c_double), ("busy_s", C.c_double), ("footprint_bytes", C.c_double),
+                ("max_footprint_bytes", C.c_double), ("budget_bytes", C.c_double), ("groups", C.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class imex_stats(C.Structure):
     _fields_ = [("steps", C.c_longlong), ("stages", C.c_longlong), ("poisson_solves", C.c_int),
                 ("helmholtz_solves", C.c_int), ("poisson_iters", C.c_longlong),
@@ -95,7 +119,16 @@ _SIGS = {
     "imex_batch_get_stats": [_P, C.POINTER(imex_stats)],
     "imex_batch_group_info": [_P, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_longlong),
                               C.POINTER(imex_stats), _D],
+    "imex_server_create": [C.POINTER(imex_server_desc), C.POINTER(_P)],
+    "imex_server_destroy": [_P],
+    "imex_server_last_error": [_P],
+    "imex_server_submit": [_P, C.POINTER(imex_request), C.POINTER(C.c_longlong)],
+    "imex_server_tick": [_P, C.POINTER(C.c_int)],
+    "imex_server_poll": [_P, C.c_longlong, C.POINTER(C.c_int), C.POINTER(C.c_int), _D],
+    "imex_server_result": [_P, C.c_longlong, _D],
+    "imex_server_get_stats": [_P, C.POINTER(imex_server_stats)],
 }
+REQ_QUEUED, REQ_ACTIVE, REQ_DONE, REQ_FAILED = range(4)
 PROF_PRESSURE_F32, PROF_PRESSURE_F64, PROF_HELMHOLTZ_F32, PROF_HELMHOLTZ_F64, PROF_CONV = range(5)
 REDUCE_DOT, REDUCE_SUM, REDUCE_MAXABS = range(3)
 
@@ -140,7 +173,8 @@ def load(path=None):
         f = getattr(lib, name)
         f.argtypes = args
         f.restype = {"imex_last_error": C.c_char_p, "imex_destroy": None, "imex_batch_last_error": C.c_char_p,
-                     "imex_batch_destroy": None, "imex_launch_count": C.c_longlong}.get(name, C.c_int)
+                     "imex_batch_destroy": None, "imex_server_last_error": C.c_char_p,
+                     "imex_server_destroy": None, "imex_launch_count": C.c_longlong}.get(name, C.c_int)
     _lib = lib
     return lib
 
@@ -443,6 +477,84 @@ class Batch:
     def close(self):
         if getattr(self, "_h", None):
             load().imex_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _fill8(arr, vals):
+    for i, v in enumerate(list(vals or ())[:8]):
+        arr[i] = float(v)
+
+
+class Server:
+    """Continuous-batching server (wraps imex_server*): requests are admitted under an HBM
+    budget and every tick advances all active requests by one step."""
+
+    def __init__(self, budget_bytes=0.0, precision=MIXED, poisson=POISSON_SIPG, tol=1e-10, maxit=20000, vmax=0.0,
+                 keep_results=False):
+        d = imex_server_desc(float(budget_bytes), precision, poisson, tol, maxit, vmax, int(bool(keep_results)))
+        h = _P()
+        st = load().imex_server_create(C.byref(d), C.byref(h))
+        if st != OK:
+            raise ImexError(st, "imex_server_create failed")
+        self._h = h
+        self._sizes = {}
+
+    def _check(self, st):
+        if st != OK:
+            raise ImexError(st, load().imex_server_last_error(self._h).decode())
+
+    def submit(self, dim, P, nelem, lo, hi, periodic, flow, flow_params=(), nu_kind=NU_CONST, nu_params=(),
+               bc_kind=FLOW_NONE, bc_params=(), f_kind=FORCE_NONE, f_params=(), t0=0.0, dt=0.01, nsteps=1):
+        r = imex_request()
+        r.dim, r.P = dim, P
+        for k in range(3):
+            r.nelem[k] = int(nelem[k]) if k < len(nelem) else 1
+            r.lo[k] = float(lo[k]) if k < len(lo) else 0.0
+            r.hi[k] = float(hi[k]) if k < len(hi) else 1.0
+            r.periodic[k] = int(bool(periodic[k])) if k < len(periodic) else 1
+        r.flow, r.nu_kind, r.bc_kind, r.f_kind = flow, nu_kind, bc_kind, f_kind
+        _fill8(r.flow_params, flow_params)
+        _fill8(r.nu_params, nu_params)
+        _fill8(r.bc_params, bc_params)
+        _fill8(r.f_params, f_params)
+        r.t0, r.dt, r.nsteps = t0, dt, nsteps
+        i = C.c_longlong()
+        self._check(load().imex_server_submit(self._h, C.byref(r), C.byref(i)))
+        ne = 1
+        for k in range(dim):
+            ne *= int(nelem[k])
+        self._sizes[i.value] = dim * ne * (P + 1) ** dim
+        return i.value
+
+    def tick(self):
+        a = C.c_int()
+        self._check(load().imex_server_tick(self._h, C.byref(a)))
+        return a.value
+
+    def poll(self, i):
+        st, n, t = C.c_int(), C.c_int(), C.c_double()
+        self._check(load().imex_server_poll(self._h, i, C.byref(st), C.byref(n), C.byref(t)))
+        return st.value, n.value, t.value
+
+    def result(self, i):
+        out = np.empty(self._sizes[i])
+        self._check(load().imex_server_result(self._h, i, out.ctypes.data_as(_D)))
+        return out
+
+    def stats(self):
+        s = imex_server_stats()
+        self._check(load().imex_server_get_stats(self._h, C.byref(s)))
+        return s.as_dict()
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().imex_server_destroy(self._h)
             self._h = None
 
     def __del__(self):
