@@ -45,8 +45,10 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-only", action="store_true", help="short run for ncu captures")
-    ap.add_argument("--workload", default="tg3d", choices=["tg3d", "ensemble"],
-                    help="tg3d: the headline line; ensemble: the 256-instance batched 2D workload alone")
+    ap.add_argument("--workload", default="tg3d", choices=["tg3d", "ensemble", "serving"],
+                    help="tg3d: the headline line; ensemble / serving: that workload alone")
+    ap.add_argument("--serving-requests", type=int, default=24,
+                    help="requests of the serving stream replayed inside the headline line (0: skip)")
     ap.add_argument("--ensemble-steps", type=int, default=3,
                     help="timed steps of the 256-instance ensemble reported inside the headline line (0: skip)")
     return ap.parse_args()
@@ -249,6 +251,89 @@ def run_ensemble(imex, torch, steps, warmup=1, precision="mixed", tol=1e-10):
             "poisson_iters": st["poisson_iters"], "max_rel_l2_error_first16": err, "groups_detail": groups}
 
 
+def serving_stream(n, seed=1, rate=50.0):
+    """The serving workload: Poisson arrivals at `rate` requests/s; d in {2, 3} equiprobable;
+    2D: K ~ U{4..32}, P ~ U{3..8}, flow TG or MMS; 3D: K ~ U{4..24}, P ~ U{3..7}, flow TG;
+    steps ~ U{10..100}; dt for CFL_lambda = 0.3."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    t, out = 0.0, []
+    for _ in range(n):
+        t += rng.exponential(1.0 / rate)
+        d = int(rng.integers(2, 4))
+        if d == 2:
+            K, P = int(rng.integers(4, 33)), int(rng.integers(3, 9))
+            flow = "mms" if rng.random() < 0.5 else "tg"
+        else:
+            K, P = int(rng.integers(4, 25)), int(rng.integers(3, 8))
+            flow = "tg"
+        steps = int(rng.integers(10, 101))
+        out.append({"arrival": t, "d": d, "K": K, "P": P, "flow": flow, "steps": steps})
+    return out
+
+
+def serving_request(imex, q):
+    d, K, P = q["d"], q["K"], q["P"]
+    if q["flow"] == "mms":
+        nu0, h, vref = 0.01, 1.0 / K, 5 ** 0.5
+        dt = 0.3 / (vref * rho_hat(P) * 2.0 / h)
+        return dict(dim=2, P=P, nelem=(K, K), lo=(0, 0), hi=(1, 1), periodic=(0, 0), flow=imex.FLOW_TGTRAVEL,
+                    flow_params=[nu0], nu_kind=imex.NU_VARXYT, nu_params=[nu0], bc_kind=imex.FLOW_TGTRAVEL,
+                    bc_params=[nu0], f_kind=imex.FORCE_TGTRAVEL_VARNU, f_params=[nu0], dt=dt, nsteps=q["steps"])
+    h = TWO_PI / K
+    dt = 0.3 / (1.0 * rho_hat(P) * 2.0 / h)
+    if d == 2:
+        nu = 0.01
+        return dict(dim=2, P=P, nelem=(K, K), lo=(0, 0), hi=(TWO_PI, TWO_PI), periodic=(1, 1), flow=imex.FLOW_TG2D,
+                    flow_params=[nu], nu_kind=imex.NU_CONST, nu_params=[nu], dt=dt, nsteps=q["steps"])
+    return dict(dim=3, P=P, nelem=(K, K, K), lo=(0, 0, 0), hi=(TWO_PI,) * 3, periodic=(1, 1, 1),
+                flow=imex.FLOW_TG3D, nu_kind=imex.NU_CONST, nu_params=[1.0 / 1600], dt=dt, nsteps=q["steps"])
+
+
+def run_serving(imex, n_requests, precision="mixed", tol=1e-10):
+    """Replays the first n_requests of the serving stream in wall-clock time: a request is
+    submitted once its arrival time has passed, and the server ticks (admission, repack,
+    one step of every active request) until every request has finished."""
+    stream = serving_stream(n_requests)
+    sv = imex.Server(budget_bytes=0.0, precision=imex.MIXED if precision == "mixed" else imex.FP64, tol=tol,
+                     maxit=20000)
+    ids, arrive, finish = [], {}, {}
+    w0 = time.perf_counter()
+    nxt = 0
+    while True:
+        now = time.perf_counter() - w0
+        while nxt < len(stream) and stream[nxt]["arrival"] <= now:
+            i = sv.submit(**serving_request(imex, stream[nxt]))
+            ids.append(i)
+            arrive[i] = now
+            nxt += 1
+        if nxt < len(stream) and sv.stats()["active"] == 0 and sv.stats()["queued"] == 0:
+            time.sleep(max(0.0, stream[nxt]["arrival"] - now))
+            continue
+        sv.tick()
+        now = time.perf_counter() - w0
+        for i in ids:
+            if i not in finish and sv.poll(i)[0] in (imex.REQ_DONE, imex.REQ_FAILED):
+                finish[i] = now
+        if nxt == len(stream) and len(finish) == len(stream):
+            break
+    wall = time.perf_counter() - w0
+    st = sv.stats()
+    lat = sorted(finish[i] - arrive[i] for i in ids)
+    sv.close()
+    return {"workload": f"first {n_requests} requests of the serving stream: Poisson arrivals at 50 req/s (seed 1), "
+                        "d in {2,3}; 2D K~U{4..32}, P~U{3..8}, TG or MMS; 3D K~U{4..24}, P~U{3..7}, TG; "
+                        "steps~U{10..100}; dt for CFL_lambda=0.3; RK-CB3e",
+            "requests": n_requests, "completed": st["completed"], "failed": st["failed"],
+            "p50_step_ms": st["p50_tick_ms"], "p99_step_ms": st["p99_tick_ms"], "ticks": st["ticks"],
+            "value": st["dof_stages"] / wall, "unit": UNIT, "dof_stages": st["dof_stages"], "wall_s": wall,
+            "busy_s": st["busy_s"], "p50_request_latency_s": lat[len(lat) // 2],
+            "p99_request_latency_s": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+            "max_footprint_gb": st["max_footprint_bytes"] / 1e9, "budget_gb": st["budget_bytes"] / 1e9,
+            "precision": precision,
+            "timing": "host wall clock; a step (tick) = admission + repack + one step of every active request"}
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
@@ -297,6 +382,14 @@ def main():
     __graft_entry__.build()
     from paper_2112_04167_gb300 import imex
 
+    if args.workload == "serving":
+        e = run_serving(imex, max(1, args.serving_requests), precision=args.precision)
+        print(json.dumps({"metric": METRIC, "value": e["value"], "unit": UNIT, "n_gpus": world, "steps": e["ticks"],
+                          "warmup": 0, "ms_per_step": e["p50_step_ms"], "higher_is_better": True,
+                          "scaling": "weak", "vs_baseline": None, "dtype": "f32 operators + f64 refinement",
+                          "data": "synthetic (closed-form flows)", "config": {"workload": e["workload"]},
+                          "serving": e}))
+        return 0
     if args.workload == "ensemble":
         e = run_ensemble(imex, torch, max(1, args.steps), warmup=args.warmup, precision=args.precision)
         print(json.dumps({"metric": METRIC, "value": e["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -423,6 +516,9 @@ def main():
     ens = None
     if args.ensemble_steps > 0:
         ens = run_ensemble(imex, torch, args.ensemble_steps, warmup=1, precision=args.precision)
+    serving = None
+    if args.serving_requests > 0:
+        serving = run_serving(imex, args.serving_requests, precision=args.precision)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -446,7 +542,7 @@ def main():
             "p50_step_ms": statistics.median(per_step),
             "p99_step_ms": sorted(per_step)[min(len(per_step) - 1, int(0.99 * len(per_step)))],
             "clocks": clocks, "gpu_launches": launches, "roofline": roof, "kernels": prof,
-            "e2e": e2e, "fp64": fp64, "cpu_baseline": cpu, "ensemble": ens,
+            "e2e": e2e, "fp64": fp64, "cpu_baseline": cpu, "ensemble": ens, "serving": serving,
             "solver": {"poisson_iters_per_call": stats["poisson_iters"], "helmholtz_iters": stats["helmholtz_iters"],
                        "refinements": stats["refinements"], "max_poisson_res": stats["max_poisson_res"],
                        "max_helmholtz_res": stats["max_helmholtz_res"]},
