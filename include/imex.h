@@ -43,7 +43,13 @@ typedef enum {
 } imex_status;
 
 /* arithmetic of the solves */
-enum { IMEX_FP64 = 0, IMEX_MIXED = 1 };
+/* IMEX_FP64: every operator and solve in FP64.
+   IMEX_MIXED: FP32 inner iterations of the Poisson and Helmholtz solves with FP64 refinement
+     (true residual, iterate); explicit operators, stage storage and combinations in FP64 --
+     the result matches IMEX_FP64 to the solver tolerance.
+   IMEX_MIXED_FAST: IMEX_MIXED plus FP32 explicit operators (convection, F_d1) on FP32 copies
+     of the state; adds an FP32 rounding error of about 1e-8 relative per step. */
+enum { IMEX_FP64 = 0, IMEX_MIXED = 1, IMEX_MIXED_FAST = 2 };
 /* pressure operator: SIPG on Q_{P-1} (Sec. 3.3), or B M^-1 B^T (discretely divergence-free) */
 enum { IMEX_POISSON_SIPG = 0, IMEX_POISSON_CONSISTENT = 1 };
 /* closed-form flows (initial / Dirichlet data); params[0] = nu_0 */
@@ -62,7 +68,7 @@ typedef struct {
   int nelem[3];         /* elements per direction (nelem[2] ignored for dim 2) */
   double lo[3], hi[3];  /* box corners */
   int periodic[3];      /* 1 periodic; 0: Dirichlet velocity / Neumann pressure on both ends */
-  int precision;        /* IMEX_FP64 or IMEX_MIXED */
+  int precision;        /* IMEX_FP64, IMEX_MIXED or IMEX_MIXED_FAST */
   int poisson;          /* IMEX_POISSON_SIPG or IMEX_POISSON_CONSISTENT */
   double tol;           /* relative residual tolerance of every solve, ||r|| <= tol ||b|| (Sec. 4 uses 1e-12) */
   int maxit;            /* CG iteration limit per (inner) solve */
@@ -197,7 +203,9 @@ imex_status imex_reduce_noalloc(int op, const double* x, const double* y, long l
    (FP32 inner / FP64) and the convection kernel */
 enum {
   IMEX_PROF_PRESSURE_F32 = 0, IMEX_PROF_PRESSURE_F64 = 1, IMEX_PROF_HELMHOLTZ_F32 = 2,
-  IMEX_PROF_HELMHOLTZ_F64 = 3, IMEX_PROF_CONV = 4, IMEX_PROF_NCLASS = 5
+  IMEX_PROF_HELMHOLTZ_F64 = 3, IMEX_PROF_CONV = 4,
+  IMEX_PROF_PCG_PERSIST = 5,   /* persistent FP32 pressure CG launches (many iterations each) */
+  IMEX_PROF_NCLASS = 6
 };
 /* enable (1) or disable (0) CUDA-event timing of the classes above on the context's
    stream; enabling resets the accumulated records */
@@ -251,7 +259,7 @@ imex_status imex_batch_group_info(const imex_batch* b, int q, int* ninst, int* P
 typedef struct imex_server imex_server;
 typedef struct {
   double hbm_budget_bytes;  /* device bytes the active requests may occupy (<= 0: half the free memory) */
-  int precision;            /* IMEX_FP64 | IMEX_MIXED */
+  int precision;            /* IMEX_FP64 | IMEX_MIXED | IMEX_MIXED_FAST */
   int poisson;              /* IMEX_POISSON_SIPG | IMEX_POISSON_CONSISTENT */
   double tol;               /* solver tolerance (<= 0: 1e-10) */
   int maxit;                /* (<= 0: 20000) */

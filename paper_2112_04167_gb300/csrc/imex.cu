@@ -229,6 +229,10 @@ struct imex_ctx {
   };
   std::vector<GraphEntry> graphs;
   bool use_graphs = true;
+  // persistent FP32 CG of the periodic 3D pressure solves: partial sums, barrier, error flag
+  bool use_persist = false;
+  double* persist_partial = nullptr;   // 5 x 4096
+  unsigned int* persist_bar = nullptr; // [2] barrier + [1] error flag (as int)
   imex_stats stats{};
   double last_res = 0.0;
   // CUDA-event timing of kernel classes
@@ -708,11 +712,26 @@ imex_status pcg_mixed(imex_ctx* c, const imex_ctx::Seg& sg, Op64 op64, Op32 op32
     }
     return IMEX_OK;
   };
+  // the periodic 3D pressure solve of one instance runs its inner iterations persistently
+  bool persist = c->use_persist && !c->batched && project && nsys == 1 && fused && c->d == 3 &&
+                 c->gp.bc[0] == 0 && c->gp.bc[1] == 0 && c->gp.bc[2] == 0;
   for (int round = 0;; ++round) {
     bool all = true;
     for (int s = 0; s < nsys; ++s) all = all && done_h[s] == 4;
     if (all) break;
-    TRY(run_graph(c, key, body));
+    int rc = -1;
+    if (persist) {
+      CK(cudaMemsetAsync(c->persist_bar, 0, 4 * sizeof(unsigned int), c->st), "memset");
+      SipgArgs<float> a = sipg_args<float>(p, Ap, 1, (long long)c->np, nullptr, 1.0, nullptr, 0.0, 1.0, 0);
+      a.ops = line_ops<float>(c, false);
+      prof_mark(c, IMEX_PROF_PCG_PERSIST, true);
+      rc = pcg_persist_f32(c->gp, c->Np, a, y, r, p, Ap, dinv, (long long)ntot, sc, delta * delta * rr_ref[0], maxit,
+                           c->persist_partial, c->persist_bar, (int*)(c->persist_bar + 2), c->st);
+      prof_mark(c, IMEX_PROF_PCG_PERSIST, false);
+      if (rc == 0) TRY(cuda_check(c, cudaGetLastError(), "pcg_persist"));
+      else persist = false;
+    }
+    if (rc != 0) TRY(run_graph(c, key, body));
     TRY(pull_scalars(c, nsys));
     bool need = false;
     for (int s = 0; s < nsys; ++s) {
@@ -895,11 +914,25 @@ imex_status graddiv(imex_ctx* c, const double* v, const double* nu, double* fd3,
 imex_status stage_rhs(imex_ctx* c, double t, const double* v, const double* nu, const double* vb, double* E,
                       double* Fd1, double* Fd3, double* Fs) {
   const size_t nt = c->nv * c->d;
-  ConvArgs<double> ca{v, (long long)c->nv, vb, 1.0, E};
-  prof_mark(c, IMEX_PROF_CONV, true);
-  const int rc = dg_conv<double>(c->gv, c->Nv, ca, c->st);
-  prof_mark(c, IMEX_PROF_CONV, false);
-  TRY(launch_check(c, rc, "dg_conv"));
+  // IMEX_MIXED_FAST applies the explicit operators (convection, F_d1) in FP32 from FP32
+  // copies of v and the boundary data; the stage storage and every combination stay FP64
+  const bool f32 = c->desc.precision == IMEX_MIXED_FAST;
+  if (f32) {
+    convert_d2f(v, c->fx, nt, c->st);
+    if (vb) convert_d2f(vb, c->fr, nt, c->st);
+    ConvArgs<float> ca{c->fx, (long long)c->nv, vb ? c->fr : nullptr, 1.f, c->fp};
+    prof_mark(c, IMEX_PROF_CONV, true);
+    const int rc = dg_conv<float>(c->gv, c->Nv, ca, c->st);
+    prof_mark(c, IMEX_PROF_CONV, false);
+    TRY(launch_check(c, rc, "dg_conv(f32)"));
+    f2d(c->fp, E, nt, c->st);
+  } else {
+    ConvArgs<double> ca{v, (long long)c->nv, vb, 1.0, E};
+    prof_mark(c, IMEX_PROF_CONV, true);
+    const int rc = dg_conv<double>(c->gv, c->Nv, ca, c->st);
+    prof_mark(c, IMEX_PROF_CONV, false);
+    TRY(launch_check(c, rc, "dg_conv"));
+  }
   const bool varnu = variable_nu(c);
   if (varnu) {
     // E += F_d2 + F_d3 (F_d2 accumulated by the kernel)
@@ -911,10 +944,25 @@ imex_status stage_rhs(imex_ctx* c, double t, const double* v, const double* nu, 
     // constant nu: F_d2 + F_d3 = 0 exactly for the discrete operators; E = F_c
     TRY(graddiv(c, v, nu, Fd3, nullptr));
   }
-  SipgArgs<double> a = sipg_args<double>(v, Fd1, c->d, (long long)c->nv, nu_ptr(c, nu), nu_const(c), vb, 0.0, -1.0, 1);
-  a.ops = c->ops64_v;
-  vel_flags(c, a, false);
-  TRY(launch_check(c, sipg_apply<double>(c->gv, c->Nv, a, c->st), "sipg_apply(Fd1)"));
+  if (f32) {
+    const float* fnu = nullptr;
+    if (nu_ptr(c, nu)) {
+      convert_d2f(nu, c->fnu, c->nv, c->st);
+      fnu = c->fnu;
+    }
+    SipgArgs<float> a = sipg_args<float>(c->fx, c->fp, c->d, (long long)c->nv, fnu, nu_const(c), vb ? c->fr : nullptr,
+                                         0.0, -1.0, 1);
+    a.ops = c->ops32_v;
+    vel_flags(c, a, false);
+    TRY(launch_check(c, sipg_apply<float>(c->gv, c->Nv, a, c->st), "sipg_apply(Fd1, f32)"));
+    f2d(c->fp, Fd1, nt, c->st);
+  } else {
+    SipgArgs<double> a = sipg_args<double>(v, Fd1, c->d, (long long)c->nv, nu_ptr(c, nu), nu_const(c), vb, 0.0, -1.0,
+                                           1);
+    a.ops = c->ops64_v;
+    vel_flags(c, a, false);
+    TRY(launch_check(c, sipg_apply<double>(c->gv, c->Nv, a, c->st), "sipg_apply(Fd1)"));
+  }
   if (Fs) {
     TRY(launch_check(c, eval_field(c->gv, c->Nv, 2, spec(c->f_kind, c->f_p), t, nullptr, (long long)c->nv, Fs, c->st),
                      "eval_field(f)"));
@@ -1395,6 +1443,10 @@ imex_status init_ctx(imex_ctx* c) {
   if ((s = dalloc(c, &c->apartial, (size_t)(c->ne_cap + 64) * 3)) != IMEX_OK) return bail(s);
   if ((s = dalloc(c, &c->counters, 8)) != IMEX_OK) return bail(s);
   cudaMemsetAsync(c->counters, 0, 8 * sizeof(unsigned int), c->st);
+  if ((s = dalloc(c, &c->persist_partial, 5 * 4096)) != IMEX_OK) return bail(s);
+  if ((s = dalloc(c, &c->persist_bar, 4)) != IMEX_OK) return bail(s);
+  c->use_persist = false;      // measured slower than the graph-replayed kernels; opt in with IMEX_PERSIST=1
+  if (const char* e = std::getenv("IMEX_PERSIST")) c->use_persist = std::atoi(e) != 0;
   if ((s = dalloc(c, &c->dscal, 128)) != IMEX_OK) return bail(s);
   if ((s = dalloc(c, &c->iscal, 64)) != IMEX_OK) return bail(s);
   if (cudaMallocHost((void**)&c->hscal, 128 * sizeof(double)) != cudaSuccess) return bail(IMEX_ENOMEM);
@@ -1692,7 +1744,8 @@ imex_status imex_create(const imex_mesh_desc* desc, imex_ctx** out) {
     if (desc->nelem[k] < 1) return IMEX_EINVAL;
     if (!(desc->hi[k] > desc->lo[k])) return IMEX_EINVAL;
   }
-  if (desc->precision != IMEX_FP64 && desc->precision != IMEX_MIXED) return IMEX_EINVAL;
+  if (desc->precision != IMEX_FP64 && desc->precision != IMEX_MIXED && desc->precision != IMEX_MIXED_FAST)
+    return IMEX_EINVAL;
   if (desc->poisson != IMEX_POISSON_SIPG && desc->poisson != IMEX_POISSON_CONSISTENT) return IMEX_EINVAL;
   imex_ctx* c = new imex_ctx();
   c->desc = *desc;
@@ -2392,7 +2445,8 @@ imex_status server_regroup(imex_server* sv, imex_server::Group& G) {
 
 imex_status imex_server_create(const imex_server_desc* desc, imex_server** out) {
   if (!desc || !out) return IMEX_EINVAL;
-  if (desc->precision != IMEX_FP64 && desc->precision != IMEX_MIXED) return IMEX_EINVAL;
+  if (desc->precision != IMEX_FP64 && desc->precision != IMEX_MIXED && desc->precision != IMEX_MIXED_FAST)
+    return IMEX_EINVAL;
   imex_server* sv = new imex_server();
   sv->desc = *desc;
   sv->budget = desc->hbm_budget_bytes;

@@ -603,6 +603,7 @@ template int dg_div<double>(const Geom&, int, const DivArgs<double>&, cudaStream
 template int dg_grad<double>(const Geom&, int, const GradArgs<double>&, cudaStream_t);
 template int dg_deriv<double>(const Geom&, int, const DerivArgs<double>&, cudaStream_t);
 template int dg_conv<double>(const Geom&, int, const ConvArgs<double>&, cudaStream_t);
+template int dg_conv<float>(const Geom&, int, const ConvArgs<float>&, cudaStream_t);
 template int dg_div<float>(const Geom&, int, const DivArgs<float>&, cudaStream_t);
 template int dg_grad<float>(const Geom&, int, const GradArgs<float>&, cudaStream_t);
 

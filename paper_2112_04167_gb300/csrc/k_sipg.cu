@@ -17,6 +17,7 @@
 
 #include "common.cuh"
 #include "kernels.h"
+#include "vec.h"
 
 namespace imex {
 
@@ -822,9 +823,12 @@ constexpr size_t sipg3p_smem() {
   return sizeof(T) * (size_t)(S::EPB * S::TILE + S::EPB * 8 * S::NN);
 }
 
+// One group of EPB elements (group index grp) of the periodic constant-coefficient apply
+// y = alpha M x + beta nu0 A x; every thread of the block must call it (it holds a barrier);
+// returns this thread's share of (x, y).  Consecutive calls need a barrier in between.
 template <typename T, int N>
-__global__ void __launch_bounds__(Sipg3pShape<T, N>::THREADS, (sizeof(T) == 4 && N <= 8) ? 3 : 1)
-sipg3p_apply_kernel(Geom g, SipgArgs<T> a) {
+__device__ __forceinline__ T sipg3p_group(const Geom& g, const SipgArgs<T>& a, const T* __restrict__ x,
+                                          T* __restrict__ y, int grp) {
   using S = Sipg3pShape<T, N>;
   constexpr int NN = S::NN, ND = N * N * N, EPB = S::EPB, NP = S::NP, TILE = S::TILE, VEC = S::VEC;
   using V = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
@@ -835,7 +839,7 @@ sipg3p_apply_kernel(Geom g, SipgArgs<T> a) {
   const int le = threadIdx.x / NN;
   const int t = threadIdx.x - le * NN;
   const int i0 = t % N, i1 = t / N;
-  const int e = blockIdx.x * EPB + le;
+  const int e = grp * EPB + le;
   const bool valid = e < g.ne;
   int el = 0;
   Geom gl = g;
@@ -859,11 +863,7 @@ sipg3p_apply_kernel(Geom g, SipgArgs<T> a) {
   const size_t ebase = (size_t)e * ND;
   const T scale = sipg_beta(a, gl) * sipg_nu0(a, gl);
   T* mytile = tile + le * TILE;
-  __shared__ double red[S::THREADS];
-  for (int s = 0; s < a.nsys; ++s) {
-    const T* x = a.x + (size_t)s * a.sys_stride;
-    T* y = a.y + (size_t)s * a.sys_stride;
-    if (s > 0) __syncthreads();
+  {
     T u[N];
     T zt0 = T(0), zd0 = T(0), zt1 = T(0), zd1 = T(0);
     T dacc = T(0);
@@ -957,12 +957,444 @@ sipg3p_apply_kernel(Geom g, SipgArgs<T> a) {
         dacc += u[k] * out;
       }
     }
+    return dacc;
+  }
+}
+
+// Line-owner form of the same group apply: three passes over the element, one per direction,
+// in each of which a thread owns one whole line of N nodes along that direction (z: column
+// (i0, i1), y: column (i0, k), x: row (i1, k)).  It reads its line once (registers for z, the
+// shared tile for y and x), loads the two neighbours' lines along the same direction from
+// global memory (coalesced across the threads of a warp), and produces the N outputs of the
+// 1D operator from registers; the three directional contributions meet in a shared
+// accumulator.  Per node: about one shared load and two global loads per pass instead of a
+// strided shared read for every term.
+template <typename T, int N>
+struct Sipg3lShape {
+  static constexpr int NN = N * N;
+  static constexpr int ND = N * N * N;
+  static constexpr int EPB = (NN >= 49) ? 4 : (NN >= 16 ? 256 / NN : 16);
+  static constexpr int THREADS = EPB * NN;
+  static constexpr int VEC = 16 / sizeof(T);
+  static constexpr int NP = ((N + VEC - 1) / VEC) * VEC;
+  static constexpr int TILE = N * N * NP;
+};
+
+template <typename T, int N>
+constexpr size_t sipg3l_smem() {
+  using S = Sipg3lShape<T, N>;
+  return sizeof(T) * (size_t)(S::EPB * S::TILE + S::EPB * S::ND);
+}
+
+template <typename T, int N>
+__device__ __forceinline__ T sipg3l_group(const Geom& g, const SipgArgs<T>& a, const T* __restrict__ x,
+                                          T* __restrict__ y, int grp) {
+  using S = Sipg3lShape<T, N>;
+  constexpr int NN = S::NN, ND = S::ND, EPB = S::EPB, NP = S::NP, TILE = S::TILE, VEC = S::VEC;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* tile = reinterpret_cast<T*>(smem_raw);                       // [EPB][z][y][NP]
+  T* acc = tile + EPB * TILE;                                     // [EPB][z][y][x]
+  const ConstLine<T>& L = cline<T>(N);
+  const int le = threadIdx.x / NN;
+  const int t = threadIdx.x - le * NN;
+  const int e = grp * EPB + le;
+  const bool valid = e < g.ne;
+  int el = 0;
+  Geom gl = g;
+  if (valid) gl = local_geom(g, e, el);
+  int nb[6] = {0, 0, 0, 0, 0, 0};
+  if (valid) {
+    int ec[3];
+    elem_coords(gl, el, ec);
+#pragma unroll
+    for (int f = 0; f < 6; ++f) nb[f] = neighbor(gl, ec, f >> 1, (f & 1) ? 1 : -1);
+  }
+  const T hx = geom_h<T>(gl, 0), hy = geom_h<T>(gl, 1), hz = geom_h<T>(gl, 2);
+  const T ihx = T(1) / hx, ihy = T(1) / hy, ihz = T(1) / hz;
+  const T scale = sipg_beta(a, gl) * sipg_nu0(a, gl);
+  T* mt = tile + le * TILE;
+  T* ma = acc + le * ND;
+  const size_t eb = (size_t)e * ND;
+  const int ta = t % N, tb = t / N;                               // the thread's two line coordinates
+  // own element into the shared tile; the z-column (ta, tb) stays in registers
+  T u[N];
+#pragma unroll
+  for (int k = 0; k < N; ++k) u[k] = T(0);
+  if (valid) {
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+      u[k] = x[eb + k * NN + t];
+      mt[(k * N + tb) * NP + ta] = u[k];
+    }
+  }
+  // pass z: line (x = ta, y = tb) along z
+  if (valid) {
+    const T* cl = x + (size_t)nb[4] * ND + t;
+    const T* cr = x + (size_t)nb[5] * ND + t;
+    T vl[N], vr[N];
+#pragma unroll
+    for (int j = 0; j < N; ++j) { vl[j] = cl[j * NN]; vr[j] = cr[j * NN]; }
+    T dl = T(0), dr = T(0);
+#pragma unroll
+    for (int j = 0; j < N; ++j) { dl += L.dnL[j] * vl[j]; dr += L.dnR[j] * vr[j]; }
+    const T tl = vl[N - 1], tr = vr[0];
+    const T wt = (T(0.5) * hx * L.w[ta]) * (T(0.5) * hy * L.w[tb]) * ihz;
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+      T sk = L.ctrL[k] * tl + L.cdnL[k] * dl + L.ctrR[k] * tr + L.cdnR[k] * dr;
+#pragma unroll
+      for (int j = 0; j < N; ++j) sk += L.A[k * N + j] * u[j];
+      ma[k * NN + t] = wt * sk;
+    }
+  }
+  __syncthreads();
+  // pass y: line (x = ta, z = tb) along y
+  if (valid) {
+    T v[N];
+#pragma unroll
+    for (int j = 0; j < N; ++j) v[j] = mt[(tb * N + j) * NP + ta];
+    const T* cl = x + (size_t)nb[2] * ND + tb * NN + ta;
+    const T* cr = x + (size_t)nb[3] * ND + tb * NN + ta;
+    T vl[N], vr[N];
+#pragma unroll
+    for (int j = 0; j < N; ++j) { vl[j] = cl[j * N]; vr[j] = cr[j * N]; }
+    T dl = T(0), dr = T(0);
+#pragma unroll
+    for (int j = 0; j < N; ++j) { dl += L.dnL[j] * vl[j]; dr += L.dnR[j] * vr[j]; }
+    const T tl = vl[N - 1], tr = vr[0];
+    const T wt = (T(0.5) * hx * L.w[ta]) * (T(0.5) * hz * L.w[tb]) * ihy;
+#pragma unroll
+    for (int o = 0; o < N; ++o) {
+      T so = L.ctrL[o] * tl + L.cdnL[o] * dl + L.ctrR[o] * tr + L.cdnR[o] * dr;
+#pragma unroll
+      for (int j = 0; j < N; ++j) so += L.A[o * N + j] * v[j];
+      ma[(tb * N + o) * N + ta] += wt * so;
+    }
+  }
+  __syncthreads();
+  // pass x: line (y = ta, z = tb) along x, and the result
+  T dacc = T(0);
+  if (valid) {
+    T v[NP];
+    using V = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+    const V* rv = reinterpret_cast<const V*>(mt + (tb * N + ta) * NP);
+#pragma unroll
+    for (int q = 0; q < NP / VEC; ++q) {
+      const V w4 = rv[q];
+      const T* pw = reinterpret_cast<const T*>(&w4);
+#pragma unroll
+      for (int j = 0; j < VEC; ++j) v[q * VEC + j] = pw[j];
+    }
+    const T* rl = x + (size_t)nb[0] * ND + tb * NN + ta * N;
+    const T* rr = x + (size_t)nb[1] * ND + tb * NN + ta * N;
+    T vl[N], vr[N];
+#pragma unroll
+    for (int j = 0; j < N; ++j) { vl[j] = rl[j]; vr[j] = rr[j]; }
+    T dl = T(0), dr = T(0);
+#pragma unroll
+    for (int j = 0; j < N; ++j) { dl += L.dnL[j] * vl[j]; dr += L.dnR[j] * vr[j]; }
+    const T tl = vl[N - 1], tr = vr[0];
+    const T wyz = (T(0.5) * hy * L.w[ta]) * (T(0.5) * hz * L.w[tb]);
+    const T wt = wyz * ihx;
+#pragma unroll
+    for (int o = 0; o < N; ++o) {
+      T so = L.ctrL[o] * tl + L.cdnL[o] * dl + L.ctrR[o] * tr + L.cdnR[o] * dr;
+#pragma unroll
+      for (int j = 0; j < N; ++j) so += L.A[o * N + j] * v[j];
+      const int node = (tb * N + ta) * N + o;
+      const T W = wyz * (T(0.5) * hx * L.w[o]);
+      T out = a.alpha * W * v[o] + scale * (ma[node] + wt * so);
+      if (a.minv) out /= W;
+      y[eb + node] = out;
+      dacc += v[o] * out;
+    }
+  }
+  return dacc;
+}
+
+template <typename T, int N>
+__global__ void __launch_bounds__(Sipg3pShape<T, N>::THREADS, (sizeof(T) == 4 && N <= 8) ? 3 : 1)
+sipg3p_apply_kernel(Geom g, SipgArgs<T> a) {
+  __shared__ double red[Sipg3pShape<T, N>::THREADS];
+  for (int s = 0; s < a.nsys; ++s) {
+    if (s > 0) __syncthreads();
+    const T dacc = sipg3l_group<T, N>(g, a, a.x + (size_t)s * a.sys_stride, a.y + (size_t)s * a.sys_stride,
+                                      blockIdx.x);
     if (a.dot_out) {
       const double bs = block_sum_any_t<T>(dacc, red);
       if (threadIdx.x == 0) a.dot_partial[(size_t)s * gridDim.x + blockIdx.x] = bs;
     }
   }
   if (a.dot_out) fused_dot_finish(a, red);
+}
+
+// ---------------------------------------------------------------------------------
+// Persistent projected CG (FP32 inner iterations of the mixed form) for the periodic
+// constant-coefficient pressure operator of one instance: one cooperative launch runs
+// iterations -- apply A p with (p, A p), step, direction -- separated by grid barriers, until
+// the recursive residual meets the tolerance, falls below the replacement threshold, the
+// iteration limit is reached or the step breaks down.  Every block adds the per-block
+// partial sums in the same order, so all blocks hold identical scalars without a
+// broadcast.  The vectors (p, A p, r, y, D^{-1}) are L2-resident at the sizes this serves.
+// ---------------------------------------------------------------------------------
+struct PcgPersist {
+  float* y;
+  float* r;
+  float* p;
+  float* Ap;
+  const float* dinv;
+  long long n;
+  double stop_rr;          // leave for a residual replacement once (r', r') < stop_rr
+  double* partial;         // [5][gridDim.x]
+  unsigned int* bar;       // [2]: arrival counter, generation (zero at launch)
+  int* err;                // set when a barrier wait gives up
+};
+
+// grid-wide barrier of a cooperative launch; bounded wait (gives up with *err = 1)
+__device__ __forceinline__ void grid_barrier(unsigned int* bar, unsigned int& gen, int* err) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned int g = gen;
+    if (atomicAdd(&bar[0], 1u) == gridDim.x - 1) {
+      atomicExch(&bar[0], 0u);
+      __threadfence();
+      atomicExch(&bar[1], g + 1u);
+    } else {
+      volatile unsigned int* vg = bar + 1;
+      long long spins = 0;
+      while (*vg == g) {
+        __nanosleep(32);
+        if (++spins > (1LL << 25)) {
+          atomicExch(err, 1);
+          break;
+        }
+      }
+    }
+    __threadfence();
+  }
+  gen++;
+  __syncthreads();
+}
+
+// K sums over the block (any block size) into out[] (valid in every thread): per-thread
+// values summed in FP32 by warp 0, the K results converted once
+template <int K>
+__device__ __forceinline__ void persist_block_sum(const float (&v)[K], double (&out)[K], double* red) {
+  float* rf = reinterpret_cast<float*>(red);
+  __shared__ double res[8];
+  __syncthreads();
+  for (int k = 0; k < K; ++k) rf[k * blockDim.x + threadIdx.x] = v[k];
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    for (int k = 0; k < K; ++k) {
+      float s = 0.f;
+      for (int i = threadIdx.x; i < (int)blockDim.x; i += 32) s += rf[k * blockDim.x + i];
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (threadIdx.x == 0) res[k] = (double)s;
+    }
+  }
+  __syncthreads();
+  for (int k = 0; k < K; ++k) out[k] = res[k];
+}
+
+// totals over the blocks of K partial arrays (fixed order; identical in every block): the
+// threads' strided shares through shared memory, added by warp 0
+template <int K>
+__device__ __forceinline__ void persist_totals(const double* partial, int q0, double (&out)[K], double* red) {
+  __syncthreads();
+  for (int k = 0; k < K; ++k) {
+    double v = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) v += partial[(size_t)(q0 + k) * gridDim.x + b];
+    red[k * blockDim.x + threadIdx.x] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    for (int k = 0; k < K; ++k) {
+      double s = 0.0;
+      for (int i = threadIdx.x; i < (int)blockDim.x; i += 32) s += red[k * blockDim.x + i];
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (threadIdx.x == 0) red[K * blockDim.x + k] = s;
+    }
+  }
+  __syncthreads();
+  for (int k = 0; k < K; ++k) out[k] = red[K * blockDim.x + k];
+}
+
+template <int N>
+__global__ void __launch_bounds__(Sipg3pShape<float, N>::THREADS, (N <= 8) ? 5 : 1)
+pcg_persist_kernel(Geom g, SipgArgs<float> a, PcgPersist q, CgScalars sc, int maxit) {
+  using S = Sipg3pShape<float, N>;
+  __shared__ double red[5 * S::THREADS];
+  constexpr int NN = N * N, ND = N * N * N;
+  const int ngroups = (g.ne + S::EPB - 1) / S::EPB;
+  const long long n = q.n;
+  const int le = threadIdx.x / NN, tcol = threadIdx.x - le * NN;    // element of the group, column
+  unsigned int gen = 0;
+  double rz = sc.rz[0];
+  const double dsum = sc.dsum[0], thr = sc.tol2 * sc.bb[0];
+  const double nd = (double)n;
+  int iters = sc.iters[0];
+  int done = sc.done[0];
+  double rr = sc.rr[0], zmean = sc.zmean[0], rmean = sc.rmean[0], beta = 0.0, rz_old = sc.rz_old[0];
+  while (done == 0) {
+    // A p and (p, A p)
+    float dacc = 0.f;
+    for (int grp = blockIdx.x; grp < ngroups; grp += gridDim.x) {
+      __syncthreads();
+      dacc += sipg3l_group<float, N>(g, a, q.p, q.Ap, grp);
+    }
+    {
+      const float v[1] = {dacc};
+      double o[1];
+      persist_block_sum<1>(v, o, red);
+      if (threadIdx.x == 0) q.partial[blockIdx.x] = o[0];
+    }
+    grid_barrier(q.bar, gen, q.err);
+    if (*((volatile int*)q.err)) break;
+    double pap[1];
+    persist_totals<1>(q.partial, 0, pap, red);
+    const double alpha = pap[0] != 0.0 ? rz / pap[0] : 0.0;
+    if (!isfinite(alpha)) {
+      done = 2;
+      break;
+    }
+    // y += alpha p, r -= alpha A p on this block's element groups (the apply's node mapping:
+    // each thread a column of N nodes, all loads issued before the arithmetic); sums of the
+    // new residual
+    float s4[4] = {0.f, 0.f, 0.f, 0.f};
+    const float af = (float)alpha;
+    for (int grp = blockIdx.x; grp < ngroups; grp += gridDim.x) {
+      const int e = grp * S::EPB + le;
+      if (e >= g.ne) continue;
+      const size_t b0 = (size_t)e * ND + tcol;
+      float rv[N], av[N], dv[N], yv[N], pv[N];
+#pragma unroll
+      for (int k = 0; k < N; ++k) {
+        const size_t i = b0 + (size_t)k * NN;
+        rv[k] = q.r[i]; av[k] = q.Ap[i]; dv[k] = q.dinv[i]; yv[k] = q.y[i]; pv[k] = q.p[i];
+      }
+#pragma unroll
+      for (int k = 0; k < N; ++k) {
+        const size_t i = b0 + (size_t)k * NN;
+        const float ri = rv[k] - af * av[k];
+        const float zi = ri * dv[k];
+        q.y[i] = yv[k] + af * pv[k];
+        q.r[i] = ri;
+        s4[0] += ri * zi;
+        s4[1] += ri * ri;
+        s4[2] += zi;
+        s4[3] += ri;
+      }
+    }
+    {
+      double o[4];
+      persist_block_sum<4>(s4, o, red);
+      if (threadIdx.x == 0)
+        for (int k = 0; k < 4; ++k) q.partial[(size_t)(1 + k) * gridDim.x + blockIdx.x] = o[k];
+    }
+    grid_barrier(q.bar, gen, q.err);
+    if (*((volatile int*)q.err)) break;
+    double tot[4];
+    persist_totals<4>(q.partial, 1, tot, red);
+    const double rho = tot[3] / nd;
+    const double rzn = tot[0] - 2.0 * rho * tot[2] + rho * rho * dsum;
+    rr = fmax(tot[1] - nd * rho * rho, 0.0);
+    zmean = (tot[2] - rho * dsum) / nd;
+    rmean = rho;
+    beta = rz != 0.0 ? rzn / rz : 0.0;
+    rz_old = rz;
+    rz = rzn;
+    iters++;
+    if (rr != rr || !isfinite(beta)) done = 2;
+    else if (rr <= thr) done = 1;
+    else if (iters >= maxit) done = 3;
+    if (done != 0) break;
+    // next direction: p = D^{-1} (r - rho) - zmean + beta p, r -= rho
+    const float bf = (float)beta, zm = (float)zmean, rm = (float)rmean;
+    for (int grp = blockIdx.x; grp < ngroups; grp += gridDim.x) {
+      const int e = grp * S::EPB + le;
+      if (e >= g.ne) continue;
+      const size_t b0 = (size_t)e * ND + tcol;
+      float rv[N], dv[N], pv[N];
+#pragma unroll
+      for (int k = 0; k < N; ++k) {
+        const size_t i = b0 + (size_t)k * NN;
+        rv[k] = q.r[i]; dv[k] = q.dinv[i]; pv[k] = q.p[i];
+      }
+#pragma unroll
+      for (int k = 0; k < N; ++k) {
+        const size_t i = b0 + (size_t)k * NN;
+        const float ri = rv[k] - rm;
+        q.r[i] = ri;
+        q.p[i] = (ri * dv[k] - zm) + bf * pv[k];
+      }
+    }
+    if (rr < q.stop_rr) break;                        // residual replacement is due (p is current)
+    grid_barrier(q.bar, gen, q.err);
+    if (*((volatile int*)q.err)) break;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    sc.rz[0] = rz;
+    sc.rz_old[0] = rz_old;
+    sc.rr[0] = rr;
+    sc.zmean[0] = zmean;
+    sc.rmean[0] = rmean;
+    sc.zmean_f[0] = (float)zmean;
+    sc.rmean_f[0] = (float)rmean;
+    sc.beta[0] = beta;
+    sc.beta_f[0] = (float)beta;
+    sc.iters[0] = iters;
+    sc.done[0] = *((volatile int*)q.err) ? 2 : done;
+  }
+}
+
+template <int N>
+static int launch_persist(const Geom& g, const SipgArgs<float>& a, const PcgPersist& q, const CgScalars& sc,
+                          int maxit, int* grid_out, cudaStream_t st) {
+  using S = Sipg3pShape<float, N>;
+  constexpr size_t sm = sipg3l_smem<float, N>();
+  smem_limit_once((const void*)pcg_persist_kernel<N>, (int)sm);
+  int dev = 0, nsm = 0, per = 0, coop = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+  if (!coop) return -1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, pcg_persist_kernel<N>, S::THREADS, sm) != cudaSuccess ||
+      per < 1)
+    return -1;
+  const int ngroups = (g.ne + S::EPB - 1) / S::EPB;
+  const int grid = std::min(std::min(per * nsm, ngroups), 4096);
+  if (grid_out) *grid_out = grid;
+  Geom gg = g;
+  SipgArgs<float> aa = a;
+  PcgPersist qq = q;
+  CgScalars ss = sc;
+  void* args[] = {&gg, &aa, &qq, &ss, &maxit};
+  IMEX_COUNTED(cudaLaunchCooperativeKernel((const void*)pcg_persist_kernel<N>, dim3(grid), dim3(S::THREADS), args,
+                                           sm, st));
+  return 0;
+}
+
+int pcg_persist_f32(const Geom& g, int N, const SipgArgs<float>& a, float* y, float* r, float* p, float* Ap,
+                    const float* dinv, long long n, const CgScalars& sc, double stop_rr, int maxit, double* partial,
+                    unsigned int* bar, int* err, cudaStream_t st) {
+  if (g.d != 3 || g.inst || g.bc[0] || g.bc[1] || g.bc[2] || a.nu || !a.ops) return -1;
+  PcgPersist q{y, r, p, Ap, dinv, n, stop_rr, partial, bar, err};
+  SipgArgs<float> aa = a;
+  aa.x = p;
+  aa.y = Ap;
+  aa.nsys = 1;
+  aa.dot_out = nullptr;
+  switch (N) {
+    case 3: return launch_persist<3>(g, aa, q, sc, maxit, nullptr, st);
+    case 4: return launch_persist<4>(g, aa, q, sc, maxit, nullptr, st);
+    case 5: return launch_persist<5>(g, aa, q, sc, maxit, nullptr, st);
+    case 6: return launch_persist<6>(g, aa, q, sc, maxit, nullptr, st);
+    case 7: return launch_persist<7>(g, aa, q, sc, maxit, nullptr, st);
+    case 8: return launch_persist<8>(g, aa, q, sc, maxit, nullptr, st);
+    default: return -1;
+  }
 }
 
 // fill the constant-memory line operators once per device
@@ -1090,7 +1522,7 @@ template <typename T, int D, int N>
 static void launch_apply3(const Geom& g, const SipgArgs<T>& a, cudaStream_t st) {
   if (!a.nu && a.ops && g.bc[0] == 0 && g.bc[1] == 0 && g.bc[2] == 0) {
     using P = Sipg3pShape<T, N>;
-    constexpr size_t sm = sipg3p_smem<T, N>();
+    constexpr size_t sm = sipg3l_smem<T, N>();
     smem_limit_once((const void*)sipg3p_apply_kernel<T, N>, (int)sm);
     IMEX_COUNTED(sipg3p_apply_kernel<T, N><<<(g.ne + P::EPB - 1) / P::EPB, P::THREADS, sm, st>>>(g, a));
     return;

@@ -79,4 +79,16 @@ void seg_remove_mean(double* x, const SegTable& t, double* mean, double* partial
 void seg_remove_wmean(double* x, const double* w, const SegTable& t, double* mean, double* partial,
                       unsigned int* counter, cudaStream_t st);
 
+// Persistent projected FP32 CG for the periodic 3D constant-coefficient pressure operator
+// of one instance (k_sipg.cu): runs iterations in one cooperative launch until the
+// recursive residual meets tol^2 bb, drops below stop_rr (replacement due), maxit or a
+// breakdown; the scalars in sc are read at start and written back at exit.  partial: 5 x
+// (number of SMs x resident blocks) doubles; bar: two zeroed counters; err: zeroed flag set
+// when a barrier wait gives up.  Returns -1 when the case is not supported (nothing launched).
+struct Geom;
+template <typename T> struct SipgArgs;
+int pcg_persist_f32(const Geom& g, int N, const SipgArgs<float>& a, float* y, float* r, float* p, float* Ap,
+                    const float* dinv, long long n, const CgScalars& sc, double stop_rr, int maxit, double* partial,
+                    unsigned int* bar, int* err, cudaStream_t st);
+
 }  // namespace imex

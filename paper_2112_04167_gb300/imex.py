@@ -14,7 +14,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_lib", "libimexgb.so")
 
 OK, EINVAL, ENOMEM, ENOTCONV, EUNSTABLE, ECUDA = range(6)
-FP64, MIXED = 0, 1
+FP64, MIXED, MIXED_FAST = 0, 1, 2
 POISSON_SIPG, POISSON_CONSISTENT = 0, 1
 FLOW_NONE, FLOW_TG2D, FLOW_TG3D, FLOW_TGTRAVEL = 0, 1, 2, 3
 NU_CONST, NU_VARXYT, NU_VELOCITY, NU_FIELD = 0, 1, 2, 3
@@ -129,7 +129,7 @@ _SIGS = {
     "imex_server_get_stats": [_P, C.POINTER(imex_server_stats)],
 }
 REQ_QUEUED, REQ_ACTIVE, REQ_DONE, REQ_FAILED = range(4)
-PROF_PRESSURE_F32, PROF_PRESSURE_F64, PROF_HELMHOLTZ_F32, PROF_HELMHOLTZ_F64, PROF_CONV = range(5)
+PROF_PRESSURE_F32, PROF_PRESSURE_F64, PROF_HELMHOLTZ_F32, PROF_HELMHOLTZ_F64, PROF_CONV, PROF_PCG_PERSIST = range(6)
 REDUCE_DOT, REDUCE_SUM, REDUCE_MAXABS = range(3)
 
 

@@ -227,3 +227,16 @@ def test_reductions():
     assert np.isnan(ctx.reduce(imex.REDUCE_MAXABS, x))
     with pytest.raises(imex.ImexError):
         ctx.reduce(imex.REDUCE_SUM, np.zeros(n + 1))
+
+
+@pytest.mark.parametrize("case", [CASES[5], (3, 3, (3, 2, 3), (True, True, True)), (3, 8, (2, 3, 2), (True, True, True))])
+def test_sipg_pressure_periodic_fp32(case):
+    """The periodic constant-coefficient FP32 kernel (line-owner passes) on the pressure space."""
+    ctx, mesh = make(case)
+    P = case[1]
+    x = inputs.field(ctx.npres, seed=23)
+    L = dg.sipg_matrix(mesh, P, 1.0, dirichlet=False)
+    M = dg.mass_diag(mesh, P)
+    assert rel(ctx.op_sipg(x, space=imex.SPACE_PRESSURE, precision=imex.MIXED), L @ x) < 1e-5
+    y = ctx.op_sipg(x, space=imex.SPACE_PRESSURE, alpha=0.3, beta=1.7, minv=1, precision=imex.MIXED)
+    assert rel(y, (0.3 * M * x + 1.7 * (L @ x)) / M) < 1e-5

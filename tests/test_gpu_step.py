@@ -165,3 +165,51 @@ def test_invalid_inputs():
     d.init_flow(imex.FLOW_TGTRAVEL, [0.01])
     with pytest.raises(imex.ImexError):                  # Dirichlet sides need boundary data
         d.step(0.01, 1)
+
+
+@pytest.mark.parametrize("P,n", [(3, (3, 2, 2)), (5, (2, 3, 2)), (7, (2, 2, 2))])
+def test_mixed_precision_tg3d(P, n):
+    # 3D periodic: the inner FP32 iterations of the pressure solves run in one persistent launch
+    ctx = imex.Context(3, P, n, [0, 0, 0], [TWO_PI] * 3, (1, 1, 1), precision=imex.MIXED, tol=1e-12, maxit=50000)
+    ctx.set_viscosity_const(1.0 / 1600)
+    mesh = dg.Mesh(3, P, n, [0, 0, 0], [TWO_PI] * 3, (True, True, True))
+    fl = flows.Flow("tg3d", 1.0 / 1600)
+    disc = ns.Discretization(mesh, fl)
+    v0 = fl.initial(disc.X).reshape(3, -1)
+    run_steps(ctx, disc, lambda v, t, dt: ns.rk_step(disc, "CB3e", v, t, dt)[0], v0, 0.0, 0.05, 2, 1e-9)
+    assert ctx.stats()["refinements"] > 0
+
+
+@pytest.mark.parametrize("P,n", [(3, (3, 2, 2)), (7, (2, 2, 2))])
+def test_mixed_fast_tg3d(P, n):
+    # IMEX_MIXED_FAST adds FP32 explicit operators: their rounding (about eps32 times the
+    # convective and viscous terms, times dt) measured at 2e-8 .. 5e-8 relative per step here
+    ctx = imex.Context(3, P, n, [0, 0, 0], [TWO_PI] * 3, (1, 1, 1), precision=imex.MIXED_FAST, tol=1e-12,
+                       maxit=50000)
+    ctx.set_viscosity_const(1.0 / 1600)
+    mesh = dg.Mesh(3, P, n, [0, 0, 0], [TWO_PI] * 3, (True, True, True))
+    fl = flows.Flow("tg3d", 1.0 / 1600)
+    disc = ns.Discretization(mesh, fl)
+    v0 = fl.initial(disc.X).reshape(3, -1)
+    run_steps(ctx, disc, lambda v, t, dt: ns.rk_step(disc, "CB3e", v, t, dt)[0], v0, 0.0, 0.05, 2, 2e-7)
+
+
+def test_mixed_fast_mms():
+    # Dirichlet faces: the penalty terms of A v and of the boundary data cancel in FP32
+    # (about 1e-8 relative after one step of 2e-3 here)
+    ctx, disc, fl = mms_pair(precision=imex.MIXED_FAST, tol=1e-12)
+    v0 = fl.initial(disc.X).reshape(2, -1)
+    run_steps(ctx, disc, lambda v, t, dt: ns.rk_step(disc, "CB3e", v, t, dt)[0], v0, 0.0, 2e-3, 1, 2e-7)
+
+
+def test_persistent_pressure_cg(monkeypatch):
+    # the opt-in persistent FP32 pressure CG (one cooperative launch per refinement cycle)
+    monkeypatch.setenv("IMEX_PERSIST", "1")
+    P, n = 5, (2, 3, 2)
+    ctx = imex.Context(3, P, n, [0, 0, 0], [TWO_PI] * 3, (1, 1, 1), precision=imex.MIXED, tol=1e-12, maxit=50000)
+    ctx.set_viscosity_const(1.0 / 1600)
+    mesh = dg.Mesh(3, P, n, [0, 0, 0], [TWO_PI] * 3, (True, True, True))
+    fl = flows.Flow("tg3d", 1.0 / 1600)
+    disc = ns.Discretization(mesh, fl)
+    v0 = fl.initial(disc.X).reshape(3, -1)
+    run_steps(ctx, disc, lambda v, t, dt: ns.rk_step(disc, "CB3e", v, t, dt)[0], v0, 0.0, 0.05, 2, 1e-9)
