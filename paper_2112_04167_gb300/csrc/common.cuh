@@ -56,9 +56,21 @@ struct Geom {
   float idtf;
 };
 
+// per-direction geometry by selects rather than array indexing, so that a Geom held by a
+// thread stays in registers when k is not a compile-time constant
 template <typename T> __host__ __device__ __forceinline__ T geom_h(const Geom& g, int k);
-template <> __host__ __device__ __forceinline__ double geom_h<double>(const Geom& g, int k) { return g.h[k]; }
-template <> __host__ __device__ __forceinline__ float geom_h<float>(const Geom& g, int k) { return g.hf[k]; }
+template <> __host__ __device__ __forceinline__ double geom_h<double>(const Geom& g, int k) {
+  return k == 0 ? g.h[0] : (k == 1 ? g.h[1] : g.h[2]);
+}
+template <> __host__ __device__ __forceinline__ float geom_h<float>(const Geom& g, int k) {
+  return k == 0 ? g.hf[0] : (k == 1 ? g.hf[1] : g.hf[2]);
+}
+__host__ __device__ __forceinline__ int geom_n(const Geom& g, int k) {
+  return k == 0 ? g.n[0] : (k == 1 ? g.n[1] : g.n[2]);
+}
+__host__ __device__ __forceinline__ int geom_bc(const Geom& g, int k) {
+  return k == 0 ? g.bc[0] : (k == 1 ? g.bc[1] : g.bc[2]);
+}
 
 // 1D tables per number of points N (index N, 2..IMEX_MAXN), in FP64 and FP32.
 //   x, w      : GLL points / weights
@@ -144,14 +156,17 @@ template <> __host__ __device__ __forceinline__ float geom_dt<float>(const Geom&
 // neighbour element (index in the union) across face (k, side) of the element with local
 // coordinates ec; -1 on a domain boundary.  g is the element's local_geom.
 __device__ __forceinline__ int neighbor(const Geom& g, const int ec[3], int k, int side) {
-  int c[3] = {ec[0], ec[1], ec[2]};
-  int j = c[k] + side;
-  if (j < 0 || j >= g.n[k]) {
-    if (g.bc[k] != 0) return -1;
-    j = (j + g.n[k]) % g.n[k];
+  int cx = ec[0], cy = ec[1], cz = ec[2];
+  const int nk = geom_n(g, k);
+  int j = (k == 0 ? cx : (k == 1 ? cy : cz)) + side;
+  if (j < 0 || j >= nk) {
+    if (geom_bc(g, k) != 0) return -1;
+    j = (j + nk) % nk;
   }
-  c[k] = j;
-  return g.e0 + c[0] + g.n[0] * (c[1] + g.n[1] * c[2]);
+  if (k == 0) cx = j;
+  else if (k == 1) cy = j;
+  else cz = j;
+  return g.e0 + cx + g.n[0] * (cy + g.n[1] * cz);
 }
 
 // local coordinates of the element with local index el (g: its local_geom)

@@ -2234,8 +2234,10 @@ imex_status imex_batch_step(imex_batch* b, const double* dt, int nsteps) {
     st[q] = s;
     b->group_ms[q] = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - g0).count();
   };
-  if (b->groups.size() == 1) {
-    run(0);
+  // IMEX_BATCH_SERIAL=1 steps the groups one after the other from the calling thread
+  const char* ser = std::getenv("IMEX_BATCH_SERIAL");
+  if (b->groups.size() == 1 || (ser && std::atoi(ser) != 0)) {
+    for (size_t q = 0; q < b->groups.size(); ++q) run(q);
   } else {
     std::vector<std::thread> th;
     for (size_t q = 0; q < b->groups.size(); ++q) th.emplace_back(run, q);

@@ -100,7 +100,8 @@ __device__ __forceinline__ bool last_block(unsigned int* counter) {
 
 // Totals over the blocks of each segment of the K partials partial[k * nblk + b], handed to
 // fn(q, tot) once per segment (by one thread).  Few segments: the whole block adds each
-// segment's partials (one load latency); many: one warp per segment.
+// segment's partials (one load latency); many short segments (a batch): one thread per
+// segment, all segments at once; otherwise one warp per segment.
 template <int K, typename Fn>
 __device__ __forceinline__ void seg_totals(const SegTable& t, const double* __restrict__ partial, Fn fn) {
   if (t.nseg <= 4) {
@@ -115,6 +116,19 @@ __device__ __forceinline__ void seg_totals(const SegTable& t, const double* __re
       double tot[K];
       block_sum_k<double, K>(v, tot);
       if (threadIdx.x == 0) fn(q, tot);
+    }
+  } else if (t.nblk <= 24 * t.nseg) {
+    for (int q = threadIdx.x; q < t.nseg; q += blockDim.x) {
+      double v[K];
+#pragma unroll
+      for (int k = 0; k < K; ++k) v[k] = 0.0;
+      const int b0 = t.seg_blk0[q], b1 = t.seg_blk0[q + 1];
+#pragma unroll 4
+      for (int b = b0; b < b1; ++b) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) v[k] += partial[(size_t)k * t.nblk + b];
+      }
+      fn(q, v);
     }
   } else {
     const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5, lane = threadIdx.x & 31;

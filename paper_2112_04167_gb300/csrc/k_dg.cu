@@ -103,7 +103,7 @@ __global__ void dg_div_kernel(Geom g, DivArgs<T> a) {
   elem_coords(gl, el, ec);
   __syncthreads();
   T jac = T(1);
-  for (int k = 0; k < D; ++k) jac *= T(gl.h[k]) * T(0.5);
+  for (int k = 0; k < D; ++k) jac *= geom_h<T>(gl, k) * T(0.5);
   for (int node = threadIdx.x; node < ND; node += blockDim.x) {
     int id[3] = {node % NV, (D > 1) ? (node / NV) % NV : 0, (D > 2) ? node / (NV * NV) : 0};
     T Wq = jac;
@@ -116,7 +116,7 @@ __global__ void dg_div_kernel(Geom g, DivArgs<T> a) {
         if (id[k] != (side ? NV - 1 : 0)) continue;
         const int nb = neighbor(gl, ec, k, side ? 1 : -1);
         const T n = side ? T(1) : T(-1);
-        T Wf = jac / (T(gl.h[k]) * T(0.5));
+        T Wf = jac / (geom_h<T>(gl, k) * T(0.5));
         for (int j = 0; j < D; ++j) if (j != k) Wf *= sw[id[j]];
         T cflux = T(0);
         if (nb >= 0) {
@@ -140,7 +140,7 @@ __global__ void dg_div_kernel(Geom g, DivArgs<T> a) {
   for (int m = 0; m < D; ++m) {
     T* src = buf + (size_t)cur * (D + 1) * ND;
     T* dst = buf + (size_t)(1 - cur) * (D + 1) * ND;
-    const T hm = T(2) / T(gl.h[m]);
+    const T hm = T(2) / geom_h<T>(gl, m);
     contract2<T, D>(src, src + (1 + m) * ND, hm, dst, sz, m, NP, sIp, sGp, threadIdx.x, blockDim.x);
     for (int k = m + 1; k < D; ++k)
       contract2<T, D>(src + (1 + k) * ND, (const T*)nullptr, T(0), dst + (1 + k) * ND, sz, m, NP, sIp,
@@ -230,7 +230,7 @@ __global__ void dg_grad_kernel(Geom g, GradArgs<T> a) {
       in = bufs[cur];
       cur ^= 1;
     }
-    const T hk = T(2) / T(gl.h[k]);
+    const T hk = T(2) / geom_h<T>(gl, k);
     for (int node = threadIdx.x; node < ND; node += blockDim.x) {
       int id[3] = {node % NV, (D > 1) ? (node / NV) % NV : 0, (D > 2) ? node / (NV * NV) : 0};
       T val = hk * in[node];
@@ -378,7 +378,7 @@ __global__ void dg_conv_kernel(Geom g, ConvArgs<T> a) {
   __syncthreads();
   const int t = threadIdx.x, nt = blockDim.x;
   T jac = T(1);
-  for (int k = 0; k < D; ++k) jac *= T(gl.h[k]) * T(0.5);
+  for (int k = 0; k < D; ++k) jac *= geom_h<T>(gl, k) * T(0.5);
   // --- interpolate v to the Gauss points
   for (int c = 0; c < D; ++c) {
     int sz[3] = {N, D > 1 ? N : 1, D > 2 ? N : 1};
@@ -397,7 +397,7 @@ __global__ void dg_conv_kernel(Geom g, ConvArgs<T> a) {
   // --- volume term: acc_c += sum_k (test derivative in k) [W_g v_c v_k]
   for (int c = 0; c < D; ++c) {
     for (int k = 0; k < D; ++k) {
-      const T hk = T(2) / T(gl.h[k]);                 // derivative scale of the test function
+      const T hk = T(2) / geom_h<T>(gl, k);                 // derivative scale of the test function
       for (int q = t; q < NQ; q += nt) {
         int r = q;
         T W = jac * hk;
@@ -484,7 +484,7 @@ __global__ void dg_conv_kernel(Geom g, ConvArgs<T> a) {
       // LLF flux per component, weighted, projected back onto the face nodes
       for (int c = 0; c < D; ++c) {
         for (int q = t; q < NFQ; q += nt) {
-          T W = jac / (T(gl.h[k]) * T(0.5));
+          T W = jac / (geom_h<T>(gl, k) * T(0.5));
           int r = q;
           for (int j = 0; j < D - 1; ++j) { W *= sgw[r % Q]; r /= Q; }
           const T vmn = n * fm[k * NFQ + q];
