@@ -61,8 +61,10 @@ __device__ __forceinline__ T warp_sum_t(T v) {
   return v;
 }
 
-// K block sums of per-thread values in T; out[] valid in thread 0 (per-warp sums in T, added
-// in FP64 in warp order).  Ends with a barrier, so it may be called repeatedly.
+// K block sums of per-thread values in T; out[] valid in thread 0.  Warp sums by shuffles,
+// then warp 0 adds the per-warp sums with one more shuffle tree in T (no serial FP64 on one
+// thread while the block waits); the K results are converted once.  Ends with a barrier, so
+// it may be called repeatedly.  blockDim.x must be a multiple of 32.
 template <typename T, int K>
 __device__ __forceinline__ void block_sum_k(T (&v)[K], double (&out)[K]) {
   __shared__ T ws[K][32];
@@ -74,13 +76,12 @@ __device__ __forceinline__ void block_sum_k(T (&v)[K], double (&out)[K]) {
     for (int k = 0; k < K; ++k) ws[k][w] = v[k];
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
+  if (w == 0) {
     const int nw = (int)(blockDim.x >> 5);
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-      double acc = 0.0;
-      for (int i = 0; i < nw; ++i) acc += (double)ws[k][i];
-      out[k] = acc;
+      const T x = warp_sum_t(lane < nw ? ws[k][lane] : T(0));
+      if (lane == 0) out[k] = (double)x;
     }
   }
   __syncthreads();
@@ -254,11 +255,21 @@ seg_xr_kernel(T* __restrict__ x, T* __restrict__ r, const T* __restrict__ p, con
     for (int k = 0; k < 4; ++k) partial[(size_t)k * t.nblk + blockIdx.x] = bs[k];
   }
   if (!last_block(counter)) return;
+  // the scalars the update needs, loaded before the partial sums (their latencies overlap)
+  struct Pre {
+    double rz, dsum, bb;
+    int done, iters, len;
+  };
+  Pre pre[4];
+  if (threadIdx.x == 0 && t.nseg <= 4)
+    for (int q = 0; q < t.nseg; ++q) pre[q] = {sc.rz[q], sc.dsum[q], sc.bb[q], sc.done[q], sc.iters[q], t.len[q]};
   seg_totals<4>(t, partial, [&](int q, const double* tot) {
-    if (sc.done[q] != 0) return;
-    const SegSums o = seg_scalars(tot, (double)t.len[q], sc.dsum[q], sc.project);
-    const double bt = sc.rz[q] != 0.0 ? o.rz / sc.rz[q] : 0.0;
-    sc.rz_old[q] = sc.rz[q];
+    const Pre v = t.nseg <= 4 ? pre[q]
+                              : Pre{sc.rz[q], sc.dsum[q], sc.bb[q], sc.done[q], sc.iters[q], t.len[q]};
+    if (v.done != 0) return;
+    const SegSums o = seg_scalars(tot, (double)v.len, v.dsum, sc.project);
+    const double bt = v.rz != 0.0 ? o.rz / v.rz : 0.0;
+    sc.rz_old[q] = v.rz;
     sc.rz[q] = o.rz;
     sc.rr[q] = o.rr;
     sc.zmean[q] = o.zmean;
@@ -267,10 +278,10 @@ seg_xr_kernel(T* __restrict__ x, T* __restrict__ r, const T* __restrict__ p, con
     sc.rmean_f[q] = (float)o.rmean;
     sc.beta[q] = bt;
     sc.beta_f[q] = (float)bt;
-    sc.iters[q] += 1;
+    sc.iters[q] = v.iters + 1;
     if (o.rr != o.rr || !isfinite(bt)) sc.done[q] = 2;
-    else if (o.rr <= sc.tol2 * sc.bb[q]) sc.done[q] = 1;
-    else if (sc.iters[q] >= maxit) sc.done[q] = 3;
+    else if (o.rr <= sc.tol2 * v.bb) sc.done[q] = 1;
+    else if (v.iters + 1 >= maxit) sc.done[q] = 3;
   });
   if (threadIdx.x == 0) *counter = 0u;
 }
