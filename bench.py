@@ -471,10 +471,13 @@ def main():
                 "bytes_per_launch": bytes_it, "avg_launch_us": per_it_s * 1e6, "iterations": its,
                 "note": "per CG iteration (many iterations per launch); its vectors are L2-resident at this size"}
     elif dom in bytes_per and prof[dom]["launches"]:
+        # DRAM bytes per launch from the ncu capture summarised in
+        # profiles/sipg3p_apply_f32_tg3d_16cube_p7.md (this workload, this kernel version)
+        traffic = {"sipg_pressure_f32": 5657600}.get(dom) if args.nelem == 16 and args.P == 7 else None
         avg_s = prof[dom]["avg_us"] * 1e-6
         ach = bytes_per[dom] / avg_s / 1e9
         roof = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": hbm, "unit": "GB/s",
-                "frac": ach / hbm, "traffic": None, "peak_source": src,
+                "frac": ach / hbm, "traffic": traffic, "peak_source": src,
                 "bytes_per_launch": bytes_per[dom], "avg_launch_us": prof[dom]["avg_us"]}
     else:
         # FP64 ALU-bound kernels: flops per launch vs the nominal FP64 rate

@@ -45,8 +45,9 @@ typedef enum {
 /* arithmetic of the solves */
 /* IMEX_FP64: every operator and solve in FP64.
    IMEX_MIXED: FP32 inner iterations of the Poisson and Helmholtz solves with FP64 refinement
-     (true residual, iterate); explicit operators, stage storage and combinations in FP64 --
-     the result matches IMEX_FP64 to the solver tolerance.
+     (true residual, iterate); stage storage and combinations in FP64, the convective
+     operator on FP64 fields in float-float arithmetic (about 48 significant bits, on the
+     FP32 pipes) -- the result matches IMEX_FP64 to the solver tolerance.
    IMEX_MIXED_FAST: IMEX_MIXED plus FP32 explicit operators (convection, F_d1) on FP32 copies
      of the state; adds an FP32 rounding error of about 1e-8 relative per step. */
 enum { IMEX_FP64 = 0, IMEX_MIXED = 1, IMEX_MIXED_FAST = 2 };

@@ -927,9 +927,12 @@ imex_status stage_rhs(imex_ctx* c, double t, const double* v, const double* nu, 
     TRY(launch_check(c, rc, "dg_conv(f32)"));
     f2d(c->fp, E, nt, c->st);
   } else {
+    // IMEX_MIXED: FP64 fields, float-float arithmetic on the FP32 pipes (about 48 bits);
+    // IMEX_FP64: FP64 arithmetic throughout
     ConvArgs<double> ca{v, (long long)c->nv, vb, 1.0, E};
     prof_mark(c, IMEX_PROF_CONV, true);
-    const int rc = dg_conv<double>(c->gv, c->Nv, ca, c->st);
+    const int rc = c->desc.precision == IMEX_MIXED ? dg_conv_ff(c->gv, c->Nv, ca, c->st)
+                                                   : dg_conv<double>(c->gv, c->Nv, ca, c->st);
     prof_mark(c, IMEX_PROF_CONV, false);
     TRY(launch_check(c, rc, "dg_conv"));
   }

@@ -6,7 +6,10 @@
 //   * the over-integrated convection term F_c with local Lax-Friedrichs flux.
 // Every kernel works on one element per thread group with its tiles in shared
 // memory and sum-factorised 1D contractions.
+#include <type_traits>
+
 #include "common.cuh"
+#include "ff.cuh"
 #include "kernels.h"
 
 namespace imex {
@@ -342,9 +345,15 @@ struct ConvShape {
                            2 * D * NFQ + 2 * NFQ + NF);
 };
 
-template <typename T, int D, int N>
-__global__ void dg_conv_kernel(Geom g, ConvArgs<T> a) {
+template <typename T> __device__ __forceinline__ T conv_h(const Geom& g, int k) { return geom_h<T>(g, k); }
+template <> __device__ __forceinline__ ff conv_h<ff>(const Geom& g, int k) { return ff(geom_h<double>(g, k)); }
+
+// T: arithmetic type (double, float, or the float-float ff for FP64-class accuracy on the
+// FP32 pipes); TS: storage type of the fields (double for ff)
+template <typename T, int D, int N, typename TS = T>
+__global__ void dg_conv_kernel(Geom g, ConvArgs<TS> a) {
   using S = ConvShape<T, D, N>;
+  using TT = typename std::conditional<std::is_same<T, ff>::value, double, T>::type;   // table type
   constexpr int Q = S::Q, ND = S::ND, NQ = S::NQ, NF = S::NF, NFQ = S::NFQ;
   extern __shared__ unsigned char smem_raw[];
   T* sIG = reinterpret_cast<T*>(smem_raw);     // [Q*N]
@@ -361,10 +370,10 @@ __global__ void dg_conv_kernel(Geom g, ConvArgs<T> a) {
   T* fh = fp + D * NFQ;                         // [NFQ] flux of one component
   T* ft = fh + NFQ;                             // [NFQ] scratch
   T* fo = ft + NFQ;                             // [NF] result on the face nodes
-  const Tables<T>& tb = tab<T>(g);
-  for (int i = threadIdx.x; i < Q * N; i += blockDim.x) { sIG[i] = tb.IG[N][i]; sDG[i] = tb.DG[N][i]; }
-  for (int i = threadIdx.x; i < Q; i += blockDim.x) sgw[i] = tb.gw[N][i];
-  for (int i = threadIdx.x; i < N; i += blockDim.x) sw[i] = tb.w[N][i];
+  const Tables<TT>& tb = tab<TT>(g);
+  for (int i = threadIdx.x; i < Q * N; i += blockDim.x) { sIG[i] = T(tb.IG[N][i]); sDG[i] = T(tb.DG[N][i]); }
+  for (int i = threadIdx.x; i < Q; i += blockDim.x) sgw[i] = T(tb.gw[N][i]);
+  for (int i = threadIdx.x; i < N; i += blockDim.x) sw[i] = T(tb.w[N][i]);
   const int e = blockIdx.x;
   int el = 0;
   const Geom gl = local_geom(g, e, el);
@@ -372,13 +381,13 @@ __global__ void dg_conv_kernel(Geom g, ConvArgs<T> a) {
   elem_coords(gl, el, ec);
   for (int c = 0; c < D; ++c)
     for (int i = threadIdx.x; i < ND; i += blockDim.x) {
-      sv[c * ND + i] = a.v[(size_t)c * a.stride + (size_t)e * ND + i];
+      sv[c * ND + i] = T(a.v[(size_t)c * a.stride + (size_t)e * ND + i]);
       acc[c * ND + i] = T(0);
     }
   __syncthreads();
   const int t = threadIdx.x, nt = blockDim.x;
   T jac = T(1);
-  for (int k = 0; k < D; ++k) jac *= geom_h<T>(gl, k) * T(0.5);
+  for (int k = 0; k < D; ++k) jac *= conv_h<T>(gl, k) * T(0.5);
   // --- interpolate v to the Gauss points
   for (int c = 0; c < D; ++c) {
     int sz[3] = {N, D > 1 ? N : 1, D > 2 ? N : 1};
@@ -397,7 +406,7 @@ __global__ void dg_conv_kernel(Geom g, ConvArgs<T> a) {
   // --- volume term: acc_c += sum_k (test derivative in k) [W_g v_c v_k]
   for (int c = 0; c < D; ++c) {
     for (int k = 0; k < D; ++k) {
-      const T hk = T(2) / geom_h<T>(gl, k);                 // derivative scale of the test function
+      const T hk = T(2) / conv_h<T>(gl, k);                 // derivative scale of the test function
       for (int q = t; q < NQ; q += nt) {
         int r = q;
         T W = jac * hk;
@@ -440,9 +449,9 @@ __global__ void dg_conv_kernel(Geom g, ConvArgs<T> a) {
           T pv;
           if (nb >= 0) {
             cc[k] = side ? 0 : N - 1;
-            pv = a.v[(size_t)c * a.stride + (size_t)nb * ND + flat3(cc, N, D)];
+            pv = T(a.v[(size_t)c * a.stride + (size_t)nb * ND + flat3(cc, N, D)]);
           } else {
-            pv = a.vb ? a.vb[(size_t)c * a.stride + (size_t)e * ND + own] : sv[c * ND + own];
+            pv = a.vb ? T(a.vb[(size_t)c * a.stride + (size_t)e * ND + own]) : sv[c * ND + own];
           }
           ft[f] = pv;
         }
@@ -484,7 +493,7 @@ __global__ void dg_conv_kernel(Geom g, ConvArgs<T> a) {
       // LLF flux per component, weighted, projected back onto the face nodes
       for (int c = 0; c < D; ++c) {
         for (int q = t; q < NFQ; q += nt) {
-          T W = jac / (geom_h<T>(gl, k) * T(0.5));
+          T W = jac / (conv_h<T>(gl, k) * T(0.5));
           int r = q;
           for (int j = 0; j < D - 1; ++j) { W *= sgw[r % Q]; r /= Q; }
           const T vmn = n * fm[k * NFQ + q];
@@ -535,7 +544,7 @@ __global__ void dg_conv_kernel(Geom g, ConvArgs<T> a) {
       int r = i;
       T W = jac;
       for (int j = 0; j < D; ++j) { W *= sw[r % N]; r /= N; }
-      a.out[(size_t)c * a.stride + (size_t)e * ND + i] = a.coef * acc[c * ND + i] / W;
+      a.out[(size_t)c * a.stride + (size_t)e * ND + i] = (TS)(T(a.coef) * acc[c * ND + i] / W);
     }
 }
 
@@ -564,6 +573,12 @@ static void launch_conv(const Geom& g, const ConvArgs<T>& a, cudaStream_t st) {
   using S = ConvShape<T, D, N>;
   smem_limit_once((const void*)dg_conv_kernel<T, D, N>, (int)S::SMEM);
   IMEX_COUNTED(dg_conv_kernel<T, D, N><<<g.ne, S::THREADS, S::SMEM, st>>>(g, a));
+}
+template <typename T, int D, int N>
+static void launch_conv_ff(const Geom& g, const ConvArgs<double>& a, cudaStream_t st) {
+  using S = ConvShape<ff, D, N>;
+  smem_limit_once((const void*)dg_conv_kernel<ff, D, N, double>, (int)S::SMEM);
+  IMEX_COUNTED(dg_conv_kernel<ff, D, N, double><<<g.ne, S::THREADS, S::SMEM, st>>>(g, a));
 }
 
 #define IMEX_DISPATCH_NV(D, FN, ...)                \
@@ -596,6 +611,13 @@ int dg_deriv(const Geom& g, int N, const DerivArgs<T>& a, cudaStream_t st) {
 template <typename T>
 int dg_conv(const Geom& g, int N, const ConvArgs<T>& a, cudaStream_t st) {
   if (g.d == 2) { IMEX_DISPATCH_NV(2, launch_conv, g, a, st) } else { IMEX_DISPATCH_NV(3, launch_conv, g, a, st) }
+  return 0;
+}
+
+// convection with float-float arithmetic on FP64 fields
+int dg_conv_ff(const Geom& g, int N, const ConvArgs<double>& a, cudaStream_t st) {
+  using T = double;
+  if (g.d == 2) { IMEX_DISPATCH_NV(2, launch_conv_ff, g, a, st) } else { IMEX_DISPATCH_NV(3, launch_conv_ff, g, a, st) }
   return 0;
 }
 

@@ -213,3 +213,23 @@ def test_persistent_pressure_cg(monkeypatch):
     disc = ns.Discretization(mesh, fl)
     v0 = fl.initial(disc.X).reshape(3, -1)
     run_steps(ctx, disc, lambda v, t, dt: ns.rk_step(disc, "CB3e", v, t, dt)[0], v0, 0.0, 0.05, 2, 1e-9)
+
+
+@pytest.mark.parametrize("case", ["tg3d", "mms"])
+def test_mixed_matches_fp64(case):
+    # IMEX_MIXED (FP32 inner CG with FP64 refinement, float-float convection) against
+    # IMEX_FP64 from the same state: equal to the solver tolerance
+    def make(prec):
+        if case == "tg3d":
+            c = imex.Context(3, 5, (2, 3, 2), [0, 0, 0], [TWO_PI] * 3, (1, 1, 1), precision=prec, tol=1e-13,
+                             maxit=50000)
+            c.set_viscosity_const(1.0 / 1600)
+            c.init_flow(imex.FLOW_TG3D, [0.0])
+            return c, 0.05
+        c = mms_pair(P=5, n=3, precision=prec, tol=1e-13)[0]
+        c.init_flow(imex.FLOW_TGTRAVEL, [0.01], 0.0)
+        return c, 2e-3
+    (a, dt), (b, _) = make(imex.MIXED), make(imex.FP64)
+    a.step(dt, 2)
+    b.step(dt, 2)
+    assert rel(a.get_velocity(), b.get_velocity()) < 1e-11
