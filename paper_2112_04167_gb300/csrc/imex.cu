@@ -423,6 +423,18 @@ void vel_flags(const imex_ctx* c, SipgArgs<T>& a, bool dt_scaled) {
   a.inst_dt = dt_scaled ? 1 : 0;
 }
 
+// SIPG apply: the FP64 applies of the mixed form (residual replacements, explicit F_d1) use
+// float-float arithmetic on FP64 fields where that kernel exists (periodic 3D, constant
+// viscosity), plain FP64 otherwise; the FP64 form always uses FP64 arithmetic
+template <typename T>
+int apply_dispatch(imex_ctx* c, const Geom& g, int N, const SipgArgs<T>& a) {
+  if (sizeof(T) == 8 && c->desc.precision == IMEX_MIXED) {
+    const int rc = sipg_apply_ff(g, N, reinterpret_cast<const SipgArgs<double>&>(a), c->st);
+    if (rc == 0) return 0;
+  }
+  return sipg_apply<T>(g, N, a, c->st);
+}
+
 // the pressure operator L psi (pressure space), T = double / float
 template <typename T>
 imex_status apply_pressure(imex_ctx* c, const T* x, T* y, T* vtmp, const CgScalars* cg = nullptr) {
@@ -432,7 +444,7 @@ imex_status apply_pressure(imex_ctx* c, const T* x, T* y, T* vtmp, const CgScala
     a.ops = line_ops<T>(c, false);
     fuse_cg(c, a, cg);
     prof_mark(c, cls, true);
-    const int rc = sipg_apply<T>(c->gp, c->Np, a, c->st);
+    const int rc = apply_dispatch<T>(c, c->gp, c->Np, a);
     prof_mark(c, cls, false);
     return launch_check(c, rc, "sipg_apply(p)");
   }
@@ -453,7 +465,7 @@ imex_status apply_helm(imex_ctx* c, const T* x, T* y, int nsys, const T* nu, dou
   vel_flags(c, a, true);
   fuse_cg(c, a, cg);
   prof_mark(c, cls, true);
-  const int rc = sipg_apply<T>(c->gv, c->Nv, a, c->st);
+  const int rc = apply_dispatch<T>(c, c->gv, c->Nv, a);
   prof_mark(c, cls, false);
   return launch_check(c, rc, "sipg_apply(v)");
 }
@@ -964,7 +976,7 @@ imex_status stage_rhs(imex_ctx* c, double t, const double* v, const double* nu, 
                                            1);
     a.ops = c->ops64_v;
     vel_flags(c, a, false);
-    TRY(launch_check(c, sipg_apply<double>(c->gv, c->Nv, a, c->st), "sipg_apply(Fd1)"));
+    TRY(launch_check(c, apply_dispatch<double>(c, c->gv, c->Nv, a), "sipg_apply(Fd1)"));
   }
   if (Fs) {
     TRY(launch_check(c, eval_field(c->gv, c->Nv, 2, spec(c->f_kind, c->f_p), t, nullptr, (long long)c->nv, Fs, c->st),

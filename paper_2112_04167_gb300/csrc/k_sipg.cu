@@ -16,6 +16,7 @@
 #include <type_traits>
 
 #include "common.cuh"
+#include "ff.cuh"
 #include "kernels.h"
 #include "vec.h"
 
@@ -803,7 +804,10 @@ struct ConstLine {
 };
 __constant__ ConstLine<float> c_line32[IMEX_MAXN + 1];
 __constant__ ConstLine<double> c_line64[IMEX_MAXN + 1];
+__constant__ ConstLine<ff> c_lineff[IMEX_MAXN + 1];
 template <typename T> __device__ __forceinline__ const ConstLine<T>& cline(int N);
+template <> __device__ __forceinline__ const ConstLine<ff>& cline<ff>(int N) { return c_lineff[N]; }
+template <> __host__ __device__ __forceinline__ ff geom_h<ff>(const Geom& g, int k) { return ff(geom_h<double>(g, k)); }
 template <> __device__ __forceinline__ const ConstLine<float>& cline<float>(int N) { return c_line32[N]; }
 template <> __device__ __forceinline__ const ConstLine<double>& cline<double>(int N) { return c_line64[N]; }
 
@@ -1064,9 +1068,9 @@ constexpr size_t sipg3l_smem() {
   return sizeof(T) * (size_t)(S::EPB * S::TILE + S::EPB * S::ND);
 }
 
-template <typename T, int N>
-__device__ __forceinline__ T sipg3l_group(const Geom& g, const SipgArgs<T>& a, const T* __restrict__ x,
-                                          T* __restrict__ y, int grp) {
+template <typename T, int N, typename TS = T>
+__device__ __forceinline__ T sipg3l_group(const Geom& g, const SipgArgs<TS>& a, const TS* __restrict__ x,
+                                          TS* __restrict__ y, int grp) {
   using S = Sipg3lShape<T, N>;
   constexpr int NN = S::NN, ND = S::ND, EPB = S::EPB, NP = S::NP, TILE = S::TILE, VEC = S::VEC;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1089,7 +1093,8 @@ __device__ __forceinline__ T sipg3l_group(const Geom& g, const SipgArgs<T>& a, c
   }
   const T hx = geom_h<T>(gl, 0), hy = geom_h<T>(gl, 1), hz = geom_h<T>(gl, 2);
   const T ihx = T(1) / hx, ihy = T(1) / hy, ihz = T(1) / hz;
-  const T scale = sipg_beta(a, gl) * sipg_nu0(a, gl);
+  const T scale = T(sipg_beta(a, gl)) * T(sipg_nu0(a, gl));
+  const T alpha = T(a.alpha);
   T* mt = tile + le * TILE;
   T* ma = acc + le * ND;
   const size_t eb = (size_t)e * ND;
@@ -1101,17 +1106,17 @@ __device__ __forceinline__ T sipg3l_group(const Geom& g, const SipgArgs<T>& a, c
   if (valid) {
 #pragma unroll
     for (int k = 0; k < N; ++k) {
-      u[k] = x[eb + k * NN + t];
+      u[k] = T(x[eb + k * NN + t]);
       mt[(k * N + tb) * NP + ta] = u[k];
     }
   }
   // pass z: line (x = ta, y = tb) along z
   if (valid) {
-    const T* cl = x + (size_t)nb[4] * ND + t;
-    const T* cr = x + (size_t)nb[5] * ND + t;
+    const TS* cl = x + (size_t)nb[4] * ND + t;
+    const TS* cr = x + (size_t)nb[5] * ND + t;
     T vl[N], vr[N];
 #pragma unroll
-    for (int j = 0; j < N; ++j) { vl[j] = cl[j * NN]; vr[j] = cr[j * NN]; }
+    for (int j = 0; j < N; ++j) { vl[j] = T(cl[j * NN]); vr[j] = T(cr[j * NN]); }
     T dl = T(0), dr = T(0);
 #pragma unroll
     for (int j = 0; j < N; ++j) { dl += L.dnL[j] * vl[j]; dr += L.dnR[j] * vr[j]; }
@@ -1131,11 +1136,11 @@ __device__ __forceinline__ T sipg3l_group(const Geom& g, const SipgArgs<T>& a, c
     T v[N];
 #pragma unroll
     for (int j = 0; j < N; ++j) v[j] = mt[(tb * N + j) * NP + ta];
-    const T* cl = x + (size_t)nb[2] * ND + tb * NN + ta;
-    const T* cr = x + (size_t)nb[3] * ND + tb * NN + ta;
+    const TS* cl = x + (size_t)nb[2] * ND + tb * NN + ta;
+    const TS* cr = x + (size_t)nb[3] * ND + tb * NN + ta;
     T vl[N], vr[N];
 #pragma unroll
-    for (int j = 0; j < N; ++j) { vl[j] = cl[j * N]; vr[j] = cr[j * N]; }
+    for (int j = 0; j < N; ++j) { vl[j] = T(cl[j * N]); vr[j] = T(cr[j * N]); }
     T dl = T(0), dr = T(0);
 #pragma unroll
     for (int j = 0; j < N; ++j) { dl += L.dnL[j] * vl[j]; dr += L.dnR[j] * vr[j]; }
@@ -1163,11 +1168,11 @@ __device__ __forceinline__ T sipg3l_group(const Geom& g, const SipgArgs<T>& a, c
 #pragma unroll
       for (int j = 0; j < VEC; ++j) v[q * VEC + j] = pw[j];
     }
-    const T* rl = x + (size_t)nb[0] * ND + tb * NN + ta * N;
-    const T* rr = x + (size_t)nb[1] * ND + tb * NN + ta * N;
+    const TS* rl = x + (size_t)nb[0] * ND + tb * NN + ta * N;
+    const TS* rr = x + (size_t)nb[1] * ND + tb * NN + ta * N;
     T vl[N], vr[N];
 #pragma unroll
-    for (int j = 0; j < N; ++j) { vl[j] = rl[j]; vr[j] = rr[j]; }
+    for (int j = 0; j < N; ++j) { vl[j] = T(rl[j]); vr[j] = T(rr[j]); }
     T dl = T(0), dr = T(0);
 #pragma unroll
     for (int j = 0; j < N; ++j) { dl += L.dnL[j] * vl[j]; dr += L.dnR[j] * vr[j]; }
@@ -1181,23 +1186,23 @@ __device__ __forceinline__ T sipg3l_group(const Geom& g, const SipgArgs<T>& a, c
       for (int j = 0; j < N; ++j) so += L.A[o * N + j] * v[j];
       const int node = (tb * N + ta) * N + o;
       const T W = wyz * (T(0.5) * hx * L.w[o]);
-      T out = a.alpha * W * v[o] + scale * (ma[node] + wt * so);
-      if (a.minv) out /= W;
-      y[eb + node] = out;
+      T out = alpha * W * v[o] + scale * (ma[node] + wt * so);
+      if (a.minv) out = out / W;
+      y[eb + node] = (TS)out;
       dacc += v[o] * out;
     }
   }
   return dacc;
 }
 
-template <typename T, int N>
+template <typename T, int N, typename TS = T>
 __global__ void __launch_bounds__(Sipg3pShape<T, N>::THREADS, (sizeof(T) == 4 && N <= 8) ? 3 : 1)
-sipg3p_apply_kernel(Geom g, SipgArgs<T> a) {
+sipg3p_apply_kernel(Geom g, SipgArgs<TS> a) {
   __shared__ double red[Sipg3pShape<T, N>::THREADS];
   for (int s = 0; s < a.nsys; ++s) {
     if (s > 0) __syncthreads();
-    const T dacc = sipg3l_group<T, N>(g, a, a.x + (size_t)s * a.sys_stride, a.y + (size_t)s * a.sys_stride,
-                                      blockIdx.x);
+    const T dacc = sipg3l_group<T, N, TS>(g, a, a.x + (size_t)s * a.sys_stride, a.y + (size_t)s * a.sys_stride,
+                                          blockIdx.x);
     if (a.dot_out) {
       const double bs = block_sum_any_t<T>(dacc, red);
       if (threadIdx.x == 0) a.dot_partial[(size_t)s * gridDim.x + blockIdx.x] = bs;
@@ -1506,8 +1511,15 @@ void init_const_lines(const Tables<double>& t) {
   delete o;
   delete of;
   if (cudaMemcpyToSymbol(c_line64, h64, sizeof(h64)) == cudaSuccess &&
-      cudaMemcpyToSymbol(c_line32, h32, sizeof(h32)) == cudaSuccess)
-    g_cline_ready[dev] = true;
+      cudaMemcpyToSymbol(c_line32, h32, sizeof(h32)) == cudaSuccess) {
+    static ConstLine<ff> hff[IMEX_MAXN + 1];
+    for (int N = 2; N <= IMEX_MAXN; ++N) {
+      const double* src = reinterpret_cast<const double*>(&h64[N]);
+      ff* dst = reinterpret_cast<ff*>(&hff[N]);
+      for (size_t i = 0; i < sizeof(ConstLine<double>) / sizeof(double); ++i) dst[i] = ff(src[i]);
+    }
+    if (cudaMemcpyToSymbol(c_lineff, hff, sizeof(hff)) == cudaSuccess) g_cline_ready[dev] = true;
+  }
 }
 
 // Diagonal of alpha M + beta A (Jacobi preconditioner).
@@ -1648,6 +1660,28 @@ static void launch_diag(const Geom& g, const SipgArgs<T>& a, cudaStream_t st) {
     case 9: FN<T, D, 9>(__VA_ARGS__); break;        \
     default: return -1;                             \
   }
+
+template <int N>
+static void launch_apply_ff(const Geom& g, const SipgArgs<double>& a, cudaStream_t st) {
+  using P = Sipg3pShape<ff, N>;
+  constexpr size_t sm = sipg3l_smem<ff, N>();
+  smem_limit_once((const void*)sipg3p_apply_kernel<ff, N, double>, (int)sm);
+  IMEX_COUNTED(sipg3p_apply_kernel<ff, N, double><<<(g.ne + P::EPB - 1) / P::EPB, P::THREADS, sm, st>>>(g, a));
+}
+
+int sipg_apply_ff(const Geom& g, int N, const SipgArgs<double>& a, cudaStream_t st) {
+  if (g.d != 3 || g.bc[0] || g.bc[1] || g.bc[2] || a.nu || !a.ops || a.gdata) return -1;
+  switch (N) {
+    case 3: launch_apply_ff<3>(g, a, st); return 0;
+    case 4: launch_apply_ff<4>(g, a, st); return 0;
+    case 5: launch_apply_ff<5>(g, a, st); return 0;
+    case 6: launch_apply_ff<6>(g, a, st); return 0;
+    case 7: launch_apply_ff<7>(g, a, st); return 0;
+    case 8: launch_apply_ff<8>(g, a, st); return 0;
+    case 9: launch_apply_ff<9>(g, a, st); return 0;
+    default: return -1;
+  }
+}
 
 template <typename T>
 int sipg_apply(const Geom& g, int N, const SipgArgs<T>& a, cudaStream_t st) {

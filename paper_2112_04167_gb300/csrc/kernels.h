@@ -48,6 +48,9 @@ __device__ __forceinline__ T sipg_beta(const SipgArgs<T>& a, const Geom& gl) {
 }
 
 template <typename T> int sipg_apply(const Geom& g, int N, const SipgArgs<T>& a, cudaStream_t st);
+// the periodic 3D constant-viscosity apply on FP64 fields with float-float arithmetic (about
+// 48 significant bits on the FP32 pipes); -1 for any other case (nothing launched)
+int sipg_apply_ff(const Geom& g, int N, const SipgArgs<double>& a, cudaStream_t st);
 // constant-memory line operators of the periodic fast path (once per device)
 void init_const_lines(const Tables<double>& t);
 template <typename T> int sipg_diag(const Geom& g, int N, const SipgArgs<T>& a, cudaStream_t st);
