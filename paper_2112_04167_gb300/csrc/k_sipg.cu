@@ -889,6 +889,122 @@ sipg2p_apply_kernel(Geom g, SipgArgs<T> a) {
   if (a.dot_out) fused_dot_finish(a, red);
 }
 
+// 2D periodic line-owner apply: two passes (y, then x), in each a thread owns one whole line
+// of an element; the block's elements are contiguous in memory and are staged into shared
+// memory with fully coalesced loads.  Many elements per block keep the grid within about
+// one wave of resident blocks.
+template <typename T, int N>
+struct Sipg2lShape {
+  static constexpr int NN = N * N;
+  static constexpr int EPB = 256 / N;
+  static constexpr int THREADS = EPB * N;
+  static constexpr int VEC = 16 / sizeof(T);
+  static constexpr int NP = ((N + VEC - 1) / VEC) * VEC;
+};
+
+template <typename T, int N>
+__global__ void __launch_bounds__(Sipg2lShape<T, N>::THREADS)
+sipg2l_apply_kernel(Geom g, SipgArgs<T> a) {
+  using S = Sipg2lShape<T, N>;
+  constexpr int NN = S::NN, EPB = S::EPB, NP = S::NP, VEC = S::VEC;
+  __shared__ __align__(16) T tile[EPB][N][NP];
+  __shared__ T acc[EPB][NN];
+  __shared__ double red[S::THREADS];
+  const ConstLine<T>& L = cline<T>(N);
+  const int le = threadIdx.x / N, ta = threadIdx.x - le * N;
+  const int e0 = blockIdx.x * EPB;
+  const int e = e0 + le;
+  const bool valid = e < g.ne;
+  int el = 0;
+  Geom gl = g;
+  if (valid) gl = local_geom(g, e, el);
+  int nb[4] = {0, 0, 0, 0};
+  if (valid) {
+    int ec[3];
+    elem_coords(gl, el, ec);
+#pragma unroll
+    for (int f = 0; f < 4; ++f) nb[f] = neighbor(gl, ec, f >> 1, (f & 1) ? 1 : -1);
+  }
+  const T hx = geom_h<T>(gl, 0), hy = geom_h<T>(gl, 1);
+  const T ihx = T(1) / hx, ihy = T(1) / hy;
+  const T scale = sipg_beta(a, gl) * sipg_nu0(a, gl);
+  const int nvalid = min(EPB, g.ne - e0);
+  for (int s = 0; s < a.nsys; ++s) {
+    const T* x = a.x + (size_t)s * a.sys_stride;
+    T* y = a.y + (size_t)s * a.sys_stride;
+    if (s > 0) __syncthreads();
+    // the block's elements, contiguous: coalesced loads into the row tiles
+    for (int i = threadIdx.x; i < nvalid * NN; i += blockDim.x) {
+      const int q = i / NN, r = i - q * NN;
+      tile[q][r / N][r % N] = x[(size_t)e0 * NN + i];
+    }
+    __syncthreads();
+    // pass y: column x = ta of element le
+    if (valid) {
+      T v[N], vl[N], vr[N];
+#pragma unroll
+      for (int j = 0; j < N; ++j) v[j] = tile[le][j][ta];
+      const T* cl = x + (size_t)nb[2] * NN + ta;
+      const T* cr = x + (size_t)nb[3] * NN + ta;
+#pragma unroll
+      for (int j = 0; j < N; ++j) { vl[j] = cl[j * N]; vr[j] = cr[j * N]; }
+      T dl = T(0), dr = T(0);
+#pragma unroll
+      for (int j = 0; j < N; ++j) { dl += L.dnL[j] * vl[j]; dr += L.dnR[j] * vr[j]; }
+      const T tl = vl[N - 1], tr = vr[0];
+      const T wt = (T(0.5) * hx * L.w[ta]) * ihy;
+#pragma unroll
+      for (int o = 0; o < N; ++o) {
+        T so = L.ctrL[o] * tl + L.cdnL[o] * dl + L.ctrR[o] * tr + L.cdnR[o] * dr;
+#pragma unroll
+        for (int j = 0; j < N; ++j) so += L.A[o * N + j] * v[j];
+        acc[le][o * N + ta] = wt * so;
+      }
+    }
+    __syncthreads();
+    // pass x: row y = ta of element le, and the result
+    T dacc = T(0);
+    if (valid) {
+      T v[NP], vl[N], vr[N];
+      using V = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+      const V* rv = reinterpret_cast<const V*>(&tile[le][ta][0]);
+#pragma unroll
+      for (int q = 0; q < NP / VEC; ++q) {
+        const V w4 = rv[q];
+        const T* pw = reinterpret_cast<const T*>(&w4);
+#pragma unroll
+        for (int j = 0; j < VEC; ++j) v[q * VEC + j] = pw[j];
+      }
+      const T* rl = x + (size_t)nb[0] * NN + ta * N;
+      const T* rr = x + (size_t)nb[1] * NN + ta * N;
+#pragma unroll
+      for (int j = 0; j < N; ++j) { vl[j] = rl[j]; vr[j] = rr[j]; }
+      T dl = T(0), dr = T(0);
+#pragma unroll
+      for (int j = 0; j < N; ++j) { dl += L.dnL[j] * vl[j]; dr += L.dnR[j] * vr[j]; }
+      const T tl = vl[N - 1], tr = vr[0];
+      const T wy = T(0.5) * hy * L.w[ta];
+      const T wt = wy * ihx;
+#pragma unroll
+      for (int o = 0; o < N; ++o) {
+        T so = L.ctrL[o] * tl + L.cdnL[o] * dl + L.ctrR[o] * tr + L.cdnR[o] * dr;
+#pragma unroll
+        for (int j = 0; j < N; ++j) so += L.A[o * N + j] * v[j];
+        const T W = wy * (T(0.5) * hx * L.w[o]);
+        T out = a.alpha * W * v[o] + scale * (acc[le][ta * N + o] + wt * so);
+        if (a.minv) out /= W;
+        y[(size_t)e * NN + ta * N + o] = out;
+        dacc += v[o] * out;
+      }
+    }
+    if (a.dot_out) {
+      const double bs = block_sum_any_t<T>(dacc, red);
+      if (threadIdx.x == 0) a.dot_partial[(size_t)s * gridDim.x + blockIdx.x] = bs;
+    }
+  }
+  if (a.dot_out) fused_dot_finish(a, red);
+}
+
 template <typename T, int N>
 struct Sipg3pShape {
   static constexpr int NN = N * N;
@@ -1597,8 +1713,8 @@ sipg_diag_kernel(Geom g, SipgArgs<T> a) {
 template <typename T, int D, int N>
 static void launch_apply(const Geom& g, const SipgArgs<T>& a, cudaStream_t st) {
   if (D == 2 && !a.nu && a.ops && g.bc[0] == 0 && g.bc[1] == 0 && N <= IMEX_MAXN) {
-    using C = Sipg2cShape<N>;
-    IMEX_COUNTED(sipg2p_apply_kernel<T, N><<<(g.ne + C::EPB - 1) / C::EPB, C::THREADS, 0, st>>>(g, a));
+    using C = Sipg2lShape<T, N>;
+    IMEX_COUNTED(sipg2l_apply_kernel<T, N><<<(g.ne + C::EPB - 1) / C::EPB, C::THREADS, 0, st>>>(g, a));
     return;
   }
   if (D == 2 && !a.nu && a.ops) {

@@ -21,6 +21,7 @@ CASES = [
     (3, 3, (3, 2, 3), (True, False, True)),
     (3, 5, (2, 3, 2), (False, True, False)),
     (3, 7, (2, 2, 3), (True, True, True)),
+    (2, 8, (7, 5), (True, True)),      # 2D periodic line-owner path: several blocks and a ragged tail
 ]
 LO = [0.1, -0.3, 0.0]
 HI = [1.3, 0.9, 2.0]
