@@ -440,6 +440,8 @@ class Batch:
         self._check(load().imex_batch_step(self._h, arr.ctypes.data_as(_D), nsteps))
 
     def get_velocity(self, i, out=None):
+        if not 0 <= i < self.n:
+            raise IndexError(f"instance {i} of {self.n}")
         d, nv, _ = self.sizes[i]
         if out is None:
             out = np.empty(d * nv)
@@ -448,6 +450,8 @@ class Batch:
         return out
 
     def get_pressure(self, i, out=None):
+        if not 0 <= i < self.n:
+            raise IndexError(f"instance {i} of {self.n}")
         _, _, npr = self.sizes[i]
         if out is None:
             out = np.empty(npr)

@@ -124,3 +124,22 @@ def test_batch_rejects_bad_arguments():
     s.set_sdc(3, 2)
     with pytest.raises(imex.ImexError):
         imex.Batch([s])
+
+
+def test_batch_edge_cases():
+    # one instance alone in a batch equals the context stepped alone; a one-element instance
+    # (the element is its own neighbour in both directions) joins a group of larger ones
+    a = tg2d(4, 3, 0.01)
+    a.step(0.01, 2)
+    b = imex.Batch([tg2d(4, 3, 0.01)])
+    b.step([0.01], 2)
+    assert rel(b.get_velocity(0), a.get_velocity()) < 1e-10
+    specs = [(4, 1, 0.01), (4, 4, 0.02)]
+    alone_vs_batch(tg2d, specs, [0.01, 0.02], 2, 1e-10)
+    # zero steps leave the state unchanged
+    c = imex.Batch([tg2d(3, 2, 0.01)])
+    v0 = c.get_velocity(0)
+    c.step([0.01], 0)
+    assert np.array_equal(c.get_velocity(0), v0) and c.time(0) == 0.0
+    with pytest.raises(IndexError):
+        c.get_velocity(1)

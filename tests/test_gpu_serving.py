@@ -98,3 +98,21 @@ def test_request_larger_than_budget_fails_alone():
     assert sv.poll(i)[0] == imex.REQ_FAILED
     with pytest.raises(imex.ImexError):
         sv.submit(**dict(tg2d(3, 4, 0.01, 0.01, 2), dt=-1.0))
+
+
+def test_server_groups_join_and_leave_repeatedly():
+    # requests of one group arriving one per tick with staggered lengths: the group is
+    # repacked on every tick (members join and leave) and grows past its first capacity
+    reqs = [tg2d(4, 2 + (i % 4), 0.01 * (1 + i % 3), 0.01, 1 + i % 5) for i in range(12)]
+    sv = imex.Server(budget_bytes=0.0, precision=imex.FP64, tol=1e-13, maxit=50000, keep_results=True)
+    ids = []
+    for r in reqs:
+        ids.append(sv.submit(**r))
+        sv.tick()
+    for _ in range(20):
+        if sv.tick() == 0 and sv.stats()["queued"] == 0:
+            break
+    st = sv.stats()
+    assert st["completed"] == len(reqs) and st["failed"] == 0
+    for i, r in zip(ids, reqs):
+        assert rel(sv.result(i), alone(r)) < 1e-10, i
