@@ -11,6 +11,8 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include "common.cuh"
+
 namespace imex {
 
 struct ff {
@@ -59,5 +61,11 @@ __device__ __forceinline__ ff& operator-=(ff& a, ff b) { return a = a - b; }
 __device__ __forceinline__ ff& operator*=(ff& a, ff b) { return a = a * b; }
 __device__ __forceinline__ bool operator<(ff a, ff b) { return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo); }
 __device__ __forceinline__ bool operator>(ff a, ff b) { return b < a; }
+
+template <> __host__ __device__ __forceinline__ ff geom_h<ff>(const Geom& g, int k) { return ff(geom_h<double>(g, k)); }
+
+// table (storage) type of an arithmetic type: ff kernels read the FP64 tables
+template <typename T> struct TableType { using type = T; };
+template <> struct TableType<ff> { using type = double; };
 
 }  // namespace imex

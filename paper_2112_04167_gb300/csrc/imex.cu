@@ -987,14 +987,17 @@ imex_status stage_rhs(imex_ctx* c, double t, const double* v, const double* nu, 
 
 // projection: psi from L psi = B v' - int (n.w) q, then v'' = v' - G psi (written to out)
 imex_status project(imex_ctx* c, const double* vin, const double* wdata, int mode, double* out) {
+  // the mixed form evaluates the projection's divergence and gradient in float-float
+  const bool ffa = c->desc.precision == IMEX_MIXED;
   DivArgs<double> da{vin, (long long)c->nv, wdata, mode, 1.0, c->bp};
-  TRY(launch_check(c, dg_div<double>(c->gv, c->Nv, da, c->st), "dg_div"));
+  TRY(launch_check(c, ffa ? dg_div_ff(c->gv, c->Nv, da, c->st) : dg_div<double>(c->gv, c->Nv, da, c->st), "dg_div"));
   double res = 0.0;
   TRY(solve_poisson(c, c->bp, c->psi, &c->stats.poisson_iters, &res));
   c->stats.poisson_solves++;
   c->stats.max_poisson_res = std::max(c->stats.max_poisson_res, res);
   GradArgs<double> ga{c->psi, vin, (long long)c->nv, -1.0, out};
-  return launch_check(c, dg_grad<double>(c->gv, c->Nv, ga, c->st), "dg_grad");
+  return launch_check(c, ffa ? dg_grad_ff(c->gv, c->Nv, ga, c->st) : dg_grad<double>(c->gv, c->Nv, ga, c->st),
+                      "dg_grad");
 }
 
 // Helmholtz stage solve: v_out = (M + gamma A(nu))^{-1} (M g + gamma r_b(nu, vb)), initial guess g

@@ -86,8 +86,9 @@ __device__ __forceinline__ void contract2(const T* in1, const T* in2, T s2, T* o
   }
 }
 
-template <typename T, int D, int NV>
-__global__ void dg_div_kernel(Geom g, DivArgs<T> a) {
+template <typename T, int D, int NV, typename TS = T>
+__global__ void dg_div_kernel(Geom g, DivArgs<TS> a) {
+  using TT = typename TableType<T>::type;
   constexpr int NP = NV - 1;
   constexpr int ND = ipow(NV, D);
   constexpr int NDP = ipow(NP, D);
@@ -96,9 +97,9 @@ __global__ void dg_div_kernel(Geom g, DivArgs<T> a) {
   T* sGp = sIp + NV * NP;
   T* sw = sGp + NV * NP;
   T* buf = sw + NV;                       // [2][D+1][ND]
-  const Tables<T>& tb = tab<T>(g);
-  for (int i = threadIdx.x; i < NV * NP; i += blockDim.x) { sIp[i] = tb.Ipv[NV][i]; sGp[i] = tb.Gpv[NV][i]; }
-  for (int i = threadIdx.x; i < NV; i += blockDim.x) sw[i] = tb.w[NV][i];
+  const Tables<TT>& tb = tab<TT>(g);
+  for (int i = threadIdx.x; i < NV * NP; i += blockDim.x) { sIp[i] = T(tb.Ipv[NV][i]); sGp[i] = T(tb.Gpv[NV][i]); }
+  for (int i = threadIdx.x; i < NV; i += blockDim.x) sw[i] = T(tb.w[NV][i]);
   const int e = blockIdx.x;
   int el = 0;
   const Geom gl = local_geom(g, e, el);
@@ -113,7 +114,7 @@ __global__ void dg_div_kernel(Geom g, DivArgs<T> a) {
     for (int k = 0; k < D; ++k) Wq *= sw[id[k]];
     T S = T(0);
     for (int k = 0; k < D; ++k) {
-      const T vk = a.v[(size_t)k * a.v_stride + (size_t)e * ND + node];
+      const T vk = T(a.v[(size_t)k * a.v_stride + (size_t)e * ND + node]);
       buf[(1 + k) * ND + node] = Wq * vk;
       for (int side = 0; side < 2; ++side) {
         if (id[k] != (side ? NV - 1 : 0)) continue;
@@ -125,10 +126,10 @@ __global__ void dg_div_kernel(Geom g, DivArgs<T> a) {
         if (nb >= 0) {
           int c[3] = {id[0], id[1], id[2]};
           c[k] = side ? 0 : NV - 1;
-          const T vn = a.v[(size_t)k * a.v_stride + (size_t)nb * ND + flat3(c, NV, D)];
+          const T vn = T(a.v[(size_t)k * a.v_stride + (size_t)nb * ND + flat3(c, NV, D)]);
           cflux = T(0.5) * (vk + vn) * n;
         } else if (a.mode == 1) {
-          cflux = a.wdata[(size_t)k * a.v_stride + (size_t)e * ND + node] * n;
+          cflux = T(a.wdata[(size_t)k * a.v_stride + (size_t)e * ND + node]) * n;
         } else if (a.mode == 2) {
           cflux = vk * n;
         }
@@ -153,14 +154,15 @@ __global__ void dg_div_kernel(Geom g, DivArgs<T> a) {
     cur ^= 1;
   }
   const T* res = buf + (size_t)cur * (D + 1) * ND;
-  for (int i = threadIdx.x; i < NDP; i += blockDim.x) a.b[(size_t)e * NDP + i] = a.coef * res[i];
+  for (int i = threadIdx.x; i < NDP; i += blockDim.x) a.b[(size_t)e * NDP + i] = (TS)(T(a.coef) * res[i]);
 }
 
 // ----------------------------------------------------------------------------
 // DG gradient of a pressure field: out_k = base_k + coef * (d_k psi - lifting of [psi])
 // ----------------------------------------------------------------------------
-template <typename T, int D, int NV>
-__global__ void dg_grad_kernel(Geom g, GradArgs<T> a) {
+template <typename T, int D, int NV, typename TS = T>
+__global__ void dg_grad_kernel(Geom g, GradArgs<TS> a) {
+  using TT = typename TableType<T>::type;
   constexpr int NP = NV - 1;
   constexpr int ND = ipow(NV, D);
   constexpr int NDP = ipow(NP, D);
@@ -171,15 +173,15 @@ __global__ void dg_grad_kernel(Geom g, GradArgs<T> a) {
   __shared__ T b1[ND], b2[ND];
   __shared__ T sjump[2 * D][NFV];
   __shared__ T sjp[2 * D][NFP];
-  const Tables<T>& tb = tab<T>(g);
-  for (int i = threadIdx.x; i < NV * NP; i += blockDim.x) { sIp[i] = tb.Ipv[NV][i]; sGp[i] = tb.Gpv[NV][i]; }
-  for (int i = threadIdx.x; i < NV; i += blockDim.x) sw[i] = tb.w[NV][i];
+  const Tables<TT>& tb = tab<TT>(g);
+  for (int i = threadIdx.x; i < NV * NP; i += blockDim.x) { sIp[i] = T(tb.Ipv[NV][i]); sGp[i] = T(tb.Gpv[NV][i]); }
+  for (int i = threadIdx.x; i < NV; i += blockDim.x) sw[i] = T(tb.w[NV][i]);
   const int e = blockIdx.x;
   int el = 0;
   const Geom gl = local_geom(g, e, el);
   int ec[3];
   elem_coords(gl, el, ec);
-  for (int i = threadIdx.x; i < NDP; i += blockDim.x) sp[i] = a.psi[(size_t)e * NDP + i];
+  for (int i = threadIdx.x; i < NDP; i += blockDim.x) sp[i] = T(a.psi[(size_t)e * NDP + i]);
   __syncthreads();
   // pressure jumps on the pressure face grid: own - neighbour, interior faces only
   for (int t = threadIdx.x; t < 2 * D * NFP; t += blockDim.x) {
@@ -191,7 +193,7 @@ __global__ void dg_grad_kernel(Geom g, GradArgs<T> a) {
       c[k] = side ? NP - 1 : 0;
       const T own = sp[flat3(c, NP, D)];
       c[k] = side ? 0 : NP - 1;
-      const T nbv = a.psi[(size_t)nb * NDP + flat3(c, NP, D)];
+      const T nbv = T(a.psi[(size_t)nb * NDP + flat3(c, NP, D)]);
       sjp[fi][f] = own - nbv;
     } else {
       sjp[fi][f] = T(0);
@@ -245,7 +247,7 @@ __global__ void dg_grad_kernel(Geom g, GradArgs<T> a) {
         val -= hk / wend * T(0.5) * sjump[2 * k + side][f] * n;
       }
       const size_t o = (size_t)k * a.stride + (size_t)e * ND + node;
-      a.out[o] = (a.base ? a.base[o] : T(0)) + a.coef * val;
+      a.out[o] = (TS)((a.base ? T(a.base[o]) : T(0)) + T(a.coef) * val);
     }
     __syncthreads();
   }
@@ -345,15 +347,13 @@ struct ConvShape {
                            2 * D * NFQ + 2 * NFQ + NF);
 };
 
-template <typename T> __device__ __forceinline__ T conv_h(const Geom& g, int k) { return geom_h<T>(g, k); }
-template <> __device__ __forceinline__ ff conv_h<ff>(const Geom& g, int k) { return ff(geom_h<double>(g, k)); }
 
 // T: arithmetic type (double, float, or the float-float ff for FP64-class accuracy on the
 // FP32 pipes); TS: storage type of the fields (double for ff)
 template <typename T, int D, int N, typename TS = T>
 __global__ void dg_conv_kernel(Geom g, ConvArgs<TS> a) {
   using S = ConvShape<T, D, N>;
-  using TT = typename std::conditional<std::is_same<T, ff>::value, double, T>::type;   // table type
+  using TT = typename TableType<T>::type;
   constexpr int Q = S::Q, ND = S::ND, NQ = S::NQ, NF = S::NF, NFQ = S::NFQ;
   extern __shared__ unsigned char smem_raw[];
   T* sIG = reinterpret_cast<T*>(smem_raw);     // [Q*N]
@@ -387,7 +387,7 @@ __global__ void dg_conv_kernel(Geom g, ConvArgs<TS> a) {
   __syncthreads();
   const int t = threadIdx.x, nt = blockDim.x;
   T jac = T(1);
-  for (int k = 0; k < D; ++k) jac *= conv_h<T>(gl, k) * T(0.5);
+  for (int k = 0; k < D; ++k) jac *= geom_h<T>(gl, k) * T(0.5);
   // --- interpolate v to the Gauss points
   for (int c = 0; c < D; ++c) {
     int sz[3] = {N, D > 1 ? N : 1, D > 2 ? N : 1};
@@ -406,7 +406,7 @@ __global__ void dg_conv_kernel(Geom g, ConvArgs<TS> a) {
   // --- volume term: acc_c += sum_k (test derivative in k) [W_g v_c v_k]
   for (int c = 0; c < D; ++c) {
     for (int k = 0; k < D; ++k) {
-      const T hk = T(2) / conv_h<T>(gl, k);                 // derivative scale of the test function
+      const T hk = T(2) / geom_h<T>(gl, k);                 // derivative scale of the test function
       for (int q = t; q < NQ; q += nt) {
         int r = q;
         T W = jac * hk;
@@ -493,7 +493,7 @@ __global__ void dg_conv_kernel(Geom g, ConvArgs<TS> a) {
       // LLF flux per component, weighted, projected back onto the face nodes
       for (int c = 0; c < D; ++c) {
         for (int q = t; q < NFQ; q += nt) {
-          T W = jac / (conv_h<T>(gl, k) * T(0.5));
+          T W = jac / (geom_h<T>(gl, k) * T(0.5));
           int r = q;
           for (int j = 0; j < D - 1; ++j) { W *= sgw[r % Q]; r /= Q; }
           const T vmn = n * fm[k * NFQ + q];
@@ -564,6 +564,20 @@ static void launch_grad(const Geom& g, const GradArgs<T>& a, cudaStream_t st) {
   IMEX_COUNTED(dg_grad_kernel<T, D, N><<<g.ne, ((ND + 31) / 32) * 32, 0, st>>>(g, a));
 }
 template <typename T, int D, int N>
+static void launch_div_ff(const Geom& g, const DivArgs<double>& a, cudaStream_t st) {
+  constexpr int ND = ipow(N, D);
+  const size_t smem = sizeof(ff) * (size_t)(2 * N * (N - 1) + N + 2 * (D + 1) * ND);
+  smem_limit_once((const void*)dg_div_kernel<ff, D, N, double>, (int)smem);
+  int threads = ND < 128 ? 128 : ((ND + 31) / 32) * 32;
+  if (threads > 512) threads = 512;
+  IMEX_COUNTED(dg_div_kernel<ff, D, N, double><<<g.ne, threads, smem, st>>>(g, a));
+}
+template <typename T, int D, int N>
+static void launch_grad_ff(const Geom& g, const GradArgs<double>& a, cudaStream_t st) {
+  constexpr int ND = ipow(N, D);
+  IMEX_COUNTED(dg_grad_kernel<ff, D, N, double><<<g.ne, ((ND + 31) / 32) * 32, 0, st>>>(g, a));
+}
+template <typename T, int D, int N>
 static void launch_deriv(const Geom& g, const DerivArgs<T>& a, cudaStream_t st) {
   constexpr int ND = ipow(N, D);
   IMEX_COUNTED(dg_deriv_kernel<T, D, N><<<g.ne, ND, 0, st>>>(g, a));
@@ -611,6 +625,18 @@ int dg_deriv(const Geom& g, int N, const DerivArgs<T>& a, cudaStream_t st) {
 template <typename T>
 int dg_conv(const Geom& g, int N, const ConvArgs<T>& a, cudaStream_t st) {
   if (g.d == 2) { IMEX_DISPATCH_NV(2, launch_conv, g, a, st) } else { IMEX_DISPATCH_NV(3, launch_conv, g, a, st) }
+  return 0;
+}
+
+// weak divergence and DG gradient with float-float arithmetic on FP64 fields
+int dg_div_ff(const Geom& g, int N, const DivArgs<double>& a, cudaStream_t st) {
+  using T = double;
+  if (g.d == 2) { IMEX_DISPATCH_NV(2, launch_div_ff, g, a, st) } else { IMEX_DISPATCH_NV(3, launch_div_ff, g, a, st) }
+  return 0;
+}
+int dg_grad_ff(const Geom& g, int N, const GradArgs<double>& a, cudaStream_t st) {
+  using T = double;
+  if (g.d == 2) { IMEX_DISPATCH_NV(2, launch_grad_ff, g, a, st) } else { IMEX_DISPATCH_NV(3, launch_grad_ff, g, a, st) }
   return 0;
 }
 

@@ -807,7 +807,6 @@ __constant__ ConstLine<double> c_line64[IMEX_MAXN + 1];
 __constant__ ConstLine<ff> c_lineff[IMEX_MAXN + 1];
 template <typename T> __device__ __forceinline__ const ConstLine<T>& cline(int N);
 template <> __device__ __forceinline__ const ConstLine<ff>& cline<ff>(int N) { return c_lineff[N]; }
-template <> __host__ __device__ __forceinline__ ff geom_h<ff>(const Geom& g, int k) { return ff(geom_h<double>(g, k)); }
 template <> __device__ __forceinline__ const ConstLine<float>& cline<float>(int N) { return c_line32[N]; }
 template <> __device__ __forceinline__ const ConstLine<double>& cline<double>(int N) { return c_line64[N]; }
 

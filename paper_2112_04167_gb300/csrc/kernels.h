@@ -111,6 +111,8 @@ struct ConvArgs {
 template <typename T> int dg_conv(const Geom& g, int N, const ConvArgs<T>& a, cudaStream_t st);
 // the same on FP64 fields with float-float arithmetic (about 48 significant bits) on the FP32 pipes
 int dg_conv_ff(const Geom& g, int N, const ConvArgs<double>& a, cudaStream_t st);
+int dg_div_ff(const Geom& g, int N, const DivArgs<double>& a, cudaStream_t st);
+int dg_grad_ff(const Geom& g, int N, const GradArgs<double>& a, cudaStream_t st);
 
 // ---- vector kernels (k_vec.cu) ------------------------------------------------
 #define IMEX_MAXTERMS 16
