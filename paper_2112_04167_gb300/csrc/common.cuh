@@ -193,6 +193,40 @@ long long thread_launch_count();     // launches issued by the calling thread
 // so that launches can be captured into CUDA graphs)
 void smem_limit_once(const void* kernel, int bytes);
 
+// Programmatic dependent launch (the kernels of the CG iteration loop).  A kernel launched
+// with the programmatic-serialization attribute may be scheduled while its predecessor in
+// the stream is still running; it calls pdl_wait() before it reads or writes anything the
+// predecessor (or an earlier kernel) touches -- the wait returns once the predecessor has
+// completed and its memory operations are visible -- and pdl_trigger() to let its own
+// successor be scheduled.  Without the attribute both are no-ops.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+// IMEX_PDL=1 in the environment launches the CG loop kernels with the attribute
+bool pdl_enabled();
+
+// launch of a kernel of the CG loop: counted, with the programmatic-serialization attribute
+// when enabled
+template <typename... KArgs, typename... Args>
+void launch_cg_kernel(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                      Args... args) {
+  count_launch();
+  if (!pdl_enabled()) {
+    kernel<<<grid, block, smem, st>>>(args...);
+    return;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 }  // namespace imex
 
 // every kernel launch of the library goes through this macro, which counts it

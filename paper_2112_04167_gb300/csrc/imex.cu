@@ -178,6 +178,10 @@ struct imex_ctx {
   double *v = nullptr, *vp = nullptr, *vpp = nullptr, *g = nullptr, *tmp = nullptr, *vb = nullptr;
   double *nu = nullptr, *nu_fixed = nullptr, *phi = nullptr, *jac = nullptr, *fsbuf = nullptr;
   double *psi = nullptr, *bp = nullptr, *mass_v = nullptr, *mass_p = nullptr;
+  // time scale tau of the stage potential held in psi (0: none): the stage projections
+  // solve for psi'' ~ tau p, so the next solve starts from psi scaled to its own tau
+  double psi_tau = 0.0;
+  double* psi_f = nullptr;     // potential of the final projection (zero initial guess)
   std::vector<double*> E, Fd1, Fd3, Fs;         // stage storage (RK)
   // SDC storage
   std::vector<double*> sv, snu, sFEX, sFIM, sFq;
@@ -985,17 +989,32 @@ imex_status stage_rhs(imex_ctx* c, double t, const double* v, const double* nu, 
   return IMEX_OK;
 }
 
-// projection: psi from L psi = B v' - int (n.w) q, then v'' = v' - G psi (written to out)
-imex_status project(imex_ctx* c, const double* vin, const double* wdata, int mode, double* out) {
+// projection: psi from L psi = B v' - int (n.w) q, then v'' = v' - G psi (written to out).
+// Stage projections (mode 1) solve for a potential of size about tau p (tau = dt c_i for an
+// RK stage, the subinterval length for an SDC correction): the previous stage's potential,
+// scaled by the ratio of the two tau, is the initial guess.  The final projection (mode 2,
+// a small correction) starts from zero in its own buffer and leaves the stage potential.
+imex_status project(imex_ctx* c, const double* vin, const double* wdata, int mode, double* out, double tau = 0.0) {
   // the mixed form evaluates the projection's divergence and gradient in float-float
   const bool ffa = c->desc.precision == IMEX_MIXED;
   DivArgs<double> da{vin, (long long)c->nv, wdata, mode, 1.0, c->bp};
   TRY(launch_check(c, ffa ? dg_div_ff(c->gv, c->Nv, da, c->st) : dg_div<double>(c->gv, c->Nv, da, c->st), "dg_div"));
+  double* psi = c->psi;
+  if (mode == 2) {
+    psi = c->psi_f;
+    CK(cudaMemsetAsync(psi, 0, c->np * sizeof(double), c->st), "memset psi_f");
+  } else if (c->psi_tau > 0.0 && tau > 0.0 && tau != c->psi_tau) {
+    LinComb lc{};
+    lc.nterms = 1;
+    lc.x[0] = psi; lc.c[0] = tau / c->psi_tau;
+    lincomb(psi, lc, c->np, c->st);
+  }
   double res = 0.0;
-  TRY(solve_poisson(c, c->bp, c->psi, &c->stats.poisson_iters, &res));
+  TRY(solve_poisson(c, c->bp, psi, &c->stats.poisson_iters, &res));
+  if (mode != 2) c->psi_tau = tau > 0.0 ? tau : 0.0;
   c->stats.poisson_solves++;
   c->stats.max_poisson_res = std::max(c->stats.max_poisson_res, res);
-  GradArgs<double> ga{c->psi, vin, (long long)c->nv, -1.0, out};
+  GradArgs<double> ga{psi, vin, (long long)c->nv, -1.0, out};
   return launch_check(c, ffa ? dg_grad_ff(c->gv, c->Nv, ga, c->st) : dg_grad<double>(c->gv, c->Nv, ga, c->st),
                       "dg_grad");
 }
@@ -1083,7 +1102,7 @@ imex_status rk_step(imex_ctx* c, const Tab& tb, double* v, double t, double dt, 
       lcomb_dt(c, c->vp, lf, 1, nt);
     }
     // lines 5-6: projection
-    TRY(project(c, c->vp, vb, 1, c->vpp));
+    TRY(project(c, c->vp, vb, 1, c->vpp, dtc(c, dt) * tb.c[i]));
     // line 7: nu_i
     TRY(eval_nu(c, ti, c->vpp, c->nu));
     // line 8: g_i
@@ -1259,7 +1278,7 @@ imex_status sdc_step(imex_ctx* c, double* v, double t, double dt) {
       for (int q = 0; q <= M; ++q) { lc.x[n] = c->sFq[q]; lc.c[n++] = dt * W[m][q]; }
       lc.nterms = n;
       lincomb(c->vp, lc, nt, c->st);
-      TRY(project(c, c->vp, vb, 1, c->vpp));
+      TRY(project(c, c->vp, vb, 1, c->vpp, dts[m]));
       // v3 - dt_m div(nu^{k+1}_{m-1} grad v3) = v'' - dt_m (F'_d1 + F'_d3)
       LinComb lg{};
       lg.nterms = 3;
@@ -1447,6 +1466,7 @@ imex_status init_ctx(imex_ctx* c) {
   if ((s = dalloc(c, &c->phi, nvc)) != IMEX_OK) return bail(s);
   if ((s = dalloc(c, &c->jac, nvc * d * d)) != IMEX_OK) return bail(s);
   if ((s = dalloc(c, &c->psi, npc)) != IMEX_OK) return bail(s);
+  if ((s = dalloc(c, &c->psi_f, npc)) != IMEX_OK) return bail(s);
   if ((s = dalloc(c, &c->bp, npc)) != IMEX_OK) return bail(s);
   if ((s = dalloc(c, &c->mass_v, nvc)) != IMEX_OK) return bail(s);
   if ((s = dalloc(c, &c->mass_p, npc)) != IMEX_OK) return bail(s);
@@ -1681,6 +1701,7 @@ imex_status regroup(imex_ctx* c, imex_ctx* dst, const std::vector<int>& keep, co
   }
   CK(cudaMemcpyAsync(dst->v, dst->tmp, d * nv_new * sizeof(double), cudaMemcpyDeviceToDevice, dst->st), "cp v");
   CK(cudaMemcpyAsync(dst->psi, dst->bp, np_new * sizeof(double), cudaMemcpyDeviceToDevice, dst->st), "cp psi");
+  dst->psi_tau = keep.empty() ? 0.0 : c->psi_tau;    // groups count tau in units of their members' steps
   dst->inst = ni;
   return set_layout(dst);
 }
@@ -2083,6 +2104,7 @@ imex_status imex_solve_poisson(imex_ctx* c, const double* b, double* psi, int on
   double res = 0.0;
   long long its = 0;
   TRY(solve_poisson(c, c->bp, c->psi, &its, &res));
+  c->psi_tau = 0.0;
   c->stats.poisson_iters = its;
   c->stats.max_poisson_res = res;
   return copy_out(c, psi, c->psi, c->np, on_device);

@@ -195,8 +195,10 @@ seg_xr_kernel(T* __restrict__ x, T* __restrict__ r, const T* __restrict__ p, con
               const T* __restrict__ dinv, SegTable t, CgScalars sc, double* __restrict__ partial,
               unsigned int* __restrict__ counter, int maxit) {
   constexpr int VN = Vec16<T>::n, U = unroll_of(VN);
+  pdl_trigger();
   const SegBlock c = chunk_of(t);
   T acc[4] = {T(0), T(0), T(0), T(0)};          // (r, z), (r, r), sum z, sum r
+  pdl_wait();
   if (sc.done[c.s] == 0) {
     const T a = pick<T>(sc.alpha, sc.alpha_f, c.s);
     T* xs = x + c.off;
@@ -293,7 +295,9 @@ __global__ void __launch_bounds__(CG_THREADS)
 seg_p_kernel(T* __restrict__ p, T* __restrict__ r, const T* __restrict__ dinv, SegTable t, CgScalars sc,
              int restart) {
   constexpr int VN = Vec16<T>::n, U = unroll_of(VN);
+  pdl_trigger();
   const SegBlock c = chunk_of(t);
+  pdl_wait();
   if (sc.done[c.s] != 0) return;
   const bool proj = sc.project != 0;
   const T beta = restart ? T(0) : pick<T>(sc.beta, sc.beta_f, c.s);
@@ -504,11 +508,11 @@ seg_sub_kernel(double* __restrict__ x, SegTable t, const double* __restrict__ me
 template <typename T>
 void seg_step_xr(T* x, T* r, const T* p, const T* Ap, const T* dinv, const SegTable& t, const CgScalars& sc,
                  int maxit, double* partial, unsigned int* counter, cudaStream_t st) {
-  IMEX_COUNTED(seg_xr_kernel<T><<<t.nblk, CG_THREADS, 0, st>>>(x, r, p, Ap, dinv, t, sc, partial, counter, maxit));
+  launch_cg_kernel(seg_xr_kernel<T>, t.nblk, CG_THREADS, 0, st, x, r, p, Ap, dinv, t, sc, partial, counter, maxit);
 }
 template <typename T>
 void seg_step_p(T* p, T* r, const T* dinv, const SegTable& t, const CgScalars& sc, int restart, cudaStream_t st) {
-  IMEX_COUNTED(seg_p_kernel<T><<<t.nblk, CG_THREADS, 0, st>>>(p, r, dinv, t, sc, restart));
+  launch_cg_kernel(seg_p_kernel<T>, t.nblk, CG_THREADS, 0, st, p, r, dinv, t, sc, restart);
 }
 template <typename T>
 void seg_dot(const T* x, const T* y, const SegTable& t, double* out, double* partial, unsigned int* counter,

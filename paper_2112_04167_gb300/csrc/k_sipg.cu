@@ -1183,11 +1183,35 @@ constexpr size_t sipg3l_smem() {
   return sizeof(T) * (size_t)(S::EPB * S::TILE + S::EPB * S::ND);
 }
 
+// what a line's face terms need of the two neighbour lines along its direction: the
+// neighbours' traces at the shared faces and their normal derivatives there (unit size)
+template <typename T>
+struct LineFaces {
+  T tl, dl, tr, dr;
+};
+template <typename T, int N, typename TS>
+__device__ __forceinline__ LineFaces<T> line_faces(const ConstLine<T>& L, const TS* cl, const TS* cr, int stride) {
+  T vl[N], vr[N];
+#pragma unroll
+  for (int j = 0; j < N; ++j) { vl[j] = T(cl[j * stride]); vr[j] = T(cr[j * stride]); }
+  LineFaces<T> f{vl[N - 1], T(0), vr[0], T(0)};
+#pragma unroll
+  for (int j = 0; j < N; ++j) { f.dl += L.dnL[j] * vl[j]; f.dr += L.dnR[j] * vr[j]; }
+  return f;
+}
+
 template <typename T, int N, typename TS = T>
 __device__ __forceinline__ T sipg3l_group(const Geom& g, const SipgArgs<TS>& a, const TS* __restrict__ x,
                                           TS* __restrict__ y, int grp) {
   using S = Sipg3lShape<T, N>;
   constexpr int NN = S::NN, ND = S::ND, EPB = S::EPB, NP = S::NP, TILE = S::TILE, VEC = S::VEC;
+  // FP32 up to N = 8: all neighbour lines are loaded before the first pass, so that their
+  // latency is paid once rather than after each of the two barriers (12 scalars stay live);
+  // the wider types and N = 9 load them pass by pass (register pressure)
+#ifndef IMEX_SIPG3L_HOIST
+#define IMEX_SIPG3L_HOIST 1
+#endif
+  constexpr bool HOIST = IMEX_SIPG3L_HOIST && sizeof(T) == 4 && N <= 8;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* tile = reinterpret_cast<T*>(smem_raw);                       // [EPB][z][y][NP]
   T* acc = tile + EPB * TILE;                                     // [EPB][z][y][x]
@@ -1214,32 +1238,37 @@ __device__ __forceinline__ T sipg3l_group(const Geom& g, const SipgArgs<TS>& a, 
   T* ma = acc + le * ND;
   const size_t eb = (size_t)e * ND;
   const int ta = t % N, tb = t / N;                               // the thread's two line coordinates
+  // neighbour lines: z at (x = ta, y = tb), y at (x = ta, z = tb), x at (y = ta, z = tb)
+  const TS* zl = x + (size_t)nb[4] * ND + t;
+  const TS* zr = x + (size_t)nb[5] * ND + t;
+  const TS* yl = x + (size_t)nb[2] * ND + tb * NN + ta;
+  const TS* yr = x + (size_t)nb[3] * ND + tb * NN + ta;
+  const TS* xl = x + (size_t)nb[0] * ND + tb * NN + ta * N;
+  const TS* xr = x + (size_t)nb[1] * ND + tb * NN + ta * N;
   // own element into the shared tile; the z-column (ta, tb) stays in registers
   T u[N];
 #pragma unroll
   for (int k = 0; k < N; ++k) u[k] = T(0);
+  LineFaces<T> fz{}, fy{}, fx{};
+  pdl_wait();
   if (valid) {
 #pragma unroll
-    for (int k = 0; k < N; ++k) {
-      u[k] = T(x[eb + k * NN + t]);
-      mt[(k * N + tb) * NP + ta] = u[k];
+    for (int k = 0; k < N; ++k) u[k] = T(x[eb + k * NN + t]);
+    if (HOIST) {
+      fz = line_faces<T, N>(L, zl, zr, NN);
+      fy = line_faces<T, N>(L, yl, yr, N);
+      fx = line_faces<T, N>(L, xl, xr, 1);
     }
+#pragma unroll
+    for (int k = 0; k < N; ++k) mt[(k * N + tb) * NP + ta] = u[k];
   }
   // pass z: line (x = ta, y = tb) along z
   if (valid) {
-    const TS* cl = x + (size_t)nb[4] * ND + t;
-    const TS* cr = x + (size_t)nb[5] * ND + t;
-    T vl[N], vr[N];
-#pragma unroll
-    for (int j = 0; j < N; ++j) { vl[j] = T(cl[j * NN]); vr[j] = T(cr[j * NN]); }
-    T dl = T(0), dr = T(0);
-#pragma unroll
-    for (int j = 0; j < N; ++j) { dl += L.dnL[j] * vl[j]; dr += L.dnR[j] * vr[j]; }
-    const T tl = vl[N - 1], tr = vr[0];
+    if (!HOIST) fz = line_faces<T, N>(L, zl, zr, NN);
     const T wt = (T(0.5) * hx * L.w[ta]) * (T(0.5) * hy * L.w[tb]) * ihz;
 #pragma unroll
     for (int k = 0; k < N; ++k) {
-      T sk = L.ctrL[k] * tl + L.cdnL[k] * dl + L.ctrR[k] * tr + L.cdnR[k] * dr;
+      T sk = L.ctrL[k] * fz.tl + L.cdnL[k] * fz.dl + L.ctrR[k] * fz.tr + L.cdnR[k] * fz.dr;
 #pragma unroll
       for (int j = 0; j < N; ++j) sk += L.A[k * N + j] * u[j];
       ma[k * NN + t] = wt * sk;
@@ -1251,19 +1280,11 @@ __device__ __forceinline__ T sipg3l_group(const Geom& g, const SipgArgs<TS>& a, 
     T v[N];
 #pragma unroll
     for (int j = 0; j < N; ++j) v[j] = mt[(tb * N + j) * NP + ta];
-    const TS* cl = x + (size_t)nb[2] * ND + tb * NN + ta;
-    const TS* cr = x + (size_t)nb[3] * ND + tb * NN + ta;
-    T vl[N], vr[N];
-#pragma unroll
-    for (int j = 0; j < N; ++j) { vl[j] = T(cl[j * N]); vr[j] = T(cr[j * N]); }
-    T dl = T(0), dr = T(0);
-#pragma unroll
-    for (int j = 0; j < N; ++j) { dl += L.dnL[j] * vl[j]; dr += L.dnR[j] * vr[j]; }
-    const T tl = vl[N - 1], tr = vr[0];
+    if (!HOIST) fy = line_faces<T, N>(L, yl, yr, N);
     const T wt = (T(0.5) * hx * L.w[ta]) * (T(0.5) * hz * L.w[tb]) * ihy;
 #pragma unroll
     for (int o = 0; o < N; ++o) {
-      T so = L.ctrL[o] * tl + L.cdnL[o] * dl + L.ctrR[o] * tr + L.cdnR[o] * dr;
+      T so = L.ctrL[o] * fy.tl + L.cdnL[o] * fy.dl + L.ctrR[o] * fy.tr + L.cdnR[o] * fy.dr;
 #pragma unroll
       for (int j = 0; j < N; ++j) so += L.A[o * N + j] * v[j];
       ma[(tb * N + o) * N + ta] += wt * so;
@@ -1283,20 +1304,12 @@ __device__ __forceinline__ T sipg3l_group(const Geom& g, const SipgArgs<TS>& a, 
 #pragma unroll
       for (int j = 0; j < VEC; ++j) v[q * VEC + j] = pw[j];
     }
-    const TS* rl = x + (size_t)nb[0] * ND + tb * NN + ta * N;
-    const TS* rr = x + (size_t)nb[1] * ND + tb * NN + ta * N;
-    T vl[N], vr[N];
-#pragma unroll
-    for (int j = 0; j < N; ++j) { vl[j] = T(rl[j]); vr[j] = T(rr[j]); }
-    T dl = T(0), dr = T(0);
-#pragma unroll
-    for (int j = 0; j < N; ++j) { dl += L.dnL[j] * vl[j]; dr += L.dnR[j] * vr[j]; }
-    const T tl = vl[N - 1], tr = vr[0];
+    if (!HOIST) fx = line_faces<T, N>(L, xl, xr, 1);
     const T wyz = (T(0.5) * hy * L.w[ta]) * (T(0.5) * hz * L.w[tb]);
     const T wt = wyz * ihx;
 #pragma unroll
     for (int o = 0; o < N; ++o) {
-      T so = L.ctrL[o] * tl + L.cdnL[o] * dl + L.ctrR[o] * tr + L.cdnR[o] * dr;
+      T so = L.ctrL[o] * fx.tl + L.cdnL[o] * fx.dl + L.ctrR[o] * fx.tr + L.cdnR[o] * fx.dr;
 #pragma unroll
       for (int j = 0; j < N; ++j) so += L.A[o * N + j] * v[j];
       const int node = (tb * N + ta) * N + o;
@@ -1310,10 +1323,17 @@ __device__ __forceinline__ T sipg3l_group(const Geom& g, const SipgArgs<TS>& a, 
   return dacc;
 }
 
+// FP32 up to N = 8: at least IMEX_SIPG3P_MINB resident blocks per SM (a register cap; 5
+// keeps the hoisted neighbour loads at 56 registers for N = 7 without spills; measured on
+// the 16^3, N = 7 pressure apply: 21.0 us against 22.0 us for the unhoisted form)
+#ifndef IMEX_SIPG3P_MINB
+#define IMEX_SIPG3P_MINB 5
+#endif
 template <typename T, int N, typename TS = T>
-__global__ void __launch_bounds__(Sipg3pShape<T, N>::THREADS, (sizeof(T) == 4 && N <= 8) ? 3 : 1)
+__global__ void __launch_bounds__(Sipg3pShape<T, N>::THREADS, (sizeof(T) == 4 && N <= 8) ? IMEX_SIPG3P_MINB : 1)
 sipg3p_apply_kernel(Geom g, SipgArgs<TS> a) {
   __shared__ double red[Sipg3pShape<T, N>::THREADS];
+  pdl_trigger();
   for (int s = 0; s < a.nsys; ++s) {
     if (s > 0) __syncthreads();
     const T dacc = sipg3l_group<T, N, TS>(g, a, a.x + (size_t)s * a.sys_stride, a.y + (size_t)s * a.sys_stride,
@@ -1734,7 +1754,7 @@ static void launch_apply3(const Geom& g, const SipgArgs<T>& a, cudaStream_t st) 
     using P = Sipg3pShape<T, N>;
     constexpr size_t sm = sipg3l_smem<T, N>();
     smem_limit_once((const void*)sipg3p_apply_kernel<T, N>, (int)sm);
-    IMEX_COUNTED(sipg3p_apply_kernel<T, N><<<(g.ne + P::EPB - 1) / P::EPB, P::THREADS, sm, st>>>(g, a));
+    launch_cg_kernel(sipg3p_apply_kernel<T, N>, (g.ne + P::EPB - 1) / P::EPB, P::THREADS, sm, st, g, a);
     return;
   }
   if (!a.nu && a.ops) {

@@ -1,6 +1,7 @@
 // Vector kernels: stage linear combinations (FP64), deterministic two-level
 // reductions (FP64 accumulation), precision conversion and the allocation-free
 // reduction entry point.  The Jacobi-PCG kernels live in k_cg.cu.
+#include <cstdlib>
 #include <atomic>
 #include <mutex>
 #include <type_traits>
@@ -20,6 +21,13 @@ void count_launch() {
   ++t_launches;
 }
 void add_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+bool pdl_enabled() {
+  static const bool on = [] {
+    const char* e = std::getenv("IMEX_PDL");
+    return e && std::atoi(e) != 0;
+  }();
+  return on;
+}
 long long thread_launch_count() { return t_launches; }
 
 void smem_limit_once(const void* kernel, int bytes) {

@@ -93,6 +93,24 @@ def test_rk_step_mms_dirichlet_varnu(tab):
     run_steps(ctx, disc, lambda v, t, dt: ns.rk_step(disc, tab, v, t, dt)[0], v0, 0.0, 2e-3, 2, 1e-11)
 
 
+@pytest.mark.parametrize("case", ["tg2d", "mms"])
+def test_pressure_is_last_stage_potential(case):
+    """get_pressure returns the potential psi'' of the last stage projection of Alg. 3
+    (mass-weighted mean removed), also when a final projection follows (variable viscosity);
+    each stage solve starts from the previous potential scaled to its own time scale, which
+    must leave every result unchanged."""
+    ctx, disc, fl = tg2d_pair() if case == "tg2d" else mms_pair()
+    dt = 0.01 if case == "tg2d" else 2e-3
+    v, t = fl.initial(disc.X).reshape(2, -1), 0.0
+    for _ in range(2):
+        ctx.set_state(t, v)
+        ctx.step(dt, 1)
+        v, info = ns.rk_step(disc, "CB3e", v, t, dt)
+        t += dt
+        assert rel(ctx.get_velocity(), v) < 1e-11
+        assert rel(ctx.get_pressure(), info["psi"]) < 1e-9
+
+
 def test_sdc_step_tg2d():
     ctx, disc, fl = tg2d_pair(P=3, n=3)
     ctx.set_sdc(3, 2, "CB3e")
