@@ -63,6 +63,7 @@ __device__ __forceinline__ bool operator<(ff a, ff b) { return a.hi < b.hi || (a
 __device__ __forceinline__ bool operator>(ff a, ff b) { return b < a; }
 
 template <> __host__ __device__ __forceinline__ ff geom_h<ff>(const Geom& g, int k) { return ff(geom_h<double>(g, k)); }
+template <> __host__ __device__ __forceinline__ ff geom_nu0<ff>(const Geom& g) { return ff(g.inu0); }
 
 // table (storage) type of an arithmetic type: ff kernels read the FP64 tables
 template <typename T> struct TableType { using type = T; };

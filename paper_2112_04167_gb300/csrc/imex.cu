@@ -191,6 +191,7 @@ struct imex_ctx {
   float *fnu = nullptr, *fvtmp = nullptr;
   double* partial = nullptr;
   double* apartial = nullptr;   // per-block partials of the fused apply + dot
+  size_t apartial_cap = 0;      // its length in doubles
   unsigned int* counters = nullptr;
   int nblocks = 0;
   double* dscal = nullptr;      // 16 x 4 doubles of scalars
@@ -216,6 +217,11 @@ struct imex_ctx {
   int* cg_hi = nullptr;
   double* seg_partial = nullptr;
   bool diag_valid_p = false;
+  // diagonal of the velocity SIPG operator with unit factor for a viscosity that is constant
+  // per element (the Helmholtz diagonals are M + gamma dt_e times it), valid for kdiag_nu
+  double* kdiag = nullptr;
+  bool kdiag_valid = false;
+  double kdiag_nu = 0.0;
   // instances of the mesh: one for a plain context; several for the union mesh of a batch
   // group, whose kernels see per-element geometry, viscosity, time step and time
   bool batched = false;
@@ -416,6 +422,10 @@ void fuse_cg(imex_ctx* c, SipgArgs<T>& a, const CgScalars* cg) {
   a.cg_alpha = cg->alpha;
   a.cg_alpha_f = cg->alpha_f;
   a.cg_done = cg->done;
+  if (cg->apart) {                       // the step kernel adds the partials itself
+    a.dot_defer = 1;
+    a.dot_nblk = const_cast<unsigned int*>(cg->apart_n);
+  }
 }
 
 // batch groups: velocity operators take the constant viscosity of each element's instance
@@ -499,7 +509,23 @@ CgScalars scalars(imex_ctx* c, double tol, bool project) {
   s.iters = c->cg_i + 1 * m;
   s.tol2 = tol * tol;
   s.project = project ? 1 : 0;
+  s.apart = nullptr;
+  s.apart_n = nullptr;
+  s.apart_seg = 0;
   return s;
+}
+
+// The (p, A p) partials of the CG loop are left to the step kernel, which forms alpha itself:
+// those of the fused apply, or else those of the dot kernel (one per segment block, when
+// they fit the partials buffer)
+void defer_dot(imex_ctx* c, CgScalars& s, bool fused, const SegTable& t) {
+  if (fused) {
+    s.apart = c->apartial;
+    s.apart_n = c->counters + 4;
+  } else if ((size_t)t.nblk <= c->apartial_cap) {
+    s.apart = c->apartial;
+    s.apart_seg = 1;
+  }
 }
 
 // Enqueue body() -- kernel launches only, no host synchronisation -- as a CUDA graph cached
@@ -567,6 +593,7 @@ imex_status pcg(imex_ctx* c, const imex_ctx::Seg& sg, Op op, OpDot op_dot, bool 
                 const std::vector<unsigned long long>& opkey, long long* iters_out, double* res_out) {
   const SegTable& t = sg.t;
   CgScalars sc = scalars(c, tol, project);
+  defer_dot(c, sc, fused, t);
   const int nsys = t.nseg;
   const int m = c->maxsys;
   double* r = c->cr;
@@ -645,6 +672,7 @@ imex_status pcg_mixed(imex_ctx* c, const imex_ctx::Seg& sg, Op64 op64, Op32 op32
   const SegTable& t = sg.t;
   const size_t ntot = sg.total;
   CgScalars sc = scalars(c, tol, project);
+  defer_dot(c, sc, fused, t);
   const int nsys = t.nseg;
   const int m = c->maxsys;
   const double delta = 1e-2;
@@ -842,13 +870,27 @@ imex_status solve_helmholtz(imex_ctx* c, const double* rhs, double* x, const dou
   // Jacobi diagonal of M + gamma A(nu)  (stored in cdiag + np region-free slot: use cdiag[np..])
   double* dg = c->cdiag + c->np;
   float* fdg = c->fdiag + c->np;
-  SipgArgs<double> a = sipg_args<double>(nullptr, dg, 1, (long long)n, nu, nu_const(c), nullptr, 1.0, gamma, 0);
-  vel_flags(c, a, true);
-  TRY(launch_check(c, sipg_diag<double>(c->gv, c->Nv, a, c->st), "sipg_diag(v)"));
-  reciprocal<double>(dg, n, c->st);
+  if (nu == nullptr) {
+    // viscosity constant per element: M and A(nu) do not change between stages
+    if (!c->kdiag_valid || c->kdiag_nu != nu_const(c)) {
+      SipgArgs<double> a = sipg_args<double>(nullptr, c->kdiag, 1, (long long)n, nullptr, nu_const(c), nullptr, 0.0,
+                                             1.0, 0);
+      vel_flags(c, a, false);
+      TRY(launch_check(c, sipg_diag<double>(c->gv, c->Nv, a, c->st), "sipg_diag(v)"));
+      c->kdiag_valid = true;
+      c->kdiag_nu = nu_const(c);
+    }
+    helm_diag(dg, c->mass_v, c->kdiag, gamma, c->batched ? c->edt : nullptr, ipow(c->Nv, d), n, c->st);
+  } else {
+    SipgArgs<double> a = sipg_args<double>(nullptr, dg, 1, (long long)n, nu, nu_const(c), nullptr, 1.0, gamma, 0);
+    vel_flags(c, a, true);
+    TRY(launch_check(c, sipg_diag<double>(c->gv, c->Nv, a, c->st), "sipg_diag(v)"));
+    reciprocal<double>(dg, n, c->st);
+  }
   const double tol = c->desc.tol;
-  // the chunk graphs depend on gamma and on whether the viscosity is a field
-  const std::vector<unsigned long long> hkey = {2, bits(gamma), addr(nu), (unsigned long long)d};
+  // the chunk graphs depend on gamma, on whether the viscosity is a field and on its constant
+  // value (captured into the kernels' arguments)
+  const std::vector<unsigned long long> hkey = {2, bits(gamma), addr(nu), (unsigned long long)d, bits(nu_const(c))};
   if (c->desc.precision == IMEX_FP64) {
     auto op = [&](const double* xx, double* yy) { return apply_helm<double>(c, xx, yy, d, nu, gamma); };
     auto opd = [&](const double* xx, double* yy, const CgScalars* dd) {
@@ -907,21 +949,25 @@ const double* nu_ptr(const imex_ctx* c, const double* nu) { return variable_nu(c
 
 // F_d3 = -D(nu D.v) into out; if E != nullptr also E += F_d2 = sum_k D_k(nu D_c v_k) (variable nu)
 imex_status graddiv(imex_ctx* c, const double* v, const double* nu, double* fd3, double* fd2_acc) {
+  // the mixed form evaluates the derivatives in float-float
+  auto deriv = [&](const DerivArgs<double>& x) {
+    return c->desc.precision == IMEX_MIXED ? dg_deriv_ff(c->gv, c->Nv, x, c->st) : dg_deriv<double>(c->gv, c->Nv, x, c->st);
+  };
   DerivArgs<double> a{};
   a.op = 0; a.in = v; a.stride = (long long)c->nv; a.nu = nu_ptr(c, nu); a.nu0 = nu_const(c); a.out = c->phi;
   a.inst_nu = c->batched && a.nu == nullptr;
-  TRY(launch_check(c, dg_deriv<double>(c->gv, c->Nv, a, c->st), "dg_deriv(div)"));
+  TRY(launch_check(c, deriv(a), "dg_deriv(div)"));
   DerivArgs<double> b{};
   b.op = 1; b.in = c->phi; b.stride = (long long)c->nv; b.coef = -1.0; b.out = fd3;
-  TRY(launch_check(c, dg_deriv<double>(c->gv, c->Nv, b, c->st), "dg_deriv(grad)"));
+  TRY(launch_check(c, deriv(b), "dg_deriv(grad)"));
   if (fd2_acc) {
     DerivArgs<double> j{};
     j.op = 2; j.in = v; j.stride = (long long)c->nv; j.nu = nu_ptr(c, nu); j.nu0 = nu_const(c); j.out = c->jac;
     j.inst_nu = c->batched && j.nu == nullptr;
-    TRY(launch_check(c, dg_deriv<double>(c->gv, c->Nv, j, c->st), "dg_deriv(jac)"));
+    TRY(launch_check(c, deriv(j), "dg_deriv(jac)"));
     DerivArgs<double> q{};
     q.op = 3; q.in = c->jac; q.stride = (long long)c->nv; q.coef = 1.0; q.out = fd2_acc;
-    TRY(launch_check(c, dg_deriv<double>(c->gv, c->Nv, q, c->st), "dg_deriv(divT)"));
+    TRY(launch_check(c, deriv(q), "dg_deriv(divT)"));
   }
   return IMEX_OK;
 }
@@ -1399,6 +1445,7 @@ imex_status set_layout(imex_ctx* c) {
   SipgArgs<double> b = sipg_args<double>(nullptr, c->mass_p, 1, (long long)c->np, nullptr, 0.0, nullptr, 1.0, 0.0, 0);
   TRY(launch_check(c, sipg_diag<double>(c->gp, c->Np, b, c->st), "mass(p)"));
   c->diag_valid_p = false;
+  c->kdiag_valid = false;
   CK(cudaStreamSynchronize(c->st), "sync");
   for (auto& gr : c->graphs) cudaGraphExecDestroy(gr.exec);
   c->graphs.clear();
@@ -1469,6 +1516,7 @@ imex_status init_ctx(imex_ctx* c) {
   if ((s = dalloc(c, &c->psi_f, npc)) != IMEX_OK) return bail(s);
   if ((s = dalloc(c, &c->bp, npc)) != IMEX_OK) return bail(s);
   if ((s = dalloc(c, &c->mass_v, nvc)) != IMEX_OK) return bail(s);
+  if ((s = dalloc(c, &c->kdiag, nvc)) != IMEX_OK) return bail(s);
   if ((s = dalloc(c, &c->mass_p, npc)) != IMEX_OK) return bail(s);
   if ((s = dalloc(c, &c->cdiag, npc + nvc)) != IMEX_OK) return bail(s);
   float** f32[] = {&c->fx, &c->fr, &c->fp, &c->fAp};
@@ -1478,7 +1526,8 @@ imex_status init_ctx(imex_ctx* c) {
   if ((s = dalloc(c, &c->fvtmp, nt + npc)) != IMEX_OK) return bail(s);
   c->nblocks = 152 * 4;
   if ((s = dalloc(c, &c->partial, (size_t)c->nblocks * 8)) != IMEX_OK) return bail(s);
-  if ((s = dalloc(c, &c->apartial, (size_t)(c->ne_cap + 64) * 3)) != IMEX_OK) return bail(s);
+  c->apartial_cap = (size_t)(c->ne_cap + 64) * 3;
+  if ((s = dalloc(c, &c->apartial, c->apartial_cap)) != IMEX_OK) return bail(s);
   if ((s = dalloc(c, &c->counters, 8)) != IMEX_OK) return bail(s);
   cudaMemsetAsync(c->counters, 0, 8 * sizeof(unsigned int), c->st);
   if ((s = dalloc(c, &c->persist_partial, 5 * 4096)) != IMEX_OK) return bail(s);

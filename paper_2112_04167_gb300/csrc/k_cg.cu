@@ -199,8 +199,40 @@ seg_xr_kernel(T* __restrict__ x, T* __restrict__ r, const T* __restrict__ p, con
   const SegBlock c = chunk_of(t);
   T acc[4] = {T(0), T(0), T(0), T(0)};          // (r, z), (r, r), sum z, sum r
   pdl_wait();
-  if (sc.done[c.s] == 0) {
-    const T a = pick<T>(sc.alpha, sc.alpha_f, c.s);
+  bool run = sc.done[c.s] == 0;
+  T a;
+  if (sc.apart) {
+    // the apply (or the dot kernel) left per-block partials of (p, A p) in T: every block
+    // adds those of its system in the same order, so all blocks of a system hold the same
+    // alpha
+    const T* pp = reinterpret_cast<const T*>(sc.apart);
+    int b0, b1;
+    if (sc.apart_seg) {
+      b0 = t.seg_blk0[c.s];
+      b1 = t.seg_blk0[c.s + 1];
+    } else {
+      const int nb = (int)*sc.apart_n;
+      b0 = c.s * nb;
+      b1 = b0 + nb;
+    }
+    T v[1] = {T(0)};
+    for (int b = b0 + threadIdx.x; b < b1; b += CG_THREADS) v[0] += pp[b];
+    double tot[1];
+    block_sum_k<T, 1>(v, tot);
+    // alpha = rz / pAp in T: the step uses it in T, and FP32 needs no FP64 division
+    __shared__ T s_alpha;
+    if (threadIdx.x == 0) {
+      const T al = tot[0] != 0.0 ? T(sc.rz[c.s]) / T(tot[0]) : T(0);
+      s_alpha = al;
+      if (!isfinite(al) && run) atomicCAS(sc.done + c.s, 0, 2);   // breakdown of this system
+    }
+    __syncthreads();
+    a = s_alpha;
+    run = run && isfinite(a);
+  } else {
+    a = pick<T>(sc.alpha, sc.alpha_f, c.s);
+  }
+  if (run) {
     T* xs = x + c.off;
     T* rs = r + c.off;
     const T* ps = p + c.off;
@@ -401,6 +433,11 @@ seg_pap_kernel(const T* __restrict__ p, const T* __restrict__ Ap, SegTable t, Cg
   T acc[1] = {sc.done[c.s] == 0 ? chunk_dot(p + c.off, Ap + c.off, c.n) : T(0)};
   double bs[1];
   block_sum_k<T, 1>(acc, bs);
+  if (sc.apart_seg) {
+    // deferred: the block's partial in T, added by the step kernel of its segment
+    if (threadIdx.x == 0) reinterpret_cast<T*>(const_cast<double*>(sc.apart))[blockIdx.x] = (T)bs[0];
+    return;
+  }
   if (threadIdx.x == 0) partial[blockIdx.x] = bs[0];
   if (!last_block(counter)) return;
   seg_totals<1>(t, partial, [&](int q, const double* tot) {

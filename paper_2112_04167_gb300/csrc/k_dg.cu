@@ -15,31 +15,65 @@
 namespace imex {
 
 // ----------------------------------------------------------------------------
-// generic 1D contraction along dimension m of a tensor with per-dimension sizes
-//   out[.., a, ..] (+)= sum_x Mat[a*sa + x*sx] * in[.., x, ..]
-// executed by `nt` threads starting at thread `t0` of the block
+// 1D contraction along dimension M of a tensor with extents S0 x S1 x S2
+//   out[.., a, ..] (+)= sum_x Mat[a*SA + x*SX] * in[.., x, ..]    (a < NA)
+// executed by `nt` threads starting at thread `t` of the block.  All extents and strides
+// are compile-time constants: the index arithmetic divides by constants and the inner sum
+// unrolls.
 // ----------------------------------------------------------------------------
-template <typename T, int D>
-__device__ __forceinline__ void contract(const T* __restrict__ in, T* __restrict__ out, const int* sz,
-                                         int m, int na, const T* Mat, int sa, int sx, bool acc,
-                                         int t, int nt) {
-  int szo[3] = {sz[0], D > 1 ? sz[1] : 1, D > 2 ? sz[2] : 1};
-  szo[m] = na;
-  int total = szo[0] * szo[1] * szo[2];
-  int sin_m = 1;
-  for (int j = 0; j < m; ++j) sin_m *= sz[j];
-  for (int o = t; o < total; o += nt) {
-    int c0 = o % szo[0];
-    int r = o / szo[0];
-    int c1 = r % szo[1];
-    int c2 = r / szo[1];
-    int c[3] = {c0, c1, c2};
-    int a = c[m];
-    c[m] = 0;
-    int ib = c[0] + sz[0] * (c[1] + (D > 1 ? sz[1] : 1) * c[2]);
+template <typename T, int S0, int S1, int S2, int M, int NA, int SA, int SX, bool ACC>
+__device__ __forceinline__ void contract_ct(const T* __restrict__ in, T* __restrict__ out, const T* __restrict__ Mat,
+                                            int t, int nt) {
+  constexpr int O0 = (M == 0) ? NA : S0, O1 = (M == 1) ? NA : S1, O2 = (M == 2) ? NA : S2;
+  constexpr int TOTAL = O0 * O1 * O2;
+  constexpr int SIN = (M == 0) ? 1 : (M == 1) ? S0 : S0 * S1;       // input stride along M
+  constexpr int SM = (M == 0) ? S0 : (M == 1) ? S1 : S2;            // summed extent
+  for (int o = t; o < TOTAL; o += nt) {
+    const int c0 = o % O0, r = o / O0, c1 = r % O1, c2 = r / O1;
+    const int a = (M == 0) ? c0 : (M == 1) ? c1 : c2;
+    const int ib = ((M == 0) ? 0 : c0) + S0 * (((M == 1) ? 0 : c1) + S1 * ((M == 2) ? 0 : c2));
     T s = T(0);
-    for (int x = 0; x < sz[m]; ++x) s += Mat[a * sa + x * sx] * in[ib + x * sin_m];
-    out[o] = acc ? out[o] + s : s;
+#pragma unroll
+    for (int x = 0; x < SM; ++x) s += Mat[a * SA + x * SX] * in[ib + x * SIN];
+    out[o] = ACC ? out[o] + s : s;
+  }
+}
+
+// N^D nodal values -> Q^D points, one direction per pass (w1, w2 scratch of Q^D)
+template <typename T, int D, int N, int Q>
+__device__ __forceinline__ void to_points(const T* in, T* out, T* w1, T* w2, const T* IG, int t, int nt) {
+  if constexpr (D == 2) {
+    contract_ct<T, N, N, 1, 0, Q, N, 1, false>(in, w1, IG, t, nt);
+    __syncthreads();
+    contract_ct<T, Q, N, 1, 1, Q, N, 1, false>(w1, out, IG, t, nt);
+    __syncthreads();
+  } else {
+    contract_ct<T, N, N, N, 0, Q, N, 1, false>(in, w1, IG, t, nt);
+    __syncthreads();
+    contract_ct<T, Q, N, N, 1, Q, N, 1, false>(w1, w2, IG, t, nt);
+    __syncthreads();
+    contract_ct<T, Q, Q, N, 2, Q, N, 1, false>(w2, out, IG, t, nt);
+    __syncthreads();
+  }
+}
+
+// Q^D point values (in w1) tested against the N^D basis with the matrices M0, M1, M2 per
+// direction (transposed: out[j] = sum_g M[g N + j] in[g]), added into acc
+template <typename T, int D, int N, int Q>
+__device__ __forceinline__ void to_nodes_add(T* acc, T* w1, T* w2, const T* M0, const T* M1, const T* M2, int t,
+                                             int nt) {
+  if constexpr (D == 2) {
+    contract_ct<T, Q, Q, 1, 0, N, 1, N, false>(w1, w2, M0, t, nt);
+    __syncthreads();
+    contract_ct<T, N, Q, 1, 1, N, 1, N, true>(w2, acc, M1, t, nt);
+    __syncthreads();
+  } else {
+    contract_ct<T, Q, Q, Q, 0, N, 1, N, false>(w1, w2, M0, t, nt);
+    __syncthreads();
+    contract_ct<T, N, Q, Q, 1, N, 1, N, false>(w2, w1, M1, t, nt);
+    __syncthreads();
+    contract_ct<T, N, N, Q, 2, N, 1, N, true>(w1, acc, M2, t, nt);
+    __syncthreads();
   }
 }
 
@@ -64,26 +98,39 @@ __device__ __forceinline__ void face_coords(int f, int k, int N, int* c) {
 // on the velocity points; phi_a = pressure basis.  Sum factorisation: per direction m
 //   U <- Ip^T U + (2/h_m) Gp^T V_m,  V_k <- Ip^T V_k (k > m),  U_0 = S, V_k = W v_k.
 // ----------------------------------------------------------------------------
-template <typename T, int D>
-__device__ __forceinline__ void contract2(const T* in1, const T* in2, T s2, T* out, const int* sz,
-                                          int m, int na, const T* M1, const T* M2, int t, int nt) {
-  int szo[3] = {sz[0], D > 1 ? sz[1] : 1, D > 2 ? sz[2] : 1};
-  szo[m] = na;
-  const int total = szo[0] * szo[1] * szo[2];
-  int sin_m = 1;
-  for (int j = 0; j < m; ++j) sin_m *= sz[j];
-  for (int o = t; o < total; o += nt) {
-    int c[3] = {o % szo[0], (o / szo[0]) % szo[1], o / (szo[0] * szo[1])};
-    const int am = c[m];
-    c[m] = 0;
-    const int ib = c[0] + sz[0] * (c[1] + (D > 1 ? sz[1] : 1) * c[2]);
+// contract2 with compile-time extents (inputs S0 x S1 x S2, direction M, output extent NA)
+template <typename T, int S0, int S1, int S2, int M, int NA>
+__device__ __forceinline__ void contract2_ct(const T* __restrict__ in1, const T* __restrict__ in2, T s2,
+                                             T* __restrict__ out, const T* __restrict__ M1,
+                                             const T* __restrict__ M2, int t, int nt) {
+  constexpr int O0 = (M == 0) ? NA : S0, O1 = (M == 1) ? NA : S1, O2 = (M == 2) ? NA : S2;
+  constexpr int TOTAL = O0 * O1 * O2;
+  constexpr int SIN = (M == 0) ? 1 : (M == 1) ? S0 : S0 * S1;
+  constexpr int SM = (M == 0) ? S0 : (M == 1) ? S1 : S2;
+  for (int o = t; o < TOTAL; o += nt) {
+    const int c0 = o % O0, r0 = o / O0, c1 = r0 % O1, c2 = r0 / O1;
+    const int am = (M == 0) ? c0 : (M == 1) ? c1 : c2;
+    const int ib = ((M == 0) ? 0 : c0) + S0 * (((M == 1) ? 0 : c1) + S1 * ((M == 2) ? 0 : c2));
     T s = T(0), r = T(0);
-    for (int x = 0; x < sz[m]; ++x) {
-      s += M1[x * na + am] * in1[ib + x * sin_m];
-      if (in2) r += M2[x * na + am] * in2[ib + x * sin_m];
+#pragma unroll
+    for (int x = 0; x < SM; ++x) {
+      s += M1[x * NA + am] * in1[ib + x * SIN];
+      r += M2[x * NA + am] * in2[ib + x * SIN];
     }
     out[o] = s + s2 * r;
   }
+}
+
+// pass M of the weak divergence: U <- Ip^T U + hm Gp^T V_M, V_k <- Ip^T V_k (k > M); the
+// directions before M are already on the NV - 1 pressure points
+template <typename T, int D, int NV, int M>
+__device__ __forceinline__ void div_pass(const T* src, T* dst, T hm, const T* sIp, const T* sGp, int t, int nt) {
+  constexpr int NP = NV - 1, ND = ipow(NV, D);
+  constexpr int S0 = (M > 0) ? NP : NV, S1 = (D > 1) ? ((M > 1) ? NP : NV) : 1, S2 = (D > 2) ? NV : 1;
+  contract2_ct<T, S0, S1, S2, M, NP>(src, src + (1 + M) * ND, hm, dst, sIp, sGp, t, nt);
+#pragma unroll
+  for (int k = M + 1; k < D; ++k)
+    contract_ct<T, S0, S1, S2, M, NP, 1, NP, false>(src + (1 + k) * ND, dst + (1 + k) * ND, sIp, t, nt);
 }
 
 template <typename T, int D, int NV, typename TS = T>
@@ -139,21 +186,18 @@ __global__ void dg_div_kernel(Geom g, DivArgs<TS> a) {
     buf[node] = S;
   }
   __syncthreads();
-  int sz[3] = {NV, D > 1 ? NV : 1, D > 2 ? NV : 1};
-  int cur = 0;
-  for (int m = 0; m < D; ++m) {
-    T* src = buf + (size_t)cur * (D + 1) * ND;
-    T* dst = buf + (size_t)(1 - cur) * (D + 1) * ND;
-    const T hm = T(2) / geom_h<T>(gl, m);
-    contract2<T, D>(src, src + (1 + m) * ND, hm, dst, sz, m, NP, sIp, sGp, threadIdx.x, blockDim.x);
-    for (int k = m + 1; k < D; ++k)
-      contract2<T, D>(src + (1 + k) * ND, (const T*)nullptr, T(0), dst + (1 + k) * ND, sz, m, NP, sIp,
-                      sIp, threadIdx.x, blockDim.x);
+  // one pass per direction, alternating between the two halves of buf
+  T* b0 = buf;
+  T* b1 = buf + (size_t)(D + 1) * ND;
+  div_pass<T, D, NV, 0>(b0, b1, T(2) / geom_h<T>(gl, 0), sIp, sGp, threadIdx.x, blockDim.x);
+  __syncthreads();
+  div_pass<T, D, NV, 1>(b1, b0, T(2) / geom_h<T>(gl, 1), sIp, sGp, threadIdx.x, blockDim.x);
+  __syncthreads();
+  if constexpr (D == 3) {
+    div_pass<T, D, NV, 2>(b0, b1, T(2) / geom_h<T>(gl, 2), sIp, sGp, threadIdx.x, blockDim.x);
     __syncthreads();
-    sz[m] = NP;
-    cur ^= 1;
   }
-  const T* res = buf + (size_t)cur * (D + 1) * ND;
+  const T* res = (D == 3) ? b1 : b0;
   for (int i = threadIdx.x; i < NDP; i += blockDim.x) a.b[(size_t)e * NDP + i] = (TS)(T(a.coef) * res[i]);
 }
 
@@ -223,17 +267,23 @@ __global__ void dg_grad_kernel(Geom g, GradArgs<TS> a) {
   const T wend = sw[0];
   for (int k = 0; k < D; ++k) {
     // d_k psi at the velocity points: Gp' in dim k, Ip elsewhere (generic contractions)
-    int sz[3] = {NP, D > 1 ? NP : 1, D > 2 ? NP : 1};
-    const T* in = sp;
-    T* bufs[2] = {b1, b2};
-    int cur = 0;
-    for (int m = 0; m < D; ++m) {
-      const T* M = (m == k) ? sGp : sIp;
-      contract<T, D>(in, bufs[cur], sz, m, NV, M, NP, 1, false, threadIdx.x, blockDim.x);
+    const T* in;
+    {
+      const T* M0 = (k == 0) ? sGp : sIp;
+      const T* M1 = (k == 1) ? sGp : sIp;
+      contract_ct<T, NP, (D > 1 ? NP : 1), (D > 2 ? NP : 1), 0, NV, NP, 1, false>(sp, b1, M0, threadIdx.x,
+                                                                                 blockDim.x);
       __syncthreads();
-      sz[m] = NV;
-      in = bufs[cur];
-      cur ^= 1;
+      contract_ct<T, NV, (D > 1 ? NP : 1), (D > 2 ? NP : 1), 1, NV, NP, 1, false>(b1, b2, M1, threadIdx.x,
+                                                                                 blockDim.x);
+      __syncthreads();
+      in = b2;
+      if constexpr (D == 3) {
+        const T* M2 = (k == 2) ? sGp : sIp;
+        contract_ct<T, NV, NV, NP, 2, NV, NP, 1, false>(b2, b1, M2, threadIdx.x, blockDim.x);
+        __syncthreads();
+        in = b1;
+      }
     }
     const T hk = T(2) / geom_h<T>(gl, k);
     for (int node = threadIdx.x; node < ND; node += blockDim.x) {
@@ -256,9 +306,9 @@ __global__ void dg_grad_kernel(Geom g, GradArgs<TS> a) {
 // ----------------------------------------------------------------------------
 // nodal DG derivative D_k u at node `node` of element e (central lifting inside)
 // ----------------------------------------------------------------------------
-template <typename T, int D, int N>
+template <typename T, int D, int N, typename TS>
 __device__ __forceinline__ T nodal_deriv(const Geom& g, const int* ec, int e, const int* id, int node,
-                                         int k, const T* su, const T* gfield, const T* sD, T wend) {
+                                         int k, const T* su, const TS* gfield, const T* sD, T wend) {
   constexpr int ND = ipow(N, D);
   int stride = 1;
   for (int j = 0; j < k; ++j) stride *= N;
@@ -266,7 +316,7 @@ __device__ __forceinline__ T nodal_deriv(const Geom& g, const int* ec, int e, co
   T acc = T(0);
 #pragma unroll
   for (int j = 0; j < N; ++j) acc += sD[id[k] * N + j] * su[base + j * stride];
-  const T hk = T(2) / T(g.h[k]);
+  const T hk = T(2) / geom_h<T>(g, k);
   T val = hk * acc;
   for (int side = 0; side < 2; ++side) {
     if (id[k] != (side ? N - 1 : 0)) continue;
@@ -274,21 +324,23 @@ __device__ __forceinline__ T nodal_deriv(const Geom& g, const int* ec, int e, co
     if (nb < 0) continue;
     int c[3] = {id[0], id[1], id[2]};
     c[k] = side ? 0 : N - 1;
-    const T un = gfield[(size_t)nb * ND + flat3(c, N, D)];
+    const T un = T(gfield[(size_t)nb * ND + flat3(c, N, D)]);
     const T n = side ? T(1) : T(-1);
     val += hk / wend * T(0.5) * (un - su[node]) * n;
   }
   return val;
 }
 
-template <typename T, int D, int N>
-__global__ void __launch_bounds__(ipow(N, D)) dg_deriv_kernel(Geom g, DerivArgs<T> a) {
+// T: arithmetic type (double, or the float-float ff); TS: storage type of the fields
+template <typename T, int D, int N, typename TS = T>
+__global__ void __launch_bounds__(ipow(N, D)) dg_deriv_kernel(Geom g, DerivArgs<TS> a) {
+  using TT = typename TableType<T>::type;
   constexpr int ND = ipow(N, D);
   __shared__ T sD[N * N], sw[N];
   __shared__ T su[D][ND];
-  const Tables<T>& tb = tab<T>(g);
-  for (int i = threadIdx.x; i < N * N; i += blockDim.x) sD[i] = tb.D[N][i];
-  for (int i = threadIdx.x; i < N; i += blockDim.x) sw[i] = tb.w[N][i];
+  const Tables<TT>& tb = tab<TT>(g);
+  for (int i = threadIdx.x; i < N * N; i += blockDim.x) sD[i] = T(tb.D[N][i]);
+  for (int i = threadIdx.x; i < N; i += blockDim.x) sw[i] = T(tb.w[N][i]);
   const int e = blockIdx.x;
   int el = 0;
   const Geom gl = local_geom(g, e, el);
@@ -297,35 +349,37 @@ __global__ void __launch_bounds__(ipow(N, D)) dg_deriv_kernel(Geom g, DerivArgs<
   elem_coords(gl, el, ec);
   int id[3] = {node % N, (D > 1) ? (node / N) % N : 0, (D > 2) ? node / (N * N) : 0};
   const size_t o = (size_t)e * ND + node;
-  const T nu = a.nu ? a.nu[o] : (a.inst_nu ? geom_nu0<T>(gl) : a.nu0);
+  const T nu = a.nu ? T(a.nu[o]) : (a.inst_nu ? geom_nu0<T>(gl) : T(a.nu0));
+  const T coef = T(a.coef);
   // op 3 runs one output component per pass over its d input fields
   const int passes = (a.op == 3) ? D : 1;
   for (int c3 = 0; c3 < passes; ++c3) {
     const int nin = (a.op == 1) ? 1 : D;
     const int f0 = (a.op == 3) ? c3 * D : 0;
     __syncthreads();
-    for (int f = 0; f < nin; ++f) su[f][node] = a.in[(size_t)(f0 + f) * a.stride + o];
+    for (int f = 0; f < nin; ++f) su[f][node] = T(a.in[(size_t)(f0 + f) * a.stride + o]);
     __syncthreads();
     const T wend = sw[0];
     if (a.op == 0) {
       T s = T(0);
       for (int k = 0; k < D; ++k)
         s += nodal_deriv<T, D, N>(gl, ec, e, id, node, k, su[k], a.in + (size_t)k * a.stride, sD, wend);
-      a.out[o] = nu * s;
+      a.out[o] = (TS)(nu * s);
     } else if (a.op == 1) {
       for (int c = 0; c < D; ++c)
         a.out[(size_t)c * a.stride + o] =
-            a.coef * nodal_deriv<T, D, N>(gl, ec, e, id, node, c, su[0], a.in, sD, wend);
+            (TS)(coef * nodal_deriv<T, D, N>(gl, ec, e, id, node, c, su[0], a.in, sD, wend));
     } else if (a.op == 2) {
       for (int c = 0; c < D; ++c)
         for (int k = 0; k < D; ++k)
-          a.out[(size_t)(c * D + k) * a.stride + o] =
-              nu * nodal_deriv<T, D, N>(gl, ec, e, id, node, c, su[k], a.in + (size_t)k * a.stride, sD, wend);
+          a.out[(size_t)(c * D + k) * a.stride + o] = (TS)(
+              nu * nodal_deriv<T, D, N>(gl, ec, e, id, node, c, su[k], a.in + (size_t)k * a.stride, sD, wend));
     } else {
       T s = T(0);
       for (int k = 0; k < D; ++k)
         s += nodal_deriv<T, D, N>(gl, ec, e, id, node, k, su[k], a.in + (size_t)(f0 + k) * a.stride, sD, wend);
-      a.out[(size_t)c3 * a.stride + o] += a.coef * s;
+      const size_t oc = (size_t)c3 * a.stride + o;
+      a.out[oc] = (TS)(T(a.out[oc]) + coef * s);
     }
   }
 }
@@ -389,20 +443,7 @@ __global__ void dg_conv_kernel(Geom g, ConvArgs<TS> a) {
   T jac = T(1);
   for (int k = 0; k < D; ++k) jac *= geom_h<T>(gl, k) * T(0.5);
   // --- interpolate v to the Gauss points
-  for (int c = 0; c < D; ++c) {
-    int sz[3] = {N, D > 1 ? N : 1, D > 2 ? N : 1};
-    const T* in = sv + c * ND;
-    T* bufs[2] = {w1, w2};
-    int cur = 0;
-    for (int m = 0; m < D; ++m) {
-      T* out = (m == D - 1) ? (vg + c * NQ) : bufs[cur];
-      contract<T, D>(in, out, sz, m, Q, sIG, N, 1, false, t, nt);
-      __syncthreads();
-      sz[m] = Q;
-      in = out;
-      cur ^= 1;
-    }
-  }
+  for (int c = 0; c < D; ++c) to_points<T, D, N, Q>(sv + c * ND, vg + c * NQ, w1, w2, sIG, t, nt);
   // --- volume term: acc_c += sum_k (test derivative in k) [W_g v_c v_k]
   for (int c = 0; c < D; ++c) {
     for (int k = 0; k < D; ++k) {
@@ -414,22 +455,9 @@ __global__ void dg_conv_kernel(Geom g, ConvArgs<TS> a) {
         w1[q] = W * vg[c * NQ + q] * vg[k * NQ + q];
       }
       __syncthreads();
-      int sz[3] = {Q, D > 1 ? Q : 1, D > 2 ? Q : 1};
-      const T* in = w1;
-      T* bufs[2] = {w2, w1};
-      int cur = 0;
-      // contract dims in order; the last writes into acc (accumulating)
-      for (int m = 0; m < D; ++m) {
-        const T* M = (m == k) ? sDG : sIG;
-        const bool last = (m == D - 1);
-        T* out = last ? (acc + c * ND) : bufs[cur];
-        // backward: out[j] = sum_g M[g*N + j] in[g]
-        contract<T, D>(in, out, sz, m, N, M, 1, N, last, t, nt);
-        __syncthreads();
-        sz[m] = N;
-        in = out;
-        cur ^= 1;
-      }
+      // contract the directions in order; the last pass adds into acc
+      to_nodes_add<T, D, N, Q>(acc + c * ND, w1, w2, k == 0 ? sDG : sIG, k == 1 ? sDG : sIG, k == 2 ? sDG : sIG,
+                               t, nt);
     }
   }
   __syncthreads();
@@ -583,6 +611,11 @@ static void launch_deriv(const Geom& g, const DerivArgs<T>& a, cudaStream_t st) 
   IMEX_COUNTED(dg_deriv_kernel<T, D, N><<<g.ne, ND, 0, st>>>(g, a));
 }
 template <typename T, int D, int N>
+static void launch_deriv_ff(const Geom& g, const DerivArgs<double>& a, cudaStream_t st) {
+  constexpr int ND = ipow(N, D);
+  IMEX_COUNTED(dg_deriv_kernel<ff, D, N, double><<<g.ne, ND, 0, st>>>(g, a));
+}
+template <typename T, int D, int N>
 static void launch_conv(const Geom& g, const ConvArgs<T>& a, cudaStream_t st) {
   using S = ConvShape<T, D, N>;
   smem_limit_once((const void*)dg_conv_kernel<T, D, N>, (int)S::SMEM);
@@ -637,6 +670,13 @@ int dg_div_ff(const Geom& g, int N, const DivArgs<double>& a, cudaStream_t st) {
 int dg_grad_ff(const Geom& g, int N, const GradArgs<double>& a, cudaStream_t st) {
   using T = double;
   if (g.d == 2) { IMEX_DISPATCH_NV(2, launch_grad_ff, g, a, st) } else { IMEX_DISPATCH_NV(3, launch_grad_ff, g, a, st) }
+  return 0;
+}
+
+// nodal DG derivatives with float-float arithmetic on FP64 fields
+int dg_deriv_ff(const Geom& g, int N, const DerivArgs<double>& a, cudaStream_t st) {
+  using T = double;
+  if (g.d == 2) { IMEX_DISPATCH_NV(2, launch_deriv_ff, g, a, st) } else { IMEX_DISPATCH_NV(3, launch_deriv_ff, g, a, st) }
   return 0;
 }
 

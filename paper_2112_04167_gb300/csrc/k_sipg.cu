@@ -56,8 +56,21 @@ __device__ __forceinline__ double block_sum_any_t(T v, double* red_storage) {
 
 // Fused CG dot: each block has left its partial per system in a.dot_partial; the last block
 // to finish adds the partials in block order and writes a.dot_out, then resets the counter.
+// a block's partial of the fused dot; the deferred form stores it in the vector type (the
+// block sums are formed in that type), which the step kernel then adds
+template <typename T>
+__device__ __forceinline__ void put_dot_partial(const SipgArgs<T>& a, int s, double bs) {
+  const size_t i = (size_t)s * gridDim.x + blockIdx.x;
+  if (a.dot_defer) reinterpret_cast<T*>(a.dot_partial)[i] = (T)bs;
+  else a.dot_partial[i] = bs;
+}
+
 template <typename T>
 __device__ void fused_dot_finish(const SipgArgs<T>& a, double* red) {
+  if (a.dot_defer) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) *a.dot_nblk = gridDim.x;
+    return;
+  }
   __shared__ int am_last;
   if (threadIdx.x == 0) {
     __threadfence();                       // this block's partials (written by thread 0) are visible
@@ -655,7 +668,7 @@ sipg3c_apply_kernel(Geom g, SipgArgs<T> a) {
     }
     if (a.dot_out) {
       const double bs = block_sum_any_t<T>(dacc, red);
-      if (threadIdx.x == 0) a.dot_partial[(size_t)s * gridDim.x + blockIdx.x] = bs;
+      if (threadIdx.x == 0) put_dot_partial(a, s, bs);
     }
   }
   if (a.dot_out) fused_dot_finish(a, red);
@@ -779,7 +792,7 @@ sipg2c_apply_kernel(Geom g, SipgArgs<T> a) {
     }
     if (a.dot_out) {
       const double bs = block_sum_any_t<T>(dacc, red);
-      if (threadIdx.x == 0) a.dot_partial[(size_t)s * gridDim.x + blockIdx.x] = bs;
+      if (threadIdx.x == 0) put_dot_partial(a, s, bs);
     }
   }
   if (a.dot_out) fused_dot_finish(a, red);
@@ -882,7 +895,7 @@ sipg2p_apply_kernel(Geom g, SipgArgs<T> a) {
     }
     if (a.dot_out) {
       const double bs = block_sum_any_t<T>(dacc, red);
-      if (threadIdx.x == 0) a.dot_partial[(size_t)s * gridDim.x + blockIdx.x] = bs;
+      if (threadIdx.x == 0) put_dot_partial(a, s, bs);
     }
   }
   if (a.dot_out) fused_dot_finish(a, red);
@@ -998,7 +1011,7 @@ sipg2l_apply_kernel(Geom g, SipgArgs<T> a) {
     }
     if (a.dot_out) {
       const double bs = block_sum_any_t<T>(dacc, red);
-      if (threadIdx.x == 0) a.dot_partial[(size_t)s * gridDim.x + blockIdx.x] = bs;
+      if (threadIdx.x == 0) put_dot_partial(a, s, bs);
     }
   }
   if (a.dot_out) fused_dot_finish(a, red);
@@ -1340,7 +1353,7 @@ sipg3p_apply_kernel(Geom g, SipgArgs<TS> a) {
                                           blockIdx.x);
     if (a.dot_out) {
       const double bs = block_sum_any_t<T>(dacc, red);
-      if (threadIdx.x == 0) a.dot_partial[(size_t)s * gridDim.x + blockIdx.x] = bs;
+      if (threadIdx.x == 0) put_dot_partial(a, s, bs);
     }
   }
   if (a.dot_out) fused_dot_finish(a, red);

@@ -231,6 +231,22 @@ void reciprocal(T* d, size_t n, cudaStream_t st) {
   IMEX_COUNTED(recip_kernel<T><<<grid_for(n, 256), 256, 0, st>>>(d, n));
 }
 
+// Jacobi diagonal of M + gamma A for a viscosity that is constant per element: from the
+// cached diagonals of M and of A (unit factor), d = 1 / (m + gamma dt_e k), with dt_e the
+// element's own time step in a batch group (edt) and 1 otherwise
+__global__ void helm_diag_kernel(double* __restrict__ d, const double* __restrict__ m, const double* __restrict__ k,
+                                 double gamma, const double* __restrict__ edt, long long nd, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const double g = edt ? gamma * edt[i / (size_t)nd] : gamma;
+    d[i] = 1.0 / (m[i] + g * k[i]);
+  }
+}
+void helm_diag(double* d, const double* m, const double* k, double gamma, const double* edt, long long nd, size_t n,
+               cudaStream_t st) {
+  if (n == 0) return;
+  IMEX_COUNTED(helm_diag_kernel<<<grid_for(n, 256), 256, 0, st>>>(d, m, k, gamma, edt, nd, n));
+}
+
 template void reciprocal<double>(double*, size_t, cudaStream_t);
 template void reciprocal<float>(float*, size_t, cudaStream_t);
 

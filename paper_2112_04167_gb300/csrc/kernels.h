@@ -32,6 +32,11 @@ struct SipgArgs {
   double* cg_alpha;
   float* cg_alpha_f;
   int* cg_done;
+  // deferred form of the fused dot: the blocks only leave their partials, block 0 stores the
+  // number of blocks in *dot_nblk, and the next kernel (the CG step) adds them itself -- no
+  // completion counter and no last-block reduction at the end of the apply
+  int dot_defer;
+  unsigned int* dot_nblk;
   // batched meshes: take the constant viscosity from each element's instance instead of nu0
   // (inst_nu), and multiply beta by the instance's time step (inst_dt)
   int inst_nu;
@@ -97,6 +102,8 @@ struct DerivArgs {
   int inst_nu;     // batched meshes: constant viscosity of each element's instance
 };
 template <typename T> int dg_deriv(const Geom& g, int N, const DerivArgs<T>& a, cudaStream_t st);
+// the same with float-float arithmetic on FP64 fields
+int dg_deriv_ff(const Geom& g, int N, const DerivArgs<double>& a, cudaStream_t st);
 
 // Convection F_c = M^{-1} [ sum_K int (v v) : grad w - sum_F int H . w ], LLF flux, Gauss
 // over-integration; vb: Dirichlet data (nodal), out = coef * F_c.
@@ -148,6 +155,9 @@ void axpy_f2d(double* y, const float* x, size_t n, cudaStream_t st);
 
 template <typename T>
 void reciprocal(T* d, size_t n, cudaStream_t st);
+// d = 1 / (m + gamma dt_e k) over n nodes, dt_e = edt[i / nd] (or 1 when edt is null)
+void helm_diag(double* d, const double* m, const double* k, double gamma, const double* edt, long long nd, size_t n,
+               cudaStream_t st);
 
 // ---- pointwise fields (k_fields.cu) --------------------------------------------
 // what: 0 velocity of a closed-form flow (d components), 1 viscosity (1 component),

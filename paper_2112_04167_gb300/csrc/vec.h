@@ -29,6 +29,12 @@ struct CgScalars {
   float* beta_f;
   float* zmean_f;
   float* rmean_f;
+  // the partials (p, A p) left in the vector type by a deferred fused apply
+  // ([system][*apart_n]) or by the deferred dot kernel (one per segment block, apart_seg = 1),
+  // or nullptr: the step kernel then forms pAp and alpha itself
+  const double* apart;
+  const unsigned int* apart_n;
+  int apart_seg;
 };
 
 // Segments of a set of CG systems sharing vectors (see k_vec.cu): system s occupies

@@ -251,3 +251,25 @@ def test_mixed_matches_fp64(case):
     a.step(dt, 2)
     b.step(dt, 2)
     assert rel(a.get_velocity(), b.get_velocity()) < 1e-11
+
+
+@pytest.mark.parametrize("precision", [imex.FP64, imex.MIXED])
+def test_viscosity_change_between_steps(precision):
+    # the Helmholtz diagonal of a constant viscosity is kept between solves: a context whose
+    # viscosity changes between steps must step exactly like a new context with the new one
+    def make(nu):
+        c = imex.Context(3, 4, (2, 2, 3), [0, 0, 0], [TWO_PI] * 3, (1, 1, 1), precision=precision, tol=1e-13,
+                         maxit=50000)
+        c.set_viscosity_const(nu)
+        c.init_flow(imex.FLOW_TG3D, [0.0])
+        return c
+    a = make(0.05)
+    a.step(0.02, 1)
+    v1 = a.get_velocity()
+    a.set_viscosity_const(0.2)
+    a.set_state(a.time(), v1)
+    a.step(0.02, 1)
+    b = make(0.2)
+    b.set_state(a.time() - 0.02, v1)
+    b.step(0.02, 1)
+    assert rel(a.get_velocity(), b.get_velocity()) < 1e-11
