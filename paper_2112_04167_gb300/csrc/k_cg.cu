@@ -6,7 +6,11 @@
 // a batch) are segments of the same vectors.  A 1D grid of blocks covers them, each block
 // one chunk of SEG_CHUNK elements of one segment, so uneven segment lengths cost no idle
 // blocks.  Per-block partial sums are combined in block order (deterministic) by the last
-// block to finish; the per-system scalars never leave device memory.
+// block to finish; the per-system scalars never leave device memory.  The step length
+// alpha = (r, z) / (p, A p) is the exception: the operator apply (or the dot kernel) only
+// leaves its per-block partials of (p, A p), and every block of the step kernel adds those
+// of its system in the same fixed order -- identical in all blocks, and no completion
+// counter, fence or last-block sum at the end of the apply.
 //
 // Singular systems (project = 1; null space = the constants) run the projected iteration:
 // the residual r' = r - rho 1 (rho = mean r) and the preconditioned residual
@@ -189,8 +193,10 @@ __host__ __device__ constexpr int unroll_of(int vec) { return SEG_CHUNK / (vec *
 
 // x += alpha p, r -= alpha A p, and the partial sums of the new residual; the last block
 // forms the new scalars and the next direction coefficient beta = rz_new / rz
+// FP32: at least 5 blocks per SM, so that a 1.4 M-node system's 686 blocks run in one wave
+// of 152 SMs (4 per SM left 78 blocks for a second wave)
 template <typename T>
-__global__ void __launch_bounds__(CG_THREADS, sizeof(T) == 4 ? 4 : 2)
+__global__ void __launch_bounds__(CG_THREADS, sizeof(T) == 4 ? 5 : 2)
 seg_xr_kernel(T* __restrict__ x, T* __restrict__ r, const T* __restrict__ p, const T* __restrict__ Ap,
               const T* __restrict__ dinv, SegTable t, CgScalars sc, double* __restrict__ partial,
               unsigned int* __restrict__ counter, int maxit) {
@@ -242,32 +248,27 @@ seg_xr_kernel(T* __restrict__ x, T* __restrict__ r, const T* __restrict__ p, con
     int done_n = 0;
     if (al16(xs) && al16(rs) && al16(ps) && al16(aps) && al16(ds)) {
       const int nv = n / VN;
-      T rv[U][VN], av[U][VN], dv[U][VN], xv[U][VN], pv[U][VN];
-#pragma unroll
+      // one 16-byte group of each vector at a time (fewer registers: more resident blocks)
+#pragma unroll 1
       for (int u = 0; u < U; ++u) {
         const int v = threadIdx.x + u * CG_THREADS;
         if (v < nv) {
-          vload(rs + v * VN, rv[u]); vload(aps + v * VN, av[u]); vload(ds + v * VN, dv[u]);
-          vload(xs + v * VN, xv[u]); vload(ps + v * VN, pv[u]);
-        }
-      }
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const int v = threadIdx.x + u * CG_THREADS;
-        if (v < nv) {
+          T rv[VN], av[VN], dv[VN], xv[VN], pv[VN];
+          vload(rs + v * VN, rv); vload(aps + v * VN, av); vload(ds + v * VN, dv);
+          vload(xs + v * VN, xv); vload(ps + v * VN, pv);
 #pragma unroll
           for (int j = 0; j < VN; ++j) {
-            const T ri = rv[u][j] - a * av[u][j];
-            const T zi = ri * dv[u][j];
-            xv[u][j] += a * pv[u][j];
-            rv[u][j] = ri;
+            const T ri = rv[j] - a * av[j];
+            const T zi = ri * dv[j];
+            xv[j] += a * pv[j];
+            rv[j] = ri;
             acc[0] += ri * zi;
             acc[1] += ri * ri;
             acc[2] += zi;
             acc[3] += ri;
           }
-          vstore(xs + v * VN, xv[u]);
-          vstore(rs + v * VN, rv[u]);
+          vstore(xs + v * VN, xv);
+          vstore(rs + v * VN, rv);
         }
       }
       done_n = nv * VN;
