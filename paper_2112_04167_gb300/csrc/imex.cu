@@ -222,6 +222,10 @@ struct imex_ctx {
   double* kdiag = nullptr;
   bool kdiag_valid = false;
   double kdiag_nu = 0.0;
+  // K v_i of the last Helmholtz solution (in cz, from its final residual check), valid for
+  // the stage right-hand side that follows the solve without Dirichlet data (F_d1 = -M^-1 K v)
+  bool kx_ready = false;
+  const double* kx_for = nullptr;
   // instances of the mesh: one for a plain context; several for the union mesh of a batch
   // group, whose kernels see per-element geometry, viscosity, time step and time
   bool batched = false;
@@ -864,7 +868,7 @@ imex_status solve_poisson(imex_ctx* c, double* b, double* psi, long long* iters,
 
 // Helmholtz: (M + gamma A(nu)) x = rhs, d components; x: initial guess in, solution out.
 imex_status solve_helmholtz(imex_ctx* c, const double* rhs, double* x, const double* nu, double gamma,
-                            long long* iters, double* res) {
+                            long long* iters, double* res, bool keep_kx = false) {
   const size_t n = c->nv;
   const int d = c->d;
   // Jacobi diagonal of M + gamma A(nu)  (stored in cdiag + np region-free slot: use cdiag[np..])
@@ -902,13 +906,30 @@ imex_status solve_helmholtz(imex_ctx* c, const double* rhs, double* x, const dou
   convert_d2f(dg, fdg, n, c->st);
   const float* fnu = nullptr;
   if (nu) { convert_d2f(nu, c->fnu, n, c->st); fnu = c->fnu; }
-  auto op64 = [&](const double* xx, double* yy) { return apply_helm<double>(c, xx, yy, d, nu, gamma); };
+  // keep_kx: the FP64-class residual apply computes K x into cz and forms (M + gamma dt_e K) x
+  // elementwise, so that K of the solution is left for F_d1 of the same stage
+  auto op64 = [&](const double* xx, double* yy) -> imex_status {
+    if (!keep_kx) return apply_helm<double>(c, xx, yy, d, nu, gamma);
+    SipgArgs<double> a = sipg_args<double>(xx, c->cz, d, (long long)n, nu, nu_const(c), nullptr, 0.0, 1.0, 0);
+    a.ops = c->ops64_v;
+    vel_flags(c, a, false);
+    prof_mark(c, IMEX_PROF_HELMHOLTZ_F64, true);
+    const int rc = apply_dispatch<double>(c, c->gv, c->Nv, a);
+    prof_mark(c, IMEX_PROF_HELMHOLTZ_F64, false);
+    TRY(launch_check(c, rc, "sipg_apply(Kx)"));
+    kx_combine(yy, xx, c->mass_v, c->cz, gamma, c->batched ? c->edt : nullptr, ipow(c->Nv, d), n, d, 0, c->st);
+    return IMEX_OK;
+  };
   auto op32 = [&](const float* xx, float* yy) { return apply_helm<float>(c, xx, yy, d, fnu, gamma); };
   auto op32d = [&](const float* xx, float* yy, const CgScalars* dd) {
     return apply_helm<float>(c, xx, yy, d, fnu, gamma, dd);
   };
   TRY(pcg_mixed(c, c->segv, op64, op32, op32d, fnu == nullptr && !c->batched, rhs, x, fdg, tol, c->desc.maxit, false,
                 hkey, iters, res));
+  if (keep_kx) {
+    c->kx_ready = true;            // the last residual check applied K to the solution x
+    c->kx_for = x;
+  }
   return IMEX_OK;
 }
 
@@ -976,6 +997,9 @@ imex_status graddiv(imex_ctx* c, const double* v, const double* nu, double* fd3,
 imex_status stage_rhs(imex_ctx* c, double t, const double* v, const double* nu, const double* vb, double* E,
                       double* Fd1, double* Fd3, double* Fs) {
   const size_t nt = c->nv * c->d;
+  // K v left by the Helmholtz solve that produced v (same viscosity, no Dirichlet data)
+  const bool use_kx = c->kx_ready && c->kx_for == v && vb == nullptr;
+  c->kx_ready = false;
   // IMEX_MIXED_FAST applies the explicit operators (convection, F_d1) in FP32 from FP32
   // copies of v and the boundary data; the stage storage and every combination stay FP64
   const bool f32 = c->desc.precision == IMEX_MIXED_FAST;
@@ -1021,6 +1045,8 @@ imex_status stage_rhs(imex_ctx* c, double t, const double* v, const double* nu, 
     vel_flags(c, a, false);
     TRY(launch_check(c, sipg_apply<float>(c->gv, c->Nv, a, c->st), "sipg_apply(Fd1, f32)"));
     f2d(c->fp, Fd1, nt, c->st);
+  } else if (use_kx) {
+    kx_combine(Fd1, v, c->mass_v, c->cz, 0.0, nullptr, 1, c->nv, c->d, 1, c->st);
   } else {
     SipgArgs<double> a = sipg_args<double>(v, Fd1, c->d, (long long)c->nv, nu_ptr(c, nu), nu_const(c), vb, 0.0, -1.0,
                                            1);
@@ -1041,6 +1067,7 @@ imex_status stage_rhs(imex_ctx* c, double t, const double* v, const double* nu, 
 // scaled by the ratio of the two tau, is the initial guess.  The final projection (mode 2,
 // a small correction) starts from zero in its own buffer and leaves the stage potential.
 imex_status project(imex_ctx* c, const double* vin, const double* wdata, int mode, double* out, double tau = 0.0) {
+  c->kx_ready = false;
   // the mixed form evaluates the projection's divergence and gradient in float-float
   const bool ffa = c->desc.precision == IMEX_MIXED;
   DivArgs<double> da{vin, (long long)c->nv, wdata, mode, 1.0, c->bp};
@@ -1069,6 +1096,7 @@ imex_status project(imex_ctx* c, const double* vin, const double* wdata, int mod
 imex_status helmholtz_stage(imex_ctx* c, const double* gfield, const double* nu, double gamma, const double* vb,
                             double* vout) {
   const size_t nt = c->nv * c->d;
+  c->kx_ready = false;
   // rhs = M g + gamma r_b : r_b = -(A 0 - r_b(vb))
   diag_mul(c, c->tmp, gfield, c->mass_v, c->nv, c->d);
   if (vb) {
@@ -1085,7 +1113,10 @@ imex_status helmholtz_stage(imex_ctx* c, const double* gfield, const double* nu,
   if (vout != gfield) CK(cudaMemcpyAsync(vout, gfield, nt * sizeof(double), cudaMemcpyDeviceToDevice, c->st), "cp");
   double res = 0.0;
   // the rhs lives in c->tmp; pcg uses cr/cz/cp/cAp as work space
-  TRY(solve_helmholtz(c, c->tmp, vout, nu_ptr(c, nu), gamma, &c->stats.helmholtz_iters, &res));
+  // without Dirichlet data F_d1 of the solution is -M^-1 K v, which the mixed form's last
+  // residual check computes anyway
+  const bool keep_kx = vb == nullptr && c->desc.precision == IMEX_MIXED;
+  TRY(solve_helmholtz(c, c->tmp, vout, nu_ptr(c, nu), gamma, &c->stats.helmholtz_iters, &res, keep_kx));
   c->stats.helmholtz_solves++;
   c->stats.max_helmholtz_res = std::max(c->stats.max_helmholtz_res, res);
   return IMEX_OK;

@@ -247,6 +247,29 @@ void helm_diag(double* d, const double* m, const double* k, double gamma, const 
   IMEX_COUNTED(helm_diag_kernel<<<grid_for(n, 256), 256, 0, st>>>(d, m, k, gamma, edt, nd, n));
 }
 
+// Helmholtz operator and F_d1 from K x (the SIPG operator with unit factor applied to the d
+// components of x, stride n each): mode 0: y = m x + gamma dt_e K x (dt_e = edt[i / nd], or
+// 1 when edt is null); mode 1: y = -K x / m
+__global__ void kx_combine_kernel(double* __restrict__ y, const double* __restrict__ x, const double* __restrict__ m,
+                                  const double* __restrict__ kx, double gamma, const double* __restrict__ edt,
+                                  long long nd, size_t n, int nsys, int mode) {
+  const size_t tot = n * (size_t)nsys;
+  for (size_t j = blockIdx.x * (size_t)blockDim.x + threadIdx.x; j < tot; j += (size_t)gridDim.x * blockDim.x) {
+    const size_t i = j % n;
+    if (mode == 0) {
+      const double g = edt ? gamma * edt[i / (size_t)nd] : gamma;
+      y[j] = m[i] * x[j] + g * kx[j];
+    } else {
+      y[j] = -kx[j] / m[i];
+    }
+  }
+}
+void kx_combine(double* y, const double* x, const double* m, const double* kx, double gamma, const double* edt,
+                long long nd, size_t n, int nsys, int mode, cudaStream_t st) {
+  if (n == 0) return;
+  IMEX_COUNTED(kx_combine_kernel<<<grid_for(n * nsys, 256), 256, 0, st>>>(y, x, m, kx, gamma, edt, nd, n, nsys, mode));
+}
+
 template void reciprocal<double>(double*, size_t, cudaStream_t);
 template void reciprocal<float>(float*, size_t, cudaStream_t);
 

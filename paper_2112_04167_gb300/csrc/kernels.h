@@ -155,6 +155,10 @@ void axpy_f2d(double* y, const float* x, size_t n, cudaStream_t st);
 
 template <typename T>
 void reciprocal(T* d, size_t n, cudaStream_t st);
+// over the nsys components (stride n) of x and kx = K x: mode 0: y = m x + gamma dt_e kx;
+// mode 1: y = -kx / m  (dt_e = edt[i / nd], or 1 when edt is null)
+void kx_combine(double* y, const double* x, const double* m, const double* kx, double gamma, const double* edt,
+                long long nd, size_t n, int nsys, int mode, cudaStream_t st);
 // d = 1 / (m + gamma dt_e k) over n nodes, dt_e = edt[i / nd] (or 1 when edt is null)
 void helm_diag(double* d, const double* m, const double* k, double gamma, const double* edt, long long nd, size_t n,
                cudaStream_t st);
