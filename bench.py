@@ -530,8 +530,9 @@ def main():
     # ---- plain FP64 form on the same workload -----------------------------------
     fp64 = None
     if args.precision == "mixed" and args.fp64_steps > 0 and rank == 0:
+        # the same warm-up as the headline form, so that all forms are timed on the same steps
         c64 = make_ctx(imex, args, "fp64", stream.cuda_stream)
-        c64.step(args.dt, 1)
+        c64.step(args.dt, args.warmup)
         torch.cuda.synchronize()
         per64 = timed_steps(torch, c64, stream, args.dt, args.fp64_steps)
         s64 = c64.stats()
@@ -542,13 +543,13 @@ def main():
         import numpy as np
         v64 = c64.get_velocity()
         cm = make_ctx(imex, args, "mixed", stream.cuda_stream)
-        cm.step(args.dt, 1 + args.fp64_steps)
+        cm.step(args.dt, args.warmup + args.fp64_steps)
         vm = cm.get_velocity()
         fp64["mixed_vs_fp64_rel_l2"] = float(np.linalg.norm(vm - v64) / np.linalg.norm(v64))
-        fp64["compared_after_steps"] = 1 + args.fp64_steps
+        fp64["compared_after_steps"] = args.warmup + args.fp64_steps
         # IMEX_MIXED_FAST (FP32 explicit operators as well): speed and distance from FP64
         cf = make_ctx(imex, args, "fast", stream.cuda_stream)
-        cf.step(args.dt, 1)
+        cf.step(args.dt, args.warmup)
         torch.cuda.synchronize()
         perf = timed_steps(torch, cf, stream, args.dt, args.fp64_steps)
         vf = cf.get_velocity()
