@@ -398,6 +398,8 @@ SipgArgs<T> sipg_args(const T* x, T* y, int nsys, long long stride, const T* nu,
   a.cg_alpha = nullptr;
   a.cg_alpha_f = nullptr;
   a.cg_done = nullptr;
+  a.dot_defer = 0;
+  a.dot_nblk = nullptr;
   a.inst_nu = 0;
   a.inst_dt = 0;
   return a;

@@ -65,6 +65,16 @@ __device__ __forceinline__ void put_dot_partial(const SipgArgs<T>& a, int s, dou
   else a.dot_partial[i] = bs;
 }
 
+// In a CG loop (the fused form) the apply skips a system whose iteration has stopped
+// (converged, broken down or out of iterations: its flag is set by an earlier kernel), so
+// that the tail of a graph-replayed chunk of iterations costs no operator work
+template <typename T>
+__device__ __forceinline__ bool cg_system_stopped(const SipgArgs<T>& a, int s) {
+  if (!a.cg_done) return false;
+  pdl_wait();
+  return a.cg_done[s] != 0;
+}
+
 template <typename T>
 __device__ void fused_dot_finish(const SipgArgs<T>& a, double* red) {
   if (a.dot_defer) {
@@ -577,6 +587,10 @@ sipg3c_apply_kernel(Geom g, SipgArgs<T> a) {
     const T* gd = a.gdata ? a.gdata + (size_t)s * a.g_stride : nullptr;
     T* y = a.y + (size_t)s * a.sys_stride;
     if (s > 0) __syncthreads();
+    if (cg_system_stopped(a, s)) {            // its CG iteration has stopped: A p not needed
+      if (a.dot_out && threadIdx.x == 0) put_dot_partial(a, s, 0.0);
+      continue;
+    }
     T u[N];
     T dacc = T(0);
     T zt[2] = {T(0), T(0)}, zd[2] = {T(0), T(0)};
@@ -738,6 +752,10 @@ sipg2c_apply_kernel(Geom g, SipgArgs<T> a) {
     const T* gd = a.gdata ? a.gdata + (size_t)s * a.g_stride : nullptr;
     T* y = a.y + (size_t)s * a.sys_stride;
     if (s > 0) __syncthreads();
+    if (cg_system_stopped(a, s)) {            // its CG iteration has stopped: A p not needed
+      if (a.dot_out && threadIdx.x == 0) put_dot_partial(a, s, 0.0);
+      continue;
+    }
     T uo = T(0);
     T dacc = T(0);
     if (valid) {
@@ -857,6 +875,10 @@ sipg2p_apply_kernel(Geom g, SipgArgs<T> a) {
     const T* x = a.x + (size_t)s * a.sys_stride;
     T* y = a.y + (size_t)s * a.sys_stride;
     if (s > 0) __syncthreads();
+    if (cg_system_stopped(a, s)) {            // its CG iteration has stopped: A p not needed
+      if (a.dot_out && threadIdx.x == 0) put_dot_partial(a, s, 0.0);
+      continue;
+    }
     T uo = T(0);
     T dacc = T(0);
     if (valid) {
@@ -945,6 +967,10 @@ sipg2l_apply_kernel(Geom g, SipgArgs<T> a) {
     const T* x = a.x + (size_t)s * a.sys_stride;
     T* y = a.y + (size_t)s * a.sys_stride;
     if (s > 0) __syncthreads();
+    if (cg_system_stopped(a, s)) {            // its CG iteration has stopped: A p not needed
+      if (a.dot_out && threadIdx.x == 0) put_dot_partial(a, s, 0.0);
+      continue;
+    }
     // the block's elements, contiguous: coalesced loads into the row tiles
     for (int i = threadIdx.x; i < nvalid * NN; i += blockDim.x) {
       const int q = i / NN, r = i - q * NN;
@@ -1349,6 +1375,10 @@ sipg3p_apply_kernel(Geom g, SipgArgs<TS> a) {
   pdl_trigger();
   for (int s = 0; s < a.nsys; ++s) {
     if (s > 0) __syncthreads();
+    if (cg_system_stopped(a, s)) {            // its CG iteration has stopped: A p not needed
+      if (a.dot_out && threadIdx.x == 0) put_dot_partial(a, s, 0.0);
+      continue;
+    }
     const T dacc = sipg3l_group<T, N, TS>(g, a, a.x + (size_t)s * a.sys_stride, a.y + (size_t)s * a.sys_stride,
                                           blockIdx.x);
     if (a.dot_out) {
