@@ -400,6 +400,8 @@ SipgArgs<T> sipg_args(const T* x, T* y, int nsys, long long stride, const T* nu,
   a.cg_done = nullptr;
   a.dot_defer = 0;
   a.dot_nblk = nullptr;
+  a.done_flags = nullptr;
+  a.done_ninst = 0;
   a.inst_nu = 0;
   a.inst_dt = 0;
   return a;
@@ -434,6 +436,16 @@ void fuse_cg(imex_ctx* c, SipgArgs<T>& a, const CgScalars* cg) {
   }
 }
 
+// batch groups in a CG loop: the operator skips the elements whose system has stopped (the
+// done flags of the CG scalars; the systems of a group are its instances, times d for the
+// velocity components)
+template <typename T>
+void skip_stopped_elems(imex_ctx* c, SipgArgs<T>& a, bool on) {
+  if (!on || !c->batched) return;
+  a.done_flags = c->cg_i;
+  a.done_ninst = (int)c->inst.size();
+}
+
 // batch groups: velocity operators take the constant viscosity of each element's instance
 // and, where their scale is a multiple of the time step, the instance's step
 template <typename T>
@@ -443,12 +455,18 @@ void vel_flags(const imex_ctx* c, SipgArgs<T>& a, bool dt_scaled) {
   a.inst_dt = dt_scaled ? 1 : 0;
 }
 
+// the mixed forms evaluate their FP64-class operators (residual checks, F_d1, projection,
+// grad-div; IMEX_MIXED also the convection) in float-float arithmetic on FP64 fields
+bool ff_class(const imex_ctx* c) {
+  return c->desc.precision == IMEX_MIXED || c->desc.precision == IMEX_MIXED_FAST;
+}
+
 // SIPG apply: the FP64 applies of the mixed form (residual replacements, explicit F_d1) use
 // float-float arithmetic on FP64 fields where that kernel exists (periodic 3D, constant
 // viscosity), plain FP64 otherwise; the FP64 form always uses FP64 arithmetic
 template <typename T>
 int apply_dispatch(imex_ctx* c, const Geom& g, int N, const SipgArgs<T>& a) {
-  if (sizeof(T) == 8 && c->desc.precision == IMEX_MIXED) {
+  if (sizeof(T) == 8 && ff_class(c)) {
     const int rc = sipg_apply_ff(g, N, reinterpret_cast<const SipgArgs<double>&>(a), c->st);
     if (rc == 0) return 0;
   }
@@ -457,12 +475,14 @@ int apply_dispatch(imex_ctx* c, const Geom& g, int N, const SipgArgs<T>& a) {
 
 // the pressure operator L psi (pressure space), T = double / float
 template <typename T>
-imex_status apply_pressure(imex_ctx* c, const T* x, T* y, T* vtmp, const CgScalars* cg = nullptr) {
+imex_status apply_pressure(imex_ctx* c, const T* x, T* y, T* vtmp, const CgScalars* cg = nullptr,
+                           bool skip_stopped = false) {
   const int cls = sizeof(T) == 4 ? IMEX_PROF_PRESSURE_F32 : IMEX_PROF_PRESSURE_F64;
   if (c->desc.poisson == IMEX_POISSON_SIPG) {
     SipgArgs<T> a = sipg_args<T>(x, y, 1, (long long)c->np, nullptr, 1.0, nullptr, 0.0, 1.0, 0);
     a.ops = line_ops<T>(c, false);
     fuse_cg(c, a, cg);
+    skip_stopped_elems(c, a, skip_stopped);
     prof_mark(c, cls, true);
     const int rc = apply_dispatch<T>(c, c->gp, c->Np, a);
     prof_mark(c, cls, false);
@@ -478,12 +498,13 @@ imex_status apply_pressure(imex_ctx* c, const T* x, T* y, T* vtmp, const CgScala
 // velocity Helmholtz operator (M + gamma A(nu)), nsys components
 template <typename T>
 imex_status apply_helm(imex_ctx* c, const T* x, T* y, int nsys, const T* nu, double gamma,
-                       const CgScalars* cg = nullptr) {
+                       const CgScalars* cg = nullptr, bool skip_stopped = false) {
   const int cls = sizeof(T) == 4 ? IMEX_PROF_HELMHOLTZ_F32 : IMEX_PROF_HELMHOLTZ_F64;
   SipgArgs<T> a = sipg_args<T>(x, y, nsys, (long long)c->nv, nu, nu_const(c), nullptr, 1.0, gamma, 0);
   a.ops = line_ops<T>(c, true);
   vel_flags(c, a, true);
   fuse_cg(c, a, cg);
+  skip_stopped_elems(c, a, skip_stopped);
   prof_mark(c, cls, true);
   const int rc = apply_dispatch<T>(c, c->gv, c->Nv, a);
   prof_mark(c, cls, false);
@@ -858,7 +879,8 @@ imex_status solve_poisson(imex_ctx* c, double* b, double* psi, long long* iters,
   }
   // mixed: FP32 operator and preconditioner, FP64 iterate and residual with reliable updates
   auto op64 = [&](const double* x, double* y) { return apply_pressure<double>(c, x, y, c->tmp); };
-  auto op32 = [&](const float* x, float* y) { return apply_pressure<float>(c, x, y, c->fvtmp); };
+  // (the FP32 operator runs in the CG loop only: a batch group skips its stopped instances)
+  auto op32 = [&](const float* x, float* y) { return apply_pressure<float>(c, x, y, c->fvtmp, nullptr, true); };
   auto op32d = [&](const float* x, float* y, const CgScalars* d) {
     return apply_pressure<float>(c, x, y, c->fvtmp, d);
   };
@@ -922,7 +944,7 @@ imex_status solve_helmholtz(imex_ctx* c, const double* rhs, double* x, const dou
     kx_combine(yy, xx, c->mass_v, c->cz, gamma, c->batched ? c->edt : nullptr, ipow(c->Nv, d), n, d, 0, c->st);
     return IMEX_OK;
   };
-  auto op32 = [&](const float* xx, float* yy) { return apply_helm<float>(c, xx, yy, d, fnu, gamma); };
+  auto op32 = [&](const float* xx, float* yy) { return apply_helm<float>(c, xx, yy, d, fnu, gamma, nullptr, true); };
   auto op32d = [&](const float* xx, float* yy, const CgScalars* dd) {
     return apply_helm<float>(c, xx, yy, d, fnu, gamma, dd);
   };
@@ -974,7 +996,7 @@ const double* nu_ptr(const imex_ctx* c, const double* nu) { return variable_nu(c
 imex_status graddiv(imex_ctx* c, const double* v, const double* nu, double* fd3, double* fd2_acc) {
   // the mixed form evaluates the derivatives in float-float
   auto deriv = [&](const DerivArgs<double>& x) {
-    return c->desc.precision == IMEX_MIXED ? dg_deriv_ff(c->gv, c->Nv, x, c->st) : dg_deriv<double>(c->gv, c->Nv, x, c->st);
+    return ff_class(c) ? dg_deriv_ff(c->gv, c->Nv, x, c->st) : dg_deriv<double>(c->gv, c->Nv, x, c->st);
   };
   DerivArgs<double> a{};
   a.op = 0; a.in = v; a.stride = (long long)c->nv; a.nu = nu_ptr(c, nu); a.nu0 = nu_const(c); a.out = c->phi;
@@ -1071,7 +1093,7 @@ imex_status stage_rhs(imex_ctx* c, double t, const double* v, const double* nu, 
 imex_status project(imex_ctx* c, const double* vin, const double* wdata, int mode, double* out, double tau = 0.0) {
   c->kx_ready = false;
   // the mixed form evaluates the projection's divergence and gradient in float-float
-  const bool ffa = c->desc.precision == IMEX_MIXED;
+  const bool ffa = ff_class(c);
   DivArgs<double> da{vin, (long long)c->nv, wdata, mode, 1.0, c->bp};
   TRY(launch_check(c, ffa ? dg_div_ff(c->gv, c->Nv, da, c->st) : dg_div<double>(c->gv, c->Nv, da, c->st), "dg_div"));
   double* psi = c->psi;

@@ -75,6 +75,14 @@ __device__ __forceinline__ bool cg_system_stopped(const SipgArgs<T>& a, int s) {
   return a.cg_done[s] != 0;
 }
 
+// In a batch group's CG loop the apply skips the elements whose system has stopped (call
+// after pdl_wait: the flags are written by earlier kernels)
+template <typename T>
+__device__ __forceinline__ bool elem_stopped(const SipgArgs<T>& a, const Geom& g, int e, int s) {
+  if (!a.done_flags || !g.elem_inst) return false;
+  return a.done_flags[s * a.done_ninst + g.elem_inst[e]] != 0;
+}
+
 template <typename T>
 __device__ void fused_dot_finish(const SipgArgs<T>& a, double* red) {
   if (a.dot_defer) {
@@ -971,6 +979,8 @@ sipg2l_apply_kernel(Geom g, SipgArgs<T> a) {
       if (a.dot_out && threadIdx.x == 0) put_dot_partial(a, s, 0.0);
       continue;
     }
+    pdl_wait();
+    const bool live = valid && !elem_stopped(a, g, e, s);
     // the block's elements, contiguous: coalesced loads into the row tiles
     for (int i = threadIdx.x; i < nvalid * NN; i += blockDim.x) {
       const int q = i / NN, r = i - q * NN;
@@ -978,7 +988,7 @@ sipg2l_apply_kernel(Geom g, SipgArgs<T> a) {
     }
     __syncthreads();
     // pass y: column x = ta of element le
-    if (valid) {
+    if (live) {
       T v[N], vl[N], vr[N];
 #pragma unroll
       for (int j = 0; j < N; ++j) v[j] = tile[le][j][ta];
@@ -1002,7 +1012,7 @@ sipg2l_apply_kernel(Geom g, SipgArgs<T> a) {
     __syncthreads();
     // pass x: row y = ta of element le, and the result
     T dacc = T(0);
-    if (valid) {
+    if (live) {
       T v[NP], vl[N], vr[N];
       using V = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
       const V* rv = reinterpret_cast<const V*>(&tile[le][ta][0]);
@@ -1241,7 +1251,7 @@ __device__ __forceinline__ LineFaces<T> line_faces(const ConstLine<T>& L, const 
 
 template <typename T, int N, typename TS = T>
 __device__ __forceinline__ T sipg3l_group(const Geom& g, const SipgArgs<TS>& a, const TS* __restrict__ x,
-                                          TS* __restrict__ y, int grp) {
+                                          TS* __restrict__ y, int grp, int sys = 0) {
   using S = Sipg3lShape<T, N>;
   constexpr int NN = S::NN, ND = S::ND, EPB = S::EPB, NP = S::NP, TILE = S::TILE, VEC = S::VEC;
   // FP32 up to N = 8: all neighbour lines are loaded before the first pass, so that their
@@ -1290,7 +1300,8 @@ __device__ __forceinline__ T sipg3l_group(const Geom& g, const SipgArgs<TS>& a, 
   for (int k = 0; k < N; ++k) u[k] = T(0);
   LineFaces<T> fz{}, fy{}, fx{};
   pdl_wait();
-  if (valid) {
+  const bool live = valid && !elem_stopped(a, g, e, sys);
+  if (live) {
 #pragma unroll
     for (int k = 0; k < N; ++k) u[k] = T(x[eb + k * NN + t]);
     if (HOIST) {
@@ -1302,7 +1313,7 @@ __device__ __forceinline__ T sipg3l_group(const Geom& g, const SipgArgs<TS>& a, 
     for (int k = 0; k < N; ++k) mt[(k * N + tb) * NP + ta] = u[k];
   }
   // pass z: line (x = ta, y = tb) along z
-  if (valid) {
+  if (live) {
     if (!HOIST) fz = line_faces<T, N>(L, zl, zr, NN);
     const T wt = (T(0.5) * hx * L.w[ta]) * (T(0.5) * hy * L.w[tb]) * ihz;
 #pragma unroll
@@ -1315,7 +1326,7 @@ __device__ __forceinline__ T sipg3l_group(const Geom& g, const SipgArgs<TS>& a, 
   }
   __syncthreads();
   // pass y: line (x = ta, z = tb) along y
-  if (valid) {
+  if (live) {
     T v[N];
 #pragma unroll
     for (int j = 0; j < N; ++j) v[j] = mt[(tb * N + j) * NP + ta];
@@ -1332,7 +1343,7 @@ __device__ __forceinline__ T sipg3l_group(const Geom& g, const SipgArgs<TS>& a, 
   __syncthreads();
   // pass x: line (y = ta, z = tb) along x, and the result
   T dacc = T(0);
-  if (valid) {
+  if (live) {
     T v[NP];
     using V = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
     const V* rv = reinterpret_cast<const V*>(mt + (tb * N + ta) * NP);
@@ -1380,7 +1391,7 @@ sipg3p_apply_kernel(Geom g, SipgArgs<TS> a) {
       continue;
     }
     const T dacc = sipg3l_group<T, N, TS>(g, a, a.x + (size_t)s * a.sys_stride, a.y + (size_t)s * a.sys_stride,
-                                          blockIdx.x);
+                                          blockIdx.x, s);
     if (a.dot_out) {
       const double bs = block_sum_any_t<T>(dacc, red);
       if (threadIdx.x == 0) put_dot_partial(a, s, bs);

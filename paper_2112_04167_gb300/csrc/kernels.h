@@ -37,6 +37,10 @@ struct SipgArgs {
   // completion counter and no last-block reduction at the end of the apply
   int dot_defer;
   unsigned int* dot_nblk;
+  // batch groups in a CG loop: elements whose system has stopped are skipped; system s of an
+  // element of instance i is segment s * done_ninst + i of done_flags (nullptr: no skipping)
+  const int* done_flags;
+  int done_ninst;
   // batched meshes: take the constant viscosity from each element's instance instead of nu0
   // (inst_nu), and multiply beta by the instance's time step (inst_dt)
   int inst_nu;
