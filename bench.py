@@ -489,7 +489,7 @@ def main():
     elif dom in bytes_per and prof[dom]["launches"]:
         # DRAM bytes per launch from the ncu capture summarised in
         # profiles/sipg3p_apply_f32_tg3d_16cube_p7.md (this workload, this kernel version)
-        traffic = {"sipg_pressure_f32": 5657856}.get(dom) if args.nelem == 16 and args.P == 7 else None
+        traffic = {"sipg_pressure_f32": 5660928}.get(dom) if args.nelem == 16 and args.P == 7 else None
         avg_s = prof[dom]["avg_us"] * 1e-6
         ach = bytes_per[dom] / avg_s / 1e9
         roof = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": hbm, "unit": "GB/s",
