@@ -22,11 +22,13 @@
 //   mean(D^{-1} r') = (S_z - rho sum D^{-1}) / n,
 // and the direction update stores r' back, so the drift never accumulates.
 //
-// Data movement: every kernel streams its vectors with 16-byte loads, all of a thread's loads
-// issued before the arithmetic (the kernels are bound by bytes in flight, not by issue), and
-// falls back to scalar accesses for chunks whose addresses are not 16-byte aligned.  FP32
-// instances accumulate per thread and per warp in FP32 and switch to FP64 at the per-warp
-// level (GB300 executes FP64 at a small fraction of the FP32 rate).
+// Data movement: every kernel streams its vectors with 16-byte loads (the direction kernel
+// issues all of a thread's loads before the arithmetic; the step kernel, with five input
+// vectors, one 16-byte group of each at a time, which keeps its register count low enough
+// for one wave of blocks), and falls back to scalar accesses for chunks whose addresses are
+// not 16-byte aligned.  FP32 instances accumulate per thread and per warp in FP32 and
+// switch to FP64 at the per-warp level (GB300 executes FP64 at a small fraction of the FP32
+// rate).
 #include <cstdint>
 #include <type_traits>
 
