@@ -54,9 +54,7 @@ __device__ __forceinline__ double block_sum_any_t(T v, double* red_storage) {
   return s;
 }
 
-// Fused CG dot: each block has left its partial per system in a.dot_partial; the last block
-// to finish adds the partials in block order and writes a.dot_out, then resets the counter.
-// a block's partial of the fused dot; the deferred form stores it in the vector type (the
+// A block's partial of the fused CG dot; the deferred form stores it in the vector type (the
 // block sums are formed in that type), which the step kernel then adds
 template <typename T>
 __device__ __forceinline__ void put_dot_partial(const SipgArgs<T>& a, int s, double bs) {
@@ -83,6 +81,10 @@ __device__ __forceinline__ bool elem_stopped(const SipgArgs<T>& a, const Geom& g
   return a.done_flags[s * a.done_ninst + g.elem_inst[e]] != 0;
 }
 
+// Fused CG dot: each block has left its partial per system in a.dot_partial; the last block
+// to finish adds the partials in block order and writes a.dot_out and the step length, then
+// resets the counter.  The deferred form only records the number of blocks (in *dot_nblk)
+// for the step kernel, which adds the partials itself.
 template <typename T>
 __device__ void fused_dot_finish(const SipgArgs<T>& a, double* red) {
   if (a.dot_defer) {
