@@ -851,88 +851,6 @@ template <> __device__ __forceinline__ const ConstLine<ff>& cline<ff>(int N) { r
 template <> __device__ __forceinline__ const ConstLine<float>& cline<float>(int N) { return c_line32[N]; }
 template <> __device__ __forceinline__ const ConstLine<double>& cline<double>(int N) { return c_line64[N]; }
 
-// 2D periodic constant-viscosity path: one thread per node, the unit-size line operators in
-// constant memory (every face interior), scaled per element as in 3D.
-template <typename T, int N>
-__global__ void __launch_bounds__(Sipg2cShape<N>::THREADS)
-sipg2p_apply_kernel(Geom g, SipgArgs<T> a) {
-  using S = Sipg2cShape<N>;
-  constexpr int NN = S::NN, EPB = S::EPB;
-  __shared__ T su[EPB][NN];
-  __shared__ T sf[EPB][8][N];
-  __shared__ int snb[EPB][4];
-  __shared__ double red[S::THREADS];
-  const ConstLine<T>& L = cline<T>(N);
-  const int le = threadIdx.x / NN;
-  const int t = threadIdx.x - le * NN;
-  const int i0 = t % N, i1 = t / N;
-  const int e = blockIdx.x * EPB + le;
-  const bool valid = e < g.ne;
-  int el = 0;
-  Geom gl = g;
-  if (valid) gl = local_geom(g, e, el);
-  int ec[3] = {0, 0, 0};
-  if (valid) elem_coords(gl, el, ec);
-  if (valid && t < 4) snb[le][t] = neighbor(gl, ec, t >> 1, (t & 1) ? 1 : -1);
-  __syncthreads();
-  const T hx = geom_h<T>(gl, 0), hy = geom_h<T>(gl, 1);
-  const T ihx = T(1) / hx, ihy = T(1) / hy;
-  const T wx = T(0.5) * hx * L.w[i0], wy = T(0.5) * hy * L.w[i1];
-  const T W = wx * wy;
-  const T scale = sipg_beta(a, gl) * sipg_nu0(a, gl);
-  const size_t ebase = (size_t)e * NN;
-  for (int s = 0; s < a.nsys; ++s) {
-    const T* x = a.x + (size_t)s * a.sys_stride;
-    T* y = a.y + (size_t)s * a.sys_stride;
-    if (s > 0) __syncthreads();
-    if (cg_system_stopped(a, s)) {            // its CG iteration has stopped: A p not needed
-      if (a.dot_out && threadIdx.x == 0) put_dot_partial(a, s, 0.0);
-      continue;
-    }
-    T uo = T(0);
-    T dacc = T(0);
-    if (valid) {
-      uo = x[ebase + t];
-      su[le][t] = uo;
-      for (int q = t; q < 4 * N; q += NN) {      // face fi = q / N, face node c = q % N
-        const int fi = q / N, c = q % N, dir = fi >> 1, side = fi & 1;
-        const T* line = x + (size_t)snb[le][fi] * NN + (dir == 0 ? c * N : c);
-        const int stride = dir == 0 ? 1 : N;
-        T dv = T(0), tr = T(0);
-#pragma unroll
-        for (int j = 0; j < N; ++j) {
-          const T v = line[j * stride];
-          dv += (side ? L.dnR[j] : L.dnL[j]) * v;
-          if (j == (side ? 0 : N - 1)) tr = v;
-        }
-        sf[le][2 * fi][c] = tr;
-        sf[le][2 * fi + 1][c] = dv;
-      }
-    }
-    __syncthreads();
-    if (valid) {
-      T yx = L.ctrL[i0] * sf[le][0][i1] + L.cdnL[i0] * sf[le][1][i1] + L.ctrR[i0] * sf[le][2][i1] +
-             L.cdnR[i0] * sf[le][3][i1];
-      T yy = L.ctrL[i1] * sf[le][4][i0] + L.cdnL[i1] * sf[le][5][i0] + L.ctrR[i1] * sf[le][6][i0] +
-             L.cdnR[i1] * sf[le][7][i0];
-#pragma unroll
-      for (int j = 0; j < N; ++j) {
-        yx += L.A[i0 * N + j] * su[le][i1 * N + j];
-        yy += L.A[i1 * N + j] * su[le][j * N + i0];
-      }
-      T out = a.alpha * W * uo + scale * (wy * ihx * yx + wx * ihy * yy);
-      if (a.minv) out /= W;
-      y[ebase + t] = out;
-      dacc = uo * out;
-    }
-    if (a.dot_out) {
-      const double bs = block_sum_any_t<T>(dacc, red);
-      if (threadIdx.x == 0) put_dot_partial(a, s, bs);
-    }
-  }
-  if (a.dot_out) fused_dot_finish(a, red);
-}
-
 // 2D periodic line-owner apply: two passes (y, then x), in each a thread owns one whole line
 // of an element; the block's elements are contiguous in memory and are staged into shared
 // memory with fully coalesced loads.  Many elements per block keep the grid within about
