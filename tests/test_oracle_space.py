@@ -272,3 +272,79 @@ def test_sipg_single_element_periodic_direction():
     y1 = dg.sipg_matrix(m1, N, nu1, True) @ u1
     y2 = dg.sipg_matrix(m2, N, np.concatenate([nu1, nu1]), True) @ np.concatenate([u1, u1])
     assert np.abs(y2[:32] - y1).max() < 1e-12 and np.abs(y2[32:] - y1).max() < 1e-12
+
+
+# ------------------------------------------------------ locality of the operators
+# The full-size GPU parity tests compare sampled elements of a large mesh with the same
+# elements of a small patch of their neighbours; this pins that reduction on meshes the
+# oracle assembles whole: every operator's output on an element depends only on the element
+# and its face neighbours (with the same fields and element sizes).
+def _rel(a, b):
+    return np.linalg.norm(np.ravel(a) - np.ravel(b)) / np.linalg.norm(np.ravel(b))
+
+
+def test_operator_locality_clipped_patches_2d():
+    # Dirichlet unit square: 3 x 3 patches clipped at the domain boundary keep its sides
+    ne, P = 6, 3
+    N, h = P + 1, 1.0 / 6
+    mesh = dg.Mesh(2, P, (ne, ne), [0, 0], [1, 1], (False, False))
+    nv, rng = ne * ne * N * N, np.random.default_rng(7)
+    x, g = rng.standard_normal(nv), rng.standard_normal(nv)
+    nu = 0.5 + rng.random(nv)
+    v, vb, w = (rng.standard_normal(2 * nv) for _ in range(3))
+    psi = rng.standard_normal(ne * ne * P * P)
+    B = dg.div_matrix(mesh, N, P)
+    full = {
+        "sipg": (dg.sipg_matrix(mesh, N, nu) @ x - dg.sipg_dirichlet_rhs(mesh, N, nu, g)).reshape(ne * ne, -1),
+        "conv": dg.Convection(mesh)(v, vb).reshape(2, ne * ne, -1),
+        "div": (B @ v - dg.div_boundary_vector(mesh, N, P, w)).reshape(ne * ne, -1),
+        "grad": ((B.T @ psi).reshape(2, -1) / dg.mass_diag(mesh, N)[None, :]).reshape(2, ne * ne, -1),
+    }
+    for ec in [(0, 0), (5, 5), (0, 3), (2, 3), (5, 1)]:
+        x0, x1 = max(ec[0] - 1, 0), min(ec[0] + 1, ne - 1)
+        y0, y1 = max(ec[1] - 1, 0), min(ec[1] + 1, ne - 1)
+        nx, ny = x1 - x0 + 1, y1 - y0 + 1
+        pm = dg.Mesh(2, P, (nx, ny), [x0 * h, y0 * h], [(x1 + 1) * h, (y1 + 1) * h], (False, False))
+        idx = [i + ne * j for j in range(y0, y1 + 1) for i in range(x0, x1 + 1)]
+        c = (ec[0] - x0) + nx * (ec[1] - y0)
+        e = idx[c]
+        el = lambda a: a.reshape(ne * ne, -1)[idx].ravel()
+        vl = lambda a: a.reshape(2, ne * ne, -1)[:, idx].ravel()
+        sip = dg.sipg_matrix(pm, N, el(nu)) @ el(x) - dg.sipg_dirichlet_rhs(pm, N, el(nu), el(g))
+        assert _rel(full["sipg"][e], sip.reshape(len(idx), -1)[c]) < 1e-13
+        cv = dg.Convection(pm)(vl(v), vl(vb)).reshape(2, len(idx), -1)[:, c]
+        assert _rel(full["conv"][:, e], cv) < 1e-13
+        Bp = dg.div_matrix(pm, N, P)
+        dv = (Bp @ vl(v) - dg.div_boundary_vector(pm, N, P, vl(w))).reshape(len(idx), -1)[c]
+        assert _rel(full["div"][e], dv) < 1e-13
+        gr = ((Bp.T @ psi.reshape(ne * ne, -1)[idx].ravel()).reshape(2, -1) /
+              dg.mass_diag(pm, N)[None, :]).reshape(2, len(idx), -1)[:, c]
+        assert _rel(full["grad"][:, e], gr) < 1e-13
+
+
+def test_operator_locality_periodic_patch_3d():
+    # periodic box: the centre of a periodic 3 x 3 x 3 patch of the same element size sees
+    # the same neighbours as the element of the large mesh (no wrap reaches it)
+    ne, P = 4, 2
+    N, L = P + 1, 2 * np.pi
+    h = L / ne
+    mesh = dg.Mesh(3, P, (ne, ne, ne), [0, 0, 0], [L] * 3, (True, True, True))
+    nd, rng = N ** 3, np.random.default_rng(8)
+    x = rng.standard_normal(ne ** 3 * nd)
+    v = rng.standard_normal(3 * ne ** 3 * nd)
+    xp = rng.standard_normal(ne ** 3 * P ** 3)
+    A = dg.sipg_matrix(mesh, N, 0.3) @ x
+    Lp = dg.sipg_matrix(mesh, P, 1.0, dirichlet=False) @ xp
+    cv = dg.Convection(mesh)(v, None).reshape(3, ne ** 3, -1)
+    pm = dg.Mesh(3, P, (3, 3, 3), [0, 0, 0], [3 * h] * 3, (True, True, True))
+    for ec in [(0, 0, 0), (3, 1, 2), (2, 3, 3)]:
+        idx = [((ec[0] + dx) % ne) + ne * (((ec[1] + dy) % ne) + ne * ((ec[2] + dz) % ne))
+               for dz in (-1, 0, 1) for dy in (-1, 0, 1) for dx in (-1, 0, 1)]
+        e = idx[13]
+        xs = x.reshape(ne ** 3, -1)[idx].ravel()
+        assert _rel(A.reshape(ne ** 3, -1)[e], (dg.sipg_matrix(pm, N, 0.3) @ xs).reshape(27, -1)[13]) < 1e-13
+        xps = xp.reshape(ne ** 3, -1)[idx].ravel()
+        ref = (dg.sipg_matrix(pm, P, 1.0, dirichlet=False) @ xps).reshape(27, -1)[13]
+        assert _rel(Lp.reshape(ne ** 3, -1)[e], ref) < 1e-13
+        vs = v.reshape(3, ne ** 3, -1)[:, idx].ravel()
+        assert _rel(cv[:, e], dg.Convection(pm)(vs, None).reshape(3, 27, -1)[:, 13]) < 1e-13
