@@ -62,6 +62,11 @@ enum { IMEX_NU_CONST = 0, IMEX_NU_VARXYT = 1, IMEX_NU_VELOCITY = 2, IMEX_NU_FIEL
 enum { IMEX_FORCE_NONE = 0, IMEX_FORCE_TGTRAVEL_VARNU = 1 };
 /* operator spaces of imex_op_sipg */
 enum { IMEX_SPACE_VELOCITY = 0, IMEX_SPACE_PRESSURE = 1 };
+/* arithmetic of the operator-level entry points (argument `arith`): FP64 kernels; FP32
+   kernels on inputs rounded to FP32 (the inner CG iterations of IMEX_MIXED and the explicit
+   operators of IMEX_MIXED_FAST); float-float kernels on FP64 fields (the FP64-class operators
+   of IMEX_MIXED).  Results are always returned in FP64.  IMEX_ARITH_FP32 equals IMEX_MIXED. */
+enum { IMEX_ARITH_FP64 = 0, IMEX_ARITH_FP32 = 1, IMEX_ARITH_FF = 3 };
 
 typedef struct {
   int dim;              /* 2 or 3 */
@@ -142,24 +147,29 @@ imex_status imex_get_stats(const imex_ctx* ctx, imex_stats* out);
    space: IMEX_SPACE_VELOCITY (degree P, Dirichlet faces on non-periodic sides, nsys
    components) or IMEX_SPACE_PRESSURE (degree P-1, nu = 1, Neumann faces, nsys = 1).
    nu: nodal viscosity (velocity space) or NULL for the context's constant viscosity.
-   g: Dirichlet data, nsys blocks, or NULL for homogeneous data.  precision: IMEX_FP64, or
-   IMEX_MIXED to run the FP32 kernel on rounded inputs (results returned in FP64). */
+   g: Dirichlet data, nsys blocks, or NULL for homogeneous data.  arith: IMEX_ARITH_* (the
+   float-float kernel exists for the periodic 3D constant-viscosity operator only: IMEX_EINVAL
+   for any other case). */
 imex_status imex_op_sipg(imex_ctx* ctx, int space, const double* x, double* y, int nsys, double alpha,
-                         double beta, const double* nu, const double* g, int minv, int precision,
+                         double beta, const double* nu, const double* g, int minv, int arith,
                          int on_device);
 /* diagonal of alpha M + beta A(nu) (the Jacobi preconditioner), one block */
 imex_status imex_op_sipg_diag(imex_ctx* ctx, int space, double* y, double alpha, double beta,
                               const double* nu, int on_device);
+/* The four operators below take `arith` = IMEX_ARITH_FP64 or IMEX_ARITH_FF (float-float on
+   FP64 fields, the form IMEX_MIXED steps with); imex_op_conv also IMEX_ARITH_FP32 (the
+   convection of IMEX_MIXED_FAST).  Other values: IMEX_EINVAL. */
 /* b = B v - int_{dOmega} (n . w) q: mode 0 no boundary term, 1 w = wdata, 2 w = v (trace) */
 imex_status imex_op_div(imex_ctx* ctx, const double* v, const double* wdata, int mode, double* b,
-                        int on_device);
+                        int arith, int on_device);
 /* out = M^{-1} B^T psi (DG gradient of a pressure field, d blocks) */
-imex_status imex_op_grad(imex_ctx* ctx, const double* psi, double* out, int on_device);
+imex_status imex_op_grad(imex_ctx* ctx, const double* psi, double* out, int arith, int on_device);
 /* out = F_c(v) = -div(v v) with LLF flux; vb: Dirichlet data or NULL */
-imex_status imex_op_conv(imex_ctx* ctx, const double* v, const double* vb, double* out, int on_device);
+imex_status imex_op_conv(imex_ctx* ctx, const double* v, const double* vb, double* out, int arith,
+                         int on_device);
 /* out = F_d3 = -grad(nu div v) and, if out2 != NULL, out2 = F_d2 = div(nu (grad v)^T) */
 imex_status imex_op_graddiv(imex_ctx* ctx, const double* v, const double* nu, double* out_fd3,
-                            double* out_fd2, int on_device);
+                            double* out_fd2, int arith, int on_device);
 /* Poisson solve L psi = b - mean(b) with the context's pressure operator; psi mean-free */
 imex_status imex_solve_poisson(imex_ctx* ctx, const double* b, double* psi, int on_device);
 /* Helmholtz solve (M + gamma A(nu)) v = M g + gamma r_b(nu, vb) for all d components */
@@ -293,6 +303,10 @@ void imex_server_destroy(imex_server* sv);
 const char* imex_server_last_error(const imex_server* sv);
 /* queue a request (copied); id: its handle.  IMEX_EINVAL for an invalid mesh or model. */
 imex_status imex_server_submit(imex_server* sv, const imex_request* r, long long* id);
+/* device bytes a request occupies once admitted (the admission model of the HBM budget:
+   fields, stage storage, CG work vectors and diagonals of its share of a union-mesh group,
+   RK-CB3e); IMEX_EINVAL for an invalid mesh */
+imex_status imex_request_footprint(const imex_request* r, double* bytes);
 /* admit, repack, one step of every active request; active: requests still running after it.
    A group whose step fails marks its requests IMEX_REQ_FAILED (message: imex_server_last_error). */
 imex_status imex_server_tick(imex_server* sv, int* active);

@@ -6,8 +6,9 @@ TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
   p = 1/4 (cos 2x + cos 2y) e^{-4 nu t}; an exact Navier-Stokes solution for
   constant nu (the periodic 2D workload on [0, 2 pi]^2).
 * ``tg3d``: the disturbed Taylor-Green initial field of Sec. 4.3, Eq.
-  (transition:v0), shifted by pi/2 in x and y so that it reads
-  (sin x cos y cos z, -cos x sin y cos z, 0) on [0, 2 pi]^3.
+  (transition:v0), evaluated at the point shifted by -pi/2 in x and +pi/2 in y
+  and z, so that it reads (sin x cos y cos z, -cos x sin y cos z, 0) on
+  [0, 2 pi]^3 (pinned in tests/test_oracle_flows.py).
 * ``tgtravel``: the traveling Taylor-Green vortex of Sec. 4.1 with phase speed 1,
   decay rate 8 pi^2 nu_0.
 * viscosity laws: constant; nu(x, y, t) = nu_0 (1 + 1/2 sin 2 pi x sin 2 pi y cos t);

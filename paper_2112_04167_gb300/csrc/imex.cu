@@ -2112,7 +2112,7 @@ imex_status imex_get_stats(const imex_ctx* c, imex_stats* out) {
 }
 
 imex_status imex_op_sipg(imex_ctx* c, int space, const double* x, double* y, int nsys, double alpha, double beta,
-                         const double* nu, const double* gd, int minv, int precision, int on_device) {
+                         const double* nu, const double* gd, int minv, int arith, int on_device) {
   if (!c || !x || !y) return IMEX_EINVAL;
   const bool vel = space == IMEX_SPACE_VELOCITY;
   if (!vel && space != IMEX_SPACE_PRESSURE) return fail(c, IMEX_EINVAL, "bad space");
@@ -2126,7 +2126,14 @@ imex_status imex_op_sipg(imex_ctx* c, int space, const double* x, double* y, int
   const double* dg = nullptr;
   if (gd) { TRY(copy_in(c, c->vb, gd, n * nsys, on_device)); dg = c->vb; }
   const double nu0 = vel ? nu_const(c) : 1.0;
-  if (precision == IMEX_FP64) {
+  if (arith != IMEX_ARITH_FP64 && arith != IMEX_ARITH_FP32 && arith != IMEX_ARITH_FF)
+    return fail(c, IMEX_EINVAL, "bad arith");
+  if (arith == IMEX_ARITH_FF) {
+    SipgArgs<double> a = sipg_args<double>(c->cx, c->cAp, nsys, (long long)n, dnu, nu0, dg, alpha, beta, minv);
+    a.ops = line_ops<double>(c, vel);
+    if (sipg_apply_ff(g, N, a, c->st) != 0) return fail(c, IMEX_EINVAL, "no float-float kernel for this operator");
+    TRY(cuda_check(c, cudaGetLastError(), "sipg_apply_ff"));
+  } else if (arith == IMEX_ARITH_FP64) {
     SipgArgs<double> a = sipg_args<double>(c->cx, c->cAp, nsys, (long long)n, dnu, nu0, dg, alpha, beta, minv);
     a.ops = line_ops<double>(c, vel);
     TRY(launch_check(c, sipg_apply<double>(g, N, a, c->st), "sipg_apply"));
@@ -2157,44 +2164,73 @@ imex_status imex_op_sipg_diag(imex_ctx* c, int space, double* y, double alpha, d
   return copy_out(c, y, c->cAp, n, on_device);
 }
 
-imex_status imex_op_div(imex_ctx* c, const double* v, const double* w, int mode, double* b, int on_device) {
+// arith of the divergence, gradient and grad-div entry points: FP64 or float-float
+static bool ff_arith(int arith, bool* ff) {
+  *ff = arith == IMEX_ARITH_FF;
+  return arith == IMEX_ARITH_FP64 || arith == IMEX_ARITH_FF;
+}
+
+imex_status imex_op_div(imex_ctx* c, const double* v, const double* w, int mode, double* b, int arith,
+                        int on_device) {
   if (!c || !v || !b || mode < 0 || mode > 2 || (mode == 1 && !w)) return IMEX_EINVAL;
+  bool ff = false;
+  if (!ff_arith(arith, &ff)) return fail(c, IMEX_EINVAL, "bad arith");
   TRY(copy_in(c, c->cx, v, c->nv * c->d, on_device));
   if (mode == 1) TRY(copy_in(c, c->vb, w, c->nv * c->d, on_device));
   DivArgs<double> da{c->cx, (long long)c->nv, c->vb, mode, 1.0, c->bp};
-  TRY(launch_check(c, dg_div<double>(c->gv, c->Nv, da, c->st), "dg_div"));
+  TRY(launch_check(c, ff ? dg_div_ff(c->gv, c->Nv, da, c->st) : dg_div<double>(c->gv, c->Nv, da, c->st), "dg_div"));
   return copy_out(c, b, c->bp, c->np, on_device);
 }
 
-imex_status imex_op_grad(imex_ctx* c, const double* psi, double* out, int on_device) {
+imex_status imex_op_grad(imex_ctx* c, const double* psi, double* out, int arith, int on_device) {
   if (!c || !psi || !out) return IMEX_EINVAL;
+  bool ff = false;
+  if (!ff_arith(arith, &ff)) return fail(c, IMEX_EINVAL, "bad arith");
   TRY(copy_in(c, c->bp, psi, c->np, on_device));
   GradArgs<double> ga{c->bp, nullptr, (long long)c->nv, 1.0, c->cAp};
-  TRY(launch_check(c, dg_grad<double>(c->gv, c->Nv, ga, c->st), "dg_grad"));
+  TRY(launch_check(c, ff ? dg_grad_ff(c->gv, c->Nv, ga, c->st) : dg_grad<double>(c->gv, c->Nv, ga, c->st),
+                   "dg_grad"));
   return copy_out(c, out, c->cAp, c->nv * c->d, on_device);
 }
 
-imex_status imex_op_conv(imex_ctx* c, const double* v, const double* vb, double* out, int on_device) {
+imex_status imex_op_conv(imex_ctx* c, const double* v, const double* vb, double* out, int arith, int on_device) {
   if (!c || !v || !out) return IMEX_EINVAL;
-  TRY(copy_in(c, c->cx, v, c->nv * c->d, on_device));
+  if (arith != IMEX_ARITH_FP64 && arith != IMEX_ARITH_FP32 && arith != IMEX_ARITH_FF)
+    return fail(c, IMEX_EINVAL, "bad arith");
+  const size_t nt = c->nv * c->d;
+  TRY(copy_in(c, c->cx, v, nt, on_device));
   const double* dvb = nullptr;
-  if (vb) { TRY(copy_in(c, c->vb, vb, c->nv * c->d, on_device)); dvb = c->vb; }
-  ConvArgs<double> ca{c->cx, (long long)c->nv, dvb, 1.0, c->cAp};
-  TRY(launch_check(c, dg_conv<double>(c->gv, c->Nv, ca, c->st), "dg_conv"));
-  return copy_out(c, out, c->cAp, c->nv * c->d, on_device);
+  if (vb) { TRY(copy_in(c, c->vb, vb, nt, on_device)); dvb = c->vb; }
+  if (arith == IMEX_ARITH_FP32) {
+    convert_d2f(c->cx, c->fx, nt, c->st);
+    if (dvb) convert_d2f(dvb, c->fr, nt, c->st);
+    ConvArgs<float> ca{c->fx, (long long)c->nv, dvb ? c->fr : nullptr, 1.f, c->fp};
+    TRY(launch_check(c, dg_conv<float>(c->gv, c->Nv, ca, c->st), "dg_conv(f32)"));
+    f2d(c->fp, c->cAp, nt, c->st);
+  } else {
+    ConvArgs<double> ca{c->cx, (long long)c->nv, dvb, 1.0, c->cAp};
+    TRY(launch_check(c, arith == IMEX_ARITH_FF ? dg_conv_ff(c->gv, c->Nv, ca, c->st)
+                                               : dg_conv<double>(c->gv, c->Nv, ca, c->st), "dg_conv"));
+  }
+  return copy_out(c, out, c->cAp, nt, on_device);
 }
 
-imex_status imex_op_graddiv(imex_ctx* c, const double* v, const double* nu, double* fd3, double* fd2,
+imex_status imex_op_graddiv(imex_ctx* c, const double* v, const double* nu, double* fd3, double* fd2, int arith,
                             int on_device) {
   if (!c || !v || !fd3) return IMEX_EINVAL;
+  bool ff = false;
+  if (!ff_arith(arith, &ff)) return fail(c, IMEX_EINVAL, "bad arith");
   const size_t nt = c->nv * c->d;
   TRY(copy_in(c, c->cx, v, nt, on_device));
   const int saved = c->nu_kind;
+  const int saved_prec = c->desc.precision;
   const double* dnu = nullptr;
   if (nu) { TRY(copy_in(c, c->nu, nu, c->nv, on_device)); dnu = c->nu; c->nu_kind = IMEX_NU_FIELD; }
   CK(cudaMemsetAsync(c->cz, 0, nt * sizeof(double), c->st), "memset");
+  c->desc.precision = ff ? IMEX_MIXED : IMEX_FP64;     // graddiv() picks float-float for the mixed form
   imex_status s = graddiv(c, c->cx, dnu, c->cAp, fd2 ? c->cz : nullptr);
   c->nu_kind = saved;
+  c->desc.precision = saved_prec;
   TRY(s);
   TRY(copy_out(c, fd3, c->cAp, nt, on_device));
   if (fd2) TRY(copy_out(c, fd2, c->cz, nt, on_device));
@@ -2637,6 +2673,16 @@ imex_status imex_server_submit(imex_server* sv, const imex_request* r, long long
   *id = (long long)sv->reqs.size();
   sv->reqs.push_back(std::move(R));
   sv->queue.push_back(*id);
+  return IMEX_OK;
+}
+
+imex_status imex_request_footprint(const imex_request* r, double* bytes) {
+  if (!r || !bytes || (r->dim != 2 && r->dim != 3) || r->P < 2 || r->P > IMEX_MAXN - 1) return IMEX_EINVAL;
+  for (int k = 0; k < r->dim; ++k)
+    if (r->nelem[k] < 1) return IMEX_EINVAL;
+  const InstGeom I = req_geom(*r);
+  const long long nv = (long long)I.ne * ipow(r->P + 1, r->dim), np = (long long)I.ne * ipow(r->P, r->dim);
+  *bytes = footprint_bytes(r->dim, nv, np, 4);
   return IMEX_OK;
 }
 

@@ -20,6 +20,7 @@ FLOW_NONE, FLOW_TG2D, FLOW_TG3D, FLOW_TGTRAVEL = 0, 1, 2, 3
 NU_CONST, NU_VARXYT, NU_VELOCITY, NU_FIELD = 0, 1, 2, 3
 FORCE_NONE, FORCE_TGTRAVEL_VARNU = 0, 1
 SPACE_VELOCITY, SPACE_PRESSURE = 0, 1
+ARITH_FP64, ARITH_FP32, ARITH_FF = 0, 1, 3
 _STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ENOTCONV", 4: "EUNSTABLE", 5: "ECUDA"}
 
 
@@ -96,10 +97,10 @@ _SIGS = {
     "imex_get_stats": [_P, C.POINTER(imex_stats)],
     "imex_op_sipg": [_P, C.c_int, _P, _P, C.c_int, C.c_double, C.c_double, _P, _P, C.c_int, C.c_int, C.c_int],
     "imex_op_sipg_diag": [_P, C.c_int, _P, C.c_double, C.c_double, _P, C.c_int],
-    "imex_op_div": [_P, _P, _P, C.c_int, _P, C.c_int],
-    "imex_op_grad": [_P, _P, _P, C.c_int],
-    "imex_op_conv": [_P, _P, _P, _P, C.c_int],
-    "imex_op_graddiv": [_P, _P, _P, _P, _P, C.c_int],
+    "imex_op_div": [_P, _P, _P, C.c_int, _P, C.c_int, C.c_int],
+    "imex_op_grad": [_P, _P, _P, C.c_int, C.c_int],
+    "imex_op_conv": [_P, _P, _P, _P, C.c_int, C.c_int],
+    "imex_op_graddiv": [_P, _P, _P, _P, _P, C.c_int, C.c_int],
     "imex_solve_poisson": [_P, _P, _P, C.c_int],
     "imex_solve_helmholtz": [_P, _P, _P, C.c_double, _P, _P, C.c_int],
     "imex_eval_field": [_P, C.c_int, C.c_int, _P, C.c_int, C.c_double, _P, _P, C.c_int],
@@ -127,6 +128,7 @@ _SIGS = {
     "imex_server_poll": [_P, C.c_longlong, C.POINTER(C.c_int), C.POINTER(C.c_int), _D],
     "imex_server_result": [_P, C.c_longlong, _D],
     "imex_server_get_stats": [_P, C.POINTER(imex_server_stats)],
+    "imex_request_footprint": [C.POINTER(imex_request), _D],
 }
 REQ_QUEUED, REQ_ACTIVE, REQ_DONE, REQ_FAILED = range(4)
 PROF_PRESSURE_F32, PROF_PRESSURE_F64, PROF_HELMHOLTZ_F32, PROF_HELMHOLTZ_F64, PROF_CONV, PROF_PCG_PERSIST = range(6)
@@ -317,7 +319,8 @@ class Context:
 
     # --- operators -------------------------------------------------------------
     def op_sipg(self, x, space=SPACE_VELOCITY, nsys=1, alpha=0.0, beta=1.0, nu=None, g=None, minv=0,
-                precision=FP64):
+                precision=ARITH_FP64):
+        """precision: ARITH_FP64, ARITH_FP32 (== MIXED) or ARITH_FF."""
         n = (self.nvel if space == SPACE_VELOCITY else self.npres) * nsys
         out = np.empty(n)
         px, dev, _a = _arr(x, n)
@@ -335,37 +338,37 @@ class Context:
         self._check(load().imex_op_sipg_diag(self._h, space, py, alpha, beta, pn, 0))
         return out
 
-    def op_div(self, v, w=None, mode=0):
+    def op_div(self, v, w=None, mode=0, arith=ARITH_FP64):
         out = np.empty(self.npres)
         pv, _, _a = _arr(v, self.dim * self.nvel)
         pw, _, _b = _arr(w, self.dim * self.nvel)
         pb, _, _c = _arr(out, self.npres, writable=True)
-        self._check(load().imex_op_div(self._h, pv, pw, mode, pb, 0))
+        self._check(load().imex_op_div(self._h, pv, pw, mode, pb, arith, 0))
         return out
 
-    def op_grad(self, psi):
+    def op_grad(self, psi, arith=ARITH_FP64):
         out = np.empty((self.dim, self.nvel))
         pp, _, _a = _arr(psi, self.npres)
         po, _, _b = _arr(out, self.dim * self.nvel, writable=True)
-        self._check(load().imex_op_grad(self._h, pp, po, 0))
+        self._check(load().imex_op_grad(self._h, pp, po, arith, 0))
         return out
 
-    def op_conv(self, v, vb=None):
+    def op_conv(self, v, vb=None, arith=ARITH_FP64):
         out = np.empty((self.dim, self.nvel))
         pv, _, _a = _arr(v, self.dim * self.nvel)
         pb, _, _b = _arr(vb, self.dim * self.nvel)
         po, _, _c = _arr(out, self.dim * self.nvel, writable=True)
-        self._check(load().imex_op_conv(self._h, pv, pb, po, 0))
+        self._check(load().imex_op_conv(self._h, pv, pb, po, arith, 0))
         return out
 
-    def op_graddiv(self, v, nu=None, with_fd2=False):
+    def op_graddiv(self, v, nu=None, with_fd2=False, arith=ARITH_FP64):
         fd3 = np.empty((self.dim, self.nvel))
         fd2 = np.empty((self.dim, self.nvel)) if with_fd2 else None
         pv, _, _a = _arr(v, self.dim * self.nvel)
         pn, _, _b = _arr(nu, self.nvel)
         p3, _, _c = _arr(fd3, self.dim * self.nvel, writable=True)
         p2, _, _d = _arr(fd2, self.dim * self.nvel, writable=True) if with_fd2 else (None, 0, None)
-        self._check(load().imex_op_graddiv(self._h, pv, pn, p3, p2, 0))
+        self._check(load().imex_op_graddiv(self._h, pv, pn, p3, p2, arith, 0))
         return (fd3, fd2) if with_fd2 else fd3
 
     def solve_poisson(self, b):
@@ -513,8 +516,10 @@ class Server:
         if st != OK:
             raise ImexError(st, load().imex_server_last_error(self._h).decode())
 
-    def submit(self, dim, P, nelem, lo, hi, periodic, flow, flow_params=(), nu_kind=NU_CONST, nu_params=(),
-               bc_kind=FLOW_NONE, bc_params=(), f_kind=FORCE_NONE, f_params=(), t0=0.0, dt=0.01, nsteps=1):
+    @staticmethod
+    def request(dim, P, nelem, lo, hi, periodic, flow, flow_params=(), nu_kind=NU_CONST, nu_params=(),
+                bc_kind=FLOW_NONE, bc_params=(), f_kind=FORCE_NONE, f_params=(), t0=0.0, dt=0.01, nsteps=1):
+        """The imex_request structure of a flow request."""
         r = imex_request()
         r.dim, r.P = dim, P
         for k in range(3):
@@ -528,6 +533,20 @@ class Server:
         _fill8(r.bc_params, bc_params)
         _fill8(r.f_params, f_params)
         r.t0, r.dt, r.nsteps = t0, dt, nsteps
+        return r
+
+    @staticmethod
+    def footprint(**req):
+        """Device bytes the request occupies once admitted (imex_request_footprint)."""
+        b = C.c_double()
+        st = load().imex_request_footprint(C.byref(Server.request(**req)), C.byref(b))
+        if st != OK:
+            raise ImexError(st, "imex_request_footprint failed")
+        return b.value
+
+    def submit(self, **req):
+        r = self.request(**req)
+        dim, P, nelem = req["dim"], req["P"], req["nelem"]
         i = C.c_longlong()
         self._check(load().imex_server_submit(self._h, C.byref(r), C.byref(i)))
         ne = 1

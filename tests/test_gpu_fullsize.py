@@ -67,6 +67,28 @@ def test_pressure_apply_sampled(full, local_ops, precision, tol):
         assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < tol, ec
 
 
+@pytest.mark.parametrize("precision,tol", [(imex.FP64, 1e-12), (imex.ARITH_FF, 1e-12), (imex.ARITH_FP32, 1e-5)])
+def test_velocity_helmholtz_apply_sampled(full, local_ops, precision, tol):
+    """The velocity operator of the Helmholtz solves, M + gamma nu A (N = P + 1 = 8), for the
+    three velocity components at once, in each arithmetic the solves use."""
+    mesh3 = local_ops[0]
+    nu, gamma = 1.0 / 1600, 0.01
+    full.set_viscosity_const(nu)
+    A3 = dg.sipg_matrix(mesh3, P + 1, nu, dirichlet=True)
+    M3 = dg.mass_diag(mesh3, P + 1)
+    ndv = (P + 1) ** 3
+    x = inputs.field(3 * full.nvel, seed=33)
+    y = full.op_sipg(x, nsys=3, alpha=1.0, beta=gamma, precision=precision).reshape(3, -1, ndv)
+    xs = x.reshape(3, -1, ndv)
+    for ec in SAMPLES:
+        idx = patch_indices(ec)
+        for c in range(3):
+            xp = xs[c, idx].ravel()
+            ref = (M3 * xp + gamma * (A3 @ xp)).reshape(27, ndv)[13]
+            got = y[c, idx[13]]
+            assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < tol, (ec, c)
+
+
 def test_convection_sampled(full, local_ops):
     _, _, conv3 = local_ops
     ndv = (P + 1) ** 3

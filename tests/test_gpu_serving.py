@@ -1,7 +1,9 @@
 """GPU parity of the serving form: requests that arrive, wait for room under an HBM budget,
 join and leave the union-mesh groups between steps (continuous batching) finish with the
 same fields as each request run alone through one context (FP64 solves to 1e-13: 1e-10
-relative), and the active footprint never exceeds the budget."""
+relative; the mixed form, whose FP32 inner iterations run differently in a group than
+alone, with its FP64 refinement to 1e-12: 1e-9 relative), and the active footprint never
+exceeds the budget."""
 import numpy as np
 import pytest
 
@@ -38,8 +40,9 @@ def mms(P, K, nu0, dt, n):
                 bc_params=[nu0], f_kind=imex.FORCE_TGTRAVEL_VARNU, f_params=[nu0], dt=dt, nsteps=n)
 
 
-def alone(r):
-    c = imex.Context(r["dim"], r["P"], r["nelem"], r["lo"], r["hi"], r["periodic"], tol=1e-13, maxit=50000)
+def alone(r, precision=imex.FP64, tol=1e-13):
+    c = imex.Context(r["dim"], r["P"], r["nelem"], r["lo"], r["hi"], r["periodic"], precision=precision, tol=tol,
+                     maxit=50000)
     if r["nu_kind"] == imex.NU_CONST:
         c.set_viscosity_const(r["nu_params"][0])
     else:
@@ -54,11 +57,7 @@ def alone(r):
 
 
 def footprint(r):
-    ne = int(np.prod(r["nelem"]))
-    d, P = r["dim"], r["P"]
-    nv, npr = ne * (P + 1) ** d, ne * P ** d
-    f64v = 11.0 * d + 4 + d * d + 2 + 4 * 4 * d
-    return nv * (8 * f64v + 4 * (5 * d + 2)) + npr * 56 + 256
+    return imex.Server.footprint(**r)
 
 
 def test_continuous_batching_matches_alone():
@@ -116,3 +115,28 @@ def test_server_groups_join_and_leave_repeatedly():
     assert st["completed"] == len(reqs) and st["failed"] == 0
     for i, r in zip(ids, reqs):
         assert rel(sv.result(i), alone(r)) < 1e-10, i
+
+
+def test_continuous_batching_mixed_matches_alone():
+    """The served form as the serving workload runs it (IMEX_MIXED): every request of the
+    mix equals the same request run alone in the mixed form, and the FP64 form, to the
+    solver tolerance."""
+    reqs = [tg2d(4, 3, 0.01, 0.02, 4), mms(4, 3, 0.01, 0.005, 3), tg3d(3, 2, 1e-3, 0.02, 3),
+            tg2d(5, 4, 0.01, 0.01, 2), tg3d(4, 3, 1e-3, 0.02, 2), mms(5, 2, 0.02, 0.01, 2)]
+    budget = 2.5 * max(footprint(r) for r in reqs)
+    sv = imex.Server(budget_bytes=budget, precision=imex.MIXED, tol=1e-12, maxit=50000, keep_results=True)
+    ids = [sv.submit(**reqs[0])]
+    sv.tick()
+    for r in reqs[1:]:
+        ids.append(sv.submit(**r))
+        sv.tick()
+    for _ in range(100):
+        if sv.tick() == 0 and sv.stats()["queued"] == 0:
+            break
+    st = sv.stats()
+    assert st["completed"] == len(reqs) and st["failed"] == 0
+    assert st["max_footprint_bytes"] <= budget
+    for i, r in zip(ids, reqs):
+        got = sv.result(i)
+        assert rel(got, alone(r, precision=imex.MIXED, tol=1e-12)) < 1e-9, i
+        assert rel(got, alone(r)) < 1e-9, i

@@ -273,3 +273,74 @@ def test_viscosity_change_between_steps(precision):
     b.set_state(a.time() - 0.02, v1)
     b.step(0.02, 1)
     assert rel(a.get_velocity(), b.get_velocity()) < 1e-11
+
+
+def test_sdc_cb3e_33_tg3d():
+    """SDC-CB3e(3,3) on 4 GLL nodes (Alg. 4 with the RK-CB3e predictor: the SDC method of the
+    3D Taylor-Green workload) on a 3D periodic mesh."""
+    P, n = 3, (3, 2, 2)
+    ctx = imex.Context(3, P, n, [0, 0, 0], [TWO_PI] * 3, (1, 1, 1), tol=1e-14, maxit=50000)
+    ctx.set_viscosity_const(1.0 / 1600)
+    ctx.set_sdc(3, 3, "CB3e")
+    mesh = dg.Mesh(3, P, n, [0, 0, 0], [TWO_PI] * 3, (True, True, True))
+    fl = flows.Flow("tg3d", 1.0 / 1600)
+    disc = ns.Discretization(mesh, fl)
+    v0 = fl.initial(disc.X).reshape(3, -1)
+    run_steps(ctx, disc, lambda v, t, dt: ns.sdc_step(disc, 3, 3, "CB3e", v, t, dt), v0, 0.0, 0.05, 1, 1e-11)
+    assert ctx.stats()["stages"] == 18
+
+
+@pytest.mark.parametrize("tab", ["CB3e", "ARS3"])
+def test_rk_step_velocity_dependent_viscosity(tab):
+    """Alg. 3 with nu = nu_0 + nu_1 (|v| / v_max)^2 (the law of Sec. 4.2): the viscosity of
+    each stage follows from the projected velocity, and the final projection applies."""
+    nu0, nu1, vmax = 0.01, 0.05, 1.0
+    ctx = imex.Context(2, 4, (4, 4), [0, 0], [TWO_PI, TWO_PI], (1, 1), tol=1e-14, maxit=50000)
+    ctx.set_viscosity_model(imex.NU_VELOCITY, [nu0, nu1, vmax])
+    ctx.set_tableau_named(tab)
+    mesh = dg.Mesh(2, 4, (4, 4), [0, 0], [TWO_PI, TWO_PI], (True, True))
+    fl = flows.Flow("tg2d", nu0, nu_kind="velocity", nu1=nu1, vmax=vmax)
+    disc = ns.Discretization(mesh, fl)
+    v0 = fl.initial(disc.X).reshape(2, -1)
+    run_steps(ctx, disc, lambda v, t, dt: ns.rk_step(disc, tab, v, t, dt)[0], v0, 0.0, 0.02, 2, 1e-11)
+
+
+def test_sdc_velocity_dependent_viscosity_3d():
+    """Alg. 4 (SDC-Eu(2,2)) with the velocity-dependent viscosity law in 3D."""
+    nu0, nu1, vmax = 1e-3, 4e-3, 1.0
+    P, n = 3, (2, 2, 3)
+    ctx = imex.Context(3, P, n, [0, 0, 0], [TWO_PI] * 3, (1, 1, 1), tol=1e-14, maxit=50000)
+    ctx.set_viscosity_model(imex.NU_VELOCITY, [nu0, nu1, vmax])
+    ctx.set_sdc(2, 2, "EULER")
+    mesh = dg.Mesh(3, P, n, [0, 0, 0], [TWO_PI] * 3, (True, True, True))
+    fl = flows.Flow("tg3d", nu0, nu_kind="velocity", nu1=nu1, vmax=vmax)
+    disc = ns.Discretization(mesh, fl)
+    v0 = fl.initial(disc.X).reshape(3, -1)
+    run_steps(ctx, disc, lambda v, t, dt: ns.sdc_step(disc, 2, 2, "EULER", v, t, dt), v0, 0.0, 0.03, 1, 1e-11)
+
+
+def test_pressure_closed_form_tg2d():
+    """imex_get_pressure against the closed-form pressure of the decaying Taylor-Green vortex,
+    p = (cos 2x + cos 2y) e^{-4 nu t} / 4: the last stage potential of Alg. 3, divided by the
+    stage's time scale c_s dt, approximates p at the stage time to first order in dt (the
+    splitting error of the projection), once the spatial error is below it (P = 6, 8^2)."""
+    from oracle import tableaux
+    P, n, nu = 6, 8, 0.01
+    cs = float(tableaux.get("CB3e").as_float()[0][-1])
+    mesh = dg.Mesh(2, P, (n, n), [0, 0], [TWO_PI, TWO_PI], (True, True))
+    Xp = mesh.node_coords(P)
+    Mp = dg.mass_diag(mesh, P)
+    errs = []
+    for dt in (0.02, 0.01, 0.005):
+        ctx = imex.Context(2, P, (n, n), [0, 0], [TWO_PI, TWO_PI], (1, 1), tol=1e-13, maxit=50000)
+        ctx.set_viscosity_const(nu)
+        ctx.init_flow(imex.FLOW_TG2D, [nu])
+        ctx.step(dt, 1)
+        q = ctx.get_pressure() / (cs * dt)
+        pex = flows.tg2d_pressure(Xp, cs * dt, nu).ravel()
+        pex -= np.dot(Mp, pex) / Mp.sum()
+        assert abs(np.dot(Mp, q)) < 1e-12 * np.abs(q).max() * Mp.sum()     # mass-weighted mean-free
+        errs.append(rel(q, pex))
+    assert errs[0] < 1e-3
+    for a, b in zip(errs, errs[1:]):
+        assert 1.6 < a / b < 2.4, errs

@@ -1,0 +1,79 @@
+"""Pins of the oracle's closed-form flows (oracle/flows.py) against what the paper and the
+mathematics fix, independently of the CUDA path.
+
+* tg3d_velocity: the initial field of the Taylor-Green transition, Eq. (transition:v0) of
+  Sec. 4.3, v0 = (cos x sin y sin z, -sin x cos y sin z, 0) on [-pi, pi]^3, is written on
+  [0, 2 pi]^3 as (sin x cos y cos z, -cos x sin y cos z, 0): the paper's field at the point
+  shifted by -pi/2 in x and +pi/2 in y and z.  It is solenoidal, 2 pi-periodic and its
+  largest velocity is v_{0,max} = 1 (the reference velocity of Sec. 4.3).
+* tg2d_velocity / tg2d_pressure: the decaying Taylor-Green vortex is an exact solution of
+  the incompressible Navier-Stokes equations, d_t v + (v . grad) v + grad p = nu lap v,
+  div v = 0 -- checked by finite differences at random points (a wrong sign, factor or
+  decay rate in either field fails it).
+"""
+import numpy as np
+
+from oracle import flows
+
+PI = np.pi
+
+
+def paper_v0(X):
+    """Eq. (transition:v0) as printed in Sec. 4.3 (domain [-pi, pi]^3)."""
+    x, y, z = X[..., 0], X[..., 1], X[..., 2]
+    return np.stack([np.cos(x) * np.sin(y) * np.sin(z), -np.sin(x) * np.cos(y) * np.sin(z), np.zeros_like(x)])
+
+
+def points(n, d, seed, lo=0.0, hi=2 * PI):
+    return np.random.default_rng(seed).uniform(lo, hi, size=(n, d))
+
+
+def fd_grad(f, X, h=1e-5):
+    """G[c, k, i] = d f_c / d x_k at the points X (central differences)."""
+    d = X.shape[-1]
+    cols = []
+    for k in range(d):
+        e = np.zeros(d)
+        e[k] = h
+        cols.append((f(X + e) - f(X - e)) / (2 * h))
+    return np.stack(cols, axis=1)
+
+
+def test_tg3d_is_the_papers_field_shifted():
+    X = points(2000, 3, 1)
+    shift = np.array([-PI / 2, PI / 2, PI / 2])
+    assert np.abs(flows.tg3d_velocity(X) - paper_v0(X + shift)).max() < 1e-14
+
+
+def test_tg3d_solenoidal_periodic_unit_maximum():
+    X = points(2000, 3, 2)
+    G = fd_grad(flows.tg3d_velocity, X)
+    assert np.abs(G[0, 0] + G[1, 1] + G[2, 2]).max() < 1e-9
+    # not trivially solenoidal: the in-plane strain is order one
+    assert np.abs(G[0, 0]).max() > 0.5
+    for k in range(3):
+        e = np.zeros(3)
+        e[k] = 2 * PI
+        assert np.abs(flows.tg3d_velocity(X + e) - flows.tg3d_velocity(X)).max() < 1e-13
+    g = np.linspace(0, 2 * PI, 33)
+    Xg = np.stack(np.meshgrid(g, g, g, indexing="ij"), axis=-1)
+    assert abs(np.abs(flows.tg3d_velocity(Xg)).max() - 1.0) < 1e-14
+
+
+def test_tg2d_exact_navier_stokes_solution():
+    nu, h = 0.037, 1e-4
+    X = points(500, 2, 3)
+    for t in (0.0, 0.7, 3.1):
+        v = flows.tg2d_velocity(X, t, nu)
+        dvdt = (flows.tg2d_velocity(X, t + h, nu) - flows.tg2d_velocity(X, t - h, nu)) / (2 * h)
+        G = fd_grad(lambda Y: flows.tg2d_velocity(Y, t, nu), X, h)
+        gp = fd_grad(lambda Y: flows.tg2d_pressure(Y, t, nu)[None], X, h)[0]
+        lap = np.zeros_like(v)
+        for k in range(2):
+            e = np.zeros(2)
+            e[k] = h
+            lap += (flows.tg2d_velocity(X + e, t, nu) - 2 * v + flows.tg2d_velocity(X - e, t, nu)) / h ** 2
+        adv = np.stack([v[0] * G[c, 0] + v[1] * G[c, 1] for c in range(2)])
+        res = dvdt + adv + gp - nu * lap
+        assert np.abs(res).max() < 1e-6, t
+        assert np.abs(G[0, 0] + G[1, 1]).max() < 1e-9
