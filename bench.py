@@ -42,6 +42,8 @@ def parse():
     ap.add_argument("--dt", type=float, default=0.01)
     ap.add_argument("--tol", type=float, default=1e-10)
     ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--precond", default="jacobi", choices=["jacobi", "pmg"],
+                    help="preconditioner of the pressure solves")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-only", action="store_true", help="short run for ncu captures")
@@ -122,6 +124,7 @@ def make_ctx(imex, args, precision, stream):
                        tol=args.tol, maxit=20000, stream=stream)
     ctx.set_viscosity_const(1.0 / 1600.0)
     ctx.set_tableau_named("CB3e")
+    ctx.set_pressure_precond(imex.PRECOND_PMG if args.precond == "pmg" else imex.PRECOND_JACOBI)
     ctx.init_flow(imex.FLOW_TG3D, [0.0])
     return ctx
 

@@ -8,7 +8,8 @@
  * of a Cartesian box (Sec. 3.3): tensor-product GLL bases of degree P for the
  * velocity and P-1 for the pressure, over-integrated convection with local
  * Lax-Friedrichs fluxes, symmetric interior penalty (SIPG) operators for the
- * pressure and viscous problems, each solved by Jacobi-preconditioned CG.
+ * pressure and viscous problems, each solved by preconditioned CG (Jacobi, or p-multigrid
+ * for the pressure).
  *
  * Conventions shared by every call
  *   - Layout: a scalar field is N_e * (P+1)^d doubles (pressure: N_e * P^d),
@@ -170,6 +171,28 @@ imex_status imex_op_conv(imex_ctx* ctx, const double* v, const double* vb, doubl
 /* out = F_d3 = -grad(nu div v) and, if out2 != NULL, out2 = F_d2 = div(nu (grad v)^T) */
 imex_status imex_op_graddiv(imex_ctx* ctx, const double* v, const double* nu, double* out_fd3,
                             double* out_fd2, int arith, int on_device);
+/* Preconditioner of the pressure Poisson solves (Sec. 3.3 solves them by preconditioned CG;
+   its preconditioners are not described there): IMEX_PRECOND_JACOBI, or IMEX_PRECOND_PMG --
+   one p-multigrid V-cycle per CG iteration over the pressure degrees P-1, halved down to 1
+   on the same mesh, with the SIPG pressure operator rediscretised on every level,
+   element-local GLL interpolation between levels (restriction: its transpose), Chebyshev-
+   accelerated Jacobi smoothing before and after each coarse correction and a fixed
+   Chebyshev polynomial on the degree-1 level.  params (nparams <= 4, optional): smoothing
+   steps (default 3), steps on the coarsest level (10), smoothing range lmax / lmin (10),
+   coarsest range (100).  The IMEX_POISSON_CONSISTENT operator always uses Jacobi.
+   IMEX_EINVAL for an unknown kind or parameters out of range. */
+enum { IMEX_PRECOND_JACOBI = 0, IMEX_PRECOND_PMG = 1 };
+imex_status imex_set_pressure_precond(imex_ctx* ctx, int kind, const double* params, int nparams);
+/* the V-cycle's levels (set up on first use): their number (<= 4), points per direction
+   N[l] (finest first) and the upper ends lmax[l] of the Chebyshev intervals -- 1.15 times a
+   40-step power-iteration estimate of the largest eigenvalue of D^{-1} A on the level.
+   Output arrays of 4 entries; any pointer may be NULL. */
+imex_status imex_pmg_info(imex_ctx* ctx, int* nlev, int* N, double* lmax);
+/* z = one V-cycle applied to r (pressure space, np doubles each), in FP64 or FP32 arithmetic
+   (arith IMEX_ARITH_FP64 / IMEX_ARITH_FP32); lmax: the upper ends of the Chebyshev intervals
+   to use instead of the context's (nlev entries), or NULL. */
+imex_status imex_op_pmg_vcycle(imex_ctx* ctx, const double* r, double* z, const double* lmax, int arith,
+                               int on_device);
 /* Poisson solve L psi = b - mean(b) with the context's pressure operator; psi mean-free */
 imex_status imex_solve_poisson(imex_ctx* ctx, const double* b, double* psi, int on_device);
 /* Helmholtz solve (M + gamma A(nu)) v = M g + gamma r_b(nu, vb) for all d components */

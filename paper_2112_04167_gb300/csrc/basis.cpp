@@ -143,6 +143,15 @@ void build_tables(Tables<double>* t, Tables<float>* f) {
   std::memcpy(f->Q, t->Q, sizeof(t->Q));
 }
 
+// E[i * Nc + j] = l_j(x_i): the Lagrange cardinal polynomials of the Nc GLL points evaluated
+// at the Nf GLL points (the 1D factor of the p-multigrid prolongation)
+void gll_interp(int Nc, int Nf, double* E) {
+  double xc[IMEX_MAXN], wc[IMEX_MAXN], xf[IMEX_MAXN], wf[IMEX_MAXN];
+  gll(Nc, xc, wc);
+  gll(Nf, xf, wf);
+  lagrange_at(Nc, xc, Nf, xf, E);
+}
+
 // 1D SIPG line operators (unit viscosity) for each direction of a Cartesian mesh:
 // volume (2/h) sum_q w_q D_qi D_qj, plus the own-element face terms of the interior-penalty
 // form at the left (outward normal -1) and right (+1) ends, factor 1/2 on interior faces,

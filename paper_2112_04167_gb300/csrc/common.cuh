@@ -181,6 +181,8 @@ __device__ __forceinline__ void elem_coords(const Geom& g, int el, int ec[3]) {
 void build_tables(Tables<double>* t64, Tables<float>* t32);
 void build_line_ops(const Tables<double>& t, int N, const double* h, int d, LineOps<double>* o64,
                     LineOps<float>* o32);
+// E[i * Nc + j] = l_j(x_i): GLL(Nc) cardinal polynomials at the GLL(Nf) points
+void gll_interp(int Nc, int Nf, double* E);
 
 // number of kernels this library has launched (all contexts, all threads); add_launches
 // accounts for the kernels of a CUDA-graph replay

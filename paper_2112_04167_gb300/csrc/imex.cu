@@ -247,6 +247,30 @@ struct imex_ctx {
   bool use_persist = false;
   double* persist_partial = nullptr;   // 5 x 4096
   unsigned int* persist_bar = nullptr; // [2] barrier + [1] error flag (as int)
+  // p-multigrid preconditioner of the pressure solves: levels of degree P-1 halved down to 1
+  // on the same mesh, the SIPG pressure operator rediscretised on each, Chebyshev-Jacobi
+  // smoothing, element-local GLL interpolation between levels
+  struct Pmg {
+    int kind = 0;                  // IMEX_PRECOND_JACOBI / IMEX_PRECOND_PMG
+    int pre = 3, coarse = 10;      // smoothing steps (before and after), steps of the coarsest level
+    double ratio = 10.0, cratio = 100.0;
+    bool alloc64 = false, alloc32 = false, ready = false;
+    int nlev = 0;
+    int N[4] = {0, 0, 0, 0};
+    size_t cap[4] = {0, 0, 0, 0};  // nodes per level at the element capacity
+    double lmax[4] = {0, 0, 0, 0};
+    Interp1D I[4];                 // I[l]: level l+1 -> level l
+    LineOps<double>* ops64[4] = {nullptr, nullptr, nullptr, nullptr};
+    LineOps<float>* ops32[4] = {nullptr, nullptr, nullptr, nullptr};
+    double* dinv64[4] = {nullptr, nullptr, nullptr, nullptr};
+    float* dinv32[4] = {nullptr, nullptr, nullptr, nullptr};
+    // per level: right-hand side, iterate, residual, Chebyshev direction, operator output (level
+    // 0's right-hand side and iterate are the CG residual and z)
+    double *b64[4] = {}, *x64[4] = {}, *r64[4] = {}, *d64[4] = {}, *ad64[4] = {};
+    float *b32[4] = {}, *x32[4] = {}, *r32[4] = {}, *d32[4] = {}, *ad32[4] = {};
+    double *z64 = nullptr, *ones64 = nullptr;
+    float *z32 = nullptr, *ones32 = nullptr;
+  } pmg;
   imex_stats stats{};
   double last_res = 0.0;
   // CUDA-event timing of kernel classes
@@ -511,6 +535,10 @@ imex_status apply_helm(imex_ctx* c, const T* x, T* y, int nsys, const T* nu, dou
   return launch_check(c, rc, "sipg_apply(v)");
 }
 
+// z = one p-multigrid V-cycle applied to r (defined with the p-multigrid code below)
+template <typename T>
+imex_status pmg_vcycle(imex_ctx* c, const T* r, T* z, const double* lm);
+
 // ---- PCG -------------------------------------------------------------------------
 // per-system CG scalars: cg_d holds rz, rz_old, rr, bb, pAp, zmean, a mean scratch, the true
 // residual norm (mixed form), rmean, dsum, alpha and beta, maxsys entries each; cg_f the FP32
@@ -614,10 +642,12 @@ imex_status pull_scalars(imex_ctx* c, int nsys) {
 // Jacobi PCG (FP64) on the systems of a segment table; x holds the initial guess.  `project`:
 // the systems are singular with the constants as null space (the pressure problems): the
 // residual is projected onto the range and the preconditioned residual kept mean-free.
+// pm: preconditioned by one p-multigrid V-cycle per iteration (pressure systems) instead of
+// the Jacobi diagonal dinv
 template <typename Op, typename OpDot>
 imex_status pcg(imex_ctx* c, const imex_ctx::Seg& sg, Op op, OpDot op_dot, bool fused, const double* b, double* x,
                 const double* dinv, double tol, int maxit, bool project,
-                const std::vector<unsigned long long>& opkey, long long* iters_out, double* res_out) {
+                const std::vector<unsigned long long>& opkey, long long* iters_out, double* res_out, bool pm = false) {
   const SegTable& t = sg.t;
   CgScalars sc = scalars(c, tol, project);
   defer_dot(c, sc, fused, t);
@@ -626,6 +656,8 @@ imex_status pcg(imex_ctx* c, const imex_ctx::Seg& sg, Op op, OpDot op_dot, bool 
   double* r = c->cr;
   double* p = c->cp;
   double* Ap = c->cAp;
+  double* z = pm ? c->pmg.z64 : nullptr;
+  const double* dj = pm ? c->pmg.ones64 : dinv;     // the step kernel's diagonal
   TRY(op(x, Ap));
   LinComb lc{};
   lc.nterms = 2;
@@ -634,12 +666,20 @@ imex_status pcg(imex_ctx* c, const imex_ctx::Seg& sg, Op op, OpDot op_dot, bool 
   lincomb(r, lc, sg.total, c->st);        // r = b - A x (the segments tile [0, total))
   if (project) seg_remove_mean(r, t, c->cg_d + 6 * m, c->seg_partial, c->counters + 3, c->st);
   seg_dot<double>(b, b, t, sc.bb, c->seg_partial, c->counters + 3, c->st);
-  seg_init<double>(r, dinv, t, sc, c->seg_partial, c->counters + 2, 1, c->st);
-  seg_step_p<double>(p, r, dinv, t, sc, 1, c->st);
+  seg_init<double>(r, dj, t, sc, c->seg_partial, c->counters + 2, 1, c->st);
+  if (pm) {
+    TRY(pmg_vcycle<double>(c, r, z, c->pmg.lmax));
+    seg_rz<double>(r, z, t, sc, c->seg_partial, c->counters + 3, 1, c->st);
+    seg_pz<double>(p, z, t, sc, 1, c->st);
+  } else {
+    seg_step_p<double>(p, r, dinv, t, sc, 1, c->st);
+  }
   CK(cudaGetLastError(), "cg_init");
-  const int chunk = 16;
+  // a V-cycle iteration costs many launches: shorter chunks waste less after convergence
+  const int chunk = pm ? 4 : 16;
   std::vector<unsigned long long> key = {64,        addr(&sg), addr(x), addr(b), addr(dinv), (unsigned long long)fused,
-                                         (unsigned long long)maxit, bits(tol), (unsigned long long)project};
+                                         (unsigned long long)maxit, bits(tol), (unsigned long long)project,
+                                         (unsigned long long)pm};
   key.insert(key.end(), opkey.begin(), opkey.end());
   auto body = [&]() -> imex_status {
     for (int k = 0; k < chunk; ++k) {
@@ -649,8 +689,15 @@ imex_status pcg(imex_ctx* c, const imex_ctx::Seg& sg, Op op, OpDot op_dot, bool 
         TRY(op(p, Ap));
         seg_pap<double>(p, Ap, t, sc, c->seg_partial, c->counters + 3, c->st);
       }
-      seg_step_xr<double>(x, r, p, Ap, dinv, t, sc, maxit, c->seg_partial, c->counters + 1, c->st);
-      seg_step_p<double>(p, r, dinv, t, sc, 0, c->st);
+      seg_step_xr<double>(x, r, p, Ap, dj, t, sc, maxit, c->seg_partial, c->counters + 1, c->st);
+      if (pm) {
+        if (project) seg_rproj<double>(r, t, sc, c->st);
+        TRY(pmg_vcycle<double>(c, r, z, c->pmg.lmax));
+        seg_rz<double>(r, z, t, sc, c->seg_partial, c->counters + 3, 0, c->st);
+        seg_pz<double>(p, z, t, sc, 0, c->st);
+      } else {
+        seg_step_p<double>(p, r, dinv, t, sc, 0, c->st);
+      }
     }
     return IMEX_OK;
   };
@@ -695,7 +742,8 @@ imex_status pcg(imex_ctx* c, const imex_ctx::Seg& sg, Op op, OpDot op_dot, bool 
 template <typename Op64, typename Op32, typename Op32Dot>
 imex_status pcg_mixed(imex_ctx* c, const imex_ctx::Seg& sg, Op64 op64, Op32 op32, Op32Dot op32dot, bool fused,
                       const double* b, double* x, const float* dinv, double tol, int maxit, bool project,
-                      const std::vector<unsigned long long>& opkey, long long* iters_out, double* res_out) {
+                      const std::vector<unsigned long long>& opkey, long long* iters_out, double* res_out,
+                      bool pm = false) {
   const SegTable& t = sg.t;
   const size_t ntot = sg.total;
   CgScalars sc = scalars(c, tol, project);
@@ -703,6 +751,8 @@ imex_status pcg_mixed(imex_ctx* c, const imex_ctx::Seg& sg, Op64 op64, Op32 op32
   const int nsys = t.nseg;
   const int m = c->maxsys;
   const double delta = 1e-2;
+  float* z = pm ? c->pmg.z32 : nullptr;
+  const float* dj = pm ? c->pmg.ones32 : dinv;      // the step kernel's diagonal
   double* r64 = c->cr;
   float* y = c->fx;
   float* r = c->fr;
@@ -757,8 +807,14 @@ imex_status pcg_mixed(imex_ctx* c, const imex_ctx::Seg& sg, Op64 op64, Op32 op32
                      (int)restart);
     CK(cudaMemcpyAsync(sc.done, done_h.data(), nsys * sizeof(int), cudaMemcpyHostToDevice, c->st), "cp flags");
     const int keep = (started && !restart) ? 1 : 0;
-    seg_init<float>(r, dinv, t, sc, c->seg_partial, c->counters + 2, 0, c->st);
-    if (!keep) seg_step_p<float>(p, r, dinv, t, sc, 1, c->st);
+    seg_init<float>(r, dj, t, sc, c->seg_partial, c->counters + 2, 0, c->st);
+    if (pm) {
+      TRY(pmg_vcycle<float>(c, r, z, c->pmg.lmax));
+      seg_rz<float>(r, z, t, sc, c->seg_partial, c->counters + 3, 1, c->st);
+      if (!keep) seg_pz<float>(p, z, t, sc, 1, c->st);
+    } else if (!keep) {
+      seg_step_p<float>(p, r, dinv, t, sc, 1, c->st);
+    }
     started = true;
     restart = false;
     c->stats.refinements++;
@@ -766,9 +822,10 @@ imex_status pcg_mixed(imex_ctx* c, const imex_ctx::Seg& sg, Op64 op64, Op32 op32
   };
   CK(cudaMemsetAsync(sc.iters, 0, nsys * sizeof(int), c->st), "memset");
   TRY(replace());
-  const int chunk = 16;
+  const int chunk = pm ? 4 : 16;
   std::vector<unsigned long long> key = {32, addr(&sg), addr(dinv), (unsigned long long)fused,
-                                         (unsigned long long)maxit, bits(tol), (unsigned long long)project};
+                                         (unsigned long long)maxit, bits(tol), (unsigned long long)project,
+                                         (unsigned long long)pm};
   key.insert(key.end(), opkey.begin(), opkey.end());
   auto body = [&]() -> imex_status {
     for (int k = 0; k < chunk; ++k) {
@@ -778,13 +835,20 @@ imex_status pcg_mixed(imex_ctx* c, const imex_ctx::Seg& sg, Op64 op64, Op32 op32
         TRY(op32(p, Ap));
         seg_pap<float>(p, Ap, t, sc, c->seg_partial, c->counters + 3, c->st);
       }
-      seg_step_xr<float>(y, r, p, Ap, dinv, t, sc, maxit, c->seg_partial, c->counters + 1, c->st);
-      seg_step_p<float>(p, r, dinv, t, sc, 0, c->st);
+      seg_step_xr<float>(y, r, p, Ap, dj, t, sc, maxit, c->seg_partial, c->counters + 1, c->st);
+      if (pm) {
+        if (project) seg_rproj<float>(r, t, sc, c->st);
+        TRY(pmg_vcycle<float>(c, r, z, c->pmg.lmax));
+        seg_rz<float>(r, z, t, sc, c->seg_partial, c->counters + 3, 0, c->st);
+        seg_pz<float>(p, z, t, sc, 0, c->st);
+      } else {
+        seg_step_p<float>(p, r, dinv, t, sc, 0, c->st);
+      }
     }
     return IMEX_OK;
   };
   // the periodic 3D pressure solve of one instance runs its inner iterations persistently
-  bool persist = c->use_persist && !c->batched && project && nsys == 1 && fused && c->d == 3 &&
+  bool persist = !pm && c->use_persist && !c->batched && project && nsys == 1 && fused && c->d == 3 &&
                  c->gp.bc[0] == 0 && c->gp.bc[1] == 0 && c->gp.bc[2] == 0;
   for (int round = 0;; ++round) {
     bool all = true;
@@ -852,6 +916,213 @@ void diag_mul(imex_ctx* c, double* out, const double* x, const double* m, size_t
 }
 
 
+// ---- p-multigrid -----------------------------------------------------------------------
+template <typename T> struct PmgVecs;
+template <> struct PmgVecs<double> {
+  static double** b(imex_ctx::Pmg& m) { return m.b64; }
+  static double** x(imex_ctx::Pmg& m) { return m.x64; }
+  static double** r(imex_ctx::Pmg& m) { return m.r64; }
+  static double** d(imex_ctx::Pmg& m) { return m.d64; }
+  static double** ad(imex_ctx::Pmg& m) { return m.ad64; }
+  static double** dinv(imex_ctx::Pmg& m) { return m.dinv64; }
+  static LineOps<double>** ops(imex_ctx::Pmg& m) { return m.ops64; }
+  static double* z(imex_ctx::Pmg& m) { return m.z64; }
+  static double* ones(imex_ctx::Pmg& m) { return m.ones64; }
+};
+template <> struct PmgVecs<float> {
+  static float** b(imex_ctx::Pmg& m) { return m.b32; }
+  static float** x(imex_ctx::Pmg& m) { return m.x32; }
+  static float** r(imex_ctx::Pmg& m) { return m.r32; }
+  static float** d(imex_ctx::Pmg& m) { return m.d32; }
+  static float** ad(imex_ctx::Pmg& m) { return m.ad32; }
+  static float** dinv(imex_ctx::Pmg& m) { return m.dinv32; }
+  static LineOps<float>** ops(imex_ctx::Pmg& m) { return m.ops32; }
+  static float* z(imex_ctx::Pmg& m) { return m.z32; }
+  static float* ones(imex_ctx::Pmg& m) { return m.ones32; }
+};
+
+// levels, line operators and interpolation matrices (once), and the vectors of precision T
+template <typename T>
+imex_status pmg_alloc(imex_ctx* c) {
+  imex_ctx::Pmg& M = c->pmg;
+  if (M.nlev == 0) {
+    int N = c->Np;
+    M.N[0] = N;
+    M.nlev = 1;
+    while (N > 2 && M.nlev < 4) {
+      N = (N - 1) / 2 + 1;                      // degree halved: p -> floor(p / 2)
+      M.N[M.nlev++] = N;
+    }
+    Tables<double>* h64 = new Tables<double>();
+    Tables<float>* h32 = new Tables<float>();
+    build_tables(h64, h32);
+    const double hh[3] = {1.0, 1.0, 1.0};
+    LineOps<double>* o64 = new LineOps<double>();
+    LineOps<float>* o32 = new LineOps<float>();
+    imex_status s = IMEX_OK;
+    M.ops64[0] = c->ops64_p;
+    M.ops32[0] = c->ops32_p;
+    for (int l = 1; l < M.nlev && s == IMEX_OK; ++l) {
+      build_line_ops(*h64, M.N[l], hh, c->d, o64, o32);
+      s = dalloc(c, &M.ops64[l], 1);
+      if (s == IMEX_OK) s = dalloc(c, &M.ops32[l], 1);
+      if (s == IMEX_OK && cudaMemcpy(M.ops64[l], o64, sizeof(*o64), cudaMemcpyHostToDevice) != cudaSuccess)
+        s = IMEX_ECUDA;
+      if (s == IMEX_OK && cudaMemcpy(M.ops32[l], o32, sizeof(*o32), cudaMemcpyHostToDevice) != cudaSuccess)
+        s = IMEX_ECUDA;
+    }
+    delete o64;
+    delete o32;
+    delete h64;
+    delete h32;
+    TRY(s);
+    for (int l = 0; l + 1 < M.nlev; ++l) gll_interp(M.N[l + 1], M.N[l], M.I[l].m);
+    for (int l = 0; l < M.nlev; ++l) {
+      M.cap[l] = (size_t)c->ne_cap * ipow(M.N[l], c->d);
+      TRY(dalloc(c, &M.dinv64[l], M.cap[l]));
+    }
+  }
+  bool& done = sizeof(T) == 8 ? M.alloc64 : M.alloc32;
+  if (done) return IMEX_OK;
+  using V = PmgVecs<T>;
+  for (int l = 0; l < M.nlev; ++l) {
+    if (l > 0) {
+      TRY(dalloc(c, &V::b(M)[l], M.cap[l]));
+      TRY(dalloc(c, &V::x(M)[l], M.cap[l]));
+    }
+    TRY(dalloc(c, &V::r(M)[l], M.cap[l]));
+    TRY(dalloc(c, &V::d(M)[l], M.cap[l]));
+    TRY(dalloc(c, &V::ad(M)[l], M.cap[l]));
+    if (sizeof(T) == 4) TRY(dalloc(c, &M.dinv32[l], M.cap[l]));
+  }
+  T* z = nullptr;
+  T* ones = nullptr;
+  TRY(dalloc(c, &z, M.cap[0]));
+  TRY(dalloc(c, &ones, M.cap[0]));
+  std::vector<T> h(M.cap[0], T(1));
+  CK(cudaMemcpy(ones, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice), "cp ones");
+  if (sizeof(T) == 8) { M.z64 = (double*)(void*)z; M.ones64 = (double*)(void*)ones; }
+  else { M.z32 = (float*)(void*)z; M.ones32 = (float*)(void*)ones; }
+  done = true;
+  // FP32 diagonals added after the set-up: rounded from the FP64 ones
+  if (sizeof(T) == 4 && M.ready)
+    for (int l = 0; l < M.nlev; ++l)
+      convert_d2f(M.dinv64[l], M.dinv32[l], (size_t)c->gp.ne * ipow(M.N[l], c->d), c->st);
+  return IMEX_OK;
+}
+
+// A x on level l (pressure space, unit viscosity, homogeneous Neumann faces)
+template <typename T>
+imex_status pmg_apply(imex_ctx* c, int l, const T* x, T* y) {
+  imex_ctx::Pmg& M = c->pmg;
+  const size_t n = (size_t)c->gp.ne * ipow(M.N[l], c->d);
+  SipgArgs<T> a = sipg_args<T>(x, y, 1, (long long)n, nullptr, 1.0, nullptr, 0.0, 1.0, 0);
+  a.ops = PmgVecs<T>::ops(M)[l];
+  return launch_check(c, sipg_apply<T>(c->gp, M.N[l], a, c->st), "sipg_apply(pmg)");
+}
+
+// Jacobi diagonals of every level and the Chebyshev upper bounds: 1.15 x the Rayleigh
+// quotient (x, A x) / (x, D x) after 40 power steps x <- D^{-1} A x (FP64, from a fixed
+// pseudo-random start), which reaches within a few percent of the largest eigenvalue of
+// D^{-1} A on these operators
+imex_status pmg_setup(imex_ctx* c) {
+  imex_ctx::Pmg& M = c->pmg;
+  if (M.ready) return IMEX_OK;
+  TRY(pmg_alloc<double>(c));
+  const int d = c->d;
+  for (int l = 0; l < M.nlev; ++l) {
+    const size_t n = (size_t)c->gp.ne * ipow(M.N[l], d);
+    SipgArgs<double> a = sipg_args<double>(nullptr, M.dinv64[l], 1, (long long)n, nullptr, 1.0, nullptr, 0.0, 1.0, 0);
+    TRY(launch_check(c, sipg_diag<double>(c->gp, M.N[l], a, c->st), "sipg_diag(pmg)"));
+    reciprocal<double>(M.dinv64[l], n, c->st);
+    if (M.alloc32) convert_d2f(M.dinv64[l], M.dinv32[l], n, c->st);
+    // power iteration with (x, D x) carried along: x = D^{-1} y, D x = y
+    double* x = M.r64[l];
+    double* Dx = M.d64[l];
+    double* ad = M.ad64[l];
+    std::vector<double> y0(n);
+    unsigned long long st = 0x9e3779b97f4a7c15ull;
+    for (size_t i = 0; i < n; ++i) {
+      st = st * 6364136223846793005ull + 1442695040888963407ull;
+      y0[i] = (double)(st >> 11) * (1.0 / 9007199254740992.0) - 0.5;
+    }
+    CK(cudaMemcpyAsync(Dx, y0.data(), n * sizeof(double), cudaMemcpyHostToDevice, c->st), "cp");
+    vec_mul(x, M.dinv64[l], Dx, 1.0, n, c->st);
+    double lam = 0.0;
+    for (int it = 0; it < 40; ++it) {
+      TRY(pmg_apply<double>(c, l, x, ad));
+      dot_batched(x, ad, n, (long long)n, 1, c->partial, c->nblocks, c->dscal + 40, c->st);
+      dot_batched(x, Dx, n, (long long)n, 1, c->partial, c->nblocks, c->dscal + 41, c->st);
+      CK(cudaMemcpyAsync(c->hscal + 40, c->dscal + 40, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->st), "cp");
+      CK(cudaStreamSynchronize(c->st), "sync");
+      const double num = c->hscal[40], den = c->hscal[41];
+      if (!(den > 0.0) || !std::isfinite(num)) return fail(c, IMEX_ECUDA, "p-multigrid eigenvalue estimate failed");
+      lam = num / den;
+      const double sc = 1.0 / std::sqrt(den);     // keep (x, D x) = 1
+      vec_mul(x, M.dinv64[l], ad, sc, n, c->st);  // x <- D^{-1} A x
+      std::swap(Dx, ad);                          // D x <- A x (scaled below)
+      LinComb lc{};
+      lc.nterms = 1; lc.x[0] = Dx; lc.c[0] = sc;
+      lincomb(Dx, lc, n, c->st);
+    }
+    M.lmax[l] = 1.15 * lam;
+  }
+  CK(cudaStreamSynchronize(c->st), "sync");
+  M.ready = true;
+  return IMEX_OK;
+}
+
+// Chebyshev steps on level l for A x = b: from x = 0 (add = 0) or from the current x
+template <typename T>
+imex_status pmg_smooth(imex_ctx* c, int l, int steps, double lmax, double ratio, bool from_x, const T* b, T* x) {
+  imex_ctx::Pmg& M = c->pmg;
+  using V = PmgVecs<T>;
+  const size_t n = (size_t)c->gp.ne * ipow(M.N[l], c->d);
+  T* r = V::r(M)[l];
+  T* dv = V::d(M)[l];
+  T* ad = V::ad(M)[l];
+  const T* dinv = V::dinv(M)[l];
+  const double lmin = lmax / ratio;
+  const double theta = 0.5 * (lmax + lmin), delta = 0.5 * (lmax - lmin), sigma = theta / delta;
+  if (from_x) TRY(pmg_apply<T>(c, l, x, ad));
+  cheb_first<T>(x, dv, r, b, from_x ? ad : nullptr, dinv, 1.0 / theta, n, from_x ? 1 : 0, c->st);
+  double rho = 1.0 / sigma;
+  for (int k = 1; k < steps; ++k) {
+    TRY(pmg_apply<T>(c, l, dv, ad));
+    const double rn = 1.0 / (2.0 * sigma - rho);
+    cheb_next<T>(x, dv, r, ad, dinv, rn * rho, 2.0 * rn / delta, n, k == steps - 1 ? 1 : 0, c->st);
+    rho = rn;
+  }
+  return IMEX_OK;
+}
+
+// z = one V-cycle applied to r (level 0); lm: the Chebyshev upper bounds of the levels
+template <typename T>
+imex_status pmg_vcycle(imex_ctx* c, const T* r, T* z, const double* lm) {
+  imex_ctx::Pmg& M = c->pmg;
+  using V = PmgVecs<T>;
+  const int L = M.nlev;
+  const T* b[4];
+  T* x[4];
+  for (int l = 0; l < L; ++l) {
+    b[l] = l == 0 ? r : V::b(M)[l];
+    x[l] = l == 0 ? z : V::x(M)[l];
+  }
+  for (int l = 0; l + 1 < L; ++l) {
+    TRY(pmg_smooth<T>(c, l, M.pre, lm[l], M.ratio, false, b[l], x[l]));
+    TRY(pmg_apply<T>(c, l, x[l], V::ad(M)[l]));
+    if (pmg_restrict<T>(c->d, c->gp.ne, M.N[l], M.N[l + 1], b[l], V::ad(M)[l], V::b(M)[l + 1], M.I[l], c->st) != 0)
+      return fail(c, IMEX_EINVAL, "p-multigrid: unsupported level pair");
+  }
+  TRY(pmg_smooth<T>(c, L - 1, M.coarse, lm[L - 1], M.cratio, false, b[L - 1], x[L - 1]));
+  for (int l = L - 2; l >= 0; --l) {
+    if (pmg_prolong<T>(c->d, c->gp.ne, M.N[l], M.N[l + 1], x[l + 1], x[l], M.I[l], c->st) != 0)
+      return fail(c, IMEX_EINVAL, "p-multigrid: unsupported level pair");
+    TRY(pmg_smooth<T>(c, l, M.pre, lm[l], M.ratio, true, b[l], x[l]));
+  }
+  return cuda_check(c, cudaGetLastError(), "pmg_vcycle");
+}
+
 // ---- solves ------------------------------------------------------------------------
 // Poisson: L psi = b (b is overwritten by its mean-free part); psi: initial guess in, solution out
 imex_status solve_poisson(imex_ctx* c, double* b, double* psi, long long* iters, double* res) {
@@ -867,13 +1138,18 @@ imex_status solve_poisson(imex_ctx* c, double* b, double* psi, long long* iters,
   }
   // the diagonal buffers are shared with the Helmholtz solves: recompute if clobbered
   const double tol = c->desc.tol;
+  const bool pm = c->pmg.kind == IMEX_PRECOND_PMG && c->desc.poisson == IMEX_POISSON_SIPG;
+  if (pm) {
+    if (c->desc.precision != IMEX_FP64) TRY(pmg_alloc<float>(c));
+    TRY(pmg_setup(c));
+  }
   if (c->desc.precision == IMEX_FP64) {
     auto op = [&](const double* x, double* y) { return apply_pressure<double>(c, x, y, c->tmp); };
     auto opd = [&](const double* x, double* y, const CgScalars* d) {
       return apply_pressure<double>(c, x, y, c->tmp, d);
     };
     const bool fused = c->desc.poisson == IMEX_POISSON_SIPG && !c->batched;
-    imex_status s = pcg(c, c->segp, op, opd, fused, b, psi, c->cdiag, tol, c->desc.maxit, true, {1}, iters, res);
+    imex_status s = pcg(c, c->segp, op, opd, fused, b, psi, c->cdiag, tol, c->desc.maxit, true, {1}, iters, res, pm);
     seg_remove_wmean(psi, c->mass_p, c->segp.t, c->cg_d + 6 * m, c->seg_partial, c->counters + 3, c->st);
     return s;
   }
@@ -885,7 +1161,8 @@ imex_status solve_poisson(imex_ctx* c, double* b, double* psi, long long* iters,
     return apply_pressure<float>(c, x, y, c->fvtmp, d);
   };
   const bool fused = c->desc.poisson == IMEX_POISSON_SIPG && !c->batched;
-  TRY(pcg_mixed(c, c->segp, op64, op32, op32d, fused, b, psi, c->fdiag, tol, c->desc.maxit, true, {1}, iters, res));
+  TRY(pcg_mixed(c, c->segp, op64, op32, op32d, fused, b, psi, c->fdiag, tol, c->desc.maxit, true, {1}, iters, res,
+                pm));
   seg_remove_wmean(psi, c->mass_p, c->segp.t, c->cg_d + 6 * m, c->seg_partial, c->counters + 3, c->st);
   return IMEX_OK;
 }
@@ -1501,6 +1778,7 @@ imex_status set_layout(imex_ctx* c) {
   TRY(launch_check(c, sipg_diag<double>(c->gp, c->Np, b, c->st), "mass(p)"));
   c->diag_valid_p = false;
   c->kdiag_valid = false;
+  c->pmg.ready = false;
   CK(cudaStreamSynchronize(c->st), "sync");
   for (auto& gr : c->graphs) cudaGraphExecDestroy(gr.exec);
   c->graphs.clear();
@@ -1627,6 +1905,9 @@ bool same_group(const imex_ctx* a, const imex_ctx* b) {
   if (a->desc.tol != b->desc.tol || a->desc.maxit != b->desc.maxit || a->desc.vmax != b->desc.vmax) return false;
   if (a->nu_kind != b->nu_kind || a->bc_kind != b->bc_kind || a->f_kind != b->f_kind) return false;
   if (a->use_sdc || b->use_sdc) return false;
+  if (a->pmg.kind != b->pmg.kind || a->pmg.pre != b->pmg.pre || a->pmg.coarse != b->pmg.coarse ||
+      a->pmg.ratio != b->pmg.ratio || a->pmg.cratio != b->pmg.cratio)
+    return false;
   return std::memcmp(&a->tab, &b->tab, sizeof(Tab)) == 0;
 }
 
@@ -1644,6 +1925,11 @@ imex_status create_union(const std::vector<imex_ctx*>& src, imex_ctx** out) {
   c->Np = s0->Np;
   c->batched = true;
   c->tab = s0->tab;
+  c->pmg.kind = s0->pmg.kind;
+  c->pmg.pre = s0->pmg.pre;
+  c->pmg.coarse = s0->pmg.coarse;
+  c->pmg.ratio = s0->pmg.ratio;
+  c->pmg.cratio = s0->pmg.cratio;
   c->nu_kind = s0->nu_kind;
   c->bc_kind = s0->bc_kind;
   c->f_kind = s0->f_kind;
@@ -2307,6 +2593,63 @@ imex_status imex_reduce(imex_ctx* c, int op, const double* x, const double* y, l
   CK(cudaStreamSynchronize(c->st), "sync");
   *out = c->hscal[64];
   return IMEX_OK;
+}
+
+imex_status imex_set_pressure_precond(imex_ctx* c, int kind, const double* p, int np) {
+  if (!c || (kind != IMEX_PRECOND_JACOBI && kind != IMEX_PRECOND_PMG) || np < 0 || np > 4 || (np > 0 && !p))
+    return IMEX_EINVAL;
+  imex_ctx::Pmg& M = c->pmg;
+  int pre = M.pre, coarse = M.coarse;
+  double ratio = M.ratio, cratio = M.cratio;
+  if (np > 0) pre = (int)p[0];
+  if (np > 1) coarse = (int)p[1];
+  if (np > 2) ratio = p[2];
+  if (np > 3) cratio = p[3];
+  if (pre < 1 || pre > 16 || coarse < 1 || coarse > 64 || !(ratio > 1.0) || !(cratio > 1.0))
+    return fail(c, IMEX_EINVAL, "bad p-multigrid parameters");
+  M.kind = kind;
+  M.pre = pre;
+  M.coarse = coarse;
+  M.ratio = ratio;
+  M.cratio = cratio;
+  for (auto& gr : c->graphs) cudaGraphExecDestroy(gr.exec);      // captured V-cycles change
+  c->graphs.clear();
+  return IMEX_OK;
+}
+
+imex_status imex_pmg_info(imex_ctx* c, int* nlev, int* N, double* lmax) {
+  if (!c) return IMEX_EINVAL;
+  TRY(pmg_setup(c));
+  if (nlev) *nlev = c->pmg.nlev;
+  for (int l = 0; l < c->pmg.nlev; ++l) {
+    if (N) N[l] = c->pmg.N[l];
+    if (lmax) lmax[l] = c->pmg.lmax[l];
+  }
+  return IMEX_OK;
+}
+
+imex_status imex_op_pmg_vcycle(imex_ctx* c, const double* r, double* z, const double* lmax, int arith,
+                               int on_device) {
+  if (!c || !r || !z || (arith != IMEX_ARITH_FP64 && arith != IMEX_ARITH_FP32)) return IMEX_EINVAL;
+  TRY(pmg_setup(c));
+  imex_ctx::Pmg& M = c->pmg;
+  double lm[4];
+  for (int l = 0; l < M.nlev; ++l) {
+    lm[l] = lmax ? lmax[l] : M.lmax[l];
+    if (!(lm[l] > 0.0)) return fail(c, IMEX_EINVAL, "bad lmax");
+  }
+  TRY(copy_in(c, c->bp, r, c->np, on_device));
+  if (arith == IMEX_ARITH_FP64) {
+    TRY(pmg_vcycle<double>(c, c->bp, c->psi_f, lm));
+  } else {
+    TRY(pmg_alloc<float>(c));
+    for (int l = 0; l < M.nlev; ++l)
+      convert_d2f(M.dinv64[l], M.dinv32[l], (size_t)c->gp.ne * ipow(M.N[l], c->d), c->st);
+    convert_d2f(c->bp, c->fr, c->np, c->st);
+    TRY(pmg_vcycle<float>(c, c->fr, c->fx, lm));
+    f2d(c->fx, c->psi_f, c->np, c->st);
+  }
+  return copy_out(c, z, c->psi_f, c->np, on_device);
 }
 
 imex_status imex_profile(imex_ctx* c, int enable) {

@@ -543,7 +543,93 @@ seg_sub_kernel(double* __restrict__ x, SegTable t, const double* __restrict__ me
   for (int i = threadIdx.x; i < c.n; i += CG_THREADS) x[c.off + i] -= m;
 }
 
+// ---- CG with a general preconditioner (see vec.h) --------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(CG_THREADS)
+seg_rproj_kernel(T* __restrict__ r, SegTable t, CgScalars sc) {
+  const SegBlock c = chunk_of(t);
+  if (sc.done[c.s] != 0) return;
+  const T rm = pick<T>(sc.rmean, sc.rmean_f, c.s);
+  T* rs = r + c.off;
+  for (int i = threadIdx.x; i < c.n; i += CG_THREADS) rs[i] -= rm;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(CG_THREADS)
+seg_rz_kernel(const T* __restrict__ r, const T* __restrict__ z, SegTable t, CgScalars sc,
+              double* __restrict__ partial, unsigned int* __restrict__ counter, int init) {
+  const SegBlock c = chunk_of(t);
+  T acc[2] = {T(0), T(0)};                      // (r, z), sum z
+  if (sc.done[c.s] == 0) {
+    const T* rs = r + c.off;
+    const T* zs = z + c.off;
+    for (int i = threadIdx.x; i < c.n; i += CG_THREADS) {
+      const T zi = zs[i];
+      acc[0] += rs[i] * zi;
+      acc[1] += zi;
+    }
+  }
+  double bs[2];
+  block_sum_k<T, 2>(acc, bs);
+  if (threadIdx.x == 0) {
+    partial[blockIdx.x] = bs[0];
+    partial[(size_t)t.nblk + blockIdx.x] = bs[1];
+  }
+  if (!last_block(counter)) return;
+  seg_totals<2>(t, partial, [&](int q, const double* tot) {
+    if (sc.done[q] != 0) return;
+    // r is mean-free for projected systems, so (r, z - mean z) = (r, z)
+    const double rz = tot[0];
+    const double zm = sc.project ? tot[1] / (double)t.len[q] : 0.0;
+    sc.rz[q] = rz;
+    sc.zmean[q] = zm;
+    sc.zmean_f[q] = (float)zm;
+    if (!init) {
+      const double bt = sc.rz_old[q] != 0.0 ? rz / sc.rz_old[q] : 0.0;
+      sc.beta[q] = bt;
+      sc.beta_f[q] = (float)bt;
+      if (!isfinite(bt)) sc.done[q] = 2;
+    }
+    if (rz != rz) sc.done[q] = 2;
+  });
+  if (threadIdx.x == 0) *counter = 0u;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(CG_THREADS)
+seg_pz_kernel(T* __restrict__ p, const T* __restrict__ z, SegTable t, CgScalars sc, int restart) {
+  const SegBlock c = chunk_of(t);
+  if (sc.done[c.s] != 0) return;
+  const T beta = restart ? T(0) : pick<T>(sc.beta, sc.beta_f, c.s);
+  const T zm = pick<T>(sc.zmean, sc.zmean_f, c.s);
+  T* ps = p + c.off;
+  const T* zs = z + c.off;
+  for (int i = threadIdx.x; i < c.n; i += CG_THREADS) ps[i] = restart ? zs[i] - zm : (zs[i] - zm) + beta * ps[i];
+}
+
 }  // namespace
+
+template <typename T>
+void seg_rproj(T* r, const SegTable& t, const CgScalars& sc, cudaStream_t st) {
+  IMEX_COUNTED(seg_rproj_kernel<T><<<t.nblk, CG_THREADS, 0, st>>>(r, t, sc));
+}
+template <typename T>
+void seg_rz(const T* r, const T* z, const SegTable& t, const CgScalars& sc, double* partial, unsigned int* counter,
+            int init, cudaStream_t st) {
+  IMEX_COUNTED(seg_rz_kernel<T><<<t.nblk, CG_THREADS, 0, st>>>(r, z, t, sc, partial, counter, init));
+}
+template <typename T>
+void seg_pz(T* p, const T* z, const SegTable& t, const CgScalars& sc, int restart, cudaStream_t st) {
+  IMEX_COUNTED(seg_pz_kernel<T><<<t.nblk, CG_THREADS, 0, st>>>(p, z, t, sc, restart));
+}
+template void seg_rproj<float>(float*, const SegTable&, const CgScalars&, cudaStream_t);
+template void seg_rproj<double>(double*, const SegTable&, const CgScalars&, cudaStream_t);
+template void seg_rz<float>(const float*, const float*, const SegTable&, const CgScalars&, double*, unsigned int*,
+                            int, cudaStream_t);
+template void seg_rz<double>(const double*, const double*, const SegTable&, const CgScalars&, double*,
+                             unsigned int*, int, cudaStream_t);
+template void seg_pz<float>(float*, const float*, const SegTable&, const CgScalars&, int, cudaStream_t);
+template void seg_pz<double>(double*, const double*, const SegTable&, const CgScalars&, int, cudaStream_t);
 
 template <typename T>
 void seg_step_xr(T* x, T* r, const T* p, const T* Ap, const T* dinv, const SegTable& t, const CgScalars& sc,

@@ -375,7 +375,9 @@ sipg3_apply_kernel(Geom g, SipgArgs<T> a) {
   if (valid) gl = local_geom(g, e, el);
   int ec[3] = {0, 0, 0};
   if (valid) elem_coords(gl, el, ec);
-  if (valid && t < 6) snb[le][t] = neighbor(gl, ec, t >> 1, (t & 1) ? 1 : -1);
+  // six neighbours per element: with N = 2 an element has only four threads
+  if (valid)
+    for (int f = t; f < 6; f += NN) snb[le][f] = neighbor(gl, ec, f >> 1, (f & 1) ? 1 : -1);
   __syncthreads();
 
   const T hx = T(2) / geom_h<T>(gl, 0), hy = T(2) / geom_h<T>(gl, 1), hz = T(2) / geom_h<T>(gl, 2);
@@ -581,7 +583,9 @@ sipg3c_apply_kernel(Geom g, SipgArgs<T> a) {
   if (valid) gl = local_geom(g, e, el);
   int ec[3] = {0, 0, 0};
   if (valid) elem_coords(gl, el, ec);
-  if (valid && t < 6) snb[le][t] = neighbor(gl, ec, t >> 1, (t & 1) ? 1 : -1);
+  // six neighbours per element: with N = 2 an element has only four threads
+  if (valid)
+    for (int f = t; f < 6; f += NN) snb[le][f] = neighbor(gl, ec, f >> 1, (f & 1) ? 1 : -1);
   __syncthreads();
   int kind[6];
 #pragma unroll

@@ -167,6 +167,29 @@ void kx_combine(double* y, const double* x, const double* m, const double* kx, d
 void helm_diag(double* d, const double* m, const double* k, double gamma, const double* edt, long long nd, size_t n,
                cudaStream_t st);
 
+// ---- p-multigrid (k_pmg.cu) -----------------------------------------------------
+// 1D interpolation between two levels, m[i * NC + j] = l_j(x_i) (NF x NC)
+struct Interp1D {
+  double m[IMEX_MAXN * IMEX_MAXN];
+};
+// xf += P xc over ne elements (element-local tensor-product interpolation NC -> NF points);
+// -1 for an unsupported (NF, NC) pair (nothing launched)
+template <typename T>
+int pmg_prolong(int d, int ne, int NF, int NC, const T* xc, T* xf, const Interp1D& I, cudaStream_t st);
+// rc = P^T (bf - axf): restriction of the fine residual
+template <typename T>
+int pmg_restrict(int d, int ne, int NF, int NC, const T* bf, const T* axf, T* rc, const Interp1D& I, cudaStream_t st);
+// Chebyshev smoother steps: first  r = b - ax (ax may be null: r = b), d = c0 D^{-1} r,
+// x = (add ? x : 0) + d;  next  r -= ad, d = c1 d + c2 D^{-1} r, x += d (last: r, d not stored)
+template <typename T>
+void cheb_first(T* x, T* d, T* r, const T* b, const T* ax, const T* dinv, double c0, size_t n, int add,
+                cudaStream_t st);
+template <typename T>
+void cheb_next(T* x, T* d, T* r, const T* ad, const T* dinv, double c1, double c2, size_t n, int last,
+               cudaStream_t st);
+// y = s a b elementwise
+void vec_mul(double* y, const double* a, const double* b, double s, size_t n, cudaStream_t st);
+
 // ---- pointwise fields (k_fields.cu) --------------------------------------------
 // what: 0 velocity of a closed-form flow (d components), 1 viscosity (1 component),
 //       2 forcing (d components).  kind / p: the flow, viscosity law or forcing and its

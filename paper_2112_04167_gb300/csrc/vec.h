@@ -81,6 +81,18 @@ void seg_init(const T* r, const T* dinv, const SegTable& t, const CgScalars& sc,
               unsigned int* counter, int reset, cudaStream_t st);
 void seg_remove_mean(double* x, const SegTable& t, double* mean, double* partial, unsigned int* counter,
                      cudaStream_t st);
+// CG with a general preconditioner z = B r (the p-multigrid V-cycle).  The step kernel runs
+// with a unit diagonal (it yields alpha, x, r, (r, r), the mean of r and the convergence
+// test); then, for the running systems of projected problems, r -= mean(r) (seg_rproj);
+// z = B r; seg_rz forms (r, z), the mean of z and beta = (r, z) / (r, z)_old (init = 1: the
+// first residual of a cycle, no beta); seg_pz sets p = z - mean(z) + beta p (restart: beta 0).
+template <typename T>
+void seg_rproj(T* r, const SegTable& t, const CgScalars& sc, cudaStream_t st);
+template <typename T>
+void seg_rz(const T* r, const T* z, const SegTable& t, const CgScalars& sc, double* partial, unsigned int* counter,
+            int init, cudaStream_t st);
+template <typename T>
+void seg_pz(T* p, const T* z, const SegTable& t, const CgScalars& sc, int restart, cudaStream_t st);
 // x -= (sum w x / sum w) per segment; w indexed like the Jacobi diagonal (doff)
 void seg_remove_wmean(double* x, const double* w, const SegTable& t, double* mean, double* partial,
                       unsigned int* counter, cudaStream_t st);

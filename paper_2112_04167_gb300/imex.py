@@ -21,6 +21,7 @@ NU_CONST, NU_VARXYT, NU_VELOCITY, NU_FIELD = 0, 1, 2, 3
 FORCE_NONE, FORCE_TGTRAVEL_VARNU = 0, 1
 SPACE_VELOCITY, SPACE_PRESSURE = 0, 1
 ARITH_FP64, ARITH_FP32, ARITH_FF = 0, 1, 3
+PRECOND_JACOBI, PRECOND_PMG = 0, 1
 _STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ENOTCONV", 4: "EUNSTABLE", 5: "ECUDA"}
 
 
@@ -102,6 +103,9 @@ _SIGS = {
     "imex_op_conv": [_P, _P, _P, _P, C.c_int, C.c_int],
     "imex_op_graddiv": [_P, _P, _P, _P, _P, C.c_int, C.c_int],
     "imex_solve_poisson": [_P, _P, _P, C.c_int],
+    "imex_set_pressure_precond": [_P, C.c_int, _P, C.c_int],
+    "imex_pmg_info": [_P, C.POINTER(C.c_int), C.POINTER(C.c_int), _D],
+    "imex_op_pmg_vcycle": [_P, _P, _P, _P, C.c_int, C.c_int],
     "imex_solve_helmholtz": [_P, _P, _P, C.c_double, _P, _P, C.c_int],
     "imex_eval_field": [_P, C.c_int, C.c_int, _P, C.c_int, C.c_double, _P, _P, C.c_int],
     "imex_reduce": [_P, C.c_int, _P, _P, C.c_longlong, _D, C.c_int],
@@ -370,6 +374,26 @@ class Context:
         p2, _, _d = _arr(fd2, self.dim * self.nvel, writable=True) if with_fd2 else (None, 0, None)
         self._check(load().imex_op_graddiv(self._h, pv, pn, p3, p2, arith, 0))
         return (fd3, fd2) if with_fd2 else fd3
+
+    def set_pressure_precond(self, kind, params=()):
+        p, n, _k = _params(params)
+        self._check(load().imex_set_pressure_precond(self._h, kind, p, n))
+
+    def pmg_info(self):
+        """(N per level, Chebyshev upper bounds per level) of the pressure V-cycle."""
+        nl = C.c_int()
+        N = (C.c_int * 4)()
+        lm = (C.c_double * 4)()
+        self._check(load().imex_pmg_info(self._h, C.byref(nl), N, lm))
+        return list(N[:nl.value]), list(lm[:nl.value])
+
+    def op_pmg_vcycle(self, r, lmax=None, arith=ARITH_FP64):
+        out = np.empty(self.npres)
+        pr, dev, _a = _arr(r, self.npres)
+        pl, _, _b = _params(lmax)
+        po, _, _c = _arr(out, self.npres, writable=True)
+        self._check(load().imex_op_pmg_vcycle(self._h, pr, po, pl, arith, dev))
+        return out
 
     def solve_poisson(self, b):
         out = np.empty(self.npres)

@@ -241,3 +241,15 @@ def test_sipg_pressure_periodic_fp32(case):
     assert rel(ctx.op_sipg(x, space=imex.SPACE_PRESSURE, precision=imex.MIXED), L @ x) < 1e-5
     y = ctx.op_sipg(x, space=imex.SPACE_PRESSURE, alpha=0.3, beta=1.7, minv=1, precision=imex.MIXED)
     assert rel(y, (0.3 * M * x + 1.7 * (L @ x)) / M) < 1e-5
+
+
+@pytest.mark.parametrize("case", [(3, 2, (3, 2, 2), (True, False, False)), (3, 2, (2, 3, 2), (False, True, True)),
+                                  (3, 2, (2, 2, 3), (False, False, False))])
+def test_sipg_pressure_two_points_3d(case):
+    """P = 2 (pressure degree 1, N = 2 points: four threads per element in the constant-
+    viscosity 3D kernel, fewer than the element's six neighbours) with non-periodic sides."""
+    ctx, mesh = make(case)
+    x = inputs.field(ctx.npres, seed=24)
+    L = dg.sipg_matrix(mesh, 2, 1.0, dirichlet=False)
+    assert rel(ctx.op_sipg(x, space=imex.SPACE_PRESSURE), L @ x) < 1e-12
+    assert rel(ctx.op_sipg(x, space=imex.SPACE_PRESSURE, precision=imex.MIXED), L @ x) < 1e-5
