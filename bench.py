@@ -42,15 +42,17 @@ def parse():
     ap.add_argument("--dt", type=float, default=0.01)
     ap.add_argument("--tol", type=float, default=1e-10)
     ap.add_argument("--fp64-steps", type=int, default=2)
-    ap.add_argument("--precond", default="jacobi", choices=["jacobi", "pmg"],
+    ap.add_argument("--precond", default="pmg", choices=["jacobi", "pmg"],
                     help="preconditioner of the pressure solves")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-only", action="store_true", help="short run for ncu captures")
-    ap.add_argument("--workload", default="tg3d", choices=["tg3d", "ensemble", "serving"],
-                    help="tg3d: the headline line; ensemble / serving: that workload alone")
+    ap.add_argument("--workload", default="tg3d", choices=["tg3d", "ensemble", "serving", "ops"],
+                    help="tg3d: the headline line; ensemble / serving / ops: that workload alone")
     ap.add_argument("--serving-requests", type=int, default=24,
                     help="requests of the serving stream replayed inside the headline line (0: skip)")
+    ap.add_argument("--ops-nelem", type=int, default=40,
+                    help="elements per direction of the above-L2 operator timing run (0: skip)")
     ap.add_argument("--ensemble-steps", type=int, default=3,
                     help="timed steps of the 256-instance ensemble reported inside the headline line (0: skip)")
     return ap.parse_args()
@@ -63,6 +65,110 @@ def peaks():
             d = json.load(f)
         return d.get("hbm_gbs", 6800.0), "measured"
     return 6800.0, "fallback"
+
+
+# ----------------------------------------------------------------------------- rooflines
+# ncu dram__bytes_read.sum + dram__bytes_write.sum per launch of the dominant kernel class of
+# the headline step, keyed by (elements per direction, P, preconditioner); filled from the
+# capture summarised under profiles/ for the current kernel version
+NCU_TRAFFIC = {}
+# ALU peaks: FP32 (non-tensor) from 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz; FP64 the
+# nominal GB300 rate.  Float-float flops are counted as FP64-equivalent operations and set
+# against the FP64 rate they replace.
+FP32_PEAK_GFLOPS = 152 * 128 * 2 * 2.07
+FP64_PEAK_GFLOPS = 1250.0
+ARITH = {0: "fp64", 1: "fp32", 3: "ff"}
+
+
+def operator_table(imex, ctx, hbm):
+    """Per profiled kernel class: launches, CUDA-event time, algorithmic bytes and flops per
+    launch, achieved GB/s against the measured HBM copy bandwidth and GFLOP/s against the ALU
+    peak of the class's arithmetic."""
+    rows = {}
+    for cls, name in enumerate(imex.PROF_NAMES):
+        n, ms = ctx.profile_read(cls)
+        if not n or ms <= 0:
+            continue
+        b, f, a = ctx.profile_work(cls)
+        sec = ms * 1e-3
+        peak = FP32_PEAK_GFLOPS if a == 1 else FP64_PEAK_GFLOPS
+        row = {"launches": n, "total_ms": ms, "avg_us": 1e3 * ms / n, "arith": ARITH.get(a),
+               "bytes_per_launch": b / n, "gbs": b / sec / 1e9, "hbm_frac": b / sec / 1e9 / hbm,
+               "flops_per_launch": f / n if f else None}
+        if f:
+            row.update({"gflops": f / sec / 1e9, "alu_peak_gflops": peak, "alu_frac": f / sec / 1e9 / peak})
+        rows[name] = row
+    return rows
+
+
+def roofline_of(rows, hbm, src, traffic=None):
+    """Roofline entry of the kernel class with the largest total time: bound by whichever of
+    HBM bandwidth and ALU rate it uses the larger fraction of."""
+    if not rows:
+        return None
+    dom = max(rows, key=lambda k: rows[k]["total_ms"])
+    r = rows[dom]
+    alu = r.get("alu_frac") or 0.0
+    if r["hbm_frac"] >= alu:
+        out = {"bound": "hbm", "kernel": dom, "achieved": r["gbs"], "peak": hbm, "unit": "GB/s",
+               "frac": r["hbm_frac"], "peak_source": src}
+    else:
+        out = {"bound": "alu", "kernel": dom, "achieved": r["gflops"], "peak": r["alu_peak_gflops"],
+               "unit": "GFLOP/s", "frac": alu,
+               "peak_source": "FP32 152 SMs x 128 lanes x 2 x 2.07 GHz" if r["arith"] == "fp32"
+               else "nominal FP64 1.25 TFLOP/s (float-float: FP64-equivalent flops)"}
+    out.update({"traffic": traffic, "bytes_per_launch": r["bytes_per_launch"], "avg_launch_us": r["avg_us"],
+                "arith": r["arith"], "share_of_profiled_ms": r["total_ms"] / sum(x["total_ms"] for x in rows.values())})
+    return out
+
+
+def run_operators(imex, torch, nelem, P, reps=5):
+    """Each operator kernel timed alone on the device (CUDA events around the kernel, inputs
+    resident) on a 3D periodic nelem^3 mesh at degree P: the SIPG applies of both spaces in
+    FP32, FP64 and float-float, the convection, divergence, gradient and grad-div derivatives,
+    and one mixed Poisson solve (CG step and direction kernels, V-cycle)."""
+    ctx = imex.Context(3, P, (nelem,) * 3, [0, 0, 0], [TWO_PI] * 3, (1, 1, 1), precision=imex.MIXED, tol=1e-10,
+                       maxit=20000)
+    ctx.set_viscosity_const(1.0 / 1600.0)
+    dev = torch.device("cuda")
+    g = torch.Generator(device=dev).manual_seed(0)
+    xp = torch.randn(ctx.npres, dtype=torch.float64, device=dev, generator=g)
+    xv = torch.randn(3 * ctx.nvel, dtype=torch.float64, device=dev, generator=g)
+    ctx.op_sipg(xp, space=imex.SPACE_PRESSURE, precision=imex.ARITH_FP32)      # warm-up
+    torch.cuda.synchronize()
+    ctx.profile(True)
+    for _ in range(reps):
+        ctx.op_sipg(xp, space=imex.SPACE_PRESSURE, precision=imex.ARITH_FP32)
+        ctx.op_sipg(xv, nsys=3, alpha=1.0, beta=0.01, precision=imex.ARITH_FP32)
+    tab32 = operator_table(imex, ctx, peaks()[0])
+    ctx.profile(True)
+    for _ in range(2):
+        ctx.op_sipg(xp, space=imex.SPACE_PRESSURE, precision=imex.ARITH_FF)
+        ctx.op_sipg(xv, nsys=3, alpha=1.0, beta=0.01, precision=imex.ARITH_FF)
+        ctx.op_conv(xv, arith=imex.ARITH_FF)
+        ctx.op_div(xv, arith=imex.ARITH_FF)
+        ctx.op_grad(xp, arith=imex.ARITH_FF)
+        ctx.op_graddiv(xv, arith=imex.ARITH_FF)
+    tabff = operator_table(imex, ctx, peaks()[0])
+    ctx.profile(True)
+    ctx.op_sipg(xp, space=imex.SPACE_PRESSURE, precision=imex.ARITH_FP64)
+    ctx.op_conv(xv, arith=imex.ARITH_FP32)
+    tab64 = operator_table(imex, ctx, peaks()[0])
+    ctx.profile(True)
+    b = torch.randn(ctx.npres, dtype=torch.float64, device=dev, generator=g)
+    ctx.solve_poisson(b)
+    tabcg = operator_table(imex, ctx, peaks()[0])
+    its = ctx.stats()["poisson_iters"]
+    ctx.profile(False)
+    ctx.close()
+    out = {}
+    for suffix, t in (("f32", tab32), ("ff", tabff), ("", tab64), ("solve", tabcg)):
+        for k, v in t.items():
+            out[f"{k}_{v['arith']}" if suffix != "solve" else f"{k}_{v['arith']}_in_solve"] = v
+    return {"mesh": f"3D periodic {nelem}^3 hex, P={P}", "pressure_nodes": nelem ** 3 * P ** 3,
+            "velocity_nodes": nelem ** 3 * (P + 1) ** 3, "poisson_iters": its,
+            "l2": "FP32 pressure vector {:.0f} MB, FP64 velocity field {:.0f} MB (L2 129 MB)".format(
+                4e-6 * nelem ** 3 * P ** 3, 24e-6 * nelem ** 3 * (P + 1) ** 3), "operators": out}
 
 
 # ----------------------------------------------------------------------------- clocks
@@ -420,6 +526,14 @@ def main():
                           "ensemble": e}))
         return 0
 
+    if args.workload == "ops":
+        e = run_operators(imex, torch, args.ops_nelem or 40, args.P)
+        print(json.dumps({"metric": METRIC, "value": None, "unit": UNIT, "n_gpus": world, "steps": 0,
+                          "warmup": 0, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+                          "vs_baseline": None, "dtype": "per operator", "data": "synthetic (seeded random fields)",
+                          "config": {"workload": e["mesh"]}, "operators_above_l2": e}))
+        return 0
+
     stream = torch.cuda.Stream()
     ctx = make_ctx(imex, args, args.precision, stream.cuda_stream)
     dpp = dof_stages_per_step(ctx)
@@ -455,57 +569,17 @@ def main():
     stats = ctx.stats()
     value = job_value(world, dpp * args.steps, elapsed_ms / 1e3)
 
-    # ---- pass B: per-kernel device time of the operator classes -------------------
+    # ---- pass B: per-kernel-class device time and algorithmic work inside the step -------
     ctx.profile(True)
     ctx.step(args.dt, max(1, min(args.steps, 3)))
     torch.cuda.synchronize()
-    stats_b = ctx.stats()
-    prof = {}
-    names = {imex.PROF_PRESSURE_F32: "sipg_pressure_f32", imex.PROF_PRESSURE_F64: "sipg_pressure_f64",
-             imex.PROF_HELMHOLTZ_F32: "sipg_helmholtz_f32", imex.PROF_HELMHOLTZ_F64: "sipg_helmholtz_f64",
-             imex.PROF_CONV: "conv_f64", imex.PROF_PCG_PERSIST: "pcg_persist_f32"}
-    for cls, nm in names.items():
-        n, ms = ctx.profile_read(cls)
-        prof[nm] = {"launches": n, "total_ms": ms, "avg_us": (1e3 * ms / n) if n else None}
-    ctx.profile(False)
-
     hbm, src = peaks()
-    npres = ctx.npres
+    prof = operator_table(imex, ctx, hbm)
+    ctx.profile(False)
+    # DRAM bytes per launch of the dominant kernel from the ncu capture of this workload
+    # summarised under profiles/ (None when that kernel has changed since the capture)
+    roof = roofline_of(prof, hbm, src, traffic=NCU_TRAFFIC.get((args.nelem, args.P, args.precond)))
     nvel = ctx.nvel
-    # algorithmic bytes per launch: read x, write y per node (constant nu, no data term)
-    bytes_per = {"sipg_pressure_f32": 8 * npres, "sipg_pressure_f64": 16 * npres,
-                 "sipg_helmholtz_f32": 8 * 3 * nvel, "sipg_helmholtz_f64": 16 * 3 * nvel}
-    dom = max(prof, key=lambda k: prof[k]["total_ms"])
-    roof = None
-    pers = prof["pcg_persist_f32"]
-    if pers["launches"] and stats_b["poisson_iters"]:
-        # persistent FP32 pressure CG: one iteration = apply (read p, write A p: 8 B/node) +
-        # step (read r, A p, D^-1, y, p; write y, r: 28 B) + direction (read r, D^-1, p; write r, p: 20 B)
-        its = stats_b["poisson_iters"]
-        per_it_s = pers["total_ms"] * 1e-3 / its
-        bytes_it = 56 * npres
-        ach = bytes_it / per_it_s / 1e9
-        roof = {"bound": "hbm", "kernel": "pcg_persist_f32 (one CG iteration)", "achieved": ach, "peak": hbm,
-                "unit": "GB/s", "frac": ach / hbm, "traffic": None, "peak_source": src,
-                "bytes_per_launch": bytes_it, "avg_launch_us": per_it_s * 1e6, "iterations": its,
-                "note": "per CG iteration (many iterations per launch); its vectors are L2-resident at this size"}
-    elif dom in bytes_per and prof[dom]["launches"]:
-        # DRAM bytes per launch from the ncu capture summarised in
-        # profiles/sipg3p_apply_f32_tg3d_16cube_p7.md (this workload, this kernel version)
-        traffic = {"sipg_pressure_f32": 5660928}.get(dom) if args.nelem == 16 and args.P == 7 else None
-        avg_s = prof[dom]["avg_us"] * 1e-6
-        ach = bytes_per[dom] / avg_s / 1e9
-        roof = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": hbm, "unit": "GB/s",
-                "frac": ach / hbm, "traffic": traffic, "peak_source": src,
-                "bytes_per_launch": bytes_per[dom], "avg_launch_us": prof[dom]["avg_us"]}
-    else:
-        # FP64 ALU-bound kernels: flops per launch vs the nominal FP64 rate
-        flops = {"conv_f64": None, "sipg_pressure_f64": 84 * npres}.get(dom)
-        roof = {"bound": "alu", "kernel": dom, "achieved": None, "peak": 1250.0, "unit": "GFLOP/s",
-                "frac": None, "traffic": None, "peak_source": "nominal FP64 1.25 TFLOP/s"}
-        if flops and prof[dom]["launches"]:
-            ach = flops / (prof[dom]["avg_us"] * 1e-6) / 1e9
-            roof.update({"achieved": ach, "frac": ach / 1250.0})
 
     # ---- e2e: through the C ABI with host buffers ------------------------------
     e2e = None
@@ -568,6 +642,10 @@ def main():
     if args.serving_requests > 0 and rank == 0:
         serving = run_serving(imex, args.serving_requests, precision=args.precision)
 
+    ops = None
+    if args.ops_nelem > 0 and rank == 0:
+        ops = run_operators(imex, torch, args.ops_nelem, args.P)
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu, err = cpu_baseline_sample(args.P, args.dt, nsteps=3)
@@ -583,7 +661,8 @@ def main():
             "dtype": "f32 operators + f64 refinement" if args.precision == "mixed" else "f64",
             "data": "synthetic (closed-form Taylor-Green initial field)",
             "config": {"workload": f"3D Taylor-Green transition, [0,2pi]^3 periodic, {n}^3 hex, P={args.P} "
-                                   f"(pressure P-1), Re=1600, RK-CB3e, dt={args.dt}, solver tol {args.tol}",
+                                   f"(pressure P-1), Re=1600, RK-CB3e, dt={args.dt}, tol {args.tol}, "
+                                   f"{args.precond} pressure",
                        "dof_per_instance": 3 * nvel, "stages_per_step": 3,
                        "l2": "working set per step > L2 (stage buffers ~1 GB)",
                        "parallelism": f"replicas x{world}"},
@@ -591,6 +670,7 @@ def main():
             "p99_step_ms": sorted(per_step)[min(len(per_step) - 1, int(0.99 * len(per_step)))],
             "clocks": clocks, "gpu_launches": launches, "roofline": roof, "kernels": prof,
             "e2e": e2e, "fp64": fp64, "cpu_baseline": cpu, "ensemble": ens, "serving": serving,
+            "operators_above_l2": ops,
             "solver": {"poisson_iters_per_call": stats["poisson_iters"], "helmholtz_iters": stats["helmholtz_iters"],
                        "refinements": stats["refinements"], "max_poisson_res": stats["max_poisson_res"],
                        "max_helmholtz_res": stats["max_helmholtz_res"]},

@@ -179,7 +179,8 @@ imex_status imex_op_graddiv(imex_ctx* ctx, const double* v, const double* nu, do
    accelerated Jacobi smoothing before and after each coarse correction and a fixed
    Chebyshev polynomial on the degree-1 level.  params (nparams <= 4, optional): smoothing
    steps (default 3), steps on the coarsest level (10), smoothing range lmax / lmin (10),
-   coarsest range (100).  The IMEX_POISSON_CONSISTENT operator always uses Jacobi.
+   coarsest range (100).  Default: IMEX_PRECOND_PMG.  The IMEX_POISSON_CONSISTENT operator
+   always uses Jacobi.
    IMEX_EINVAL for an unknown kind or parameters out of range. */
 enum { IMEX_PRECOND_JACOBI = 0, IMEX_PRECOND_PMG = 1 };
 imex_status imex_set_pressure_precond(imex_ctx* ctx, int kind, const double* params, int nparams);
@@ -233,19 +234,28 @@ imex_status imex_reduce_noalloc(int op, const double* x, const double* y, long l
 
 /* ---- instrumentation ---------------------------------------------------------------- */
 
-/* kernel classes timed by imex_profile: the operator applies inside the CG solves
-   (FP32 inner / FP64) and the convection kernel */
+/* kernel classes timed by imex_profile: the operator applies (CG applies of the pressure and
+   Helmholtz solves, FP32 inner / FP64-class), the convection, the p-multigrid V-cycle (level
+   applies; smoother vector updates and transfers), the CG vector kernels (step: x, r and the
+   residual sums; direction: p and the preconditioned-residual scalars), and the projection's
+   divergence and gradient and the grad-div derivatives */
 enum {
   IMEX_PROF_PRESSURE_F32 = 0, IMEX_PROF_PRESSURE_F64 = 1, IMEX_PROF_HELMHOLTZ_F32 = 2,
   IMEX_PROF_HELMHOLTZ_F64 = 3, IMEX_PROF_CONV = 4,
   IMEX_PROF_PCG_PERSIST = 5,   /* persistent FP32 pressure CG launches (many iterations each) */
-  IMEX_PROF_NCLASS = 6
+  IMEX_PROF_PMG_APPLY = 6, IMEX_PROF_PMG_VEC = 7, IMEX_PROF_CG_STEP = 8, IMEX_PROF_CG_DIR = 9,
+  IMEX_PROF_DIV = 10, IMEX_PROF_GRAD = 11, IMEX_PROF_DERIV = 12,
+  IMEX_PROF_NCLASS = 13
 };
 /* enable (1) or disable (0) CUDA-event timing of the classes above on the context's
    stream; enabling resets the accumulated records */
 imex_status imex_profile(imex_ctx* ctx, int enable);
 /* launches and summed device time (ms) of one class since imex_profile(ctx, 1) */
 imex_status imex_profile_read(imex_ctx* ctx, int cls, long long* launches, double* total_ms);
+/* algorithmic work of those launches: bytes (every input read once, every output written
+   once, in the arithmetic's storage type) and floating-point operations (FP64-equivalent for
+   float-float), and the arithmetic (IMEX_ARITH_*) of the last launch (-1: none) */
+imex_status imex_profile_work(imex_ctx* ctx, int cls, double* bytes, double* flops, int* arith);
 /* kernels launched by this library so far, all contexts */
 long long imex_launch_count(void);
 

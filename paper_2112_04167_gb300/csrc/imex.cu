@@ -251,7 +251,7 @@ struct imex_ctx {
   // on the same mesh, the SIPG pressure operator rediscretised on each, Chebyshev-Jacobi
   // smoothing, element-local GLL interpolation between levels
   struct Pmg {
-    int kind = 0;                  // IMEX_PRECOND_JACOBI / IMEX_PRECOND_PMG
+    int kind = IMEX_PRECOND_PMG;   // IMEX_PRECOND_JACOBI / IMEX_PRECOND_PMG
     int pre = 3, coarse = 10;      // smoothing steps (before and after), steps of the coarsest level
     double ratio = 10.0, cratio = 100.0;
     bool alloc64 = false, alloc32 = false, ready = false;
@@ -279,6 +279,8 @@ struct imex_ctx {
     int used = 0;
     long long n = 0;
     double ms = 0.0;
+    double bytes = 0.0, flops = 0.0;   // algorithmic work of the launches (see prof_end)
+    int arith = -1;                    // IMEX_ARITH_* of the last launch
   };
   bool prof = false;
   Prof profc[IMEX_PROF_NCLASS];
@@ -323,6 +325,33 @@ void prof_mark(imex_ctx* c, int cls, bool begin) {
   if (begin && P.used == cap) prof_flush(c, cls);
   cudaEventRecord(P.ev[2 * P.used + (begin ? 0 : 1)], c->st);
   if (!begin) P.used++;
+}
+
+// end of one launch of a timed class with its algorithmic work: the bytes the operation must
+// move (each input read once, each output written once) and its floating-point operations
+void prof_end(imex_ctx* c, int cls, double bytes, double flops, int arith) {
+  if (!c->prof) return;
+  prof_mark(c, cls, false);
+  auto& P = c->profc[cls];
+  P.bytes += bytes;
+  P.flops += flops;
+  P.arith = arith;
+}
+
+// flops per node of the constant-viscosity SIPG apply on N points per direction (line form):
+// per direction N multiply-adds of the element's own line operator row, four of the two
+// neighbours' trace and derivative terms and two (amortised) forming those derivatives; six
+// more to weight and combine the directions
+double sipg_flops_per_node(int d, int N) { return 2.0 * d * (N + 6) + 6.0; }
+
+// flops per element of the over-integrated convection on N points (Q Gauss points per
+// direction): the d components interpolated to the Q^d points and the d^2 flux components
+// differentiated back, each a sum-factorised sequence of d 1D passes
+double conv_flops_per_elem(int d, int N) {
+  const int Q = over_q(N);
+  double pass = 0.0;
+  for (int j = 1; j <= d; ++j) pass += std::pow((double)Q, j) * std::pow((double)N, d + 1 - j);
+  return 2.0 * (d + d * d) * pass;
 }
 
 template <typename T>
@@ -485,6 +514,11 @@ bool ff_class(const imex_ctx* c) {
   return c->desc.precision == IMEX_MIXED || c->desc.precision == IMEX_MIXED_FAST;
 }
 
+// arithmetic of an operator apply of type T on this context (the FP64 applies of the mixed
+// forms run in float-float)
+template <typename T>
+int arith_of(const imex_ctx* c);
+
 // SIPG apply: the FP64 applies of the mixed form (residual replacements, explicit F_d1) use
 // float-float arithmetic on FP64 fields where that kernel exists (periodic 3D, constant
 // viscosity), plain FP64 otherwise; the FP64 form always uses FP64 arithmetic
@@ -495,6 +529,12 @@ int apply_dispatch(imex_ctx* c, const Geom& g, int N, const SipgArgs<T>& a) {
     if (rc == 0) return 0;
   }
   return sipg_apply<T>(g, N, a, c->st);
+}
+
+template <typename T>
+int arith_of(const imex_ctx* c) {
+  if (sizeof(T) == 4) return IMEX_ARITH_FP32;
+  return ff_class(c) ? IMEX_ARITH_FF : IMEX_ARITH_FP64;
 }
 
 // the pressure operator L psi (pressure space), T = double / float
@@ -509,7 +549,7 @@ imex_status apply_pressure(imex_ctx* c, const T* x, T* y, T* vtmp, const CgScala
     skip_stopped_elems(c, a, skip_stopped);
     prof_mark(c, cls, true);
     const int rc = apply_dispatch<T>(c, c->gp, c->Np, a);
-    prof_mark(c, cls, false);
+    prof_end(c, cls, 2.0 * sizeof(T) * c->np, sipg_flops_per_node(c->d, c->Np) * c->np, arith_of<T>(c));
     return launch_check(c, rc, "sipg_apply(p)");
   }
   // consistent: L = B M^{-1} B^T
@@ -531,8 +571,46 @@ imex_status apply_helm(imex_ctx* c, const T* x, T* y, int nsys, const T* nu, dou
   skip_stopped_elems(c, a, skip_stopped);
   prof_mark(c, cls, true);
   const int rc = apply_dispatch<T>(c, c->gv, c->Nv, a);
-  prof_mark(c, cls, false);
+  prof_end(c, cls, sizeof(T) * (double)c->nv * (2.0 * nsys + (nu ? 1.0 : 0.0)),
+           sipg_flops_per_node(c->d, c->Nv) * c->nv * nsys, arith_of<T>(c));
   return launch_check(c, rc, "sipg_apply(v)");
+}
+
+// CG vector kernels of the iteration loop, timed as the CG_STEP / CG_DIR classes (words per
+// node: step reads r, A p, D^-1, x, p and writes x, r; direction reads r, D^-1, p and writes p,
+// and r when projected; the p-multigrid iteration's projection of r 2, (r, z) 2, p = z + beta p 3)
+template <typename T>
+int arith_t() { return sizeof(T) == 4 ? IMEX_ARITH_FP32 : IMEX_ARITH_FP64; }
+template <typename T>
+void cg_step(imex_ctx* c, T* x, T* r, const T* p, const T* Ap, const T* dj, const imex_ctx::Seg& sg,
+             const CgScalars& sc, int maxit) {
+  prof_mark(c, IMEX_PROF_CG_STEP, true);
+  seg_step_xr<T>(x, r, p, Ap, dj, sg.t, sc, maxit, c->seg_partial, c->counters + 1, c->st);
+  prof_end(c, IMEX_PROF_CG_STEP, 7.0 * sizeof(T) * sg.total, 10.0 * sg.total, arith_t<T>());
+}
+template <typename T>
+void cg_dir(imex_ctx* c, T* p, T* r, const T* dinv, const imex_ctx::Seg& sg, const CgScalars& sc, int restart) {
+  prof_mark(c, IMEX_PROF_CG_DIR, true);
+  seg_step_p<T>(p, r, dinv, sg.t, sc, restart, c->st);
+  prof_end(c, IMEX_PROF_CG_DIR, (sc.project ? 5.0 : 4.0) * sizeof(T) * sg.total, 4.0 * sg.total, arith_t<T>());
+}
+template <typename T>
+void cg_rproj(imex_ctx* c, T* r, const imex_ctx::Seg& sg, const CgScalars& sc) {
+  prof_mark(c, IMEX_PROF_CG_DIR, true);
+  seg_rproj<T>(r, sg.t, sc, c->st);
+  prof_end(c, IMEX_PROF_CG_DIR, 2.0 * sizeof(T) * sg.total, 1.0 * sg.total, arith_t<T>());
+}
+template <typename T>
+void cg_rz(imex_ctx* c, const T* r, const T* z, const imex_ctx::Seg& sg, const CgScalars& sc, int init) {
+  prof_mark(c, IMEX_PROF_CG_DIR, true);
+  seg_rz<T>(r, z, sg.t, sc, c->seg_partial, c->counters + 3, init, c->st);
+  prof_end(c, IMEX_PROF_CG_DIR, 2.0 * sizeof(T) * sg.total, 3.0 * sg.total, arith_t<T>());
+}
+template <typename T>
+void cg_pz(imex_ctx* c, T* p, const T* z, const imex_ctx::Seg& sg, const CgScalars& sc, int restart) {
+  prof_mark(c, IMEX_PROF_CG_DIR, true);
+  seg_pz<T>(p, z, sg.t, sc, restart, c->st);
+  prof_end(c, IMEX_PROF_CG_DIR, 3.0 * sizeof(T) * sg.total, 3.0 * sg.total, arith_t<T>());
 }
 
 // z = one p-multigrid V-cycle applied to r (defined with the p-multigrid code below)
@@ -669,10 +747,10 @@ imex_status pcg(imex_ctx* c, const imex_ctx::Seg& sg, Op op, OpDot op_dot, bool 
   seg_init<double>(r, dj, t, sc, c->seg_partial, c->counters + 2, 1, c->st);
   if (pm) {
     TRY(pmg_vcycle<double>(c, r, z, c->pmg.lmax));
-    seg_rz<double>(r, z, t, sc, c->seg_partial, c->counters + 3, 1, c->st);
-    seg_pz<double>(p, z, t, sc, 1, c->st);
+    cg_rz<double>(c, r, z, sg, sc, 1);
+    cg_pz<double>(c, p, z, sg, sc, 1);
   } else {
-    seg_step_p<double>(p, r, dinv, t, sc, 1, c->st);
+    cg_dir<double>(c, p, r, dinv, sg, sc, 1);
   }
   CK(cudaGetLastError(), "cg_init");
   // a V-cycle iteration costs many launches: shorter chunks waste less after convergence
@@ -689,14 +767,14 @@ imex_status pcg(imex_ctx* c, const imex_ctx::Seg& sg, Op op, OpDot op_dot, bool 
         TRY(op(p, Ap));
         seg_pap<double>(p, Ap, t, sc, c->seg_partial, c->counters + 3, c->st);
       }
-      seg_step_xr<double>(x, r, p, Ap, dj, t, sc, maxit, c->seg_partial, c->counters + 1, c->st);
+      cg_step<double>(c, x, r, p, Ap, dj, sg, sc, maxit);
       if (pm) {
-        if (project) seg_rproj<double>(r, t, sc, c->st);
+        if (project) cg_rproj<double>(c, r, sg, sc);
         TRY(pmg_vcycle<double>(c, r, z, c->pmg.lmax));
-        seg_rz<double>(r, z, t, sc, c->seg_partial, c->counters + 3, 0, c->st);
-        seg_pz<double>(p, z, t, sc, 0, c->st);
+        cg_rz<double>(c, r, z, sg, sc, 0);
+        cg_pz<double>(c, p, z, sg, sc, 0);
       } else {
-        seg_step_p<double>(p, r, dinv, t, sc, 0, c->st);
+        cg_dir<double>(c, p, r, dinv, sg, sc, 0);
       }
     }
     return IMEX_OK;
@@ -810,10 +888,10 @@ imex_status pcg_mixed(imex_ctx* c, const imex_ctx::Seg& sg, Op64 op64, Op32 op32
     seg_init<float>(r, dj, t, sc, c->seg_partial, c->counters + 2, 0, c->st);
     if (pm) {
       TRY(pmg_vcycle<float>(c, r, z, c->pmg.lmax));
-      seg_rz<float>(r, z, t, sc, c->seg_partial, c->counters + 3, 1, c->st);
-      if (!keep) seg_pz<float>(p, z, t, sc, 1, c->st);
+      cg_rz<float>(c, r, z, sg, sc, 1);
+      if (!keep) cg_pz<float>(c, p, z, sg, sc, 1);
     } else if (!keep) {
-      seg_step_p<float>(p, r, dinv, t, sc, 1, c->st);
+      cg_dir<float>(c, p, r, dinv, sg, sc, 1);
     }
     started = true;
     restart = false;
@@ -835,14 +913,14 @@ imex_status pcg_mixed(imex_ctx* c, const imex_ctx::Seg& sg, Op64 op64, Op32 op32
         TRY(op32(p, Ap));
         seg_pap<float>(p, Ap, t, sc, c->seg_partial, c->counters + 3, c->st);
       }
-      seg_step_xr<float>(y, r, p, Ap, dj, t, sc, maxit, c->seg_partial, c->counters + 1, c->st);
+      cg_step<float>(c, y, r, p, Ap, dj, sg, sc, maxit);
       if (pm) {
-        if (project) seg_rproj<float>(r, t, sc, c->st);
+        if (project) cg_rproj<float>(c, r, sg, sc);
         TRY(pmg_vcycle<float>(c, r, z, c->pmg.lmax));
-        seg_rz<float>(r, z, t, sc, c->seg_partial, c->counters + 3, 0, c->st);
-        seg_pz<float>(p, z, t, sc, 0, c->st);
+        cg_rz<float>(c, r, z, sg, sc, 0);
+        cg_pz<float>(c, p, z, sg, sc, 0);
       } else {
-        seg_step_p<float>(p, r, dinv, t, sc, 0, c->st);
+        cg_dir<float>(c, p, r, dinv, sg, sc, 0);
       }
     }
     return IMEX_OK;
@@ -1018,7 +1096,10 @@ imex_status pmg_apply(imex_ctx* c, int l, const T* x, T* y) {
   const size_t n = (size_t)c->gp.ne * ipow(M.N[l], c->d);
   SipgArgs<T> a = sipg_args<T>(x, y, 1, (long long)n, nullptr, 1.0, nullptr, 0.0, 1.0, 0);
   a.ops = PmgVecs<T>::ops(M)[l];
-  return launch_check(c, sipg_apply<T>(c->gp, M.N[l], a, c->st), "sipg_apply(pmg)");
+  prof_mark(c, IMEX_PROF_PMG_APPLY, true);
+  const int rc = sipg_apply<T>(c->gp, M.N[l], a, c->st);
+  prof_end(c, IMEX_PROF_PMG_APPLY, 2.0 * sizeof(T) * n, sipg_flops_per_node(c->d, M.N[l]) * n, arith_t<T>());
+  return launch_check(c, rc, "sipg_apply(pmg)");
 }
 
 // Jacobi diagonals of every level and the Chebyshev upper bounds: 1.15 x the Rayleigh
@@ -1085,12 +1166,17 @@ imex_status pmg_smooth(imex_ctx* c, int l, int steps, double lmax, double ratio,
   const double lmin = lmax / ratio;
   const double theta = 0.5 * (lmax + lmin), delta = 0.5 * (lmax - lmin), sigma = theta / delta;
   if (from_x) TRY(pmg_apply<T>(c, l, x, ad));
+  prof_mark(c, IMEX_PROF_PMG_VEC, true);
   cheb_first<T>(x, dv, r, b, from_x ? ad : nullptr, dinv, 1.0 / theta, n, from_x ? 1 : 0, c->st);
+  prof_end(c, IMEX_PROF_PMG_VEC, (from_x ? 7.0 : 5.0) * sizeof(T) * n, (from_x ? 4.0 : 2.0) * n, arith_t<T>());
   double rho = 1.0 / sigma;
   for (int k = 1; k < steps; ++k) {
     TRY(pmg_apply<T>(c, l, dv, ad));
     const double rn = 1.0 / (2.0 * sigma - rho);
-    cheb_next<T>(x, dv, r, ad, dinv, rn * rho, 2.0 * rn / delta, n, k == steps - 1 ? 1 : 0, c->st);
+    const int last = k == steps - 1 ? 1 : 0;
+    prof_mark(c, IMEX_PROF_PMG_VEC, true);
+    cheb_next<T>(x, dv, r, ad, dinv, rn * rho, 2.0 * rn / delta, n, last, c->st);
+    prof_end(c, IMEX_PROF_PMG_VEC, (last ? 6.0 : 8.0) * sizeof(T) * n, 6.0 * n, arith_t<T>());
     rho = rn;
   }
   return IMEX_OK;
@@ -1104,6 +1190,13 @@ imex_status pmg_vcycle(imex_ctx* c, const T* r, T* z, const double* lm) {
   const int L = M.nlev;
   const T* b[4];
   T* x[4];
+  auto nodes = [&](int l) { return (double)c->gp.ne * ipow(M.N[l], c->d); };
+  // a transfer between levels l and l+1: d passes of 1D contractions per element
+  auto xfer_flops = [&](int l) {
+    double f = 0.0;
+    for (int j = 1; j <= c->d; ++j) f += std::pow((double)M.N[l + 1], j) * std::pow((double)M.N[l], c->d + 1 - j);
+    return 2.0 * f * c->gp.ne;
+  };
   for (int l = 0; l < L; ++l) {
     b[l] = l == 0 ? r : V::b(M)[l];
     x[l] = l == 0 ? z : V::x(M)[l];
@@ -1111,13 +1204,17 @@ imex_status pmg_vcycle(imex_ctx* c, const T* r, T* z, const double* lm) {
   for (int l = 0; l + 1 < L; ++l) {
     TRY(pmg_smooth<T>(c, l, M.pre, lm[l], M.ratio, false, b[l], x[l]));
     TRY(pmg_apply<T>(c, l, x[l], V::ad(M)[l]));
+    prof_mark(c, IMEX_PROF_PMG_VEC, true);
     if (pmg_restrict<T>(c->d, c->gp.ne, M.N[l], M.N[l + 1], b[l], V::ad(M)[l], V::b(M)[l + 1], M.I[l], c->st) != 0)
       return fail(c, IMEX_EINVAL, "p-multigrid: unsupported level pair");
+    prof_end(c, IMEX_PROF_PMG_VEC, sizeof(T) * (2.0 * nodes(l) + nodes(l + 1)), xfer_flops(l), arith_t<T>());
   }
   TRY(pmg_smooth<T>(c, L - 1, M.coarse, lm[L - 1], M.cratio, false, b[L - 1], x[L - 1]));
   for (int l = L - 2; l >= 0; --l) {
+    prof_mark(c, IMEX_PROF_PMG_VEC, true);
     if (pmg_prolong<T>(c->d, c->gp.ne, M.N[l], M.N[l + 1], x[l + 1], x[l], M.I[l], c->st) != 0)
       return fail(c, IMEX_EINVAL, "p-multigrid: unsupported level pair");
+    prof_end(c, IMEX_PROF_PMG_VEC, sizeof(T) * (2.0 * nodes(l) + nodes(l + 1)), xfer_flops(l), arith_t<T>());
     TRY(pmg_smooth<T>(c, l, M.pre, lm[l], M.ratio, true, b[l], x[l]));
   }
   return cuda_check(c, cudaGetLastError(), "pmg_vcycle");
@@ -1216,7 +1313,8 @@ imex_status solve_helmholtz(imex_ctx* c, const double* rhs, double* x, const dou
     vel_flags(c, a, false);
     prof_mark(c, IMEX_PROF_HELMHOLTZ_F64, true);
     const int rc = apply_dispatch<double>(c, c->gv, c->Nv, a);
-    prof_mark(c, IMEX_PROF_HELMHOLTZ_F64, false);
+    prof_end(c, IMEX_PROF_HELMHOLTZ_F64, 8.0 * (double)n * (2.0 * d + (nu ? 1.0 : 0.0)),
+             sipg_flops_per_node(d, c->Nv) * n * d, arith_of<double>(c));
     TRY(launch_check(c, rc, "sipg_apply(Kx)"));
     kx_combine(yy, xx, c->mass_v, c->cz, gamma, c->batched ? c->edt : nullptr, ipow(c->Nv, d), n, d, 0, c->st);
     return IMEX_OK;
@@ -1272,8 +1370,14 @@ const double* nu_ptr(const imex_ctx* c, const double* nu) { return variable_nu(c
 // F_d3 = -D(nu D.v) into out; if E != nullptr also E += F_d2 = sum_k D_k(nu D_c v_k) (variable nu)
 imex_status graddiv(imex_ctx* c, const double* v, const double* nu, double* fd3, double* fd2_acc) {
   // the mixed form evaluates the derivatives in float-float
+  // words per node moved by the four derivative forms (in, nu, out)
   auto deriv = [&](const DerivArgs<double>& x) {
-    return ff_class(c) ? dg_deriv_ff(c->gv, c->Nv, x, c->st) : dg_deriv<double>(c->gv, c->Nv, x, c->st);
+    const double d = c->d;
+    const double w[4] = {d + 1.0 + (x.nu ? 1.0 : 0.0), 1.0 + d, d + d * d + (x.nu ? 1.0 : 0.0), d * d + 2.0 * d};
+    prof_mark(c, IMEX_PROF_DERIV, true);
+    const int rc = ff_class(c) ? dg_deriv_ff(c->gv, c->Nv, x, c->st) : dg_deriv<double>(c->gv, c->Nv, x, c->st);
+    prof_end(c, IMEX_PROF_DERIV, 8.0 * w[x.op] * c->nv, 0.0, ff_class(c) ? IMEX_ARITH_FF : IMEX_ARITH_FP64);
+    return rc;
   };
   DerivArgs<double> a{};
   a.op = 0; a.in = v; a.stride = (long long)c->nv; a.nu = nu_ptr(c, nu); a.nu0 = nu_const(c); a.out = c->phi;
@@ -1310,7 +1414,8 @@ imex_status stage_rhs(imex_ctx* c, double t, const double* v, const double* nu, 
     ConvArgs<float> ca{c->fx, (long long)c->nv, vb ? c->fr : nullptr, 1.f, c->fp};
     prof_mark(c, IMEX_PROF_CONV, true);
     const int rc = dg_conv<float>(c->gv, c->Nv, ca, c->st);
-    prof_mark(c, IMEX_PROF_CONV, false);
+    prof_end(c, IMEX_PROF_CONV, 4.0 * nt * (vb ? 3.0 : 2.0), conv_flops_per_elem(c->d, c->Nv) * c->gv.ne,
+             IMEX_ARITH_FP32);
     TRY(launch_check(c, rc, "dg_conv(f32)"));
     f2d(c->fp, E, nt, c->st);
   } else {
@@ -1320,7 +1425,8 @@ imex_status stage_rhs(imex_ctx* c, double t, const double* v, const double* nu, 
     prof_mark(c, IMEX_PROF_CONV, true);
     const int rc = c->desc.precision == IMEX_MIXED ? dg_conv_ff(c->gv, c->Nv, ca, c->st)
                                                    : dg_conv<double>(c->gv, c->Nv, ca, c->st);
-    prof_mark(c, IMEX_PROF_CONV, false);
+    prof_end(c, IMEX_PROF_CONV, 8.0 * nt * (vb ? 3.0 : 2.0), conv_flops_per_elem(c->d, c->Nv) * c->gv.ne,
+             c->desc.precision == IMEX_MIXED ? IMEX_ARITH_FF : IMEX_ARITH_FP64);
     TRY(launch_check(c, rc, "dg_conv"));
   }
   const bool varnu = variable_nu(c);
@@ -1372,7 +1478,11 @@ imex_status project(imex_ctx* c, const double* vin, const double* wdata, int mod
   // the mixed form evaluates the projection's divergence and gradient in float-float
   const bool ffa = ff_class(c);
   DivArgs<double> da{vin, (long long)c->nv, wdata, mode, 1.0, c->bp};
-  TRY(launch_check(c, ffa ? dg_div_ff(c->gv, c->Nv, da, c->st) : dg_div<double>(c->gv, c->Nv, da, c->st), "dg_div"));
+  const int ar = ffa ? IMEX_ARITH_FF : IMEX_ARITH_FP64;
+  prof_mark(c, IMEX_PROF_DIV, true);
+  const int rcd = ffa ? dg_div_ff(c->gv, c->Nv, da, c->st) : dg_div<double>(c->gv, c->Nv, da, c->st);
+  prof_end(c, IMEX_PROF_DIV, 8.0 * ((mode == 1 ? 2.0 : 1.0) * c->d * c->nv + c->np), 0.0, ar);
+  TRY(launch_check(c, rcd, "dg_div"));
   double* psi = c->psi;
   if (mode == 2) {
     psi = c->psi_f;
@@ -1389,8 +1499,10 @@ imex_status project(imex_ctx* c, const double* vin, const double* wdata, int mod
   c->stats.poisson_solves++;
   c->stats.max_poisson_res = std::max(c->stats.max_poisson_res, res);
   GradArgs<double> ga{psi, vin, (long long)c->nv, -1.0, out};
-  return launch_check(c, ffa ? dg_grad_ff(c->gv, c->Nv, ga, c->st) : dg_grad<double>(c->gv, c->Nv, ga, c->st),
-                      "dg_grad");
+  prof_mark(c, IMEX_PROF_GRAD, true);
+  const int rcg = ffa ? dg_grad_ff(c->gv, c->Nv, ga, c->st) : dg_grad<double>(c->gv, c->Nv, ga, c->st);
+  prof_end(c, IMEX_PROF_GRAD, 8.0 * (2.0 * c->d * c->nv + c->np), 0.0, ar);
+  return launch_check(c, rcg, "dg_grad");
 }
 
 // Helmholtz stage solve: v_out = (M + gamma A(nu))^{-1} (M g + gamma r_b(nu, vb)), initial guess g
@@ -2414,15 +2526,26 @@ imex_status imex_op_sipg(imex_ctx* c, int space, const double* x, double* y, int
   const double nu0 = vel ? nu_const(c) : 1.0;
   if (arith != IMEX_ARITH_FP64 && arith != IMEX_ARITH_FP32 && arith != IMEX_ARITH_FF)
     return fail(c, IMEX_EINVAL, "bad arith");
+  // timed as the pressure / Helmholtz classes: read x (and nu, g), write y
+  const int cls64 = vel ? IMEX_PROF_HELMHOLTZ_F64 : IMEX_PROF_PRESSURE_F64;
+  const int cls32 = vel ? IMEX_PROF_HELMHOLTZ_F32 : IMEX_PROF_PRESSURE_F32;
+  const double words = (double)n * (2.0 * nsys + (dnu ? 1.0 : 0.0) + (dg ? nsys : 0.0));
+  const double flops = sipg_flops_per_node(c->d, N) * n * nsys;
   if (arith == IMEX_ARITH_FF) {
     SipgArgs<double> a = sipg_args<double>(c->cx, c->cAp, nsys, (long long)n, dnu, nu0, dg, alpha, beta, minv);
     a.ops = line_ops<double>(c, vel);
-    if (sipg_apply_ff(g, N, a, c->st) != 0) return fail(c, IMEX_EINVAL, "no float-float kernel for this operator");
+    prof_mark(c, cls64, true);
+    const int rc = sipg_apply_ff(g, N, a, c->st);
+    prof_end(c, cls64, 8.0 * words, flops, IMEX_ARITH_FF);
+    if (rc != 0) return fail(c, IMEX_EINVAL, "no float-float kernel for this operator");
     TRY(cuda_check(c, cudaGetLastError(), "sipg_apply_ff"));
   } else if (arith == IMEX_ARITH_FP64) {
     SipgArgs<double> a = sipg_args<double>(c->cx, c->cAp, nsys, (long long)n, dnu, nu0, dg, alpha, beta, minv);
     a.ops = line_ops<double>(c, vel);
-    TRY(launch_check(c, sipg_apply<double>(g, N, a, c->st), "sipg_apply"));
+    prof_mark(c, cls64, true);
+    const int rc = sipg_apply<double>(g, N, a, c->st);
+    prof_end(c, cls64, 8.0 * words, flops, IMEX_ARITH_FP64);
+    TRY(launch_check(c, rc, "sipg_apply"));
   } else {
     convert_d2f(c->cx, c->fx, n * nsys, c->st);
     const float* fnu = nullptr;
@@ -2431,7 +2554,10 @@ imex_status imex_op_sipg(imex_ctx* c, int space, const double* x, double* y, int
     if (dg) { convert_d2f(dg, c->fr, n * nsys, c->st); fg = c->fr; }
     SipgArgs<float> a = sipg_args<float>(c->fx, c->fAp, nsys, (long long)n, fnu, nu0, fg, alpha, beta, minv);
     a.ops = line_ops<float>(c, vel);
-    TRY(launch_check(c, sipg_apply<float>(g, N, a, c->st), "sipg_apply(f32)"));
+    prof_mark(c, cls32, true);
+    const int rc = sipg_apply<float>(g, N, a, c->st);
+    prof_end(c, cls32, 4.0 * words, flops, IMEX_ARITH_FP32);
+    TRY(launch_check(c, rc, "sipg_apply(f32)"));
     f2d(c->fAp, c->cAp, n * nsys, c->st);
   }
   return copy_out(c, y, c->cAp, n * nsys, on_device);
@@ -2464,7 +2590,11 @@ imex_status imex_op_div(imex_ctx* c, const double* v, const double* w, int mode,
   TRY(copy_in(c, c->cx, v, c->nv * c->d, on_device));
   if (mode == 1) TRY(copy_in(c, c->vb, w, c->nv * c->d, on_device));
   DivArgs<double> da{c->cx, (long long)c->nv, c->vb, mode, 1.0, c->bp};
-  TRY(launch_check(c, ff ? dg_div_ff(c->gv, c->Nv, da, c->st) : dg_div<double>(c->gv, c->Nv, da, c->st), "dg_div"));
+  prof_mark(c, IMEX_PROF_DIV, true);
+  const int rc = ff ? dg_div_ff(c->gv, c->Nv, da, c->st) : dg_div<double>(c->gv, c->Nv, da, c->st);
+  prof_end(c, IMEX_PROF_DIV, 8.0 * ((mode == 1 ? 2.0 : 1.0) * c->d * c->nv + c->np), 0.0,
+           ff ? IMEX_ARITH_FF : IMEX_ARITH_FP64);
+  TRY(launch_check(c, rc, "dg_div"));
   return copy_out(c, b, c->bp, c->np, on_device);
 }
 
@@ -2474,8 +2604,10 @@ imex_status imex_op_grad(imex_ctx* c, const double* psi, double* out, int arith,
   if (!ff_arith(arith, &ff)) return fail(c, IMEX_EINVAL, "bad arith");
   TRY(copy_in(c, c->bp, psi, c->np, on_device));
   GradArgs<double> ga{c->bp, nullptr, (long long)c->nv, 1.0, c->cAp};
-  TRY(launch_check(c, ff ? dg_grad_ff(c->gv, c->Nv, ga, c->st) : dg_grad<double>(c->gv, c->Nv, ga, c->st),
-                   "dg_grad"));
+  prof_mark(c, IMEX_PROF_GRAD, true);
+  const int rc = ff ? dg_grad_ff(c->gv, c->Nv, ga, c->st) : dg_grad<double>(c->gv, c->Nv, ga, c->st);
+  prof_end(c, IMEX_PROF_GRAD, 8.0 * ((double)c->d * c->nv + c->np), 0.0, ff ? IMEX_ARITH_FF : IMEX_ARITH_FP64);
+  TRY(launch_check(c, rc, "dg_grad"));
   return copy_out(c, out, c->cAp, c->nv * c->d, on_device);
 }
 
@@ -2491,12 +2623,19 @@ imex_status imex_op_conv(imex_ctx* c, const double* v, const double* vb, double*
     convert_d2f(c->cx, c->fx, nt, c->st);
     if (dvb) convert_d2f(dvb, c->fr, nt, c->st);
     ConvArgs<float> ca{c->fx, (long long)c->nv, dvb ? c->fr : nullptr, 1.f, c->fp};
-    TRY(launch_check(c, dg_conv<float>(c->gv, c->Nv, ca, c->st), "dg_conv(f32)"));
+    prof_mark(c, IMEX_PROF_CONV, true);
+    const int rc = dg_conv<float>(c->gv, c->Nv, ca, c->st);
+    prof_end(c, IMEX_PROF_CONV, 4.0 * nt * (dvb ? 3.0 : 2.0), conv_flops_per_elem(c->d, c->Nv) * c->gv.ne,
+             IMEX_ARITH_FP32);
+    TRY(launch_check(c, rc, "dg_conv(f32)"));
     f2d(c->fp, c->cAp, nt, c->st);
   } else {
     ConvArgs<double> ca{c->cx, (long long)c->nv, dvb, 1.0, c->cAp};
-    TRY(launch_check(c, arith == IMEX_ARITH_FF ? dg_conv_ff(c->gv, c->Nv, ca, c->st)
-                                               : dg_conv<double>(c->gv, c->Nv, ca, c->st), "dg_conv"));
+    prof_mark(c, IMEX_PROF_CONV, true);
+    const int rc = arith == IMEX_ARITH_FF ? dg_conv_ff(c->gv, c->Nv, ca, c->st)
+                                          : dg_conv<double>(c->gv, c->Nv, ca, c->st);
+    prof_end(c, IMEX_PROF_CONV, 8.0 * nt * (dvb ? 3.0 : 2.0), conv_flops_per_elem(c->d, c->Nv) * c->gv.ne, arith);
+    TRY(launch_check(c, rc, "dg_conv"));
   }
   return copy_out(c, out, c->cAp, nt, on_device);
 }
@@ -2658,6 +2797,9 @@ imex_status imex_profile(imex_ctx* c, int enable) {
     prof_flush(c, k);
     c->profc[k].n = 0;
     c->profc[k].ms = 0.0;
+    c->profc[k].bytes = 0.0;
+    c->profc[k].flops = 0.0;
+    c->profc[k].arith = -1;
   }
   c->prof = enable != 0;
   return IMEX_OK;
@@ -2669,6 +2811,14 @@ imex_status imex_profile_read(imex_ctx* c, int cls, long long* launches, double*
   prof_flush(c, cls);
   if (launches) *launches = c->profc[cls].n;
   if (total_ms) *total_ms = c->profc[cls].ms;
+  return IMEX_OK;
+}
+
+imex_status imex_profile_work(imex_ctx* c, int cls, double* bytes, double* flops, int* arith) {
+  if (!c || cls < 0 || cls >= IMEX_PROF_NCLASS) return IMEX_EINVAL;
+  if (bytes) *bytes = c->profc[cls].bytes;
+  if (flops) *flops = c->profc[cls].flops;
+  if (arith) *arith = c->profc[cls].arith;
   return IMEX_OK;
 }
 

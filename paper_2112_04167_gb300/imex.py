@@ -112,6 +112,7 @@ _SIGS = {
     "imex_reduce_noalloc": [C.c_int, _P, _P, C.c_longlong, _D, _P],
     "imex_profile": [_P, C.c_int],
     "imex_profile_read": [_P, C.c_int, C.POINTER(C.c_longlong), _D],
+    "imex_profile_work": [_P, C.c_int, _D, _D, C.POINTER(C.c_int)],
     "imex_launch_count": [],
     "imex_batch_create": [C.POINTER(_P), C.c_int, C.POINTER(_P)],
     "imex_batch_destroy": [_P],
@@ -135,7 +136,10 @@ _SIGS = {
     "imex_request_footprint": [C.POINTER(imex_request), _D],
 }
 REQ_QUEUED, REQ_ACTIVE, REQ_DONE, REQ_FAILED = range(4)
-PROF_PRESSURE_F32, PROF_PRESSURE_F64, PROF_HELMHOLTZ_F32, PROF_HELMHOLTZ_F64, PROF_CONV, PROF_PCG_PERSIST = range(6)
+(PROF_PRESSURE_F32, PROF_PRESSURE_F64, PROF_HELMHOLTZ_F32, PROF_HELMHOLTZ_F64, PROF_CONV, PROF_PCG_PERSIST,
+ PROF_PMG_APPLY, PROF_PMG_VEC, PROF_CG_STEP, PROF_CG_DIR, PROF_DIV, PROF_GRAD, PROF_DERIV) = range(13)
+PROF_NAMES = ["sipg_pressure_f32", "sipg_pressure_f64", "sipg_helmholtz_f32", "sipg_helmholtz_f64", "conv",
+              "pcg_persist_f32", "pmg_apply", "pmg_vec", "cg_step", "cg_dir", "div", "grad", "deriv"]
 REDUCE_DOT, REDUCE_SUM, REDUCE_MAXABS = range(3)
 
 
@@ -427,6 +431,12 @@ class Context:
         n, ms = C.c_longlong(), C.c_double()
         self._check(load().imex_profile_read(self._h, cls, C.byref(n), C.byref(ms)))
         return n.value, ms.value
+
+    def profile_work(self, cls):
+        """(algorithmic bytes, flops, arith of the last launch) of a profiled kernel class."""
+        b, f, a = C.c_double(), C.c_double(), C.c_int()
+        self._check(load().imex_profile_work(self._h, cls, C.byref(b), C.byref(f), C.byref(a)))
+        return b.value, f.value, a.value
 
     def eval_field(self, what, kind, params=(), t=0.0, v=None):
         ncomp = 1 if what == 1 else self.dim

@@ -163,10 +163,12 @@ def test_graddiv(case):
     del fl
 
 
+@pytest.mark.parametrize("precond", [imex.PRECOND_JACOBI, imex.PRECOND_PMG])
 @pytest.mark.parametrize("mode", [imex.POISSON_SIPG, imex.POISSON_CONSISTENT])
 @pytest.mark.parametrize("case", [CASES[0], CASES[3], CASES[2]])
-def test_poisson_solve(case, mode):
+def test_poisson_solve(case, mode, precond):
     ctx, mesh = make(case, poisson=mode, tol=1e-14, maxit=20000)
+    ctx.set_pressure_precond(precond)
     d, P = case[0], case[1]
     fl = flows.Flow("tgtravel", 0.01)
     disc = ns.Discretization(mesh, fl, poisson="sipg" if mode == imex.POISSON_SIPG else "consistent")

@@ -66,6 +66,15 @@ def test_rk_step_tg2d(tab):
     run_steps(ctx, disc, lambda v, t, dt: ns.rk_step(disc, tab, v, t, dt)[0], v0, 0.0, 0.01, 3, 1e-11)
 
 
+@pytest.mark.parametrize("precision,tol", [(imex.FP64, 1e-11), (imex.MIXED, 1e-9)])
+def test_rk_step_jacobi_pressure(precision, tol):
+    """Alg. 3 with Jacobi-preconditioned pressure solves (the default is p-multigrid)."""
+    ctx, disc, fl = tg2d_pair(precision=precision, tol=1e-14 if precision == imex.FP64 else 1e-12)
+    ctx.set_pressure_precond(imex.PRECOND_JACOBI)
+    v0 = fl.initial(disc.X).reshape(2, -1)
+    run_steps(ctx, disc, lambda v, t, dt: ns.rk_step(disc, "CB3e", v, t, dt)[0], v0, 0.0, 0.01, 2, tol)
+
+
 def test_rk_step_tg2d_consistent_projection():
     ctx, disc, fl = tg2d_pair(poisson=imex.POISSON_CONSISTENT)
     v0 = fl.initial(disc.X).reshape(2, -1)
