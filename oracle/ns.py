@@ -288,3 +288,49 @@ def rms(x):
 
 def relative_l2(a, b):
     return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+
+
+# ---------------------------------------------------------------------------
+# IMEX BDF2 of Sec. 3.2.1: extrapolation, projection, diffusion, additional projection
+# ---------------------------------------------------------------------------
+def bdf2_step(disc, v, t, dt, prev=None, final_projection=None):
+    """One step of IMEX BDF2 from v = v^n at t = t^n (the first step, prev = None, with the
+    IMEX Euler coefficients of its start).  prev: the history returned by the previous step
+    (v^{n-1} and its right-hand sides).  Returns (v^{n+1}, history for the next step, info).
+
+    Readings: the projection solves psi = (dt / gamma_0) p'' from the same Poisson problem as
+    Alg. 3 (weak divergence of v' with the boundary flux of v_b(t^{n+1})); the diffusion step
+    uses the extrapolated viscosity beta_0 nu^n + beta_1 nu^{n-1} with nu^n = nu(x, t^n, v^n);
+    the additional projection (variable viscosity) uses homogeneous Neumann data for the
+    pressure increment, as the final projection of Alg. 3 does.
+    """
+    from .scalar import BDF2, EULER_START
+    co = EULER_START if prev is None else BDF2
+    a0, a1 = co["alpha"]
+    b0, b1 = co["beta"]
+    g0 = co["gamma0"]
+    varnu = disc.flow.variable_nu()
+    if final_projection is None:
+        final_projection = varnu
+    v = np.asarray(v, dtype=np.float64).reshape(disc.d, disc.nv)
+    nu_n = disc.nu_field(t, v)
+    E, Fd1, Fd3, _ = disc.stage_rhs(v, nu_n, t, disc.vb(t))
+    cur = {"v": v, "E": E, "Fd1": Fd1, "Fd3": Fd3, "nu": nu_n}
+    old = prev if prev is not None else cur
+    t1 = t + dt
+    vb1 = disc.vb(t1)
+    # 1. extrapolation (forcing implicit: at t^{n+1})
+    vp = (a0 * v + a1 * old["v"]
+          + dt * (b0 * (E + Fd1 + Fd3) + b1 * (old["E"] + old["Fd1"] + old["Fd3"]) + disc.fs(t1))) / g0
+    # 2. projection
+    psi = disc.poisson(disc.div_rhs(vp, vb1, "data"))
+    vpp = vp - disc.grad_p(psi)
+    # 3. diffusion with the extrapolated viscosity
+    nu_star = b0 * nu_n + b1 * old["nu"]
+    g = vpp - (dt / g0) * (b0 * (Fd1 + Fd3) + b1 * (old["Fd1"] + old["Fd3"]))
+    vnew = disc.helmholtz(g, nu_star, dt / g0, vb1)
+    # 4. additional projection
+    if final_projection:
+        psi_f = disc.poisson(disc.div_rhs(vnew, None, "trace"))
+        vnew = vnew - disc.grad_p(psi_f)
+    return vnew, cur, {"psi": psi, "pressure": g0 / dt * psi}

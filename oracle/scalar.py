@@ -177,3 +177,28 @@ def substeps(method):
             return M * (K + 1)
         return M * (K + get_tableau(pred).s - 1)
     return get_tableau(name).s - 1
+
+
+# IMEX BDF2 of Eq. (bdf2:constant-nu), Sec. 2.2: gamma_0 = 3/2, alpha = (2, -1/2),
+# beta = (2, -1); not self-starting, so its first step is IMEX Euler (all coefficients 1 or 0)
+BDF2 = {"alpha": (2.0, -0.5), "beta": (2.0, -1.0), "gamma0": 1.5}
+EULER_START = {"alpha": (1.0, 0.0), "beta": (1.0, 0.0), "gamma0": 1.0}
+
+
+def bdf2_run(u0, dt, nsteps, fc, fd_solve):
+    """nsteps of IMEX BDF2 on du/dt = f_c(u) + f_d(u), the first an IMEX Euler step.
+
+    Each step solves (gamma_0 u^{n+1} - alpha_0 u^n - alpha_1 u^{n-1}) / dt
+        = beta_0 f_c(u^n) + beta_1 f_c(u^{n-1}) + f_d(u^{n+1})
+    for u^{n+1}; fd_solve(rhs, g) returns u with u - g f_d(u) = rhs.  Returns the list u^0..u^n.
+    """
+    us = [u0]
+    for n in range(nsteps):
+        co = EULER_START if n == 0 else BDF2
+        a0, a1 = co["alpha"]
+        b0, b1 = co["beta"]
+        g0 = co["gamma0"]
+        u, up = us[-1], (us[-2] if n > 0 else us[-1])
+        rhs = (a0 * u + a1 * up + dt * (b0 * fc(u) + b1 * fc(up))) / g0
+        us.append(fd_solve(rhs, dt / g0))
+    return us
