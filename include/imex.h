@@ -54,13 +54,16 @@ typedef enum {
 enum { IMEX_FP64 = 0, IMEX_MIXED = 1, IMEX_MIXED_FAST = 2 };
 /* pressure operator: SIPG on Q_{P-1} (Sec. 3.3), or B M^-1 B^T (discretely divergence-free) */
 enum { IMEX_POISSON_SIPG = 0, IMEX_POISSON_CONSISTENT = 1 };
-/* closed-form flows (initial / Dirichlet data); params[0] = nu_0 */
-enum { IMEX_FLOW_NONE = 0, IMEX_FLOW_TG2D = 1, IMEX_FLOW_TG3D = 2, IMEX_FLOW_TGTRAVEL = 3 };
+/* closed-form flows (initial / Dirichlet data); params[0] = nu_0.  IMEX_FLOW_VV: the
+   travelling 3D vortex array of Sec. 4.2, Eq. (var-visc-test) (no parameters) */
+enum { IMEX_FLOW_NONE = 0, IMEX_FLOW_TG2D = 1, IMEX_FLOW_TG3D = 2, IMEX_FLOW_TGTRAVEL = 3, IMEX_FLOW_VV = 4 };
 /* viscosity laws: params {nu_0}; {nu_0} for nu0(1 + sin 2pi x sin 2pi y cos t / 2);
    {nu_0, nu_1, v_max} for nu_0 + nu_1 (|v|/v_max)^2 (Sec. 4.2); nodal field */
 enum { IMEX_NU_CONST = 0, IMEX_NU_VARXYT = 1, IMEX_NU_VELOCITY = 2, IMEX_NU_FIELD = 3 };
-/* forcing: none, or the manufactured forcing of the traveling vortex under IMEX_NU_VARXYT */
-enum { IMEX_FORCE_NONE = 0, IMEX_FORCE_TGTRAVEL_VARNU = 1 };
+/* forcing: none, the manufactured forcing of the traveling vortex under IMEX_NU_VARXYT, or
+   the forcing of Eq. (var-visc-test:rhs) that makes the vortex array exact under the
+   velocity-dependent viscosity (params {nu_0, nu_1, v_max}, 3D) */
+enum { IMEX_FORCE_NONE = 0, IMEX_FORCE_TGTRAVEL_VARNU = 1, IMEX_FORCE_VV = 2 };
 /* operator spaces of imex_op_sipg */
 enum { IMEX_SPACE_VELOCITY = 0, IMEX_SPACE_PRESSURE = 1 };
 /* arithmetic of the operator-level entry points (argument `arith`): FP64 kernels; FP32
@@ -117,6 +120,13 @@ imex_status imex_set_tableau_named(imex_ctx* ctx, const char* name);
 /* SISDC of Sec. 3.2.3 with M subintervals on GLL nodes, K correction sweeps and the named
    predictor tableau ("EULER" for SDC-Eu).  Selects SDC stepping. */
 imex_status imex_set_sdc(imex_ctx* ctx, int M, int K, const char* predictor);
+/* IMEX BDF2 of Sec. 3.2.1 (Eq. (bdf2:variable-nu) with the splitting into extrapolation,
+   projection, diffusion with the extrapolated viscosity and, for variable viscosity, an
+   additional projection).  Not self-starting: the first step after this call, after
+   imex_set_state / imex_init_flow, or after a change of dt is an IMEX Euler step.  Selects
+   BDF2 stepping (one nontrivial substep per step); imex_set_tableau* / imex_set_sdc switch
+   back.  Batches reject BDF2 contexts (IMEX_EINVAL). */
+imex_status imex_set_bdf2(imex_ctx* ctx);
 
 imex_status imex_set_viscosity_const(imex_ctx* ctx, double nu);
 imex_status imex_set_viscosity_model(imex_ctx* ctx, int kind, const double* params, int nparams);

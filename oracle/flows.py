@@ -11,6 +11,12 @@ TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
   [0, 2 pi]^3 (pinned in tests/test_oracle_flows.py).
 * ``tgtravel``: the traveling Taylor-Green vortex of Sec. 4.1 with phase speed 1,
   decay rate 8 pi^2 nu_0.
+* ``vv``: the travelling 3D vortex array of Sec. 4.2, Eq. (var-visc-test), with wave length 1,
+  maximum speed 2 and phase speed 1 in each direction, and its pressure; with the
+  velocity-dependent viscosity it is exact under the forcing ``forcing_vv``, Eq.
+  (var-visc-test:rhs): f = d_t v + div(v v) - div[nu(v) (grad v + grad v^T)] + grad p,
+  here with div v = 0 written as d_t v + (grad v) v - nu lap v - (grad v + grad v^T) grad nu
+  + grad p;
 * viscosity laws: constant; nu(x, y, t) = nu_0 (1 + 1/2 sin 2 pi x sin 2 pi y cos t);
   nu(v) = nu_0 + nu_1 (|v| / v_max)^2 (Sec. 4.2).
 * forcing ``tgtravel_varnu``: f = (nu_0 - nu) lap v - (grad v + grad v^T) grad nu, the
@@ -88,6 +94,48 @@ def forcing_tgtravel_varnu(X, t, nu0):
     return f
 
 
+def vv_velocity(X, t):
+    A, B, Cz = (TWO_PI * (X[..., k] + t) for k in range(3))
+    return np.stack([(np.sin(A) + np.cos(B)) * np.sin(Cz),
+                     (np.cos(A) + np.sin(B)) * np.sin(Cz),
+                     (np.cos(A) + np.cos(B)) * np.cos(Cz)])
+
+
+def vv_pressure(X, t):
+    A, B, Cz = (TWO_PI * (X[..., k] + t) for k in range(3))
+    return np.sin(A) * np.sin(B) * np.sin(Cz)
+
+
+def vv_grad(X, t):
+    """G[c, k] = d v_c / d x_k of the vortex array."""
+    A, B, Cz = (TWO_PI * (X[..., k] + t) for k in range(3))
+    sA, cA, sB, cB, sC, cC = np.sin(A), np.cos(A), np.sin(B), np.cos(B), np.sin(Cz), np.cos(Cz)
+    k = TWO_PI
+    G = np.zeros((3, 3) + A.shape)
+    G[0, 0], G[0, 1], G[0, 2] = k * cA * sC, -k * sB * sC, k * (sA + cB) * cC
+    G[1, 0], G[1, 1], G[1, 2] = -k * sA * sC, k * cB * sC, k * (cA + sB) * cC
+    G[2, 0], G[2, 1], G[2, 2] = -k * sA * cC, -k * sB * cC, -k * (cA + cB) * sC
+    return G
+
+
+def forcing_vv(X, t, nu0, nu1, vmax):
+    v = vv_velocity(X, t)
+    G = vv_grad(X, t)
+    k = TWO_PI
+    A, B, Cz = (TWO_PI * (X[..., j] + t) for j in range(3))
+    gp = k * np.stack([np.cos(A) * np.sin(B) * np.sin(Cz), np.sin(A) * np.cos(B) * np.sin(Cz),
+                       np.sin(A) * np.sin(B) * np.cos(Cz)])
+    nu = nu0 + nu1 * np.sum(v ** 2, axis=0) / vmax ** 2
+    gnu = np.stack([2.0 * nu1 / vmax ** 2 * sum(v[j] * G[j, i] for j in range(3)) for i in range(3)])
+    f = np.zeros_like(v)
+    for c in range(3):
+        dt = G[c, 0] + G[c, 1] + G[c, 2]                  # every argument is (x_k + t)
+        adv = sum(v[i] * G[c, i] for i in range(3))
+        lap = -2.0 * k * k * v[c]                         # each term varies along two directions
+        f[c] = dt + adv - nu * lap - sum((G[c, i] + G[i, c]) * gnu[i] for i in range(3)) + gp[c]
+    return f
+
+
 class Flow:
     """A flow case: initial data, viscosity law, forcing, boundary data, exact solution."""
 
@@ -118,6 +166,8 @@ class Flow:
             return tg2d_velocity(X, t, self.nu0)
         if self.kind == "tgtravel":
             return tgtravel_velocity(X, t, self.nu0)
+        if self.kind == "vv":
+            return vv_velocity(X, t)
         if self.kind == "tg3d":
             if t != 0.0:
                 raise ValueError("tg3d has no closed form for t > 0")
@@ -131,9 +181,11 @@ class Flow:
         return self.exact(X, t)
 
     def has_forcing(self):
-        return self.kind == "tgtravel" and self.nu_kind == "varxyt"
+        return (self.kind == "tgtravel" and self.nu_kind == "varxyt") or self.kind == "vv"
 
     def forcing(self, X, t):
+        if self.kind == "vv":
+            return forcing_vv(X, t, self.nu0, self.nu1, self.vmax)
         if self.has_forcing():
             return forcing_tgtravel_varnu(X, t, self.nu0)
         return np.zeros((X.shape[-1],) + X.shape[:-1])

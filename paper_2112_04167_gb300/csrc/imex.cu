@@ -156,6 +156,13 @@ struct imex_ctx {
   std::string err;
   Tab tab;
   bool use_sdc = false;
+  // IMEX BDF2 (Sec. 3.2.1): steps taken since its start (the first is IMEX Euler), the step
+  // size of the history, and the history itself (v^{n-1}, nu^{n-1}; its right-hand sides are
+  // E[1], Fd1[1], Fd3[1]) plus the extrapolated viscosity of the diffusion step
+  bool use_bdf2 = false;
+  long long bdf_n = 0;
+  double bdf_dt = 0.0;
+  double *bdf_vprev = nullptr, *bdf_nuprev = nullptr, *bdf_nustar = nullptr;
   int sdc_M = 0, sdc_K = 0;
   Tab sdc_pred;
   // models
@@ -457,6 +464,11 @@ SipgArgs<T> sipg_args(const T* x, T* y, int nsys, long long stride, const T* nu,
   a.done_ninst = 0;
   a.inst_nu = 0;
   a.inst_dt = 0;
+  a.cheb = 0;
+  a.ch_last = 0;
+  a.ch_r = a.ch_dout = a.ch_s = nullptr;
+  a.ch_dinv = nullptr;
+  a.ch_c1 = a.ch_c2 = T(0);
   return a;
 }
 
@@ -1170,13 +1182,29 @@ imex_status pmg_smooth(imex_ctx* c, int l, int steps, double lmax, double ratio,
   cheb_first<T>(x, dv, r, b, from_x ? ad : nullptr, dinv, 1.0 / theta, n, from_x ? 1 : 0, c->st);
   prof_end(c, IMEX_PROF_PMG_VEC, (from_x ? 7.0 : 5.0) * sizeof(T) * n, (from_x ? 4.0 : 2.0) * n, arith_t<T>());
   double rho = 1.0 / sigma;
+  // each further step is one apply whose output stage performs the update (the new direction
+  // alternates between the two direction buffers, as neighbours still read the old one)
+  T* dcur = dv;
+  T* dnext = ad;
   for (int k = 1; k < steps; ++k) {
-    TRY(pmg_apply<T>(c, l, dv, ad));
     const double rn = 1.0 / (2.0 * sigma - rho);
     const int last = k == steps - 1 ? 1 : 0;
-    prof_mark(c, IMEX_PROF_PMG_VEC, true);
-    cheb_next<T>(x, dv, r, ad, dinv, rn * rho, 2.0 * rn / delta, n, last, c->st);
-    prof_end(c, IMEX_PROF_PMG_VEC, (last ? 6.0 : 8.0) * sizeof(T) * n, 6.0 * n, arith_t<T>());
+    SipgArgs<T> a = sipg_args<T>(dcur, nullptr, 1, (long long)n, nullptr, 1.0, nullptr, 0.0, 1.0, 0);
+    a.ops = V::ops(M)[l];
+    a.cheb = 1;
+    a.ch_last = last;
+    a.ch_r = r;
+    a.ch_dout = dnext;
+    a.ch_s = x;
+    a.ch_dinv = dinv;
+    a.ch_c1 = (T)(rn * rho);
+    a.ch_c2 = (T)(2.0 * rn / delta);
+    prof_mark(c, IMEX_PROF_PMG_APPLY, true);
+    const int rc = sipg_apply<T>(c->gp, M.N[l], a, c->st);
+    prof_end(c, IMEX_PROF_PMG_APPLY, (last ? 5.0 : 7.0) * sizeof(T) * n,
+             (sipg_flops_per_node(c->d, M.N[l]) + 6.0) * n, arith_t<T>());
+    TRY(launch_check(c, rc, "sipg_apply(chebyshev)"));
+    std::swap(dcur, dnext);
     rho = rn;
   }
   return IMEX_OK;
@@ -1795,6 +1823,91 @@ imex_status sdc_step(imex_ctx* c, double* v, double t, double dt) {
   return IMEX_OK;
 }
 
+// ---- IMEX BDF2 (Sec. 3.2.1) ----------------------------------------------------------
+// One step from v = v^n at t, with v1 the extrapolated, v2 the projected and v3 the
+// diffused velocity:
+//   (1) v1 = [a0 v^n + a1 v^{n-1} + dt (b0 (F_c + F_d + F_d3)^n + b1 (...)^{n-1} + F_s(t + dt))] / g0,
+//       where F_c + F_d + F_d3 = E + F_d1 + F_d3 (E = F_c + F_d2 + F_d3);
+//   (2) projection of v1 with the boundary flux of v_b(t + dt), psi = (dt / g0) p'';
+//   (3) v3 - (dt / g0) div(nu* grad v3) = v2 - (dt / g0)[b0 (F_d1 + F_d3)^n + b1 (...)^{n-1}],
+//       nu* = b0 nu^n + b1 nu^{n-1}, v3 = v_b(t + dt) on the boundary;
+//   (4) the additional projection (homogeneous Neumann data) when the viscosity varies.
+// The first step after a start, a new state or a change of dt uses the IMEX Euler
+// coefficients (a0 = b0 = g0 = 1, a1 = b1 = 0).
+imex_status bdf2_step(imex_ctx* c, double* v, double t, double dt) {
+  const size_t nt = c->nv * c->d;
+  const bool first = c->bdf_n == 0 || dt != c->bdf_dt;
+  const double a0 = first ? 1.0 : 2.0, a1 = first ? 0.0 : -0.5;
+  const double b0 = first ? 1.0 : 2.0, b1 = first ? 0.0 : -1.0;
+  const double g0 = first ? 1.0 : 1.5;
+  const bool forcing = c->f_kind != IMEX_FORCE_NONE;
+  const bool varnu = variable_nu(c);
+  c->kx_ready = false;
+  const double* vb = nullptr;
+  TRY(eval_vb(c, t, &vb));
+  TRY(eval_nu(c, t, v, c->nu));
+  TRY(stage_rhs(c, t, v, c->nu, vb, c->E[0], c->Fd1[0], c->Fd3[0], nullptr));
+  TRY(eval_vb(c, t + dt, &vb));
+  if (forcing)
+    TRY(launch_check(c, eval_field(c->gv, c->Nv, 2, spec(c->f_kind, c->f_p), t + dt, nullptr, (long long)c->nv,
+                                   c->Fs[0], c->st), "eval_field(f)"));
+  // (1) extrapolation
+  LinComb lc{};
+  int k = 0;
+  lc.x[k] = v; lc.c[k++] = a0 / g0;
+  if (a1 != 0.0) { lc.x[k] = c->bdf_vprev; lc.c[k++] = a1 / g0; }
+  const double* cur[3] = {c->E[0], c->Fd1[0], c->Fd3[0]};
+  const double* prev[3] = {c->E[1], c->Fd1[1], c->Fd3[1]};
+  for (int q = 0; q < 3; ++q) {
+    lc.x[k] = cur[q]; lc.c[k++] = dt * b0 / g0;
+    if (b1 != 0.0) { lc.x[k] = prev[q]; lc.c[k++] = dt * b1 / g0; }
+  }
+  if (forcing) { lc.x[k] = c->Fs[0]; lc.c[k++] = dt / g0; }
+  lc.nterms = k;
+  lincomb(c->vp, lc, nt, c->st);
+  // (2) projection
+  TRY(project(c, c->vp, vb, 1, c->vpp, dt / g0));
+  // (3) diffusion with the extrapolated viscosity
+  const double* nus = c->nu;
+  if (varnu && b1 != 0.0) {
+    LinComb ln{};
+    ln.nterms = 2; ln.x[0] = c->nu; ln.c[0] = b0; ln.x[1] = c->bdf_nuprev; ln.c[1] = b1;
+    lincomb(c->bdf_nustar, ln, c->nv, c->st);
+    nus = c->bdf_nustar;
+  }
+  LinComb lg{};
+  k = 0;
+  lg.x[k] = c->vpp; lg.c[k++] = 1.0;
+  lg.x[k] = c->Fd1[0]; lg.c[k++] = -dt * b0 / g0;
+  lg.x[k] = c->Fd3[0]; lg.c[k++] = -dt * b0 / g0;
+  if (b1 != 0.0) {
+    lg.x[k] = c->Fd1[1]; lg.c[k++] = -dt * b1 / g0;
+    lg.x[k] = c->Fd3[1]; lg.c[k++] = -dt * b1 / g0;
+  }
+  lg.nterms = k;
+  lincomb(c->g, lg, nt, c->st);
+  imex_status hs = helmholtz_stage(c, c->g, nus, dt / g0, vb, c->vp);
+  TRY(hs);
+  c->kx_ready = false;
+  c->stats.stages++;
+  // history: v^n, its right-hand sides and viscosity become the previous step's
+  CK(cudaMemcpyAsync(c->bdf_vprev, v, nt * sizeof(double), cudaMemcpyDeviceToDevice, c->st), "cp");
+  std::swap(c->E[0], c->E[1]);
+  std::swap(c->Fd1[0], c->Fd1[1]);
+  std::swap(c->Fd3[0], c->Fd3[1]);
+  std::swap(c->nu, c->bdf_nuprev);
+  // (4) additional projection
+  if (varnu) {
+    TRY(project(c, c->vp, nullptr, 2, c->vpp));
+    CK(cudaMemcpyAsync(v, c->vpp, nt * sizeof(double), cudaMemcpyDeviceToDevice, c->st), "cp");
+  } else {
+    CK(cudaMemcpyAsync(v, c->vp, nt * sizeof(double), cudaMemcpyDeviceToDevice, c->st), "cp");
+  }
+  c->bdf_n++;
+  c->bdf_dt = dt;
+  return IMEX_OK;
+}
+
 imex_status check_state(imex_ctx* c) {
   reduce_max_abs(c->v, c->nv * c->d, c->partial, c->nblocks, c->dscal + 60, c->st);
   CK(cudaMemcpyAsync(c->hscal + 60, c->dscal + 60, sizeof(double), cudaMemcpyDeviceToHost, c->st), "cp");
@@ -2016,7 +2129,7 @@ bool same_group(const imex_ctx* a, const imex_ctx* b) {
   if (a->desc.precision != b->desc.precision || a->desc.poisson != b->desc.poisson) return false;
   if (a->desc.tol != b->desc.tol || a->desc.maxit != b->desc.maxit || a->desc.vmax != b->desc.vmax) return false;
   if (a->nu_kind != b->nu_kind || a->bc_kind != b->bc_kind || a->f_kind != b->f_kind) return false;
-  if (a->use_sdc || b->use_sdc) return false;
+  if (a->use_sdc || b->use_sdc || a->use_bdf2 || b->use_bdf2) return false;
   if (a->pmg.kind != b->pmg.kind || a->pmg.pre != b->pmg.pre || a->pmg.coarse != b->pmg.coarse ||
       a->pmg.ratio != b->pmg.ratio || a->pmg.cratio != b->pmg.cratio)
     return false;
@@ -2383,6 +2496,7 @@ imex_status imex_set_tableau(imex_ctx* c, int s, const double* cc, const double*
   TRY(alloc_stages(c, s));
   c->tab = t;
   c->use_sdc = false;
+  c->use_bdf2 = false;
   return IMEX_OK;
 }
 
@@ -2393,6 +2507,7 @@ imex_status imex_set_tableau_named(imex_ctx* c, const char* name) {
   TRY(alloc_stages(c, t.s));
   c->tab = t;
   c->use_sdc = false;
+  c->use_bdf2 = false;
   return IMEX_OK;
 }
 
@@ -2404,6 +2519,21 @@ imex_status imex_set_sdc(imex_ctx* c, int M, int K, const char* predictor) {
   c->sdc_M = M; c->sdc_K = K; c->sdc_pred = t;
   TRY(alloc_sdc(c));
   c->use_sdc = true;
+  c->use_bdf2 = false;
+  return IMEX_OK;
+}
+
+imex_status imex_set_bdf2(imex_ctx* c) {
+  if (!c) return IMEX_EINVAL;
+  TRY(alloc_stages(c, 2));
+  if (!c->bdf_vprev) {
+    TRY(dalloc(c, &c->bdf_vprev, c->nv * c->d));
+    TRY(dalloc(c, &c->bdf_nuprev, c->nv));
+    TRY(dalloc(c, &c->bdf_nustar, c->nv));
+  }
+  c->use_bdf2 = true;
+  c->use_sdc = false;
+  c->bdf_n = 0;
   return IMEX_OK;
 }
 
@@ -2432,7 +2562,7 @@ imex_status imex_set_viscosity_field(imex_ctx* c, const double* nu, int on_devic
 }
 
 imex_status imex_set_boundary(imex_ctx* c, int kind, const double* p, int np) {
-  if (!c || kind < IMEX_FLOW_NONE || kind > IMEX_FLOW_TGTRAVEL || np < 0 || np > 8 || (np > 0 && !p))
+  if (!c || kind < IMEX_FLOW_NONE || kind > IMEX_FLOW_VV || np < 0 || np > 8 || (np > 0 && !p))
     return fail(c, IMEX_EINVAL, "bad boundary kind");
   c->bc_kind = kind;
   std::memset(c->bc_p, 0, sizeof(c->bc_p));
@@ -2441,9 +2571,10 @@ imex_status imex_set_boundary(imex_ctx* c, int kind, const double* p, int np) {
 }
 
 imex_status imex_set_forcing(imex_ctx* c, int kind, const double* p, int np) {
-  if (!c || kind < IMEX_FORCE_NONE || kind > IMEX_FORCE_TGTRAVEL_VARNU || np < 0 || np > 8 || (np > 0 && !p))
+  if (!c || kind < IMEX_FORCE_NONE || kind > IMEX_FORCE_VV || np < 0 || np > 8 || (np > 0 && !p))
     return fail(c, IMEX_EINVAL, "bad forcing kind");
   if (kind == IMEX_FORCE_TGTRAVEL_VARNU && c->d != 2) return fail(c, IMEX_EINVAL, "forcing is 2D only");
+  if (kind == IMEX_FORCE_VV && c->d != 3) return fail(c, IMEX_EINVAL, "forcing is 3D only");
   c->f_kind = kind;
   std::memset(c->f_p, 0, sizeof(c->f_p));
   for (int i = 0; i < np; ++i) c->f_p[i] = p[i];
@@ -2454,17 +2585,19 @@ imex_status imex_set_state(imex_ctx* c, double t, const double* v, int on_device
   if (!c || !v) return IMEX_EINVAL;
   TRY(copy_in(c, c->v, v, c->nv * c->d, on_device));
   c->t = t;
+  c->bdf_n = 0;                 // a new state restarts IMEX BDF2 with an Euler step
   return IMEX_OK;
 }
 
 imex_status imex_init_flow(imex_ctx* c, int kind, const double* p, int np, double t) {
-  if (!c || kind < IMEX_FLOW_NONE || kind > IMEX_FLOW_TGTRAVEL || np < 0 || np > 8 || (np > 0 && !p))
+  if (!c || kind < IMEX_FLOW_NONE || kind > IMEX_FLOW_VV || np < 0 || np > 8 || (np > 0 && !p))
     return fail(c, IMEX_EINVAL, "bad flow kind");
   double pp[8] = {0};
   for (int i = 0; i < np; ++i) pp[i] = p[i];
   TRY(launch_check(c, eval_field(c->gv, c->Nv, 0, spec(kind, pp), t, nullptr, (long long)c->nv, c->v, c->st),
                    "eval_field"));
   c->t = t;
+  c->bdf_n = 0;
   return IMEX_OK;
 }
 
@@ -2478,7 +2611,9 @@ imex_status imex_step(imex_ctx* c, double dt, int nsteps) {
   c->stats.refinements = 0;
   c->stats.max_poisson_res = c->stats.max_helmholtz_res = 0.0;
   for (int n = 0; n < nsteps; ++n) {
-    imex_status s = c->use_sdc ? sdc_step(c, c->v, c->t, dt) : rk_step(c, c->tab, c->v, c->t, dt, variable_nu(c));
+    imex_status s = c->use_bdf2 ? bdf2_step(c, c->v, c->t, dt)
+                    : c->use_sdc ? sdc_step(c, c->v, c->t, dt)
+                                 : rk_step(c, c->tab, c->v, c->t, dt, variable_nu(c));
     if (s != IMEX_OK) return s;
     c->t += dt;
     c->stats.steps++;
@@ -2840,7 +2975,7 @@ imex_status imex_batch_create(imex_ctx* const* insts, int n, imex_batch** out) {
   *out = nullptr;
   for (int i = 0; i < n; ++i) {
     if (!insts[i] || insts[i]->batched) return IMEX_EINVAL;
-    if (insts[i]->use_sdc || insts[i]->nu_kind == IMEX_NU_FIELD) return IMEX_EINVAL;
+    if (insts[i]->use_sdc || insts[i]->use_bdf2 || insts[i]->nu_kind == IMEX_NU_FIELD) return IMEX_EINVAL;
     if (has_boundary(insts[i]) && insts[i]->bc_kind == IMEX_FLOW_NONE) return IMEX_EINVAL;
   }
   imex_batch* b = new imex_batch();

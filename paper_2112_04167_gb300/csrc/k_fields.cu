@@ -1,9 +1,9 @@
 // Pointwise fields evaluated on the device at the GLL nodes: closed-form flows
 // used as initial / boundary data (Sec. 4.1 traveling Taylor-Green vortex, the
 // decaying 2D Taylor-Green vortex, the 3D Taylor-Green initial field of
-// Sec. 4.3), viscosity laws (constant, nu(x, y, t), nu(|v|) of Sec. 4.2) and the
-// manufactured forcing that makes the traveling vortex exact under the variable
-// viscosity nu(x, y, t).
+// Sec. 4.3, the travelling vortex array of Sec. 4.2), viscosity laws (constant,
+// nu(x, y, t), nu(|v|) of Sec. 4.2) and the manufactured forcing that makes the traveling
+// vortex exact under nu(x, y, t) and the vortex array exact under nu(|v|).
 #include <math.h>
 
 #include "../../include/imex.h"
@@ -30,6 +30,12 @@ __device__ void flow_velocity(int kind, const double* p, const double* X, double
     out[0] = 1.0 + sin(a) * cos(b) * F;
     out[1] = 1.0 - cos(a) * sin(b) * F;
     if (d > 2) out[2] = 0.0;
+  } else if (kind == IMEX_FLOW_VV && d == 3) {
+    const double tp = 2.0 * M_PI;
+    const double A = tp * (x + t), B = tp * (y + t), C = tp * (z + t);
+    out[0] = (sin(A) + cos(B)) * sin(C);
+    out[1] = (cos(A) + sin(B)) * sin(C);
+    out[2] = (cos(A) + cos(B)) * cos(C);
   } else {
     for (int c = 0; c < d; ++c) out[c] = 0.0;
   }
@@ -67,6 +73,29 @@ __device__ void forcing_tgtravel_varnu(const double* p, const double* X, double 
   f[1] = (nu0 - nu) * lapy - (gnx * (G10 + G01) + gny * (G11 + G11));
 }
 
+// f = d_t v + (grad v) v - nu lap v - (grad v + grad v^T) grad nu + grad p for the vortex array
+// of Sec. 4.2 (solenoidal, so div(v v) = (grad v) v and div(grad v^T) = 0), nu = nu(|v|):
+// every argument is x_k + t, so d_t v_c = sum_k dv_c/dx_k, and lap v = -2 (2 pi)^2 v
+__device__ void forcing_vv(const double* p, const double* X, double t, double* f) {
+  const double nu0 = p[0], nu1 = p[1], vm = p[2];
+  const double k = 2.0 * M_PI;
+  const double A = k * (X[0] + t), B = k * (X[1] + t), C = k * (X[2] + t);
+  const double sA = sin(A), cA = cos(A), sB = sin(B), cB = cos(B), sC = sin(C), cC = cos(C);
+  const double v[3] = {(sA + cB) * sC, (cA + sB) * sC, (cA + cB) * cC};
+  const double G[3][3] = {{k * cA * sC, -k * sB * sC, k * (sA + cB) * cC},
+                          {-k * sA * sC, k * cB * sC, k * (cA + sB) * cC},
+                          {-k * sA * cC, -k * sB * cC, -k * (cA + cB) * sC}};
+  const double gp[3] = {k * cA * sB * sC, k * sA * cB * sC, k * sA * sB * cC};
+  const double nu = nu0 + nu1 * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]) / (vm * vm);
+  double gnu[3];
+  for (int i = 0; i < 3; ++i) gnu[i] = 2.0 * nu1 / (vm * vm) * (v[0] * G[0][i] + v[1] * G[1][i] + v[2] * G[2][i]);
+  for (int c = 0; c < 3; ++c) {
+    double r = G[c][0] + G[c][1] + G[c][2] + 2.0 * k * k * nu * v[c] + gp[c];
+    for (int i = 0; i < 3; ++i) r += v[i] * G[c][i] - (G[c][i] + G[i][c]) * gnu[i];
+    f[c] = r;
+  }
+}
+
 template <int D, int N>
 __global__ void field_kernel(Geom g, int what, FieldSpec fs, double t, const double* __restrict__ v,
                              long long stride, double* __restrict__ out) {
@@ -100,6 +129,7 @@ __global__ void field_kernel(Geom g, int what, FieldSpec fs, double t, const dou
   } else {
     double f[3] = {0, 0, 0};
     if (fs.kind == IMEX_FORCE_TGTRAVEL_VARNU && D == 2) forcing_tgtravel_varnu(fs.p, X, t, f);
+    if (fs.kind == IMEX_FORCE_VV && D == 3) forcing_vv(fs.p, X, t, f);
     for (int c = 0; c < D; ++c) out[(size_t)c * stride + idx] = f[c];
   }
 }

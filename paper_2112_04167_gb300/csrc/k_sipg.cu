@@ -22,6 +22,23 @@
 
 namespace imex {
 
+// Output of one node of an apply: y = A x, or the fused Chebyshev step of the p-multigrid
+// smoother (a.cheb): r -= A x, d' = c1 x + c2 D^{-1} r, s += d' (xin: this node's input x)
+template <typename T, typename TS>
+__device__ __forceinline__ void sipg_out(const SipgArgs<TS>& a, TS* __restrict__ y, size_t i, T xin, T out) {
+  if (!a.cheb) {
+    y[i] = (TS)out;
+    return;
+  }
+  const T r = T(a.ch_r[i]) - out;
+  const T dn = T(a.ch_c1) * xin + T(a.ch_c2) * T(a.ch_dinv[i]) * r;
+  a.ch_s[i] = (TS)(T(a.ch_s[i]) + dn);
+  if (!a.ch_last) {
+    a.ch_r[i] = (TS)r;
+    a.ch_dout[i] = (TS)dn;
+  }
+}
+
 // Deterministic block sum for any block size: thread values through shared memory, then
 // warp 0 adds them in a fixed order.  Result valid in thread 0.
 __device__ __forceinline__ double block_sum_any(double v, double* red) {
@@ -690,7 +707,7 @@ sipg3c_apply_kernel(Geom g, SipgArgs<T> a) {
         const T yv = wy * wz * ihx * yx + wx * wz * ihy * yy + wx * wy * ihz * yz;
         T out = a.alpha * W * u[k] + scale * yv;
         if (a.minv) out /= W;
-        y[ebase + k * NN + t] = out;
+        sipg_out<T, T>(a, y, ebase + k * NN + t, u[k], out);
         dacc += u[k] * out;
       }
     }
@@ -819,7 +836,7 @@ sipg2c_apply_kernel(Geom g, SipgArgs<T> a) {
       const T W = wx * wy;
       T out = a.alpha * W * uo + scale * (wy * yx / hx + wx * yy / hy);
       if (a.minv) out /= W;
-      y[ebase + t] = out;
+      sipg_out<T, T>(a, y, ebase + t, uo, out);
       dacc = uo * out;
     }
     if (a.dot_out) {
@@ -965,7 +982,7 @@ sipg2l_apply_kernel(Geom g, SipgArgs<T> a) {
         const T W = wy * (T(0.5) * hx * L.w[o]);
         T out = a.alpha * W * v[o] + scale * (acc[le][ta * N + o] + wt * so);
         if (a.minv) out /= W;
-        y[(size_t)e * NN + ta * N + o] = out;
+        sipg_out<T, T>(a, y, (size_t)e * NN + ta * N + o, v[o], out);
         dacc += v[o] * out;
       }
     }
@@ -1290,7 +1307,7 @@ __device__ __forceinline__ T sipg3l_group(const Geom& g, const SipgArgs<TS>& a, 
       const T W = wyz * (T(0.5) * hx * L.w[o]);
       T out = alpha * W * v[o] + scale * (ma[node] + wt * so);
       if (a.minv) out = out / W;
-      y[eb + node] = (TS)out;
+      sipg_out<T, TS>(a, y, eb + node, v[o], out);
       dacc += v[o] * out;
     }
   }
@@ -1799,6 +1816,7 @@ int sipg_apply_ff(const Geom& g, int N, const SipgArgs<double>& a, cudaStream_t 
 template <typename T>
 int sipg_apply(const Geom& g, int N, const SipgArgs<T>& a, cudaStream_t st) {
   if (a.dot_out && (a.nu || !a.ops)) return -2;     // the fused dot exists on the constant-nu path only
+  if (a.cheb && (a.nu || !a.ops || a.gdata)) return -3;  // so does the fused Chebyshev step
   if (g.d == 2) { IMEX_DISPATCH_N(2, launch_apply, g, a, st) }
   else { IMEX_DISPATCH_N(3, launch_apply3, g, a, st) }
   return 0;

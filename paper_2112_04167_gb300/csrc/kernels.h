@@ -45,6 +45,17 @@ struct SipgArgs {
   // (inst_nu), and multiply beta by the instance's time step (inst_dt)
   int inst_nu;
   int inst_dt;
+  // Chebyshev smoother step fused into the apply (p-multigrid, constant-viscosity kernels):
+  // instead of y = A x the kernel updates, node by node, r -= A x, d' = c1 x + c2 D^{-1} r,
+  // s += d' (x is the previous direction; d' goes to a buffer other than x); with ch_last
+  // only s is stored.  cheb = 0: the plain apply.
+  int cheb;
+  int ch_last;
+  T* ch_r;
+  T* ch_dout;
+  T* ch_s;
+  const T* ch_dinv;
+  T ch_c1, ch_c2;
 };
 
 template <typename T>

@@ -16,9 +16,9 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libimexgb.so")
 OK, EINVAL, ENOMEM, ENOTCONV, EUNSTABLE, ECUDA = range(6)
 FP64, MIXED, MIXED_FAST = 0, 1, 2
 POISSON_SIPG, POISSON_CONSISTENT = 0, 1
-FLOW_NONE, FLOW_TG2D, FLOW_TG3D, FLOW_TGTRAVEL = 0, 1, 2, 3
+FLOW_NONE, FLOW_TG2D, FLOW_TG3D, FLOW_TGTRAVEL, FLOW_VV = 0, 1, 2, 3, 4
 NU_CONST, NU_VARXYT, NU_VELOCITY, NU_FIELD = 0, 1, 2, 3
-FORCE_NONE, FORCE_TGTRAVEL_VARNU = 0, 1
+FORCE_NONE, FORCE_TGTRAVEL_VARNU, FORCE_VV = 0, 1, 2
 SPACE_VELOCITY, SPACE_PRESSURE = 0, 1
 ARITH_FP64, ARITH_FP32, ARITH_FF = 0, 1, 3
 PRECOND_JACOBI, PRECOND_PMG = 0, 1
@@ -84,6 +84,7 @@ _SIGS = {
     "imex_set_tableau": [_P, C.c_int, _P, _P, _P, _P, _P],
     "imex_set_tableau_named": [_P, C.c_char_p],
     "imex_set_sdc": [_P, C.c_int, C.c_int, C.c_char_p],
+    "imex_set_bdf2": [_P],
     "imex_set_viscosity_const": [_P, C.c_double],
     "imex_set_viscosity_model": [_P, C.c_int, _P, C.c_int],
     "imex_set_viscosity_field": [_P, _P, C.c_int],
@@ -269,6 +270,9 @@ class Context:
 
     def set_sdc(self, M, K, predictor="EULER"):
         self._check(load().imex_set_sdc(self._h, M, K, predictor.encode()))
+
+    def set_bdf2(self):
+        self._check(load().imex_set_bdf2(self._h))
 
     def set_viscosity_const(self, nu):
         self._check(load().imex_set_viscosity_const(self._h, nu))

@@ -77,3 +77,43 @@ def test_tg2d_exact_navier_stokes_solution():
         res = dvdt + adv + gp - nu * lap
         assert np.abs(res).max() < 1e-6, t
         assert np.abs(G[0, 0] + G[1, 1]).max() < 1e-9
+
+
+def vv_flux_divergence_fd(X, t, nu0, nu1, vmax, h=1e-4):
+    """div(v v) - div[nu(v) (grad v + grad v^T)] at X by central differences of the fluxes,
+    each flux built from the closed-form velocity and a finite-difference gradient."""
+    def flux(Y):
+        v = flows.vv_velocity(Y, t)
+        G = fd_grad(lambda Z: flows.vv_velocity(Z, t), Y, 1e-5)
+        nu = nu0 + nu1 * np.sum(v ** 2, axis=0) / vmax ** 2
+        return np.stack([np.stack([v[c] * v[k] - nu * (G[c, k] + G[k, c]) for k in range(3)]) for c in range(3)])
+    out = np.zeros((3,) + X.shape[:-1])
+    for k in range(3):
+        e = np.zeros(3)
+        e[k] = h
+        out += (flux(X + e)[:, k] - flux(X - e)[:, k]) / (2 * h)
+    return out
+
+
+def test_vv_exact_solution_of_the_forced_problem():
+    """Eq. (var-visc-test): solenoidal, period 1, maximum speed 2, and the forcing of Eq.
+    (var-visc-test:rhs) equals d_t v + div(v v) - div[nu(v)(grad v + grad v^T)] + grad p
+    evaluated by finite differences of the closed forms."""
+    nu0, nu1, vmax, t = 0.01, 0.03, 2.0, 0.37
+    X = points(200, 3, 5, -0.5, 0.5)
+    G = fd_grad(lambda Y: flows.vv_velocity(Y, t), X)
+    assert np.abs(G[0, 0] + G[1, 1] + G[2, 2]).max() < 1e-8
+    assert np.abs(G - flows.vv_grad(X, t)).max() < 1e-7
+    for k in range(3):
+        e = np.zeros(3)
+        e[k] = 1.0
+        assert np.abs(flows.vv_velocity(X + e, t) - flows.vv_velocity(X, t)).max() < 1e-12
+    g = np.linspace(-0.5, 0.5, 41)
+    Xg = np.stack(np.meshgrid(g, g, g, indexing="ij"), axis=-1)
+    assert abs(np.sqrt(np.sum(flows.vv_velocity(Xg, 0.0) ** 2, axis=0)).max() - 2.0) < 1e-12
+    h = 1e-5
+    dvdt = (flows.vv_velocity(X, t + h) - flows.vv_velocity(X, t - h)) / (2 * h)
+    gp = fd_grad(lambda Y: flows.vv_pressure(Y, t)[None], X)[0]
+    ref = dvdt + vv_flux_divergence_fd(X, t, nu0, nu1, vmax) + gp
+    f = flows.forcing_vv(X, t, nu0, nu1, vmax)
+    assert np.abs(f - ref).max() < 1e-4 * np.abs(ref).max()
