@@ -214,6 +214,20 @@ imex_status imex_solve_helmholtz(imex_ctx* ctx, const double* g, const double* n
 imex_status imex_eval_field(imex_ctx* ctx, int what, int kind, const double* params, int nparams,
                             double t, const double* v, double* out, int on_device);
 
+/* ---- flow statistics of Sec. 4.3 (of the current velocity; single contexts only) ------ */
+/* viscous dissipation rate eps = (1 / |Omega|) int nu grad v : grad v dOmega (the paper's
+   nu / (8 pi^3) int grad v : grad v on [-pi, pi]^3), with the element-local gradient of the
+   DG velocity and the GLL quadrature of its nodes; nu: the context's viscosity law at the
+   current time and velocity */
+imex_status imex_dissipation(imex_ctx* ctx, double* eps);
+/* energy spectrum E[k], k = 0..kmax-1 (host array): the velocity interpolated to a regular
+   grid of M points per direction (M a power of two, 2..1024; x_j = lo + j L / M, evaluated by
+   the element containing it), a discrete Fourier transform normalised by M^-d, and
+   E(k) = |Omega| / 2 sum |v^(n)|^2 over the integer wave vectors with k - 1/2 <= |n| < k + 1/2,
+   so that the shells add up to the grid's kinetic energy ~ 1/2 int |v|^2.  The device
+   scratch (d M^d complex values) is kept by the context. */
+imex_status imex_energy_spectrum(imex_ctx* ctx, int M, int kmax, double* E);
+
 /* ---- reductions (FP64 accumulation, deterministic two-level sums) -------------------- */
 enum { IMEX_REDUCE_DOT = 0, IMEX_REDUCE_SUM = 1, IMEX_REDUCE_MAXABS = 2 };
 /* *out (host) = sum_i x_i y_i (DOT), sum_i x_i (SUM) or max_i |x_i| (MAXABS; NaN if any x_i

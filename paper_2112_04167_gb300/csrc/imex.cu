@@ -278,6 +278,11 @@ struct imex_ctx {
     double *z64 = nullptr, *ones64 = nullptr;
     float *z32 = nullptr, *ones32 = nullptr;
   } pmg;
+  // scratch of the flow statistics (grown on demand)
+  double2* diag_grid = nullptr;
+  size_t diag_grid_cap = 0;
+  double* diag_part = nullptr;
+  size_t diag_part_cap = 0;
   imex_stats stats{};
   double last_res = 0.0;
   // CUDA-event timing of kernel classes
@@ -2924,6 +2929,55 @@ imex_status imex_op_pmg_vcycle(imex_ctx* c, const double* r, double* z, const do
     f2d(c->fx, c->psi_f, c->np, c->st);
   }
   return copy_out(c, z, c->psi_f, c->np, on_device);
+}
+
+static double box_volume(const imex_ctx* c) {
+  double vol = 1.0;
+  for (int k = 0; k < c->d; ++k) vol *= c->desc.hi[k] - c->desc.lo[k];
+  return vol;
+}
+
+imex_status imex_dissipation(imex_ctx* c, double* eps) {
+  if (!c || !eps) return IMEX_EINVAL;
+  if (c->batched) return fail(c, IMEX_EINVAL, "statistics of a single instance only");
+  const double* nu = nullptr;
+  if (variable_nu(c)) {
+    TRY(eval_nu(c, c->t, c->v, c->nu));
+    nu = c->nu;
+  }
+  if (dissipation_elems(c->gv, c->Nv, c->v, (long long)c->nv, nu, nu_const(c), c->tmp, c->st) != 0)
+    return fail(c, IMEX_EINVAL, "dissipation: unsupported (d, P)");
+  reduce_sum(c->tmp, (size_t)c->gv.ne, c->partial, c->nblocks, c->dscal + 42, c->st);
+  CK(cudaMemcpyAsync(c->hscal + 42, c->dscal + 42, sizeof(double), cudaMemcpyDeviceToHost, c->st), "cp");
+  CK(cudaStreamSynchronize(c->st), "sync");
+  *eps = c->hscal[42] / box_volume(c);
+  return IMEX_OK;
+}
+
+imex_status imex_energy_spectrum(imex_ctx* c, int M, int kmax, double* E) {
+  if (!c || !E || kmax < 1 || kmax > 4096 || M < 2 || M > 1024 || (M & (M - 1))) return IMEX_EINVAL;
+  if (c->batched) return fail(c, IMEX_EINVAL, "statistics of a single instance only");
+  size_t npts = 1;
+  for (int k = 0; k < c->d; ++k) npts *= (size_t)M;
+  const size_t ng = npts * c->d;
+  if (ng > ((size_t)1 << 31)) return fail(c, IMEX_EINVAL, "grid too large");
+  if (ng > c->diag_grid_cap) {
+    TRY(dalloc(c, &c->diag_grid, ng));
+    c->diag_grid_cap = ng;
+  }
+  const int nb = 152 * 4;
+  if ((size_t)nb * kmax + kmax > c->diag_part_cap) {
+    TRY(dalloc(c, &c->diag_part, (size_t)nb * kmax + kmax));
+    c->diag_part_cap = (size_t)nb * kmax + kmax;
+  }
+  double* dE = c->diag_part + (size_t)nb * kmax;
+  if (energy_spectrum(c->gv, c->Nv, c->v, (long long)c->nv, M, kmax, box_volume(c), c->diag_grid, c->diag_part, nb,
+                      dE, c->st) != 0)
+    return fail(c, IMEX_EINVAL, "energy spectrum: unsupported arguments");
+  TRY(cuda_check(c, cudaGetLastError(), "energy_spectrum"));
+  CK(cudaMemcpyAsync(E, dE, kmax * sizeof(double), cudaMemcpyDeviceToHost, c->st), "cp");
+  CK(cudaStreamSynchronize(c->st), "sync");
+  return IMEX_OK;
 }
 
 imex_status imex_profile(imex_ctx* c, int enable) {

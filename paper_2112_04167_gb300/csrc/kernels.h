@@ -201,6 +201,16 @@ void cheb_next(T* x, T* d, T* r, const T* ad, const T* dinv, double c1, double c
 // y = s a b elementwise
 void vec_mul(double* y, const double* a, const double* b, double s, size_t n, cudaStream_t st);
 
+// ---- flow statistics (k_diag.cu) ------------------------------------------------
+// per element e: out[e] = int_e nu grad v : grad v (broken gradient, GLL quadrature); nu:
+// nodal viscosity or nullptr for nu0.  -1 for an unsupported (d, N)
+int dissipation_elems(const Geom& g, int N, const double* v, long long stride, const double* nu, double nu0,
+                      double* out, cudaStream_t st);
+// E[0..kmax) of v on an M^d regular grid (M a power of two, 2..1024); grid: d * M^d complex
+// scratch, part: nbin_blocks * kmax scratch; vol: |Omega|.  -1 for unsupported arguments
+int energy_spectrum(const Geom& g, int N, const double* v, long long stride, int M, int kmax, double vol,
+                    double2* grid, double* part, int nbin_blocks, double* E, cudaStream_t st);
+
 // ---- pointwise fields (k_fields.cu) --------------------------------------------
 // what: 0 velocity of a closed-form flow (d components), 1 viscosity (1 component),
 //       2 forcing (d components).  kind / p: the flow, viscosity law or forcing and its

@@ -110,6 +110,8 @@ _SIGS = {
     "imex_solve_helmholtz": [_P, _P, _P, C.c_double, _P, _P, C.c_int],
     "imex_eval_field": [_P, C.c_int, C.c_int, _P, C.c_int, C.c_double, _P, _P, C.c_int],
     "imex_reduce": [_P, C.c_int, _P, _P, C.c_longlong, _D, C.c_int],
+    "imex_dissipation": [_P, _D],
+    "imex_energy_spectrum": [_P, C.c_int, C.c_int, _D],
     "imex_reduce_noalloc": [C.c_int, _P, _P, C.c_longlong, _D, _P],
     "imex_profile": [_P, C.c_int],
     "imex_profile_read": [_P, C.c_int, C.POINTER(C.c_longlong), _D],
@@ -427,6 +429,18 @@ class Context:
         out = C.c_double()
         self._check(load().imex_reduce(self._h, op, px, py, n, C.byref(out), dev))
         return out.value
+
+    def dissipation(self):
+        """Viscous dissipation rate of the current velocity (Sec. 4.3)."""
+        e = C.c_double()
+        self._check(load().imex_dissipation(self._h, C.byref(e)))
+        return e.value
+
+    def energy_spectrum(self, M, kmax):
+        """E(0..kmax-1) of the current velocity on an M^d regular grid (Sec. 4.3)."""
+        out = np.empty(kmax)
+        self._check(load().imex_energy_spectrum(self._h, M, kmax, out.ctypes.data_as(_D)))
+        return out
 
     def profile(self, enable=True):
         self._check(load().imex_profile(self._h, int(enable)))
