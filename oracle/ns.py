@@ -29,12 +29,13 @@ from .tableaux import get as get_tableau
 
 
 class Discretization:
-    def __init__(self, mesh, flow, poisson="sipg"):
+    def __init__(self, mesh, flow, poisson="sipg", stab=None):
         if mesh.P < 2:
             raise ValueError("velocity degree P must be at least 2")
         self.mesh = mesh
         self.flow = flow
         self.poisson_mode = poisson
+        self.stab = stab                  # (zeta_D, zeta_C) of the stabilisation, or None
         d = mesh.d
         self.d = d
         self.Nv = mesh.P + 1
@@ -112,6 +113,14 @@ class Discretization:
             for k in range(self.d):
                 out[c] += self.Dk[k] @ (nu * (self.Dk[c] @ v[k]))
         return out
+
+    def stabilized(self, v, dt):
+        """The projected velocity after the divergence / mass-flux stabilisation (oracle/stab.py),
+        with the time step dt in its penalty factors; unchanged without stabilisation."""
+        if self.stab is None:
+            return v
+        from .stab import stabilize
+        return stabilize(self.mesh, v, dt, *self.stab)
 
     def grad_p(self, psi):
         g = self.BT @ psi
@@ -194,7 +203,7 @@ def rk_step(disc, tab, v, t, dt, final_projection=None):
         for j in range(i + 1):
             vp += dt * AI[i][j] * Fs[j]
         psi = disc.poisson(disc.div_rhs(vp, vb_i, "data"))
-        vpp = vp - disc.grad_p(psi)
+        vpp = disc.stabilized(vp - disc.grad_p(psi), dt)
         nu_i = disc.nu_field(ti, vpp)
         g = vpp.copy()
         for j in range(i):
@@ -266,7 +275,7 @@ def sdc_step(disc, M, K, predictor, v, t, dt, final_projection=None):
             S = sum(dt * W[m, q] * Fq[q] for q in range(M + 1))
             vp = vnew[m - 1] + dts[m - 1] * (FEXn[m - 1] + Fd1p + Fd3p - (FEX[m - 1] + FIM[m])) + S
             psi = disc.poisson(disc.div_rhs(vp, vb_m, "data"))
-            vpp = vp - disc.grad_p(psi)
+            vpp = disc.stabilized(vp - disc.grad_p(psi), dt)
             g = vpp - dts[m - 1] * (Fd1p + Fd3p)
             vppp = disc.helmholtz(g, nunew[m - 1], dts[m - 1], vb_m)
             if final_projection:
@@ -324,7 +333,7 @@ def bdf2_step(disc, v, t, dt, prev=None, final_projection=None):
           + dt * (b0 * (E + Fd1 + Fd3) + b1 * (old["E"] + old["Fd1"] + old["Fd3"]) + disc.fs(t1))) / g0
     # 2. projection
     psi = disc.poisson(disc.div_rhs(vp, vb1, "data"))
-    vpp = vp - disc.grad_p(psi)
+    vpp = disc.stabilized(vp - disc.grad_p(psi), dt)
     # 3. diffusion with the extrapolated viscosity
     nu_star = b0 * nu_n + b1 * old["nu"]
     g = vpp - (dt / g0) * (b0 * (Fd1 + Fd3) + b1 * (old["Fd1"] + old["Fd3"]))
