@@ -128,6 +128,20 @@ imex_status imex_set_sdc(imex_ctx* ctx, int M, int K, const char* predictor);
    back.  Batches reject BDF2 contexts (IMEX_EINVAL). */
 imex_status imex_set_bdf2(imex_ctx* ctx);
 
+/* Divergence / mass-flux stabilisation after every stage projection (Sec. 3.3 adds one "for
+   pressure robustness" without stating its form).  This library's reading, the penalised
+   projection: the projected velocity v'' is replaced by v~ solving
+     (M + A_D + A_C) v~ = M v'',
+   A_D = sum_K tau_D,K B_K^T W_K B_K with tau_D,K = zeta_d |u_K| h_K / (P + 1) dt (B_K the
+   element-local divergence at the GLL nodes, W_K the GLL weights, |u_K| the magnitude of the
+   element's mean velocity, h_K the geometric mean element size, dt the step), and
+   A_C = sum_F tau_C,F J_F^T W_F J_F with tau_C,F = zeta_c (|u_K-| + |u_K+|) / 2 dt (J_F the jump
+   of the normal velocity component across an interior face).  Solved by CG to the context's
+   tolerance.  zeta_d = zeta_c = 0 (the default) switches it off; batches reject it. */
+imex_status imex_set_stabilization(imex_ctx* ctx, double zeta_d, double zeta_c);
+/* out = v~ of the stabilisation above applied to the velocity v (d blocks) with time step dt;
+   IMEX_EINVAL while the stabilisation is off */
+imex_status imex_stabilize(imex_ctx* ctx, const double* v, double dt, double* out, int on_device);
 imex_status imex_set_viscosity_const(imex_ctx* ctx, double nu);
 imex_status imex_set_viscosity_model(imex_ctx* ctx, int kind, const double* params, int nparams);
 /* nodal viscosity field (used as a fixed nu(x)); copied into the context */

@@ -278,6 +278,15 @@ struct imex_ctx {
     double *z64 = nullptr, *ones64 = nullptr;
     float *z32 = nullptr, *ones32 = nullptr;
   } pmg;
+  // divergence / mass-flux stabilisation after each stage projection (zeta_D, zeta_C; both
+  // 0: off), the time step of the step in progress, the element speeds, the inverse mass of
+  // the d components and the single CG system spanning them
+  double stab_zd = 0.0, stab_zc = 0.0;
+  double cur_dt = 0.0;
+  double* stab_speed = nullptr;
+  double* stab_minv = nullptr;
+  Seg segs;
+  long long stab_iters = 0;
   // scratch of the flow statistics (grown on demand)
   double2* diag_grid = nullptr;
   size_t diag_grid_cap = 0;
@@ -1501,6 +1510,25 @@ imex_status stage_rhs(imex_ctx* c, double t, const double* v, const double* nu, 
   return IMEX_OK;
 }
 
+// divergence / mass-flux stabilisation of the projected velocity v (in place):
+// (M + A_D + A_C) v~ = M v by CG with the inverse mass as preconditioner, from v
+imex_status stabilize(imex_ctx* c, double* v) {
+  const size_t nt = c->nv * c->d;
+  if (stab_speed(c->gv, c->Nv, v, (long long)c->nv, c->stab_speed, c->st) != 0)
+    return fail(c, IMEX_EINVAL, "stabilisation: unsupported (d, P)");
+  diag_mul(c, c->tmp, v, c->mass_v, c->nv, c->d);
+  const double zd = c->stab_zd, zc = c->stab_zc, dt = c->cur_dt;
+  auto op = [&](const double* x, double* y) -> imex_status {
+    return launch_check(c, stab_apply(c->gv, c->Nv, x, y, (long long)c->nv, c->stab_speed, zd, zc, dt, c->st) == 0
+                               ? 0 : -1, "stab_apply");
+  };
+  auto opd = [&](const double* x, double* y, const CgScalars*) { return op(x, y); };   // (no fused dot)
+  double res = 0.0;
+  (void)nt;
+  return pcg(c, c->segs, op, opd, false, c->tmp, v, c->stab_minv, c->desc.tol, c->desc.maxit, false,
+             {3, bits(zd), bits(zc), bits(dt)}, &c->stab_iters, &res);
+}
+
 // projection: psi from L psi = B v' - int (n.w) q, then v'' = v' - G psi (written to out).
 // Stage projections (mode 1) solve for a potential of size about tau p (tau = dt c_i for an
 // RK stage, the subinterval length for an SDC correction): the previous stage's potential,
@@ -1535,7 +1563,9 @@ imex_status project(imex_ctx* c, const double* vin, const double* wdata, int mod
   prof_mark(c, IMEX_PROF_GRAD, true);
   const int rcg = ffa ? dg_grad_ff(c->gv, c->Nv, ga, c->st) : dg_grad<double>(c->gv, c->Nv, ga, c->st);
   prof_end(c, IMEX_PROF_GRAD, 8.0 * (2.0 * c->d * c->nv + c->np), 0.0, ar);
-  return launch_check(c, rcg, "dg_grad");
+  TRY(launch_check(c, rcg, "dg_grad"));
+  if (mode == 1 && (c->stab_zd > 0.0 || c->stab_zc > 0.0)) TRY(stabilize(c, out));
+  return IMEX_OK;
 }
 
 // Helmholtz stage solve: v_out = (M + gamma A(nu))^{-1} (M g + gamma r_b(nu, vb)), initial guess g
@@ -1588,6 +1618,7 @@ void lcomb_dt(imex_ctx* c, double* out, LinComb& lc, int nfixed, size_t n) {
 }
 
 imex_status rk_step(imex_ctx* c, const Tab& tb, double* v, double t, double dt, bool final_projection) {
+  c->cur_dt = dt;
   const int s = tb.s;
   const size_t nt = c->nv * c->d;
   const bool forcing = c->f_kind != IMEX_FORCE_NONE;
@@ -1673,6 +1704,7 @@ imex_status rk_step(imex_ctx* c, const Tab& tb, double* v, double t, double dt, 
 
 // ---- Alg. 4 -------------------------------------------------------------------------
 imex_status sdc_step(imex_ctx* c, double* v, double t, double dt) {
+  c->cur_dt = dt;
   const int M = c->sdc_M, K = c->sdc_K, d = c->d;
   const size_t nt = c->nv * d;
   const bool varnu = variable_nu(c);
@@ -1733,6 +1765,7 @@ imex_status sdc_step(imex_ctx* c, double* v, double t, double dt) {
     CK(cudaMemcpyAsync(c->sv[m], c->sv[m - 1], nt * sizeof(double), cudaMemcpyDeviceToDevice, c->st), "cp");
     TRY(rk_step(c, c->sdc_pred, c->sv[m], tm[m - 1], dts[m], fproj));
   }
+  c->cur_dt = dt;              // the stabilisation scales with the step, not the subinterval
   const double* vb = nullptr;
   // F^EX_m = F_c + F_d2 + F_d3 at (v_m, nu_m); F^IM_m = F_d1(nu_{m-1}, v_m)
   auto f_ex = [&](int m, double* out) -> imex_status {
@@ -1840,6 +1873,7 @@ imex_status sdc_step(imex_ctx* c, double* v, double t, double dt) {
 // The first step after a start, a new state or a change of dt uses the IMEX Euler
 // coefficients (a0 = b0 = g0 = 1, a1 = b1 = 0).
 imex_status bdf2_step(imex_ctx* c, double* v, double t, double dt) {
+  c->cur_dt = dt;
   const size_t nt = c->nv * c->d;
   const bool first = c->bdf_n == 0 || dt != c->bdf_dt;
   const double a0 = first ? 1.0 : 2.0, a1 = first ? 0.0 : -0.5;
@@ -2135,6 +2169,7 @@ bool same_group(const imex_ctx* a, const imex_ctx* b) {
   if (a->desc.tol != b->desc.tol || a->desc.maxit != b->desc.maxit || a->desc.vmax != b->desc.vmax) return false;
   if (a->nu_kind != b->nu_kind || a->bc_kind != b->bc_kind || a->f_kind != b->f_kind) return false;
   if (a->use_sdc || b->use_sdc || a->use_bdf2 || b->use_bdf2) return false;
+  if (a->stab_zd > 0.0 || a->stab_zc > 0.0 || b->stab_zd > 0.0 || b->stab_zc > 0.0) return false;
   if (a->pmg.kind != b->pmg.kind || a->pmg.pre != b->pmg.pre || a->pmg.coarse != b->pmg.coarse ||
       a->pmg.ratio != b->pmg.ratio || a->pmg.cratio != b->pmg.cratio)
     return false;
@@ -2526,6 +2561,39 @@ imex_status imex_set_sdc(imex_ctx* c, int M, int K, const char* predictor) {
   c->use_sdc = true;
   c->use_bdf2 = false;
   return IMEX_OK;
+}
+
+imex_status imex_set_stabilization(imex_ctx* c, double zeta_d, double zeta_c) {
+  if (!c || !(zeta_d >= 0.0) || !(zeta_c >= 0.0)) return IMEX_EINVAL;
+  if (c->batched) return fail(c, IMEX_EINVAL, "stabilisation of batched instances is not supported");
+  if ((zeta_d > 0.0 || zeta_c > 0.0) && !c->stab_speed) {
+    const size_t nt = c->nv * c->d;
+    TRY(dalloc(c, &c->stab_speed, (size_t)c->gv.ne));
+    TRY(dalloc(c, &c->stab_minv, nt));
+    for (int k = 0; k < c->d; ++k)
+      CK(cudaMemcpyAsync(c->stab_minv + k * c->nv, c->mass_v, c->nv * sizeof(double), cudaMemcpyDeviceToDevice,
+                         c->st), "cp");
+    reciprocal<double>(c->stab_minv, nt, c->st);
+    const long long off = 0, len = (long long)nt;
+    TRY(make_seg(c, 1, &off, &off, &len, &c->segs, 1, (int)(nt / SEG_CHUNK) + 2));
+  }
+  c->stab_zd = zeta_d;
+  c->stab_zc = zeta_c;
+  return IMEX_OK;
+}
+
+imex_status imex_stabilize(imex_ctx* c, const double* v, double dt, double* out, int on_device) {
+  if (!c || !v || !out || !(dt > 0.0)) return IMEX_EINVAL;
+  if (!(c->stab_zd > 0.0 || c->stab_zc > 0.0)) return fail(c, IMEX_EINVAL, "stabilisation is off");
+  const size_t nt = c->nv * c->d;
+  TRY(copy_in(c, c->vpp, v, nt, on_device));
+  const double saved = c->cur_dt;
+  c->cur_dt = dt;
+  c->stab_iters = 0;
+  imex_status s = stabilize(c, c->vpp);
+  c->cur_dt = saved;
+  TRY(s);
+  return copy_out(c, out, c->vpp, nt, on_device);
 }
 
 imex_status imex_set_bdf2(imex_ctx* c) {
@@ -3029,7 +3097,9 @@ imex_status imex_batch_create(imex_ctx* const* insts, int n, imex_batch** out) {
   *out = nullptr;
   for (int i = 0; i < n; ++i) {
     if (!insts[i] || insts[i]->batched) return IMEX_EINVAL;
-    if (insts[i]->use_sdc || insts[i]->use_bdf2 || insts[i]->nu_kind == IMEX_NU_FIELD) return IMEX_EINVAL;
+    if (insts[i]->use_sdc || insts[i]->use_bdf2 || insts[i]->nu_kind == IMEX_NU_FIELD || insts[i]->stab_zd > 0.0 ||
+        insts[i]->stab_zc > 0.0)
+      return IMEX_EINVAL;
     if (has_boundary(insts[i]) && insts[i]->bc_kind == IMEX_FLOW_NONE) return IMEX_EINVAL;
   }
   imex_batch* b = new imex_batch();

@@ -211,6 +211,13 @@ int dissipation_elems(const Geom& g, int N, const double* v, long long stride, c
 int energy_spectrum(const Geom& g, int N, const double* v, long long stride, int M, int kmax, double vol,
                     double2* grid, double* part, int nbin_blocks, double* E, cudaStream_t st);
 
+// ---- divergence / mass-flux stabilisation (k_stab.cu) ---------------------------
+// speed[e] = |mass-weighted mean velocity of element e|
+int stab_speed(const Geom& g, int N, const double* v, long long stride, double* speed, cudaStream_t st);
+// y = (M + A_D + A_C) u for the d components (stride apart) with the element speeds
+int stab_apply(const Geom& g, int N, const double* u, double* y, long long stride, const double* speed, double zd,
+               double zc, double dt, cudaStream_t st);
+
 // ---- pointwise fields (k_fields.cu) --------------------------------------------
 // what: 0 velocity of a closed-form flow (d components), 1 viscosity (1 component),
 //       2 forcing (d components).  kind / p: the flow, viscosity law or forcing and its

@@ -85,6 +85,8 @@ _SIGS = {
     "imex_set_tableau_named": [_P, C.c_char_p],
     "imex_set_sdc": [_P, C.c_int, C.c_int, C.c_char_p],
     "imex_set_bdf2": [_P],
+    "imex_set_stabilization": [_P, C.c_double, C.c_double],
+    "imex_stabilize": [_P, _P, C.c_double, _P, C.c_int],
     "imex_set_viscosity_const": [_P, C.c_double],
     "imex_set_viscosity_model": [_P, C.c_int, _P, C.c_int],
     "imex_set_viscosity_field": [_P, _P, C.c_int],
@@ -272,6 +274,16 @@ class Context:
 
     def set_sdc(self, M, K, predictor="EULER"):
         self._check(load().imex_set_sdc(self._h, M, K, predictor.encode()))
+
+    def set_stabilization(self, zeta_d, zeta_c):
+        self._check(load().imex_set_stabilization(self._h, zeta_d, zeta_c))
+
+    def stabilize(self, v, dt):
+        out = np.empty((self.dim, self.nvel))
+        pv, dev, _a = _arr(v, self.dim * self.nvel)
+        po, _, _b = _arr(out, self.dim * self.nvel, writable=True)
+        self._check(load().imex_stabilize(self._h, pv, dt, po, dev))
+        return out
 
     def set_bdf2(self):
         self._check(load().imex_set_bdf2(self._h))
