@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--precond", default="pmg", choices=["jacobi", "pmg"],
                     help="preconditioner of the pressure solves")
+    ap.add_argument("--pmg", default="", help="V-cycle parameters: smoothing steps, coarsest-level steps, "
+                    "smoothing range, coarsest range (comma-separated; empty: library defaults)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-only", action="store_true", help="short run for ncu captures")
@@ -230,7 +232,8 @@ def make_ctx(imex, args, precision, stream):
                        tol=args.tol, maxit=20000, stream=stream)
     ctx.set_viscosity_const(1.0 / 1600.0)
     ctx.set_tableau_named("CB3e")
-    ctx.set_pressure_precond(imex.PRECOND_PMG if args.precond == "pmg" else imex.PRECOND_JACOBI)
+    ctx.set_pressure_precond(imex.PRECOND_PMG if args.precond == "pmg" else imex.PRECOND_JACOBI,
+                             [float(v) for v in args.pmg.split(",")] if args.pmg else ())
     ctx.init_flow(imex.FLOW_TG3D, [0.0])
     return ctx
 
@@ -523,7 +526,7 @@ def main():
                           "warmup": args.warmup, "ms_per_step": e["ms_per_step"], "higher_is_better": True,
                           "scaling": "weak", "vs_baseline": None, "dtype": "f32 operators + f64 refinement",
                           "data": "synthetic (closed-form Taylor-Green)", "config": {"workload": e["workload"]},
-                          "ensemble": e}))
+                          "ensemble": e, "tuning": imex.tuning_info()}))
         return 0
 
     if args.workload == "ops":
@@ -671,6 +674,7 @@ def main():
             "clocks": clocks, "gpu_launches": launches, "roofline": roof, "kernels": prof,
             "e2e": e2e, "fp64": fp64, "cpu_baseline": cpu, "ensemble": ens, "serving": serving,
             "operators_above_l2": ops,
+            "tuning": imex.tuning_info(),
             "solver": {"poisson_iters_per_call": stats["poisson_iters"], "helmholtz_iters": stats["helmholtz_iters"],
                        "refinements": stats["refinements"], "max_poisson_res": stats["max_poisson_res"],
                        "max_helmholtz_res": stats["max_helmholtz_res"]},

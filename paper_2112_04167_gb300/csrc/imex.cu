@@ -16,6 +16,7 @@
 #include <deque>
 #include <string>
 #include <thread>
+#include <mutex>
 #include <vector>
 
 #include "../../include/imex.h"
@@ -478,6 +479,7 @@ SipgArgs<T> sipg_args(const T* x, T* y, int nsys, long long stride, const T* nu,
   a.done_ninst = 0;
   a.inst_nu = 0;
   a.inst_dt = 0;
+  a.variant = 0;
   a.cheb = 0;
   a.ch_last = 0;
   a.ch_r = a.ch_dout = a.ch_s = nullptr;
@@ -540,6 +542,28 @@ bool ff_class(const imex_ctx* c) {
   return c->desc.precision == IMEX_MIXED || c->desc.precision == IMEX_MIXED_FAST;
 }
 
+// ---- launch-shape tuner ----------------------------------------------------------------
+// The periodic constant-viscosity SIPG kernels (the CG and V-cycle applies) exist in three
+// launch shapes: the default elements per block, half and twice as many.  On first use for a
+// (d, N, precision, element count) the tuner times each shape with CUDA events on the
+// context's stream (outside any graph capture) and keeps the fastest, when it beats the
+// default by more than 3%; the choice is cached for the process.  IMEX_TUNE=0 disables it.
+struct TuneEntry {
+  int d, N, f32;
+  long long ne;
+  int variant;
+  double us[3];
+};
+std::mutex g_tune_mu;
+std::vector<TuneEntry> g_tune;
+
+int tuned_variant(const imex_ctx* c, int N, bool f32) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  for (const auto& t : g_tune)
+    if (t.d == c->d && t.N == N && t.f32 == (int)f32 && t.ne == c->gp.ne) return t.variant;
+  return 0;
+}
+
 // arithmetic of an operator apply of type T on this context (the FP64 applies of the mixed
 // forms run in float-float)
 template <typename T>
@@ -571,6 +595,7 @@ imex_status apply_pressure(imex_ctx* c, const T* x, T* y, T* vtmp, const CgScala
   if (c->desc.poisson == IMEX_POISSON_SIPG) {
     SipgArgs<T> a = sipg_args<T>(x, y, 1, (long long)c->np, nullptr, 1.0, nullptr, 0.0, 1.0, 0);
     a.ops = line_ops<T>(c, false);
+    a.variant = tuned_variant(c, c->Np, sizeof(T) == 4);
     fuse_cg(c, a, cg);
     skip_stopped_elems(c, a, skip_stopped);
     prof_mark(c, cls, true);
@@ -592,6 +617,7 @@ imex_status apply_helm(imex_ctx* c, const T* x, T* y, int nsys, const T* nu, dou
   const int cls = sizeof(T) == 4 ? IMEX_PROF_HELMHOLTZ_F32 : IMEX_PROF_HELMHOLTZ_F64;
   SipgArgs<T> a = sipg_args<T>(x, y, nsys, (long long)c->nv, nu, nu_const(c), nullptr, 1.0, gamma, 0);
   a.ops = line_ops<T>(c, true);
+  if (!nu) a.variant = tuned_variant(c, c->Nv, sizeof(T) == 4);
   vel_flags(c, a, true);
   fuse_cg(c, a, cg);
   skip_stopped_elems(c, a, skip_stopped);
@@ -1122,6 +1148,7 @@ imex_status pmg_apply(imex_ctx* c, int l, const T* x, T* y) {
   const size_t n = (size_t)c->gp.ne * ipow(M.N[l], c->d);
   SipgArgs<T> a = sipg_args<T>(x, y, 1, (long long)n, nullptr, 1.0, nullptr, 0.0, 1.0, 0);
   a.ops = PmgVecs<T>::ops(M)[l];
+  a.variant = tuned_variant(c, M.N[l], sizeof(T) == 4);
   prof_mark(c, IMEX_PROF_PMG_APPLY, true);
   const int rc = sipg_apply<T>(c->gp, M.N[l], a, c->st);
   prof_end(c, IMEX_PROF_PMG_APPLY, 2.0 * sizeof(T) * n, sipg_flops_per_node(c->d, M.N[l]) * n, arith_t<T>());
@@ -1205,6 +1232,7 @@ imex_status pmg_smooth(imex_ctx* c, int l, int steps, double lmax, double ratio,
     const int last = k == steps - 1 ? 1 : 0;
     SipgArgs<T> a = sipg_args<T>(dcur, nullptr, 1, (long long)n, nullptr, 1.0, nullptr, 0.0, 1.0, 0);
     a.ops = V::ops(M)[l];
+    a.variant = tuned_variant(c, M.N[l], sizeof(T) == 4);
     a.cheb = 1;
     a.ch_last = last;
     a.ch_r = r;
@@ -1262,6 +1290,54 @@ imex_status pmg_vcycle(imex_ctx* c, const T* r, T* z, const double* lm) {
   return cuda_check(c, cudaGetLastError(), "pmg_vcycle");
 }
 
+// Tune the launch shape of the periodic constant-viscosity apply on N points of type T
+// (nsys systems of the space's size n, its line operators ops): times each shape on the
+// work vectors x, y (contents irrelevant) and records the choice.
+template <typename T>
+imex_status tune_apply(imex_ctx* c, int N, int nsys, size_t n, const LineOps<T>* ops, const T* x, T* y) {
+  for (int k = 0; k < c->d; ++k)
+    if (c->gp.bc[k] != 0) return IMEX_OK;                 // the tuned kernels are the periodic ones
+  const char* env = std::getenv("IMEX_TUNE");
+  if (env && env[0] == '0') return IMEX_OK;
+  const bool f32 = sizeof(T) == 4;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    for (const auto& t : g_tune)
+      if (t.d == c->d && t.N == N && t.f32 == (int)f32 && t.ne == c->gp.ne) return IMEX_OK;
+  }
+  const int nvar = (c->d == 2 && !f32) ? 2 : 3;           // 2D FP64: no doubled block (static shared memory)
+  TuneEntry te{c->d, N, (int)f32, c->gp.ne, 0, {0, 0, 0}};
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0), "event");
+  CK(cudaEventCreate(&e1), "event");
+  for (int v = 0; v < nvar; ++v) {
+    SipgArgs<T> a = sipg_args<T>(x, y, nsys, (long long)n, nullptr, 1.0, nullptr, 0.0, 1.0, 0);
+    a.ops = ops;
+    a.variant = v;
+    double best = 1e30;
+    for (int it = 0; it < 7; ++it) {
+      CK(cudaEventRecord(e0, c->st), "event");
+      const int rc = sipg_apply<T>(c->gp, N, a, c->st);
+      CK(cudaEventRecord(e1, c->st), "event");
+      TRY(launch_check(c, rc, "sipg_apply(tune)"));
+      CK(cudaEventSynchronize(e1), "event");
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (it >= 2) best = std::min(best, 1e3 * (double)ms);
+    }
+    te.us[v] = best;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  int pick = 0;
+  for (int v = 1; v < nvar; ++v)
+    if (te.us[v] < 0.97 * te.us[0] && te.us[v] < te.us[pick]) pick = v;
+  te.variant = pick;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune.push_back(te);
+  return IMEX_OK;
+}
+
 // ---- solves ------------------------------------------------------------------------
 // Poisson: L psi = b (b is overwritten by its mean-free part); psi: initial guess in, solution out
 imex_status solve_poisson(imex_ctx* c, double* b, double* psi, long long* iters, double* res) {
@@ -1281,6 +1357,20 @@ imex_status solve_poisson(imex_ctx* c, double* b, double* psi, long long* iters,
   if (pm) {
     if (c->desc.precision != IMEX_FP64) TRY(pmg_alloc<float>(c));
     TRY(pmg_setup(c));
+  }
+  if (c->desc.poisson == IMEX_POISSON_SIPG) {
+    // launch shapes of the CG and V-cycle applies (first use only)
+    if (c->desc.precision == IMEX_FP64) {
+      TRY(tune_apply<double>(c, c->Np, 1, n, c->ops64_p, c->cx, c->cAp));
+      for (int l = 1; pm && l < c->pmg.nlev; ++l)
+        TRY(tune_apply<double>(c, c->pmg.N[l], 1, (size_t)c->gp.ne * ipow(c->pmg.N[l], c->d), c->pmg.ops64[l],
+                               c->pmg.r64[l], c->pmg.ad64[l]));
+    } else {
+      TRY(tune_apply<float>(c, c->Np, 1, n, c->ops32_p, c->fx, c->fAp));
+      for (int l = 1; pm && l < c->pmg.nlev; ++l)
+        TRY(tune_apply<float>(c, c->pmg.N[l], 1, (size_t)c->gp.ne * ipow(c->pmg.N[l], c->d), c->pmg.ops32[l],
+                              c->pmg.r32[l], c->pmg.ad32[l]));
+    }
   }
   if (c->desc.precision == IMEX_FP64) {
     auto op = [&](const double* x, double* y) { return apply_pressure<double>(c, x, y, c->tmp); };
@@ -1335,6 +1425,10 @@ imex_status solve_helmholtz(imex_ctx* c, const double* rhs, double* x, const dou
   // the chunk graphs depend on gamma, on whether the viscosity is a field and on its constant
   // value (captured into the kernels' arguments)
   const std::vector<unsigned long long> hkey = {2, bits(gamma), addr(nu), (unsigned long long)d, bits(nu_const(c))};
+  if (!nu && !c->batched) {
+    if (c->desc.precision == IMEX_FP64) TRY(tune_apply<double>(c, c->Nv, d, n, c->ops64_v, c->cx, c->cAp));
+    else TRY(tune_apply<float>(c, c->Nv, d, n, c->ops32_v, c->fx, c->fAp));
+  }
   if (c->desc.precision == IMEX_FP64) {
     auto op = [&](const double* xx, double* yy) { return apply_helm<double>(c, xx, yy, d, nu, gamma); };
     auto opd = [&](const double* xx, double* yy, const CgScalars* dd) {
@@ -2750,6 +2844,7 @@ imex_status imex_op_sipg(imex_ctx* c, int space, const double* x, double* y, int
   } else if (arith == IMEX_ARITH_FP64) {
     SipgArgs<double> a = sipg_args<double>(c->cx, c->cAp, nsys, (long long)n, dnu, nu0, dg, alpha, beta, minv);
     a.ops = line_ops<double>(c, vel);
+    a.variant = tuned_variant(c, N, false);
     prof_mark(c, cls64, true);
     const int rc = sipg_apply<double>(g, N, a, c->st);
     prof_end(c, cls64, 8.0 * words, flops, IMEX_ARITH_FP64);
@@ -2762,6 +2857,7 @@ imex_status imex_op_sipg(imex_ctx* c, int space, const double* x, double* y, int
     if (dg) { convert_d2f(dg, c->fr, n * nsys, c->st); fg = c->fr; }
     SipgArgs<float> a = sipg_args<float>(c->fx, c->fAp, nsys, (long long)n, fnu, nu0, fg, alpha, beta, minv);
     a.ops = line_ops<float>(c, vel);
+    a.variant = tuned_variant(c, N, true);
     prof_mark(c, cls32, true);
     const int rc = sipg_apply<float>(g, N, a, c->st);
     prof_end(c, cls32, 4.0 * words, flops, IMEX_ARITH_FP32);
@@ -3077,6 +3173,34 @@ imex_status imex_profile_work(imex_ctx* c, int cls, double* bytes, double* flops
   if (flops) *flops = c->profc[cls].flops;
   if (arith) *arith = c->profc[cls].arith;
   return IMEX_OK;
+}
+
+int imex_set_apply_variant(int d, int N, int fp32, long long ne, int variant) {
+  if ((d != 2 && d != 3) || N < 2 || N > IMEX_MAXN || ne < 1 || variant < 0 || variant > 2 ||
+      (d == 2 && !fp32 && variant == 2))
+    return IMEX_EINVAL;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  for (auto& t : g_tune)
+    if (t.d == d && t.N == N && t.f32 == (fp32 ? 1 : 0) && t.ne == ne) {
+      t.variant = variant;
+      return IMEX_OK;
+    }
+  g_tune.push_back(TuneEntry{d, N, fp32 ? 1 : 0, ne, variant, {0, 0, 0}});
+  return IMEX_OK;
+}
+
+int imex_tuning_info(int i, int* d, int* N, int* fp32, long long* ne, int* variant, double* us) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  if (i < 0) return (int)g_tune.size();
+  if (i >= (int)g_tune.size()) return -1;
+  const TuneEntry& t = g_tune[i];
+  if (d) *d = t.d;
+  if (N) *N = t.N;
+  if (fp32) *fp32 = t.f32;
+  if (ne) *ne = t.ne;
+  if (variant) *variant = t.variant;
+  if (us) for (int k = 0; k < 3; ++k) us[k] = t.us[k];
+  return (int)g_tune.size();
 }
 
 long long imex_launch_count(void) { return imex::launch_count(); }

@@ -876,19 +876,24 @@ template <> __device__ __forceinline__ const ConstLine<double>& cline<double>(in
 // of an element; the block's elements are contiguous in memory and are staged into shared
 // memory with fully coalesced loads.  Many elements per block keep the grid within about
 // one wave of resident blocks.
-template <typename T, int N>
+// elements per block of the tuned kernels: variant 0 the default, 1 half of it, 2 twice it
+__host__ __device__ constexpr int epb_variant(int base, int V) {
+  return V == 1 ? (base / 2 > 0 ? base / 2 : 1) : (V == 2 ? base * 2 : base);
+}
+
+template <typename T, int N, int V = 0>
 struct Sipg2lShape {
   static constexpr int NN = N * N;
-  static constexpr int EPB = 256 / N;
+  static constexpr int EPB = epb_variant(256 / N, V);
   static constexpr int THREADS = EPB * N;
   static constexpr int VEC = 16 / sizeof(T);
   static constexpr int NP = ((N + VEC - 1) / VEC) * VEC;
 };
 
-template <typename T, int N>
-__global__ void __launch_bounds__(Sipg2lShape<T, N>::THREADS)
+template <typename T, int N, int V = 0>
+__global__ void __launch_bounds__(Sipg2lShape<T, N, V>::THREADS)
 sipg2l_apply_kernel(Geom g, SipgArgs<T> a) {
-  using S = Sipg2lShape<T, N>;
+  using S = Sipg2lShape<T, N, V>;
   constexpr int NN = S::NN, EPB = S::EPB, NP = S::NP, VEC = S::VEC;
   __shared__ __align__(16) T tile[EPB][N][NP];
   __shared__ T acc[EPB][NN];
@@ -955,11 +960,11 @@ sipg2l_apply_kernel(Geom g, SipgArgs<T> a) {
     T dacc = T(0);
     if (live) {
       T v[NP], vl[N], vr[N];
-      using V = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
-      const V* rv = reinterpret_cast<const V*>(&tile[le][ta][0]);
+      using VT = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+      const VT* rv = reinterpret_cast<const VT*>(&tile[le][ta][0]);
 #pragma unroll
       for (int q = 0; q < NP / VEC; ++q) {
-        const V w4 = rv[q];
+        const VT w4 = rv[q];
         const T* pw = reinterpret_cast<const T*>(&w4);
 #pragma unroll
         for (int j = 0; j < VEC; ++j) v[q * VEC + j] = pw[j];
@@ -994,13 +999,13 @@ sipg2l_apply_kernel(Geom g, SipgArgs<T> a) {
   if (a.dot_out) fused_dot_finish(a, red);
 }
 
-template <typename T, int N>
+template <typename T, int N, int V = 0>
 struct Sipg3pShape {
   static constexpr int NN = N * N;
   static constexpr int VEC = 16 / sizeof(T);                       // elements per 16-byte load
   static constexpr int NP = ((N + VEC - 1) / VEC) * VEC;           // padded row length
   static constexpr int TILE = N * N * NP;
-  static constexpr int EPB = (NN >= 49) ? 4 : (NN >= 16 ? 256 / NN : 16);
+  static constexpr int EPB = epb_variant((NN >= 49) ? 4 : (NN >= 16 ? 256 / NN : 16), V);
   static constexpr int THREADS = EPB * NN;
 };
 
@@ -1018,7 +1023,7 @@ __device__ __forceinline__ T sipg3p_group(const Geom& g, const SipgArgs<T>& a, c
                                           T* __restrict__ y, int grp) {
   using S = Sipg3pShape<T, N>;
   constexpr int NN = S::NN, ND = N * N * N, EPB = S::EPB, NP = S::NP, TILE = S::TILE, VEC = S::VEC;
-  using V = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+  using VT = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* tile = reinterpret_cast<T*>(smem_raw);                       // [EPB][z][y][NP]
   T (*sf)[8][NN] = reinterpret_cast<T (*)[8][NN]>(tile + EPB * TILE);
@@ -1108,10 +1113,10 @@ __device__ __forceinline__ T sipg3p_group(const Geom& g, const SipgArgs<T>& a, c
       for (int k = 0; k < N; ++k) {
         // x: the padded row (y = i1, z = k) by 16-byte loads
         T row[NP];
-        const V* rv = reinterpret_cast<const V*>(mytile + (k * N + i1) * NP);
+        const VT* rv = reinterpret_cast<const VT*>(mytile + (k * N + i1) * NP);
 #pragma unroll
         for (int q = 0; q < NP / VEC; ++q) {
-          const V v = rv[q];
+          const VT v = rv[q];
           if (VEC == 4) {
             const float4 f = *reinterpret_cast<const float4*>(&v);
             reinterpret_cast<float*>(row)[4 * q + 0] = f.x;
@@ -1156,20 +1161,20 @@ __device__ __forceinline__ T sipg3p_group(const Geom& g, const SipgArgs<T>& a, c
 // 1D operator from registers; the three directional contributions meet in a shared
 // accumulator.  Per node: about one shared load and two global loads per pass instead of a
 // strided shared read for every term.
-template <typename T, int N>
+template <typename T, int N, int V = 0>
 struct Sipg3lShape {
   static constexpr int NN = N * N;
   static constexpr int ND = N * N * N;
-  static constexpr int EPB = (NN >= 49) ? 4 : (NN >= 16 ? 256 / NN : 16);
+  static constexpr int EPB = epb_variant((NN >= 49) ? 4 : (NN >= 16 ? 256 / NN : 16), V);
   static constexpr int THREADS = EPB * NN;
   static constexpr int VEC = 16 / sizeof(T);
   static constexpr int NP = ((N + VEC - 1) / VEC) * VEC;
   static constexpr int TILE = N * N * NP;
 };
 
-template <typename T, int N>
+template <typename T, int N, int V = 0>
 constexpr size_t sipg3l_smem() {
-  using S = Sipg3lShape<T, N>;
+  using S = Sipg3lShape<T, N, V>;
   return sizeof(T) * (size_t)(S::EPB * S::TILE + S::EPB * S::ND);
 }
 
@@ -1190,10 +1195,10 @@ __device__ __forceinline__ LineFaces<T> line_faces(const ConstLine<T>& L, const 
   return f;
 }
 
-template <typename T, int N, typename TS = T>
+template <typename T, int N, typename TS = T, int V = 0>
 __device__ __forceinline__ T sipg3l_group(const Geom& g, const SipgArgs<TS>& a, const TS* __restrict__ x,
                                           TS* __restrict__ y, int grp, int sys = 0) {
-  using S = Sipg3lShape<T, N>;
+  using S = Sipg3lShape<T, N, V>;
   constexpr int NN = S::NN, ND = S::ND, EPB = S::EPB, NP = S::NP, TILE = S::TILE, VEC = S::VEC;
   // FP32 up to N = 8: all neighbour lines are loaded before the first pass, so that their
   // latency is paid once rather than after each of the two barriers (12 scalars stay live);
@@ -1286,11 +1291,11 @@ __device__ __forceinline__ T sipg3l_group(const Geom& g, const SipgArgs<TS>& a, 
   T dacc = T(0);
   if (live) {
     T v[NP];
-    using V = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
-    const V* rv = reinterpret_cast<const V*>(mt + (tb * N + ta) * NP);
+    using VT = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+    const VT* rv = reinterpret_cast<const VT*>(mt + (tb * N + ta) * NP);
 #pragma unroll
     for (int q = 0; q < NP / VEC; ++q) {
-      const V w4 = rv[q];
+      const VT w4 = rv[q];
       const T* pw = reinterpret_cast<const T*>(&w4);
 #pragma unroll
       for (int j = 0; j < VEC; ++j) v[q * VEC + j] = pw[j];
@@ -1320,10 +1325,14 @@ __device__ __forceinline__ T sipg3l_group(const Geom& g, const SipgArgs<TS>& a, 
 #ifndef IMEX_SIPG3P_MINB
 #define IMEX_SIPG3P_MINB 5
 #endif
-template <typename T, int N, typename TS = T>
-__global__ void __launch_bounds__(Sipg3pShape<T, N>::THREADS, (sizeof(T) == 4 && N <= 8) ? IMEX_SIPG3P_MINB : 1)
+// resident blocks asked of the compiler: IMEX_SIPG3P_MINB for the FP32 default and halved
+// shapes; none for the doubled blocks (a forced count would make them spill)
+__host__ __device__ constexpr int sipg3p_minb(int V, bool f32) { return (!f32 || V == 2) ? 1 : IMEX_SIPG3P_MINB; }
+template <typename T, int N, typename TS = T, int V = 0>
+__global__ void __launch_bounds__(Sipg3pShape<T, N, V>::THREADS,
+                                  sipg3p_minb(V, sizeof(T) == 4 && N <= 8))
 sipg3p_apply_kernel(Geom g, SipgArgs<TS> a) {
-  __shared__ double red[Sipg3pShape<T, N>::THREADS];
+  __shared__ double red[Sipg3pShape<T, N, V>::THREADS];
   pdl_trigger();
   for (int s = 0; s < a.nsys; ++s) {
     if (s > 0) __syncthreads();
@@ -1331,8 +1340,8 @@ sipg3p_apply_kernel(Geom g, SipgArgs<TS> a) {
       if (a.dot_out && threadIdx.x == 0) put_dot_partial(a, s, 0.0);
       continue;
     }
-    const T dacc = sipg3l_group<T, N, TS>(g, a, a.x + (size_t)s * a.sys_stride, a.y + (size_t)s * a.sys_stride,
-                                          blockIdx.x, s);
+    const T dacc = sipg3l_group<T, N, TS, V>(g, a, a.x + (size_t)s * a.sys_stride,
+                                             a.y + (size_t)s * a.sys_stride, blockIdx.x, s);
     if (a.dot_out) {
       const double bs = block_sum_any_t<T>(dacc, red);
       if (threadIdx.x == 0) put_dot_partial(a, s, bs);
@@ -1724,11 +1733,24 @@ sipg_diag_kernel(Geom g, SipgArgs<T> a) {
   a.y[(size_t)e * ND + node] = a.alpha * Wq + sipg_beta(a, gl) * diag;
 }
 
+template <typename T, int N, int V>
+static void launch_apply2l(const Geom& g, const SipgArgs<T>& a, cudaStream_t st) {
+  using C = Sipg2lShape<T, N, V>;
+  IMEX_COUNTED((sipg2l_apply_kernel<T, N, V><<<(g.ne + C::EPB - 1) / C::EPB, C::THREADS, 0, st>>>(g, a)));
+}
+
 template <typename T, int D, int N>
 static void launch_apply(const Geom& g, const SipgArgs<T>& a, cudaStream_t st) {
   if (D == 2 && !a.nu && a.ops && g.bc[0] == 0 && g.bc[1] == 0 && N <= IMEX_MAXN) {
-    using C = Sipg2lShape<T, N>;
-    IMEX_COUNTED(sipg2l_apply_kernel<T, N><<<(g.ne + C::EPB - 1) / C::EPB, C::THREADS, 0, st>>>(g, a));
+    // the variant chosen by the tuner (twice the elements per block: FP32 only, for the
+    // static shared memory)
+    if (a.variant == 1) launch_apply2l<T, N, 1>(g, a, st);
+    else if constexpr (sizeof(T) == 4) {
+      if (a.variant == 2) launch_apply2l<T, N, 2>(g, a, st);
+      else launch_apply2l<T, N, 0>(g, a, st);
+    } else {
+      launch_apply2l<T, N, 0>(g, a, st);
+    }
     return;
   }
   if (D == 2 && !a.nu && a.ops) {
@@ -1743,13 +1765,20 @@ static void launch_apply(const Geom& g, const SipgArgs<T>& a, cudaStream_t st) {
   IMEX_COUNTED(sipg_apply_kernel<T, D, N><<<blocks, S::THREADS, 0, st>>>(g, a));
 }
 
+template <typename T, int N, int V>
+static void launch_apply3p(const Geom& g, const SipgArgs<T>& a, cudaStream_t st) {
+  using P = Sipg3pShape<T, N, V>;
+  constexpr size_t sm = sipg3l_smem<T, N, V>();
+  smem_limit_once((const void*)sipg3p_apply_kernel<T, N, T, V>, (int)sm);
+  launch_cg_kernel(sipg3p_apply_kernel<T, N, T, V>, (g.ne + P::EPB - 1) / P::EPB, P::THREADS, sm, st, g, a);
+}
+
 template <typename T, int D, int N>
 static void launch_apply3(const Geom& g, const SipgArgs<T>& a, cudaStream_t st) {
   if (!a.nu && a.ops && g.bc[0] == 0 && g.bc[1] == 0 && g.bc[2] == 0) {
-    using P = Sipg3pShape<T, N>;
-    constexpr size_t sm = sipg3l_smem<T, N>();
-    smem_limit_once((const void*)sipg3p_apply_kernel<T, N>, (int)sm);
-    launch_cg_kernel(sipg3p_apply_kernel<T, N>, (g.ne + P::EPB - 1) / P::EPB, P::THREADS, sm, st, g, a);
+    if (a.variant == 1) launch_apply3p<T, N, 1>(g, a, st);
+    else if (a.variant == 2) launch_apply3p<T, N, 2>(g, a, st);
+    else launch_apply3p<T, N, 0>(g, a, st);
     return;
   }
   if (!a.nu && a.ops) {

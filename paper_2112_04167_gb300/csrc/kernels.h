@@ -49,6 +49,9 @@ struct SipgArgs {
   // instead of y = A x the kernel updates, node by node, r -= A x, d' = c1 x + c2 D^{-1} r,
   // s += d' (x is the previous direction; d' goes to a buffer other than x); with ch_last
   // only s is stored.  cheb = 0: the plain apply.
+  // launch shape chosen by the tuner for the periodic constant-viscosity kernels (elements
+  // per block: 0 the default, 1 half, 2 twice; other kernels ignore it)
+  int variant;
   int cheb;
   int ch_last;
   T* ch_r;

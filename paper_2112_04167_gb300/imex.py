@@ -119,6 +119,9 @@ _SIGS = {
     "imex_profile_read": [_P, C.c_int, C.POINTER(C.c_longlong), _D],
     "imex_profile_work": [_P, C.c_int, _D, _D, C.POINTER(C.c_int)],
     "imex_launch_count": [],
+    "imex_set_apply_variant": [C.c_int, C.c_int, C.c_int, C.c_longlong, C.c_int],
+    "imex_tuning_info": [C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
+                         C.POINTER(C.c_longlong), C.POINTER(C.c_int), _D],
     "imex_batch_create": [C.POINTER(_P), C.c_int, C.POINTER(_P)],
     "imex_batch_destroy": [_P],
     "imex_batch_last_error": [_P],
@@ -150,6 +153,28 @@ REDUCE_DOT, REDUCE_SUM, REDUCE_MAXABS = range(3)
 
 def exported_symbols():
     return sorted(_SIGS)
+
+
+def tuning_info():
+    """Launch shapes chosen by the apply tuner: one dict per tuned (d, N, precision, elements)."""
+    lib = load()
+    out = []
+    n = lib.imex_tuning_info(-1, None, None, None, None, None, None)
+    for i in range(n):
+        d, N, f32, v = C.c_int(), C.c_int(), C.c_int(), C.c_int()
+        ne = C.c_longlong()
+        us = (C.c_double * 3)()
+        lib.imex_tuning_info(i, C.byref(d), C.byref(N), C.byref(f32), C.byref(ne), C.byref(v), us)
+        out.append({"d": d.value, "N": N.value, "fp32": bool(f32.value), "elements": ne.value, "variant": v.value,
+                    "us": [round(x, 2) for x in us]})
+    return out
+
+
+def set_apply_variant(d, N, fp32, elements, variant):
+    """Fix the launch shape of the periodic constant-viscosity apply (imex_set_apply_variant)."""
+    st = load().imex_set_apply_variant(d, N, int(bool(fp32)), elements, variant)
+    if st != OK:
+        raise ImexError(st, "imex_set_apply_variant failed")
 
 
 def launch_count():
