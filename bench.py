@@ -48,6 +48,8 @@ def parse():
                     "smoothing range, coarsest range (comma-separated; empty: library defaults)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra-configs", action="store_true",
+                    help="skip the SDC / BDF2 lines, the 2D Taylor-Green run and the Dirichlet dt sweep")
     ap.add_argument("--profile-only", action="store_true", help="short run for ncu captures")
     ap.add_argument("--workload", default="tg3d", choices=["tg3d", "ensemble", "serving", "ops"],
                     help="tg3d: the headline line; ensemble / serving / ops: that workload alone")
@@ -253,9 +255,10 @@ def timed_steps(torch, ctx, stream, dt, k):
     return [a.elapsed_time(b) for a, b in evs]
 
 
-def cpu_baseline_sample(P, dt, nelem=2, nsteps=1, timeout=900):
-    """The oracle (1 thread) on RK-CB3e steps of the same flow on an nelem^3 periodic mesh:
-    one setup (assembly and factorisations), then nsteps steps each timed."""
+def cpu_baseline_sample(P, dt, nelem=2, nsteps=1, timeout=900, threads=1):
+    """The oracle (`threads` BLAS / OpenMP threads) on RK-CB3e steps of the same flow on an
+    nelem^3 periodic mesh: one setup (assembly and factorisations), then nsteps steps each
+    timed."""
     code = f"""
 import sys, time, json
 sys.path.insert(0, {ROOT!r})
@@ -276,17 +279,165 @@ for _ in range({nsteps}):
     t += {dt}
 print(json.dumps({{"setup_s": setup, "steps_s": steps, "nvel": int(disc.nv)}}))
 """
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    nt = str(threads)
+    env = dict(os.environ, OMP_NUM_THREADS=nt, OPENBLAS_NUM_THREADS=nt, MKL_NUM_THREADS=nt)
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=timeout)
     if r.returncode != 0:
         return None, r.stderr[-400:]
     d = json.loads(r.stdout.strip().splitlines()[-1])
     per = [3 * d["nvel"] * 3 / s for s in d["steps_s"]]
     sample = (f"RK-CB3e steps of the same flow (P={P}, nu=1/1600, dt={dt}) on a {nelem}^3-element periodic mesh "
-              f"({3 * d['nvel']} velocity DOF), 1 thread; one-off setup {d['setup_s']:.1f} s not counted, "
-              f"{sum(d['steps_s']):.1f} s of steps")
-    return {"value": statistics.mean(per), "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+              f"({3 * d['nvel']} velocity DOF), {threads} thread(s); one-off setup {d['setup_s']:.1f} s not "
+              f"counted, {sum(d['steps_s']):.1f} s of steps")
+    return {"value": statistics.mean(per), "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample,
             "per_step": per, "setup_s": d["setup_s"]}, None
+
+
+def cpu_oracle_configs(threads, timeout=900):
+    """The oracle as it stands on the 2D configurations, `threads` BLAS/OpenMP threads: the
+    2D Taylor-Green vortex run in full (4^2, P=4, RK-CB3e, dt=0.01 to t=1) and a bounded
+    sample of the manufactured Dirichlet flow with nu(x, y, t) (3 RK-CB3e steps of dt=1e-3 on
+    8^2 elements at P=8; the 32^2 mesh is beyond the oracle's assembly in minutes)."""
+    code = f"""
+import sys, time, json
+sys.path.insert(0, {ROOT!r})
+import numpy as np
+from oracle import dg, flows, ns
+out = {{}}
+m = dg.Mesh(2, 4, (4, 4), [0, 0], [{TWO_PI}] * 2, (True, True))
+fl = flows.Flow('tg2d', 0.01)
+disc = ns.Discretization(m, fl)
+v = fl.initial(disc.X).reshape(2, -1)
+t0 = time.time(); t = 0.0
+for _ in range(100):
+    v, _ = ns.rk_step(disc, 'CB3e', v, t, 0.01); t += 0.01
+el = time.time() - t0
+ex = fl.exact(disc.X, t).reshape(2, -1)
+out['config1'] = {{'s': el, 'steps': 100, 'dof': int(2 * disc.nv),
+                   'rel_l2_vs_exact': float(np.linalg.norm(v - ex) / np.linalg.norm(ex))}}
+m = dg.Mesh(2, 8, (8, 8), [0, 0], [1, 1], (False, False))
+fl = flows.Flow('tgtravel', 0.01, nu_kind='varxyt')
+disc = ns.Discretization(m, fl)
+v = fl.initial(disc.X).reshape(2, -1)
+t0 = time.time(); t = 0.0
+for _ in range(3):
+    v, _ = ns.rk_step(disc, 'CB3e', v, t, 1e-3); t += 1e-3
+out['config3_sample'] = {{'s': time.time() - t0, 'steps': 3, 'dof': int(2 * disc.nv)}}
+print(json.dumps(out))
+"""
+    n = str(threads)
+    env = dict(os.environ, OMP_NUM_THREADS=n, OPENBLAS_NUM_THREADS=n, MKL_NUM_THREADS=n)
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=timeout)
+    if r.returncode != 0:
+        return {"unavailable": r.stderr[-300:]}
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    for k, v in d.items():
+        v["value"] = v["dof"] * 3 * v["steps"] / v["s"]
+        v["unit"] = UNIT
+    d["threads"] = threads
+    return d
+
+
+def run_config1(imex):
+    """The 2D decaying Taylor-Green vortex in full (4^2, P=4, nu=0.01, RK-CB3e, dt=0.01 to
+    t=1): error against the closed form and throughput, FP64 and mixed."""
+    import numpy as np
+    out = {}
+    for name, prec in (("fp64", imex.FP64), ("mixed", imex.MIXED)):
+        c = imex.Context(2, 4, (4, 4), [0, 0], [TWO_PI, TWO_PI], (1, 1), precision=prec, tol=1e-12, maxit=20000)
+        c.set_viscosity_const(0.01)
+        c.init_flow(imex.FLOW_TG2D, [0.01])
+        c.step(0.01, 2)                                   # warm-up (graphs, tuning)
+        c.init_flow(imex.FLOW_TG2D, [0.01])
+        w0 = time.perf_counter()
+        c.step(0.01, 100)
+        el = time.perf_counter() - w0
+        v = c.get_velocity()
+        # the closed form at the GLL nodes, evaluated by the library's field kernel
+        ex = c.eval_field(0, imex.FLOW_TG2D, [0.01], t=c.time())
+        out[name] = {"value": 2 * c.nvel * 3 * 100 / el, "unit": UNIT, "ms_per_step": el * 10.0,
+                     "rel_l2_vs_exact": float(np.linalg.norm(v - ex) / np.linalg.norm(ex))}
+        c.close()
+    out["workload"] = "2D decaying Taylor-Green, [0,2pi]^2 periodic, 4^2 quads, P=4, nu=0.01, RK-CB3e, dt=0.01 to t=1"
+    out["timing"] = "host wall clock around the 100 synchronous steps"
+    return out
+
+
+def run_config3(imex, dts=(1e-1, 3e-2, 1e-2, 3e-3, 1e-3, 3e-4, 1e-4), T=0.1):
+    """The manufactured traveling vortex on [0,1]^2 with time-dependent Dirichlet data and
+    nu(x, y, t) = 0.01 (1 + 0.5 sin 2 pi x sin 2 pi y cos t), 32^2 quads, P=8, RK-CB3e to T
+    for each dt: relative L2 error against the exact solution, its order between successive
+    dt, unstable runs (NaN or |v| > 10) reported as such, FP64 and mixed."""
+    import numpy as np
+    res = {"workload": "2D manufactured traveling vortex, [0,1]^2, Dirichlet v_b = v_ex(t), "
+                       "nu(x,y,t)=0.01(1+0.5 sin2pix sin2piy cos t), 32^2 quads, P=8, RK-CB3e to T=0.1",
+           "runs": []}
+    for name, prec in (("fp64", imex.FP64), ("mixed", imex.MIXED)):
+        prev = None
+        for dt in dts:
+            n = int(round(T / dt))
+            c = imex.Context(2, 8, (32, 32), [0, 0], [1, 1], (0, 0), precision=prec, tol=1e-10, maxit=20000,
+                             vmax=10.0)
+            c.set_viscosity_model(imex.NU_VARXYT, [0.01])
+            c.set_boundary(imex.FLOW_TGTRAVEL, [0.01])
+            c.set_forcing(imex.FORCE_TGTRAVEL_VARNU, [0.01])
+            c.init_flow(imex.FLOW_TGTRAVEL, [0.01])
+            row = {"form": name, "dt": dt, "steps": n}
+            w0 = time.perf_counter()
+            try:
+                c.step(dt, n)
+                el = time.perf_counter() - w0
+                v = c.get_velocity()
+                ex = c.eval_field(0, imex.FLOW_TGTRAVEL, [0.01], t=c.time())
+                err = float(np.linalg.norm(v - ex) / np.linalg.norm(ex))
+                row.update({"status": "ok", "rel_l2_vs_exact": err, "s": el,
+                            "value": 2 * c.nvel * 3 * n / el})
+                if prev is not None and prev[1] is not None:
+                    row["eoc"] = float(np.log(prev[1] / err) / np.log(prev[0] / dt))
+                prev = (dt, err)
+            except imex.ImexError as e:
+                row.update({"status": str(e).split(":")[0], "s": time.perf_counter() - w0})
+                prev = (dt, None)
+            res["runs"].append(row)
+            c.close()
+    return res
+
+
+def run_method_lines(imex, args, stream):
+    """SDC-CB3e(3,3) and IMEX BDF2 on the headline workload (16^3, P=7): throughput of the
+    mixed form and its distance from the FP64 form after the same steps."""
+    import numpy as np
+    out = {}
+
+    def make(prec, method):
+        c = make_ctx(imex, args, prec, stream)
+        if method == "sdc":
+            c.set_sdc(3, 3, "CB3e")
+        else:
+            c.set_bdf2()
+        return c
+    for method, nsteps, stages in (("sdc", 2, 18), ("bdf2", 6, 1)):
+        cm = make("mixed", method)
+        cm.step(args.dt, 1)                                # warm-up
+        w0 = time.perf_counter()
+        cm.step(args.dt, nsteps)
+        el = time.perf_counter() - w0
+        vm = cm.get_velocity().copy()
+        c64 = make("fp64", method)
+        w1 = time.perf_counter()
+        c64.step(args.dt, 1 + nsteps)
+        el64 = (time.perf_counter() - w1) * nsteps / (1 + nsteps)
+        v64 = c64.get_velocity()
+        dofs = 3 * cm.nvel * stages * nsteps
+        out[method] = {"value": dofs / el, "unit": UNIT, "ms_per_step": 1e3 * el / nsteps,
+                       "fp64_value": dofs / el64, "stages_per_step": stages,
+                       "mixed_vs_fp64_rel_l2": float(np.linalg.norm(vm - v64) / np.linalg.norm(v64)),
+                       "compared_after_steps": 1 + nsteps,
+                       "method": "SDC-CB3e(3,3) on 4 GLL nodes" if method == "sdc" else "IMEX BDF2",
+                       "timing": "host wall clock around synchronous steps"}
+        cm.close()
+        c64.close()
+    return out
 
 
 def rho_hat(P):
@@ -648,12 +799,22 @@ def main():
     ops = None
     if args.ops_nelem > 0 and rank == 0:
         ops = run_operators(imex, torch, args.ops_nelem, args.P)
+    methods = config1 = config3 = None
+    if rank == 0 and not args.no_extra_configs:
+        methods = run_method_lines(imex, args, stream.cuda_stream)
+        config1 = run_config1(imex)
+        config3 = run_config3(imex)
 
-    cpu = None
+    cpu = cpu_all = cpu_configs = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu, err = cpu_baseline_sample(args.P, args.dt, nsteps=3)
         if cpu is None:
             cpu = {"unavailable": err}
+        ncores = os.cpu_count() or 1
+        cpu_all, err = cpu_baseline_sample(args.P, args.dt, nsteps=3, threads=ncores)
+        if cpu_all is None:
+            cpu_all = {"unavailable": err}
+        cpu_configs = {"1_thread": cpu_oracle_configs(1), "all_cores": cpu_oracle_configs(ncores)}
 
     if rank == 0:
         n = args.nelem
@@ -673,7 +834,8 @@ def main():
             "p99_step_ms": sorted(per_step)[min(len(per_step) - 1, int(0.99 * len(per_step)))],
             "clocks": clocks, "gpu_launches": launches, "roofline": roof, "kernels": prof,
             "e2e": e2e, "fp64": fp64, "cpu_baseline": cpu, "ensemble": ens, "serving": serving,
-            "operators_above_l2": ops,
+            "operators_above_l2": ops, "methods": methods, "config1": config1, "config3_dt_sweep": config3,
+            "cpu_baseline_all_cores": cpu_all, "cpu_oracle_configs": cpu_configs,
             "tuning": imex.tuning_info(),
             "solver": {"poisson_iters_per_call": stats["poisson_iters"], "helmholtz_iters": stats["helmholtz_iters"],
                        "refinements": stats["refinements"], "max_poisson_res": stats["max_poisson_res"],

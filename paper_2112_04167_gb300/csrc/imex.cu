@@ -893,6 +893,12 @@ imex_status pcg_mixed(imex_ctx* c, const imex_ctx::Seg& sg, Op64 op64, Op32 op32
   CK(cudaMemsetAsync(y, 0, ntot * sizeof(float), c->st), "memset");
   std::vector<double> rr_ref(nsys, 0.0);
   std::vector<int> done_h(nsys, 0);
+  // stagnation of the true residual at its rounding floor: a system whose inner iteration
+  // converged three times in a row without the true residual falling below a quarter of its
+  // best value is accepted there (the FP64 form, which stops on its recursive residual, does
+  // not see this floor; the achieved residual is reported in the statistics)
+  std::vector<double> best_true(nsys, 0.0);
+  std::vector<int> inner_conv(nsys, 0), stall(nsys, 0);
   bool started = false, restart = true;
   int breakdowns = 0;
   auto replace = [&]() -> imex_status {
@@ -923,7 +929,12 @@ imex_status pcg_mixed(imex_ctx* c, const imex_ctx::Seg& sg, Op64 op64, Op32 op32
     for (int s = 0; s < nsys; ++s) {
       if (rt[s] != rt[s]) return fail(c, IMEX_EUNSTABLE, "NaN in the residual");
       if (done_h[s] == 4) continue;
-      if (rt[s] <= tol * tol * bbh[s]) {
+      if (started && inner_conv[s]) {
+        stall[s] = (best_true[s] > 0.0 && rt[s] > 0.0625 * best_true[s]) ? stall[s] + 1 : 0;
+        inner_conv[s] = 0;
+      }
+      if (best_true[s] == 0.0 || rt[s] < best_true[s]) best_true[s] = rt[s];
+      if (rt[s] <= tol * tol * bbh[s] || stall[s] >= 3) {
         done_h[s] = 4;
       } else {
         done_h[s] = 0;
@@ -1010,7 +1021,7 @@ imex_status pcg_mixed(imex_ctx* c, const imex_ctx::Seg& sg, Op64 op64, Op32 op32
         restart = true;
       }
       if (st == 3) return fail(c, IMEX_ENOTCONV, "CG did not converge within maxit");
-      if (st == 1) { need = true; restart = true; }                  // recursive residual converged
+      if (st == 1) { need = true; restart = true; inner_conv[s] = 1; }  // recursive residual converged
       if (st == 0 && c->cg_hd[2 * m + s] < delta * delta * rr_ref[s]) need = true;
       done_h[s] = st;
     }
