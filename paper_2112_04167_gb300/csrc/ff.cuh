@@ -62,6 +62,45 @@ __device__ __forceinline__ ff& operator*=(ff& a, ff b) { return a = a * b; }
 __device__ __forceinline__ bool operator<(ff a, ff b) { return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo); }
 __device__ __forceinline__ bool operator>(ff a, ff b) { return b < a; }
 
+// Compensated dot product of float-float operands (the Dot2 scheme of Ogita, Rump and Oishi,
+// "Accurate sum and dot product", 2005, with the low parts' cross products added by FMA): the
+// high parts' products and running sum are kept exactly by TwoProd / TwoSum, their errors
+// and the cross terms m.hi v.lo + m.lo v.hi gather in two FP32 accumulators, and one
+// renormalisation at the end gives the float-float result -- as accurate as the operator
+// arithmetic above, in about two thirds of its instructions per term.
+struct ff_dot {
+  float s = 0.f, err = 0.f, lo = 0.f;
+  __device__ __forceinline__ void add(ff m, ff v) {
+    const float p = m.hi * v.hi;
+    const float ep = fmaf(m.hi, v.hi, -p);
+    const float t = s + p;
+    const float bb = t - s;
+    const float es = (s - (t - bb)) + (p - bb);
+    s = t;
+    err += es + ep;
+    lo = fmaf(m.hi, v.lo, fmaf(m.lo, v.hi, lo));
+  }
+  __device__ __forceinline__ ff value() const {
+    const float t = s + (err + lo);
+    return ff(t, (err + lo) - (t - s));
+  }
+};
+
+// Sum of products in the arithmetic type T: plain accumulation for float and double (the
+// order of the terms as written), the compensated dot product for float-float
+template <typename T>
+struct DotAcc {
+  T s = T(0);
+  __device__ __forceinline__ void add(T m, T v) { s += m * v; }
+  __device__ __forceinline__ T value() const { return s; }
+};
+template <>
+struct DotAcc<ff> {
+  ff_dot d;
+  __device__ __forceinline__ void add(ff m, ff v) { d.add(m, v); }
+  __device__ __forceinline__ ff value() const { return d.value(); }
+};
+
 template <> __host__ __device__ __forceinline__ ff geom_h<ff>(const Geom& g, int k) { return ff(geom_h<double>(g, k)); }
 template <> __host__ __device__ __forceinline__ ff geom_nu0<ff>(const Geom& g) { return ff(g.inu0); }
 

@@ -32,9 +32,17 @@ __device__ __forceinline__ void contract_ct(const T* __restrict__ in, T* __restr
     const int c0 = o % O0, r = o / O0, c1 = r % O1, c2 = r / O1;
     const int a = (M == 0) ? c0 : (M == 1) ? c1 : c2;
     const int ib = ((M == 0) ? 0 : c0) + S0 * (((M == 1) ? 0 : c1) + S1 * ((M == 2) ? 0 : c2));
-    T s = T(0);
+    T s;
+    if constexpr (std::is_same<T, ff>::value) {
+      ff_dot acc;                                 // compensated float-float dot product
 #pragma unroll
-    for (int x = 0; x < SM; ++x) s += Mat[a * SA + x * SX] * in[ib + x * SIN];
+      for (int x = 0; x < SM; ++x) acc.add(Mat[a * SA + x * SX], in[ib + x * SIN]);
+      s = acc.value();
+    } else {
+      s = T(0);
+#pragma unroll
+      for (int x = 0; x < SM; ++x) s += Mat[a * SA + x * SX] * in[ib + x * SIN];
+    }
     out[o] = ACC ? out[o] + s : s;
   }
 }
@@ -313,9 +321,10 @@ __device__ __forceinline__ T nodal_deriv(const Geom& g, const int* ec, int e, co
   int stride = 1;
   for (int j = 0; j < k; ++j) stride *= N;
   const int base = node - id[k] * stride;
-  T acc = T(0);
+  DotAcc<T> dacc;
 #pragma unroll
-  for (int j = 0; j < N; ++j) acc += sD[id[k] * N + j] * su[base + j * stride];
+  for (int j = 0; j < N; ++j) dacc.add(sD[id[k] * N + j], su[base + j * stride]);
+  const T acc = dacc.value();
   const T hk = T(2) / geom_h<T>(g, k);
   T val = hk * acc;
   for (int side = 0; side < 2; ++side) {
