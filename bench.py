@@ -77,10 +77,13 @@ def peaks():
 # capture summarised under profiles/ for the current kernel version
 NCU_TRAFFIC = {}
 # ALU peaks: FP32 (non-tensor) from 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz; FP64 the
-# nominal GB300 rate.  Float-float flops are counted as FP64-equivalent operations and set
-# against the FP64 rate they replace.
+# nominal GB300 rate.  Float-float flops are counted as the FP64 operations they replace and
+# set against the rate at which the FP32 pipes execute float-float multiply-adds: one term of
+# the compensated dot product is 15 FP32 flops (one FMUL, three FFMA, eight FADD) for the 2
+# flops of an FP64 multiply-add.
 FP32_PEAK_GFLOPS = 152 * 128 * 2 * 2.07
 FP64_PEAK_GFLOPS = 1250.0
+FF_PEAK_GFLOPS = FP32_PEAK_GFLOPS * 2.0 / 15.0
 ARITH = {0: "fp64", 1: "fp32", 3: "ff"}
 
 
@@ -95,7 +98,7 @@ def operator_table(imex, ctx, hbm):
             continue
         b, f, a = ctx.profile_work(cls)
         sec = ms * 1e-3
-        peak = FP32_PEAK_GFLOPS if a == 1 else FP64_PEAK_GFLOPS
+        peak = {1: FP32_PEAK_GFLOPS, 3: FF_PEAK_GFLOPS}.get(a, FP64_PEAK_GFLOPS)
         row = {"launches": n, "total_ms": ms, "avg_us": 1e3 * ms / n, "arith": ARITH.get(a),
                "bytes_per_launch": b / n, "gbs": b / sec / 1e9, "hbm_frac": b / sec / 1e9 / hbm,
                "flops_per_launch": f / n if f else None}
@@ -119,8 +122,9 @@ def roofline_of(rows, hbm, src, traffic=None):
     else:
         out = {"bound": "alu", "kernel": dom, "achieved": r["gflops"], "peak": r["alu_peak_gflops"],
                "unit": "GFLOP/s", "frac": alu,
-               "peak_source": "FP32 152 SMs x 128 lanes x 2 x 2.07 GHz" if r["arith"] == "fp32"
-               else "nominal FP64 1.25 TFLOP/s (float-float: FP64-equivalent flops)"}
+               "peak_source": {"fp32": "FP32 152 SMs x 128 lanes x 2 x 2.07 GHz",
+                               "ff": "float-float multiply-adds on the FP32 pipes: FP32 peak x 2 / 15 "
+                                     "(FP64-equivalent flops)"}.get(r["arith"], "nominal FP64 1.25 TFLOP/s")}
     out.update({"traffic": traffic, "bytes_per_launch": r["bytes_per_launch"], "avg_launch_us": r["avg_us"],
                 "arith": r["arith"], "share_of_profiled_ms": r["total_ms"] / sum(x["total_ms"] for x in rows.values())})
     return out

@@ -283,7 +283,8 @@ enum {
   IMEX_PROF_PCG_PERSIST = 5,   /* persistent FP32 pressure CG launches (many iterations each) */
   IMEX_PROF_PMG_APPLY = 6, IMEX_PROF_PMG_VEC = 7, IMEX_PROF_CG_STEP = 8, IMEX_PROF_CG_DIR = 9,
   IMEX_PROF_DIV = 10, IMEX_PROF_GRAD = 11, IMEX_PROF_DERIV = 12,
-  IMEX_PROF_NCLASS = 13
+  IMEX_PROF_PMG_APPLY_COARSE = 13,   /* the V-cycle's applies on the coarser levels (PMG_APPLY: finest) */
+  IMEX_PROF_NCLASS = 14
 };
 /* enable (1) or disable (0) CUDA-event timing of the classes above on the context's
    stream; enabling resets the accumulated records */

@@ -1160,9 +1160,10 @@ imex_status pmg_apply(imex_ctx* c, int l, const T* x, T* y) {
   SipgArgs<T> a = sipg_args<T>(x, y, 1, (long long)n, nullptr, 1.0, nullptr, 0.0, 1.0, 0);
   a.ops = PmgVecs<T>::ops(M)[l];
   a.variant = tuned_variant(c, M.N[l], sizeof(T) == 4);
-  prof_mark(c, IMEX_PROF_PMG_APPLY, true);
+  const int cls = l == 0 ? IMEX_PROF_PMG_APPLY : IMEX_PROF_PMG_APPLY_COARSE;
+  prof_mark(c, cls, true);
   const int rc = sipg_apply<T>(c->gp, M.N[l], a, c->st);
-  prof_end(c, IMEX_PROF_PMG_APPLY, 2.0 * sizeof(T) * n, sipg_flops_per_node(c->d, M.N[l]) * n, arith_t<T>());
+  prof_end(c, cls, 2.0 * sizeof(T) * n, sipg_flops_per_node(c->d, M.N[l]) * n, arith_t<T>());
   return launch_check(c, rc, "sipg_apply(pmg)");
 }
 
@@ -1252,9 +1253,10 @@ imex_status pmg_smooth(imex_ctx* c, int l, int steps, double lmax, double ratio,
     a.ch_dinv = dinv;
     a.ch_c1 = (T)(rn * rho);
     a.ch_c2 = (T)(2.0 * rn / delta);
-    prof_mark(c, IMEX_PROF_PMG_APPLY, true);
+    const int cls = l == 0 ? IMEX_PROF_PMG_APPLY : IMEX_PROF_PMG_APPLY_COARSE;
+    prof_mark(c, cls, true);
     const int rc = sipg_apply<T>(c->gp, M.N[l], a, c->st);
-    prof_end(c, IMEX_PROF_PMG_APPLY, (last ? 5.0 : 7.0) * sizeof(T) * n,
+    prof_end(c, cls, (last ? 5.0 : 7.0) * sizeof(T) * n,
              (sipg_flops_per_node(c->d, M.N[l]) + 6.0) * n, arith_t<T>());
     TRY(launch_check(c, rc, "sipg_apply(chebyshev)"));
     std::swap(dcur, dnext);

@@ -145,9 +145,11 @@ _SIGS = {
 }
 REQ_QUEUED, REQ_ACTIVE, REQ_DONE, REQ_FAILED = range(4)
 (PROF_PRESSURE_F32, PROF_PRESSURE_F64, PROF_HELMHOLTZ_F32, PROF_HELMHOLTZ_F64, PROF_CONV, PROF_PCG_PERSIST,
- PROF_PMG_APPLY, PROF_PMG_VEC, PROF_CG_STEP, PROF_CG_DIR, PROF_DIV, PROF_GRAD, PROF_DERIV) = range(13)
+ PROF_PMG_APPLY, PROF_PMG_VEC, PROF_CG_STEP, PROF_CG_DIR, PROF_DIV, PROF_GRAD, PROF_DERIV,
+ PROF_PMG_APPLY_COARSE) = range(14)
 PROF_NAMES = ["sipg_pressure_f32", "sipg_pressure_f64", "sipg_helmholtz_f32", "sipg_helmholtz_f64", "conv",
-              "pcg_persist_f32", "pmg_apply", "pmg_vec", "cg_step", "cg_dir", "div", "grad", "deriv"]
+              "pcg_persist_f32", "pmg_apply", "pmg_vec", "cg_step", "cg_dir", "div", "grad", "deriv",
+              "pmg_apply_coarse"]
 REDUCE_DOT, REDUCE_SUM, REDUCE_MAXABS = range(3)
 
 
