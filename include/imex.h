@@ -297,11 +297,12 @@ imex_status imex_profile_read(imex_ctx* ctx, int cls, long long* launches, doubl
 imex_status imex_profile_work(imex_ctx* ctx, int cls, double* bytes, double* flops, int* arith);
 /* Launch shapes chosen by the tuner of the periodic constant-viscosity SIPG applies (the CG
    and p-multigrid applies): on first use for a (d, N, precision, element count) each shape --
-   the default elements per block (0), half (1), twice (2; not for 2D FP64) -- is timed with
-   CUDA events and the fastest kept when it beats the default by more than 3% (IMEX_TUNE=0 in
-   the environment: always the default).  Entry i: dimension, points per direction, FP32 (1)
-   or FP64, elements, the chosen shape and the per-launch times (us) of the three shapes
-   (0: not timed).  Returns the number of entries (i < 0: just that), -1 for i out of range. */
+   the default elements per block (0), half (1), twice (2; not for 2D FP64), one more (3; 3D
+   FP32 only) -- is timed with CUDA events and the fastest kept when it beats the default by
+   more than 3% (IMEX_TUNE=0 in the environment: always the default).  Entry i: dimension,
+   points per direction, FP32 (1) or FP64, elements, the chosen shape and the per-launch
+   times (us) of the four shapes (us holds 4 values; 0: not timed).  Returns the number of
+   entries (i < 0: just that), -1 for i out of range. */
 int imex_tuning_info(int i, int* d, int* N, int* fp32, long long* ne, int* variant, double* us);
 /* fix the launch shape for a (d, N, precision, element count) instead of the tuner's choice
    (also used by the operator entry points); IMEX_EINVAL for an unknown shape */

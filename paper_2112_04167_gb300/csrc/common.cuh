@@ -154,14 +154,14 @@ template <> __host__ __device__ __forceinline__ double geom_dt<double>(const Geo
 template <> __host__ __device__ __forceinline__ float geom_dt<float>(const Geom& g) { return g.idtf; }
 
 // neighbour element (index in the union) across face (k, side) of the element with local
-// coordinates ec; -1 on a domain boundary.  g is the element's local_geom.
+// coordinates ec (side -1 or +1); -1 on a domain boundary.  g is the element's local_geom.
 __device__ __forceinline__ int neighbor(const Geom& g, const int ec[3], int k, int side) {
   int cx = ec[0], cy = ec[1], cz = ec[2];
   const int nk = geom_n(g, k);
   int j = (k == 0 ? cx : (k == 1 ? cy : cz)) + side;
   if (j < 0 || j >= nk) {
     if (geom_bc(g, k) != 0) return -1;
-    j = (j + nk) % nk;
+    j = j < 0 ? j + nk : j - nk;                 // periodic wrap by one element
   }
   if (k == 0) cx = j;
   else if (k == 1) cy = j;

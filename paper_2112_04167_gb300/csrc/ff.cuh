@@ -19,11 +19,129 @@ struct ff {
   float hi, lo;
   ff() = default;
   __host__ __device__ constexpr ff(float h, float l) : hi(h), lo(l) {}
-  __host__ __device__ ff(double x) : hi((float)x), lo((float)(x - (double)(float)x)) {}
+  __host__ __device__ inline ff(double x);
   __host__ __device__ constexpr ff(float x) : hi(x), lo(0.f) {}
   __host__ __device__ constexpr ff(int x) : hi((float)x), lo(0.f) {}
-  __host__ __device__ explicit operator double() const { return (double)hi + (double)lo; }
+  __host__ __device__ inline explicit operator double() const;
 };
+
+// Conversions between FP64 and float-float.  On this GPU the FP64 pipe -- which also
+// executes the FP32 <-> FP64 conversions -- issues at a small fraction of the FP32 rate, so
+// a kernel that converts every FP64 value it loads or stores spends most of its time there.
+// The device forms below work on the bit patterns with integer operations instead; values
+// whose parts would leave the normal FP32 range take the FP64 route (the host always does).
+namespace ffbits {
+__host__ __device__ __forceinline__ unsigned long long d2u(double x) {
+#ifdef __CUDA_ARCH__
+  return (unsigned long long)__double_as_longlong(x);
+#else
+  unsigned long long u;
+  __builtin_memcpy(&u, &x, 8);
+  return u;
+#endif
+}
+__host__ __device__ __forceinline__ double u2d(unsigned long long u) {
+#ifdef __CUDA_ARCH__
+  return __longlong_as_double((long long)u);
+#else
+  double x;
+  __builtin_memcpy(&x, &u, 8);
+  return x;
+#endif
+}
+__host__ __device__ __forceinline__ unsigned f2u(float x) {
+#ifdef __CUDA_ARCH__
+  return __float_as_uint(x);
+#else
+  unsigned u;
+  __builtin_memcpy(&u, &x, 4);
+  return u;
+#endif
+}
+__host__ __device__ __forceinline__ float u2f(unsigned u) {
+#ifdef __CUDA_ARCH__
+  return __uint_as_float(u);
+#else
+  float x;
+  __builtin_memcpy(&x, &u, 4);
+  return x;
+#endif
+}
+}  // namespace ffbits
+
+// the FP64 route: hi = x rounded to FP32, lo = the rest rounded to FP32
+__host__ __device__ __forceinline__ ff ff_split_fp64(double x) {
+  const float h = (float)x;
+  return ff(h, (float)(x - (double)h));
+}
+__host__ __device__ __forceinline__ double ff_join_fp64(ff a) { return (double)a.hi + (double)a.lo; }
+// the same out of line, for the rare operands of the integer forms: a call keeps their FP64
+// instructions on a branch of their own (inlined, they would be predicated into every use)
+static __host__ __device__ __noinline__ ff ff_split_rare(double x) { return ff_split_fp64(x); }
+static __host__ __device__ __noinline__ double ff_join_rare(ff a) { return ff_join_fp64(a); }
+
+// x = M 2^(e - 1075) with the 53-bit significand M, in 32-bit words: hi takes M's leading 24
+// bits rounded to nearest (ties to even), lo the remainder R (|R| <= 2^28) rounded to FP32
+// and scaled by the exact power of two -- the FP64 route's result bit for bit.  Both parts
+// are normal floats for biased exponents e in [953, 1149]; zero is exact; anything else
+// takes the FP64 route.
+__host__ __device__ __forceinline__ ff ff_split_bits(double x) {
+  using namespace ffbits;
+  const unsigned long long b = d2u(x);
+  const unsigned bh = (unsigned)(b >> 32), bl = (unsigned)b;
+  if (((bh << 1) | bl) == 0u) return ff(u2f(bh), 0.f);                     // +-0
+  const unsigned e = (bh >> 20) & 0x7ffu;
+  if (e - 953u > 196u) return ff_split_rare(x);
+  // rounding bit 28 of the low word, to even on a tie
+  const unsigned rnd = (bl >> 28) & (((bl & 0x0fffffffu) != 0u) | (bl >> 29)) & 1u;
+  // exponent and the leading 23 fraction bits (the sign and the exponent's top bits shift
+  // out; the rebias is taken modulo 2^32), a carried rounding moves into the exponent
+  const unsigned hmag = (((bh << 3) | (bl >> 29)) - (896u << 23)) + rnd;
+  const int R = (int)(bl & 0x1fffffffu) - (int)(rnd << 29);
+  const float scale = u2f((e - 948u) << 23);                                // 2^(e - 1075)
+  return ff(u2f((bh & 0x80000000u) | hmag), (float)((bh >> 31) ? -R : R) * scale);
+}
+
+// hi + lo to FP64 in 32-bit words: FP64 bits of hi, then lo's significand added to (or taken
+// from) the 64-bit pattern in units of hi's FP64 last place (rounded to that unit: within one
+// unit of the correctly rounded sum).  A normalised lo never carries into the exponent; when
+// hi is a power of two and lo has the other sign the sum lies in the binade below, whose unit
+// is half as large.  Zero, subnormal or non-finite high parts, subnormal low parts and low
+// parts that are not normalised take the FP64 route.
+__host__ __device__ __forceinline__ double ff_join_bits(ff a) {
+  using namespace ffbits;
+  const unsigned hb = f2u(a.hi), lb = f2u(a.lo);
+  const unsigned eh = (hb >> 23) & 0xffu;
+  if (eh - 1u > 253u) return ff_join_rare(a);
+  const unsigned hw = (hb & 0x80000000u) | (((hb & 0x7fffffffu) >> 3) + (896u << 20));
+  unsigned long long v = ((unsigned long long)hw << 32) | (unsigned long long)(hb << 29);
+  if ((lb << 1) != 0u) {
+    const unsigned el = (lb >> 23) & 0xffu;
+    const int d = (int)eh - (int)el;
+    if (el == 0u || d < 24) return ff_join_rare(a);
+    const bool opp = ((hb ^ lb) & 0x80000000u) != 0u;
+    const int sh = 29 - d + ((opp && (hb & 0x7fffffu) == 0u) ? 1 : 0);
+    const unsigned Sl = (lb & 0x7fffffu) | 0x800000u;
+    const unsigned L = sh >= 0 ? (Sl << sh) : (sh > -25 ? ((Sl + (1u << (-sh - 1))) >> (-sh)) : 0u);
+    v = opp ? v - L : v + L;
+  }
+  return u2d(v);
+}
+
+__host__ __device__ inline ff::ff(double x) {
+#ifdef __CUDA_ARCH__
+  *this = ff_split_bits(x);
+#else
+  *this = ff_split_fp64(x);
+#endif
+}
+__host__ __device__ inline ff::operator double() const {
+#ifdef __CUDA_ARCH__
+  return ff_join_bits(*this);
+#else
+  return ff_join_fp64(*this);
+#endif
+}
 
 // s + e = a + b exactly (no precondition on the magnitudes)
 __device__ __forceinline__ ff ff_two_sum(float a, float b) {

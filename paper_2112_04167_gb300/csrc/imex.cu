@@ -552,7 +552,7 @@ struct TuneEntry {
   int d, N, f32;
   long long ne;
   int variant;
-  double us[3];
+  double us[4];
 };
 std::mutex g_tune_mu;
 std::vector<TuneEntry> g_tune;
@@ -1318,8 +1318,9 @@ imex_status tune_apply(imex_ctx* c, int N, int nsys, size_t n, const LineOps<T>*
     for (const auto& t : g_tune)
       if (t.d == c->d && t.N == N && t.f32 == (int)f32 && t.ne == c->gp.ne) return IMEX_OK;
   }
-  const int nvar = (c->d == 2 && !f32) ? 2 : 3;           // 2D FP64: no doubled block (static shared memory)
-  TuneEntry te{c->d, N, (int)f32, c->gp.ne, 0, {0, 0, 0}};
+  // 2D FP64: no doubled block (static shared memory); one element more: 3D FP32 only
+  const int nvar = (c->d == 2 && !f32) ? 2 : ((c->d == 3 && f32) ? 4 : 3);
+  TuneEntry te{c->d, N, (int)f32, c->gp.ne, 0, {0, 0, 0, 0}};
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0), "event");
   CK(cudaEventCreate(&e1), "event");
@@ -3189,8 +3190,8 @@ imex_status imex_profile_work(imex_ctx* c, int cls, double* bytes, double* flops
 }
 
 int imex_set_apply_variant(int d, int N, int fp32, long long ne, int variant) {
-  if ((d != 2 && d != 3) || N < 2 || N > IMEX_MAXN || ne < 1 || variant < 0 || variant > 2 ||
-      (d == 2 && !fp32 && variant == 2))
+  if ((d != 2 && d != 3) || N < 2 || N > IMEX_MAXN || ne < 1 || variant < 0 || variant > 3 ||
+      (d == 2 && !fp32 && variant == 2) || (variant == 3 && (d != 3 || !fp32)))
     return IMEX_EINVAL;
   std::lock_guard<std::mutex> lk(g_tune_mu);
   for (auto& t : g_tune)
@@ -3198,7 +3199,7 @@ int imex_set_apply_variant(int d, int N, int fp32, long long ne, int variant) {
       t.variant = variant;
       return IMEX_OK;
     }
-  g_tune.push_back(TuneEntry{d, N, fp32 ? 1 : 0, ne, variant, {0, 0, 0}});
+  g_tune.push_back(TuneEntry{d, N, fp32 ? 1 : 0, ne, variant, {0, 0, 0, 0}});
   return IMEX_OK;
 }
 
@@ -3212,7 +3213,7 @@ int imex_tuning_info(int i, int* d, int* N, int* fp32, long long* ne, int* varia
   if (fp32) *fp32 = t.f32;
   if (ne) *ne = t.ne;
   if (variant) *variant = t.variant;
-  if (us) for (int k = 0; k < 3; ++k) us[k] = t.us[k];
+  if (us) for (int k = 0; k < 4; ++k) us[k] = t.us[k];
   return (int)g_tune.size();
 }
 

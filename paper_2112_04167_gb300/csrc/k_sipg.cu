@@ -25,11 +25,7 @@ namespace imex {
 // Output of one node of an apply: y = A x, or the fused Chebyshev step of the p-multigrid
 // smoother (a.cheb): r -= A x, d' = c1 x + c2 D^{-1} r, s += d' (xin: this node's input x)
 template <typename T, typename TS>
-__device__ __forceinline__ void sipg_out(const SipgArgs<TS>& a, TS* __restrict__ y, size_t i, T xin, T out) {
-  if (!a.cheb) {
-    y[i] = (TS)out;
-    return;
-  }
+__device__ __forceinline__ void sipg_cheb_out(const SipgArgs<TS>& a, size_t i, T xin, T out) {
   const T r = T(a.ch_r[i]) - out;
   const T dn = T(a.ch_c1) * xin + T(a.ch_c2) * T(a.ch_dinv[i]) * r;
   a.ch_s[i] = (TS)(T(a.ch_s[i]) + dn);
@@ -38,6 +34,32 @@ __device__ __forceinline__ void sipg_out(const SipgArgs<TS>& a, TS* __restrict__
     a.ch_dout[i] = (TS)dn;
   }
 }
+template <typename T, typename TS>
+__device__ __forceinline__ void sipg_out(const SipgArgs<TS>& a, TS* __restrict__ y, size_t i, T xin, T out) {
+  if (!a.cheb) {
+    y[i] = (TS)out;
+    return;
+  }
+  sipg_cheb_out<T, TS>(a, i, xin, out);
+}
+// Output stage chosen at compile time: EP = 0 reads the flags (M^{-1}, Chebyshev) at run
+// time, 1 writes y = A x, 2 performs the Chebyshev step.  Fixed stages keep the unused
+// branches -- a precise division, the Chebyshev loads and stores -- out of the unrolled
+// output loop, where the compiler would otherwise predicate them into every node.
+constexpr int SIPG_EP_ANY = 0, SIPG_EP_PLAIN = 1, SIPG_EP_CHEB = 2;
+template <int EP, typename T, typename TS>
+__device__ __forceinline__ T sipg_out_ep(const SipgArgs<TS>& a, TS* __restrict__ y, size_t i, T xin, T out, T W) {
+  if constexpr (EP == SIPG_EP_PLAIN) {
+    y[i] = (TS)out;
+  } else if constexpr (EP == SIPG_EP_CHEB) {
+    sipg_cheb_out<T, TS>(a, i, xin, out);
+  } else {
+    if (a.minv) out = out / W;
+    sipg_out<T, TS>(a, y, i, xin, out);
+  }
+  return out;
+}
+
 
 // Deterministic block sum for any block size: thread values through shared memory, then
 // warp 0 adds them in a fixed order.  Result valid in thread 0.
@@ -876,9 +898,11 @@ template <> __device__ __forceinline__ const ConstLine<double>& cline<double>(in
 // of an element; the block's elements are contiguous in memory and are staged into shared
 // memory with fully coalesced loads.  Many elements per block keep the grid within about
 // one wave of resident blocks.
-// elements per block of the tuned kernels: variant 0 the default, 1 half of it, 2 twice it
+// elements per block of the tuned kernels: variant 0 the default, 1 half of it, 2 twice it,
+// 3 (3D FP32 only) one more element -- for N = 7 and 9, whose N^2 lines per element fill
+// whole warps badly at the default (4 x 49 = 196 threads in 7 warps, 5 x 49 = 245 in 8)
 __host__ __device__ constexpr int epb_variant(int base, int V) {
-  return V == 1 ? (base / 2 > 0 ? base / 2 : 1) : (V == 2 ? base * 2 : base);
+  return V == 1 ? (base / 2 > 0 ? base / 2 : 1) : (V == 2 ? base * 2 : (V == 3 ? base + 1 : base));
 }
 
 template <typename T, int N, int V = 0>
@@ -1195,7 +1219,7 @@ __device__ __forceinline__ LineFaces<T> line_faces(const ConstLine<T>& L, const 
   return f;
 }
 
-template <typename T, int N, typename TS = T, int V = 0>
+template <typename T, int N, typename TS = T, int V = 0, int EP = SIPG_EP_ANY>
 __device__ __forceinline__ T sipg3l_group(const Geom& g, const SipgArgs<TS>& a, const TS* __restrict__ x,
                                           TS* __restrict__ y, int grp, int sys = 0) {
   using S = Sipg3lShape<T, N, V>;
@@ -1233,6 +1257,18 @@ __device__ __forceinline__ T sipg3l_group(const Geom& g, const SipgArgs<TS>& a, 
   T* ma = acc + le * ND;
   const size_t eb = (size_t)e * ND;
   const int ta = t % N, tb = t / N;                               // the thread's two line coordinates
+  // the GLL weights at the thread's two line coordinates, read once: FP32 and FP64 from the
+  // global tables (an L1 hit; the constant cache would serialise the warp's distinct
+  // addresses), float-float from constant memory
+  T wa, wb;
+  if constexpr (std::is_same<T, ff>::value) {
+    wa = L.w[ta];
+    wb = L.w[tb];
+  } else {
+    const Tables<T>& tbl = tab<T>(g);
+    wa = tbl.w[N][ta];
+    wb = tbl.w[N][tb];
+  }
   // neighbour lines: z at (x = ta, y = tb), y at (x = ta, z = tb), x at (y = ta, z = tb)
   const TS* zl = x + (size_t)nb[4] * ND + t;
   const TS* zr = x + (size_t)nb[5] * ND + t;
@@ -1261,7 +1297,7 @@ __device__ __forceinline__ T sipg3l_group(const Geom& g, const SipgArgs<TS>& a, 
   // pass z: line (x = ta, y = tb) along z
   if (live) {
     if (!HOIST) fz = line_faces<T, N>(L, zl, zr, NN);
-    const T wt = (T(0.5) * hx * L.w[ta]) * (T(0.5) * hy * L.w[tb]) * ihz;
+    const T wt = (T(0.5) * hx * wa) * (T(0.5) * hy * wb) * ihz;
 #pragma unroll
     for (int k = 0; k < N; ++k) {
       T sk = L.ctrL[k] * fz.tl + L.cdnL[k] * fz.dl + L.ctrR[k] * fz.tr + L.cdnR[k] * fz.dr;
@@ -1277,7 +1313,7 @@ __device__ __forceinline__ T sipg3l_group(const Geom& g, const SipgArgs<TS>& a, 
 #pragma unroll
     for (int j = 0; j < N; ++j) v[j] = mt[(tb * N + j) * NP + ta];
     if (!HOIST) fy = line_faces<T, N>(L, yl, yr, N);
-    const T wt = (T(0.5) * hx * L.w[ta]) * (T(0.5) * hz * L.w[tb]) * ihy;
+    const T wt = (T(0.5) * hx * wa) * (T(0.5) * hz * wb) * ihy;
 #pragma unroll
     for (int o = 0; o < N; ++o) {
       T so = L.ctrL[o] * fy.tl + L.cdnL[o] * fy.dl + L.ctrR[o] * fy.tr + L.cdnR[o] * fy.dr;
@@ -1301,7 +1337,7 @@ __device__ __forceinline__ T sipg3l_group(const Geom& g, const SipgArgs<TS>& a, 
       for (int j = 0; j < VEC; ++j) v[q * VEC + j] = pw[j];
     }
     if (!HOIST) fx = line_faces<T, N>(L, xl, xr, 1);
-    const T wyz = (T(0.5) * hy * L.w[ta]) * (T(0.5) * hz * L.w[tb]);
+    const T wyz = (T(0.5) * hy * wa) * (T(0.5) * hz * wb);
     const T wt = wyz * ihx;
 #pragma unroll
     for (int o = 0; o < N; ++o) {
@@ -1310,9 +1346,7 @@ __device__ __forceinline__ T sipg3l_group(const Geom& g, const SipgArgs<TS>& a, 
       for (int j = 0; j < N; ++j) so += L.A[o * N + j] * v[j];
       const int node = (tb * N + ta) * N + o;
       const T W = wyz * (T(0.5) * hx * L.w[o]);
-      T out = alpha * W * v[o] + scale * (ma[node] + wt * so);
-      if (a.minv) out = out / W;
-      sipg_out<T, TS>(a, y, eb + node, v[o], out);
+      const T out = sipg_out_ep<EP, T, TS>(a, y, eb + node, v[o], alpha * W * v[o] + scale * (ma[node] + wt * so), W);
       dacc += v[o] * out;
     }
   }
@@ -1327,10 +1361,14 @@ __device__ __forceinline__ T sipg3l_group(const Geom& g, const SipgArgs<TS>& a, 
 #endif
 // resident blocks asked of the compiler: IMEX_SIPG3P_MINB for the FP32 default and halved
 // shapes; none for the doubled blocks (a forced count would make them spill)
-__host__ __device__ constexpr int sipg3p_minb(int V, bool f32) { return (!f32 || V == 2) ? 1 : IMEX_SIPG3P_MINB; }
-template <typename T, int N, typename TS = T, int V = 0>
+// float-float: two resident blocks (128 registers; uncapped, the unrolled neighbour-line
+// conversions take 255 registers and spill)
+__host__ __device__ constexpr int sipg3p_minb(int V, bool f32, bool isff) {
+  return V == 2 ? 1 : (f32 ? IMEX_SIPG3P_MINB : (isff ? 2 : 1));
+}
+template <typename T, int N, typename TS = T, int V = 0, int EP = SIPG_EP_ANY>
 __global__ void __launch_bounds__(Sipg3pShape<T, N, V>::THREADS,
-                                  sipg3p_minb(V, sizeof(T) == 4 && N <= 8))
+                                  sipg3p_minb(V, sizeof(T) == 4 && N <= 8, std::is_same<T, ff>::value))
 sipg3p_apply_kernel(Geom g, SipgArgs<TS> a) {
   __shared__ double red[Sipg3pShape<T, N, V>::THREADS];
   pdl_trigger();
@@ -1340,7 +1378,7 @@ sipg3p_apply_kernel(Geom g, SipgArgs<TS> a) {
       if (a.dot_out && threadIdx.x == 0) put_dot_partial(a, s, 0.0);
       continue;
     }
-    const T dacc = sipg3l_group<T, N, TS, V>(g, a, a.x + (size_t)s * a.sys_stride,
+    const T dacc = sipg3l_group<T, N, TS, V, EP>(g, a, a.x + (size_t)s * a.sys_stride,
                                              a.y + (size_t)s * a.sys_stride, blockIdx.x, s);
     if (a.dot_out) {
       const double bs = block_sum_any_t<T>(dacc, red);
@@ -1765,12 +1803,25 @@ static void launch_apply(const Geom& g, const SipgArgs<T>& a, cudaStream_t st) {
   IMEX_COUNTED(sipg_apply_kernel<T, D, N><<<blocks, S::THREADS, 0, st>>>(g, a));
 }
 
-template <typename T, int N, int V>
-static void launch_apply3p(const Geom& g, const SipgArgs<T>& a, cudaStream_t st) {
+template <typename T, int N, int V, int EP>
+static void launch_apply3p_ep(const Geom& g, const SipgArgs<T>& a, cudaStream_t st) {
   using P = Sipg3pShape<T, N, V>;
   constexpr size_t sm = sipg3l_smem<T, N, V>();
-  smem_limit_once((const void*)sipg3p_apply_kernel<T, N, T, V>, (int)sm);
-  launch_cg_kernel(sipg3p_apply_kernel<T, N, T, V>, (g.ne + P::EPB - 1) / P::EPB, P::THREADS, sm, st, g, a);
+  smem_limit_once((const void*)sipg3p_apply_kernel<T, N, T, V, EP>, (int)sm);
+  launch_cg_kernel(sipg3p_apply_kernel<T, N, T, V, EP>, (g.ne + P::EPB - 1) / P::EPB, P::THREADS, sm, st, g, a);
+}
+// FP32 (the CG and V-cycle applies): the output stage fixed at compile time unless M^{-1}
+// is asked for
+template <typename T, int N, int V>
+static void launch_apply3p(const Geom& g, const SipgArgs<T>& a, cudaStream_t st) {
+  if constexpr (sizeof(T) == 4) {
+    if (!a.minv) {
+      if (a.cheb) launch_apply3p_ep<T, N, V, SIPG_EP_CHEB>(g, a, st);
+      else launch_apply3p_ep<T, N, V, SIPG_EP_PLAIN>(g, a, st);
+      return;
+    }
+  }
+  launch_apply3p_ep<T, N, V, SIPG_EP_ANY>(g, a, st);
 }
 
 template <typename T, int D, int N>
@@ -1778,7 +1829,12 @@ static void launch_apply3(const Geom& g, const SipgArgs<T>& a, cudaStream_t st) 
   if (!a.nu && a.ops && g.bc[0] == 0 && g.bc[1] == 0 && g.bc[2] == 0) {
     if (a.variant == 1) launch_apply3p<T, N, 1>(g, a, st);
     else if (a.variant == 2) launch_apply3p<T, N, 2>(g, a, st);
-    else launch_apply3p<T, N, 0>(g, a, st);
+    else if constexpr (sizeof(T) == 4) {
+      if (a.variant == 3) launch_apply3p<T, N, 3>(g, a, st);
+      else launch_apply3p<T, N, 0>(g, a, st);
+    } else {
+      launch_apply3p<T, N, 0>(g, a, st);
+    }
     return;
   }
   if (!a.nu && a.ops) {

@@ -165,7 +165,7 @@ def tuning_info():
     for i in range(n):
         d, N, f32, v = C.c_int(), C.c_int(), C.c_int(), C.c_int()
         ne = C.c_longlong()
-        us = (C.c_double * 3)()
+        us = (C.c_double * 4)()
         lib.imex_tuning_info(i, C.byref(d), C.byref(N), C.byref(f32), C.byref(ne), C.byref(v), us)
         out.append({"d": d.value, "N": N.value, "fp32": bool(f32.value), "elements": ne.value, "variant": v.value,
                     "us": [round(x, 2) for x in us]})
