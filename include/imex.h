@@ -298,7 +298,7 @@ imex_status imex_profile_work(imex_ctx* ctx, int cls, double* bytes, double* flo
 /* Launch shapes chosen by the tuner of the periodic constant-viscosity SIPG applies (the CG
    and p-multigrid applies): on first use for a (d, N, precision, element count) each shape --
    the default elements per block (0), half (1), twice (2; not for 2D FP64), one more (3; 3D
-   FP32 only) -- is timed with CUDA events and the fastest kept when it beats the default by
+   FP32 with N = 7 or 9) -- is timed with CUDA events and the fastest kept when it beats the default by
    more than 3% (IMEX_TUNE=0 in the environment: always the default).  Entry i: dimension,
    points per direction, FP32 (1) or FP64, elements, the chosen shape and the per-launch
    times (us) of the four shapes (us holds 4 values; 0: not timed).  Returns the number of

@@ -14,7 +14,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT, "libimexgb.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["k_sipg.cu", "k_dg.cu", "k_vec.cu", "k_cg.cu", "k_fields.cu", "k_pmg.cu", "k_diag.cu", "k_stab.cu", "imex.cu", "basis.cpp"]
+SOURCES = ["k_sipg.cu", "k_sipg_line32.cu", "k_sipg_line64.cu", "k_dg.cu", "k_dg_ff.cu", "k_vec.cu", "k_cg.cu", "k_fields.cu", "k_pmg.cu", "k_diag.cu", "k_stab.cu", "imex.cu", "basis.cpp"]
 
 
 def _nvcc():

@@ -278,6 +278,8 @@ struct imex_ctx {
     float *b32[4] = {}, *x32[4] = {}, *r32[4] = {}, *d32[4] = {}, *ad32[4] = {};
     double *z64 = nullptr, *ones64 = nullptr;
     float *z32 = nullptr, *ones32 = nullptr;
+    // the FP32 coarsest level (N = 2, 3D periodic) smoothed by one cluster launch
+    bool cluster = false;
   } pmg;
   // divergence / mass-flux stabilisation after each stage projection (zeta_D, zeta_C; both
   // 0: off), the time step of the step in progress, the element speeds, the inverse mass of
@@ -482,8 +484,10 @@ SipgArgs<T> sipg_args(const T* x, T* y, int nsys, long long stride, const T* nu,
   a.variant = 0;
   a.cheb = 0;
   a.ch_last = 0;
+  a.ch_addx = 0;
   a.ch_r = a.ch_dout = a.ch_s = nullptr;
   a.ch_dinv = nullptr;
+  a.ch_b = nullptr;
   a.ch_c1 = a.ch_c2 = T(0);
   return a;
 }
@@ -855,6 +859,18 @@ imex_status pcg(imex_ctx* c, const imex_ctx::Seg& sg, Op op, OpDot op_dot, bool 
   return IMEX_OK;
 }
 
+// Decrease of the recursive FP32 residual between two replacements by the true FP64
+// residual (reliable updates of the mixed form): 1e-2, or IMEX_REFINE_DECADES decades
+// (1 to 5) from the environment
+static double refine_delta() {
+  static double d = [] {
+    const char* ev = std::getenv("IMEX_REFINE_DECADES");
+    const double k = ev ? std::atof(ev) : 2.0;
+    return std::pow(10.0, -((k >= 1.0 && k <= 5.0) ? k : 2.0));
+  }();
+  return d;
+}
+
 // Mixed-precision PCG (the IMEX_MIXED form).  The iteration itself runs entirely in FP32:
 // operator and Jacobi preconditioner applies, the correction y, the recursive residual and
 // the search directions (GB300's FP64 rate is a small fraction of its FP32 rate, so FP64
@@ -880,7 +896,7 @@ imex_status pcg_mixed(imex_ctx* c, const imex_ctx::Seg& sg, Op64 op64, Op32 op32
   defer_dot(c, sc, fused, t);
   const int nsys = t.nseg;
   const int m = c->maxsys;
-  const double delta = 1e-2;
+  const double delta = refine_delta();
   float* z = pm ? c->pmg.z32 : nullptr;
   const float* dj = pm ? c->pmg.ones32 : dinv;      // the step kernel's diagonal
   double* r64 = c->cr;
@@ -1214,13 +1230,20 @@ imex_status pmg_setup(imex_ctx* c) {
     M.lmax[l] = 1.15 * lam;
   }
   CK(cudaStreamSynchronize(c->st), "sync");
+  {
+    const char* ev = std::getenv("IMEX_PMG_CLUSTER");          // "0": separate launches per step
+    M.cluster = pmg_cluster_prepare(c->gp, M.N[M.nlev - 1]) && !(ev && ev[0] == '0');
+  }
   M.ready = true;
   return IMEX_OK;
 }
 
-// Chebyshev steps on level l for A x = b: from x = 0 (add = 0) or from the current x
+// Chebyshev steps on level l for A x = b, started from x = 0 (PMG_FROM_ZERO), from the
+// current x (PMG_FROM_X), or with the first step from zero already taken by the restriction
+// that produced b (PMG_PRESET: r = b, d = x = D^{-1} b / theta)
+enum { PMG_FROM_ZERO = 0, PMG_FROM_X = 1, PMG_PRESET = 2 };
 template <typename T>
-imex_status pmg_smooth(imex_ctx* c, int l, int steps, double lmax, double ratio, bool from_x, const T* b, T* x) {
+imex_status pmg_smooth(imex_ctx* c, int l, int steps, double lmax, double ratio, int start, const T* b, T* x) {
   imex_ctx::Pmg& M = c->pmg;
   using V = PmgVecs<T>;
   const size_t n = (size_t)c->gp.ne * ipow(M.N[l], c->d);
@@ -1230,10 +1253,33 @@ imex_status pmg_smooth(imex_ctx* c, int l, int steps, double lmax, double ratio,
   const T* dinv = V::dinv(M)[l];
   const double lmin = lmax / ratio;
   const double theta = 0.5 * (lmax + lmin), delta = 0.5 * (lmax - lmin), sigma = theta / delta;
-  if (from_x) TRY(pmg_apply<T>(c, l, x, ad));
-  prof_mark(c, IMEX_PROF_PMG_VEC, true);
-  cheb_first<T>(x, dv, r, b, from_x ? ad : nullptr, dinv, 1.0 / theta, n, from_x ? 1 : 0, c->st);
-  prof_end(c, IMEX_PROF_PMG_VEC, (from_x ? 7.0 : 5.0) * sizeof(T) * n, (from_x ? 4.0 : 2.0) * n, arith_t<T>());
+  const int cls = l == 0 ? IMEX_PROF_PMG_APPLY : IMEX_PROF_PMG_APPLY_COARSE;
+  const double apply_flops = sipg_flops_per_node(c->d, M.N[l]) * (double)n;
+  bool addx = false;
+  if (start == PMG_FROM_X && steps >= 2) {
+    // the first step from x in the apply of x: r = b - A x, d = D^{-1} r / theta; x itself
+    // takes d in the next step (ch_addx)
+    SipgArgs<T> a = sipg_args<T>(x, nullptr, 1, (long long)n, nullptr, 1.0, nullptr, 0.0, 1.0, 0);
+    a.ops = V::ops(M)[l];
+    a.variant = tuned_variant(c, M.N[l], sizeof(T) == 4);
+    a.cheb = 2;
+    a.ch_b = b;
+    a.ch_r = r;
+    a.ch_dout = dv;
+    a.ch_dinv = dinv;
+    a.ch_c1 = (T)(1.0 / theta);
+    prof_mark(c, cls, true);
+    const int rc = sipg_apply<T>(c->gp, M.N[l], a, c->st);
+    prof_end(c, cls, 5.0 * sizeof(T) * n, apply_flops + 3.0 * n, arith_t<T>());
+    TRY(launch_check(c, rc, "sipg_apply(chebyshev first)"));
+    addx = true;
+  } else if (start != PMG_PRESET) {
+    const bool from_x = start == PMG_FROM_X;
+    if (from_x) TRY(pmg_apply<T>(c, l, x, ad));
+    prof_mark(c, IMEX_PROF_PMG_VEC, true);
+    cheb_first<T>(x, dv, r, b, from_x ? ad : nullptr, dinv, 1.0 / theta, n, from_x ? 1 : 0, c->st);
+    prof_end(c, IMEX_PROF_PMG_VEC, (from_x ? 7.0 : 5.0) * sizeof(T) * n, (from_x ? 4.0 : 2.0) * n, arith_t<T>());
+  }
   double rho = 1.0 / sigma;
   // each further step is one apply whose output stage performs the update (the new direction
   // alternates between the two direction buffers, as neighbours still read the old one)
@@ -1247,17 +1293,16 @@ imex_status pmg_smooth(imex_ctx* c, int l, int steps, double lmax, double ratio,
     a.variant = tuned_variant(c, M.N[l], sizeof(T) == 4);
     a.cheb = 1;
     a.ch_last = last;
+    a.ch_addx = (k == 1 && addx) ? 1 : 0;
     a.ch_r = r;
     a.ch_dout = dnext;
     a.ch_s = x;
     a.ch_dinv = dinv;
     a.ch_c1 = (T)(rn * rho);
     a.ch_c2 = (T)(2.0 * rn / delta);
-    const int cls = l == 0 ? IMEX_PROF_PMG_APPLY : IMEX_PROF_PMG_APPLY_COARSE;
     prof_mark(c, cls, true);
     const int rc = sipg_apply<T>(c->gp, M.N[l], a, c->st);
-    prof_end(c, cls, (last ? 5.0 : 7.0) * sizeof(T) * n,
-             (sipg_flops_per_node(c->d, M.N[l]) + 6.0) * n, arith_t<T>());
+    prof_end(c, cls, (last ? 5.0 : 7.0) * sizeof(T) * n, apply_flops + (a.ch_addx ? 7.0 : 6.0) * n, arith_t<T>());
     TRY(launch_check(c, rc, "sipg_apply(chebyshev)"));
     std::swap(dcur, dnext);
     rho = rn;
@@ -1284,21 +1329,47 @@ imex_status pmg_vcycle(imex_ctx* c, const T* r, T* z, const double* lm) {
     b[l] = l == 0 ? r : V::b(M)[l];
     x[l] = l == 0 ? z : V::x(M)[l];
   }
+  // the coarsest level on one cluster (FP32): its restriction then writes b only
+  const bool clus = sizeof(T) == 4 && M.cluster && L >= 2;
   for (int l = 0; l + 1 < L; ++l) {
-    TRY(pmg_smooth<T>(c, l, M.pre, lm[l], M.ratio, false, b[l], x[l]));
+    TRY(pmg_smooth<T>(c, l, M.pre, lm[l], M.ratio, l == 0 ? PMG_FROM_ZERO : PMG_PRESET, b[l], x[l]));
     TRY(pmg_apply<T>(c, l, x[l], V::ad(M)[l]));
+    // restriction of the residual, with the first smoothing step (from zero) of level l + 1
+    const bool first = !(clus && l + 2 == L);
+    const double ratio1 = (l + 2 == L) ? M.cratio : M.ratio;
+    const double theta1 = 0.5 * (lm[l + 1] + lm[l + 1] / ratio1);
+    const ChebInit<T> ci = first ? ChebInit<T>{x[l + 1], V::d(M)[l + 1], V::r(M)[l + 1], V::dinv(M)[l + 1],
+                                               (T)(1.0 / theta1)}
+                                 : ChebInit<T>{nullptr, nullptr, nullptr, nullptr, T(0)};
     prof_mark(c, IMEX_PROF_PMG_VEC, true);
-    if (pmg_restrict<T>(c->d, c->gp.ne, M.N[l], M.N[l + 1], b[l], V::ad(M)[l], V::b(M)[l + 1], M.I[l], c->st) != 0)
+    if (pmg_restrict_cheb<T>(c->d, c->gp.ne, M.N[l], M.N[l + 1], b[l], V::ad(M)[l], V::b(M)[l + 1], M.I[l], ci,
+                             c->st) != 0)
       return fail(c, IMEX_EINVAL, "p-multigrid: unsupported level pair");
-    prof_end(c, IMEX_PROF_PMG_VEC, sizeof(T) * (2.0 * nodes(l) + nodes(l + 1)), xfer_flops(l), arith_t<T>());
+    prof_end(c, IMEX_PROF_PMG_VEC, sizeof(T) * (2.0 * nodes(l) + (first ? 5.0 : 1.0) * nodes(l + 1)),
+             xfer_flops(l) + (first ? 2.0 : 0.0) * nodes(l + 1), arith_t<T>());
   }
-  TRY(pmg_smooth<T>(c, L - 1, M.coarse, lm[L - 1], M.cratio, false, b[L - 1], x[L - 1]));
+  int crc = -1;
+  if constexpr (sizeof(T) == 4) {
+    if (clus) {
+      prof_mark(c, IMEX_PROF_PMG_APPLY_COARSE, true);
+      crc = pmg_coarse_cluster(c->gp, M.N[L - 1], b[L - 1], V::dinv(M)[L - 1], x[L - 1], M.coarse, lm[L - 1], M.cratio,
+                               c->st);
+      // b and D^{-1} read once, x written once; per step one apply and the update
+      prof_end(c, IMEX_PROF_PMG_APPLY_COARSE, 3.0 * sizeof(T) * nodes(L - 1),
+               (M.coarse - 1) * (sipg_flops_per_node(c->d, M.N[L - 1]) + 6.0) * nodes(L - 1) + 2.0 * nodes(L - 1),
+               arith_t<T>());
+      TRY(cuda_check(c, cudaGetLastError(), "pmg_coarse_cluster"));
+    }
+  }
+  if (crc != 0)
+    TRY(pmg_smooth<T>(c, L - 1, M.coarse, lm[L - 1], M.cratio, (L > 1 && !clus) ? PMG_PRESET : PMG_FROM_ZERO,
+                      b[L - 1], x[L - 1]));
   for (int l = L - 2; l >= 0; --l) {
     prof_mark(c, IMEX_PROF_PMG_VEC, true);
     if (pmg_prolong<T>(c->d, c->gp.ne, M.N[l], M.N[l + 1], x[l + 1], x[l], M.I[l], c->st) != 0)
       return fail(c, IMEX_EINVAL, "p-multigrid: unsupported level pair");
     prof_end(c, IMEX_PROF_PMG_VEC, sizeof(T) * (2.0 * nodes(l) + nodes(l + 1)), xfer_flops(l), arith_t<T>());
-    TRY(pmg_smooth<T>(c, l, M.pre, lm[l], M.ratio, true, b[l], x[l]));
+    TRY(pmg_smooth<T>(c, l, M.pre, lm[l], M.ratio, PMG_FROM_X, b[l], x[l]));
   }
   return cuda_check(c, cudaGetLastError(), "pmg_vcycle");
 }
@@ -1318,8 +1389,8 @@ imex_status tune_apply(imex_ctx* c, int N, int nsys, size_t n, const LineOps<T>*
     for (const auto& t : g_tune)
       if (t.d == c->d && t.N == N && t.f32 == (int)f32 && t.ne == c->gp.ne) return IMEX_OK;
   }
-  // 2D FP64: no doubled block (static shared memory); one element more: 3D FP32 only
-  const int nvar = (c->d == 2 && !f32) ? 2 : ((c->d == 3 && f32) ? 4 : 3);
+  // 2D FP64: no doubled block (static shared memory); one element more: 3D FP32, N = 7, 9
+  const int nvar = (c->d == 2 && !f32) ? 2 : ((c->d == 3 && f32 && (N == 7 || N == 9)) ? 4 : 3);
   TuneEntry te{c->d, N, (int)f32, c->gp.ne, 0, {0, 0, 0, 0}};
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0), "event");
@@ -3191,7 +3262,7 @@ imex_status imex_profile_work(imex_ctx* c, int cls, double* bytes, double* flops
 
 int imex_set_apply_variant(int d, int N, int fp32, long long ne, int variant) {
   if ((d != 2 && d != 3) || N < 2 || N > IMEX_MAXN || ne < 1 || variant < 0 || variant > 3 ||
-      (d == 2 && !fp32 && variant == 2) || (variant == 3 && (d != 3 || !fp32)))
+      (d == 2 && !fp32 && variant == 2) || (variant == 3 && (d != 3 || !fp32 || (N != 7 && N != 9))))
     return IMEX_EINVAL;
   std::lock_guard<std::mutex> lk(g_tune_mu);
   for (auto& t : g_tune)

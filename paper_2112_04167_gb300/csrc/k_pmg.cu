@@ -38,7 +38,8 @@ __host__ __device__ constexpr int xfer_epb() {
 // MODE 0: xf += P xc (prolongation and add); MODE 1: rc = P^T (bf - axf) (restriction)
 template <typename T, int D, int NF, int NC, int MODE>
 __global__ void __launch_bounds__(XF_THREADS)
-pmg_transfer_kernel(int ne, const T* __restrict__ in0, const T* __restrict__ in1, T* __restrict__ out, Interp1D I) {
+pmg_transfer_kernel(int ne, const T* __restrict__ in0, const T* __restrict__ in1, T* __restrict__ out, Interp1D I,
+                    ChebInit<T> ci) {
   constexpr int EPB = xfer_epb<D, NF>();
   constexpr int NFD = TileN<D, NF>::n, NCD = TileN<D, NC>::n;
   constexpr int BIG = NFD;                        // largest intermediate tile
@@ -95,24 +96,36 @@ pmg_transfer_kernel(int ne, const T* __restrict__ in0, const T* __restrict__ in1
     dst = t;
   }
   if (MODE == 1) {
-    for (int i = threadIdx.x; i < nel * NCD; i += blockDim.x) out[(size_t)e0 * NCD + i] = src[i / NCD][i % NCD];
+    for (int i = threadIdx.x; i < nel * NCD; i += blockDim.x) {
+      const size_t gi = (size_t)e0 * NCD + i;
+      const T v = src[i / NCD][i % NCD];
+      out[gi] = v;
+      if (ci.x) {                                 // the coarse level's first smoothing step
+        const T dd = ci.c0 * ci.dinv[gi] * v;
+        ci.r[gi] = v;
+        ci.d[gi] = dd;
+        ci.x[gi] = dd;
+      }
+    }
   } else {
     for (int i = threadIdx.x; i < nel * NFD; i += blockDim.x) out[(size_t)e0 * NFD + i] += src[i / NFD][i % NFD];
   }
 }
 
 template <typename T, int D, int NF, int NC, int MODE>
-void launch_transfer(int ne, const T* in0, const T* in1, T* out, const Interp1D& I, cudaStream_t st) {
+void launch_transfer(int ne, const T* in0, const T* in1, T* out, const Interp1D& I, const ChebInit<T>& ci,
+                     cudaStream_t st) {
   constexpr int EPB = xfer_epb<D, NF>();
   const int blocks = (ne + EPB - 1) / EPB;
-  IMEX_COUNTED((pmg_transfer_kernel<T, D, NF, NC, MODE><<<blocks, XF_THREADS, 0, st>>>(ne, in0, in1, out, I)));
+  IMEX_COUNTED((pmg_transfer_kernel<T, D, NF, NC, MODE><<<blocks, XF_THREADS, 0, st>>>(ne, in0, in1, out, I, ci)));
 }
 
 template <typename T, int D, int MODE>
-int transfer_d(int ne, int NF, int NC, const T* in0, const T* in1, T* out, const Interp1D& I, cudaStream_t st) {
+int transfer_d(int ne, int NF, int NC, const T* in0, const T* in1, T* out, const Interp1D& I, const ChebInit<T>& ci,
+               cudaStream_t st) {
 #define IMEX_XF(A, B)                                                    \
   if (NF == A && NC == B) {                                              \
-    launch_transfer<T, D, A, B, MODE>(ne, in0, in1, out, I, st);         \
+    launch_transfer<T, D, A, B, MODE>(ne, in0, in1, out, I, ci, st);     \
     return 0;                                                            \
   }
   IMEX_XF(9, 5) IMEX_XF(8, 4) IMEX_XF(7, 4) IMEX_XF(6, 3) IMEX_XF(5, 3) IMEX_XF(4, 2) IMEX_XF(3, 2)
@@ -165,14 +178,21 @@ int grid_for(size_t n) {
 
 template <typename T>
 int pmg_prolong(int d, int ne, int NF, int NC, const T* xc, T* xf, const Interp1D& I, cudaStream_t st) {
-  return d == 2 ? transfer_d<T, 2, 0>(ne, NF, NC, xc, nullptr, xf, I, st)
-                : transfer_d<T, 3, 0>(ne, NF, NC, xc, nullptr, xf, I, st);
+  const ChebInit<T> none{nullptr, nullptr, nullptr, nullptr, T(0)};
+  return d == 2 ? transfer_d<T, 2, 0>(ne, NF, NC, xc, nullptr, xf, I, none, st)
+                : transfer_d<T, 3, 0>(ne, NF, NC, xc, nullptr, xf, I, none, st);
+}
+template <typename T>
+int pmg_restrict_cheb(int d, int ne, int NF, int NC, const T* bf, const T* axf, T* rc, const Interp1D& I,
+                      const ChebInit<T>& ci, cudaStream_t st) {
+  return d == 2 ? transfer_d<T, 2, 1>(ne, NF, NC, bf, axf, rc, I, ci, st)
+                : transfer_d<T, 3, 1>(ne, NF, NC, bf, axf, rc, I, ci, st);
 }
 template <typename T>
 int pmg_restrict(int d, int ne, int NF, int NC, const T* bf, const T* axf, T* rc, const Interp1D& I,
                  cudaStream_t st) {
-  return d == 2 ? transfer_d<T, 2, 1>(ne, NF, NC, bf, axf, rc, I, st)
-                : transfer_d<T, 3, 1>(ne, NF, NC, bf, axf, rc, I, st);
+  const ChebInit<T> none{nullptr, nullptr, nullptr, nullptr, T(0)};
+  return pmg_restrict_cheb<T>(d, ne, NF, NC, bf, axf, rc, I, none, st);
 }
 template <typename T>
 void cheb_first(T* x, T* dv, T* r, const T* b, const T* ax, const T* dinv, double c0, size_t n, int add,
@@ -195,6 +215,10 @@ template int pmg_restrict<float>(int, int, int, int, const float*, const float*,
                                  cudaStream_t);
 template int pmg_restrict<double>(int, int, int, int, const double*, const double*, double*, const Interp1D&,
                                   cudaStream_t);
+template int pmg_restrict_cheb<float>(int, int, int, int, const float*, const float*, float*, const Interp1D&,
+                                      const ChebInit<float>&, cudaStream_t);
+template int pmg_restrict_cheb<double>(int, int, int, int, const double*, const double*, double*, const Interp1D&,
+                                       const ChebInit<double>&, cudaStream_t);
 template void cheb_first<float>(float*, float*, float*, const float*, const float*, const float*, double, size_t, int,
                                 cudaStream_t);
 template void cheb_first<double>(double*, double*, double*, const double*, const double*, const double*, double,

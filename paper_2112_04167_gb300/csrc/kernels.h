@@ -45,19 +45,25 @@ struct SipgArgs {
   // (inst_nu), and multiply beta by the instance's time step (inst_dt)
   int inst_nu;
   int inst_dt;
-  // Chebyshev smoother step fused into the apply (p-multigrid, constant-viscosity kernels):
-  // instead of y = A x the kernel updates, node by node, r -= A x, d' = c1 x + c2 D^{-1} r,
-  // s += d' (x is the previous direction; d' goes to a buffer other than x); with ch_last
-  // only s is stored.  cheb = 0: the plain apply.
   // launch shape chosen by the tuner for the periodic constant-viscosity kernels (elements
-  // per block: 0 the default, 1 half, 2 twice; other kernels ignore it)
+  // per block: 0 the default, 1 half, 2 twice, 3 one more; other kernels ignore it)
   int variant;
+  // Chebyshev smoother steps fused into the apply (p-multigrid, constant-viscosity kernels),
+  // node by node instead of y = A x:
+  //   cheb = 1: r -= A x, d' = c1 x + c2 D^{-1} r, s += d' (x is the previous direction; d'
+  //             goes to a buffer other than x); ch_last: only s is stored; ch_addx: s += x + d'
+  //             (the first step's direction, not yet added to s)
+  //   cheb = 2: the first step from the current s = x: r = b - A x, d = c1 D^{-1} r (s is left
+  //             for the next step to add d to, with ch_addx)
+  //   cheb = 0: the plain apply.
   int cheb;
   int ch_last;
+  int ch_addx;
   T* ch_r;
   T* ch_dout;
   T* ch_s;
   const T* ch_dinv;
+  const T* ch_b;
   T ch_c1, ch_c2;
 };
 
@@ -193,6 +199,27 @@ int pmg_prolong(int d, int ne, int NF, int NC, const T* xc, T* xf, const Interp1
 // rc = P^T (bf - axf): restriction of the fine residual
 template <typename T>
 int pmg_restrict(int d, int ne, int NF, int NC, const T* bf, const T* axf, T* rc, const Interp1D& I, cudaStream_t st);
+// the same, with the coarse level's first Chebyshev step from zero fused into the output:
+// r = rc, d = x = c0 D^{-1} rc
+// The coarsest p-multigrid level (N = 2, 3D, every face periodic, one mesh instance, FP32)
+// on one thread-block cluster: pmg_cluster_prepare decides once per device and element
+// count whether the GPU can run it (call it outside stream capture); pmg_coarse_cluster then
+// runs all `steps` Chebyshev steps from x = 0 for A x = b on [lmax / ratio, lmax] in one
+// launch, or returns -1 (nothing launched) when it was not prepared for this mesh
+bool pmg_cluster_prepare(const Geom& g, int N);
+int pmg_coarse_cluster(const Geom& g, int N, const float* b, const float* dinv, float* x, int steps, double lmax,
+                       double ratio, cudaStream_t st);
+template <typename T>
+struct ChebInit {
+  T* x;
+  T* d;
+  T* r;
+  const T* dinv;
+  T c0;
+};
+template <typename T>
+int pmg_restrict_cheb(int d, int ne, int NF, int NC, const T* bf, const T* axf, T* rc, const Interp1D& I,
+                      const ChebInit<T>& ci, cudaStream_t st);
 // Chebyshev smoother steps: first  r = b - ax (ax may be null: r = b), d = c0 D^{-1} r,
 // x = (add ? x : 0) + d;  next  r -= ad, d = c1 d + c2 D^{-1} r, x += d (last: r, d not stored)
 template <typename T>

@@ -76,6 +76,45 @@ def test_vcycle_parity(case, oracles):
     assert rel(ctx.op_pmg_vcycle(r, lmax=M.lmax, arith=imex.ARITH_FP32), ref) < 1e-5
 
 
+@pytest.mark.parametrize("case", [(2, 6, (6, 1), (True, True)), (3, 5, (4, 1, 1), (True, True, True)),
+                                  (3, 4, (1, 3, 2), (True, False, True))])
+def test_vcycle_single_element_periodic(case):
+    """One element across a periodic direction is its own neighbour there: the Jacobi diagonal
+    of every level and the V-cycle equal the oracle's (assembled matrix)."""
+    d, P, n, per = case
+    mesh = dg.Mesh(d, P, n, LO[:d], HI[:d], per)
+    M = pmg.PMG(mesh, P)
+    ctx, _ = make(case)
+    r = inputs.field(ctx.npres, seed=64)
+    ref = M.vcycle(r)
+    assert rel(ctx.op_pmg_vcycle(r, lmax=M.lmax), ref) < 1e-11
+    assert rel(ctx.op_pmg_vcycle(r, lmax=M.lmax, arith=imex.ARITH_FP32), ref) < 1e-5
+
+
+@pytest.mark.parametrize("n", [(5, 4, 3), (3, 2, 3), (17, 2, 2), (17, 1, 1)])
+def test_coarsest_level_on_one_cluster(n, monkeypatch):
+    """The FP32 coarsest level (N = 2) of a 3D periodic mesh smoothed in one cluster launch
+    (elements split over the CTAs, neighbours across CTAs read from their shared memory)
+    gives the oracle's V-cycle and that of one launch per Chebyshev step, with fewer launches
+    (meshes with several elements per CTA, idle CTAs, a ragged last CTA)."""
+    case = (3, 7, n, (True, True, True))
+    mesh = dg.Mesh(3, 7, n, LO, HI, case[3])
+    M = pmg.PMG(mesh, 7)
+    r = inputs.field(M.A[0].shape[0], seed=63)
+    ref = M.vcycle(r)
+    out = {}
+    for flag in ("1", "0"):
+        monkeypatch.setenv("IMEX_PMG_CLUSTER", flag)
+        ctx, _ = make(case)
+        ctx.op_pmg_vcycle(r, lmax=M.lmax, arith=imex.ARITH_FP32)         # set-up, tuning
+        before = imex.launch_count()
+        out[flag] = ctx.op_pmg_vcycle(r, lmax=M.lmax, arith=imex.ARITH_FP32)
+        out[flag + "n"] = imex.launch_count() - before
+    errs = (rel(out["1"], ref), rel(out["0"], ref), rel(out["1"], out["0"]))
+    assert max(errs) < 1e-5, errs
+    assert out["1n"] < out["0n"]
+
+
 @pytest.mark.parametrize("case", CASES)
 def test_chebyshev_bounds_estimate(case, oracles):
     _, exact = oracles[case]

@@ -1,5 +1,5 @@
 """The launch-shape tuner of the periodic constant-viscosity SIPG applies: every shape (the
-default elements per block, half and twice as many, one more in 3D FP32) gives the oracle's operator element by
+default elements per block, half and twice as many, one more in 3D FP32 at N = 7, 9) gives the oracle's operator element by
 element (FP64 1e-12, FP32 1e-5) in 2D and 3D on meshes with ragged last blocks, and the tuner
 records a timed choice for the applies a solve uses, with the solve still equal to the
 oracle's."""
@@ -37,7 +37,7 @@ def test_every_launch_shape(case, variant):
     x = inputs.field(ctx.npres, seed=91)
     L = dg.sipg_matrix(mesh, P, 1.0, dirichlet=False)
     for fp32, tol in ((True, 1e-5), (False, 1e-12)):
-        if (d == 2 and not fp32 and variant == 2) or (variant == 3 and (d == 2 or not fp32)):
+        if (d == 2 and not fp32 and variant == 2) or (variant == 3 and (d == 2 or not fp32 or P not in (7, 9))):
             continue
         imex.set_apply_variant(d, P, fp32, ne, variant)
         y = ctx.op_sipg(x, space=imex.SPACE_PRESSURE, precision=imex.ARITH_FP32 if fp32 else imex.ARITH_FP64)
@@ -55,4 +55,5 @@ def test_tuner_records_and_solve_matches():
     tuned = [t for t in imex.tuning_info() if t["d"] == 3 and t["elements"] == 36 and t["fp32"]]
     assert {t["N"] for t in tuned} >= {5, 3, 2}          # the CG apply and the V-cycle levels
     for t in tuned:
-        assert t["variant"] in (0, 1, 2, 3) and min(t["us"]) > 0.0
+        timed = 4 if t["N"] in (7, 9) else 3           # the one-more-element shape: N = 7, 9
+        assert t["variant"] in range(timed) and min(t["us"][:timed]) > 0.0
