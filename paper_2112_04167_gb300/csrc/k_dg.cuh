@@ -408,10 +408,19 @@ struct ConvShape {
   static constexpr int NF = ipow(N, D - 1);
   static constexpr int NFQ = ipow(Q, D - 1);
   static constexpr int THREADS = (ND < 128) ? 128 : ((ND + 31) / 32) * 32;
-  // shared: tables + sv[D][ND] + vg[D][NQ] + 2 work[NQ] + acc[D][ND] + face buffers
-  static constexpr size_t SMEM =
-      sizeof(T) * (size_t)(2 * Q * N + Q + N + D * ND + D * NQ + 2 * NQ + D * ND +
-                           2 * D * NFQ + 2 * NFQ + NF);
+  // face phase, all 2D faces x D components x {own, neighbour} in every pass, in two
+  // alternating regions: R2 (first tangential pass, flux, result on the face nodes) from the
+  // start of sv, R1 (traces, Gauss-point values, first pass back) after R2 and after sv
+  // (the traces are written while sv is still read)
+  static constexpr int NFC = 2 * D;
+  static constexpr int R1 = NFC * D * 2 * NFQ;
+  static constexpr int R2 = D == 3 ? NFC * D * 2 * Q * N : NFC * D * 2 * Q;
+  static constexpr int R1_OFF = R2 > D * ND ? R2 : D * ND;
+  // free after the volume term: sv, vg, w1, w2 (contiguous, the end of the layout)
+  static constexpr int FREE = D * ND + D * NQ + 2 * NQ;
+  static constexpr int EXTRA = R1_OFF + R1 > FREE ? R1_OFF + R1 - FREE : 0;
+  // shared: tables + acc[D][ND] + sv[D][ND] + vg[D][NQ] + 2 work[NQ] + extra face scratch
+  static constexpr size_t SMEM = sizeof(T) * (size_t)(2 * Q * N + Q + N + D * ND + FREE + EXTRA);
 };
 
 
@@ -427,16 +436,12 @@ __global__ void dg_conv_kernel(Geom g, ConvArgs<TS> a) {
   T* sDG = sIG + Q * N;                         // [Q*N]
   T* sgw = sDG + Q * N;                         // [Q]
   T* sw = sgw + Q;                              // [N]
-  T* sv = sw + N;                               // [D][ND]
+  T* acc = sw + N;                              // [D][ND]
+  T* sv = acc + D * ND;                         // [D][ND]
   T* vg = sv + D * ND;                          // [D][NQ]
   T* w1 = vg + D * NQ;                          // [NQ]
   T* w2 = w1 + NQ;                              // [NQ]
-  T* acc = w2 + NQ;                             // [D][ND]
-  T* fm = acc + D * ND;                         // [D][NFQ] own trace at face Gauss points
-  T* fp = fm + D * NFQ;                         // [D][NFQ] neighbour trace
-  T* fh = fp + D * NFQ;                         // [NFQ] flux of one component
-  T* ft = fh + NFQ;                             // [NFQ] scratch
-  T* fo = ft + NFQ;                             // [NF] result on the face nodes
+  __shared__ int snb[6];
   const Tables<TT>& tb = tab<TT>(g);
   for (int i = threadIdx.x; i < Q * N; i += blockDim.x) { sIG[i] = T(tb.IG[N][i]); sDG[i] = T(tb.DG[N][i]); }
   for (int i = threadIdx.x; i < Q; i += blockDim.x) sgw[i] = T(tb.gw[N][i]);
@@ -474,111 +479,136 @@ __global__ void dg_conv_kernel(Geom g, ConvArgs<TS> a) {
     }
   }
   __syncthreads();
-  // --- face terms
-  for (int k = 0; k < D; ++k) {
-    for (int side = 0; side < 2; ++side) {
-      const int nb = neighbor(gl, ec, k, side ? 1 : -1);
-      const T n = side ? T(1) : T(-1);
-      // traces on the N^{D-1} face nodes -> interpolate tangentially to Q^{D-1}
-      for (int c = 0; c < D; ++c) {
-        for (int f = t; f < NF; f += nt) {
-          int cc[3] = {0, 0, 0};
-          face_coords<D>(f, k, N, cc);
-          cc[k] = side ? N - 1 : 0;
-          const int own = flat3(cc, N, D);
-          fo[f] = sv[c * ND + own];
-          T pv;
-          if (nb >= 0) {
-            cc[k] = side ? 0 : N - 1;
-            pv = T(a.v[(size_t)c * a.stride + (size_t)nb * ND + flat3(cc, N, D)]);
-          } else {
-            pv = a.vb ? T(a.vb[(size_t)c * a.stride + (size_t)e * ND + own]) : sv[c * ND + own];
-          }
-          ft[f] = pv;
-        }
-        __syncthreads();
-        // tangential interpolation (D-1 dims)
-        if (D == 2) {
-          for (int q = t; q < Q; q += nt) {
-            T s1 = T(0), s2 = T(0);
-            for (int j = 0; j < N; ++j) { s1 += sIG[q * N + j] * fo[j]; s2 += sIG[q * N + j] * ft[j]; }
-            fm[c * NFQ + q] = s1;
-            fp[c * NFQ + q] = s2;
-          }
-        } else {
-          // first tangential dim: (N x N) -> (Q x N), stored in fh / w1 scratch
-          for (int o = t; o < Q * N; o += nt) {
-            const int q0 = o % Q, j1 = o / Q;
-            T s1 = T(0), s2 = T(0);
-            for (int j = 0; j < N; ++j) {
-              s1 += sIG[q0 * N + j] * fo[j + N * j1];
-              s2 += sIG[q0 * N + j] * ft[j + N * j1];
-            }
-            w1[o] = s1;
-            w2[o] = s2;
-          }
-          __syncthreads();
-          for (int o = t; o < NFQ; o += nt) {
-            const int q0 = o % Q, q1 = o / Q;
-            T s1 = T(0), s2 = T(0);
-            for (int j = 0; j < N; ++j) {
-              s1 += sIG[q1 * N + j] * w1[q0 + Q * j];
-              s2 += sIG[q1 * N + j] * w2[q0 + Q * j];
-            }
-            fm[c * NFQ + o] = s1;
-            fp[c * NFQ + o] = s2;
-          }
-        }
-        __syncthreads();
-      }
-      // LLF flux per component, weighted, projected back onto the face nodes
-      for (int c = 0; c < D; ++c) {
-        for (int q = t; q < NFQ; q += nt) {
-          T W = jac / (geom_h<T>(gl, k) * T(0.5));
-          int r = q;
-          for (int j = 0; j < D - 1; ++j) { W *= sgw[r % Q]; r /= Q; }
-          const T vmn = n * fm[k * NFQ + q];
-          const T vpn = n * fp[k * NFQ + q];
-          const T am = vmn < T(0) ? -vmn : vmn;
-          const T ap = vpn < T(0) ? -vpn : vpn;
-          const T lam = am > ap ? am : ap;
-          const T H = T(0.5) * (fm[c * NFQ + q] * vmn + fp[c * NFQ + q] * vpn) +
-                      T(0.5) * lam * (fm[c * NFQ + q] - fp[c * NFQ + q]);
-          fh[q] = W * H;
-        }
-        __syncthreads();
-        if (D == 2) {
-          for (int f = t; f < N; f += nt) {
-            T s = T(0);
-            for (int q = 0; q < Q; ++q) s += sIG[q * N + f] * fh[q];
-            fo[f] = s;
-          }
-        } else {
-          for (int o = t; o < N * Q; o += nt) {      // (Q x Q) -> (N x Q)
-            const int j0 = o % N, q1 = o / N;
-            T s = T(0);
-            for (int q = 0; q < Q; ++q) s += sIG[q * N + j0] * fh[q + Q * q1];
-            ft[o] = s;
-          }
-          __syncthreads();
-          for (int o = t; o < NF; o += nt) {          // (N x Q) -> (N x N)
-            const int j0 = o % N, j1 = o / N;
-            T s = T(0);
-            for (int q = 0; q < Q; ++q) s += sIG[q * N + j1] * ft[j0 + N * q];
-            fo[o] = s;
-          }
-        }
-        __syncthreads();
-        for (int f = t; f < NF; f += nt) {
-          int cc[3] = {0, 0, 0};
-          face_coords<D>(f, k, N, cc);
-          cc[k] = side ? N - 1 : 0;
-          acc[c * ND + flat3(cc, N, D)] -= fo[f];
-        }
-        __syncthreads();
-      }
+  // --- face terms: every face, component and side in each pass
+  constexpr int NFC = S::NFC;
+  if (t < NFC) snb[t] = neighbor(gl, ec, t >> 1, (t & 1) ? 1 : -1);
+  __syncthreads();
+  T* const R2 = sv;                             // see ConvShape
+  T* const R1 = sv + S::R1_OFF;
+  // traces at the face nodes, R1[((f D + c) 2 + s) NF + node], s = 0 own, 1 neighbour
+  // (Dirichlet data, or the own trace without data, on a domain boundary)
+  for (int task = t; task < NFC * D * NF; task += nt) {
+    const int f = task / (D * NF), rem = task - f * (D * NF), c = rem / NF, fn = rem - c * NF;
+    const int k = f >> 1, side = f & 1;
+    int cc[3] = {0, 0, 0};
+    face_coords<D>(fn, k, N, cc);
+    cc[k] = side ? N - 1 : 0;
+    const int own = flat3(cc, N, D);
+    const T ov = sv[c * ND + own];
+    const int nb = snb[f];
+    T pv;
+    if (nb >= 0) {
+      cc[k] = side ? 0 : N - 1;
+      pv = T(a.v[(size_t)c * a.stride + (size_t)nb * ND + flat3(cc, N, D)]);
+    } else {
+      pv = a.vb ? T(a.vb[(size_t)c * a.stride + (size_t)e * ND + own]) : ov;
+    }
+    const int base = ((f * D + c) * 2) * NF + fn;
+    R1[base] = ov;
+    R1[base + NF] = pv;
+  }
+  __syncthreads();
+  // the traces at the face Gauss points, R1[((f D + c) 2 + s) NFQ + q] (tangential
+  // interpolation; in 3D the first tangential direction into R2 first)
+  constexpr int NTR = NFC * D * 2;              // trace fields
+  if constexpr (D == 2) {
+    for (int task = t; task < NTR * Q; task += nt) {
+      const int fld = task / Q, q = task - fld * Q;
+      DotAcc<T> s1;
+#pragma unroll
+      for (int j = 0; j < N; ++j) s1.add(sIG[q * N + j], R1[fld * NF + j]);
+      R2[fld * Q + q] = s1.value();
+    }
+    __syncthreads();
+    for (int task = t; task < NTR * Q; task += nt) R1[task] = R2[task];
+  } else {
+    for (int task = t; task < NTR * Q * N; task += nt) {
+      const int fld = task / (Q * N), o = task - fld * (Q * N), q0 = o % Q, j1 = o / Q;
+      DotAcc<T> s1;
+#pragma unroll
+      for (int j = 0; j < N; ++j) s1.add(sIG[q0 * N + j], R1[fld * NF + j + N * j1]);
+      R2[task] = s1.value();
+    }
+    __syncthreads();
+    for (int task = t; task < NTR * NFQ; task += nt) {
+      const int fld = task / NFQ, o = task - fld * NFQ, q0 = o % Q, q1 = o / Q;
+      DotAcc<T> s1;
+#pragma unroll
+      for (int j = 0; j < N; ++j) s1.add(sIG[q1 * N + j], R2[fld * (Q * N) + q0 + Q * j]);
+      R1[task] = s1.value();
     }
   }
+  __syncthreads();
+  // LLF flux of every face and component at the face Gauss points, weighted:
+  // R2[(f D + c) NFQ + q]
+  for (int task = t; task < NFC * D * NFQ; task += nt) {
+    const int f = task / (D * NFQ), rem = task - f * (D * NFQ), c = rem / NFQ, q = rem - c * NFQ;
+    const int k = f >> 1;
+    const T n = (f & 1) ? T(1) : T(-1);
+    T W = jac / (geom_h<T>(gl, k) * T(0.5));
+    int r = q;
+    for (int j = 0; j < D - 1; ++j) { W *= sgw[r % Q]; r /= Q; }
+    const T* fk = R1 + ((f * D + k) * 2) * NFQ;           // normal component, own / neighbour
+    const T* fc = R1 + ((f * D + c) * 2) * NFQ;
+    const T vmn = n * fk[q];
+    const T vpn = n * fk[NFQ + q];
+    const T am = vmn < T(0) ? -vmn : vmn;
+    const T ap = vpn < T(0) ? -vpn : vpn;
+    const T lam = am > ap ? am : ap;
+    const T H = T(0.5) * (fc[q] * vmn + fc[NFQ + q] * vpn) + T(0.5) * lam * (fc[q] - fc[NFQ + q]);
+    R2[task] = W * H;
+  }
+  __syncthreads();
+  // tested against the face basis: back to the face nodes, R2[(f D + c) NF + node]
+  constexpr int NHF = NFC * D;                  // flux fields
+  if constexpr (D == 2) {
+    for (int task = t; task < NHF * N; task += nt) {
+      const int fld = task / N, j0 = task - fld * N;
+      DotAcc<T> s1;
+#pragma unroll
+      for (int q = 0; q < Q; ++q) s1.add(sIG[q * N + j0], R2[fld * Q + q]);
+      R1[task] = s1.value();
+    }
+    __syncthreads();
+    for (int task = t; task < NHF * N; task += nt) R2[task] = R1[task];
+  } else {
+    for (int task = t; task < NHF * N * Q; task += nt) {
+      const int fld = task / (N * Q), o = task - fld * (N * Q), j0 = o % N, q1 = o / N;
+      DotAcc<T> s1;
+#pragma unroll
+      for (int q = 0; q < Q; ++q) s1.add(sIG[q * N + j0], R2[fld * NFQ + q + Q * q1]);
+      R1[task] = s1.value();
+    }
+    __syncthreads();
+    for (int task = t; task < NHF * NF; task += nt) {
+      const int fld = task / NF, o = task - fld * NF, j0 = o % N, j1 = o / N;
+      DotAcc<T> s1;
+#pragma unroll
+      for (int q = 0; q < Q; ++q) s1.add(sIG[q * N + j1], R1[fld * (N * Q) + j0 + N * q]);
+      R2[task] = s1.value();
+    }
+  }
+  __syncthreads();
+  // subtract from the nodes on the faces (a node on an edge or corner: every face it is on)
+  for (int task = t; task < D * ND; task += nt) {
+    const int c = task / ND, node = task - c * ND;
+    const int id[3] = {node % N, D > 1 ? (node / N) % N : 0, D > 2 ? node / (N * N) : 0};
+    T s1 = acc[task];
+#pragma unroll
+    for (int f = 0; f < NFC; ++f) {
+      const int k = f >> 1;
+      if (id[k] != ((f & 1) ? N - 1 : 0)) continue;
+      int fn = 0, mul = 1;
+      for (int j = 0; j < D; ++j) {
+        if (j == k) continue;
+        fn += id[j] * mul;
+        mul *= N;
+      }
+      s1 -= R2[(f * D + c) * NF + fn];
+    }
+    acc[task] = s1;
+  }
+  __syncthreads();
   // --- M^{-1}
   for (int c = 0; c < D; ++c)
     for (int i = t; i < ND; i += nt) {
