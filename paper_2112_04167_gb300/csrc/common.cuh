@@ -120,9 +120,6 @@ template <> __device__ __forceinline__ const Tables<float>& tab<float>(const Geo
 }
 
 __host__ __device__ constexpr int ipow(int b, int e) { return e == 0 ? 1 : b * ipow(b, e - 1); }
-
-// bring the 128-byte line holding p into L1 (p must point into an allocation)
-__device__ __forceinline__ void prefetch_l1(const void* p) { asm volatile("prefetch.global.L1 [%0];" ::"l"(p)); }
 __host__ __device__ constexpr int over_q(int N) { return (3 * N + 1) / 2; }
 
 // The geometry of element e as seen from its own instance: box, counts and sizes of the

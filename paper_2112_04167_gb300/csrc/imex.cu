@@ -195,6 +195,7 @@ struct imex_ctx {
   std::vector<double*> sv, snu, sFEX, sFIM, sFq;
   // CG (FP64 and FP32)
   double *cx = nullptr, *cr = nullptr, *cz = nullptr, *cp = nullptr, *cAp = nullptr, *cdiag = nullptr;
+  double* ffx = nullptr;     // float-float pairs of a float-float apply's input (same size as FP64)
   float *fx = nullptr, *fr = nullptr, *fp = nullptr, *fAp = nullptr, *fdiag = nullptr;
   float *fnu = nullptr, *fvtmp = nullptr;
   double* partial = nullptr;
@@ -488,6 +489,7 @@ SipgArgs<T> sipg_args(const T* x, T* y, int nsys, long long stride, const T* nu,
   a.ch_r = a.ch_dout = a.ch_s = nullptr;
   a.ch_dinv = nullptr;
   a.ch_b = nullptr;
+  a.xff = nullptr;
   a.ch_c1 = a.ch_c2 = T(0);
   return a;
 }
@@ -579,7 +581,7 @@ int arith_of(const imex_ctx* c);
 template <typename T>
 int apply_dispatch(imex_ctx* c, const Geom& g, int N, const SipgArgs<T>& a) {
   if (sizeof(T) == 8 && ff_class(c)) {
-    const int rc = sipg_apply_ff(g, N, reinterpret_cast<const SipgArgs<double>&>(a), c->st);
+    const int rc = sipg_apply_ff(g, N, reinterpret_cast<const SipgArgs<double>&>(a), c->ffx, c->st);
     if (rc == 0) return 0;
   }
   return sipg_apply<T>(g, N, a, c->st);
@@ -2286,7 +2288,8 @@ imex_status init_ctx(imex_ctx* c) {
   }
   const size_t nt = nvc * d;
   const size_t big = std::max(nt, npc);
-  double** f64[] = {&c->v, &c->vp, &c->vpp, &c->g, &c->tmp, &c->vb, &c->cx, &c->cr, &c->cz, &c->cp, &c->cAp};
+  double** f64[] = {&c->v, &c->vp, &c->vpp, &c->g, &c->tmp, &c->vb, &c->cx, &c->cr, &c->cz, &c->cp, &c->cAp,
+                     &c->ffx};
   for (double** p : f64) if ((s = dalloc(c, p, big)) != IMEX_OK) return bail(s);
   if ((s = dalloc(c, &c->nu, nvc)) != IMEX_OK) return bail(s);
   if ((s = dalloc(c, &c->nu_fixed, nvc)) != IMEX_OK) return bail(s);
@@ -2926,7 +2929,7 @@ imex_status imex_op_sipg(imex_ctx* c, int space, const double* x, double* y, int
     SipgArgs<double> a = sipg_args<double>(c->cx, c->cAp, nsys, (long long)n, dnu, nu0, dg, alpha, beta, minv);
     a.ops = line_ops<double>(c, vel);
     prof_mark(c, cls64, true);
-    const int rc = sipg_apply_ff(g, N, a, c->st);
+    const int rc = sipg_apply_ff(g, N, a, c->ffx, c->st);
     prof_end(c, cls64, 8.0 * words, flops, IMEX_ARITH_FF);
     if (rc != 0) return fail(c, IMEX_EINVAL, "no float-float kernel for this operator");
     TRY(cuda_check(c, cudaGetLastError(), "sipg_apply_ff"));

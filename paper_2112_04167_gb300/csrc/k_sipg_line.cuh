@@ -202,8 +202,9 @@ __device__ __forceinline__ LineFaces<T> line_faces(const ConstLine<T>& L, const 
   return f;
 }
 
-template <typename T, int N, typename TS = T, int V = 0, int EP = SIPG_EP_ANY>
-__device__ __forceinline__ T sipg3l_group(const Geom& g, const SipgArgs<TS>& a, const TS* __restrict__ x,
+// TX: the input's storage type (TS, or float-float pairs converted beforehand)
+template <typename T, int N, typename TS = T, int V = 0, int EP = SIPG_EP_ANY, typename TX = TS>
+__device__ __forceinline__ T sipg3l_group(const Geom& g, const SipgArgs<TS>& a, const TX* __restrict__ x,
                                           TS* __restrict__ y, int grp, int sys = 0) {
   using S = Sipg3lShape<T, N, V>;
   constexpr int NN = S::NN, ND = S::ND, EPB = S::EPB, NP = S::NP, TILE = S::TILE, VEC = S::VEC;
@@ -214,6 +215,8 @@ __device__ __forceinline__ T sipg3l_group(const Geom& g, const SipgArgs<TS>& a, 
 #define IMEX_SIPG3L_HOIST 1
 #endif
   constexpr bool HOIST = IMEX_SIPG3L_HOIST && sizeof(T) == 4 && N <= 8;
+  // the fixed output stages (no M^{-1}) write through the shared accumulator tile
+  constexpr bool COAL = EP != SIPG_EP_ANY;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* tile = reinterpret_cast<T*>(smem_raw);                       // [EPB][z][y][NP]
   T* acc = tile + EPB * TILE;                                     // [EPB][z][y][x]
@@ -253,12 +256,12 @@ __device__ __forceinline__ T sipg3l_group(const Geom& g, const SipgArgs<TS>& a, 
     wb = tbl.w[N][tb];
   }
   // neighbour lines: z at (x = ta, y = tb), y at (x = ta, z = tb), x at (y = ta, z = tb)
-  const TS* zl = x + (size_t)nb[4] * ND + t;
-  const TS* zr = x + (size_t)nb[5] * ND + t;
-  const TS* yl = x + (size_t)nb[2] * ND + tb * NN + ta;
-  const TS* yr = x + (size_t)nb[3] * ND + tb * NN + ta;
-  const TS* xl = x + (size_t)nb[0] * ND + tb * NN + ta * N;
-  const TS* xr = x + (size_t)nb[1] * ND + tb * NN + ta * N;
+  const TX* zl = x + (size_t)nb[4] * ND + t;
+  const TX* zr = x + (size_t)nb[5] * ND + t;
+  const TX* yl = x + (size_t)nb[2] * ND + tb * NN + ta;
+  const TX* yr = x + (size_t)nb[3] * ND + tb * NN + ta;
+  const TX* xl = x + (size_t)nb[0] * ND + tb * NN + ta * N;
+  const TX* xr = x + (size_t)nb[1] * ND + tb * NN + ta * N;
   // own element into the shared tile; the z-column (ta, tb) stays in registers
   T u[N];
 #pragma unroll
@@ -276,18 +279,6 @@ __device__ __forceinline__ T sipg3l_group(const Geom& g, const SipgArgs<TS>& a, 
     }
 #pragma unroll
     for (int k = 0; k < N; ++k) mt[(k * N + tb) * NP + ta] = u[k];
-    // the Chebyshev stages' operands at the thread's output line (x = 0..N-1 at y = ta,
-    // z = tb), fetched into L1 now so that the output stage does not wait on L2
-    if constexpr (EP == SIPG_EP_CHEB || EP == SIPG_EP_CHEB_FIRST) {
-      const size_t o0 = eb + (size_t)(tb * N + ta) * N;
-      prefetch_l1(a.ch_dinv + o0);
-      if constexpr (EP == SIPG_EP_CHEB) {
-        prefetch_l1(a.ch_r + o0);
-        prefetch_l1(a.ch_s + o0);
-      } else {
-        prefetch_l1(a.ch_b + o0);
-      }
-    }
   }
   // pass z: line (x = ta, y = tb) along z
   if (live) {
@@ -341,8 +332,27 @@ __device__ __forceinline__ T sipg3l_group(const Geom& g, const SipgArgs<TS>& a, 
       for (int j = 0; j < N; ++j) so += L.A[o * N + j] * v[j];
       const int node = (tb * N + ta) * N + o;
       const T W = wyz * (T(0.5) * hx * L.w[o]);
-      const T out = sipg_out_ep<EP, T, TS>(a, y, eb + node, v[o], alpha * W * v[o] + scale * (ma[node] + wt * so), W);
-      dacc += v[o] * out;
+      const T res = alpha * W * v[o] + scale * (ma[node] + wt * so);
+      if constexpr (COAL) {
+        ma[node] = res;                         // staged: the output stage runs by z-columns
+      } else {
+        const T out = sipg_out_ep<EP, T, TS>(a, y, eb + node, v[o], res, W);
+        dacc += v[o] * out;
+      }
+    }
+  }
+  if constexpr (COAL) {
+    // the fixed output stages by z-columns (x = ta, y = tb): a warp's accesses to y and to
+    // the Chebyshev vectors are contiguous, where the x-lines of the pass are 4N bytes apart
+    __syncthreads();
+    if (live) {
+#pragma unroll
+      for (int k = 0; k < N; ++k) {
+        const int node = k * NN + t;
+        const T xin = mt[(k * N + tb) * NP + ta];
+        const T out = sipg_out_ep<EP, T, TS>(a, y, eb + node, xin, ma[node], T(1));
+        dacc += xin * out;
+      }
     }
   }
   return dacc;
@@ -361,7 +371,9 @@ __device__ __forceinline__ T sipg3l_group(const Geom& g, const SipgArgs<TS>& a, 
 __host__ __device__ constexpr int sipg3p_minb(int V, bool f32, bool isff) {
   return V == 2 ? 1 : (f32 ? IMEX_SIPG3P_MINB : (isff ? 2 : 1));
 }
-template <typename T, int N, typename TS = T, int V = 0, int EP = SIPG_EP_ANY>
+// XFF: the input is a.xff, float-float pairs converted from a.x beforehand (float-float
+// applies: no FP64 conversions in the kernel)
+template <typename T, int N, typename TS = T, int V = 0, int EP = SIPG_EP_ANY, bool XFF = false>
 __global__ void __launch_bounds__(Sipg3pShape<T, N, V>::THREADS,
                                   sipg3p_minb(V, sizeof(T) == 4 && N <= 8, std::is_same<T, ff>::value))
 sipg3p_apply_kernel(Geom g, SipgArgs<TS> a) {
@@ -373,8 +385,13 @@ sipg3p_apply_kernel(Geom g, SipgArgs<TS> a) {
       if (a.dot_out && threadIdx.x == 0) put_dot_partial(a, s, 0.0);
       continue;
     }
-    const T dacc = sipg3l_group<T, N, TS, V, EP>(g, a, a.x + (size_t)s * a.sys_stride,
-                                             a.y + (size_t)s * a.sys_stride, blockIdx.x, s);
+    T dacc;
+    if constexpr (XFF)
+      dacc = sipg3l_group<T, N, TS, V, EP, ff>(g, a, reinterpret_cast<const ff*>(a.xff) + (size_t)s * a.sys_stride,
+                                               a.y + (size_t)s * a.sys_stride, blockIdx.x, s);
+    else
+      dacc = sipg3l_group<T, N, TS, V, EP>(g, a, a.x + (size_t)s * a.sys_stride, a.y + (size_t)s * a.sys_stride,
+                                           blockIdx.x, s);
     if (a.dot_out) {
       const double bs = block_sum_any_t<T>(dacc, red);
       if (threadIdx.x == 0) put_dot_partial(a, s, bs);

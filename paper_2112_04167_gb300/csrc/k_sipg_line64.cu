@@ -19,24 +19,44 @@ int sipg_apply_line(const Geom& g, int N, const SipgArgs<double>& a, cudaStream_
   return sipg_apply_line_t<double>(g, N, a, st);
 }
 
-template <int N>
+template <int N, bool XFF>
 static void launch_apply_ff(const Geom& g, const SipgArgs<double>& a, cudaStream_t st) {
   using P = Sipg3pShape<ff, N>;
   constexpr size_t sm = sipg3l_smem<ff, N>();
-  smem_limit_once((const void*)sipg3p_apply_kernel<ff, N, double>, (int)sm);
-  IMEX_COUNTED(sipg3p_apply_kernel<ff, N, double><<<(g.ne + P::EPB - 1) / P::EPB, P::THREADS, sm, st>>>(g, a));
+  smem_limit_once((const void*)sipg3p_apply_kernel<ff, N, double, 0, SIPG_EP_ANY, XFF>, (int)sm);
+  IMEX_COUNTED((sipg3p_apply_kernel<ff, N, double, 0, SIPG_EP_ANY, XFF>
+                <<<(g.ne + P::EPB - 1) / P::EPB, P::THREADS, sm, st>>>(g, a)));
 }
 
-int sipg_apply_ff(const Geom& g, int N, const SipgArgs<double>& a, cudaStream_t st) {
-  if (g.d != 3 || g.bc[0] || g.bc[1] || g.bc[2] || a.nu || !a.ops || a.gdata) return -1;
+namespace {
+// x -> float-float pairs (the split of every value, by integer operations)
+__global__ void __launch_bounds__(256) to_ff_kernel(const double* __restrict__ x, ff* __restrict__ y, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    y[i] = ff(x[i]);
+}
+}  // namespace
+
+int sipg_apply_ff(const Geom& g, int N, const SipgArgs<double>& a, void* scratch, cudaStream_t st) {
+  if (g.d != 3 || g.bc[0] || g.bc[1] || g.bc[2] || a.nu || !a.ops || a.gdata || N < 3 || N > 9) return -1;
+  SipgArgs<double> aa = a;
+  const bool pre = scratch != nullptr;
+  if (pre) {
+    // the input converted once, so that the apply's loads (each value about seven times:
+    // own line and six neighbour lines) take no conversion
+    const size_t n = (size_t)a.nsys * (size_t)a.sys_stride;
+    const size_t b = (n + 255) / 256;
+    IMEX_COUNTED((to_ff_kernel<<<(int)(b < (size_t)152 * 16 ? b : (size_t)152 * 16), 256, 0, st>>>(
+        a.x, reinterpret_cast<ff*>(scratch), n)));
+    aa.xff = scratch;
+  }
   switch (N) {
-    case 3: launch_apply_ff<3>(g, a, st); return 0;
-    case 4: launch_apply_ff<4>(g, a, st); return 0;
-    case 5: launch_apply_ff<5>(g, a, st); return 0;
-    case 6: launch_apply_ff<6>(g, a, st); return 0;
-    case 7: launch_apply_ff<7>(g, a, st); return 0;
-    case 8: launch_apply_ff<8>(g, a, st); return 0;
-    case 9: launch_apply_ff<9>(g, a, st); return 0;
+#define IMEX_FFN(NN)                                                            \
+    case NN:                                                                   \
+      if (pre) launch_apply_ff<NN, true>(g, aa, st);                           \
+      else launch_apply_ff<NN, false>(g, aa, st);                              \
+      return 0;
+    IMEX_FFN(3) IMEX_FFN(4) IMEX_FFN(5) IMEX_FFN(6) IMEX_FFN(7) IMEX_FFN(8) IMEX_FFN(9)
+#undef IMEX_FFN
     default: return -1;
   }
 }

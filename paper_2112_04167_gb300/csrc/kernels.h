@@ -65,6 +65,8 @@ struct SipgArgs {
   const T* ch_dinv;
   const T* ch_b;
   T ch_c1, ch_c2;
+  // float-float applies: the input x converted to float-float pairs (sipg_apply_ff)
+  const void* xff;
 };
 
 template <typename T>
@@ -79,7 +81,9 @@ __device__ __forceinline__ T sipg_beta(const SipgArgs<T>& a, const Geom& gl) {
 template <typename T> int sipg_apply(const Geom& g, int N, const SipgArgs<T>& a, cudaStream_t st);
 // the periodic 3D constant-viscosity apply on FP64 fields with float-float arithmetic (about
 // 48 significant bits on the FP32 pipes); -1 for any other case (nothing launched)
-int sipg_apply_ff(const Geom& g, int N, const SipgArgs<double>& a, cudaStream_t st);
+// scratch: room for nsys * sys_stride float-float pairs (8 bytes each) to hold the input
+// converted beforehand, or nullptr (the kernel converts as it loads)
+int sipg_apply_ff(const Geom& g, int N, const SipgArgs<double>& a, void* scratch, cudaStream_t st);
 // constant-memory line operators of the periodic fast path (once per device)
 void init_const_lines(const Tables<double>& t);
 template <typename T> int sipg_diag(const Geom& g, int N, const SipgArgs<T>& a, cudaStream_t st);
