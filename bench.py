@@ -47,6 +47,9 @@ def parse():
     ap.add_argument("--pmg", default="", help="V-cycle parameters: smoothing steps, coarsest-level steps, "
                     "smoothing range, coarsest range (comma-separated; empty: library defaults)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--tc-experiment", action="store_true",
+                    help="time one convection contraction pass as a cuBLAS GEMM (FP32, TF32, BF16) against "
+                         "the fused convection kernel, print one JSON line and exit")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra-configs", action="store_true",
                     help="skip the SDC / BDF2 lines, the 2D Taylor-Green run and the Dirichlet dt sweep")
@@ -127,6 +130,58 @@ def roofline_of(rows, hbm, src, traffic=None):
                                      "(FP64-equivalent flops)"}.get(r["arith"], "nominal FP64 1.25 TFLOP/s")}
     out.update({"traffic": traffic, "bytes_per_launch": r["bytes_per_launch"], "avg_launch_us": r["avg_us"],
                 "arith": r["arith"], "share_of_profiled_ms": r["total_ms"] / sum(x["total_ms"] for x in rows.values())})
+    return out
+
+
+def tensor_core_experiment(imex, torch, nelem=16, P=7, reps=20):
+    """The convection's first Gauss-point interpolation pass (x direction, every line of every
+    element and component: C (L x Q) = V (L x N) IG^T, L = d N^(d-1) elements) as one cuBLAS
+    GEMM -- FP32 on the CUDA cores, TF32 and BF16 on the tensor cores -- against the fused
+    convection kernel (FP32 and float-float) on the same 3D periodic nelem^3 mesh at degree P.
+    The fused kernel performs 36 such contraction passes per element (3 interpolations to
+    the Gauss points per component, 3 passes back per component pair) plus the pointwise
+    fluxes and the face terms, keeping every intermediate in shared memory; a GEMM
+    formulation moves each pass's operands through L2 / HBM."""
+    N = P + 1
+    Q = (3 * N + 1) // 2
+    ctx = imex.Context(3, P, (nelem,) * 3, [0, 0, 0], [TWO_PI] * 3, (1, 1, 1), precision=imex.MIXED_FAST)
+    dev = torch.device("cuda")
+    g = torch.Generator(device=dev).manual_seed(0)
+    v = torch.randn(3 * ctx.nvel, dtype=torch.float64, device=dev, generator=g)
+    out = {"mesh": "3D periodic %d^3, P=%d (N=%d, Q=%d)" % (nelem, P, N, Q)}
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) * 1e3 / reps
+
+    for name, arith in (("fused_conv_fp32_us", imex.ARITH_FP32), ("fused_conv_ff_us", imex.ARITH_FF)):
+        out[name] = round(timed(lambda: ctx.op_conv(v, arith=arith)), 2)
+    L = v.numel() // N
+    ig = torch.randn(Q, N, device=dev, generator=g, dtype=torch.float32)
+    vf = v.to(torch.float32).view(L, N)
+    old = torch.backends.cuda.matmul.allow_tf32
+    try:
+        torch.backends.cuda.matmul.allow_tf32 = False
+        out["gemm_pass_fp32_us"] = round(timed(lambda: torch.matmul(vf, ig.t())), 2)
+        torch.backends.cuda.matmul.allow_tf32 = True
+        out["gemm_pass_tf32_us"] = round(timed(lambda: torch.matmul(vf, ig.t())), 2)
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = old
+    vb, igb = vf.to(torch.bfloat16), ig.to(torch.bfloat16)
+    out["gemm_pass_bf16_us"] = round(timed(lambda: torch.matmul(vb, igb.t())), 2)
+    out["gemm_pass_bytes"] = int(L * (N + Q) * 4)
+    out["passes_per_convection"] = 36
+    best = min(out["gemm_pass_tf32_us"], out["gemm_pass_bf16_us"])
+    out["gemm_lower_bound_us"] = round(36 * best, 1)
     return out
 
 
@@ -684,6 +739,10 @@ def main():
                           "ensemble": e, "tuning": imex.tuning_info()}))
         return 0
 
+    if args.tc_experiment:
+        e = tensor_core_experiment(imex, torch, args.nelem, args.P)
+        print(json.dumps({"tensor_core_experiment": e}))
+        return 0
     if args.workload == "ops":
         e = run_operators(imex, torch, args.ops_nelem or 40, args.P)
         print(json.dumps({"metric": METRIC, "value": None, "unit": UNIT, "n_gpus": world, "steps": 0,

@@ -179,11 +179,24 @@ struct Sipg3lShape {
   static constexpr int TILE = N * N * NP;
 };
 
-template <typename T, int N, int V = 0>
+// vectors of the output stage EP copied into shared memory ahead of it (Chebyshev step: r,
+// D^{-1}, s; first step: b, D^{-1}), FP32 only
+template <typename T, int EP>
+__host__ __device__ constexpr int sipg3l_staged() {
+  return sizeof(T) != 4 ? 0 : (EP == SIPG_EP_CHEB ? 3 : (EP == SIPG_EP_CHEB_FIRST ? 2 : 0));
+}
+template <typename T, int N, int V = 0, int EP = SIPG_EP_ANY>
 constexpr size_t sipg3l_smem() {
   using S = Sipg3lShape<T, N, V>;
-  return sizeof(T) * (size_t)(S::EPB * S::TILE + S::EPB * S::ND);
+  return sizeof(T) * (size_t)(S::EPB * S::TILE + S::EPB * S::ND * (1 + sipg3l_staged<T, EP>()));
 }
+
+// 4-byte asynchronous copy global -> shared (no register holds the value in flight)
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 // what a line's face terms need of the two neighbour lines along its direction: the
 // neighbours' traces at the shared faces and their normal derivatives there (unit size)
@@ -208,6 +221,7 @@ __device__ __forceinline__ T sipg3l_group(const Geom& g, const SipgArgs<TS>& a, 
                                           TS* __restrict__ y, int grp, int sys = 0) {
   using S = Sipg3lShape<T, N, V>;
   constexpr int NN = S::NN, ND = S::ND, EPB = S::EPB, NP = S::NP, TILE = S::TILE, VEC = S::VEC;
+  constexpr int NSTG = sipg3l_staged<T, EP>();
   // FP32 up to N = 8: all neighbour lines are loaded before the first pass, so that their
   // latency is paid once rather than after each of the two barriers (12 scalars stay live);
   // the wider types and N = 9 load them pass by pass (register pressure)
@@ -220,6 +234,7 @@ __device__ __forceinline__ T sipg3l_group(const Geom& g, const SipgArgs<TS>& a, 
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* tile = reinterpret_cast<T*>(smem_raw);                       // [EPB][z][y][NP]
   T* acc = tile + EPB * TILE;                                     // [EPB][z][y][x]
+  T* stg = acc + EPB * ND;                                        // [NSTG][EPB][z][y][x]
   const ConstLine<T>& L = cline<T>(N);
   const int le = threadIdx.x / NN;
   const int t = threadIdx.x - le * NN;
@@ -279,6 +294,15 @@ __device__ __forceinline__ T sipg3l_group(const Geom& g, const SipgArgs<TS>& a, 
     }
 #pragma unroll
     for (int k = 0; k < N; ++k) mt[(k * N + tb) * NP + ta] = u[k];
+    // the output stage's vectors at the thread's z-column, copied into shared memory while
+    // the three passes run
+    if constexpr (NSTG > 0) {
+      const TS* src[3] = {EP == SIPG_EP_CHEB ? a.ch_r : a.ch_b, a.ch_dinv, a.ch_s};
+#pragma unroll
+      for (int v = 0; v < NSTG; ++v)
+#pragma unroll
+        for (int k = 0; k < N; ++k) cp_async4(stg + (v * EPB + le) * ND + k * NN + t, src[v] + eb + k * NN + t);
+    }
   }
   // pass z: line (x = ta, y = tb) along z
   if (live) {
@@ -344,13 +368,33 @@ __device__ __forceinline__ T sipg3l_group(const Geom& g, const SipgArgs<TS>& a, 
   if constexpr (COAL) {
     // the fixed output stages by z-columns (x = ta, y = tb): a warp's accesses to y and to
     // the Chebyshev vectors are contiguous, where the x-lines of the pass are 4N bytes apart
+    if constexpr (NSTG > 0) cp_async_wait_all();
     __syncthreads();
     if (live) {
+      const T* s0 = stg + le * ND;                                // r (or b), D^{-1}, s
+      const T* s1 = s0 + EPB * ND;
+      const T* s2 = s1 + EPB * ND;
 #pragma unroll
       for (int k = 0; k < N; ++k) {
         const int node = k * NN + t;
+        const size_t i = eb + node;
         const T xin = mt[(k * N + tb) * NP + ta];
-        const T out = sipg_out_ep<EP, T, TS>(a, y, eb + node, xin, ma[node], T(1));
+        const T out = ma[node];
+        if constexpr (NSTG > 0 && EP == SIPG_EP_CHEB) {
+          const T r = s0[node] - out;
+          const T dn = T(a.ch_c1) * xin + T(a.ch_c2) * s1[node] * r;
+          a.ch_s[i] = (TS)(s2[node] + (a.ch_addx ? xin + dn : dn));
+          if (!a.ch_last) {
+            a.ch_r[i] = (TS)r;
+            a.ch_dout[i] = (TS)dn;
+          }
+        } else if constexpr (NSTG > 0 && EP == SIPG_EP_CHEB_FIRST) {
+          const T r = s0[node] - out;
+          a.ch_r[i] = (TS)r;
+          a.ch_dout[i] = (TS)(T(a.ch_c1) * s1[node] * r);
+        } else {
+          sipg_out_ep<EP, T, TS>(a, y, i, xin, out, T(1));
+        }
         dacc += xin * out;
       }
     }
@@ -657,7 +701,7 @@ static void launch_apply2l(const Geom& g, const SipgArgs<T>& a, cudaStream_t st)
 template <typename T, int N, int V, int EP>
 static void launch_apply3p_ep(const Geom& g, const SipgArgs<T>& a, cudaStream_t st) {
   using P = Sipg3pShape<T, N, V>;
-  constexpr size_t sm = sipg3l_smem<T, N, V>();
+  constexpr size_t sm = sipg3l_smem<T, N, V, EP>();
   smem_limit_once((const void*)sipg3p_apply_kernel<T, N, T, V, EP>, (int)sm);
   launch_cg_kernel(sipg3p_apply_kernel<T, N, T, V, EP>, (g.ne + P::EPB - 1) / P::EPB, P::THREADS, sm, st, g, a);
 }
