@@ -673,7 +673,8 @@ void cg_pz(imex_ctx* c, T* p, const T* z, const imex_ctx::Seg& sg, const CgScala
 
 // z = one p-multigrid V-cycle applied to r (defined with the p-multigrid code below)
 template <typename T>
-imex_status pmg_vcycle(imex_ctx* c, const T* r, T* z, const double* lm);
+imex_status pmg_vcycle(imex_ctx* c, const T* r, T* z, const double* lm, T* rproj = nullptr,
+                       const T* rmean = nullptr, const int* rdone = nullptr);
 
 // ---- PCG -------------------------------------------------------------------------
 // per-system CG scalars: cg_d holds rz, rz_old, rr, bb, pAp, zmean, a mean scratch, the true
@@ -921,6 +922,8 @@ imex_status pcg_mixed(imex_ctx* c, const imex_ctx::Seg& sg, Op64 op64, Op32 op32
   // not see this floor; the achieved residual is reported in the statistics)
   std::vector<double> best_true(nsys, 0.0);
   std::vector<int> inner_conv(nsys, 0), stall(nsys, 0);
+  std::vector<long long> its_ref(nsys, 0);        // iterations at the last replacement
+  const long long cycle_cap = pm ? 64 : 2000;
   bool started = false, restart = true;
   int breakdowns = 0;
   auto replace = [&]() -> imex_status {
@@ -956,6 +959,7 @@ imex_status pcg_mixed(imex_ctx* c, const imex_ctx::Seg& sg, Op64 op64, Op32 op32
         inner_conv[s] = 0;
       }
       if (best_true[s] == 0.0 || rt[s] < best_true[s]) best_true[s] = rt[s];
+      its_ref[s] = started ? c->cg_hi[m + s] : 0;
       if (rt[s] <= tol * tol * bbh[s] || stall[s] >= 3) {
         done_h[s] = 4;
       } else {
@@ -1000,8 +1004,11 @@ imex_status pcg_mixed(imex_ctx* c, const imex_ctx::Seg& sg, Op64 op64, Op32 op32
       }
       cg_step<float>(c, y, r, p, Ap, dj, sg, sc, maxit);
       if (pm) {
-        if (project) cg_rproj<float>(c, r, sg, sc);
-        TRY(pmg_vcycle<float>(c, r, z, c->pmg.lmax));
+        // one projected segment: the mean comes off r in the V-cycle's first kernel
+        const bool fuse = project && t.nseg == 1 && c->pmg.nlev > 1;
+        if (project && !fuse) cg_rproj<float>(c, r, sg, sc);
+        if (fuse) TRY(pmg_vcycle<float>(c, r, z, c->pmg.lmax, r, sc.rmean_f, sc.done));
+        else TRY(pmg_vcycle<float>(c, r, z, c->pmg.lmax));
         cg_rz<float>(c, r, z, sg, sc, 0);
         cg_pz<float>(c, p, z, sg, sc, 0);
       } else {
@@ -1042,9 +1049,26 @@ imex_status pcg_mixed(imex_ctx* c, const imex_ctx::Seg& sg, Op64 op64, Op32 op32
         need = true;
         restart = true;
       }
-      if (st == 3) return fail(c, IMEX_ENOTCONV, "CG did not converge within maxit");
+      if (st == 3) {
+        char msg[256];
+        std::snprintf(msg, sizeof msg,
+                      "CG did not converge within maxit (system %d of %d, %lld iterations, recursive residual "
+                      "%.3e, last true residual %.3e, |b| %.3e)",
+                      s, nsys, (long long)c->cg_hi[m + s], std::sqrt(c->cg_hd[2 * m + s]),
+                      std::sqrt(c->cg_hd[7 * m + s]), std::sqrt(c->cg_hd[3 * m + s]));
+        return fail(c, IMEX_ENOTCONV, msg);
+      }
       if (st == 1) { need = true; restart = true; inner_conv[s] = 1; }  // recursive residual converged
       if (st == 0 && c->cg_hd[2 * m + s] < delta * delta * rr_ref[s]) need = true;
+      // a cycle that has not reached its target after cycle_cap iterations (a V-cycle gains
+      // about a decade per iteration, Jacobi a healthy two decades in a few hundred) has met
+      // the FP32 floor of this system: replace, counted as an inner convergence for the
+      // stagnation rule of the true residual
+      if (st == 0 && c->cg_hi[m + s] - its_ref[s] > cycle_cap) {
+        need = true;
+        restart = true;
+        inner_conv[s] = 1;
+      }
       done_h[s] = st;
     }
     if (need) TRY(replace());
@@ -1249,7 +1273,8 @@ imex_status pmg_setup(imex_ctx* c) {
 // that produced b (PMG_PRESET: r = b, d = x = D^{-1} b / theta)
 enum { PMG_FROM_ZERO = 0, PMG_FROM_X = 1, PMG_PRESET = 2 };
 template <typename T>
-imex_status pmg_smooth(imex_ctx* c, int l, int steps, double lmax, double ratio, int start, const T* b, T* x) {
+imex_status pmg_smooth(imex_ctx* c, int l, int steps, double lmax, double ratio, int start, const T* b, T* x,
+                       T* bproj = nullptr, const T* bmean = nullptr, const int* bdone = nullptr) {
   imex_ctx::Pmg& M = c->pmg;
   using V = PmgVecs<T>;
   const size_t n = (size_t)c->gp.ne * ipow(M.N[l], c->d);
@@ -1279,6 +1304,11 @@ imex_status pmg_smooth(imex_ctx* c, int l, int steps, double lmax, double ratio,
     prof_end(c, cls, 5.0 * sizeof(T) * n, apply_flops + 3.0 * n, arith_t<T>());
     TRY(launch_check(c, rc, "sipg_apply(chebyshev first)"));
     addx = true;
+  } else if (start == PMG_FROM_ZERO && bproj) {
+    // from zero for a projected CG residual: its mean taken off here (and written back)
+    prof_mark(c, IMEX_PROF_PMG_VEC, true);
+    cheb_first_proj<T>(x, dv, r, bproj, dinv, 1.0 / theta, bmean, bdone, n, c->st);
+    prof_end(c, IMEX_PROF_PMG_VEC, 6.0 * sizeof(T) * n, 3.0 * n, arith_t<T>());
   } else if (start != PMG_PRESET) {
     const bool from_x = start == PMG_FROM_X;
     if (from_x) TRY(pmg_apply<T>(c, l, x, ad));
@@ -1316,9 +1346,12 @@ imex_status pmg_smooth(imex_ctx* c, int l, int steps, double lmax, double ratio,
   return IMEX_OK;
 }
 
-// z = one V-cycle applied to r (level 0); lm: the Chebyshev upper bounds of the levels
+// z = one V-cycle applied to r (level 0); lm: the Chebyshev upper bounds of the levels;
+// rproj (== r, one-segment projected CG systems): the mean *rmean is taken off r in the
+// first kernel and the projected r written back, unless *rdone
 template <typename T>
-imex_status pmg_vcycle(imex_ctx* c, const T* r, T* z, const double* lm) {
+imex_status pmg_vcycle(imex_ctx* c, const T* r, T* z, const double* lm, T* rproj, const T* rmean,
+                       const int* rdone) {
   imex_ctx::Pmg& M = c->pmg;
   using V = PmgVecs<T>;
   const int L = M.nlev;
@@ -1338,7 +1371,8 @@ imex_status pmg_vcycle(imex_ctx* c, const T* r, T* z, const double* lm) {
   // the coarsest level on one cluster (FP32): its restriction then writes b only
   const bool clus = sizeof(T) == 4 && M.cluster && L >= 2;
   for (int l = 0; l + 1 < L; ++l) {
-    TRY(pmg_smooth<T>(c, l, M.pre, lm[l], M.ratio, l == 0 ? PMG_FROM_ZERO : PMG_PRESET, b[l], x[l]));
+    if (l == 0) TRY(pmg_smooth<T>(c, l, M.pre, lm[l], M.ratio, PMG_FROM_ZERO, b[l], x[l], rproj, rmean, rdone));
+    else TRY(pmg_smooth<T>(c, l, M.pre, lm[l], M.ratio, PMG_PRESET, b[l], x[l]));
     TRY(pmg_apply<T>(c, l, x[l], V::ad(M)[l]));
     // restriction of the residual, with the first smoothing step (from zero) of level l + 1
     const bool first = !(clus && l + 2 == L);

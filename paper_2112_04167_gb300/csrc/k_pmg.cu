@@ -147,6 +147,25 @@ cheb_first_kernel(T* __restrict__ x, T* __restrict__ d, T* __restrict__ r, const
   }
 }
 
+// the same from zero for the residual of a singular (projected) one-segment CG system: the
+// segment mean is taken off r first and the projected r written back (the CG keeps it)
+template <typename T>
+__global__ void __launch_bounds__(256)
+cheb_first_proj_kernel(T* __restrict__ x, T* __restrict__ d, T* __restrict__ r, T* __restrict__ b,
+                       const T* __restrict__ dinv, T c0, const T* __restrict__ mean, const int* __restrict__ done,
+                       size_t n) {
+  const bool proj = *done == 0;
+  const T m = proj ? *mean : T(0);
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const T bi = b[i] - m;
+    if (proj) b[i] = bi;
+    const T di = c0 * dinv[i] * bi;
+    r[i] = bi;
+    d[i] = di;
+    x[i] = di;
+  }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256)
 cheb_next_kernel(T* __restrict__ x, T* __restrict__ d, T* __restrict__ r, const T* __restrict__ ad,
@@ -200,6 +219,11 @@ void cheb_first(T* x, T* dv, T* r, const T* b, const T* ax, const T* dinv, doubl
   IMEX_COUNTED(cheb_first_kernel<T><<<grid_for(n), 256, 0, st>>>(x, dv, r, b, ax, dinv, (T)c0, n, add));
 }
 template <typename T>
+void cheb_first_proj(T* x, T* dv, T* r, T* b, const T* dinv, double c0, const T* mean, const int* done, size_t n,
+                     cudaStream_t st) {
+  IMEX_COUNTED(cheb_first_proj_kernel<T><<<grid_for(n), 256, 0, st>>>(x, dv, r, b, dinv, (T)c0, mean, done, n));
+}
+template <typename T>
 void cheb_next(T* x, T* dv, T* r, const T* ad, const T* dinv, double c1, double c2, size_t n, int last,
                cudaStream_t st) {
   IMEX_COUNTED(cheb_next_kernel<T><<<grid_for(n), 256, 0, st>>>(x, dv, r, ad, dinv, (T)c1, (T)c2, n, last));
@@ -219,6 +243,10 @@ template int pmg_restrict_cheb<float>(int, int, int, int, const float*, const fl
                                       const ChebInit<float>&, cudaStream_t);
 template int pmg_restrict_cheb<double>(int, int, int, int, const double*, const double*, double*, const Interp1D&,
                                        const ChebInit<double>&, cudaStream_t);
+template void cheb_first_proj<float>(float*, float*, float*, float*, const float*, double, const float*, const int*,
+                                     size_t, cudaStream_t);
+template void cheb_first_proj<double>(double*, double*, double*, double*, const double*, double, const double*,
+                                      const int*, size_t, cudaStream_t);
 template void cheb_first<float>(float*, float*, float*, const float*, const float*, const float*, double, size_t, int,
                                 cudaStream_t);
 template void cheb_first<double>(double*, double*, double*, const double*, const double*, const double*, double,

@@ -229,6 +229,11 @@ int pmg_restrict_cheb(int d, int ne, int NF, int NC, const T* bf, const T* axf, 
 template <typename T>
 void cheb_first(T* x, T* d, T* r, const T* b, const T* ax, const T* dinv, double c0, size_t n, int add,
                 cudaStream_t st);
+// the first step from zero for a projected one-segment CG residual b (its mean *mean taken
+// off and the projected b written back unless *done)
+template <typename T>
+void cheb_first_proj(T* x, T* d, T* r, T* b, const T* dinv, double c0, const T* mean, const int* done, size_t n,
+                     cudaStream_t st);
 template <typename T>
 void cheb_next(T* x, T* d, T* r, const T* ad, const T* dinv, double c1, double c2, size_t n, int last,
                cudaStream_t st);

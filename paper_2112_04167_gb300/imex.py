@@ -646,6 +646,10 @@ class Server:
         self._sizes[i.value] = dim * ne * (P + 1) ** dim
         return i.value
 
+    def last_error(self):
+        """The server's last error message (a failed group step names its group)."""
+        return load().imex_server_last_error(self._h).decode()
+
     def tick(self):
         a = C.c_int()
         self._check(load().imex_server_tick(self._h, C.byref(a)))
