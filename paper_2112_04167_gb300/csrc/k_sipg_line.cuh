@@ -41,9 +41,12 @@ struct Sipg2lShape {
   static constexpr int NP = ((N + VEC - 1) / VEC) * VEC;
 };
 
-template <typename T, int N, int V = 0>
+// EP: the output stage, fixed at compile time for the FP32 applies (as in 3D), which then
+// write the x pass's results into the accumulator tile and run the stage by columns
+template <typename T, int N, int V = 0, int EP = SIPG_EP_ANY>
 __global__ void __launch_bounds__(Sipg2lShape<T, N, V>::THREADS)
 sipg2l_apply_kernel(Geom g, SipgArgs<T> a) {
+  constexpr bool COAL = EP != SIPG_EP_ANY;
   using S = Sipg2lShape<T, N, V>;
   constexpr int NN = S::NN, EPB = S::EPB, NP = S::NP, VEC = S::VEC;
   __shared__ __align__(16) T tile[EPB][N][NP];
@@ -68,6 +71,9 @@ sipg2l_apply_kernel(Geom g, SipgArgs<T> a) {
   const T ihx = T(1) / hx, ihy = T(1) / hy;
   const T scale = sipg_beta(a, gl) * sipg_nu0(a, gl);
   const int nvalid = min(EPB, g.ne - e0);
+  // the GLL weight at the thread's line coordinate, from the global tables (the constant
+  // cache would serialise the warp's distinct addresses)
+  const T wta = tab<T>(g).w[N][ta];
   for (int s = 0; s < a.nsys; ++s) {
     const T* x = a.x + (size_t)s * a.sys_stride;
     T* y = a.y + (size_t)s * a.sys_stride;
@@ -97,7 +103,7 @@ sipg2l_apply_kernel(Geom g, SipgArgs<T> a) {
 #pragma unroll
       for (int j = 0; j < N; ++j) { dl += L.dnL[j] * vl[j]; dr += L.dnR[j] * vr[j]; }
       const T tl = vl[N - 1], tr = vr[0];
-      const T wt = (T(0.5) * hx * L.w[ta]) * ihy;
+      const T wt = (T(0.5) * hx * wta) * ihy;
 #pragma unroll
       for (int o = 0; o < N; ++o) {
         T so = L.ctrL[o] * tl + L.cdnL[o] * dl + L.ctrR[o] * tr + L.cdnR[o] * dr;
@@ -128,7 +134,7 @@ sipg2l_apply_kernel(Geom g, SipgArgs<T> a) {
 #pragma unroll
       for (int j = 0; j < N; ++j) { dl += L.dnL[j] * vl[j]; dr += L.dnR[j] * vr[j]; }
       const T tl = vl[N - 1], tr = vr[0];
-      const T wy = T(0.5) * hy * L.w[ta];
+      const T wy = T(0.5) * hy * wta;
       const T wt = wy * ihx;
 #pragma unroll
       for (int o = 0; o < N; ++o) {
@@ -136,10 +142,27 @@ sipg2l_apply_kernel(Geom g, SipgArgs<T> a) {
 #pragma unroll
         for (int j = 0; j < N; ++j) so += L.A[o * N + j] * v[j];
         const T W = wy * (T(0.5) * hx * L.w[o]);
-        T out = a.alpha * W * v[o] + scale * (acc[le][ta * N + o] + wt * so);
-        if (a.minv) out /= W;
-        sipg_out<T, T>(a, y, (size_t)e * NN + ta * N + o, v[o], out);
-        dacc += v[o] * out;
+        const T res = a.alpha * W * v[o] + scale * (acc[le][ta * N + o] + wt * so);
+        if constexpr (COAL) {
+          acc[le][ta * N + o] = res;            // own row: staged for the column-ordered stage
+        } else {
+          T out = res;
+          if (a.minv) out /= W;
+          sipg_out<T, T>(a, y, (size_t)e * NN + ta * N + o, v[o], out);
+          dacc += v[o] * out;
+        }
+      }
+    }
+    if constexpr (COAL) {
+      // the output stage by columns (x = ta): a warp's accesses are contiguous
+      __syncthreads();
+      if (live) {
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+          const T xin = tile[le][j][ta];
+          const T out = sipg_out_ep<EP, T, T>(a, y, (size_t)e * NN + j * N + ta, xin, acc[le][j * N + ta], T(1));
+          dacc += xin * out;
+        }
       }
     }
     if (a.dot_out) {
@@ -692,10 +715,25 @@ static int launch_persist(const Geom& g, const SipgArgs<float>& a, const PcgPers
   return 0;
 }
 
+template <typename T, int N, int V, int EP>
+static void launch_apply2l_ep(const Geom& g, const SipgArgs<T>& a, cudaStream_t st) {
+  using C = Sipg2lShape<T, N, V>;
+  IMEX_COUNTED((sipg2l_apply_kernel<T, N, V, EP><<<(g.ne + C::EPB - 1) / C::EPB, C::THREADS, 0, st>>>(g, a)));
+}
+// FP32: the output stage fixed at compile time unless M^{-1} is asked for
 template <typename T, int N, int V>
 static void launch_apply2l(const Geom& g, const SipgArgs<T>& a, cudaStream_t st) {
-  using C = Sipg2lShape<T, N, V>;
-  IMEX_COUNTED((sipg2l_apply_kernel<T, N, V><<<(g.ne + C::EPB - 1) / C::EPB, C::THREADS, 0, st>>>(g, a)));
+  if constexpr (sizeof(T) == 4) {
+    if (!a.minv) {
+      if (a.cheb == 2) launch_apply2l_ep<T, N, V, SIPG_EP_CHEB_FIRST>(g, a, st);
+      else if (a.cheb) launch_apply2l_ep<T, N, V, SIPG_EP_CHEB>(g, a, st);
+      else launch_apply2l_ep<T, N, V, SIPG_EP_PLAIN>(g, a, st);
+    } else {
+      launch_apply2l_ep<T, N, 0, SIPG_EP_ANY>(g, a, st);
+    }
+  } else {
+    launch_apply2l_ep<T, N, V, SIPG_EP_ANY>(g, a, st);
+  }
 }
 
 template <typename T, int N, int V, int EP>
