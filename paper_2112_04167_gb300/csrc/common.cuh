@@ -54,6 +54,9 @@ struct Geom {
   float inu0f;
   double idt;            // the instance's time step
   float idtf;
+  // element neighbours across the 2d faces ([element][2d], face 2k + side, side 1 the upper
+  // one; -1 on a domain boundary), built on the host for the context's layout, or nullptr
+  const int* nbr = nullptr;
 };
 
 // per-direction geometry by selects rather than array indexing, so that a Geom held by a

@@ -243,6 +243,7 @@ struct imex_ctx {
   std::vector<InstGeom> inst;
   InstGeom* inst_d = nullptr;
   int* elem_inst_d = nullptr;
+  int* nbr_d = nullptr;       // element neighbour table of the layout (Geom::nbr)
   double* edt = nullptr;        // per-element time step (batched)
   // CUDA graphs of CG iteration chunks, keyed by everything their launches depend on
   struct GraphEntry {
@@ -2236,6 +2237,34 @@ imex_status set_layout(imex_ctx* c) {
       for (int e = 0; e < c->inst[i].ne; ++e) ei[c->inst[i].e0 + e] = i;
     CK(cudaMemcpy(c->inst_d, c->inst.data(), ni * sizeof(InstGeom), cudaMemcpyHostToDevice), "cp inst");
     CK(cudaMemcpy(c->elem_inst_d, ei.data(), ei.size() * sizeof(int), cudaMemcpyHostToDevice), "cp inst");
+  }
+  // element neighbours across the faces, for the kernels that would otherwise recompute
+  // them per thread (index arithmetic with run-time divisions)
+  {
+    std::vector<int> nb((size_t)ne * 2 * d);
+    for (int i = 0; i < ni; ++i) {
+      const InstGeom& I = c->inst[i];
+      for (int el = 0; el < I.ne; ++el) {
+        const int ec[3] = {el % I.n[0], (el / I.n[0]) % I.n[1], el / (I.n[0] * I.n[1])};
+        for (int k = 0; k < d; ++k)
+          for (int side = 0; side < 2; ++side) {
+            int cc[3] = {ec[0], ec[1], ec[2]};
+            int j = cc[k] + (side ? 1 : -1);
+            int v = -1;
+            if (j >= 0 && j < I.n[k]) {
+              cc[k] = j;
+              v = I.e0 + cc[0] + I.n[0] * (cc[1] + I.n[1] * cc[2]);
+            } else if (c->gv.bc[k] == 0) {
+              cc[k] = j < 0 ? j + I.n[k] : j - I.n[k];
+              v = I.e0 + cc[0] + I.n[0] * (cc[1] + I.n[1] * cc[2]);
+            }
+            nb[((size_t)(I.e0 + el) * d + k) * 2 + side] = v;
+          }
+      }
+    }
+    if (!c->nbr_d) TRY(dalloc(c, &c->nbr_d, (size_t)std::max<long long>(c->ne_cap, ne) * 2 * d));
+    CK(cudaMemcpy(c->nbr_d, nb.data(), nb.size() * sizeof(int), cudaMemcpyHostToDevice), "cp nbr");
+    c->gv.nbr = c->gp.nbr = c->nbr_d;
   }
   // CG systems: the pressure of each instance, and each velocity component of each
   // instance (component-major); the Jacobi diagonal of the velocity is shared by the

@@ -62,10 +62,15 @@ sipg2l_apply_kernel(Geom g, SipgArgs<T> a) {
   if (valid) gl = local_geom(g, e, el);
   int nb[4] = {0, 0, 0, 0};
   if (valid) {
-    int ec[3];
-    elem_coords(gl, el, ec);
+    if (g.nbr) {                                                  // the layout's table
+      const int4 q = reinterpret_cast<const int4*>(g.nbr)[e];
+      nb[0] = q.x; nb[1] = q.y; nb[2] = q.z; nb[3] = q.w;
+    } else {
+      int ec[3];
+      elem_coords(gl, el, ec);
 #pragma unroll
-    for (int f = 0; f < 4; ++f) nb[f] = neighbor(gl, ec, f >> 1, (f & 1) ? 1 : -1);
+      for (int f = 0; f < 4; ++f) nb[f] = neighbor(gl, ec, f >> 1, (f & 1) ? 1 : -1);
+    }
   }
   const T hx = geom_h<T>(gl, 0), hy = geom_h<T>(gl, 1);
   const T ihx = T(1) / hx, ihy = T(1) / hy;
@@ -268,10 +273,16 @@ __device__ __forceinline__ T sipg3l_group(const Geom& g, const SipgArgs<TS>& a, 
   if (valid) gl = local_geom(g, e, el);
   int nb[6] = {0, 0, 0, 0, 0, 0};
   if (valid) {
-    int ec[3];
-    elem_coords(gl, el, ec);
+    if (g.nbr) {                                                  // the layout's table
+      const int2* p = reinterpret_cast<const int2*>(g.nbr) + (size_t)e * 3;
+      const int2 a0 = p[0], a1 = p[1], a2 = p[2];
+      nb[0] = a0.x; nb[1] = a0.y; nb[2] = a1.x; nb[3] = a1.y; nb[4] = a2.x; nb[5] = a2.y;
+    } else {
+      int ec[3];
+      elem_coords(gl, el, ec);
 #pragma unroll
-    for (int f = 0; f < 6; ++f) nb[f] = neighbor(gl, ec, f >> 1, (f & 1) ? 1 : -1);
+      for (int f = 0; f < 6; ++f) nb[f] = neighbor(gl, ec, f >> 1, (f & 1) ? 1 : -1);
+    }
   }
   const T hx = geom_h<T>(gl, 0), hy = geom_h<T>(gl, 1), hz = geom_h<T>(gl, 2);
   const T ihx = T(1) / hx, ihy = T(1) / hy, ihz = T(1) / hz;
