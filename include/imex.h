@@ -204,7 +204,11 @@ imex_status imex_op_graddiv(imex_ctx* ctx, const double* v, const double* nu, do
    Chebyshev polynomial on the degree-1 level.  params (nparams <= 4, optional): smoothing
    steps (default 3), steps on the coarsest level (10), smoothing range lmax / lmin (10),
    coarsest range (100).  Default: IMEX_PRECOND_PMG.  The IMEX_POISSON_CONSISTENT operator
-   always uses Jacobi.
+   always uses Jacobi.  In the mixed forms the degree-1 level of a single 3D periodic mesh
+   runs all its steps in one launch on one thread-block cluster (up to about 15,000
+   elements); IMEX_PMG_CLUSTER=0 in the environment keeps one launch per step.  The mixed
+   forms replace the FP32 recursion's residual by the FP64 one every four decades with the
+   V-cycle, every two with Jacobi (IMEX_REFINE_DECADES=1..5 in the environment sets both).
    IMEX_EINVAL for an unknown kind or parameters out of range. */
 enum { IMEX_PRECOND_JACOBI = 0, IMEX_PRECOND_PMG = 1 };
 imex_status imex_set_pressure_precond(imex_ctx* ctx, int kind, const double* params, int nparams);
