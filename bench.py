@@ -644,7 +644,7 @@ def run_serving(imex, n_requests, precision="mixed", tol=1e-10):
     stream = serving_stream(n_requests)
     sv = imex.Server(budget_bytes=0.0, precision=imex.MIXED if precision == "mixed" else imex.FP64, tol=tol,
                      maxit=20000)
-    ids, arrive, finish = [], {}, {}
+    ids, arrive, start, finish, nsteps = [], {}, {}, {}, {}
     w0 = time.perf_counter()
     nxt = 0
     while True:
@@ -653,14 +653,21 @@ def run_serving(imex, n_requests, precision="mixed", tol=1e-10):
             i = sv.submit(**serving_request(imex, stream[nxt]))
             ids.append(i)
             arrive[i] = now
+            nsteps[i] = stream[nxt]["steps"]
             nxt += 1
         if nxt < len(stream) and sv.stats()["active"] == 0 and sv.stats()["queued"] == 0:
             time.sleep(max(0.0, stream[nxt]["arrival"] - now))
             continue
+        tick0 = now
         sv.tick()
         now = time.perf_counter() - w0
         for i in ids:
-            if i not in finish and sv.poll(i)[0] in (imex.REQ_DONE, imex.REQ_FAILED):
+            if i in finish:
+                continue
+            state, done, _ = sv.poll(i)
+            if i not in start and done > 0:
+                start[i] = tick0  # the tick that took the request's first step began here
+            if state in (imex.REQ_DONE, imex.REQ_FAILED):
                 finish[i] = now
         if nxt == len(stream) and len(finish) == len(stream):
             break
@@ -668,6 +675,13 @@ def run_serving(imex, n_requests, precision="mixed", tol=1e-10):
     st = sv.stats()
     err = sv.last_error() if st["failed"] else ""
     lat = sorted(finish[i] - arrive[i] for i in ids)
+    # a request's own step latency: from the start of the tick that took its first step to
+    # the end of the tick that took its last, over its steps (queueing excluded)
+    step_lat = sorted((finish[i] - start[i]) / nsteps[i] for i in ids if i in start)
+    wait = sorted(start[i] - arrive[i] for i in ids if i in start)
+
+    def pct(v, q):
+        return v[min(len(v) - 1, int(q * len(v)))] if v else None
     sv.close()
     return {"workload": f"first {n_requests} requests of the serving stream: Poisson arrivals at 50 req/s (seed 1), "
                         "d in {2,3}; 2D K~U{4..32}, P~U{3..8}, TG or MMS; 3D K~U{4..24}, P~U{3..7}, TG; "
@@ -678,9 +692,13 @@ def run_serving(imex, n_requests, precision="mixed", tol=1e-10):
             "value": st["dof_stages"] / wall, "unit": UNIT, "dof_stages": st["dof_stages"], "wall_s": wall,
             "busy_s": st["busy_s"], "p50_request_latency_s": lat[len(lat) // 2],
             "p99_request_latency_s": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+            "p50_request_step_ms": None if not step_lat else 1e3 * pct(step_lat, 0.5),
+            "p99_request_step_ms": None if not step_lat else 1e3 * pct(step_lat, 0.99),
+            "p50_queue_wait_s": pct(wait, 0.5),
             "max_footprint_gb": st["max_footprint_bytes"] / 1e9, "budget_gb": st["budget_bytes"] / 1e9,
             "precision": precision,
-            "timing": "host wall clock; a step (tick) = admission + repack + one step of every active request"}
+            "timing": "host wall clock; a step (tick) = admission + repack + one step of every active request; "
+                      "request step = (end of its last tick - start of its first tick) / its steps"}
 
 
 def reduce_max(dist, value, device):

@@ -1,0 +1,129 @@
+"""Host logic of bench.py's serving replay on CPU: the request stream follows its stated
+recipe (arrival order, ranges, time-step bounds), and the replay's latency figures are
+consistent when the server is a fake that takes one step of every admitted request per
+tick and admits at most two requests per tick."""
+import os
+import sys
+import time
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+import bench  # noqa: E402
+
+
+class FakeImex:
+    REQ_QUEUED, REQ_ACTIVE, REQ_DONE, REQ_FAILED = range(4)
+    MIXED, FP64 = 1, 0
+    FLOW_TG2D, FLOW_TG3D, FLOW_TGTRAVEL = 1, 2, 3
+    NU_CONST, NU_VARXYT = 0, 1
+    FORCE_TGTRAVEL_VARNU = 4
+
+    class Server:
+        TICK_S = 0.002
+
+        def __init__(self, budget_bytes, precision, tol, maxit):
+            self.reqs, self.order, self.ticks, self.tick_ms = {}, [], 0, []
+            self.dof_stages = 0.0
+
+        def submit(self, **req):
+            i = len(self.order)
+            self.reqs[i] = {"req": req, "state": FakeImex.REQ_QUEUED, "done": 0}
+            self.order.append(i)
+            return i
+
+        def tick(self):
+            t0 = time.perf_counter()
+            admitted = 0
+            for i in self.order:
+                r = self.reqs[i]
+                if r["state"] == FakeImex.REQ_QUEUED and admitted < 2:
+                    r["state"] = FakeImex.REQ_ACTIVE
+                    admitted += 1
+            active = 0
+            for i in self.order:
+                r = self.reqs[i]
+                if r["state"] != FakeImex.REQ_ACTIVE:
+                    continue
+                active += 1
+                r["done"] += 1
+                q = r["req"]
+                n = q["dim"] * (q["P"] + 1) ** q["dim"]
+                for k in q["nelem"]:
+                    n *= k
+                self.dof_stages += 3 * n
+                if r["done"] == q["nsteps"]:
+                    r["state"] = FakeImex.REQ_DONE
+            time.sleep(self.TICK_S)
+            self.ticks += 1
+            self.tick_ms.append(1e3 * (time.perf_counter() - t0))
+            return active
+
+        def poll(self, i):
+            r = self.reqs[i]
+            return r["state"], r["done"], 0.0
+
+        def stats(self):
+            st = [r["state"] for r in self.reqs.values()]
+            ms = sorted(self.tick_ms) or [0.0]
+            return {"active": st.count(FakeImex.REQ_ACTIVE), "queued": st.count(FakeImex.REQ_QUEUED),
+                    "completed": st.count(FakeImex.REQ_DONE), "failed": st.count(FakeImex.REQ_FAILED),
+                    "p50_tick_ms": ms[len(ms) // 2], "p99_tick_ms": ms[-1], "ticks": self.ticks,
+                    "dof_stages": self.dof_stages, "busy_s": 1e-3 * sum(self.tick_ms),
+                    "max_footprint_bytes": 0.0, "budget_bytes": 1e9}
+
+        def last_error(self):
+            return ""
+
+        def close(self):
+            pass
+
+
+def test_stream_recipe():
+    s = bench.serving_stream(400)
+    arr = [q["arrival"] for q in s]
+    assert all(b > a for a, b in zip(arr, arr[1:]))
+    # Poisson arrivals at 50 per second: the mean gap is 1/50 s within sampling error
+    assert abs(arr[-1] / len(arr) - 0.02) < 0.004
+    for q in s:
+        assert q["d"] in (2, 3) and 10 <= q["steps"] <= 100
+        if q["d"] == 2:
+            assert 4 <= q["K"] <= 32 and 3 <= q["P"] <= 8 and q["flow"] in ("tg", "mms")
+        else:
+            assert 4 <= q["K"] <= 24 and 3 <= q["P"] <= 7 and q["flow"] == "tg"
+    assert {q["d"] for q in s} == {2, 3} and {q["flow"] for q in s} == {"tg", "mms"}
+    assert bench.serving_stream(50) == s[:50]  # the stream is a prefix-stable seeded sequence
+
+
+def test_request_time_steps():
+    for q in bench.serving_stream(200):
+        r = bench.serving_request(FakeImex, q)
+        K, P = q["K"], q["P"]
+        assert r["nsteps"] == q["steps"] and r["P"] == P and r["dim"] == q["d"]
+        if q["flow"] == "mms":
+            h, nu0 = 1.0 / K, 0.01
+            assert r["dt"] <= 4.0 * h * h / (nu0 * (P + 1) ** 4) * (1 + 1e-12)
+            assert r["dt"] <= 0.3 / (5 ** 0.5 * bench.rho_hat(P) * 2.0 / h) * (1 + 1e-12)
+            assert r["periodic"] == (0, 0)
+        else:
+            h = bench.TWO_PI / K
+            assert r["dt"] == pytest.approx(0.3 / (bench.rho_hat(P) * 2.0 / h))
+            assert all(r["periodic"])
+
+
+def test_replay_latencies():
+    n = 6
+    out = bench.run_serving(FakeImex, n)
+    assert out["requests"] == n and out["completed"] == n and out["failed"] == 0
+    stream = bench.serving_stream(n)
+    ticks_min = max(q["steps"] for q in stream)
+    assert out["ticks"] >= ticks_min
+    # a request steps once per tick, so its own step latency is about one tick
+    tick_ms = 1e3 * FakeImex.Server.TICK_S
+    assert tick_ms * 0.9 <= out["p50_request_step_ms"] <= out["p99_request_step_ms"]
+    assert out["p50_request_step_ms"] < 5 * out["p99_step_ms"]
+    # end-to-end latency covers queueing plus every step
+    assert out["p50_queue_wait_s"] >= 0.0
+    assert out["p99_request_latency_s"] >= 1e-3 * out["p50_request_step_ms"] * min(q["steps"] for q in stream)
+    assert out["value"] > 0 and out["dof_stages"] > 0
