@@ -117,3 +117,77 @@ def test_vv_exact_solution_of_the_forced_problem():
     ref = dvdt + vv_flux_divergence_fd(X, t, nu0, nu1, vmax) + gp
     f = flows.forcing_vv(X, t, nu0, nu1, vmax)
     assert np.abs(f - ref).max() < 1e-4 * np.abs(ref).max()
+
+
+def tgtravel_pressure(X, t, nu0):
+    """Pressure of the traveling Taylor-Green vortex (the uniform translation (1, 1) carries
+    the classical field p = (cos 2a + cos 2b) / 4 decaying with the square of the velocity's
+    factor), written out here so that the pin below does not rest on the oracle's fields."""
+    a = 2 * PI * (X[..., 0] - t)
+    b = 2 * PI * (X[..., 1] - 0.125 - t)
+    return 0.25 * (np.cos(2 * a) + np.cos(2 * b)) * np.exp(-16 * PI ** 2 * nu0 * t)
+
+
+def test_tgtravel_gradients_are_the_derivatives():
+    """The closed-form gradients of the traveling vortex and of the viscosity nu(x, y, t) used
+    by the manufactured forcing equal central differences of the fields themselves."""
+    nu0, t = 0.01, 0.41
+    X = points(400, 2, 7, 0.0, 1.0)
+    G = fd_grad(lambda Y: flows.tgtravel_velocity(Y, t, nu0), X)
+    assert np.abs(G - flows.tgtravel_grad(X, t, nu0)).max() < 1e-8
+    gn = fd_grad(lambda Y: flows.nu_varxyt(Y, t, nu0)[None], X)[0]
+    assert np.abs(gn - flows.nu_varxyt_grad(X, t, nu0)).max() < 1e-10
+    # the viscosity law: nu0 (1 + sin(2 pi x) sin(2 pi y) cos(t) / 2) stays within nu0 [1/2, 3/2]
+    nu = flows.nu_varxyt(points(4000, 2, 8, 0.0, 1.0), 0.0, nu0)
+    assert nu.min() >= 0.5 * nu0 - 1e-15 and nu.max() <= 1.5 * nu0 + 1e-15
+    assert nu.max() - nu.min() > 0.9 * nu0
+
+
+def test_tgtravel_constant_viscosity_is_exact():
+    """With nu = nu0 the traveling vortex solves the unforced Navier-Stokes equations with the
+    pressure above and is solenoidal (so the forcing below carries only the viscosity's
+    variation)."""
+    nu0, h = 0.01, 1e-4
+    X = points(400, 2, 9, 0.0, 1.0)
+    for t in (0.0, 0.23, 0.9):
+        v = flows.tgtravel_velocity(X, t, nu0)
+        dvdt = (flows.tgtravel_velocity(X, t + h, nu0) - flows.tgtravel_velocity(X, t - h, nu0)) / (2 * h)
+        G = fd_grad(lambda Y: flows.tgtravel_velocity(Y, t, nu0), X, h)
+        gp = fd_grad(lambda Y: tgtravel_pressure(Y, t, nu0)[None], X, h)[0]
+        lap = np.zeros_like(v)
+        for k in range(2):
+            e = np.zeros(2)
+            e[k] = h
+            lap += (flows.tgtravel_velocity(X + e, t, nu0) - 2 * v + flows.tgtravel_velocity(X - e, t, nu0)) / h ** 2
+        adv = np.stack([v[0] * G[c, 0] + v[1] * G[c, 1] for c in range(2)])
+        res = dvdt + adv + gp - nu0 * lap
+        assert np.abs(res).max() < 1e-5 * np.abs(dvdt).max(), t
+        assert np.abs(G[0, 0] + G[1, 1]).max() < 1e-8
+        assert np.abs(flows.forcing_tgtravel_varnu(X, t, nu0) - 0.0).max() > 1e-3  # nu varies: f != 0
+
+
+def test_tgtravel_varnu_forcing_closes_the_equations():
+    """The manufactured forcing of the variable-viscosity traveling vortex equals
+    d_t v + div(v v) + grad p - div[nu(x, y, t) (grad v + grad v^T)] evaluated by finite
+    differences of the closed forms (a dropped term, a wrong sign or a transposed gradient
+    in the forcing fails this)."""
+    nu0, t, h = 0.01, 0.37, 1e-4
+    X = points(300, 2, 11, 0.0, 1.0)
+
+    def flux(Y):
+        v = flows.tgtravel_velocity(Y, t, nu0)
+        G = fd_grad(lambda Z: flows.tgtravel_velocity(Z, t, nu0), Y, 1e-5)
+        nu = flows.nu_varxyt(Y, t, nu0)
+        return np.stack([np.stack([v[c] * v[k] - nu * (G[c, k] + G[k, c]) for k in range(2)]) for c in range(2)])
+
+    div = np.zeros((2, X.shape[0]))
+    for k in range(2):
+        e = np.zeros(2)
+        e[k] = h
+        div += (flux(X + e)[:, k] - flux(X - e)[:, k]) / (2 * h)
+    dvdt = (flows.tgtravel_velocity(X, t + 1e-5, nu0) - flows.tgtravel_velocity(X, t - 1e-5, nu0)) / 2e-5
+    gp = fd_grad(lambda Y: tgtravel_pressure(Y, t, nu0)[None], X)[0]
+    ref = dvdt + div + gp
+    f = flows.forcing_tgtravel_varnu(X, t, nu0)
+    assert np.abs(ref).max() > 0.05
+    assert np.abs(f - ref).max() < 1e-4 * np.abs(ref).max()
