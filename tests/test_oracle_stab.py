@@ -60,3 +60,22 @@ def test_minimiser_of_the_penalised_distance():
     for _ in range(5):
         assert J(vt) <= J(vt + 1e-3 * rng.standard_normal(vt.size))
     assert vt @ (A @ vt) < vr @ (A @ vr)
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_mean_speed_closed_forms(d):
+    """|u_K| of a constant field is its length on every element; the mass-weighted mean of an
+    affine field over an element is its value at the element's centre (GLL quadrature is
+    exact for degree 1), so |u_K| is the speed there."""
+    mesh = dg.Mesh(d, 3, (3, 2, 2)[:d], [0.0] * d, [1.0, 1.3, 0.8][:d], (False,) * d)
+    n = mesh.ne * (mesh.P + 1) ** d
+    c = np.array([0.3, -1.2, 0.7][:d])
+    v = np.repeat(c[:, None], n, axis=1)
+    assert np.abs(stab.mean_speed(mesh, v) - np.linalg.norm(c)).max() < 1e-14
+    X = mesh.node_coords(mesh.P + 1)                       # (ne, N^d, d)
+    A = np.random.default_rng(4).standard_normal((d, d))
+    b = np.random.default_rng(5).standard_normal(d)
+    v = (np.einsum("ck,enk->cen", A, X) + b[:, None, None]).reshape(d, -1)
+    centre = X.mean(axis=1)                                # symmetric nodes: the mean is the centre
+    exact = np.linalg.norm(np.einsum("ck,ek->ce", A, centre) + b[:, None], axis=0)
+    assert np.abs(stab.mean_speed(mesh, v) - exact).max() < 1e-13

@@ -163,3 +163,47 @@ def test_alg2_order_nonlinear(name, ns):
         else:
             errs.append(abs(u - ref))
     assert np.log(errs[0] / errs[1]) / np.log(2) == pytest.approx(3.0, abs=0.3)
+
+
+@pytest.mark.parametrize("name", RK_NAMES + ["EULER"])
+def test_stability_function_is_the_partitioned_rk_closed_form(name):
+    """On u' = z_E u + z_I u the stages of an additive RK method solve the linear system
+    (I - z_E A^EX - z_I A^IM) U = 1 and R = 1 + (z_E b^EX + z_I b^IM)^T U (the textbook
+    stability function of a partitioned RK method, here with z_E = i Im z and z_I = Re z as
+    Sec. 2.5 assigns them); the stage-by-stage step of Alg. 1 must give the same number."""
+    t = tableaux.get(name)
+    _, AI, bI, AE, bE = (np.array(a, dtype=float) for a in t.as_float())
+    rng = np.random.default_rng(3)
+    for _ in range(20):
+        z = complex(-3.0 * rng.random(), 4.0 * rng.standard_normal())
+        zE, zI = 1j * z.imag, z.real
+        U = np.linalg.solve(np.eye(t.s) - zE * AE - zI * AI, np.ones(t.s))
+        R = 1 + (zE * bE + zI * bI) @ U
+        assert abs(scalar.stability_function("RK-" + name if name != "EULER" else "EULER", z) - R) < 1e-13 * max(1, abs(R))
+
+
+def test_imex_euler_and_one_node_sdc_closed_form():
+    """IMEX Euler: R(x + i y) = (1 + i y) / (1 - x); SDC with one subinterval and no sweep
+    is that predictor step."""
+    for z in (complex(-0.3, 0.8), complex(-2.0, -1.5), complex(0.0, 3.0)):
+        R = (1 + 1j * z.imag) / (1 - z.real)
+        assert abs(scalar.stability_function("EULER", z) - R) < 1e-15
+        assert abs(scalar.stability_function("SDC-Eu(1,0)", z) - R) < 1e-15
+
+
+@pytest.mark.parametrize("M", [1, 2, 3, 5])
+def test_sdc_nodes_and_subinterval_weights(M):
+    """The SDC sub-nodes are the M+1 GLL points mapped to [0, 1] (symmetric, ends included),
+    and the weights w_{q,m} integrate every polynomial of degree <= M exactly over each
+    subinterval (t_{m-1}, t_m): sum_q w_{q,m} t_q^k = (t_m^{k+1} - t_{m-1}^{k+1}) / (k+1)."""
+    tau, W = scalar.sdc_nodes(M)
+    assert tau[0] == 0.0 and tau[-1] == 1.0 and np.all(np.diff(tau) > 0)
+    assert np.abs(tau + tau[::-1] - 1.0).max() < 1e-14
+    for m in range(1, M + 1):
+        for k in range(M + 1):
+            exact = (tau[m] ** (k + 1) - tau[m - 1] ** (k + 1)) / (k + 1)
+            assert abs(W[m] @ tau ** k - exact) < 1e-12   # power-basis rounding at M = 5
+    if M == 2:
+        # over the whole step the subinterval weights add up to the 3-point GLL weights on
+        # [0, 1], Simpson's 1/6, 2/3, 1/6
+        assert np.abs(W[1:].sum(axis=0) - np.array([1 / 6, 2 / 3, 1 / 6])).max() < 1e-15
