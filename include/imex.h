@@ -22,6 +22,20 @@
  *   - Errors: every call returns an imex_status; no C++ exception crosses the ABI.
  *     imex_last_error() gives a human-readable message for the last failure.
  *   - Threads: one context must not be used from two host threads at once.
+ *   - Environment switches (read once; none changes a result beyond rounding):
+ *       IMEX_REFINE_DECADES=1..5  decades of FP32 residual decrease between FP64
+ *                                 residual replacements (mixed forms; default 4 with the
+ *                                 V-cycle, 2 with Jacobi)
+ *       IMEX_PMG_CLUSTER=0        one launch per coarsest-level smoothing step instead of
+ *                                 the single-cluster kernel
+ *       IMEX_TUNE=0               default launch shapes, no timing of the alternatives
+ *       IMEX_PERSIST=1            the persistent-kernel FP32 Jacobi pressure CG (measured
+ *                                 slower than the graph-replayed iteration kernels)
+ *       IMEX_PDL=1                CG loop kernels launched with programmatic dependent
+ *                                 launch
+ *       IMEX_BATCH_SERIAL=1       the groups of a batch stepped one after the other from the
+ *                                 calling thread instead of one host thread per group
+ *       IMEX_DEBUG=1              one stderr line per FP64 residual replacement
  */
 #ifndef IMEX_GB300_H
 #define IMEX_GB300_H
