@@ -1,7 +1,8 @@
-"""Host logic of bench.py's serving replay on CPU: the request stream follows its stated
-recipe (arrival order, ranges, time-step bounds), and the replay's latency figures are
-consistent when the server is a fake that takes one step of every admitted request per
-tick and admits at most two requests per tick."""
+"""Host logic of bench.py on CPU: the synthetic workloads follow their stated recipes (the
+256-instance ensemble, the serving stream's arrival order, ranges and time-step bounds, the
+CFL eigenvalue the time steps use), and the serving replay's latency figures are consistent
+when the server is a fake that takes one step of every admitted request per tick and admits
+at most two requests per tick."""
 import os
 import sys
 import time
@@ -127,3 +128,25 @@ def test_replay_latencies():
     assert out["p50_queue_wait_s"] >= 0.0
     assert out["p99_request_latency_s"] >= 1e-3 * out["p50_request_step_ms"] * min(q["steps"] for q in stream)
     assert out["value"] > 0 and out["dof_stages"] > 0
+
+
+def test_cfl_eigenvalue():
+    """rho_hat(P), the largest eigenvalue modulus of the GLL collocation derivative with the
+    inflow node removed, has the values the workloads' CFL_lambda numbers rest on
+    (rho_hat(7) = 5.656, rho_hat(8) = 6.967) and grows with P."""
+    assert bench.rho_hat(7) == pytest.approx(5.656, abs=5e-4)
+    assert bench.rho_hat(8) == pytest.approx(6.967, abs=5e-4)
+    r = [bench.rho_hat(P) for P in range(2, 9)]
+    assert all(b > a for a, b in zip(r, r[1:]))
+
+
+def test_ensemble_recipe():
+    """256 decaying Taylor-Green instances from seed 0: K in 4..32, P in 3..8 (six degree
+    groups), nu in [1e-3, 1e-1], dt at CFL_lambda = 0.3; 9,851,694 velocity DOF in all."""
+    s = bench.ensemble_specs()
+    assert len(s) == 256 and s == bench.ensemble_specs()
+    assert {P for _, P, _, _ in s} == set(range(3, 9))
+    for K, P, nu, dt in s:
+        assert 4 <= K <= 32 and 3 <= P <= 8 and 1e-3 <= nu <= 1e-1
+        assert 0.3 == pytest.approx(dt * bench.rho_hat(P) * 2.0 / (bench.TWO_PI / K))
+    assert sum(2 * K * K * (P + 1) ** 2 for K, P, _, _ in s) == 9851694
