@@ -54,8 +54,11 @@ def parse():
     ap.add_argument("--no-extra-configs", action="store_true",
                     help="skip the SDC / BDF2 lines, the 2D Taylor-Green run and the Dirichlet dt sweep")
     ap.add_argument("--profile-only", action="store_true", help="short run for ncu captures")
-    ap.add_argument("--workload", default="tg3d", choices=["tg3d", "ensemble", "serving", "ops"],
-                    help="tg3d: the headline line; ensemble / serving / ops: that workload alone")
+    ap.add_argument("--workload", default="tg3d", choices=["tg3d", "ensemble", "serving", "ops", "next"],
+                    help="tg3d: the headline line; ensemble / serving / ops / next: that workload alone "
+                         "(next: the velocity-dependent viscosity, stabilisation and statistics rows)")
+    ap.add_argument("--no-next-rows", action="store_true",
+                    help="skip the velocity-dependent viscosity, stabilisation and statistics timings")
     ap.add_argument("--serving-requests", type=int, default=24,
                     help="requests of the serving stream replayed inside the headline line (0: skip)")
     ap.add_argument("--ops-nelem", type=int, default=40,
@@ -514,6 +517,108 @@ def run_method_lines(imex, args, stream):
     return out
 
 
+def run_next_rows(imex, args, nsteps=3):
+    """The rows built on the stage work, each timed through the public API on the headline
+    mesh size (16^3, P = 7) in FP64, the precision their parity tests cover: the
+    velocity-dependent viscosity on the periodic vortex array of Sec. 4.2 (Alg. 3 with the
+    semi-implicit viscosity), the divergence / mass-flux stabilisation after every stage
+    projection (Sec. 3.3) against the same steps without it, and the flow statistics of
+    Sec. 4.3 (the dissipation rate and the energy spectrum of the Taylor-Green field).  Each
+    item records its error message instead of a figure if its call fails."""
+    import numpy as np
+    n, P = args.nelem, args.P
+    out = {}
+
+    def timed(c, dt, k):
+        s0 = c.stats()["stages"]
+        c.step(dt, 1)                                           # warm-up (set-up, tuning)
+        s1 = c.stats()["stages"]
+        w0 = time.perf_counter()
+        c.step(dt, k)
+        el = time.perf_counter() - w0
+        st = c.stats()
+        stages = st["stages"] - s1
+        return {"value": 3 * c.nvel * stages / el, "unit": UNIT, "ms_per_step": 1e3 * el / k, "steps": k,
+                "warmup": 1, "stages_per_step": stages / k, "first_step_stages": s1 - s0,
+                "poisson_iters_last_call": st["poisson_iters"], "helmholtz_iters_last_call": st["helmholtz_iters"],
+                "timing": "host wall clock around one synchronous imex_step call of all timed steps"}
+
+    # velocity-dependent viscosity: the periodic vortex array VVP, nu = nu0 + nu1 (|v| / vmax)^2,
+    # its manufactured forcing; dt within the diffusive limit of the explicit nu terms
+    nu0, nu1, vmax, dt = 0.01, 0.01, 2.0, 1e-4
+    c = None
+    try:
+        c = imex.Context(3, P, (n, n, n), [-0.5] * 3, [0.5] * 3, (1, 1, 1), precision=imex.FP64, tol=args.tol,
+                         maxit=20000)
+        c.set_viscosity_model(imex.NU_VELOCITY, [nu0, nu1, vmax])
+        c.set_forcing(imex.FORCE_VV, [nu0, nu1, vmax])
+        c.set_tableau_named("CB3e")
+        c.init_flow(imex.FLOW_VV, (), 0.0)
+        r = timed(c, dt, nsteps)
+        v = c.get_velocity()
+        ex = c.eval_field(0, imex.FLOW_VV, (), t=c.time())
+        r.update(workload=f"3D vortex array VVP, [-1/2,1/2]^3 periodic, {n}^3 hex, P={P}, nu = {nu0} + {nu1} "
+                          f"(|v|/{vmax})^2 with its forcing, RK-CB3e, dt={dt}, tol {args.tol}, FP64",
+                 rel_l2_vs_exact=float(np.linalg.norm(v - ex) / np.linalg.norm(ex)), t=c.time())
+        out["velocity_dependent_viscosity_vvp"] = r
+    except Exception as e:          # noqa: BLE001 -- recorded in the line
+        out["velocity_dependent_viscosity_vvp"] = {"error": str(e)}
+    finally:
+        if c is not None:
+            c.close()
+
+    # stabilisation: the headline flow with zeta_D = zeta_C = 1, and the same steps without it
+    cs = cp = None
+    try:
+        mk = lambda: make_ctx(imex, args, "fp64", None)     # noqa: E731
+        cs, cp = mk(), mk()
+        cs.set_stabilization(1.0, 1.0)
+        rs, rp = timed(cs, args.dt, nsteps), timed(cp, args.dt, nsteps)
+        vs, vp = cs.get_velocity(), cp.get_velocity()
+        rs.update(workload=f"3D Taylor-Green transition, {n}^3 hex, P={P}, RK-CB3e, dt={args.dt}, tol {args.tol}, "
+                           "FP64, zeta_D = zeta_C = 1 after every stage projection",
+                  without_stabilization=rp["value"], cost_ratio=rp["value"] / rs["value"],
+                  rel_l2_change=float(np.linalg.norm(vs - vp) / np.linalg.norm(vp)))
+        out["stabilization"] = rs
+    except Exception as e:          # noqa: BLE001
+        out["stabilization"] = {"error": str(e)}
+    finally:
+        for c in (cs, cp):
+            if c is not None:
+                c.close()
+
+    # statistics of the initial Taylor-Green field: eps = 3 nu / 4 and all energy, pi^3, in
+    # shell 2 of a 128^3 grid
+    c = None
+    try:
+        c = make_ctx(imex, args, "fp64", None)
+        nu = 1.0 / 1600.0
+        eps = c.dissipation()
+        M, kmax, reps = 128, 64, 5
+        E = c.energy_spectrum(M, kmax)
+        w0 = time.perf_counter()
+        for _ in range(reps):
+            c.dissipation()
+        t_eps = (time.perf_counter() - w0) / reps
+        w0 = time.perf_counter()
+        for _ in range(reps):
+            c.energy_spectrum(M, kmax)
+        t_spec = (time.perf_counter() - w0) / reps
+        out["statistics"] = {
+            "workload": f"3D Taylor-Green initial field, {n}^3 hex, P={P}; spectrum on a {M}^3 grid, {kmax} shells",
+            "dissipation_ms": 1e3 * t_eps, "dissipation_gbs": 8.0 * 3 * c.nvel / t_eps / 1e9,
+            "spectrum_ms": 1e3 * t_spec, "spectrum_grid_points_per_s": M ** 3 / t_spec,
+            "eps_rel_error_vs_3nu_over_4": abs(eps - 0.75 * nu) / (0.75 * nu),
+            "shell2_share": float(E[2] / E.sum()), "shell2_rel_error_vs_pi3": abs(E[2] - np.pi ** 3) / np.pi ** 3,
+            "timing": "host wall clock per synchronous call (device work, one device-to-host copy)"}
+    except Exception as e:          # noqa: BLE001
+        out["statistics"] = {"error": str(e)}
+    finally:
+        if c is not None:
+            c.close()
+    return out
+
+
 def rho_hat(P):
     """Largest eigenvalue modulus of the 1D GLL collocation derivative of degree P with a
     one-sided Dirichlet condition (the element convection operator for unit velocity)."""
@@ -783,6 +888,14 @@ def main():
         e = tensor_core_experiment(imex, torch, args.nelem, args.P)
         print(json.dumps({"tensor_core_experiment": e}))
         return 0
+    if args.workload == "next":
+        e = run_next_rows(imex, args)
+        print(json.dumps({"metric": METRIC, "value": None, "unit": UNIT, "n_gpus": world, "steps": 0,
+                          "warmup": 0, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+                          "vs_baseline": None, "dtype": "f64", "data": "synthetic (closed-form flows)",
+                          "config": {"workload": "velocity-dependent viscosity, stabilisation, statistics"},
+                          "next_rows": e}))
+        return 0
     if args.workload == "ops":
         e = run_operators(imex, torch, args.ops_nelem or 40, args.P)
         print(json.dumps({"metric": METRIC, "value": None, "unit": UNIT, "n_gpus": world, "steps": 0,
@@ -908,6 +1021,9 @@ def main():
         methods = run_method_lines(imex, args, stream.cuda_stream)
         config1 = run_config1(imex)
         config3 = run_config3(imex)
+    next_rows = None
+    if rank == 0 and not args.no_next_rows:
+        next_rows = run_next_rows(imex, args)
 
     cpu = cpu_all = cpu_configs = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -939,6 +1055,7 @@ def main():
             "clocks": clocks, "gpu_launches": launches, "roofline": roof, "kernels": prof,
             "e2e": e2e, "fp64": fp64, "cpu_baseline": cpu, "ensemble": ens, "serving": serving,
             "operators_above_l2": ops, "methods": methods, "config1": config1, "config3_dt_sweep": config3,
+            "next_rows": next_rows,
             "cpu_baseline_all_cores": cpu_all, "cpu_oracle_configs": cpu_configs,
             "tuning": imex.tuning_info(),
             "solver": {"poisson_iters_per_call": stats["poisson_iters"], "helmholtz_iters": stats["helmholtz_iters"],
