@@ -1,6 +1,7 @@
-// Host dump of the one-dimensional tables the kernels read (basis.cpp build_tables and
-// gll_interp): one line per table, "name N v0 v1 ...", every value printed with 17
-// significant digits, for N = 2 .. IMEX_MAXN points per direction.  Only host code runs.
+// Host dump of the one-dimensional tables the kernels read (basis.cpp build_tables,
+// gll_interp and build_line_ops): one line per table, "name N [indices] v0 v1 ...", every
+// value printed with 17 significant digits, for N = 2 .. IMEX_MAXN points per direction.
+// Only host code runs.
 #include <cstdio>
 
 #include "common.cuh"
@@ -46,5 +47,31 @@ int main() {
       for (int i = 0; i < Nc * Nf; ++i) std::printf(" %.17g", E[i]);
       std::printf("\n");
     }
+  // 1D SIPG line operators of a unit element (h = 1, unit viscosity): own blocks for every
+  // pair of face kinds, the neighbour couplings of every side and face kind, the rows forming
+  // a neighbour's normal derivative
+  static LineOps<double> o;
+  static LineOps<float> of;
+  const double one[3] = {1.0, 1.0, 1.0};
+  for (int N = 2; N <= IMEX_MAXN; ++N) {
+    build_line_ops(t, N, one, 1, &o, &of);
+    for (int kl = 0; kl < 3; ++kl)
+      for (int kr = 0; kr < 3; ++kr) {
+        std::printf("LA %d %d %d", N, kl, kr);
+        for (int i = 0; i < N * N; ++i) std::printf(" %.17g", o.A[0][3 * kl + kr][i]);
+        std::printf("\n");
+      }
+    for (int side = 0; side < 2; ++side) {
+      for (int kind = 0; kind < 3; ++kind)
+        for (int c = 0; c < 2; ++c) {
+          std::printf("LC %d %d %d %d", N, side, kind, c);
+          for (int i = 0; i < N; ++i) std::printf(" %.17g", o.C[0][side][kind][c][i]);
+          std::printf("\n");
+        }
+      std::printf("LDN %d %d", N, side);
+      for (int j = 0; j < N; ++j) std::printf(" %.17g", o.dn[0][side][j]);
+      std::printf("\n");
+    }
+  }
   return 0;
 }
