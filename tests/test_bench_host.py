@@ -1,8 +1,9 @@
 """Host logic of bench.py on CPU: the synthetic workloads follow their stated recipes (the
 256-instance ensemble, the serving stream's arrival order, ranges and time-step bounds, the
-CFL eigenvalue the time steps use), and the serving replay's latency figures are consistent
+CFL eigenvalue the time steps use), the serving replay's latency figures are consistent
 when the server is a fake that takes one step of every admitted request per tick and admits
-at most two requests per tick."""
+at most two requests per tick, and the per-class roofline arithmetic of the line recomputes
+from the algorithmic work and the timings."""
 import os
 import sys
 import time
@@ -150,3 +151,58 @@ def test_ensemble_recipe():
         assert 4 <= K <= 32 and 3 <= P <= 8 and 1e-3 <= nu <= 1e-1
         assert 0.3 == pytest.approx(dt * bench.rho_hat(P) * 2.0 / (bench.TWO_PI / K))
     assert sum(2 * K * K * (P + 1) ** 2 for K, P, _, _ in s) == 9851694
+
+
+class FakeProfiledContext:
+    """Per-class launches / milliseconds and algorithmic work, as imex_profile_read and
+    imex_profile_work return them."""
+
+    def __init__(self, rows):
+        self.rows = rows
+
+    def profile_read(self, cls):
+        r = self.rows.get(cls)
+        return (r[0], r[1]) if r else (0, 0.0)
+
+    def profile_work(self, cls):
+        r = self.rows.get(cls)
+        return (r[2], r[3], r[4]) if r else (0.0, 0.0, 0)
+
+
+def test_operator_table_and_roofline():
+    """Achieved GB/s and GFLOP/s are the algorithmic work over the CUDA-event time, the
+    fractions divide by the HBM copy rate or the ALU peak of the class's arithmetic, and the
+    roofline names the class with the largest time, bound by the larger of its two fractions,
+    with the DRAM traffic of that class's capture."""
+    import types
+    names = ["a_fp32", "b_ff", "c_fp64"]
+    imex = types.SimpleNamespace(PROF_NAMES=names)
+    hbm = 8000.0
+    # (launches, total ms, bytes, flops, arith) per class; b_ff has the largest time
+    ctx = FakeProfiledContext({0: (100, 2.0, 100 * 8e6, 100 * 1e6, 1),
+                               1: (4, 5.0, 4 * 1e8, 4 * 2.8e9, 3),
+                               2: (10, 1.0, 10 * 1.6e7, 0.0, 0)})
+    rows = bench.operator_table(imex, ctx, hbm)
+    a = rows["a_fp32"]
+    assert a["avg_us"] == pytest.approx(20.0) and a["bytes_per_launch"] == pytest.approx(8e6)
+    assert a["gbs"] == pytest.approx(100 * 8e6 / 2e-3 / 1e9) and a["hbm_frac"] == pytest.approx(a["gbs"] / hbm)
+    assert a["alu_peak_gflops"] == pytest.approx(bench.FP32_PEAK_GFLOPS)
+    assert rows["b_ff"]["alu_peak_gflops"] == pytest.approx(bench.FP32_PEAK_GFLOPS * 2 / 15)
+    assert rows["c_fp64"]["flops_per_launch"] is None and "alu_frac" not in rows["c_fp64"]
+    roof = bench.roofline_of(rows, hbm, "measured", traffic={"b_ff": 6.6e7})
+    assert roof["kernel"] == "b_ff" and roof["bound"] == "alu" and roof["unit"] == "GFLOP/s"
+    assert roof["achieved"] == pytest.approx(4 * 2.8e9 / 5e-3 / 1e9)
+    assert roof["frac"] == pytest.approx(roof["achieved"] / roof["peak"])
+    assert roof["traffic"] == 6.6e7 and roof["avg_launch_us"] == pytest.approx(1250.0)
+    assert roof["share_of_profiled_ms"] == pytest.approx(5.0 / 8.0)
+    # an HBM-bound dominant class reports GB/s against the copy rate, traffic unknown: None
+    ctx2 = FakeProfiledContext({2: (10, 9.0, 10 * 6e8, 0.0, 0)})
+    roof2 = bench.roofline_of(bench.operator_table(imex, ctx2, hbm), hbm, "measured")
+    assert roof2["bound"] == "hbm" and roof2["unit"] == "GB/s" and roof2["traffic"] is None
+    assert roof2["frac"] == pytest.approx(10 * 6e8 / 9e-3 / 1e9 / hbm)
+    assert bench.roofline_of({}, hbm, "measured") is None
+
+
+def test_whole_job_value():
+    """The whole-job throughput is all ranks' units over the slowest rank's time."""
+    assert bench.job_value(4, 1e6, 2.0) == pytest.approx(2e6)
