@@ -1,6 +1,7 @@
 """Host-side logic behind the C ABI, exercised on CPU through the binding without any CUDA
 call: argument validation that returns before the device is touched, the serving form's
-request footprint model, and the launch-shape table of the apply tuner."""
+request footprint model, the launch-shape table of the apply tuner, and the binding's
+argument marshalling."""
 import numpy as np
 import pytest
 
@@ -94,3 +95,37 @@ def test_launch_counter_without_launches():
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
         assert n == 0
+
+
+def test_binding_marshalling():
+    """Host arrays reach the library as contiguous float64 (other dtypes and strides are
+    copied), output arrays must already be writable contiguous float64, short buffers are
+    refused before any call; parameter lists become float64 arrays; a request structure
+    carries the mesh with the unused third direction set to one periodic element."""
+    import ctypes
+    p, dev, keep = imex._arr(np.arange(6, dtype=np.float32))
+    assert dev == 0 and keep.dtype == np.float64 and np.array_equal(keep, np.arange(6.0))
+    strided = np.arange(12.0)[::2]
+    p, dev, keep = imex._arr(strided)
+    assert keep.flags.c_contiguous and np.array_equal(keep, strided)
+    assert ctypes.cast(p, ctypes.POINTER(ctypes.c_double))[3] == 6.0
+    a = np.zeros(4)
+    assert imex._arr(a, 4, writable=True)[2] is a              # no copy of a valid output
+    for bad in (np.zeros(4, dtype=np.float32), np.zeros(8)[::2]):
+        with pytest.raises(ValueError):
+            imex._arr(bad, 4, writable=True)
+    ro = np.zeros(4)
+    ro.setflags(write=False)
+    with pytest.raises(ValueError):
+        imex._arr(ro, 4, writable=True)
+    with pytest.raises(ValueError):
+        imex._arr(np.zeros(3), 4)
+    assert imex._arr(None) == (None, 0, None)
+    p, n, keep = imex._params([1, 2.5])
+    assert n == 2 and keep.dtype == np.float64 and list(keep) == [1.0, 2.5]
+    assert imex._params(()) == (None, 0, None)
+    r = imex.Server.request(dim=2, P=5, nelem=(7, 3), lo=(0, -1), hi=(1, 2), periodic=(1, 0), flow=imex.FLOW_TG2D,
+                            nu_params=[0.01], dt=0.002, nsteps=9)
+    assert (r.dim, r.P, list(r.nelem), list(r.periodic)) == (2, 5, [7, 3, 1], [1, 0, 1])
+    assert list(r.lo)[:2] == [0.0, -1.0] and list(r.hi)[:2] == [1.0, 2.0]
+    assert r.nu_params[0] == 0.01 and r.dt == 0.002 and r.nsteps == 9
