@@ -367,7 +367,7 @@ print(json.dumps({{"setup_s": setup, "steps_s": steps, "nvel": int(disc.nv)}}))
               f"({3 * d['nvel']} velocity DOF), {threads} thread(s); one-off setup {d['setup_s']:.1f} s not "
               f"counted, {sum(d['steps_s']):.1f} s of steps")
     return {"value": statistics.mean(per), "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample,
-            "per_step": per, "setup_s": d["setup_s"]}, None
+            "per_step": per, "steps_s": d["steps_s"], "setup_s": d["setup_s"]}, None
 
 
 def cpu_oracle_configs(threads, timeout=900):
@@ -860,13 +860,15 @@ def run_reference(args, rank, world):
         return 0
     timed = base["per_step"][args.warmup:]
     value = statistics.mean(timed)
+    ms = 1e3 * statistics.mean(base["steps_s"][args.warmup:])   # one step of the sampled mesh
     n = args.nelem
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (closed-form Taylor-Green)",
         "config": {"workload": f"3D Taylor-Green transition, {n}^3 hex, P={args.P}, Re=1600, RK-CB3e, "
-                               f"dt={args.dt}", "sample": base["sample"]},
+                               f"dt={args.dt}", "sample": base["sample"],
+                   "ms_per_step": "one RK-CB3e step of the sampled 2^3-element mesh"},
         "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": base["sample"], "value": value, "unit": UNIT},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
