@@ -143,42 +143,45 @@ __host__ __device__ inline ff::operator double() const {
 #endif
 }
 
+// The operations below compile for the host as well (the same FP32 operations), so that
+// host programs can check them against exact arithmetic.
+
 // s + e = a + b exactly (no precondition on the magnitudes)
-__device__ __forceinline__ ff ff_two_sum(float a, float b) {
+__host__ __device__ __forceinline__ ff ff_two_sum(float a, float b) {
   const float s = a + b;
   const float bb = s - a;
   const float e = (a - (s - bb)) + (b - bb);
   return ff(s, e);
 }
 // s + e = a + b exactly when |a| >= |b|
-__device__ __forceinline__ ff ff_fast_two_sum(float a, float b) {
+__host__ __device__ __forceinline__ ff ff_fast_two_sum(float a, float b) {
   const float s = a + b;
   return ff(s, b - (s - a));
 }
 
-__device__ __forceinline__ ff operator+(ff a, ff b) {
+__host__ __device__ __forceinline__ ff operator+(ff a, ff b) {
   const ff s = ff_two_sum(a.hi, b.hi);
   return ff_fast_two_sum(s.hi, s.lo + (a.lo + b.lo));
 }
-__device__ __forceinline__ ff operator-(ff a) { return ff(-a.hi, -a.lo); }
-__device__ __forceinline__ ff operator-(ff a, ff b) { return a + (-b); }
-__device__ __forceinline__ ff operator*(ff a, ff b) {
+__host__ __device__ __forceinline__ ff operator-(ff a) { return ff(-a.hi, -a.lo); }
+__host__ __device__ __forceinline__ ff operator-(ff a, ff b) { return a + (-b); }
+__host__ __device__ __forceinline__ ff operator*(ff a, ff b) {
   const float p = a.hi * b.hi;
   float e = fmaf(a.hi, b.hi, -p);                // exact error of the leading product
   e = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, e));
   return ff_fast_two_sum(p, e);
 }
-__device__ __forceinline__ ff operator/(ff a, ff b) {
+__host__ __device__ __forceinline__ ff operator/(ff a, ff b) {
   const float q1 = a.hi / b.hi;
   const ff r = a - b * ff(q1);
   const float q2 = r.hi / b.hi;
   return ff_fast_two_sum(q1, q2);
 }
-__device__ __forceinline__ ff& operator+=(ff& a, ff b) { return a = a + b; }
-__device__ __forceinline__ ff& operator-=(ff& a, ff b) { return a = a - b; }
-__device__ __forceinline__ ff& operator*=(ff& a, ff b) { return a = a * b; }
-__device__ __forceinline__ bool operator<(ff a, ff b) { return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo); }
-__device__ __forceinline__ bool operator>(ff a, ff b) { return b < a; }
+__host__ __device__ __forceinline__ ff& operator+=(ff& a, ff b) { return a = a + b; }
+__host__ __device__ __forceinline__ ff& operator-=(ff& a, ff b) { return a = a - b; }
+__host__ __device__ __forceinline__ ff& operator*=(ff& a, ff b) { return a = a * b; }
+__host__ __device__ __forceinline__ bool operator<(ff a, ff b) { return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo); }
+__host__ __device__ __forceinline__ bool operator>(ff a, ff b) { return b < a; }
 
 // Compensated dot product of float-float operands (the Dot2 scheme of Ogita, Rump and Oishi,
 // "Accurate sum and dot product", 2005, with the low parts' cross products added by FMA): the
@@ -188,7 +191,7 @@ __device__ __forceinline__ bool operator>(ff a, ff b) { return b < a; }
 // arithmetic above, in about two thirds of its instructions per term.
 struct ff_dot {
   float s = 0.f, err = 0.f, lo = 0.f;
-  __device__ __forceinline__ void add(ff m, ff v) {
+  __host__ __device__ __forceinline__ void add(ff m, ff v) {
     const float p = m.hi * v.hi;
     const float ep = fmaf(m.hi, v.hi, -p);
     const float t = s + p;
@@ -198,7 +201,7 @@ struct ff_dot {
     err += es + ep;
     lo = fmaf(m.hi, v.lo, fmaf(m.lo, v.hi, lo));
   }
-  __device__ __forceinline__ ff value() const {
+  __host__ __device__ __forceinline__ ff value() const {
     const float t = s + (err + lo);
     return ff(t, (err + lo) - (t - s));
   }
