@@ -118,9 +118,14 @@ typedef struct {
    Returns IMEX_EINVAL for an unsupported mesh (dim, P range, nelem < 1) and IMEX_ENOMEM if
    the device state does not fit.  The default method is RK-CB3e, nu = 0, no forcing. */
 imex_status imex_create(const imex_mesh_desc* desc, imex_ctx** out);
+/* frees every device and pinned host buffer of the context after its stream has finished
+   (NULL: nothing) */
 void imex_destroy(imex_ctx* ctx);
+/* message of the context's last failed call; owned by the context, valid until its next
+   call */
 const char* imex_last_error(const imex_ctx* ctx);
-/* velocity nodes per component and pressure nodes */
+/* velocity nodes per component, N_e (P+1)^d, and pressure nodes, N_e P^d (the Q_P / Q_{P-1}
+   pair of Sec. 3.3) */
 imex_status imex_sizes(const imex_ctx* ctx, long long* nvel, long long* npres);
 
 /* IMEX RK tableau in the CK form of Eq. (imex-rk:butcher), row-major s x s arrays:
@@ -156,17 +161,31 @@ imex_status imex_set_stabilization(imex_ctx* ctx, double zeta_d, double zeta_c);
 /* out = v~ of the stabilisation above applied to the velocity v (d blocks) with time step dt;
    IMEX_EINVAL while the stabilisation is off */
 imex_status imex_stabilize(imex_ctx* ctx, const double* v, double dt, double* out, int on_device);
+/* The viscosity nu(x, t, v) of Eq. (momentum), Sec. 3.1.  Constant: nu >= 0 (IMEX_EINVAL
+   otherwise).  Model: IMEX_NU_CONST {nu_0}; IMEX_NU_VARXYT {nu_0}, the nu(x, y, t) of the
+   manufactured flow of Sec. 4.1; IMEX_NU_VELOCITY {nu_0, nu_1, v_max}, the law of Sec. 4.2,
+   treated semi-implicitly as Alg. 2 / Alg. 3 prescribe (stage viscosities from the projected
+   velocities).  IMEX_EINVAL for another kind, more than 8 parameters or v_max <= 0. */
 imex_status imex_set_viscosity_const(imex_ctx* ctx, double nu);
 imex_status imex_set_viscosity_model(imex_ctx* ctx, int kind, const double* params, int nparams);
-/* nodal viscosity field (used as a fixed nu(x)); copied into the context */
+/* nodal viscosity field (nvel doubles, used as a fixed nu(x) in Eq. (momentum)); copied into
+   the context; IMEX_EINVAL for a NULL field */
 imex_status imex_set_viscosity_field(imex_ctx* ctx, const double* nu, int on_device);
-/* Dirichlet data v_b(x, t) on non-periodic boundaries: a closed-form flow (IMEX_FLOW_*) */
+/* Dirichlet data v_b(x, t) of Eq. (bc) on non-periodic boundaries: a closed-form flow
+   (IMEX_FLOW_*, at most 8 parameters), evaluated on the device at every stage time; a
+   non-periodic mesh needs it before imex_step.  IMEX_EINVAL for an unknown kind. */
 imex_status imex_set_boundary(imex_ctx* ctx, int kind, const double* params, int nparams);
+/* forcing f of Eq. (momentum): IMEX_FORCE_* with its parameters, evaluated on the device at
+   every stage time (F_s of Alg. 3).  IMEX_EINVAL for an unknown kind or a forcing of the
+   other dimension (IMEX_FORCE_TGTRAVEL_VARNU is 2D, IMEX_FORCE_VV 3D). */
 imex_status imex_set_forcing(imex_ctx* ctx, int kind, const double* params, int nparams);
 
-/* velocity state (d * nvel doubles) at time t; copied into the context */
+/* the initial condition of Eq. (ic): velocity state (d * nvel doubles, layout above) at time
+   t, copied into the context; restarts BDF2 with its Euler step */
 imex_status imex_set_state(imex_ctx* ctx, double t, const double* v, int on_device);
-/* velocity state from a closed-form flow evaluated on the device at time t */
+/* the initial condition of Eq. (ic) from a closed-form flow of Sec. 4 evaluated on the device
+   at time t (IMEX_FLOW_TG3D: Eq. (transition:v0) at the shifted point; IMEX_FLOW_VV: Eq.
+   (var-visc-test)); IMEX_EINVAL for an unknown kind */
 imex_status imex_init_flow(imex_ctx* ctx, int kind, const double* params, int nparams, double t);
 
 /* Advance nsteps steps of size dt (Alg. 3 per step, or Alg. 4 after imex_set_sdc).
@@ -174,15 +193,22 @@ imex_status imex_init_flow(imex_ctx* ctx, int kind, const double* params, int np
    IMEX_EUNSTABLE: NaN or max |v| > vmax after a step. */
 imex_status imex_step(imex_ctx* ctx, double dt, int nsteps);
 
+/* the velocity v of Eq. (momentum) at the context's time (d * nvel doubles, layout above) */
 imex_status imex_get_velocity(imex_ctx* ctx, double* out, int on_device);
 /* psi'' of the last stage projection (Alg. 3 / Alg. 4), mass-weighted mean removed */
 imex_status imex_get_pressure(imex_ctx* ctx, double* out, int on_device);
+/* the context's time t^n */
 imex_status imex_get_time(const imex_ctx* ctx, double* t);
+/* solver statistics of the last imex_step call (iterations, the final relative residuals
+   ||r|| / ||b|| of Sec. 4's stopping rule) and counters since creation; every call returns
+   IMEX_EINVAL for NULL arguments */
 imex_status imex_get_stats(const imex_ctx* ctx, imex_stats* out);
 
 /* ---- operator-level entry points (same discretisation, for composition and testing) ---- */
 
-/* y = alpha M x + beta (A(nu) x - r_b(g)), optionally multiplied by M^{-1} (minv = 1).
+/* The SIPG operator of Sec. 3.3 (F_d1 = -M^{-1}(A(nu) v - r_b(v_b)) of Alg. 3, the Helmholtz
+   operator of its implicit stage, the pressure operator of its projection):
+   y = alpha M x + beta (A(nu) x - r_b(g)), optionally multiplied by M^{-1} (minv = 1).
    space: IMEX_SPACE_VELOCITY (degree P, Dirichlet faces on non-periodic sides, nsys
    components) or IMEX_SPACE_PRESSURE (degree P-1, nu = 1, Neumann faces, nsys = 1).
    nu: nodal viscosity (velocity space) or NULL for the context's constant viscosity.
@@ -198,15 +224,20 @@ imex_status imex_op_sipg_diag(imex_ctx* ctx, int space, double* y, double alpha,
 /* The four operators below take `arith` = IMEX_ARITH_FP64 or IMEX_ARITH_FF (float-float on
    FP64 fields, the form IMEX_MIXED steps with); imex_op_conv also IMEX_ARITH_FP32 (the
    convection of IMEX_MIXED_FAST).  Other values: IMEX_EINVAL. */
-/* b = B v - int_{dOmega} (n . w) q: mode 0 no boundary term, 1 w = wdata, 2 w = v (trace) */
+/* the right-hand side of the projection's Poisson problem (Alg. 3, Sec. 3.3):
+   b = B v - int_{dOmega} (n . w) q: mode 0 no boundary term, 1 w = wdata, 2 w = v (trace) */
 imex_status imex_op_div(imex_ctx* ctx, const double* v, const double* wdata, int mode, double* b,
                         int arith, int on_device);
-/* out = M^{-1} B^T psi (DG gradient of a pressure field, d blocks) */
+/* the projection's correction v'' = v' - grad psi of Alg. 3 uses out = M^{-1} B^T psi (DG
+   gradient of a pressure field, d blocks) */
 imex_status imex_op_grad(imex_ctx* ctx, const double* psi, double* out, int arith, int on_device);
-/* out = F_c(v) = -div(v v) with LLF flux; vb: Dirichlet data or NULL */
+/* the convective term of Eq. (momentum) as Sec. 3.3 discretises it: out = F_c(v) =
+   -M^{-1} div(v v) with the local Lax-Friedrichs flux and over-integration on Gauss points;
+   vb: Dirichlet data (d blocks) or NULL */
 imex_status imex_op_conv(imex_ctx* ctx, const double* v, const double* vb, double* out, int arith,
                          int on_device);
-/* out = F_d3 = -grad(nu div v) and, if out2 != NULL, out2 = F_d2 = div(nu (grad v)^T) */
+/* the parts of the viscous term of Sec. 3.2 that Alg. 3 treats explicitly: out = F_d3 =
+   -grad(nu div v) and, if out2 != NULL, out2 = F_d2 = div(nu (grad v)^T) */
 imex_status imex_op_graddiv(imex_ctx* ctx, const double* v, const double* nu, double* out_fd3,
                             double* out_fd2, int arith, int on_device);
 /* Preconditioner of the pressure Poisson solves (Sec. 3.3 solves them by preconditioned CG;
@@ -236,9 +267,11 @@ imex_status imex_pmg_info(imex_ctx* ctx, int* nlev, int* N, double* lmax);
    to use instead of the context's (nlev entries), or NULL. */
 imex_status imex_op_pmg_vcycle(imex_ctx* ctx, const double* r, double* z, const double* lmax, int arith,
                                int on_device);
-/* Poisson solve L psi = b - mean(b) with the context's pressure operator; psi mean-free */
+/* the projection's Poisson solve of Alg. 3: L psi = b - mean(b) with the context's pressure
+   operator and preconditioner; psi mean-free; IMEX_ENOTCONV at maxit */
 imex_status imex_solve_poisson(imex_ctx* ctx, const double* b, double* psi, int on_device);
-/* Helmholtz solve (M + gamma A(nu)) v = M g + gamma r_b(nu, vb) for all d components */
+/* the implicit viscous solve of an Alg. 3 stage: (M + gamma A(nu)) v = M g + gamma
+   r_b(nu, vb) for all d components (gamma = dt a^IM_ii); IMEX_ENOTCONV at maxit */
 imex_status imex_solve_helmholtz(imex_ctx* ctx, const double* g, const double* nu, double gamma,
                                  const double* vb, double* v, int on_device);
 /* nodal evaluation: what 0 flow velocity (kind IMEX_FLOW_*), 1 viscosity law (IMEX_NU_*, v may
