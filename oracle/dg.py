@@ -39,7 +39,8 @@ from . import gll
 # mesh
 # ----------------------------------------------------------------------------
 class Mesh:
-    """Cartesian box [lo, hi] split into n[0] x ... x n[d-1] equal elements.
+    """Cartesian box [lo, hi] split into n[0] x ... x n[d-1] equal elements (the hexahedral /
+    quadrilateral meshes of Sec. 3.3 on the boxes of Sec. 4).
 
     periodic[k]: True for a periodic direction; a non-periodic direction has
     Dirichlet velocity data (and Neumann pressure data) on both of its ends.
@@ -96,7 +97,8 @@ class Mesh:
 
 
 def node_multi_indices(N, d):
-    """(i_0, ..., i_{d-1}) for the lexicographic node order with i_0 fastest."""
+    """(i_0, ..., i_{d-1}) for the lexicographic node order with i_0 fastest (the tensor-product
+    GLL nodes of Sec. 3.3)."""
     out = []
     for flat in range(N ** d):
         idx = []
@@ -108,7 +110,8 @@ def node_multi_indices(N, d):
 
 
 def kron_dims(mats):
-    """Kronecker product with mats[0] acting on the fastest (x) index."""
+    """Kronecker product with mats[0] acting on the fastest (x) index (the tensor-product
+    element matrices of Sec. 3.3 on affine elements)."""
     out = np.array([[1.0]])
     for m in mats:
         out = np.kron(m, out)
@@ -123,7 +126,8 @@ def face_nodes(N, d, k, side):
 
 
 def face_weights(mesh, N, k):
-    """GLL quadrature weights (with the face Jacobian) of the nodes of a face normal to k."""
+    """GLL quadrature weights (with the face Jacobian) of the nodes of a face normal to k (the
+    face integrals of Sec. 3.3 on GLL points; R3, R5)."""
     _, w = gll.gll_nodes_weights(N)
     mats = []
     for j in range(mesh.d):
@@ -136,12 +140,14 @@ def face_weights(mesh, N, k):
 
 
 def volume_weights(mesh, N):
+    """GLL volume quadrature weights of one element's nodes (R2: collocation quadrature)."""
     _, w = gll.gll_nodes_weights(N)
     return np.diag(kron_dims([np.diag(w * mesh.h[k] / 2.0) for k in range(mesh.d)]))
 
 
 def grad_mats(mesh, N):
-    """G[k] (N^d x N^d): nodal values of d/dx_k of the element's Lagrange basis."""
+    """G[k] (N^d x N^d): nodal values of d/dx_k of the element's Lagrange basis (the GLL
+    basis of Sec. 3.3)."""
     xi, _ = gll.gll_nodes_weights(N)
     Dh = gll.lagrange_eval(xi, xi, deriv=1)
     I = np.eye(N)
@@ -153,11 +159,12 @@ def grad_mats(mesh, N):
 
 
 def mass_diag(mesh, N):
-    """Diagonal of the GLL mass matrix, whole mesh."""
+    """Diagonal of the GLL mass matrix, whole mesh (R2)."""
     return np.tile(volume_weights(mesh, N), mesh.ne)
 
 
 def _bc_kind(mesh, k, velocity):
+    """Face kind of direction k: periodic, Dirichlet velocity (Eq. (bc)) or Neumann pressure (R4)."""
     if mesh.periodic[k]:
         return "periodic"
     return "dirichlet" if velocity else "neumann"
@@ -167,7 +174,8 @@ def _bc_kind(mesh, k, velocity):
 # SIPG
 # ----------------------------------------------------------------------------
 def sipg_matrix(mesh, N, nu, dirichlet=True):
-    """Assembled SIPG matrix A with a(u, w) = w^T A u.
+    """Assembled SIPG matrix A with a(u, w) = w^T A u (the interior penalty form of Sec. 3.3 for
+    -div(nu grad u); penalty of R3).
 
     nu: scalar or nodal array (ne * N^d).  dirichlet: non-periodic directions
     carry Dirichlet faces (velocity problems); False gives homogeneous Neumann
@@ -244,7 +252,8 @@ def sipg_matrix(mesh, N, nu, dirichlet=True):
 
 
 def sipg_dirichlet_rhs(mesh, N, nu, g):
-    """r_b(w) = sum over Dirichlet faces of int (-nu dn w g + 2 tau g w) (Nitsche data term).
+    """r_b(w) = sum over Dirichlet faces of int (-nu dn w g + 2 tau g w) (Nitsche data term of
+    the SIPG form of Sec. 3.3 with the data v_b of Eq. (bc); R3).
 
     g: nodal array (ne * N^d); only its values on Dirichlet-face nodes are used.
     """
@@ -278,7 +287,8 @@ def sipg_dirichlet_rhs(mesh, N, nu, g):
 # divergence / gradient between Q_P (velocity) and Q_{P-1} (pressure)
 # ----------------------------------------------------------------------------
 def div_matrix(mesh, Nv, Np):
-    """B with B(v, q) = q^T B v, v = [v_0; ...; v_{d-1}] (component-major).
+    """B with B(v, q) = q^T B v, v = [v_0; ...; v_{d-1}] (component-major): the weak divergence
+    of the projection's Poisson problem (Alg. 3, Sec. 3.3; R5).
 
     B(v, q) = sum_K sum_x W_x v(x).grad q(x) - sum_{interior F} sum_f W_f {v}.n [q],
     quadrature on the velocity GLL(Nv) points (exact for affine elements).
@@ -331,7 +341,8 @@ def div_matrix(mesh, Nv, Np):
 
 
 def div_boundary_vector(mesh, Nv, Np, vb):
-    """int over the Dirichlet boundary of (n . v_b) q for every pressure test function q.
+    """int over the Dirichlet boundary of (n . v_b) q for every pressure test function q (the
+    boundary flux of the projection's Poisson right-hand side, Alg. 3; R5).
 
     vb: (d, ne*Nv^d) nodal boundary velocity (only face values are used).
     """
@@ -362,7 +373,8 @@ def div_boundary_vector(mesh, Nv, Np, vb):
 # nodal DG derivative (grad-div terms)
 # ----------------------------------------------------------------------------
 def dg_derivative_matrix(mesh, N, k):
-    """Nodal DG derivative along x_k:  M (Dk u) = w-weak form
+    """Nodal DG derivative along x_k (R9: the derivatives of F_d2, F_d3 of Sec. 3.2):
+    M (Dk u) = w-weak form
         -sum_K int u d_k w + sum_{interior F} int {u} [w]_k + sum_{boundary} int u n_k w,
     i.e. central flux inside, the element's own trace on the domain boundary."""
     d = mesh.d
@@ -409,7 +421,8 @@ def dg_derivative_matrix(mesh, N, k):
 # convection with LLF flux and over-integration
 # ----------------------------------------------------------------------------
 class Convection:
-    """M F_c(v) = sum_K int (v v) : grad w - sum_F int H(v-, v+, n) . w, with
+    """The convective term F_c of Sec. 3.2 as Sec. 3.3 discretises it (R7, R8):
+    M F_c(v) = sum_K int (v v) : grad w - sum_F int H(v-, v+, n) . w, with
     H = 1/2 (v- (v-.n) + v+ (v+.n)) + 1/2 lambda (v- - v+),
     lambda = max(|v-.n|, |v+.n|) pointwise, volume and face integrals on
     Q = ceil(3(P+1)/2) Gauss points per direction; v+ = v_b on Dirichlet faces."""

@@ -29,17 +29,22 @@ TWO_PI = 2.0 * np.pi
 
 
 def tg2d_velocity(X, t, nu):
+    """Decaying 2D Taylor-Green velocity, an exact solution of Eqs. (momentum), (continuity) of
+    Sec. 3.1 with constant nu (the 2D periodic test flow; R18)."""
     x, y = X[..., 0], X[..., 1]
     F = np.exp(-2.0 * nu * t)
     return np.stack([np.sin(x) * np.cos(y) * F, -np.cos(x) * np.sin(y) * F])
 
 
 def tg2d_pressure(X, t, nu):
+    """Pressure of the decaying 2D Taylor-Green vortex (R18), mean-free."""
     x, y = X[..., 0], X[..., 1]
     return 0.25 * (np.cos(2 * x) + np.cos(2 * y)) * np.exp(-4.0 * nu * t)
 
 
 def tg3d_velocity(X):
+    """Initial field of the Taylor-Green transition, Eq. (transition:v0) of Sec. 4.3, at the
+    point shifted by -pi/2 in x and +pi/2 in y and z (R18)."""
     x, y, z = X[..., 0], X[..., 1], X[..., 2]
     return np.stack([np.sin(x) * np.cos(y) * np.cos(z),
                      -np.cos(x) * np.sin(y) * np.cos(z),
@@ -47,6 +52,8 @@ def tg3d_velocity(X):
 
 
 def tgtravel_velocity(X, t, nu0):
+    """Traveling Taylor-Green vortex of Sec. 4.1 on [0, 1]^2: phase speed 1 in x and y,
+    decay rate 8 pi^2 nu_0 (R18)."""
     x, y = X[..., 0], X[..., 1]
     a = TWO_PI * (x - t)
     b = TWO_PI * (y - 0.125 - t)
@@ -69,11 +76,14 @@ def tgtravel_grad(X, t, nu0):
 
 
 def nu_varxyt(X, t, nu0):
+    """Viscosity nu(x, y, t) = nu_0 (1 + sin 2 pi x sin 2 pi y cos t / 2) of the manufactured
+    variable-viscosity flow (Sec. 4.1 pattern; R18)."""
     x, y = X[..., 0], X[..., 1]
     return nu0 * (1.0 + 0.5 * np.sin(TWO_PI * x) * np.sin(TWO_PI * y) * np.cos(t))
 
 
 def nu_varxyt_grad(X, t, nu0):
+    """Spatial gradient of nu_varxyt."""
     x, y = X[..., 0], X[..., 1]
     c = 0.5 * nu0 * np.cos(t) * TWO_PI
     return np.stack([c * np.cos(TWO_PI * x) * np.sin(TWO_PI * y),
@@ -81,6 +91,9 @@ def nu_varxyt_grad(X, t, nu0):
 
 
 def forcing_tgtravel_varnu(X, t, nu0):
+    """Forcing that keeps the traveling vortex exact under nu(x, y, t): f = (nu_0 - nu) lap v
+    - (grad v + grad v^T) grad nu, the right-hand side of the pattern of Eq.
+    (var-visc-test:rhs) with the constant-nu_0 solution (R18)."""
     v = tgtravel_velocity(X, t, nu0)
     lap = -8.0 * np.pi ** 2 * (v - 1.0)          # Laplacian of the oscillating part
     nu = nu_varxyt(X, t, nu0)
@@ -95,6 +108,8 @@ def forcing_tgtravel_varnu(X, t, nu0):
 
 
 def vv_velocity(X, t):
+    """Travelling 3D vortex array of Sec. 4.2, Eq. (var-visc-test): wave length 1, phase speed
+    1 in each direction, maximum speed 2."""
     A, B, Cz = (TWO_PI * (X[..., k] + t) for k in range(3))
     return np.stack([(np.sin(A) + np.cos(B)) * np.sin(Cz),
                      (np.cos(A) + np.sin(B)) * np.sin(Cz),
@@ -102,6 +117,7 @@ def vv_velocity(X, t):
 
 
 def vv_pressure(X, t):
+    """Pressure of the vortex array, Eq. (var-visc-test:p)."""
     A, B, Cz = (TWO_PI * (X[..., k] + t) for k in range(3))
     return np.sin(A) * np.sin(B) * np.sin(Cz)
 
@@ -119,6 +135,8 @@ def vv_grad(X, t):
 
 
 def forcing_vv(X, t, nu0, nu1, vmax):
+    """Forcing of Eq. (var-visc-test:rhs) for the vortex array under nu(v) = nu_0 + nu_1
+    (|v| / v_max)^2 (Sec. 4.2), in closed form with div v = 0 (R27)."""
     v = vv_velocity(X, t)
     G = vv_grad(X, t)
     k = TWO_PI
@@ -148,9 +166,11 @@ class Flow:
 
     # --- viscosity ------------------------------------------------------
     def variable_nu(self):
+        """True unless nu is constant (Alg. 2 / Alg. 3 then update nu per stage)."""
         return self.nu_kind != "const"
 
     def nu(self, X, t, v):
+        """The viscosity law nu(x, t, v) of Eq. (momentum) at the points X (Sec. 3.1, 4.1, 4.2)."""
         if self.nu_kind == "const":
             return np.full(X.shape[:-1], self.nu0)
         if self.nu_kind == "varxyt":
@@ -162,6 +182,7 @@ class Flow:
 
     # --- fields -----------------------------------------------------------
     def exact(self, X, t):
+        """The closed-form velocity at time t (the reference of the error and order pins)."""
         if self.kind == "tg2d":
             return tg2d_velocity(X, t, self.nu0)
         if self.kind == "tgtravel":
@@ -175,15 +196,19 @@ class Flow:
         raise ValueError(self.kind)
 
     def initial(self, X):
+        """Initial condition, Eq. (ic)."""
         return self.exact(X, 0.0)
 
     def boundary(self, X, t):
+        """Dirichlet data v_b of Eq. (bc): the closed form on the boundary."""
         return self.exact(X, t)
 
     def has_forcing(self):
+        """Whether the case carries a manufactured forcing f (Eq. (momentum))."""
         return (self.kind == "tgtravel" and self.nu_kind == "varxyt") or self.kind == "vv"
 
     def forcing(self, X, t):
+        """The forcing f of Eq. (momentum) at the points X, d components."""
         if self.kind == "vv":
             return forcing_vv(X, t, self.nu0, self.nu1, self.vmax)
         if self.has_forcing():

@@ -22,7 +22,8 @@ from numpy.polynomial import polynomial as nppoly
 
 
 def gll_nodes_weights(n):
-    """n >= 2 GLL points on [-1, 1] (degree P = n-1) and their quadrature weights."""
+    """n >= 2 GLL points on [-1, 1] (degree P = n-1) and their quadrature weights (the nodes of
+    the basis of Sec. 3.3; R1, R2)."""
     if n < 2:
         raise ValueError("GLL rule needs at least two points")
     p = n - 1
@@ -34,13 +35,15 @@ def gll_nodes_weights(n):
 
 
 def gauss_nodes_weights(q):
-    """q Gauss-Legendre points and weights on [-1, 1]."""
+    """q Gauss-Legendre points and weights on [-1, 1] (the consistent integration of the
+    convective term, Sec. 3.3; R7)."""
     x, w = npleg.leggauss(q)
     return x, w
 
 
 def lagrange_polys(nodes):
-    """Power-basis coefficients of the Lagrange cardinal polynomials on ``nodes``."""
+    """Power-basis coefficients of the Lagrange cardinal polynomials on ``nodes`` (the nodal
+    basis of Sec. 3.3)."""
     nodes = np.asarray(nodes, dtype=np.float64)
     polys = []
     for j, xj in enumerate(nodes):
@@ -52,7 +55,8 @@ def lagrange_polys(nodes):
 
 
 def lagrange_eval(nodes, pts, deriv=0):
-    """Matrix E[i, j] = l_j^{(deriv)}(pts[i]) for the cardinal polynomials on ``nodes``."""
+    """Matrix E[i, j] = l_j^{(deriv)}(pts[i]) for the cardinal polynomials on ``nodes`` (Sec. 3.3:
+    differentiation, interpolation between the P-1 and P bases (R1) and to the Gauss points (R7))."""
     pts = np.asarray(pts, dtype=np.float64)
     polys = lagrange_polys(nodes)
     E = np.zeros((len(pts), len(polys)))
@@ -65,7 +69,8 @@ def lagrange_eval(nodes, pts, deriv=0):
 
 
 def lagrange_integrals(nodes, a, b):
-    """int_a^b l_j(t) dt for every cardinal polynomial on ``nodes`` (exact polynomial integral)."""
+    """int_a^b l_j(t) dt for every cardinal polynomial on ``nodes`` (exact polynomial integral;
+    the SDC quadrature weights of Sec. 2.4, R12)."""
     out = []
     for c in lagrange_polys(nodes):
         ci = nppoly.polyint(c)

@@ -29,6 +29,10 @@ from .tableaux import get as get_tableau
 
 
 class Discretization:
+    """The DG-SEM discretisation of Sec. 3.3 on a mesh: GLL velocity space of degree P and
+    pressure space of degree P-1 (R1), the assembled operators of Sec. 3.2's splitting of
+    the right-hand side and the pressure Poisson operator of the projection (R4)."""
+
     def __init__(self, mesh, flow, poisson="sipg", stab=None):
         if mesh.P < 2:
             raise ValueError("velocity degree P must be at least 2")
@@ -65,22 +69,27 @@ class Discretization:
 
     # ------------------------------------------------------------------ fields
     def nodal(self, field_fn, t):
+        """A closed-form field at the velocity nodes, d blocks."""
         return np.asarray(field_fn(self.X, t)).reshape(self.d, -1) if field_fn else None
 
     def nu_field(self, t, v):
+        """Nodal viscosity nu(x, t, v) of Eq. (momentum) (Alg. 3: the stage viscosity)."""
         X = self.X
         return np.asarray(self.flow.nu(X, t, np.asarray(v).reshape(self.d, *X.shape[:-1]))).ravel()
 
     def vb(self, t):
+        """Nodal Dirichlet data v_b(t) of Eq. (bc), or None on a periodic mesh."""
         if not self.has_boundary:
             return None
         return np.asarray(self.flow.boundary(self.X, t)).reshape(self.d, -1)
 
     def fs(self, t):
+        """F_s = f(x, t) of Sec. 3.2's splitting at the velocity nodes."""
         return np.asarray(self.flow.forcing(self.X, t)).reshape(self.d, -1)
 
     # -------------------------------------------------------------- operators
     def A(self, nu):
+        """The assembled SIPG matrix of the viscous operator (Sec. 3.3, R3) for nodal nu."""
         if not self.flow.variable_nu():
             if self._A_const is None:
                 self._A_const = dg.sipg_matrix(self.mesh, self.Nv, self.flow.nu0, dirichlet=True)
@@ -88,9 +97,11 @@ class Discretization:
         return dg.sipg_matrix(self.mesh, self.Nv, nu, dirichlet=True)
 
     def Fc(self, v, vb):
+        """F_c = -div(v v) of Sec. 3.2 (LLF flux, over-integration; R7, R8)."""
         return self.conv(v, vb)
 
     def Fd1(self, v, nu, vb, A=None):
+        """F_d1 = div(nu grad v) of Sec. 3.2 = -M^{-1}(A(nu) v - r_b(nu, v_b)) (SIPG)."""
         A = self.A(nu) if A is None else A
         out = np.empty((self.d, self.nv))
         for c in range(self.d):
@@ -101,13 +112,16 @@ class Discretization:
         return out
 
     def divergence_nodal(self, v):
+        """sum_k D_k v_k, the nodal DG divergence (R9)."""
         return sum(self.Dk[k] @ v[k] for k in range(self.d))
 
     def Fd3(self, v, nu):
+        """F_d3 = -grad(nu div v) of Sec. 3.2 with the nodal DG derivatives (R9)."""
         phi = nu * self.divergence_nodal(v)
         return np.stack([-(self.Dk[c] @ phi) for c in range(self.d)])
 
     def Fd2(self, v, nu):
+        """F_d2 = div(nu (grad v)^T) of Sec. 3.2 with the nodal DG derivatives (R9)."""
         out = np.zeros((self.d, self.nv))
         for c in range(self.d):
             for k in range(self.d):
@@ -123,6 +137,7 @@ class Discretization:
         return stabilize(self.mesh, v, dt, *self.stab)
 
     def grad_p(self, psi):
+        """G psi = M^{-1} B^T psi, the DG gradient of the projection's correction (Alg. 3; R6)."""
         g = self.BT @ psi
         return g.reshape(self.d, self.nv) / self.Mv[None, :]
 
@@ -251,6 +266,7 @@ def sdc_step(disc, M, K, predictor, v, t, dt, final_projection=None):
         vk.append(vn)
 
     def f_ex(vm, num, tq):
+        """F(t_q, v_q) = F_c + F_d1 + F_d2 + F_d3 + F_s at one sub-node (R13)."""
         vb = disc.vb(tq)
         return disc.Fc(vm, vb) + disc.Fd2(vm, num) + disc.Fd3(vm, num)
 
@@ -292,10 +308,12 @@ def sdc_step(disc, M, K, predictor, v, t, dt, final_projection=None):
 
 
 def rms(x):
+    """Root mean square (the norm of Sec. 4's residuals and errors)."""
     return float(np.sqrt(np.mean(np.asarray(x) ** 2)))
 
 
 def relative_l2(a, b):
+    """||a - b|| / ||b|| (the relative L2 error of Sec. 4)."""
     return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
 
 

@@ -112,6 +112,7 @@ def sdc_step(M, K, predictor, u, dt, fc, fd, solve_d):
 
 
 def linear_problem(lc, ld):
+    """f_c, f_d and the implicit solve of the linear test equation, Eq. (conv-diff:ode) of Sec. 2.1."""
     fc = lambda u: lc * u
     fd = lambda u: ld * u
     solve = lambda rhs, g: rhs / (1.0 - g * ld)
@@ -119,7 +120,7 @@ def linear_problem(lc, ld):
 
 
 def method_step(method):
-    """Return step(u, dt, lc, ld) for 'RK-<name>' or 'SDC-<pred>(M,K)'."""
+    """Return step(u, dt, lc, ld) for 'RK-<name>' (Alg. 1) or 'SDC-<pred>(M,K)' (Sec. 2.4)."""
     name = method.strip()
     if name.upper().startswith("SDC-"):
         inner = name[4:]

@@ -25,7 +25,8 @@ from . import dg, gll
 
 
 def mean_speed(mesh, v):
-    """|u_K|: magnitude of the mass-weighted mean velocity of every element."""
+    """|u_K|: magnitude of the mass-weighted mean velocity of every element (the speed in the
+    penalty factors of R25)."""
     N = mesh.P + 1
     W = dg.volume_weights(mesh, N)
     u = np.asarray(v).reshape(mesh.d, mesh.ne, -1)
@@ -34,7 +35,8 @@ def mean_speed(mesh, v):
 
 
 def penalty_matrix(mesh, v, dt, zeta_d, zeta_c):
-    """A_D + A_C (d components, component-major) for the element speeds of v."""
+    """A_D + A_C (d components, component-major) for the element speeds of v: the divergence and
+    normal-jump penalties of the stabilisation Sec. 3.3 adds (R25)."""
     d, N = mesh.d, mesh.P + 1
     nd = N ** d
     nv = mesh.ne * nd
@@ -84,7 +86,8 @@ def penalty_matrix(mesh, v, dt, zeta_d, zeta_c):
 
 
 def stabilize(mesh, v, dt, zeta_d, zeta_c):
-    """v~ = (M + A_D + A_C)^{-1} M v for the velocity v ([d][nv])."""
+    """v~ = (M + A_D + A_C)^{-1} M v for the velocity v ([d][nv]): the stabilised projection
+    (Sec. 3.3; R25)."""
     d = mesh.d
     M = np.tile(dg.mass_diag(mesh, mesh.P + 1), d)
     A = (sp.diags(M) + penalty_matrix(mesh, v, dt, zeta_d, zeta_c)).tocsc()

@@ -31,6 +31,7 @@ class Tableau:
         self.order = order
 
     def as_float(self):
+        """The coefficients of Eq. (imex-rk:butcher) as floats: c, A^IM, b^IM, A^EX, b^EX."""
         f = float
         return ([f(x) for x in self.c], [[f(x) for x in r] for r in self.AI],
                 [f(x) for x in self.bI], [[f(x) for x in r] for r in self.AE],
@@ -46,6 +47,7 @@ def _lower(rows, s):
 
 
 def _F(p, q):
+    """The exact rational p / q of a printed coefficient."""
     return Fr(p, q)
 
 
@@ -157,6 +159,7 @@ TABLEAUX = {t.name: t for t in (RK_TR, RK_CB2, RK_CB3C, RK_CB3E, RK_CB4, RK_ARS3
 
 
 def get(name):
+    """The tableau of the appendix (or IMEX Euler) by name, with or without the "RK-" prefix."""
     key = name.upper().replace("RK-", "")
     for k, t in TABLEAUX.items():
         if k.upper() == key:
