@@ -127,7 +127,7 @@ def face_nodes(N, d, k, side):
 
 def face_weights(mesh, N, k):
     """GLL quadrature weights (with the face Jacobian) of the nodes of a face normal to k (the
-    face integrals of Sec. 3.3 on GLL points; R3, R5)."""
+    face integrals of Sec. 3.3 on GLL points)."""
     _, w = gll.gll_nodes_weights(N)
     mats = []
     for j in range(mesh.d):
@@ -140,7 +140,7 @@ def face_weights(mesh, N, k):
 
 
 def volume_weights(mesh, N):
-    """GLL volume quadrature weights of one element's nodes (R2: collocation quadrature)."""
+    """GLL volume quadrature weights of one element's nodes (collocation quadrature, Sec. 3.3)."""
     _, w = gll.gll_nodes_weights(N)
     return np.diag(kron_dims([np.diag(w * mesh.h[k] / 2.0) for k in range(mesh.d)]))
 
@@ -159,12 +159,12 @@ def grad_mats(mesh, N):
 
 
 def mass_diag(mesh, N):
-    """Diagonal of the GLL mass matrix, whole mesh (R2)."""
+    """Diagonal of the GLL mass matrix, whole mesh (collocation quadrature)."""
     return np.tile(volume_weights(mesh, N), mesh.ne)
 
 
 def _bc_kind(mesh, k, velocity):
-    """Face kind of direction k: periodic, Dirichlet velocity (Eq. (bc)) or Neumann pressure (R4)."""
+    """Face kind of direction k: periodic, Dirichlet velocity (Eq. (bc)) or Neumann pressure."""
     if mesh.periodic[k]:
         return "periodic"
     return "dirichlet" if velocity else "neumann"
@@ -175,7 +175,7 @@ def _bc_kind(mesh, k, velocity):
 # ----------------------------------------------------------------------------
 def sipg_matrix(mesh, N, nu, dirichlet=True):
     """Assembled SIPG matrix A with a(u, w) = w^T A u (the interior penalty form of Sec. 3.3 for
-    -div(nu grad u); penalty of R3).
+    -div(nu grad u); penalty N^2 / h_perp max(nu-, nu+), twice that on Dirichlet faces).
 
     nu: scalar or nodal array (ne * N^d).  dirichlet: non-periodic directions
     carry Dirichlet faces (velocity problems); False gives homogeneous Neumann
@@ -253,7 +253,7 @@ def sipg_matrix(mesh, N, nu, dirichlet=True):
 
 def sipg_dirichlet_rhs(mesh, N, nu, g):
     """r_b(w) = sum over Dirichlet faces of int (-nu dn w g + 2 tau g w) (Nitsche data term of
-    the SIPG form of Sec. 3.3 with the data v_b of Eq. (bc); R3).
+    the SIPG form of Sec. 3.3 with the data v_b of Eq. (bc)).
 
     g: nodal array (ne * N^d); only its values on Dirichlet-face nodes are used.
     """
@@ -288,7 +288,7 @@ def sipg_dirichlet_rhs(mesh, N, nu, g):
 # ----------------------------------------------------------------------------
 def div_matrix(mesh, Nv, Np):
     """B with B(v, q) = q^T B v, v = [v_0; ...; v_{d-1}] (component-major): the weak divergence
-    of the projection's Poisson problem (Alg. 3, Sec. 3.3; R5).
+    of the projection's Poisson problem (Alg. 3, Sec. 3.3).
 
     B(v, q) = sum_K sum_x W_x v(x).grad q(x) - sum_{interior F} sum_f W_f {v}.n [q],
     quadrature on the velocity GLL(Nv) points (exact for affine elements).
@@ -342,7 +342,7 @@ def div_matrix(mesh, Nv, Np):
 
 def div_boundary_vector(mesh, Nv, Np, vb):
     """int over the Dirichlet boundary of (n . v_b) q for every pressure test function q (the
-    boundary flux of the projection's Poisson right-hand side, Alg. 3; R5).
+    boundary flux of the projection's Poisson right-hand side, Alg. 3).
 
     vb: (d, ne*Nv^d) nodal boundary velocity (only face values are used).
     """
@@ -373,7 +373,7 @@ def div_boundary_vector(mesh, Nv, Np, vb):
 # nodal DG derivative (grad-div terms)
 # ----------------------------------------------------------------------------
 def dg_derivative_matrix(mesh, N, k):
-    """Nodal DG derivative along x_k (R9: the derivatives of F_d2, F_d3 of Sec. 3.2):
+    """Nodal DG derivative along x_k (the derivatives of F_d2, F_d3 of Sec. 3.2):
     M (Dk u) = w-weak form
         -sum_K int u d_k w + sum_{interior F} int {u} [w]_k + sum_{boundary} int u n_k w,
     i.e. central flux inside, the element's own trace on the domain boundary."""
@@ -421,7 +421,7 @@ def dg_derivative_matrix(mesh, N, k):
 # convection with LLF flux and over-integration
 # ----------------------------------------------------------------------------
 class Convection:
-    """The convective term F_c of Sec. 3.2 as Sec. 3.3 discretises it (R7, R8):
+    """The convective term F_c of Sec. 3.2 as Sec. 3.3 discretises it:
     M F_c(v) = sum_K int (v v) : grad w - sum_F int H(v-, v+, n) . w, with
     H = 1/2 (v- (v-.n) + v+ (v+.n)) + 1/2 lambda (v- - v+),
     lambda = max(|v-.n|, |v+.n|) pointwise, volume and face integrals on

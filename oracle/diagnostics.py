@@ -22,7 +22,7 @@ from . import dg, gll
 
 def dissipation(mesh, v, nu):
     """eps of the velocity v ([d][ne * N^d]) with nodal (or constant) viscosity nu: the
-    dissipation rate of Sec. 4.3 (R26)."""
+    dissipation rate of Sec. 4.3 (broken gradient, GLL quadrature)."""
     d, N = mesh.d, mesh.P + 1
     D = gll.lagrange_eval(gll.gll_nodes_weights(N)[0], gll.gll_nodes_weights(N)[0], deriv=1)
     I = np.eye(N)
@@ -41,7 +41,7 @@ def dissipation(mesh, v, nu):
 
 def regular_grid(mesh, v, M):
     """v interpolated to the M^d regular grid, shape (d, M, ..., M) with x the last axis (the
-    grid of the energy spectrum of Sec. 4.3; R26)."""
+    grid of the energy spectrum of Sec. 4.3)."""
     d, N = mesh.d, mesh.P + 1
     xg, _ = gll.gll_nodes_weights(N)
     v = np.asarray(v).reshape(d, mesh.ne, *([N] * d))      # [c][e][z][y][x] (x fastest)
@@ -68,7 +68,7 @@ def regular_grid(mesh, v, M):
 
 def energy_spectrum(mesh, v, M, kmax):
     """E(0..kmax-1) of the velocity v on an M^d regular grid: the energy spectrum of Sec. 4.3
-    (R26)."""
+    (shells k - 1/2 <= |n| < k + 1/2)."""
     d = mesh.d
     grid = regular_grid(mesh, v, M)
     vol = np.prod([mesh.hi[k] - mesh.lo[k] for k in range(d)])

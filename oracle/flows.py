@@ -30,21 +30,21 @@ TWO_PI = 2.0 * np.pi
 
 def tg2d_velocity(X, t, nu):
     """Decaying 2D Taylor-Green velocity, an exact solution of Eqs. (momentum), (continuity) of
-    Sec. 3.1 with constant nu (the 2D periodic test flow; R18)."""
+    Sec. 3.1 with constant nu (the 2D periodic test flow)."""
     x, y = X[..., 0], X[..., 1]
     F = np.exp(-2.0 * nu * t)
     return np.stack([np.sin(x) * np.cos(y) * F, -np.cos(x) * np.sin(y) * F])
 
 
 def tg2d_pressure(X, t, nu):
-    """Pressure of the decaying 2D Taylor-Green vortex (R18), mean-free."""
+    """Pressure of the decaying 2D Taylor-Green vortex, mean-free."""
     x, y = X[..., 0], X[..., 1]
     return 0.25 * (np.cos(2 * x) + np.cos(2 * y)) * np.exp(-4.0 * nu * t)
 
 
 def tg3d_velocity(X):
     """Initial field of the Taylor-Green transition, Eq. (transition:v0) of Sec. 4.3, at the
-    point shifted by -pi/2 in x and +pi/2 in y and z (R18)."""
+    point shifted by -pi/2 in x and +pi/2 in y and z."""
     x, y, z = X[..., 0], X[..., 1], X[..., 2]
     return np.stack([np.sin(x) * np.cos(y) * np.cos(z),
                      -np.cos(x) * np.sin(y) * np.cos(z),
@@ -53,7 +53,7 @@ def tg3d_velocity(X):
 
 def tgtravel_velocity(X, t, nu0):
     """Traveling Taylor-Green vortex of Sec. 4.1 on [0, 1]^2: phase speed 1 in x and y,
-    decay rate 8 pi^2 nu_0 (R18)."""
+    decay rate 8 pi^2 nu_0."""
     x, y = X[..., 0], X[..., 1]
     a = TWO_PI * (x - t)
     b = TWO_PI * (y - 0.125 - t)
@@ -77,7 +77,7 @@ def tgtravel_grad(X, t, nu0):
 
 def nu_varxyt(X, t, nu0):
     """Viscosity nu(x, y, t) = nu_0 (1 + sin 2 pi x sin 2 pi y cos t / 2) of the manufactured
-    variable-viscosity flow (Sec. 4.1 pattern; R18)."""
+    variable-viscosity flow (the pattern of Sec. 4.1)."""
     x, y = X[..., 0], X[..., 1]
     return nu0 * (1.0 + 0.5 * np.sin(TWO_PI * x) * np.sin(TWO_PI * y) * np.cos(t))
 
@@ -93,7 +93,7 @@ def nu_varxyt_grad(X, t, nu0):
 def forcing_tgtravel_varnu(X, t, nu0):
     """Forcing that keeps the traveling vortex exact under nu(x, y, t): f = (nu_0 - nu) lap v
     - (grad v + grad v^T) grad nu, the right-hand side of the pattern of Eq.
-    (var-visc-test:rhs) with the constant-nu_0 solution (R18)."""
+    (var-visc-test:rhs) with the constant-nu_0 solution."""
     v = tgtravel_velocity(X, t, nu0)
     lap = -8.0 * np.pi ** 2 * (v - 1.0)          # Laplacian of the oscillating part
     nu = nu_varxyt(X, t, nu0)
@@ -136,7 +136,7 @@ def vv_grad(X, t):
 
 def forcing_vv(X, t, nu0, nu1, vmax):
     """Forcing of Eq. (var-visc-test:rhs) for the vortex array under nu(v) = nu_0 + nu_1
-    (|v| / v_max)^2 (Sec. 4.2), in closed form with div v = 0 (R27)."""
+    (|v| / v_max)^2 (Sec. 4.2), in closed form with div v = 0."""
     v = vv_velocity(X, t)
     G = vv_grad(X, t)
     k = TWO_PI

@@ -23,7 +23,8 @@ from numpy.polynomial import polynomial as nppoly
 
 def gll_nodes_weights(n):
     """n >= 2 GLL points on [-1, 1] (degree P = n-1) and their quadrature weights (the nodes of
-    the basis of Sec. 3.3; R1, R2)."""
+    the basis of Sec. 3.3: degree P for the velocity, P-1 for the pressure; the
+    collocation mass)."""
     if n < 2:
         raise ValueError("GLL rule needs at least two points")
     p = n - 1
@@ -36,7 +37,7 @@ def gll_nodes_weights(n):
 
 def gauss_nodes_weights(q):
     """q Gauss-Legendre points and weights on [-1, 1] (the consistent integration of the
-    convective term, Sec. 3.3; R7)."""
+    convective term, Sec. 3.3: ceil(3N/2) points per direction)."""
     x, w = npleg.leggauss(q)
     return x, w
 
@@ -56,7 +57,7 @@ def lagrange_polys(nodes):
 
 def lagrange_eval(nodes, pts, deriv=0):
     """Matrix E[i, j] = l_j^{(deriv)}(pts[i]) for the cardinal polynomials on ``nodes`` (Sec. 3.3:
-    differentiation, interpolation between the P-1 and P bases (R1) and to the Gauss points (R7))."""
+    differentiation, interpolation between the P-1 and P bases and to the Gauss points)."""
     pts = np.asarray(pts, dtype=np.float64)
     polys = lagrange_polys(nodes)
     E = np.zeros((len(pts), len(polys)))
@@ -70,7 +71,7 @@ def lagrange_eval(nodes, pts, deriv=0):
 
 def lagrange_integrals(nodes, a, b):
     """int_a^b l_j(t) dt for every cardinal polynomial on ``nodes`` (exact polynomial integral;
-    the SDC quadrature weights of Sec. 2.4, R12)."""
+    the SDC quadrature weights of Sec. 2.4 over each subinterval)."""
     out = []
     for c in lagrange_polys(nodes):
         ci = nppoly.polyint(c)

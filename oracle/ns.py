@@ -30,8 +30,9 @@ from .tableaux import get as get_tableau
 
 class Discretization:
     """The DG-SEM discretisation of Sec. 3.3 on a mesh: GLL velocity space of degree P and
-    pressure space of degree P-1 (R1), the assembled operators of Sec. 3.2's splitting of
-    the right-hand side and the pressure Poisson operator of the projection (R4)."""
+    pressure space of degree P-1, the assembled operators of Sec. 3.2's splitting of
+    the right-hand side and the pressure Poisson operator of the projection (SIPG on Q_{P-1}
+    with Neumann faces, or B M^{-1} B^T)."""
 
     def __init__(self, mesh, flow, poisson="sipg", stab=None):
         if mesh.P < 2:
@@ -89,7 +90,7 @@ class Discretization:
 
     # -------------------------------------------------------------- operators
     def A(self, nu):
-        """The assembled SIPG matrix of the viscous operator (Sec. 3.3, R3) for nodal nu."""
+        """The assembled SIPG matrix of the viscous operator (Sec. 3.3; penalty N^2 / h max(nu-, nu+)) for nodal nu."""
         if not self.flow.variable_nu():
             if self._A_const is None:
                 self._A_const = dg.sipg_matrix(self.mesh, self.Nv, self.flow.nu0, dirichlet=True)
@@ -97,7 +98,7 @@ class Discretization:
         return dg.sipg_matrix(self.mesh, self.Nv, nu, dirichlet=True)
 
     def Fc(self, v, vb):
-        """F_c = -div(v v) of Sec. 3.2 (LLF flux, over-integration; R7, R8)."""
+        """F_c = -div(v v) of Sec. 3.2 (LLF flux, over-integration on Gauss points)."""
         return self.conv(v, vb)
 
     def Fd1(self, v, nu, vb, A=None):
@@ -112,16 +113,16 @@ class Discretization:
         return out
 
     def divergence_nodal(self, v):
-        """sum_k D_k v_k, the nodal DG divergence (R9)."""
+        """sum_k D_k v_k, the nodal DG divergence (central lifting inside, own trace on the boundary)."""
         return sum(self.Dk[k] @ v[k] for k in range(self.d))
 
     def Fd3(self, v, nu):
-        """F_d3 = -grad(nu div v) of Sec. 3.2 with the nodal DG derivatives (R9)."""
+        """F_d3 = -grad(nu div v) of Sec. 3.2 with the nodal DG derivatives."""
         phi = nu * self.divergence_nodal(v)
         return np.stack([-(self.Dk[c] @ phi) for c in range(self.d)])
 
     def Fd2(self, v, nu):
-        """F_d2 = div(nu (grad v)^T) of Sec. 3.2 with the nodal DG derivatives (R9)."""
+        """F_d2 = div(nu (grad v)^T) of Sec. 3.2 with the nodal DG derivatives."""
         out = np.zeros((self.d, self.nv))
         for c in range(self.d):
             for k in range(self.d):
@@ -137,7 +138,7 @@ class Discretization:
         return stabilize(self.mesh, v, dt, *self.stab)
 
     def grad_p(self, psi):
-        """G psi = M^{-1} B^T psi, the DG gradient of the projection's correction (Alg. 3; R6)."""
+        """G psi = M^{-1} B^T psi, the DG gradient of the projection's correction (Alg. 3)."""
         g = self.BT @ psi
         return g.reshape(self.d, self.nv) / self.Mv[None, :]
 
@@ -266,7 +267,7 @@ def sdc_step(disc, M, K, predictor, v, t, dt, final_projection=None):
         vk.append(vn)
 
     def f_ex(vm, num, tq):
-        """F(t_q, v_q) = F_c + F_d1 + F_d2 + F_d3 + F_s at one sub-node (R13)."""
+        """F(t_q, v_q) = F_c + F_d1 + F_d2 + F_d3 + F_s at one sub-node t_q (Alg. 4's quadrature term)."""
         vb = disc.vb(tq)
         return disc.Fc(vm, vb) + disc.Fd2(vm, num) + disc.Fd3(vm, num)
 

@@ -43,7 +43,7 @@ SAFETY = 1.1          # lmax = SAFETY x the estimated largest eigenvalue of D^{-
 
 
 def level_points(P):
-    """Points per direction of the pressure levels, finest first: degree P-1, then halved (R23)."""
+    """Points per direction of the pressure levels, finest first: degree P-1, then halved."""
     deg = [P - 1]
     while deg[-1] > 1:
         deg.append(deg[-1] // 2)
@@ -51,14 +51,14 @@ def level_points(P):
 
 
 def interp_1d(Nc, Nf):
-    """I[i, j] = l_j(x_i): the GLL(Nc) cardinal polynomials at the GLL(Nf) nodes (R23)."""
+    """I[i, j] = l_j(x_i): the GLL(Nc) cardinal polynomials at the GLL(Nf) nodes."""
     xc, _ = gll.gll_nodes_weights(Nc)
     xf, _ = gll.gll_nodes_weights(Nf)
     return gll.lagrange_eval(xc, xf)
 
 
 def prolongation(mesh, Nc, Nf):
-    """Block-diagonal prolongation: the element-local tensor-product interpolation (R23)."""
+    """Block-diagonal prolongation: the element-local tensor-product interpolation."""
     Ie = dg.kron_dims([interp_1d(Nc, Nf)] * mesh.d)
     return sp.kron(sp.identity(mesh.ne, format="csr"), sp.csr_matrix(Ie), format="csr")
 
@@ -92,7 +92,7 @@ def chebyshev(A, dinv, b, x0, steps, lmax, ratio):
 
 class PMG:
     """The V-cycle of the pressure operator of a mesh with velocity degree P (the multigrid
-    preconditioner Sec. 3.3 names for the pressure solves; R23)."""
+    preconditioner Sec. 3.3 names for the pressure solves, in this library's form)."""
 
     def __init__(self, mesh, P, lmax=None, pre_post=PRE_POST, coarse_steps=COARSE_STEPS, ratio=RATIO,
                  coarse_ratio=COARSE_RATIO):
@@ -108,7 +108,7 @@ class PMG:
         self.lmax = list(lmax) if lmax is not None else [SAFETY * largest_eig(A, d) for A, d in zip(self.A, self.dinv)]
 
     def vcycle(self, r, level=0):
-        """z = B r: one V-cycle from level `level` applied to the residual r (R23)."""
+        """z = B r: one V-cycle from level `level` applied to the residual r."""
         A, dinv, lm = self.A[level], self.dinv[level], self.lmax[level]
         if level == len(self.N) - 1:
             return chebyshev(A, dinv, r, None, self.coarse_steps, lm, self.coarse_ratio)
@@ -121,7 +121,7 @@ class PMG:
 
 def largest_eig(A, dinv):
     """Largest eigenvalue of D^{-1} A (symmetric form D^{-1/2} A D^{-1/2}), by ARPACK (the
-    Chebyshev interval of R23)."""
+    Chebyshev smoothing interval)."""
     s = np.sqrt(dinv)
     S = sp.diags(s) @ A @ sp.diags(s)
     n = A.shape[0]

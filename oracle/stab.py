@@ -26,7 +26,7 @@ from . import dg, gll
 
 def mean_speed(mesh, v):
     """|u_K|: magnitude of the mass-weighted mean velocity of every element (the speed in the
-    penalty factors of R25)."""
+    penalty factors of the stabilisation)."""
     N = mesh.P + 1
     W = dg.volume_weights(mesh, N)
     u = np.asarray(v).reshape(mesh.d, mesh.ne, -1)
@@ -36,7 +36,8 @@ def mean_speed(mesh, v):
 
 def penalty_matrix(mesh, v, dt, zeta_d, zeta_c):
     """A_D + A_C (d components, component-major) for the element speeds of v: the divergence and
-    normal-jump penalties of the stabilisation Sec. 3.3 adds (R25)."""
+    normal-jump penalties of the stabilisation Sec. 3.3 adds (this library's reading of its
+    form: a penalised projection)."""
     d, N = mesh.d, mesh.P + 1
     nd = N ** d
     nv = mesh.ne * nd
@@ -87,7 +88,7 @@ def penalty_matrix(mesh, v, dt, zeta_d, zeta_c):
 
 def stabilize(mesh, v, dt, zeta_d, zeta_c):
     """v~ = (M + A_D + A_C)^{-1} M v for the velocity v ([d][nv]): the stabilised projection
-    (Sec. 3.3; R25)."""
+    (Sec. 3.3)."""
     d = mesh.d
     M = np.tile(dg.mass_diag(mesh, mesh.P + 1), d)
     A = (sp.diags(M) + penalty_matrix(mesh, v, dt, zeta_d, zeta_c)).tocsc()

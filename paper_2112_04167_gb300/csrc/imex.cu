@@ -1091,6 +1091,7 @@ imex_status pcg_mixed(imex_ctx* c, const imex_ctx::Seg& sg, Op64 op64, Op32 op32
 
 // small helper kernels local to this file
 namespace imex {
+// y = m x per component (mass products of the stage combinations, Alg. 3)
 __global__ void diag_mul_kernel(double* out, const double* x, const double* m, size_t n, int nsys) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n * nsys; i += (size_t)gridDim.x * blockDim.x)
     out[i] = x[i] * m[i % n];
@@ -3899,6 +3900,7 @@ imex_status imex_server_get_stats(const imex_server* sv, imex_server_stats* out)
 }  // extern "C"
 
 namespace imex {
+// FP32 -> FP64 copy (the FP64 refinement of the mixed-precision solves)
 __global__ void f2d_kernel(const float* in, double* out, size_t n) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
     out[i] = (double)in[i];

@@ -1,5 +1,5 @@
-// Segmented Jacobi-PCG kernels (the linear solves of Sec. 3: pressure Poisson and viscous
-// Helmholtz problems, both symmetric positive (semi-)definite, preconditioned by the
+// Segmented Jacobi-PCG kernels (the linear solves of Alg. 3 / Alg. 4, which Sec. 3.3 solves by
+// preconditioned CG: pressure Poisson and viscous Helmholtz problems, both symmetric positive (semi-)definite, preconditioned by the
 // operator's diagonal).
 //
 // The systems solved together (the vector components of one instance, or the instances of
@@ -194,7 +194,8 @@ template <> __device__ __forceinline__ double pick<double>(const double* d, cons
 __host__ __device__ constexpr int unroll_of(int vec) { return SEG_CHUNK / (vec * CG_THREADS); }
 
 // x += alpha p, r -= alpha A p, and the partial sums of the new residual; the last block
-// forms the new scalars and the next direction coefficient beta = rz_new / rz
+// forms the new scalars, the stopping test of Sec. 4 and the next direction
+// coefficient beta = rz_new / rz
 // FP32: at least 5 blocks per SM, so that a 1.4 M-node system's 686 blocks run in one wave
 // of 152 SMs (4 per SM left 78 blocks for a second wave)
 template <typename T>
@@ -323,6 +324,7 @@ seg_xr_kernel(T* __restrict__ x, T* __restrict__ r, const T* __restrict__ p, con
   if (threadIdx.x == 0) *counter = 0u;
 }
 
+// the Jacobi-preconditioned direction of the CG of Sec. 3.3 (projected for singular systems):
 // z' = D^{-1} (r - rmean) - zmean, p = z' + beta p (beta = 0 with restart = 1); projected
 // systems store r - rmean back
 template <typename T>
@@ -412,7 +414,7 @@ __device__ __forceinline__ T chunk_dot(const T* xs, const T* ys, int n) {
   return acc;
 }
 
-// dot per segment into out[s]
+// dot per segment into out[s] (the CG scalars and residual norms of Sec. 4)
 template <typename T>
 __global__ void __launch_bounds__(CG_THREADS)
 seg_dot_kernel(const T* __restrict__ x, const T* __restrict__ y, SegTable t, double* __restrict__ out,
@@ -427,7 +429,7 @@ seg_dot_kernel(const T* __restrict__ x, const T* __restrict__ y, SegTable t, dou
   if (threadIdx.x == 0) *counter = 0u;
 }
 
-// (p, A p) per running system into sc.pAp and the step length alpha = rz / pAp
+// (p, A p) per running system into sc.pAp and the CG step length alpha = rz / pAp
 template <typename T>
 __global__ void __launch_bounds__(CG_THREADS)
 seg_pap_kernel(const T* __restrict__ p, const T* __restrict__ Ap, SegTable t, CgScalars sc,
@@ -455,7 +457,8 @@ seg_pap_kernel(const T* __restrict__ p, const T* __restrict__ Ap, SegTable t, Cg
   if (threadIdx.x == 0) *counter = 0u;
 }
 
-// CG scalars of a new residual r for the running systems (all systems with reset = 1,
+// CG scalars of a new residual r for the running systems, with the stopping test of Sec. 4
+// (all systems with reset = 1,
 // which also restarts their iteration counts and convergence flags); also sum D^{-1}
 template <typename T>
 __global__ void __launch_bounds__(CG_THREADS)
@@ -501,7 +504,7 @@ seg_init_kernel(const T* __restrict__ r, const T* __restrict__ dinv, SegTable t,
   if (threadIdx.x == 0) *counter = 0u;
 }
 
-// per-segment mean removal: x -= mean over the segment (two passes)
+// per-segment mean removal of the singular problems: x -= mean over the segment (two passes)
 __global__ void __launch_bounds__(CG_THREADS)
 seg_sum_kernel(const double* __restrict__ x, SegTable t, double* __restrict__ out, double* __restrict__ partial,
                unsigned int* __restrict__ counter) {
@@ -515,7 +518,7 @@ seg_sum_kernel(const double* __restrict__ x, SegTable t, double* __restrict__ ou
   seg_totals<1>(t, partial, [&](int q, const double* tot) { out[q] = tot[0] / (double)t.len[q]; });
   if (threadIdx.x == 0) *counter = 0u;
 }
-// weighted mean per segment: out[q] = sum w x / sum w
+// weighted mean per segment (the mass-weighted pressure mean): out[q] = sum w x / sum w
 __global__ void __launch_bounds__(CG_THREADS)
 seg_wsum_kernel(const double* __restrict__ x, const double* __restrict__ w, SegTable t, double* __restrict__ out,
                 double* __restrict__ partial, unsigned int* __restrict__ counter) {
@@ -536,6 +539,7 @@ seg_wsum_kernel(const double* __restrict__ x, const double* __restrict__ w, SegT
   seg_totals<2>(t, partial, [&](int q, const double* tot) { out[q] = tot[1] != 0.0 ? tot[0] / tot[1] : 0.0; });
   if (threadIdx.x == 0) *counter = 0u;
 }
+// x -= the segment's mean (the mean removal of the singular problems)
 __global__ void __launch_bounds__(CG_THREADS)
 seg_sub_kernel(double* __restrict__ x, SegTable t, const double* __restrict__ mean) {
   const SegBlock c = chunk_of(t);
@@ -554,6 +558,8 @@ seg_rproj_kernel(T* __restrict__ r, SegTable t, CgScalars sc) {
   for (int i = threadIdx.x; i < c.n; i += CG_THREADS) rs[i] -= rm;
 }
 
+// (r, z) and sum z of the V-cycle-preconditioned CG: the last block forms beta, the
+// mean of z (projected systems) and the breakdown flag
 template <typename T>
 __global__ void __launch_bounds__(CG_THREADS)
 seg_rz_kernel(const T* __restrict__ r, const T* __restrict__ z, SegTable t, CgScalars sc,
@@ -595,6 +601,7 @@ seg_rz_kernel(const T* __restrict__ r, const T* __restrict__ z, SegTable t, CgSc
   if (threadIdx.x == 0) *counter = 0u;
 }
 
+// direction of the V-cycle-preconditioned CG: p = z - mean z + beta p
 template <typename T>
 __global__ void __launch_bounds__(CG_THREADS)
 seg_pz_kernel(T* __restrict__ p, const T* __restrict__ z, SegTable t, CgScalars sc, int restart) {

@@ -145,6 +145,7 @@ __device__ __forceinline__ void div_pass(const T* src, T* dst, T hm, const T* sI
     contract_ct<T, S0, S1, S2, M, NP, 1, NP, false>(src + (1 + k) * ND, dst + (1 + k) * ND, sIp, t, nt);
 }
 
+// the weak divergence of the projection's Poisson right-hand side (Alg. 3, Sec. 3.3)
 template <typename T, int D, int NV, typename TS = T>
 __global__ void dg_div_kernel(Geom g, DivArgs<TS> a) {
   using TT = typename TableType<T>::type;
@@ -216,6 +217,7 @@ __global__ void dg_div_kernel(Geom g, DivArgs<TS> a) {
 // ----------------------------------------------------------------------------
 // DG gradient of a pressure field: out_k = base_k + coef * (d_k psi - lifting of [psi])
 // ----------------------------------------------------------------------------
+// the DG gradient M^{-1} B^T psi of the projection's correction (Alg. 3)
 template <typename T, int D, int NV, typename TS = T>
 __global__ void dg_grad_kernel(Geom g, GradArgs<TS> a) {
   using TT = typename TableType<T>::type;
@@ -344,6 +346,7 @@ __device__ __forceinline__ T nodal_deriv(const Geom& g, const int* ec, int e, co
   return val;
 }
 
+// the nodal DG derivatives of F_d2, F_d3 (Sec. 3.2; central lifting inside, own trace on the boundary)
 // T: arithmetic type (double, or the float-float ff); TS: storage type of the fields
 template <typename T, int D, int N, typename TS = T>
 __global__ void __launch_bounds__(ipow(N, D)) dg_deriv_kernel(Geom g, DerivArgs<TS> a) {
@@ -424,6 +427,8 @@ struct ConvShape {
 };
 
 
+// the convective term F_c = -div(v v) of Sec. 3.2 as Sec. 3.3 discretises it: LLF flux with the
+// pointwise max |v.n|, over-integration on ceil(3N/2) Gauss points per direction
 // T: arithmetic type (double, float, or the float-float ff for FP64-class accuracy on the
 // FP32 pipes); TS: storage type of the fields (double for ff)
 template <typename T, int D, int N, typename TS = T>

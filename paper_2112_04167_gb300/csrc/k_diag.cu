@@ -17,7 +17,7 @@
 namespace imex {
 namespace {
 
-// per element: sum over the nodes of W_q nu_q sum_{c,k} (d v_c / d x_k)^2
+// per element: sum over the nodes of W_q nu_q sum_{c,k} (d v_c / d x_k)^2 (eps of Sec. 4.3)
 template <int D, int N>
 __global__ void dissipation_kernel(Geom g, const double* __restrict__ v, long long stride, const double* __restrict__ nu,
                                    double nu0, double* __restrict__ out) {
@@ -57,6 +57,7 @@ __global__ void dissipation_kernel(Geom g, const double* __restrict__ v, long lo
 }
 
 // v on the regular grid (component c of point i at out[c * M^D + i], x fastest), complex
+// (the grid of E(k), Sec. 4.3)
 template <int D, int N>
 __global__ void regular_grid_kernel(Geom g, const double* __restrict__ v, long long stride, int M,
                                     double2* __restrict__ out) {
@@ -101,7 +102,7 @@ __global__ void regular_grid_kernel(Geom g, const double* __restrict__ v, long l
 }
 
 // forward DFT of every grid line along `axis` (length M, a power of two <= 1024): the line
-// loaded into shared memory in bit-reversed order, log2 M butterfly stages
+// loaded into shared memory in bit-reversed order, log2 M butterfly stages (E(k))
 __global__ void fft_lines_kernel(double2* __restrict__ a, int M, int logM, int D, int axis) {
   extern __shared__ double2 sl[];
   size_t axstride = 1;
@@ -139,6 +140,7 @@ __global__ void fft_lines_kernel(double2* __restrict__ a, int M, int logM, int D
 }
 
 // per block: shell sums of |a|^2 (all components), kmax shells, into part[block][kmax]
+// (E(k) of Sec. 4.3)
 __global__ void shell_bin_kernel(const double2* __restrict__ a, int M, int D, int kmax, double scale,
                                  double* __restrict__ part) {
   extern __shared__ double hist[];
@@ -168,6 +170,7 @@ __global__ void shell_bin_kernel(const double2* __restrict__ a, int M, int D, in
   for (int k = threadIdx.x; k < kmax; k += blockDim.x) part[(size_t)blockIdx.x * kmax + k] = hist[k];
 }
 
+// fixed-order total of the blocks' shell sums into E(k) (Sec. 4.3)
 __global__ void shell_sum_kernel(const double* __restrict__ part, int nblocks, int kmax, double* __restrict__ E) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= kmax) return;

@@ -96,6 +96,7 @@ __device__ void forcing_vv(const double* p, const double* X, double t, double* f
   }
 }
 
+// nodal evaluation of a closed-form flow, viscosity law or forcing (Sec. 4)
 template <int D, int N>
 __global__ void field_kernel(Geom g, int what, FieldSpec fs, double t, const double* __restrict__ v,
                              long long stride, double* __restrict__ out) {

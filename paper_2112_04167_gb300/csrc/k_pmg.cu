@@ -35,7 +35,8 @@ __host__ __device__ constexpr int xfer_epb() {
   return TileN<D, NF>::n >= XF_THREADS ? 1 : XF_THREADS / TileN<D, NF>::n;
 }
 
-// MODE 0: xf += P xc (prolongation and add); MODE 1: rc = P^T (bf - axf) (restriction)
+// MODE 0: xf += P xc (prolongation and add); MODE 1: rc = P^T (bf - axf) (restriction): the
+// GLL transfers between p-multigrid levels
 template <typename T, int D, int NF, int NC, int MODE>
 __global__ void __launch_bounds__(XF_THREADS)
 pmg_transfer_kernel(int ne, const T* __restrict__ in0, const T* __restrict__ in1, T* __restrict__ out, Interp1D I,
@@ -166,6 +167,7 @@ cheb_first_proj_kernel(T* __restrict__ x, T* __restrict__ d, T* __restrict__ r, 
   }
 }
 
+// a further Chebyshev step: r -= A d, d = c1 d + c2 D^{-1} r, x += d
 template <typename T>
 __global__ void __launch_bounds__(256)
 cheb_next_kernel(T* __restrict__ x, T* __restrict__ d, T* __restrict__ r, const T* __restrict__ ad,
@@ -181,6 +183,7 @@ cheb_next_kernel(T* __restrict__ x, T* __restrict__ d, T* __restrict__ r, const 
   }
 }
 
+// y = s a b elementwise (the power iteration of the Chebyshev bounds)
 template <typename T>
 __global__ void __launch_bounds__(256)
 vec_mul_kernel(T* __restrict__ y, const T* __restrict__ a, const T* __restrict__ b, T s, size_t n) {

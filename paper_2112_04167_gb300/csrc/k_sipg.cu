@@ -25,6 +25,8 @@ struct SipgShape {
   static constexpr int THREADS = EPB * ND;
 };
 
+// the SIPG operator of Sec. 3.3 (penalty N^2 / h max(nu-, nu+)), generic form: y = alpha M x + beta (A(nu) x -
+// r_b(g)) for any face kinds and a nodal or constant viscosity
 template <typename T, int D, int N>
 __global__ void __launch_bounds__(SipgShape<T, D, N>::THREADS)
 sipg_apply_kernel(Geom g, SipgArgs<T> a) {
@@ -246,6 +248,8 @@ constexpr size_t sipg3_smem() {
   return sizeof(T) * (size_t)(N * N + N + 3 * S::EPB * S::ND + 3 * S::EPB * 4 * S::NN);
 }
 
+// the SIPG operator of Sec. 3.3 in 3D, variable or constant viscosity: gradient, flux and
+// transposed derivative passes
 template <typename T, int N, bool VARNU>
 __global__ void __launch_bounds__(Sipg3Shape<N>::THREADS)
 sipg3_apply_kernel(Geom g, SipgArgs<T> a) {
@@ -449,6 +453,8 @@ constexpr size_t sipg3c_smem() {
   return sizeof(T) * (size_t)(27 * N * N + 36 * N + 6 * N + 3 * N + S::EPB * S::ND + S::EPB * 8 * S::NN);
 }
 
+// the constant-viscosity SIPG operator of Sec. 3.3 in 3D with Dirichlet / Neumann sides,
+// from the line operators of every face kind
 template <typename T, int N>
 __global__ void __launch_bounds__(Sipg3cShape<N>::THREADS)
 sipg3c_apply_kernel(Geom g, SipgArgs<T> a) {
@@ -616,6 +622,7 @@ constexpr size_t sipg2c_smem() {
   return sizeof(T) * (size_t)(18 * N * N + 24 * N + 4 * N + 2 * N + S::EPB * S::NN + S::EPB * 8 * N);
 }
 
+// the constant-viscosity SIPG operator of Sec. 3.3 in 2D with Dirichlet / Neumann sides
 template <typename T, int N>
 __global__ void __launch_bounds__(Sipg2cShape<N>::THREADS)
 sipg2c_apply_kernel(Geom g, SipgArgs<T> a) {
@@ -730,7 +737,8 @@ sipg2c_apply_kernel(Geom g, SipgArgs<T> a) {
   if (a.dot_out) fused_dot_finish(a, red);
 }
 
-// Diagonal of alpha M + beta A (Jacobi preconditioner).
+// Diagonal of alpha M + beta A (Jacobi preconditioner of the CG solves of Sec. 3.3; the
+// self-neighbour term of an element that meets itself across a periodic direction).
 template <typename T, int D, int N>
 __global__ void __launch_bounds__(SipgShape<T, D, N>::THREADS)
 sipg_diag_kernel(Geom g, SipgArgs<T> a) {

@@ -41,6 +41,7 @@ struct Sipg2lShape {
   static constexpr int NP = ((N + VEC - 1) / VEC) * VEC;
 };
 
+// The periodic constant-viscosity SIPG operator of Sec. 3.3 in 2D by line-owner passes.
 // EP: the output stage, fixed at compile time for the FP32 applies (as in 3D), which then
 // write the x pass's results into the accumulator tile and run the stage by columns
 template <typename T, int N, int V = 0, int EP = SIPG_EP_ANY>
@@ -449,6 +450,8 @@ __device__ __forceinline__ T sipg3l_group(const Geom& g, const SipgArgs<TS>& a, 
 __host__ __device__ constexpr int sipg3p_minb(int V, bool f32, bool isff) {
   return V == 2 ? 1 : (f32 ? IMEX_SIPG3P_MINB : (isff ? 2 : 1));
 }
+// The periodic constant-viscosity SIPG operator of Sec. 3.3 in 3D by line-owner passes (the
+// CG and V-cycle applies; the Chebyshev step fused in the output stage).
 // XFF: the input is a.xff, float-float pairs converted from a.x beforehand (float-float
 // applies: no FP64 conversions in the kernel)
 template <typename T, int N, typename TS = T, int V = 0, int EP = SIPG_EP_ANY, bool XFF = false>
@@ -571,6 +574,8 @@ __device__ __forceinline__ void persist_totals(const double* partial, int q0, do
   for (int k = 0; k < K; ++k) out[k] = red[K * blockDim.x + k];
 }
 
+// the whole FP32 Jacobi-preconditioned pressure CG of Alg. 3's projection in one cooperative
+// launch (opt-in; the projected iteration of the singular system)
 template <int N>
 __global__ void __launch_bounds__(Sipg3pShape<float, N>::THREADS, (N <= 8) ? 5 : 1)
 pcg_persist_kernel(Geom g, SipgArgs<float> a, PcgPersist q, CgScalars sc, int maxit) {

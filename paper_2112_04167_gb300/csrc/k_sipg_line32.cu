@@ -115,6 +115,8 @@ __device__ __forceinline__ float pmgc_apply_node(const PmgcNode& c, float dl0, f
   return out;
 }
 
+// all Chebyshev steps of the FP32 coarsest (degree-1) p-multigrid level on one thread-block
+// cluster (the three-term Chebyshev recurrence)
 __global__ void __launch_bounds__(PMGC_THREADS) pmg_coarse_cluster_kernel(Geom g, const float* __restrict__ b,
                                                                           const float* __restrict__ dinv,
                                                                           float* __restrict__ x, CoarseCheb cc) {

@@ -20,6 +20,7 @@
 namespace imex {
 namespace {
 
+// element mean speeds |u_K| of the stabilisation penalties (Sec. 3.3)
 template <int D, int N>
 __global__ void stab_speed_kernel(Geom g, const double* __restrict__ v, long long stride, double* __restrict__ speed) {
   constexpr int ND = ipow(N, D);
@@ -45,6 +46,7 @@ __global__ void stab_speed_kernel(Geom g, const double* __restrict__ v, long lon
   }
 }
 
+// y = (M + A_D + A_C) u, the operator of the stabilised projection (Sec. 3.3)
 template <int D, int N>
 __global__ void stab_apply_kernel(Geom g, const double* __restrict__ u, double* __restrict__ y, long long stride,
                                   const double* __restrict__ speed, double zd, double zc, double dt, int P) {

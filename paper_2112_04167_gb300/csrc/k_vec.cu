@@ -43,6 +43,8 @@ void smem_limit_once(const void* kernel, int bytes) {
 }
 long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
 
+// out = sum_j c_j x_j: the stage extrapolation, the Helmholtz right-hand side and the final
+// assembly of Alg. 3 (its stage sums in FP64), the SDC quadrature sums of Alg. 4
 __global__ void lincomb_kernel(double* __restrict__ out, LinComb lc, size_t n) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
     double s = 0.0;
@@ -106,6 +108,8 @@ __device__ __forceinline__ double block_max(double v) {
   return v;
 }
 
+// per-block partial dot products of nsys systems (the CG dots and the relative residual
+// norms of the stopping rule of Sec. 4), FP64 accumulation
 template <typename T>
 __global__ void dot_partial_kernel(const T* __restrict__ x, const T* __restrict__ y, size_t n,
                                    long long stride, double* __restrict__ partial) {
@@ -119,7 +123,7 @@ __global__ void dot_partial_kernel(const T* __restrict__ x, const T* __restrict_
   if (threadIdx.x == 0) partial[(size_t)s * gridDim.x + blockIdx.x] = acc;
 }
 
-// fixed-order final sum of nblocks partials per system
+// fixed-order final sum of nblocks partials per system (deterministic)
 __global__ void finish_sum_kernel(const double* __restrict__ partial, int nblocks, double* __restrict__ dst) {
   const int s = blockIdx.x;
   double acc = 0.0;
@@ -146,6 +150,7 @@ int dot_batched_f(const float* x, const float* y, size_t n, long long stride, in
   return dot_impl<float>(x, y, n, stride, nsys, partial, nblocks, dst, st);
 }
 
+// per-block partial sums (the mean removal of the singular pressure problems)
 __global__ void sum_partial_kernel(const double* __restrict__ x, size_t n, double* __restrict__ partial) {
   double acc = 0.0;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
@@ -159,7 +164,8 @@ int reduce_sum(const double* x, size_t n, double* partial, int nblocks, double* 
   return 0;
 }
 
-// max |x| with NaN propagation: a NaN entry makes the result NaN
+// max |x| with NaN propagation: a NaN entry makes the result NaN (the instability check,
+// Sec. 4.2.3)
 __global__ void maxabs_partial_kernel(const double* __restrict__ x, size_t n, double* __restrict__ partial) {
   double m = 0.0;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
@@ -175,6 +181,7 @@ __global__ void maxabs_partial_kernel(const double* __restrict__ x, size_t n, do
   __syncthreads();
   if (threadIdx.x == 0) partial[blockIdx.x] = has_nan ? nan("") : m;
 }
+// max over the partials, NaN propagated (the instability check of Sec. 4.2.3)
 __global__ void finish_max_kernel(const double* __restrict__ partial, int nblocks, double* __restrict__ dst) {
   __shared__ int has_nan;
   if (threadIdx.x == 0) has_nan = 0;
@@ -194,7 +201,7 @@ int reduce_max_abs(const double* x, size_t n, double* partial, int nblocks, doub
   return 0;
 }
 
-// x -= num/den (w == nullptr) or x -= (num/den) elementwise constant
+// x -= num/den (w == nullptr) or x -= (num/den) elementwise constant (mean removal of the singular pressure problems)
 __global__ void subtract_scalar_kernel(double* x, size_t n, const double* num, const double* den) {
   const double c = num[0] / den[0];
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
@@ -206,6 +213,7 @@ void subtract_scaled_scalar(double* x, size_t n, const double* num, const double
   IMEX_COUNTED(subtract_scalar_kernel<<<grid_for(n, 256), 256, 0, st>>>(x, n, num, den));
 }
 
+// FP64 -> FP32 and FP32 correction added to an FP64 iterate: the FP64 refinement of the mixed-precision solves
 __global__ void d2f_kernel(const double* in, float* out, size_t n) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
     out[i] = (float)in[i];
@@ -221,6 +229,7 @@ void axpy_f2d(double* y, const float* x, size_t n, cudaStream_t st) {
   IMEX_COUNTED(axpy_f2d_kernel<<<grid_for(n, 256), 256, 0, st>>>(y, x, n));
 }
 
+// d = 1 / d: the Jacobi preconditioner of the CG solves (Sec. 3.3) from an operator diagonal
 template <typename T>
 __global__ void recip_kernel(T* d, size_t n) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
@@ -231,7 +240,8 @@ void reciprocal(T* d, size_t n, cudaStream_t st) {
   IMEX_COUNTED(recip_kernel<T><<<grid_for(n, 256), 256, 0, st>>>(d, n));
 }
 
-// Jacobi diagonal of M + gamma A for a viscosity that is constant per element: from the
+// Jacobi diagonal of M + gamma A (the Helmholtz operator of an Alg. 3 stage) for a viscosity
+// that is constant per element: from the
 // cached diagonals of M and of A (unit factor), d = 1 / (m + gamma dt_e k), with dt_e the
 // element's own time step in a batch group (edt) and 1 otherwise
 __global__ void helm_diag_kernel(double* __restrict__ d, const double* __restrict__ m, const double* __restrict__ k,
@@ -247,7 +257,7 @@ void helm_diag(double* d, const double* m, const double* k, double gamma, const 
   IMEX_COUNTED(helm_diag_kernel<<<grid_for(n, 256), 256, 0, st>>>(d, m, k, gamma, edt, nd, n));
 }
 
-// Helmholtz operator and F_d1 from K x (the SIPG operator with unit factor applied to the d
+// Helmholtz operator and F_d1 of Alg. 3 from K x (the SIPG operator with unit factor applied to the d
 // components of x, stride n each): mode 0: y = m x + gamma dt_e K x (dt_e = edt[i / nd], or
 // 1 when edt is null); mode 1: y = -K x / m
 __global__ void kx_combine_kernel(double* __restrict__ y, const double* __restrict__ x, const double* __restrict__ m,
@@ -299,6 +309,7 @@ static __device__ __align__(256) double g_noalloc_scratch[kNoallocSlots + 32];
 std::mutex g_noalloc_mu;
 double* g_noalloc_ptr[kNoallocMaxDevices] = {nullptr};
 
+// The allocation-free reduction entry point (no counterpart in the paper).
 // block b reduces exactly the elements [256 b, 256 b + 256) into partial[b]
 __global__ void noalloc_chunk_kernel(int op, const double* __restrict__ x, const double* __restrict__ y,
                                      long long n, double* __restrict__ partial) {
@@ -324,7 +335,8 @@ __global__ void noalloc_chunk_kernel(int op, const double* __restrict__ x, const
   }
 }
 
-// one block: fixed-order combination of nb partial sums into out[0]
+// one block: fixed-order combination of nb partial sums into out[0] (allocation-free entry;
+// no counterpart in the paper)
 __global__ void noalloc_finish_kernel(int op, const double* __restrict__ partial, int nb, double* __restrict__ out) {
   if (op == IMEX_REDUCE_MAXABS) {
     __shared__ int has_nan;

@@ -4,7 +4,7 @@ for the host and compared with the oracle's independent construction (numpy's Le
 roots and product-form Lagrange polynomials, oracle/gll.py) for every supported N = 2..9:
 GLL points and weights, differentiation matrices, the pressure basis (N-1 GLL points)
 and its derivative at the velocity points, the Gauss over-integration points' weights,
-interpolation and derivative matrices (R7: Q = ceil(3N/2) points), the FP32 copies, the
+interpolation and derivative matrices (Q = ceil(3N/2) points), the FP32 copies, the
 p-multigrid prolongation factors between GLL sets, and the one-dimensional SIPG line
 operators (own blocks and neighbour couplings of interior, Dirichlet and Neumann faces)
 against the direction-x factor of the oracle's assembled 2D SIPG matrix."""

@@ -1,6 +1,6 @@
 """The float-float arithmetic the mixed form's FP64-class kernels execute (csrc/ff.cuh: sums
 from TwoSum / FastTwoSum, products with the exact FMA error term, one-correction division,
-the compensated Dot2 dot product; R22), compiled for the host from the same header and
+the compensated Dot2 dot product), compiled for the host from the same header and
 checked against exact rational arithmetic on seeded operands of mixed magnitudes and signs,
 near cancellations included.  u = 2^-24 is the FP32 unit roundoff; a float-float result is
 hi + lo with hi the FP32 rounding of hi + lo (normalised).  Bounds, in units of u^2 = 2^-48:
