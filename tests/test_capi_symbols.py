@@ -46,3 +46,24 @@ def _load_fresh(imex, path):
         return imex.load(path)
     finally:
         imex._lib = saved
+
+
+def test_build_targets_sm103a_in_tree(monkeypatch):
+    """Every translation unit compiles for sm_103a alone (one -gencode), with line info, into
+    the package's own _lib directory; the C++ unit is compiled as CUDA."""
+    from paper_2112_04167_gb300 import build
+    assert build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+    assert os.path.dirname(build.LIB) == os.path.join(ROOT, "paper_2112_04167_gb300", "_lib")
+    seen = []
+
+    class R:
+        returncode, stdout, stderr = 0, "", ""
+
+    monkeypatch.setattr(build.subprocess, "run", lambda cmd, **kw: (seen.append(cmd), R())[1])
+    for src in ("k_sipg.cu", "basis.cpp"):
+        build._compile(src, "nvcc", [])
+    for cmd in seen:
+        assert cmd.count("-gencode") == 1 and "arch=compute_103a,code=sm_103a" in cmd
+        assert "-lineinfo" in cmd and "-O3" in cmd
+    assert seen[1][-2:] == ["-x", "cu"]
+    assert all(s in build.SOURCES for s in ("imex.cu", "k_sipg_line32.cu", "k_sipg_line64.cu", "basis.cpp"))
